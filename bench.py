@@ -1,0 +1,352 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the EA spin-glass Monte Carlo engine on B300.
+
+Workload: Gaussian couplings, L = 8 and L = 12, h in {0.1, 0.2, 0.3}, 512
+disorder samples per (L, h), 2 replicas x 24 temperatures geometric in
+0.5-1.6, replica exchange and overlap measurement after every sweep. All six
+ensembles run batched (one CUDA graph launch per step, one persistent fused
+kernel per ensemble on parallel graph branches). A step is SWEEPS_PER_STEP
+sweeps of every chain of every sample, exchange and measurement included.
+
+Metric: spin-flip attempts per ns (one attempt = one Metropolis proposal on
+one site of one chain). Printed as one JSON line by rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (the plain sequential restatement of the
+method) on the host cores for the same metric, on a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "spin-flip attempts/ns on 1 B300, batched vs plain, oracle-matched; p50/p99 lat"
+UNIT = "spin-flip attempts/ns"
+LS = (8, 12)
+HS = (0.1, 0.2, 0.3)
+N_SAMPLES = 512
+N_T = 24
+T_MIN, T_MAX = 0.5, 1.6
+SWEEPS_PER_STEP = 256
+B_ALG_CONST = 2.0     # int8 spin read + write per attempt, bytes
+B_ALG_COUPLING = 12.0  # three FP32 bonds per site, shared by the 2*N_T chains
+WORKLOAD = ("gaussian EA 3D, L=8 and 12 x h=0.1,0.2,0.3, 512 samples each, "
+            "2 replicas x 24 T geometric 0.5-1.6, exchange+measure every sweep")
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=24)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--sweeps-per-step", type=int, default=SWEEPS_PER_STEP)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def attempts_per_sweep() -> int:
+    return sum(L ** 3 * 2 * N_T * N_SAMPLES for L in LS for _ in HS)
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.gpu), "-lms", "200"], stdout=open(self.path, "w"),
+                stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            self.proc.wait(timeout=10)
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return None
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for _, _, flags in rows for k, f in enumerate(flags)
+                          if f.lower() == "active"})
+        loaded = [r[0] for r in rows]
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(r[1] for r in rows),
+                "samples": len(rows), "reasons": reasons}
+
+
+def make_ensembles(sgmc, inputs, rank, stream, **opt):
+    T = inputs.geometric_ladder(T_MIN, T_MAX, N_T)
+    ens, host = [], []
+    for li, L in enumerate(LS):
+        for hi, h in enumerate(HS):
+            seed = 1000 * rank + 10 * li + hi + 1
+            J, s0 = inputs.make_instance("gauss", L, N_SAMPLES, N_T, seed=seed)
+            ens.append(sgmc.Ensemble(L, h, T, "gauss", N_SAMPLES, seed, J=J, spins=s0,
+                                     stream=stream, n_therm=0, **opt))
+            host.append(s0)
+    return ens, host
+
+
+def cpu_baseline(budget_s: float):
+    """The oracle, as it stands, on a bounded sample of the workload: L = 12,
+    Gaussian, h = 0.2, 2 x 24 temperatures, one sample per host core."""
+    from oracle import oracle as orc
+    from paper_1403_4560_b300 import inputs
+
+    cores = os.cpu_count() or 1
+    L = 12
+    T = inputs.geometric_ladder(T_MIN, T_MAX, N_T)
+    J, s0 = inputs.make_instance("gauss", L, cores, N_T, seed=99)
+    st = orc.State(L, T, 0.2, True, seed=99, J=J, spins=s0, n_therm=0)
+    t0 = time.perf_counter()
+    st.run(1, threads=cores)
+    t1 = time.perf_counter() - t0
+    n = max(1, min(500, int(budget_s / max(t1, 1e-3)) - 1))
+    t0 = time.perf_counter()
+    st.run(n, threads=cores)
+    dt = time.perf_counter() - t0
+    att = L ** 3 * 2 * N_T * cores * n
+    return {"value": att / (dt * 1e9), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"L=12 gaussian, 2x24 T, h=0.2, {cores} samples x {n} sweeps "
+                      f"(exchange+measure every sweep), {dt:.1f} s"}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    cb = cpu_baseline(args.cpu_seconds)
+    steps = []
+    from oracle import oracle as orc
+    from paper_1403_4560_b300 import inputs
+    cores = cb["cores"]
+    T = inputs.geometric_ladder(T_MIN, T_MAX, N_T)
+    J, s0 = inputs.make_instance("gauss", 12, cores, N_T, seed=5)
+    st = orc.State(12, T, 0.2, True, seed=5, J=J, spins=s0, n_therm=0)
+    for _ in range(args.warmup):
+        st.run(1, threads=cores)
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        st.run(1, threads=cores)
+        steps.append(time.perf_counter() - t0)
+    att = 12 ** 3 * 2 * N_T * cores
+    value = att * len(steps) / (sum(steps) * 1e9)
+    cb["value"] = value
+    cb["sample"] = (f"each step: 1 sweep of {cores} L=12 gaussian samples, 2x24 T, "
+                    f"exchange+measure, on {cores} host cores")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(steps) / len(steps), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "fp32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "reference": "CPU oracle (plain sequential C)"},
+            "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    from paper_1403_4560_b300 import build as sgbuild
+    from paper_1403_4560_b300 import inputs, sgmc
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        sgbuild.build()
+    if dist is not None:
+        dist.barrier()
+    sgmc.lib()
+    stream = torch.cuda.current_stream()
+    K, W, nsw = args.steps, args.warmup, args.sweeps_per_step
+    ens, host_spins = make_ensembles(sgmc, inputs, rank, stream)
+    n_launch_per_step = 2 * len(ens)  # fused kernel + sweep-counter update per ensemble
+
+    def step():
+        sgmc.sweep_batch(ens, nsw, use_graph=True)
+
+    for _ in range(W):
+        step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        start.record(stream)
+        for _ in range(K):
+            step()
+        stop.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    ms = start.elapsed_time(stop)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    for e in ens:
+        e.synchronize()
+    att_total = attempts_per_sweep() * nsw * K * world
+    value = att_total / (ms * 1e6)
+
+    # dominant kernel alone: L = 12 fused kernel, timed on its launch stream
+    dom = ens[len(HS)]
+    dom_att = dom.info().attempts_per_sweep * nsw
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    reps = 3
+    dom.sweep(nsw)
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for _ in range(reps):
+        dom.sweep(nsw)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    dom_ms = ev[0].elapsed_time(ev[1]) / reps
+    b_alg = B_ALG_CONST + B_ALG_COUPLING / (2 * N_T)
+    achieved = b_alg * dom_att / (dom_ms * 1e6)  # GB/s
+    peak, peak_kind = peaks()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "int8_run_kernel<L=12, gauss>",
+                "b_alg_bytes_per_attempt": b_alg, "peak_kind": peak_kind,
+                "attempts_per_ns": dom_att / (dom_ms * 1e6)}
+
+    plain = None
+    if not args.no_plain and rank == 0:
+        pens, _ = make_ensembles(sgmc, inputs, rank, stream, sweeps_per_launch=1)
+        for e in pens:
+            e.sweep(1)
+        torch.cuda.synchronize()
+        nplain = 16
+        ev[0].record(stream)
+        for e in pens:
+            e.sweep(nplain)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        pms = ev[0].elapsed_time(ev[1])
+        plain = {"value": attempts_per_sweep() * nplain / (pms * 1e6), "unit": UNIT,
+                 "how": "one launch per sweep per ensemble, ensembles one after another"}
+        for e in pens:
+            e.close()
+
+    e2e = None
+    if not args.no_e2e:
+        pinned = [torch.from_numpy(s).pin_memory().numpy() for s in host_spins]
+        n_e2e = max(2, min(K, 6))
+        acc_bytes = 0
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            for e, s in zip(ens, pinned):
+                e.set_spins(s)
+            step()
+            acc_bytes = 0
+            for e in ens:
+                acc_bytes += e.accumulators().nbytes
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        if dist is not None:
+            t = torch.tensor([dt], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": attempts_per_sweep() * nsw * n_e2e * world / (dt * 1e9), "unit": UNIT,
+               "h2d_bytes_per_step": int(sum(s.nbytes for s in pinned)),
+               "d2h_bytes_per_step": int(acc_bytes), "steps": n_e2e,
+               "how": "per step: sg_set_spins from pinned host spins for all 6 ensembles, "
+                      "batched sweeps, sg_get_accumulators to host"}
+
+    cb = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cb = cpu_baseline(args.cpu_seconds)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+                "warmup": W, "ms_per_step": ms / K, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "fp32",
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD, "sweeps_per_step": nsw,
+                           "parallelism": f"independent samples, {world} GPU(s)",
+                           "l2": "state+couplings 206 MB per GPU, larger than L2",
+                           "batched": "one CUDA graph per step, 6 parallel branches"},
+                "gpu_launches": n_launch_per_step * K,
+                "roofline": roofline, "plain": plain, "e2e": e2e, "cpu_baseline": cb,
+                "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    for e in ens:
+        e.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

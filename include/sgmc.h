@@ -1,0 +1,241 @@
+/*
+ * sgmc.h -- C ABI of the B300 Monte Carlo engine for the three-dimensional
+ * Edwards-Anderson spin glass in a uniform field (arXiv:1403.4560).
+ *
+ * What the engine computes (paper, "Methods and Measured Quantities"):
+ *   H = -sum_<ij> J_ij S_i S_j - h sum_i S_i on an L^3 simple cubic lattice
+ *   with periodic boundaries (eq. Hamiltonian); couplings bimodal +-1 or
+ *   Gaussian N(0,1); two replicas at each of N_T temperatures joined by
+ *   parallel tempering (methods section); checkerboard single-spin Metropolis
+ *   sweeps; the overlap q(k) (eq. overlap) accumulated per sample and
+ *   temperature, from which the Binder ratio (eq. binder), chi_SG(k)
+ *   (eq. chi), the correlation length (eq. corr) and R12 (eq. r12) follow.
+ *
+ * Conventions shared by every call:
+ *   - Host arrays use the canonical layouts below; device state is private.
+ *       couplings  float  [S][3][N]      J[s][d][i] joins i and i + e_d (mod L),
+ *                                        d = 0,1,2 for x,y,z; N = L^3,
+ *                                        i = x + L*(y + L*z)
+ *       spins      int8   [S][2][n_T][N] +1 / -1 per sample, replica, slot
+ *                                        (slot t holds temperature T[t]), site
+ *       energies   int64  [S][2][n_T]    B = sum_bonds (J/qJ) s s (qJ = 1 for
+ *                                        +-J, 2^-17 for Gaussian couplings);
+ *                                        M = sum_i s_i;  E = -(qJ*B + h*M)
+ *       accumulators double [S][n_T][40] sweep sums of the measurements; the
+ *                                        index table is listed at
+ *                                        SG_ACC_* below
+ *   - Every call that launches work is asynchronous on the ensemble's CUDA
+ *     stream (the cudaStream_t passed at creation, 0 = legacy default
+ *     stream). Calls that return host data synchronise that stream first.
+ *   - No call throws or aborts. Errors come back as sg_status codes; device
+ *     faults detected by the kernels are reported through a status word
+ *     that sg_synchronize() reads.
+ *   - One ensemble must not be used from two host threads at once.
+ *   - Results depend only on (instance, seed, sweep count, options): not on
+ *     the launch shape, the sweeps-per-launch chunking, or batching.
+ */
+#ifndef SGMC_H
+#define SGMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sg_ensemble sg_ensemble; /* opaque, owned by the library */
+
+typedef enum {
+    SG_OK = 0,
+    SG_EINVAL = 1,       /* invalid argument (message via sg_last_error) */
+    SG_ENOMEM = 2,       /* device or host allocation failed */
+    SG_ECUDA = 3,        /* a CUDA runtime call failed */
+    SG_ETIMEOUT = 4,     /* a kernel gave up after its watchdog budget */
+    SG_ECANCELLED = 5,   /* work was cancelled through the cancel flag */
+    SG_EBUSY = 6,        /* resource held by other work (serving slots) */
+    SG_EUNSUPPORTED = 7  /* valid request this build does not support */
+} sg_status;
+
+typedef enum { SG_PM_J = 0, SG_GAUSS = 1 } sg_coupling;
+
+/* Storage of the spins on the device. */
+typedef enum {
+    SG_LAYOUT_INT8 = 0,  /* one byte per spin; +-J or Gaussian couplings */
+    SG_LAYOUT_MSC64 = 1  /* 64 samples per uint64 word; +-J only,
+                            n_samples % 64 == 0, rng_group = 64 */
+} sg_layout;
+
+/* Accumulator indices (per sample and slot; see sg_get_accumulators). */
+enum {
+    SG_ACC_COUNT = 0, /* number of measurements                           */
+    SG_ACC_Q1 = 1,    /* sum Q, Q = sum_i q_i, q_i = s_i^(0) s_i^(1)      */
+    SG_ACC_Q2 = 2,    /* sum Q^2                                          */
+    SG_ACC_Q3 = 3,    /* sum Q^3                                          */
+    SG_ACC_Q4 = 4,    /* sum (Q^2)^2                                      */
+    SG_ACC_E1 = 5,    /* sum E over both replicas                         */
+    SG_ACC_E2 = 6,    /* sum E^2 over both replicas                       */
+    SG_ACC_M1 = 7,    /* sum M over both replicas                         */
+    SG_ACC_M2 = 8,    /* sum M^2 over both replicas                       */
+    SG_ACC_K = 9,     /* 9 + 3v + {0,1,2}: sum Re, Im, Re^2+Im^2 of
+                         sum_i q_i exp(i k_v . r_i), v = 0..8 with k_v in
+                         units 2pi/L: (1,0,0) (0,1,0) (0,0,1) (1,1,0)
+                         (1,-1,0) (1,0,1) (1,0,-1) (0,1,1) (0,1,-1)     */
+    SG_NACC = 40
+};
+
+typedef struct {
+    int32_t layout;            /* sg_layout                                   */
+    int32_t rng_group;         /* samples sharing Metropolis random numbers:
+                                  1 (independent) or 64 (as the MSC64 path)  */
+    int32_t exchange_every;    /* replica exchange after every k-th sweep;
+                                  0 = never                                  */
+    int32_t measure_every;     /* measure every k-th sweep once measuring     */
+    int64_t n_therm;           /* first measured sweep (global sweep index);
+                                  the paper thermalises for the first half   */
+    int32_t threads_per_block; /* 0 = library choice (autotuned where known)  */
+    int32_t sweeps_per_launch; /* 0 = library choice                          */
+    uint64_t watchdog_cycles;  /* 0 = no limit; else per-launch clock64 budget
+                                  after which kernels stop and report
+                                  SG_ETIMEOUT                                 */
+} sg_options;
+
+/* Fill *opt with the defaults: INT8 layout, rng_group 1, exchange and
+ * measure every sweep, n_therm 0, library-chosen launch shape, no watchdog. */
+void sg_options_default(sg_options *opt);
+
+/* Number of device bytes sg_create_ensemble allocates for this problem
+ * (state, couplings, accumulators, tables); 0 for invalid arguments. */
+size_t sg_ensemble_bytes(int L, int n_T, int64_t n_samples, sg_coupling dist,
+                         const sg_options *opt);
+
+/*
+ * Create an ensemble of n_samples disorder samples on the current device.
+ *   L        even, 2 <= L <= 32 (even L keeps the two-colour checkerboard a
+ *            proper colouring under periodic boundaries)
+ *   h        uniform field (eq. Hamiltonian); rounded to the 2^-17 grid when
+ *            dist == SG_GAUSS
+ *   T        host array of n_T temperatures, strictly ascending, > 0 (the
+ *            paper uses a geometric set, Table I caption); 1 <= n_T <= 64
+ *   dist     coupling distribution (+-1 bimodal, model section; or Gaussian)
+ *   seed     64-bit key of every random number the engine draws
+ *   opt      options (NULL = defaults)
+ *   J_host   NULL: couplings drawn on the device from seed (+-J: one Philox
+ *            bit per bond; Gaussian: Box-Muller on Philox output, rounded to
+ *            the 2^-17 grid, clamped to |J| <= 16). Else a host array in the
+ *            canonical layout: +-1 values for SG_PM_J, values on the 2^-17
+ *            grid with |J| <= 16 for SG_GAUSS (checked; SG_EINVAL otherwise).
+ *   spins_host  NULL: initial spins drawn from seed; else canonical host
+ *            array of +-1 (checked).
+ *   stream   cudaStream_t for all work of this ensemble (NULL = default).
+ *   out      receives the ensemble; *out is NULL on failure.
+ * The host arrays are copied before the call returns; the caller keeps
+ * ownership. Returns SG_EINVAL for bad arguments, SG_ENOMEM if device memory
+ * is short, SG_ECUDA for other CUDA failures.
+ */
+sg_status sg_create_ensemble(int L, double h, const double *T, int n_T, sg_coupling dist,
+                             int64_t n_samples, uint64_t seed, const sg_options *opt,
+                             const float *J_host, const int8_t *spins_host, void *stream,
+                             sg_ensemble **out);
+
+/* Release every resource of e (synchronises its stream first). NULL is a no-op. */
+void sg_destroy(sg_ensemble *e);
+
+/*
+ * Run n >= 0 Monte Carlo sweeps (paper: methods section; one sweep = one
+ * Metropolis attempt on every site of every replica and slot, colour 0 then
+ * colour 1), each followed by the parallel-tempering exchange when the
+ * schedule calls for it and by the overlap measurement once the global sweep
+ * index reaches n_therm. Asynchronous.
+ */
+sg_status sg_sweep(sg_ensemble *e, int64_t n);
+
+/*
+ * Run n sweeps of several ensembles together: one launch sequence covering all
+ * of them, each ensemble's kernels on a branch of one CUDA graph when
+ * use_graph != 0 (the graph is cached per ensemble set and n). Results are
+ * identical to calling sg_sweep on each. All ensembles must share one stream.
+ */
+sg_status sg_sweep_batch(sg_ensemble *const *es, int n_ens, int64_t n, int use_graph);
+
+/*
+ * One standalone parallel-tempering step (paper: methods section) on the
+ * current configurations: energies are recomputed, then pairs (p, p+1) with
+ * p = parity, parity+2, ... are offered a swap per replica. Its random numbers
+ * are keyed apart from the sweep schedule by the call's own counter.
+ */
+sg_status sg_exchange(sg_ensemble *e, int parity);
+
+/*
+ * Instantaneous overlap at arbitrary wave vectors (eq. overlap):
+ * out[s][t][j][0..1] = Re, Im of sum_i q_i exp(i 2pi/L k_j . r_i) for the
+ * current configurations, k_j = (k[3j], k[3j+1], k[3j+2]) integers, in FP32,
+ * divided by N. out is a host array of n_samples*n_T*nk*2 floats.
+ */
+sg_status sg_measure(sg_ensemble *e, const int *k, int nk, float *out);
+
+/* Copy the accumulators (canonical layout) to a host array. */
+sg_status sg_get_accumulators(sg_ensemble *e, double *acc_out);
+/* Zero the accumulators. */
+sg_status sg_reset_accumulators(sg_ensemble *e);
+/* Copy the current spins (canonical layout, +-1) to a host array. */
+sg_status sg_get_spins(sg_ensemble *e, int8_t *spins_out);
+/* Replace the current spins from a host array (canonical layout, +-1). */
+sg_status sg_set_spins(sg_ensemble *e, const int8_t *spins_host);
+/* Copy B and M ([S][2][n_T] each) of the configuration after the last sweep
+ * or exchange; either pointer may be NULL. */
+sg_status sg_get_energies(sg_ensemble *e, int64_t *B_out, int64_t *M_out);
+/* Copy the couplings on the device back in the canonical layout. */
+sg_status sg_get_couplings(sg_ensemble *e, float *J_out);
+/* Number of sweeps done so far (the global sweep index of the next sweep). */
+int64_t sg_sweeps_done(const sg_ensemble *e);
+/* Set the global sweep counter (checkpoint restore together with
+ * sg_set_spins and the accumulators; results then continue bit-exactly). */
+sg_status sg_set_sweeps_done(sg_ensemble *e, int64_t n);
+/* Replace the accumulators from a host array (checkpoint restore). */
+sg_status sg_set_accumulators(sg_ensemble *e, const double *acc_host);
+
+/* Wait for the ensemble's stream and report the first device-side error. */
+sg_status sg_synchronize(sg_ensemble *e);
+
+/* Static description of an ensemble. */
+typedef struct {
+    int32_t L, n_T, layout, dist;
+    int64_t n_samples;
+    double h;          /* field actually used (rounded for Gaussian)   */
+    int64_t attempts_per_sweep; /* N * 2 * n_T * n_samples           */
+    size_t device_bytes;
+} sg_info;
+sg_status sg_get_info(const sg_ensemble *e, sg_info *out);
+
+/*
+ * Disorder-averaged observables per slot from the accumulators (paper:
+ * eqs. binder, chi, corr, r12; point-group averaging of chi over the three
+ * k1 directions and the six k2 directions; delete-one jackknife errors over
+ * samples). Every output array has n_T entries and may be NULL.
+ */
+typedef struct {
+    double *g, *g_err;             /* Binder ratio, global centring        */
+    double *chi0, *chi0_err;       /* chi_SG(0)                            */
+    double *chi1, *chi1_err;       /* chi_SG(k1), mean over 3 directions   */
+    double *chi2, *chi2_err;       /* chi_SG(k2), mean over 6 directions   */
+    double *xi, *xi_err;           /* xi_L (NaN when chi0/chi1 < 1)        */
+    double *r12, *r12_err;         /* chi1 / chi2                          */
+    double *e, *e_err;             /* energy per spin                      */
+    double *q2, *q2_err;           /* [<q(0)^2>]                           */
+    double *q4, *q4_err;           /* [<q(0)^4>]                           */
+} sg_observables;
+sg_status sg_results(sg_ensemble *e, const sg_observables *out);
+
+/* The same estimators on a host accumulator array [S][n_T][40]. */
+sg_status sg_observables_from_acc(const double *acc, int64_t n_samples, int n_T, int L,
+                                  const sg_observables *out);
+
+/* Text for a status code, and the message of the last error on this thread. */
+const char *sg_status_str(sg_status s);
+const char *sg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SGMC_H */

@@ -1,0 +1,720 @@
+// sg_api.cpp -- host side of the C ABI declared in include/sgmc.h.
+//
+// Owns ensembles (device arena, tables, stream), builds the per-temperature
+// tables on the host (acceptance thresholds from the C library's exp, FP32
+// inverse temperatures, DFT twiddles), picks launch shapes and drives the
+// fused kernels, alone or batched through a CUDA graph.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "sg_internal.h"
+
+using namespace sg;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+sg_status fail(sg_status s, const std::string &msg)
+{
+    g_last_error = msg;
+    return s;
+}
+
+sg_status cuda_fail(cudaError_t e, const char *where)
+{
+    g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? SG_ENOMEM : SG_ECUDA;
+}
+
+#define SG_CUDA(call, where)                           \
+    do {                                               \
+        cudaError_t e_ = (call);                       \
+        if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+    } while (0)
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+struct sg_ensemble {
+    int L = 0, nt = 0, Tp = 0, layout = 0;
+    bool gauss = false;
+    int64_t S = 0;
+    double h = 0.0, h_used = 0.0;
+    uint64_t seed = 0;
+    sg_options opt{};
+    cudaStream_t stream = nullptr;
+    cudaStream_t branch = nullptr;  // private stream for batched branches
+    cudaEvent_t ev = nullptr;
+    int device = 0;
+    int num_sms = 148;
+    // device arena and views
+    void *arena = nullptr;
+    size_t bytes = 0;
+    uint8_t *spins = nullptr, *J8 = nullptr;
+    float *Jg = nullptr;
+    int64_t *B = nullptr, *M = nullptr;
+    double *acc = nullptr;
+    uint32_t *thr = nullptr;
+    float *negbeta = nullptr, *dbeta = nullptr, *twid = nullptr;
+    int *status = nullptr;
+    int64_t *sweep_ctr = nullptr;
+    int64_t sweeps_done = 0;
+    int64_t exchanges_done = 0;
+    std::vector<double> T;
+    Int8Launch launch{};
+    int mchunk = 1;
+};
+
+namespace {
+
+std::mutex g_graph_mu;
+struct GraphEntry {
+    std::vector<sg_ensemble *> ens;
+    cudaGraphExec_t exec = nullptr;
+};
+std::map<std::string, GraphEntry> g_graphs;
+
+void purge_graphs(sg_ensemble *e)
+{
+    std::lock_guard<std::mutex> lk(g_graph_mu);
+    for (auto it = g_graphs.begin(); it != g_graphs.end();) {
+        if (std::find(it->second.ens.begin(), it->second.ens.end(), e) != it->second.ens.end()) {
+            cudaGraphExecDestroy(it->second.exec);
+            it = g_graphs.erase(it);
+        } else {
+            ++it;
+        }
+    }
+}
+
+struct ArenaPlan {
+    size_t spins, J, BM, acc, thr, tab, twid, misc, total;
+};
+
+ArenaPlan plan_arena(int L, int nt, int Tp, int64_t S, bool gauss)
+{
+    const size_t N = (size_t)L * L * L;
+    ArenaPlan p;
+    p.spins = align256((size_t)S * N * 2 * Tp);
+    p.J = align256(gauss ? (size_t)S * 3 * N * sizeof(float) : (size_t)S * N * 8);
+    p.BM = align256((size_t)S * 2 * Tp * sizeof(int64_t));
+    p.acc = align256((size_t)S * nt * SG_NACC * sizeof(double));
+    p.thr = align256((size_t)Tp * 16 * sizeof(uint32_t));
+    p.tab = align256((size_t)Tp * sizeof(float));
+    p.twid = align256((size_t)2 * L * sizeof(float));
+    p.misc = 256;
+    p.total = p.spins + p.J + 2 * p.BM + p.acc + p.thr + 2 * p.tab + p.twid + p.misc;
+    return p;
+}
+
+int pad_slots(int nt) { return (nt + 3) & ~3; }
+
+// Threads per CTA: a multiple of the per-site word count W = Tp/2 (each
+// thread keeps one 4-slot word for the whole half-sweep), chosen so that the
+// half-sweep work items divide evenly where possible.
+int pick_threads(int L, int Tp, int requested)
+{
+    const int W = Tp / 2;
+    const int H = L / 2;
+    int run = H;
+    while (run % 4) run += H;
+    const int items = (L * L * L / 2) / run * W;
+    const int maxt = int8_max_threads();
+    if (requested > 0) {
+        int t = std::max(W, (requested / W) * W);
+        return std::min(t, (maxt / W) * W);
+    }
+    int best = W, best_score = -1;
+    for (int t = W; t <= maxt; t += W) {
+        if (t < 64 && t + W <= maxt) continue;
+        const int rounds = (items + t - 1) / t;
+        // efficiency of the last round, then prefer 256-384 threads
+        const double eff = (double)items / (double)(rounds * t);
+        const int score = (int)(eff * 1000) - std::abs(t - 320) / 16;
+        if (score > best_score) {
+            best_score = score;
+            best = t;
+        }
+    }
+    return best;
+}
+
+sg_status configure_launch(sg_ensemble *e)
+{
+    const int WR = e->Tp / 4;
+    const int threads = pick_threads(e->L, e->Tp, e->opt.threads_per_block);
+    int best_m = 0, best_occ = 0;
+    for (int m = WR; m >= 1; --m) {
+        const size_t smem = int8_smem_bytes(e->L, e->Tp, e->gauss, m);
+        if (!smem) continue;
+        const int occ = int8_ctas_per_sm(e->L, e->gauss, threads, smem);
+        if (occ > best_occ) {
+            best_occ = occ;
+            best_m = m;
+        }
+    }
+    if (best_occ == 0)
+        return fail(SG_EUNSUPPORTED, "int8 state of one sample does not fit in shared memory "
+                                     "(use fewer temperatures or a smaller L)");
+    e->mchunk = best_m;
+    e->launch.threads = threads;
+    e->launch.smem = int8_smem_bytes(e->L, e->Tp, e->gauss, best_m);
+    const int64_t resident = (int64_t)best_occ * e->num_sms;
+    e->launch.grid = (int)std::min<int64_t>(e->S, resident);
+    return SG_OK;
+}
+
+Int8Args make_args(sg_ensemble *e)
+{
+    Int8Args a{};
+    a.spins = e->spins;
+    a.J8 = e->J8;
+    a.Jg = e->Jg;
+    a.B = e->B;
+    a.M = e->M;
+    a.acc = e->acc;
+    a.thr = e->thr;
+    a.negbeta = e->negbeta;
+    a.dbeta = e->dbeta;
+    a.twid = e->twid;
+    a.status = e->status;
+    a.S = e->S;
+    a.nt = e->nt;
+    a.Tp = e->Tp;
+    a.h_f = (float)e->h_used;
+    a.qJ_f = e->gauss ? (1.0f / 131072.0f) : 1.0f;
+    a.h_d = e->h_used;
+    a.qJ_d = e->gauss ? (1.0 / 131072.0) : 1.0;
+    a.seed_lo = (uint32_t)e->seed;
+    a.seed_hi = (uint32_t)(e->seed >> 32);
+    a.rng_group = e->opt.rng_group;
+    a.sweep0 = e->sweeps_done;
+    a.sweep0_dev = nullptr;
+    a.n_sweeps = 0;
+    a.exchange_every = e->opt.exchange_every;
+    a.measure_every = e->opt.measure_every;
+    a.n_therm = e->opt.n_therm;
+    a.mchunk = e->mchunk;
+    a.watchdog = e->opt.watchdog_cycles;
+    a.cancel = nullptr;
+    a.s_begin = 0;
+    a.s_end = e->S;
+    return a;
+}
+
+// Host tables: +-J thresholds (FP64 exp of the C library), FP32 -beta and
+// beta differences, FP32 twiddles of the DFT.
+void host_tables(const sg_ensemble *e, std::vector<uint32_t> &thr, std::vector<float> &nb,
+                 std::vector<float> &db, std::vector<float> &tw)
+{
+    thr.assign((size_t)e->Tp * 16, 0u);
+    nb.assign((size_t)e->Tp, 0.0f);
+    db.assign((size_t)e->Tp, 0.0f);
+    for (int t = 0; t < e->nt; ++t) {
+        const double beta = 1.0 / e->T[(size_t)t];
+        nb[(size_t)t] = -(float)beta;
+        if (t + 1 < e->nt) db[(size_t)t] = (float)(beta - 1.0 / e->T[(size_t)t + 1]);
+        for (int sb = 0; sb < 2; ++sb)
+            for (int u = 0; u <= 6; ++u) {
+                const double dE = (double)(12 - 4 * u) + (sb ? -2.0 * e->h_used : 2.0 * e->h_used);
+                uint32_t v;
+                if (dE <= 0.0) {
+                    v = 0xFFFFFFFFu;
+                } else {
+                    const double p = std::floor(std::exp(-(beta * dE)) * 4294967296.0);
+                    v = p >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)p;
+                }
+                thr[(size_t)t * 16 + sb * 8 + u] = v;
+            }
+    }
+    tw.assign((size_t)2 * e->L, 0.0f);
+    for (int d = 0; d < e->L; ++d) {
+        const double ang = ((2.0 * M_PI) * (double)d) / (double)e->L;
+        tw[(size_t)d] = (float)std::cos(ang);
+        tw[(size_t)e->L + d] = (float)std::sin(ang);
+    }
+}
+
+sg_status validate(int L, const double *T, int nt, sg_coupling dist, int64_t S,
+                   const sg_options &o)
+{
+    if (L < 2 || (L & 1) || L > 32) return fail(SG_EINVAL, "L must be even and in [2, 32]");
+    if (nt < 1 || nt > 64) return fail(SG_EINVAL, "n_T must be in [1, 64]");
+    if (!T) return fail(SG_EINVAL, "temperature array is NULL");
+    for (int t = 0; t < nt; ++t) {
+        if (!(T[t] > 0.0) || !std::isfinite(T[t]))
+            return fail(SG_EINVAL, "temperatures must be finite and positive");
+        if (t > 0 && !(T[t] > T[t - 1]))
+            return fail(SG_EINVAL, "temperatures must be strictly ascending");
+    }
+    if (dist != SG_PM_J && dist != SG_GAUSS) return fail(SG_EINVAL, "unknown coupling distribution");
+    if (S < 1 || S > (int64_t)1 << 31) return fail(SG_EINVAL, "n_samples must be in [1, 2^31]");
+    if (o.rng_group < 1) return fail(SG_EINVAL, "rng_group must be >= 1");
+    if (o.exchange_every < 0) return fail(SG_EINVAL, "exchange_every must be >= 0");
+    if (o.measure_every < 1) return fail(SG_EINVAL, "measure_every must be >= 1");
+    if (o.layout != SG_LAYOUT_INT8 && o.layout != SG_LAYOUT_MSC64)
+        return fail(SG_EINVAL, "unknown layout");
+    if (o.layout == SG_LAYOUT_MSC64)
+        return fail(SG_EUNSUPPORTED, "the MSC64 layout is not available in this build");
+    return SG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void sg_options_default(sg_options *o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof *o);
+    o->layout = SG_LAYOUT_INT8;
+    o->rng_group = 1;
+    o->exchange_every = 1;
+    o->measure_every = 1;
+    o->n_therm = 0;
+}
+
+const char *sg_status_str(sg_status s)
+{
+    switch (s) {
+    case SG_OK: return "ok";
+    case SG_EINVAL: return "invalid argument";
+    case SG_ENOMEM: return "out of memory";
+    case SG_ECUDA: return "CUDA error";
+    case SG_ETIMEOUT: return "watchdog timeout";
+    case SG_ECANCELLED: return "cancelled";
+    case SG_EBUSY: return "busy";
+    case SG_EUNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+const char *sg_last_error(void) { return g_last_error.c_str(); }
+
+size_t sg_ensemble_bytes(int L, int nt, int64_t S, sg_coupling dist, const sg_options *opt)
+{
+    sg_options o;
+    if (opt) o = *opt; else sg_options_default(&o);
+    std::vector<double> T((size_t)std::max(nt, 1));
+    for (size_t k = 0; k < T.size(); ++k) T[k] = 1.0 + (double)k;
+    if (validate(L, T.data(), nt, dist, S, o) != SG_OK) return 0;
+    return plan_arena(L, nt, pad_slots(nt), S, dist == SG_GAUSS).total;
+}
+
+sg_status sg_create_ensemble(int L, double h, const double *T, int nt, sg_coupling dist,
+                             int64_t S, uint64_t seed, const sg_options *opt,
+                             const float *J_host, const int8_t *spins_host, void *stream,
+                             sg_ensemble **out)
+{
+    if (!out) return fail(SG_EINVAL, "out is NULL");
+    *out = nullptr;
+    sg_options o;
+    if (opt) o = *opt; else sg_options_default(&o);
+    sg_status st = validate(L, T, nt, dist, S, o);
+    if (st != SG_OK) return st;
+    if (!std::isfinite(h)) return fail(SG_EINVAL, "field must be finite");
+    const size_t N = (size_t)L * L * L;
+    const bool gauss = dist == SG_GAUSS;
+    if (J_host) {
+        const size_t nJ = (size_t)S * 3 * N;
+        for (size_t k = 0; k < nJ; ++k) {
+            const float v = J_host[k];
+            if (!gauss) {
+                if (v != 1.0f && v != -1.0f) return fail(SG_EINVAL, "+-J couplings must be +1 or -1");
+            } else {
+                const double q = (double)v * 131072.0;
+                if (!(std::fabs(v) <= 16.0f) || q != std::rint(q))
+                    return fail(SG_EINVAL, "Gaussian couplings must lie on the 2^-17 grid, |J| <= 16");
+            }
+        }
+    }
+    if (spins_host) {
+        const size_t ns = (size_t)S * 2 * nt * N;
+        for (size_t k = 0; k < ns; ++k)
+            if (spins_host[k] != 1 && spins_host[k] != -1)
+                return fail(SG_EINVAL, "spins must be +1 or -1");
+    }
+
+    sg_ensemble *e = new sg_ensemble();
+    e->L = L;
+    e->nt = nt;
+    e->Tp = pad_slots(nt);
+    e->layout = o.layout;
+    e->gauss = gauss;
+    e->S = S;
+    e->h = h;
+    e->h_used = gauss ? std::rint(h * 131072.0) / 131072.0 : h;
+    e->seed = seed;
+    e->opt = o;
+    e->stream = (cudaStream_t)stream;
+    e->T.assign(T, T + nt);
+    auto bail = [&](sg_status s) {
+        sg_destroy(e);
+        return s;
+    };
+    cudaError_t ce = cudaGetDevice(&e->device);
+    if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaGetDevice"));
+    cudaDeviceGetAttribute(&e->num_sms, cudaDevAttrMultiProcessorCount, e->device);
+    if ((st = configure_launch(e)) != SG_OK) return bail(st);
+
+    const ArenaPlan p = plan_arena(L, nt, e->Tp, S, gauss);
+    ce = cudaMalloc(&e->arena, p.total);
+    if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaMalloc(ensemble)"));
+    e->bytes = p.total;
+    uint8_t *base = (uint8_t *)e->arena;
+    size_t off = 0;
+    e->spins = base + off; off += p.spins;
+    if (gauss) e->Jg = (float *)(base + off); else e->J8 = base + off;
+    off += p.J;
+    e->B = (int64_t *)(base + off); off += p.BM;
+    e->M = (int64_t *)(base + off); off += p.BM;
+    e->acc = (double *)(base + off); off += p.acc;
+    e->thr = (uint32_t *)(base + off); off += p.thr;
+    e->negbeta = (float *)(base + off); off += p.tab;
+    e->dbeta = (float *)(base + off); off += p.tab;
+    e->twid = (float *)(base + off); off += p.twid;
+    e->status = (int *)(base + off);
+    e->sweep_ctr = (int64_t *)(base + off + 64);
+
+    ce = cudaStreamCreateWithFlags(&e->branch, cudaStreamNonBlocking);
+    if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaStreamCreate"));
+    ce = cudaEventCreateWithFlags(&e->ev, cudaEventDisableTiming);
+    if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaEventCreate"));
+
+    std::vector<uint32_t> thr;
+    std::vector<float> nb, db, tw;
+    host_tables(e, thr, nb, db, tw);
+    cudaStream_t s = e->stream;
+    const uint32_t slo = (uint32_t)seed, shi = (uint32_t)(seed >> 32);
+    auto run = [&]() -> cudaError_t {
+        cudaError_t r;
+        if ((r = cudaMemsetAsync(e->status, 0, 256, s)) != cudaSuccess) return r;
+        if ((r = cudaMemsetAsync(e->acc, 0, p.acc, s)) != cudaSuccess) return r;
+        if ((r = cudaMemcpyAsync(e->thr, thr.data(), thr.size() * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess) return r;
+        if ((r = cudaMemcpyAsync(e->negbeta, nb.data(), nb.size() * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess) return r;
+        if ((r = cudaMemcpyAsync(e->dbeta, db.data(), db.size() * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess) return r;
+        if ((r = cudaMemcpyAsync(e->twid, tw.data(), tw.size() * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess) return r;
+        if (J_host) {
+            float *stage = nullptr;
+            const size_t bytes = (size_t)S * 3 * N * sizeof(float);
+            if ((r = cudaMalloc(&stage, bytes)) != cudaSuccess) return r;
+            r = cudaMemcpyAsync(stage, J_host, bytes, cudaMemcpyHostToDevice, s);
+            if (r == cudaSuccess) r = int8_import_J(e->J8, e->Jg, stage, S, L, gauss, s);
+            if (r == cudaSuccess) r = cudaStreamSynchronize(s);
+            cudaFree(stage);
+            if (r != cudaSuccess) return r;
+        } else {
+            r = gauss ? int8_gen_gauss(e->Jg, S, L, slo, shi, s) : int8_gen_pmj(e->J8, S, L, slo, shi, s);
+            if (r != cudaSuccess) return r;
+        }
+        if (spins_host) {
+            int8_t *stage = nullptr;
+            const size_t bytes = (size_t)S * 2 * nt * N;
+            if ((r = cudaMalloc(&stage, bytes)) != cudaSuccess) return r;
+            r = cudaMemcpyAsync(stage, spins_host, bytes, cudaMemcpyHostToDevice, s);
+            if (r == cudaSuccess) r = int8_import_spins(e->spins, stage, S, L, nt, e->Tp, s);
+            if (r == cudaSuccess) r = cudaStreamSynchronize(s);
+            cudaFree(stage);
+            if (r != cudaSuccess) return r;
+        } else {
+            if ((r = int8_gen_spins(e->spins, S, L, nt, e->Tp, slo, shi, s)) != cudaSuccess) return r;
+        }
+        Int8Args a = make_args(e);
+        if ((r = int8_energies(a, L, gauss, s)) != cudaSuccess) return r;
+        return cudaStreamSynchronize(s);
+    };
+    ce = run();
+    if (ce != cudaSuccess) return bail(cuda_fail(ce, "ensemble set-up"));
+    *out = e;
+    return SG_OK;
+}
+
+void sg_destroy(sg_ensemble *e)
+{
+    if (!e) return;
+    purge_graphs(e);
+    if (e->stream || e->arena) cudaStreamSynchronize(e->stream);
+    if (e->branch) cudaStreamSynchronize(e->branch);
+    if (e->arena) cudaFree(e->arena);
+    if (e->branch) cudaStreamDestroy(e->branch);
+    if (e->ev) cudaEventDestroy(e->ev);
+    delete e;
+}
+
+static sg_status launch_sweeps(sg_ensemble *e, int64_t n, cudaStream_t s, bool device_counter)
+{
+    int64_t chunk = e->opt.sweeps_per_launch > 0 ? e->opt.sweeps_per_launch : n;
+    if (chunk < 1) chunk = 1;
+    chunk = std::min<int64_t>(chunk, 1 << 30);
+    for (int64_t done = 0; done < n; done += chunk) {
+        Int8Args a = make_args(e);
+        a.n_sweeps = (int)std::min<int64_t>(chunk, n - done);
+        a.sweep0 = e->sweeps_done + done;
+        if (device_counter) a.sweep0_dev = e->sweep_ctr;
+        SG_CUDA(int8_launch(e->L, e->gauss, a, e->launch, s), "sweep kernel launch");
+        if (device_counter) SG_CUDA(advance_counter(e->sweep_ctr, a.n_sweeps, s), "counter");
+    }
+    return SG_OK;
+}
+
+sg_status sg_sweep(sg_ensemble *e, int64_t n)
+{
+    if (!e) return fail(SG_EINVAL, "ensemble is NULL");
+    if (n < 0) return fail(SG_EINVAL, "sweep count must be >= 0");
+    if (n == 0) return SG_OK;
+    sg_status st = launch_sweeps(e, n, e->stream, false);
+    if (st != SG_OK) return st;
+    e->sweeps_done += n;
+    return SG_OK;
+}
+
+sg_status sg_sweep_batch(sg_ensemble *const *es, int n_ens, int64_t n, int use_graph)
+{
+    if (!es || n_ens < 1) return fail(SG_EINVAL, "no ensembles");
+    if (n < 0) return fail(SG_EINVAL, "sweep count must be >= 0");
+    for (int k = 0; k < n_ens; ++k) {
+        if (!es[k]) return fail(SG_EINVAL, "ensemble is NULL");
+        if (es[k]->stream != es[0]->stream) return fail(SG_EINVAL, "ensembles must share one stream");
+        for (int j = 0; j < k; ++j)
+            if (es[j] == es[k]) return fail(SG_EINVAL, "an ensemble appears twice");
+    }
+    if (n == 0) return SG_OK;
+    cudaStream_t main = es[0]->stream;
+    if (!use_graph) {
+        SG_CUDA(cudaEventRecord(es[0]->ev, main), "event");
+        for (int k = 0; k < n_ens; ++k) {
+            SG_CUDA(cudaStreamWaitEvent(es[k]->branch, es[0]->ev, 0), "fork");
+            sg_status st = launch_sweeps(es[k], n, es[k]->branch, false);
+            if (st != SG_OK) return st;
+        }
+        for (int k = 0; k < n_ens; ++k) {
+            SG_CUDA(cudaEventRecord(es[k]->ev, es[k]->branch), "event");
+            SG_CUDA(cudaStreamWaitEvent(main, es[k]->ev, 0), "join");
+            es[k]->sweeps_done += n;
+        }
+        return SG_OK;
+    }
+    // graph path: the sweep index comes from a device counter, so one
+    // instantiated graph serves every call with the same ensembles and n
+    std::string key = std::to_string(n);
+    for (int k = 0; k < n_ens; ++k) {
+        char buf[32];
+        std::snprintf(buf, sizeof buf, ":%p", (void *)es[k]);
+        key += buf;
+    }
+    cudaGraphExec_t exec = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_graph_mu);
+        auto it = g_graphs.find(key);
+        if (it != g_graphs.end()) exec = it->second.exec;
+    }
+    for (int k = 0; k < n_ens; ++k)
+        SG_CUDA(cudaMemcpyAsync(es[k]->sweep_ctr, &es[k]->sweeps_done, sizeof(int64_t),
+                                cudaMemcpyHostToDevice, main), "counter upload");
+    if (!exec) {
+        cudaStream_t cap = nullptr;
+        SG_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "capture stream");
+        cudaGraph_t graph = nullptr;
+        cudaError_t ce = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (ce == cudaSuccess) {
+            ce = cudaEventRecord(es[0]->ev, cap);
+            for (int k = 0; k < n_ens && ce == cudaSuccess; ++k) {
+                ce = cudaStreamWaitEvent(es[k]->branch, es[0]->ev, 0);
+                if (ce == cudaSuccess && launch_sweeps(es[k], n, es[k]->branch, true) != SG_OK)
+                    ce = cudaErrorUnknown;
+            }
+            for (int k = 0; k < n_ens && ce == cudaSuccess; ++k) {
+                ce = cudaEventRecord(es[k]->ev, es[k]->branch);
+                if (ce == cudaSuccess) ce = cudaStreamWaitEvent(cap, es[k]->ev, 0);
+            }
+            cudaError_t ce2 = cudaStreamEndCapture(cap, &graph);
+            if (ce == cudaSuccess) ce = ce2;
+        }
+        if (ce == cudaSuccess) ce = cudaGraphInstantiate(&exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        cudaStreamDestroy(cap);
+        if (ce != cudaSuccess) return cuda_fail(ce, "graph capture");
+        std::lock_guard<std::mutex> lk(g_graph_mu);
+        GraphEntry ge;
+        ge.ens.assign(es, es + n_ens);
+        ge.exec = exec;
+        g_graphs[key] = ge;
+    }
+    SG_CUDA(cudaGraphLaunch(exec, main), "graph launch");
+    for (int k = 0; k < n_ens; ++k) es[k]->sweeps_done += n;
+    return SG_OK;
+}
+
+sg_status sg_exchange(sg_ensemble *e, int parity)
+{
+    if (!e) return fail(SG_EINVAL, "ensemble is NULL");
+    Int8Args a = make_args(e);
+    SG_CUDA(int8_exchange(a, e->L, e->gauss, parity & 1, (uint32_t)e->exchanges_done, e->stream),
+            "exchange");
+    ++e->exchanges_done;
+    return SG_OK;
+}
+
+sg_status sg_measure(sg_ensemble *e, const int *k, int nk, float *out)
+{
+    if (!e || !k || nk < 1 || !out) return fail(SG_EINVAL, "bad measure arguments");
+    int *kd = nullptr;
+    float *od = nullptr;
+    const size_t ob = (size_t)e->S * e->nt * nk * 2 * sizeof(float);
+    SG_CUDA(cudaMalloc(&kd, sizeof(int) * 3 * nk), "cudaMalloc");
+    cudaError_t ce = cudaMalloc(&od, ob);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(kd, k, sizeof(int) * 3 * nk, cudaMemcpyHostToDevice, e->stream);
+    if (ce == cudaSuccess) ce = int8_measure_k(make_args(e), e->L, kd, nk, od, e->stream);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(out, od, ob, cudaMemcpyDeviceToHost, e->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(e->stream);
+    cudaFree(kd);
+    cudaFree(od);
+    if (ce != cudaSuccess) return cuda_fail(ce, "measure");
+    return SG_OK;
+}
+
+sg_status sg_get_accumulators(sg_ensemble *e, double *out)
+{
+    if (!e || !out) return fail(SG_EINVAL, "bad arguments");
+    SG_CUDA(cudaMemcpyAsync(out, e->acc, (size_t)e->S * e->nt * SG_NACC * sizeof(double),
+                            cudaMemcpyDeviceToHost, e->stream), "copy accumulators");
+    SG_CUDA(cudaStreamSynchronize(e->stream), "sync");
+    return SG_OK;
+}
+
+sg_status sg_set_accumulators(sg_ensemble *e, const double *in)
+{
+    if (!e || !in) return fail(SG_EINVAL, "bad arguments");
+    SG_CUDA(cudaMemcpyAsync(e->acc, in, (size_t)e->S * e->nt * SG_NACC * sizeof(double),
+                            cudaMemcpyHostToDevice, e->stream), "copy accumulators");
+    SG_CUDA(cudaStreamSynchronize(e->stream), "sync");
+    return SG_OK;
+}
+
+sg_status sg_reset_accumulators(sg_ensemble *e)
+{
+    if (!e) return fail(SG_EINVAL, "ensemble is NULL");
+    SG_CUDA(cudaMemsetAsync(e->acc, 0, (size_t)e->S * e->nt * SG_NACC * sizeof(double), e->stream),
+            "memset");
+    return SG_OK;
+}
+
+sg_status sg_get_spins(sg_ensemble *e, int8_t *out)
+{
+    if (!e || !out) return fail(SG_EINVAL, "bad arguments");
+    const size_t bytes = (size_t)e->S * 2 * e->nt * e->L * e->L * e->L;
+    int8_t *d = nullptr;
+    SG_CUDA(cudaMalloc(&d, bytes), "cudaMalloc");
+    cudaError_t ce = int8_export_spins(d, e->spins, e->S, e->L, e->nt, e->Tp, e->stream);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(out, d, bytes, cudaMemcpyDeviceToHost, e->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(e->stream);
+    cudaFree(d);
+    if (ce != cudaSuccess) return cuda_fail(ce, "get spins");
+    return SG_OK;
+}
+
+sg_status sg_set_spins(sg_ensemble *e, const int8_t *in)
+{
+    if (!e || !in) return fail(SG_EINVAL, "bad arguments");
+    const size_t bytes = (size_t)e->S * 2 * e->nt * e->L * e->L * e->L;
+    for (size_t k = 0; k < bytes; ++k)
+        if (in[k] != 1 && in[k] != -1) return fail(SG_EINVAL, "spins must be +1 or -1");
+    int8_t *d = nullptr;
+    SG_CUDA(cudaMalloc(&d, bytes), "cudaMalloc");
+    cudaError_t ce = cudaMemcpyAsync(d, in, bytes, cudaMemcpyHostToDevice, e->stream);
+    if (ce == cudaSuccess) ce = int8_import_spins(e->spins, d, e->S, e->L, e->nt, e->Tp, e->stream);
+    if (ce == cudaSuccess) ce = int8_energies(make_args(e), e->L, e->gauss, e->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(e->stream);
+    cudaFree(d);
+    if (ce != cudaSuccess) return cuda_fail(ce, "set spins");
+    return SG_OK;
+}
+
+sg_status sg_get_energies(sg_ensemble *e, int64_t *Bo, int64_t *Mo)
+{
+    if (!e) return fail(SG_EINVAL, "ensemble is NULL");
+    std::vector<int64_t> tmp((size_t)e->S * 2 * e->Tp);
+    for (int which = 0; which < 2; ++which) {
+        int64_t *dst = which == 0 ? Bo : Mo;
+        if (!dst) continue;
+        SG_CUDA(cudaMemcpyAsync(tmp.data(), which == 0 ? e->B : e->M, tmp.size() * sizeof(int64_t),
+                                cudaMemcpyDeviceToHost, e->stream), "copy energies");
+        SG_CUDA(cudaStreamSynchronize(e->stream), "sync");
+        for (int64_t s = 0; s < e->S; ++s)
+            for (int r = 0; r < 2; ++r)
+                for (int t = 0; t < e->nt; ++t)
+                    dst[(s * 2 + r) * e->nt + t] = tmp[(size_t)(s * 2 + r) * e->Tp + t];
+    }
+    return SG_OK;
+}
+
+sg_status sg_get_couplings(sg_ensemble *e, float *out)
+{
+    if (!e || !out) return fail(SG_EINVAL, "bad arguments");
+    const size_t bytes = (size_t)e->S * 3 * e->L * e->L * e->L * sizeof(float);
+    float *d = nullptr;
+    SG_CUDA(cudaMalloc(&d, bytes), "cudaMalloc");
+    cudaError_t ce = int8_export_J(d, e->J8, e->Jg, e->S, e->L, e->gauss, e->stream);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(out, d, bytes, cudaMemcpyDeviceToHost, e->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(e->stream);
+    cudaFree(d);
+    if (ce != cudaSuccess) return cuda_fail(ce, "get couplings");
+    return SG_OK;
+}
+
+int64_t sg_sweeps_done(const sg_ensemble *e) { return e ? e->sweeps_done : -1; }
+
+sg_status sg_set_sweeps_done(sg_ensemble *e, int64_t n)
+{
+    if (!e || n < 0) return fail(SG_EINVAL, "bad arguments");
+    e->sweeps_done = n;
+    return SG_OK;
+}
+
+sg_status sg_synchronize(sg_ensemble *e)
+{
+    if (!e) return fail(SG_EINVAL, "ensemble is NULL");
+    SG_CUDA(cudaStreamSynchronize(e->stream), "stream synchronize");
+    int status = 0;
+    SG_CUDA(cudaMemcpy(&status, e->status, sizeof(int), cudaMemcpyDeviceToHost), "status");
+    if (status != 0) {
+        SG_CUDA(cudaMemset(e->status, 0, sizeof(int)), "status reset");
+        return fail((sg_status)status, "device reported an error");
+    }
+    return SG_OK;
+}
+
+sg_status sg_get_info(const sg_ensemble *e, sg_info *out)
+{
+    if (!e || !out) return fail(SG_EINVAL, "bad arguments");
+    out->L = e->L;
+    out->n_T = e->nt;
+    out->layout = e->layout;
+    out->dist = e->gauss ? SG_GAUSS : SG_PM_J;
+    out->n_samples = e->S;
+    out->h = e->h_used;
+    out->attempts_per_sweep = (int64_t)e->L * e->L * e->L * 2 * e->nt * e->S;
+    out->device_bytes = e->bytes;
+    return SG_OK;
+}
+
+sg_status sg_results(sg_ensemble *e, const sg_observables *out)
+{
+    if (!e || !out) return fail(SG_EINVAL, "bad arguments");
+    std::vector<double> acc((size_t)e->S * e->nt * SG_NACC);
+    sg_status st = sg_get_accumulators(e, acc.data());
+    if (st != SG_OK) return st;
+    return sg_observables_from_acc(acc.data(), e->S, e->nt, e->L, out);
+}
+
+}  // extern "C"

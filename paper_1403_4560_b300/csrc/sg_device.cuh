@@ -1,0 +1,82 @@
+// sg_device.cuh -- device-side building blocks of the EA spin-glass engine:
+// the counter-based random number generator, the FP32 exponential used for
+// continuous acceptance probabilities, and the 32-bit threshold map.
+//
+// Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random
+// numbers: as easy as 1, 2, 3", SC'11). The paper drew its numbers from a
+// different generator (XORWOW); a counter-based generator lets every
+// (sample, replica, slot, sweep, site) address its own number, so the result
+// does not depend on launch shape, and a checkpoint is just the sweep index.
+#pragma once
+#include <stdint.h>
+
+namespace sg {
+
+constexpr uint32_t kTagMet = 0x4D455452u;
+constexpr uint32_t kTagExc = 0x45584348u;
+constexpr uint32_t kTagInit = 0x494E4954u;
+constexpr uint32_t kTagBond = 0x424F4E44u;
+
+struct u32x4 {
+    uint32_t v[4];
+};
+
+// Ten Philox rounds: two 32x32->64 multiplies per round, the high halves mixed
+// with the other two counter words and the round key, then the Weyl key bump.
+__device__ __forceinline__ u32x4 philox10(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1,
+                                          uint32_t c2, uint32_t c3)
+{
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint64_t pa = (uint64_t)0xD2511F53u * c0;
+        const uint64_t pb = (uint64_t)0xCD9E8D57u * c2;
+        const uint32_t n0 = (uint32_t)(pb >> 32) ^ c1 ^ k0;
+        const uint32_t n2 = (uint32_t)(pa >> 32) ^ c3 ^ k1;
+        c1 = (uint32_t)pb;
+        c3 = (uint32_t)pa;
+        c0 = n0;
+        c2 = n2;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    u32x4 r;
+    r.v[0] = c0;
+    r.v[1] = c1;
+    r.v[2] = c2;
+    r.v[3] = c3;
+    return r;
+}
+
+// e^x on [-64, 0] from IEEE basic operations only, so that host and device
+// agree bit for bit: Cody-Waite reduction x = n*ln2 + r with ln2 split into
+// 0.693359375 + (-2.12194440e-4), then e^r by its degree-7 Taylor polynomial
+// (coefficients 1/k! rounded to FP32) in Horner form with fused multiply-adds,
+// and the factor 2^n assembled from exponent bits.
+__device__ __forceinline__ float exp_cw32(float x)
+{
+    const float n = rintf(__fmul_rn(x, 1.44269502f));
+    float r = __fmaf_rn(-n, 0.693359375f, x);
+    r = __fmaf_rn(-n, -2.12194440e-4f, r);
+    float p = 1.0f / 5040.0f;
+    p = __fmaf_rn(p, r, 1.0f / 720.0f);
+    p = __fmaf_rn(p, r, 1.0f / 120.0f);
+    p = __fmaf_rn(p, r, 1.0f / 24.0f);
+    p = __fmaf_rn(p, r, 1.0f / 6.0f);
+    p = __fmaf_rn(p, r, 0.5f);
+    p = __fmaf_rn(p, r, 1.0f);
+    p = __fmaf_rn(p, r, 1.0f);
+    const int ni = __float2int_rn(n);
+    return __fmul_rn(p, __int_as_float((ni + 127) << 23));
+}
+
+// Acceptance threshold for an FP32 log-probability x <= 0: a uniform 32-bit
+// word r is accepted iff r <= thr, i.e. with probability (thr + 1)/2^32.
+__device__ __forceinline__ uint32_t thr_of_logp(float x)
+{
+    const float xc = fmaxf(x, -64.0f);
+    const float v = __fmul_rn(exp_cw32(xc), 4294967296.0f);
+    uint32_t t = v >= 4294967296.0f ? 0xFFFFFFFFu : __float2uint_rz(v);
+    return x < -64.0f ? 0u : t;
+}
+
+}  // namespace sg

@@ -1,0 +1,1005 @@
+// sg_int8.cu -- int8-spin path of the EA spin-glass engine on B300 (sm_103a).
+//
+// One CTA owns one disorder sample at a time and keeps its whole state in
+// shared memory for a chunk of sweeps: the 2 x Tp chains (two replicas, Tp
+// temperature slots padded to a multiple of 4) of every site, the couplings,
+// the threshold table and the energies. The CTA runs the paper's method for
+// that sample (methods section: checkerboard single-spin Metropolis sweeps,
+// parallel tempering between neighbouring temperatures with two replicas per
+// temperature, overlap measurement after thermalisation), then writes the
+// state back. HBM is touched only at chunk boundaries, so the sweep loop is
+// bound by the SM's integer / FP32 issue rate rather than by HBM.
+//
+// Shared-memory layout of one sample:
+//   spins  [N][2*Tp] bytes   byte r*Tp + t of site i is replica r, slot t;
+//                            value 0 => +1, 1 => -1. A 32-bit word holds four
+//                            consecutive slots of one replica, so one
+//                            neighbour load serves four chains (SIMD within a
+//                            register).
+//   +-J    [N][8] bytes      bond bits (+x, -x, +y, -y, +z, -z, 0, 0), 1 => J = -1
+//   Gauss  [3][N] float      J[d][i] joins i and i + e_d
+// Work unit of a half-sweep: (run of RUN = lcm(L/2, 4) consecutive sites of one
+// colour, one 4-slot word). RUN is a multiple of 4, so the Philox calls (four
+// sites each) never straddle two units.
+#include <cuda_runtime.h>
+
+#include "sg_device.cuh"
+#include "sg_internal.h"
+
+namespace sg {
+
+namespace {
+
+constexpr int kMaxThreads = 512;
+
+__host__ __device__ constexpr int gcd_c(int a, int b) { return b == 0 ? a : gcd_c(b, a % b); }
+__host__ __device__ constexpr int lcm_c(int a, int b) { return a / gcd_c(a, b) * b; }
+
+__device__ __forceinline__ uint32_t lds32(const uint8_t *base, int off)
+{
+    return *reinterpret_cast<const uint32_t *>(base + off);
+}
+__device__ __forceinline__ void sts32(uint8_t *base, int off, uint32_t v)
+{
+    *reinterpret_cast<uint32_t *>(base + off) = v;
+}
+
+struct Smem {
+    uint8_t *spins;
+    uint8_t *J8;
+    float *Jg;
+    uint32_t *thr;
+    float *negbeta, *dbeta, *twid;
+    unsigned long long *B, *M;  // [2][Tp], two's complement int64
+    uint32_t *xflag;            // [2][Tp] exchange stamps
+    uint32_t *sel;              // [2][Tp/4][2] byte-permutation selectors
+    int *anyswap;               // [2]
+    uint32_t *marg;             // [mchunk][3][L*L] byte counts of q = -1
+};
+
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+// Carve the dynamic shared memory; returns the bytes used.
+__host__ __device__ inline size_t carve(uint8_t *base, int L, int Tp, bool gauss, int mchunk,
+                                        Smem *sm)
+{
+    const size_t N = (size_t)L * L * L;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        uint8_t *p = base ? base + off : nullptr;
+        off = align16(off + bytes);
+        return p;
+    };
+    Smem s;
+    s.spins = take(N * 2 * Tp);
+    s.J8 = gauss ? nullptr : take(N * 8);
+    s.Jg = gauss ? reinterpret_cast<float *>(take(N * 3 * sizeof(float))) : nullptr;
+    s.thr = gauss ? nullptr : reinterpret_cast<uint32_t *>(take((size_t)Tp * 16 * 4));
+    s.negbeta = reinterpret_cast<float *>(take((size_t)Tp * 4));
+    s.dbeta = reinterpret_cast<float *>(take((size_t)Tp * 4));
+    s.twid = reinterpret_cast<float *>(take((size_t)2 * L * 4));
+    s.B = reinterpret_cast<unsigned long long *>(take((size_t)2 * Tp * 8));
+    s.M = reinterpret_cast<unsigned long long *>(take((size_t)2 * Tp * 8));
+    s.xflag = reinterpret_cast<uint32_t *>(take((size_t)2 * Tp * 4));
+    s.sel = reinterpret_cast<uint32_t *>(take((size_t)2 * (Tp / 4) * 2 * 4));
+    s.anyswap = reinterpret_cast<int *>(take(2 * 4));
+    s.marg = reinterpret_cast<uint32_t *>(take((size_t)mchunk * 3 * L * L * 4));
+    if (sm) *sm = s;
+    return off;
+}
+
+struct Ctx {
+    int nt, Tp, WR, W, RB;
+    int64_t s;
+    uint32_t k0, k1;  // Metropolis Philox key
+    uint32_t seed_lo, seed_hi;
+    float hq;         // Gaussian: field on the 2^-17 grid
+};
+
+// ---------------------------------------------------------------------------
+// One checkerboard half-sweep of colour COL over all chains of the sample.
+// For COL == 1 it also accumulates B and M of the post-sweep configuration:
+// every bond has exactly one colour-1 end, so summing s_i * b_i over colour-1
+// sites counts each bond once; M pairs each colour-1 site with its x^1
+// partner (colour 0, final after the colour-0 half).
+// ---------------------------------------------------------------------------
+template <int L, bool GAUSS, int COL>
+__device__ __forceinline__ void half_sweep(const Smem &sm, const Ctx &cx, uint32_t n_sweep)
+{
+    constexpr int H = L / 2;
+    constexpr int N = L * L * L;
+    constexpr int RUN = lcm_c(H, 4);
+    constexpr int R = RUN / H;
+    constexpr int U = (N / 2) / RUN;
+    const int W = cx.W, RB = cx.RB;
+    const int w = threadIdx.x % W;  // fixed per thread: blockDim.x is a multiple of W
+    const int r = w / cx.WR;
+    const int t0 = 4 * (w % cx.WR);
+    const int items = U * W;
+
+    // bytes of real (not padding) slots in this thread's word
+    uint32_t valid = 0;
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk)
+        if (t0 + kk < cx.nt) valid |= 1u << (8 * kk);
+
+    long long bacc[4] = {0, 0, 0, 0};  // +-J: sum of u_new; Gauss: sum s*b/qJ
+    int macc_t[4] = {0, 0, 0, 0};      // count of -1 spins over site + partner
+    int nsites = 0;
+
+    float nbeta[4];
+    const uint32_t *thr_t[4];
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+        nbeta[kk] = GAUSS ? sm.negbeta[t0 + kk] : 0.0f;
+        thr_t[kk] = GAUSS ? nullptr : sm.thr + (t0 + kk) * 16;
+    }
+
+    for (int item = threadIdx.x; item < items; item += blockDim.x) {
+        const int u = item / W;
+        uint32_t eacc = 0, macc = 0;  // byte-wise partial sums over this run
+        int bgi[4] = {0, 0, 0, 0};    // Gauss: int32 partial of s*b/qJ
+        uint32_t rnd[4][4];
+#pragma unroll
+        for (int rho = 0; rho < R; ++rho) {
+            const int row = u * R + rho;
+            const int y = row % L;
+            const int z = row / L;
+            const int par = (COL + y + z) & 1;
+            const int dyp = (y == L - 1) ? -(L - 1) * L : L;
+            const int dym = (y == 0) ? (L - 1) * L : -L;
+            const int dzp = (z == L - 1) ? -(L - 1) * L * L : L * L;
+            const int dzm = (z == 0) ? (L - 1) * L * L : -L * L;
+#pragma unroll
+            for (int x2 = 0; x2 < H; ++x2) {
+                const int k = rho * H + x2;
+                if ((k & 3) == 0) {
+                    const uint32_t c0 = (uint32_t)(u * (RUN / 4) + (k >> 2));
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const uint32_t c2 = ((uint32_t)COL << 24) | ((uint32_t)r << 16) |
+                                            (uint32_t)(t0 + kk);
+                        const u32x4 o = philox10(cx.k0, cx.k1, c0, n_sweep, c2, cx.seed_hi);
+                        rnd[kk][0] = o.v[0];
+                        rnd[kk][1] = o.v[1];
+                        rnd[kk][2] = o.v[2];
+                        rnd[kk][3] = o.v[3];
+                    }
+                }
+                const int lane = k & 3;
+                const int x = 2 * x2 + par;
+                const int i = x + L * row;
+                const int dxp = (x == L - 1) ? -(L - 1) : 1;
+                const int dxm = (x == 0) ? (L - 1) : -1;
+                const int own = i * RB + 4 * w;
+                const uint32_t s = lds32(sm.spins, own);
+                const uint32_t nxp = lds32(sm.spins, own + dxp * RB);
+                const uint32_t nxm = lds32(sm.spins, own + dxm * RB);
+                const uint32_t nyp = lds32(sm.spins, own + dyp * RB);
+                const uint32_t nym = lds32(sm.spins, own + dym * RB);
+                const uint32_t nzp = lds32(sm.spins, own + dzp * RB);
+                const uint32_t nzm = lds32(sm.spins, own + dzm * RB);
+                uint32_t fm = 0;  // 0x01 in each flipped byte
+                if constexpr (!GAUSS) {
+                    const uint2 jb = *reinterpret_cast<const uint2 *>(sm.J8 + 8 * i);
+                    const uint32_t m0 = __byte_perm(jb.x, jb.y, 0x0000);
+                    const uint32_t m1 = __byte_perm(jb.x, jb.y, 0x1111);
+                    const uint32_t m2 = __byte_perm(jb.x, jb.y, 0x2222);
+                    const uint32_t m3 = __byte_perm(jb.x, jb.y, 0x3333);
+                    const uint32_t m4 = __byte_perm(jb.x, jb.y, 0x4444);
+                    const uint32_t m5 = __byte_perm(jb.x, jb.y, 0x5555);
+                    // unsatisfied-bond count per byte (0..6): s ^ s_nb ^ jbit
+                    const uint32_t uw = (s ^ nxp ^ m0) + (s ^ nxm ^ m1) + (s ^ nyp ^ m2) +
+                                        (s ^ nym ^ m3) + (s ^ nzp ^ m4) + (s ^ nzm ^ m5);
+                    const uint32_t idx = (s << 3) | uw;  // per byte: sb*8 + u
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const uint32_t th = thr_t[kk][(idx >> (8 * kk)) & 15u];
+                        fm |= (uint32_t)(rnd[kk][lane] <= th) << (8 * kk);
+                    }
+                    fm &= valid;
+                    if (COL == 1) {
+                        const uint32_t fm8 = fm * 0xFFu;
+                        const uint32_t unew = uw ^ ((uw ^ (0x06060606u - uw)) & fm8);
+                        eacc += unew;
+                    }
+                } else {
+                    const float j0 = sm.Jg[i];
+                    const float j1 = sm.Jg[i + dxm];
+                    const float j2 = sm.Jg[N + i];
+                    const float j3 = sm.Jg[N + i + dym];
+                    const float j4 = sm.Jg[2 * N + i];
+                    const float j5 = sm.Jg[2 * N + i + dzm];
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const int sh = 31 - 8 * kk;
+                        // J * s_nb: flip the sign bit of J where the neighbour is -1
+                        float b = __int_as_float(__float_as_int(j0) ^ ((nxp << sh) & 0x80000000u));
+                        b = __fadd_rn(b, __int_as_float(__float_as_int(j1) ^ ((nxm << sh) & 0x80000000u)));
+                        b = __fadd_rn(b, __int_as_float(__float_as_int(j2) ^ ((nyp << sh) & 0x80000000u)));
+                        b = __fadd_rn(b, __int_as_float(__float_as_int(j3) ^ ((nym << sh) & 0x80000000u)));
+                        b = __fadd_rn(b, __int_as_float(__float_as_int(j4) ^ ((nzp << sh) & 0x80000000u)));
+                        b = __fadd_rn(b, __int_as_float(__float_as_int(j5) ^ ((nzm << sh) & 0x80000000u)));
+                        const uint32_t sgn = (s << sh) & 0x80000000u;  // own spin -1 => sign bit
+                        const float zf = __fadd_rn(b, cx.hq);
+                        const float dE = __int_as_float(__float_as_int(__fadd_rn(zf, zf)) ^ sgn);
+                        const float xl = __fmul_rn(nbeta[kk], dE);
+                        const bool acc = (dE <= 0.0f) || (rnd[kk][lane] <= thr_of_logp(xl));
+                        const uint32_t flip = acc && (valid >> (8 * kk) & 1u);
+                        fm |= flip << (8 * kk);
+                        if (COL == 1) {
+                            const int bq = __float2int_rn(__fmul_rn(b, 131072.0f));
+                            // s_new * b / qJ, s_new = -1 when (old bit) xor flip is 1
+                            bgi[kk] += (((s >> (8 * kk)) ^ flip) & 1u) ? -bq : bq;
+                        }
+                    }
+                }
+                const uint32_t snew = s ^ fm;
+                sts32(sm.spins, own, snew);
+                if (COL == 1) {
+                    const uint32_t partner = (x & 1) ? nxm : nxp;
+                    macc += snew + partner;
+                }
+            }
+        }
+        if (COL == 1) {
+            nsites += RUN;
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                if (!GAUSS)
+                    bacc[kk] += (eacc >> (8 * kk)) & 0xFFu;
+                else
+                    bacc[kk] += bgi[kk];
+                macc_t[kk] += (macc >> (8 * kk)) & 0xFFu;
+            }
+        }
+    }
+    if (COL == 1 && nsites > 0) {
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+            const int t = t0 + kk;
+            if (t >= cx.nt) continue;
+            // +-J: s b = 6 - 2u per colour-1 site; M: each pair contributes 2 - 2*(#-1)
+            const long long b = GAUSS ? bacc[kk] : 6LL * nsites - 2LL * bacc[kk];
+            const long long m = 2LL * nsites - 2LL * macc_t[kk];
+            atomicAdd(&sm.B[r * cx.Tp + t], (unsigned long long)b);
+            atomicAdd(&sm.M[r * cx.Tp + t], (unsigned long long)m);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Replica exchange between slots p and p+1 of each replica (pairs of one
+// parity), then the state swap of accepted pairs as byte permutations of the
+// 4-slot words. stamp identifies this exchange in xflag.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void exchange_decide(const Smem &sm, const Ctx &cx, const Int8Args &a,
+                                                int parity, uint32_t ctr1, uint32_t rflag,
+                                                uint32_t stamp)
+{
+    const int nt = cx.nt, Tp = cx.Tp;
+    const int np = (nt - parity) / 2;
+    for (int id = threadIdx.x; id < 2 * np; id += blockDim.x) {
+        const int r = id / np;
+        const int p = parity + 2 * (id % np);
+        if (p + 1 >= nt) continue;
+        unsigned long long *Bp = sm.B + r * Tp + p;
+        unsigned long long *Mp = sm.M + r * Tp + p;
+        const long long dB = (long long)Bp[0] - (long long)Bp[1];
+        const long long dM = (long long)Mp[0] - (long long)Mp[1];
+        const float t1 = __fmul_rn(__ll2float_rn(dB), a.qJ_f);
+        const float t2 = __fmul_rn(a.h_f, __ll2float_rn(dM));
+        const float dE = -__fadd_rn(t1, t2);
+        const float D = __fmul_rn(sm.dbeta[p], dE);
+        const u32x4 o = philox10(cx.seed_lo ^ kTagExc, (uint32_t)cx.s, (uint32_t)p, ctr1,
+                                 (uint32_t)r | rflag, cx.seed_hi);
+        const bool acc = (D >= 0.0f) || (o.v[0] <= thr_of_logp(D));
+        if (acc) {
+            const unsigned long long tb = Bp[0];
+            Bp[0] = Bp[1];
+            Bp[1] = tb;
+            const unsigned long long tm = Mp[0];
+            Mp[0] = Mp[1];
+            Mp[1] = tm;
+            sm.xflag[r * Tp + p] = stamp;
+        }
+    }
+}
+
+template <int L>
+__device__ __forceinline__ void exchange_apply(const Smem &sm, const Ctx &cx, uint32_t stamp)
+{
+    constexpr int N = L * L * L;
+    const int nt = cx.nt, Tp = cx.Tp, WR = cx.WR;
+    if (threadIdx.x < 2) sm.anyswap[threadIdx.x] = 0;
+    __syncthreads();
+    for (int id = threadIdx.x; id < 2 * WR; id += blockDim.x) {
+        const int r = id / WR, j = id % WR;
+        const uint32_t *fl = sm.xflag + r * Tp;
+        uint32_t s1 = 0, s2 = 0;
+        bool any = false;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int t = 4 * j + k;
+            int src = t;
+            if (t + 1 < nt && fl[t] == stamp) src = t + 1;
+            else if (t >= 1 && t < nt && fl[t - 1] == stamp) src = t - 1;
+            any |= (src != t);
+            // first permutation over {next word : this word}, second brings in
+            // byte 3 of the previous word
+            uint32_t n1 = (uint32_t)k, n2 = (uint32_t)k;
+            if (src >= 4 * j && src < 4 * j + 4) n1 = (uint32_t)(src - 4 * j);
+            else if (src == 4 * j + 4) n1 = 4u;
+            else n2 = 7u;  // src == 4j - 1
+            s1 |= n1 << (4 * k);
+            s2 |= n2 << (4 * k);
+        }
+        sm.sel[(r * WR + j) * 2 + 0] = s1;
+        sm.sel[(r * WR + j) * 2 + 1] = s2;
+        if (any) atomicOr(&sm.anyswap[r], 1);
+    }
+    __syncthreads();
+    const int RB = cx.RB;
+    for (int id = threadIdx.x; id < 2 * N; id += blockDim.x) {
+        const int r = id & 1, site = id >> 1;
+        if (!sm.anyswap[r]) continue;
+        uint8_t *row = sm.spins + site * RB + r * Tp;
+        const uint32_t *sel = sm.sel + r * WR * 2;
+        uint32_t prev = 0, cur = lds32(row, 0);
+        for (int j = 0; j < WR; ++j) {
+            const uint32_t next = (j + 1 < WR) ? lds32(row, 4 * (j + 1)) : 0u;
+            const uint32_t tmp = __byte_perm(cur, next, sel[2 * j]);
+            sts32(row, 4 * j, __byte_perm(tmp, prev, sel[2 * j + 1]));
+            prev = cur;
+            cur = next;
+        }
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Overlap measurement (eq. overlap) for every slot: q = s^(0) s^(1); 2D
+// marginals of the q = -1 counts over the xy, xz and yz planes; the nine
+// projections P_v[d] (v over the k1 and k2 orbits); FP32 DFT of each
+// projection; FP64 accumulation.
+// ---------------------------------------------------------------------------
+template <int L>
+__device__ __forceinline__ void measure_step(const Smem &sm, const Ctx &cx, const Int8Args &a)
+{
+    constexpr int N = L * L * L;
+    constexpr int LL = L * L;
+    const int WR = cx.WR, RB = cx.RB, Tp = cx.Tp, nt = cx.nt;
+    double *accs = a.acc + (size_t)cx.s * nt * SG_NACC;
+    for (int j0 = 0; j0 < WR; j0 += a.mchunk) {
+        const int nw = min(a.mchunk, WR - j0);
+        for (int id = threadIdx.x; id < nw * 3 * LL; id += blockDim.x) {
+            const int jj = id / (3 * LL);
+            const int rem = id % (3 * LL);
+            const int plane = rem / LL;
+            const int ab = rem % LL;
+            const int A = ab / L, Bc = ab % L;
+            int base, step;
+            if (plane == 0) {        // (x=A, y=Bc), over z
+                base = A + L * Bc;
+                step = LL;
+            } else if (plane == 1) { // (x=A, z=Bc), over y
+                base = A + LL * Bc;
+                step = L;
+            } else {                 // (y=A, z=Bc), over x
+                base = L * A + LL * Bc;
+                step = 1;
+            }
+            const int woff = 4 * (j0 + jj);
+            uint32_t cnt = 0;
+#pragma unroll 4
+            for (int m = 0; m < L; ++m) {
+                const int off = (base + m * step) * RB + woff;
+                cnt += lds32(sm.spins, off) ^ lds32(sm.spins, off + Tp);
+            }
+            sm.marg[id] = cnt;
+        }
+        __syncthreads();
+        for (int id = threadIdx.x; id < nw * 4 * 10; id += blockDim.x) {
+            const int v = id % 10;
+            const int rest = id / 10;
+            const int kk = rest % 4;
+            const int jj = rest / 4;
+            const int t = 4 * (j0 + jj) + kk;
+            if (t >= nt) continue;
+            const uint32_t *mg = sm.marg + jj * 3 * LL;
+            const int sh = 8 * kk;
+            double *ac = accs + (size_t)t * SG_NACC;
+            if (v == 9) {
+                int cq = 0;
+                for (int e = 0; e < LL; ++e) cq += (mg[e] >> sh) & 0xFF;
+                const double Q = (double)(N - 2 * cq);
+                const double Q2 = __dmul_rn(Q, Q);
+                ac[0] = __dadd_rn(ac[0], 1.0);
+                ac[1] = __dadd_rn(ac[1], Q);
+                ac[2] = __dadd_rn(ac[2], Q2);
+                ac[3] = __dadd_rn(ac[3], __dmul_rn(Q2, Q));
+                ac[4] = __dadd_rn(ac[4], __dmul_rn(Q2, Q2));
+                for (int r = 0; r < 2; ++r) {
+                    const long long Bv = (long long)sm.B[r * Tp + t];
+                    const long long Mv = (long long)sm.M[r * Tp + t];
+                    const double e = -__dadd_rn(__dmul_rn((double)Bv, a.qJ_d),
+                                                __dmul_rn(a.h_d, (double)Mv));
+                    ac[5] = __dadd_rn(ac[5], e);
+                    ac[6] = __dadd_rn(ac[6], __dmul_rn(e, e));
+                }
+                for (int r = 0; r < 2; ++r) {
+                    const double m = (double)(long long)sm.M[r * Tp + t];
+                    ac[7] = __dadd_rn(ac[7], m);
+                    ac[8] = __dadd_rn(ac[8], __dmul_rn(m, m));
+                }
+                continue;
+            }
+            // plane and index map of the projection for wave vector v
+            const int plane = (v == 0 || v == 1 || v == 3 || v == 4) ? 0
+                              : (v == 2 || v == 5 || v == 6)         ? 1
+                                                                     : 2;
+            const uint32_t *pm = mg + plane * LL;
+            float re = 0.0f, im = 0.0f;
+            for (int d = 0; d < L; ++d) {
+                int cs = 0;
+                for (int aa = 0; aa < L; ++aa) {
+                    int A, Bc;
+                    switch (v) {
+                    case 0: A = d; Bc = aa; break;                 // x = d
+                    case 1: A = aa; Bc = d; break;                 // y = d
+                    case 2: A = aa; Bc = d; break;                 // z = d (xz plane)
+                    case 3: case 5: case 7: A = aa; Bc = (d - aa + L) % L; break;  // a + b = d
+                    default: A = aa; Bc = (aa - d + L) % L; break;                 // a - b = d
+                    }
+                    cs += (pm[A * L + Bc] >> sh) & 0xFF;
+                }
+                const float P = (float)(LL - 2 * cs);
+                re = __fmaf_rn(P, sm.twid[d], re);
+                im = __fmaf_rn(P, sm.twid[L + d], im);
+            }
+            const double dr = (double)re, di = (double)im;
+            ac[9 + 3 * v] = __dadd_rn(ac[9 + 3 * v], dr);
+            ac[10 + 3 * v] = __dadd_rn(ac[10 + 3 * v], di);
+            ac[11 + 3 * v] = __dadd_rn(ac[11 + 3 * v], __dadd_rn(__dmul_rn(dr, dr), __dmul_rn(di, di)));
+        }
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ void copy16(void *dst, const void *src, size_t bytes)
+{
+    int4 *d = reinterpret_cast<int4 *>(dst);
+    const int4 *s = reinterpret_cast<const int4 *>(src);
+    for (size_t k = threadIdx.x; k < bytes / 16; k += blockDim.x) d[k] = s[k];
+}
+
+// ---------------------------------------------------------------------------
+// The fused kernel: for each sample of this CTA, load, run n_sweeps sweeps
+// (half-sweeps, energies, exchange, measurement), store.
+// ---------------------------------------------------------------------------
+template <int L, bool GAUSS>
+__global__ void __launch_bounds__(kMaxThreads) int8_run_kernel(const Int8Args a)
+{
+    constexpr int N = L * L * L;
+    extern __shared__ __align__(16) uint8_t smem_raw[];
+    Smem sm;
+    carve(smem_raw, L, a.Tp, GAUSS, a.mchunk, &sm);
+    Ctx cx;
+    cx.nt = a.nt;
+    cx.Tp = a.Tp;
+    cx.WR = a.Tp / 4;
+    cx.W = a.Tp / 2;
+    cx.RB = 2 * a.Tp;
+    cx.seed_lo = a.seed_lo;
+    cx.seed_hi = a.seed_hi;
+    cx.hq = a.h_f;
+    const long long t_start = clock64();
+
+    // per-launch tables
+    for (int k = threadIdx.x; k < a.Tp; k += blockDim.x) {
+        sm.negbeta[k] = a.negbeta[k];
+        sm.dbeta[k] = a.dbeta[k];
+    }
+    for (int k = threadIdx.x; k < 2 * L; k += blockDim.x) sm.twid[k] = a.twid[k];
+    if (!GAUSS)
+        for (int k = threadIdx.x; k < a.Tp * 16; k += blockDim.x) sm.thr[k] = a.thr[k];
+
+    for (int64_t s = a.s_begin + blockIdx.x; s < a.s_end; s += gridDim.x) {
+        cx.s = s;
+        cx.k0 = a.seed_lo ^ kTagMet;
+        cx.k1 = (uint32_t)(s / a.rng_group);
+        __syncthreads();
+        copy16(sm.spins, a.spins + (size_t)s * N * cx.RB, (size_t)N * cx.RB);
+        if (!GAUSS)
+            copy16(sm.J8, a.J8 + (size_t)s * N * 8, (size_t)N * 8);
+        else
+            copy16(sm.Jg, a.Jg + (size_t)s * 3 * N, (size_t)3 * N * sizeof(float));
+        for (int k = threadIdx.x; k < 2 * a.Tp; k += blockDim.x) {
+            sm.xflag[k] = 0;
+            sm.B[k] = (unsigned long long)a.B[s * 2 * a.Tp + k];
+            sm.M[k] = (unsigned long long)a.M[s * 2 * a.Tp + k];
+        }
+        __syncthreads();
+
+        uint32_t stamp = 0;
+        bool stop = false;
+        const int64_t sweep0 = a.sweep0_dev ? *a.sweep0_dev : a.sweep0;
+        for (int it = 0; it < a.n_sweeps; ++it) {
+            const int64_t n = sweep0 + it;
+            if (a.watchdog || a.cancel) {  // launch-uniform branch
+                int why = 0;
+                if (threadIdx.x == 0) {
+                    if (a.watchdog && (unsigned long long)(clock64() - t_start) > a.watchdog)
+                        why = (int)SG_ETIMEOUT;
+                    else if (a.cancel && *a.cancel)
+                        why = (int)SG_ECANCELLED;
+                    if (why) atomicCAS(a.status, 0, why);
+                }
+                stop = __syncthreads_or(why != 0);
+                if (stop) break;
+            }
+            half_sweep<L, GAUSS, 0>(sm, cx, (uint32_t)n);
+            for (int k = threadIdx.x; k < 2 * a.Tp; k += blockDim.x) {
+                sm.B[k] = 0;
+                sm.M[k] = 0;
+            }
+            __syncthreads();
+            half_sweep<L, GAUSS, 1>(sm, cx, (uint32_t)n);
+            __syncthreads();
+            if (a.exchange_every > 0 && (n + 1) % a.exchange_every == 0) {
+                const int64_t e = (n + 1) / a.exchange_every - 1;
+                ++stamp;
+                exchange_decide(sm, cx, a, (int)(e & 1), (uint32_t)n, 0u, stamp);
+                __syncthreads();
+                exchange_apply<L>(sm, cx, stamp);
+            }
+            if (n >= a.n_therm && (n - a.n_therm) % a.measure_every == 0) measure_step<L>(sm, cx, a);
+        }
+        __syncthreads();
+        copy16(a.spins + (size_t)s * N * cx.RB, sm.spins, (size_t)N * cx.RB);
+        for (int k = threadIdx.x; k < 2 * a.Tp; k += blockDim.x) {
+            a.B[s * 2 * a.Tp + k] = (int64_t)sm.B[k];
+            a.M[s * 2 * a.Tp + k] = (int64_t)sm.M[k];
+        }
+        // a stopped launch leaves later samples untouched; the status word tells
+        if (__syncthreads_or(stop)) break;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Instance preparation, conversion and standalone kernels (global memory).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int site_nb(int L, int i, int d, int step)
+{
+    int x = i % L, y = (i / L) % L, z = i / (L * L);
+    if (d == 0) x = (x + step + L) % L;
+    if (d == 1) y = (y + step + L) % L;
+    if (d == 2) z = (z + step + L) % L;
+    return x + L * (y + L * z);
+}
+
+__global__ void gen_pmj_kernel(uint8_t *J8, int64_t S, int L, uint32_t slo, uint32_t shi)
+{
+    const int N = L * L * L;
+    const int64_t total = S * N;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = g / N;
+        const int i = (int)(g % N);
+        uint8_t out[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int d = 0; d < 3; ++d) {
+            for (int side = 0; side < 2; ++side) {
+                const int owner = side == 0 ? i : site_nb(L, i, d, -1);  // bond owner site
+                const u32x4 o = philox10(slo ^ kTagBond, (uint32_t)s, (uint32_t)(owner >> 7),
+                                         (uint32_t)d, 0u, shi);
+                out[2 * d + side] = (uint8_t)((o.v[(owner >> 5) & 3] >> (owner & 31)) & 1u);
+            }
+        }
+        uint2 v;
+        v.x = out[0] | (out[1] << 8) | (out[2] << 16) | ((uint32_t)out[3] << 24);
+        v.y = out[4] | (out[5] << 8);
+        reinterpret_cast<uint2 *>(J8)[g] = v;
+    }
+}
+
+__global__ void gen_gauss_kernel(float *Jg, int64_t S, int L, uint32_t slo, uint32_t shi)
+{
+    const int N = L * L * L;
+    const int64_t pairs = S * 3 * (int64_t)((N + 1) / 2);
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < pairs;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const int half = (N + 1) / 2;
+        const int64_t s = g / (3 * half);
+        const int d = (int)((g / half) % 3);
+        const int m = (int)(g % half);
+        const u32x4 o = philox10(slo ^ kTagBond, (uint32_t)s, (uint32_t)m, (uint32_t)d, 1u, shi);
+        // two uniforms in (0, 1) with 53 bits each, then Box-Muller
+        const uint64_t a53 = (((uint64_t)o.v[0] << 21) ^ (o.v[1] >> 11)) & ((1ull << 53) - 1);
+        const uint64_t b53 = (((uint64_t)o.v[2] << 21) ^ (o.v[3] >> 11)) & ((1ull << 53) - 1);
+        const double u1 = ((double)a53 + 0.5) * 0x1.0p-53;
+        const double u2 = ((double)b53 + 0.5) * 0x1.0p-53;
+        const double rad = sqrt(-2.0 * log(u1));
+        double sn, cs;
+        sincospi(2.0 * u2, &sn, &cs);
+        const double gv[2] = {rad * cs, rad * sn};
+        for (int q = 0; q < 2; ++q) {
+            const int i = 2 * m + q;
+            if (i >= N) break;
+            double v = rint(gv[q] * 131072.0);
+            v = fmin(fmax(v, -16.0 * 131072.0), 16.0 * 131072.0);
+            Jg[(s * 3 + d) * N + i] = (float)(v / 131072.0);
+        }
+    }
+}
+
+__global__ void gen_spins_kernel(uint8_t *spins, int64_t S, int L, int nt, int Tp, uint32_t slo,
+                                 uint32_t shi)
+{
+    const int N = L * L * L;
+    const int RB = 2 * Tp;
+    const int64_t total = S * N * (int64_t)RB;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = g / ((int64_t)N * RB);
+        const int i = (int)((g / RB) % N);
+        const int rb = (int)(g % RB);
+        const int r = rb / Tp, t = rb % Tp;
+        uint8_t v = 0;
+        if (t < nt) {
+            const u32x4 o = philox10(slo ^ kTagInit, (uint32_t)s, (uint32_t)(i >> 7),
+                                     ((uint32_t)r << 16) | (uint32_t)t, 0u, shi);
+            v = (uint8_t)((o.v[(i >> 5) & 3] >> (i & 31)) & 1u);
+        }
+        spins[g] = v;
+    }
+}
+
+__global__ void import_J_kernel(uint8_t *J8, float *Jg, const float *Jc, int64_t S, int L,
+                                int gauss)
+{
+    const int N = L * L * L;
+    const int64_t total = S * N;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = g / N;
+        const int i = (int)(g % N);
+        const float *Js = Jc + s * 3 * N;
+        if (gauss) {
+            for (int d = 0; d < 3; ++d) Jg[(s * 3 + d) * N + i] = Js[d * N + i];
+        } else {
+            uint8_t out[6];
+            for (int d = 0; d < 3; ++d) {
+                out[2 * d] = Js[d * N + i] < 0.0f;
+                out[2 * d + 1] = Js[d * N + site_nb(L, i, d, -1)] < 0.0f;
+            }
+            uint2 v;
+            v.x = out[0] | (out[1] << 8) | (out[2] << 16) | ((uint32_t)out[3] << 24);
+            v.y = out[4] | (out[5] << 8);
+            reinterpret_cast<uint2 *>(J8)[g] = v;
+        }
+    }
+}
+
+__global__ void export_J_kernel(float *Jc, const uint8_t *J8, const float *Jg, int64_t S, int L,
+                                int gauss)
+{
+    const int N = L * L * L;
+    const int64_t total = S * 3 * (int64_t)N;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = g / (3 * N);
+        const int d = (int)((g / N) % 3);
+        const int i = (int)(g % N);
+        Jc[g] = gauss ? Jg[g] : (J8[(s * N + i) * 8 + 2 * d] ? -1.0f : 1.0f);
+    }
+}
+
+__global__ void import_spins_kernel(uint8_t *spins, const int8_t *c, int64_t S, int L, int nt,
+                                    int Tp)
+{
+    const int N = L * L * L;
+    const int RB = 2 * Tp;
+    const int64_t total = S * N * (int64_t)RB;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = g / ((int64_t)N * RB);
+        const int i = (int)((g / RB) % N);
+        const int rb = (int)(g % RB);
+        const int r = rb / Tp, t = rb % Tp;
+        spins[g] = t < nt ? (uint8_t)(c[((s * 2 + r) * nt + t) * N + i] < 0) : (uint8_t)0;
+    }
+}
+
+__global__ void export_spins_kernel(int8_t *c, const uint8_t *spins, int64_t S, int L, int nt,
+                                    int Tp)
+{
+    const int N = L * L * L;
+    const int64_t total = S * 2 * (int64_t)nt * N;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(g % N);
+        const int t = (int)((g / N) % nt);
+        const int r = (int)((g / ((int64_t)N * nt)) % 2);
+        const int64_t s = g / ((int64_t)2 * nt * N);
+        c[g] = spins[(s * N + i) * (2 * Tp) + r * Tp + t] ? -1 : 1;
+    }
+}
+
+// Energies straight from the bond sum, one thread per chain (small helper
+// used at creation and by the standalone exchange).
+__device__ void chain_energy(const Int8Args &a, int L, bool gauss, int64_t s, int r, int t,
+                             long long *Bo, long long *Mo)
+{
+    const int N = L * L * L;
+    const int RB = 2 * a.Tp;
+    const uint8_t *sp = a.spins + (size_t)s * N * RB + r * a.Tp + t;
+    long long b = 0, m = 0;
+    for (int i = 0; i < N; ++i) {
+        const int si = sp[(size_t)i * RB] ? -1 : 1;
+        m += si;
+        for (int d = 0; d < 3; ++d) {
+            const int j = site_nb(L, i, d, +1);
+            const int sj = sp[(size_t)j * RB] ? -1 : 1;
+            long long jq;
+            if (gauss)
+                jq = __float2ll_rn(__fmul_rn(a.Jg[((size_t)s * 3 + d) * N + i], 131072.0f));
+            else
+                jq = a.J8[((size_t)s * N + i) * 8 + 2 * d] ? -1 : 1;
+            b += jq * si * sj;
+        }
+    }
+    *Bo = b;
+    *Mo = m;
+}
+
+__global__ void energies_kernel(const Int8Args a, int L, int gauss)
+{
+    const int64_t total = (a.s_end - a.s_begin) * 2 * a.Tp;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = a.s_begin + g / (2 * a.Tp);
+        const int r = (int)((g / a.Tp) % 2), t = (int)(g % a.Tp);
+        long long b = 0, m = 0;
+        if (t < a.nt) chain_energy(a, L, gauss, s, r, t, &b, &m);
+        a.B[s * 2 * a.Tp + r * a.Tp + t] = b;
+        a.M[s * 2 * a.Tp + r * a.Tp + t] = m;
+    }
+}
+
+// Standalone exchange: one CTA per sample, on the global-memory state.
+__global__ void exchange_kernel(const Int8Args a, int L, int parity, uint32_t call_id)
+{
+    const int N = L * L * L;
+    const int Tp = a.Tp, nt = a.nt, RB = 2 * Tp;
+    __shared__ int accept[2][64];
+    for (int64_t s = a.s_begin + blockIdx.x; s < a.s_end; s += gridDim.x) {
+        __syncthreads();
+        for (int k = threadIdx.x; k < 128; k += blockDim.x) accept[k / 64][k % 64] = 0;
+        __syncthreads();
+        const int np = (nt - parity) / 2;
+        for (int id = threadIdx.x; id < 2 * np; id += blockDim.x) {
+            const int r = id / np;
+            const int p = parity + 2 * (id % np);
+            int64_t *Bp = a.B + s * 2 * Tp + r * Tp + p;
+            int64_t *Mp = a.M + s * 2 * Tp + r * Tp + p;
+            const long long dB = Bp[0] - Bp[1];
+            const long long dM = Mp[0] - Mp[1];
+            const float t1 = __fmul_rn(__ll2float_rn(dB), a.qJ_f);
+            const float t2 = __fmul_rn(a.h_f, __ll2float_rn(dM));
+            const float dE = -__fadd_rn(t1, t2);
+            const float D = __fmul_rn(a.dbeta[p], dE);
+            const u32x4 o = philox10(a.seed_lo ^ kTagExc, (uint32_t)s, (uint32_t)p, call_id,
+                                     (uint32_t)r | 0x100u, a.seed_hi);
+            if ((D >= 0.0f) || (o.v[0] <= thr_of_logp(D))) {
+                accept[r][p] = 1;
+                const int64_t tb = Bp[0];
+                Bp[0] = Bp[1];
+                Bp[1] = tb;
+                const int64_t tm = Mp[0];
+                Mp[0] = Mp[1];
+                Mp[1] = tm;
+            }
+        }
+        __syncthreads();
+        uint8_t *sp = a.spins + (size_t)s * N * RB;
+        for (int id = threadIdx.x; id < N * 2 * (nt / 2 + 1); id += blockDim.x) {
+            const int i = id % N;
+            const int rest = id / N;
+            const int r = rest % 2;
+            const int p = parity + 2 * (rest / 2);
+            if (p + 1 >= nt || !accept[r][p]) continue;
+            uint8_t *row = sp + (size_t)i * RB + r * Tp;
+            const uint8_t tv = row[p];
+            row[p] = row[p + 1];
+            row[p + 1] = tv;
+        }
+    }
+}
+
+// q(k) for arbitrary integer k: one thread per (sample, slot, k).
+__global__ void measure_k_kernel(const Int8Args a, int L, const int *kv, int nk, float *out)
+{
+    const int N = L * L * L;
+    const int RB = 2 * a.Tp;
+    const int64_t total = (a.s_end - a.s_begin) * a.nt * (int64_t)nk;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const int j = (int)(g % nk);
+        const int t = (int)((g / nk) % a.nt);
+        const int64_t s = a.s_begin + g / ((int64_t)nk * a.nt);
+        const uint8_t *sp = a.spins + (size_t)s * N * RB;
+        float re = 0.0f, im = 0.0f;
+        for (int i = 0; i < N; ++i) {
+            const int x = i % L, y = (i / L) % L, z = i / (L * L);
+            const int q = (sp[(size_t)i * RB + t] ^ sp[(size_t)i * RB + a.Tp + t]) ? -1 : 1;
+            int ph = (kv[3 * j] * x + kv[3 * j + 1] * y + kv[3 * j + 2] * z) % L;
+            if (ph < 0) ph += L;
+            float sn, cs;
+            sincospif(2.0f * (float)ph / (float)L, &sn, &cs);
+            re += q * cs;
+            im += q * sn;
+        }
+        out[2 * g] = re / (float)N;
+        out[2 * g + 1] = im / (float)N;
+    }
+}
+
+__global__ void advance_kernel(int64_t *ctr, int64_t n)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) *ctr += n;
+}
+
+inline int grid_for(int64_t work, int threads)
+{
+    int64_t b = (work + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > 148 * 32) b = 148 * 32;
+    return (int)b;
+}
+
+constexpr int kMaxSmem = 227 * 1024;
+
+// Raise the kernel's dynamic shared-memory limit once (before any capture).
+template <int L, bool G>
+cudaError_t ensure_attr()
+{
+    static cudaError_t done = cudaFuncSetAttribute(
+        int8_run_kernel<L, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+    return done;
+}
+
+template <int L, bool G>
+cudaError_t launch_t(const Int8Args &a, const Int8Launch &c, cudaStream_t st)
+{
+    cudaError_t e = ensure_attr<L, G>();
+    if (e != cudaSuccess) return e;
+    int8_run_kernel<L, G><<<c.grid, c.threads, c.smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int L, bool G>
+int occ_t(int threads, size_t smem)
+{
+    auto k = int8_run_kernel<L, G>;
+    if (ensure_attr<L, G>() != cudaSuccess) return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, threads, smem) != cudaSuccess)
+        return 0;
+    return n;
+}
+
+#define SG_FOR_EACH_L(X) X(2) X(4) X(6) X(8) X(10) X(12) X(14) X(16)
+
+}  // namespace
+
+size_t int8_smem_bytes(int L, int Tp, bool gauss, int mchunk)
+{
+    size_t b = carve(nullptr, L, Tp, gauss, mchunk, nullptr);
+    return b <= (size_t)kMaxSmem ? b : 0;
+}
+
+int int8_max_threads() { return kMaxThreads; }
+
+cudaError_t int8_launch(int L, bool gauss, const Int8Args &a, const Int8Launch &cfg,
+                        cudaStream_t st)
+{
+#define X(LL)                                                                           \
+    if (L == LL) return gauss ? launch_t<LL, true>(a, cfg, st) : launch_t<LL, false>(a, cfg, st);
+    SG_FOR_EACH_L(X)
+#undef X
+    return cudaErrorInvalidValue;
+}
+
+int int8_ctas_per_sm(int L, bool gauss, int threads, size_t smem)
+{
+#define X(LL) \
+    if (L == LL) return gauss ? occ_t<LL, true>(threads, smem) : occ_t<LL, false>(threads, smem);
+    SG_FOR_EACH_L(X)
+#undef X
+    return 0;
+}
+
+cudaError_t int8_gen_pmj(uint8_t *J8, int64_t S, int L, uint32_t slo, uint32_t shi,
+                         cudaStream_t st)
+{
+    gen_pmj_kernel<<<grid_for(S * L * L * L, 256), 256, 0, st>>>(J8, S, L, slo, shi);
+    return cudaGetLastError();
+}
+
+cudaError_t int8_gen_gauss(float *Jg, int64_t S, int L, uint32_t slo, uint32_t shi,
+                           cudaStream_t st)
+{
+    gen_gauss_kernel<<<grid_for(S * 3 * (L * L * L + 1) / 2, 256), 256, 0, st>>>(Jg, S, L, slo,
+                                                                                  shi);
+    return cudaGetLastError();
+}
+
+cudaError_t int8_gen_spins(uint8_t *spins, int64_t S, int L, int nt, int Tp, uint32_t slo,
+                           uint32_t shi, cudaStream_t st)
+{
+    gen_spins_kernel<<<grid_for(S * L * L * L * 2 * Tp, 256), 256, 0, st>>>(spins, S, L, nt, Tp,
+                                                                             slo, shi);
+    return cudaGetLastError();
+}
+
+cudaError_t int8_import_J(uint8_t *J8, float *Jg, const float *Jc, int64_t S, int L, bool gauss,
+                          cudaStream_t st)
+{
+    import_J_kernel<<<grid_for(S * L * L * L, 256), 256, 0, st>>>(J8, Jg, Jc, S, L, gauss);
+    return cudaGetLastError();
+}
+
+cudaError_t int8_export_J(float *Jc, const uint8_t *J8, const float *Jg, int64_t S, int L,
+                          bool gauss, cudaStream_t st)
+{
+    export_J_kernel<<<grid_for(S * 3 * L * L * L, 256), 256, 0, st>>>(Jc, J8, Jg, S, L, gauss);
+    return cudaGetLastError();
+}
+
+cudaError_t int8_import_spins(uint8_t *spins, const int8_t *c, int64_t S, int L, int nt, int Tp,
+                              cudaStream_t st)
+{
+    import_spins_kernel<<<grid_for(S * L * L * L * 2 * Tp, 256), 256, 0, st>>>(spins, c, S, L,
+                                                                                nt, Tp);
+    return cudaGetLastError();
+}
+
+cudaError_t int8_export_spins(int8_t *c, const uint8_t *spins, int64_t S, int L, int nt, int Tp,
+                              cudaStream_t st)
+{
+    export_spins_kernel<<<grid_for(S * 2 * nt * L * L * L, 256), 256, 0, st>>>(c, spins, S, L,
+                                                                                nt, Tp);
+    return cudaGetLastError();
+}
+
+cudaError_t int8_energies(const Int8Args &a, int L, bool gauss, cudaStream_t st)
+{
+    energies_kernel<<<grid_for((a.s_end - a.s_begin) * 2 * a.Tp, 128), 128, 0, st>>>(a, L, gauss);
+    return cudaGetLastError();
+}
+
+cudaError_t int8_exchange(const Int8Args &a, int L, bool gauss, int parity, uint32_t call_id,
+                          cudaStream_t st)
+{
+    cudaError_t e = int8_energies(a, L, gauss, st);
+    if (e != cudaSuccess) return e;
+    const int64_t n = a.s_end - a.s_begin;
+    exchange_kernel<<<(int)(n < 148 * 16 ? n : 148 * 16), 256, 0, st>>>(a, L, parity & 1, call_id);
+    return cudaGetLastError();
+}
+
+cudaError_t advance_counter(int64_t *ctr, int64_t n, cudaStream_t st)
+{
+    advance_kernel<<<1, 32, 0, st>>>(ctr, n);
+    return cudaGetLastError();
+}
+
+cudaError_t int8_measure_k(const Int8Args &a, int L, const int *k_dev, int nk, float *out,
+                           cudaStream_t st)
+{
+    measure_k_kernel<<<grid_for((a.s_end - a.s_begin) * a.nt * nk, 128), 128, 0, st>>>(a, L, k_dev,
+                                                                                        nk, out);
+    return cudaGetLastError();
+}
+
+}  // namespace sg

@@ -1,0 +1,79 @@
+// sg_internal.h -- declarations shared by the host API and the kernel files
+// of the library (not part of the public ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/sgmc.h"
+
+namespace sg {
+
+// Arguments of the fused int8 sweep kernel (one CTA owns one sample at a time
+// and keeps its whole state -- every replica and slot -- in shared memory).
+struct Int8Args {
+    uint8_t *spins;        // [S][N][2*Tp] bytes, 0 => +1, 1 => -1; byte r*Tp + t
+    const uint8_t *J8;     // [S][N][8] +-J bond bits (+x,-x,+y,-y,+z,-z,0,0), 1 => J=-1
+    const float *Jg;       // [S][3][N] Gaussian couplings
+    int64_t *B;            // [S][2][Tp] bond sums of the current configuration
+    int64_t *M;            // [S][2][Tp] magnetisations
+    double *acc;           // [S][nt][40] measurement accumulators
+    const uint32_t *thr;   // [Tp][16] +-J thresholds, entry sb*8 + u
+    const float *negbeta;  // [Tp] -(float)beta_t (0 for padding slots)
+    const float *dbeta;    // [Tp] (float)(beta_t - beta_{t+1})
+    const float *twid;     // [2][L] FP32 cos, sin of 2 pi d / L
+    int *status;           // device status word (0 = OK)
+    int64_t S;
+    int nt, Tp;
+    float h_f, qJ_f;       // FP32 field and coupling quantum (exchange rule)
+    double h_d, qJ_d;      // FP64 copies (energies in the measurement)
+    uint32_t seed_lo, seed_hi;
+    int rng_group;
+    int64_t sweep0;
+    const int64_t *sweep0_dev;   // if set, the first sweep index is read here
+    int n_sweeps;
+    int exchange_every, measure_every;
+    int64_t n_therm;
+    int mchunk;            // slot words per measurement pass
+    unsigned long long watchdog;
+    const volatile int *cancel;  // optional host-mapped cancel flag
+    int64_t s_begin, s_end;      // samples handled by this launch
+};
+
+struct Int8Launch {
+    int threads, grid;
+    size_t smem;
+};
+
+// Shared-memory bytes of the fused kernel, or 0 when the state does not fit.
+size_t int8_smem_bytes(int L, int Tp, bool gauss, int mchunk);
+int int8_max_threads();
+// Configure and launch the fused kernel.
+cudaError_t int8_launch(int L, bool gauss, const Int8Args &a, const Int8Launch &cfg,
+                        cudaStream_t st);
+// Occupancy of the fused kernel (CTAs per SM), 0 if it cannot launch.
+int int8_ctas_per_sm(int L, bool gauss, int threads, size_t smem);
+
+// Instance preparation and state conversion kernels.
+cudaError_t int8_gen_pmj(uint8_t *J8, int64_t S, int L, uint32_t seed_lo, uint32_t seed_hi,
+                         cudaStream_t st);
+cudaError_t int8_gen_gauss(float *Jg, int64_t S, int L, uint32_t seed_lo, uint32_t seed_hi,
+                           cudaStream_t st);
+cudaError_t int8_gen_spins(uint8_t *spins, int64_t S, int L, int nt, int Tp, uint32_t seed_lo,
+                           uint32_t seed_hi, cudaStream_t st);
+cudaError_t int8_import_J(uint8_t *J8, float *Jg, const float *Jcanon, int64_t S, int L,
+                          bool gauss, cudaStream_t st);
+cudaError_t int8_export_J(float *Jcanon, const uint8_t *J8, const float *Jg, int64_t S, int L,
+                          bool gauss, cudaStream_t st);
+cudaError_t int8_import_spins(uint8_t *spins, const int8_t *canon, int64_t S, int L, int nt,
+                              int Tp, cudaStream_t st);
+cudaError_t int8_export_spins(int8_t *canon, const uint8_t *spins, int64_t S, int L, int nt,
+                              int Tp, cudaStream_t st);
+cudaError_t int8_energies(const Int8Args &a, int L, bool gauss, cudaStream_t st);
+cudaError_t int8_exchange(const Int8Args &a, int L, bool gauss, int parity, uint32_t call_id,
+                          cudaStream_t st);
+cudaError_t advance_counter(int64_t *ctr, int64_t n, cudaStream_t st);
+cudaError_t int8_measure_k(const Int8Args &a, int L, const int *k_dev, int nk, float *out,
+                           cudaStream_t st);
+
+}  // namespace sg

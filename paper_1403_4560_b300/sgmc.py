@@ -1,0 +1,268 @@
+"""Thin Python binding of libsgmc.so (the C ABI in include/sgmc.h).
+
+Argument marshalling only: every step of the Monte Carlo runs in the library's
+CUDA kernels. Importing this module does not need a GPU; creating an ensemble
+does, and fails loudly (RuntimeError) when the library or the GPU is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsgmc.so")
+
+SG_OK, SG_EINVAL, SG_ENOMEM, SG_ECUDA, SG_ETIMEOUT, SG_ECANCELLED, SG_EBUSY, \
+    SG_EUNSUPPORTED = range(8)
+SG_PM_J, SG_GAUSS = 0, 1
+SG_LAYOUT_INT8, SG_LAYOUT_MSC64 = 0, 1
+NACC = 40
+
+
+class SgError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"sgmc error {status}: {msg}")
+        self.status = status
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("layout", ctypes.c_int32), ("rng_group", ctypes.c_int32),
+                ("exchange_every", ctypes.c_int32), ("measure_every", ctypes.c_int32),
+                ("n_therm", ctypes.c_int64), ("threads_per_block", ctypes.c_int32),
+                ("sweeps_per_launch", ctypes.c_int32), ("watchdog_cycles", ctypes.c_uint64)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int32), ("n_T", ctypes.c_int32), ("layout", ctypes.c_int32),
+                ("dist", ctypes.c_int32), ("n_samples", ctypes.c_int64), ("h", ctypes.c_double),
+                ("attempts_per_sweep", ctypes.c_int64), ("device_bytes", ctypes.c_size_t)]
+
+
+_OBS_FIELDS = ["g", "chi0", "chi1", "chi2", "xi", "r12", "e", "q2", "q4"]
+
+
+class Observables(ctypes.Structure):
+    _fields_ = [(f, ctypes.POINTER(ctypes.c_double)) for name in _OBS_FIELDS
+                for f in (name, name + "_err")]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libsgmc.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: run python -m paper_1403_4560_b300.build")
+    L = ctypes.CDLL(LIB_PATH)
+    P, i32, i64, u64, f64 = (ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_uint64,
+                             ctypes.c_double)
+    st = ctypes.c_int
+    sigs = {
+        "sg_options_default": (None, [P]),
+        "sg_ensemble_bytes": (ctypes.c_size_t, [i32, i32, i64, i32, P]),
+        "sg_create_ensemble": (st, [i32, f64, P, i32, i32, i64, u64, P, P, P, P, P]),
+        "sg_destroy": (None, [P]),
+        "sg_sweep": (st, [P, i64]),
+        "sg_sweep_batch": (st, [P, i32, i64, i32]),
+        "sg_exchange": (st, [P, i32]),
+        "sg_measure": (st, [P, P, i32, P]),
+        "sg_get_accumulators": (st, [P, P]),
+        "sg_set_accumulators": (st, [P, P]),
+        "sg_reset_accumulators": (st, [P]),
+        "sg_get_spins": (st, [P, P]),
+        "sg_set_spins": (st, [P, P]),
+        "sg_get_energies": (st, [P, P, P]),
+        "sg_get_couplings": (st, [P, P]),
+        "sg_sweeps_done": (i64, [P]),
+        "sg_set_sweeps_done": (st, [P, i64]),
+        "sg_synchronize": (st, [P]),
+        "sg_get_info": (st, [P, P]),
+        "sg_results": (st, [P, P]),
+        "sg_observables_from_acc": (st, [P, i64, i32, i32, P]),
+        "sg_status_str": (ctypes.c_char_p, [i32]),
+        "sg_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sigs.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(status: int):
+    if status != SG_OK:
+        msg = lib().sg_last_error().decode(errors="replace")
+        raise SgError(status, msg)
+
+
+def _ptr(a: np.ndarray):
+    assert a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def default_options(**kw) -> Options:
+    o = Options()
+    lib().sg_options_default(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return 0
+    return int(getattr(stream, "cuda_stream", stream))
+
+
+class Ensemble:
+    """One ensemble of disorder samples (see sg_create_ensemble)."""
+
+    def __init__(self, L: int, h: float, T, dist: str = "pmj", n_samples: int = 1,
+                 seed: int = 1, J: np.ndarray | None = None, spins: np.ndarray | None = None,
+                 stream=None, **options):
+        self.L, self.n_samples = int(L), int(n_samples)
+        self.T = np.ascontiguousarray(T, dtype=np.float64)
+        self.n_T = len(self.T)
+        self.dist = SG_GAUSS if dist in ("gauss", SG_GAUSS) else SG_PM_J
+        self.opt = default_options(**options)
+        self._keep = []
+        Jp = None
+        sp = None
+        if J is not None:
+            J = np.ascontiguousarray(J, dtype=np.float32)
+            assert J.shape == (n_samples, 3, L ** 3)
+            Jp = _ptr(J)
+        if spins is not None:
+            spins = np.ascontiguousarray(spins, dtype=np.int8)
+            assert spins.shape == (n_samples, 2, self.n_T, L ** 3)
+            sp = _ptr(spins)
+        h_ = ctypes.c_void_p()
+        self._h = None
+        _check(lib().sg_create_ensemble(self.L, float(h), _ptr(self.T), self.n_T, self.dist,
+                                        self.n_samples, int(seed) & (2 ** 64 - 1),
+                                        ctypes.byref(self.opt), Jp, sp,
+                                        ctypes.c_void_p(_stream_handle(stream)),
+                                        ctypes.byref(h_)))
+        self._h = h_
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h is not None and _lib is not None:
+            _lib.sg_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ---- work ------------------------------------------------------------
+    def sweep(self, n: int):
+        _check(lib().sg_sweep(self._h, int(n)))
+
+    def exchange(self, parity: int = 0):
+        _check(lib().sg_exchange(self._h, int(parity)))
+
+    def synchronize(self):
+        _check(lib().sg_synchronize(self._h))
+
+    # ---- data ------------------------------------------------------------
+    def accumulators(self) -> np.ndarray:
+        out = np.zeros((self.n_samples, self.n_T, NACC), dtype=np.float64)
+        _check(lib().sg_get_accumulators(self._h, _ptr(out)))
+        return out
+
+    def set_accumulators(self, acc: np.ndarray):
+        acc = np.ascontiguousarray(acc, dtype=np.float64)
+        _check(lib().sg_set_accumulators(self._h, _ptr(acc)))
+
+    def reset_accumulators(self):
+        _check(lib().sg_reset_accumulators(self._h))
+
+    def spins(self) -> np.ndarray:
+        out = np.zeros((self.n_samples, 2, self.n_T, self.L ** 3), dtype=np.int8)
+        _check(lib().sg_get_spins(self._h, _ptr(out)))
+        return out
+
+    def set_spins(self, s: np.ndarray):
+        s = np.ascontiguousarray(s, dtype=np.int8)
+        _check(lib().sg_set_spins(self._h, _ptr(s)))
+
+    def energies(self):
+        B = np.zeros((self.n_samples, 2, self.n_T), dtype=np.int64)
+        M = np.zeros_like(B)
+        _check(lib().sg_get_energies(self._h, _ptr(B), _ptr(M)))
+        return B, M
+
+    def couplings(self) -> np.ndarray:
+        out = np.zeros((self.n_samples, 3, self.L ** 3), dtype=np.float32)
+        _check(lib().sg_get_couplings(self._h, _ptr(out)))
+        return out
+
+    def measure(self, k) -> np.ndarray:
+        k = np.ascontiguousarray(k, dtype=np.int32).reshape(-1, 3)
+        out = np.zeros((self.n_samples, self.n_T, len(k), 2), dtype=np.float32)
+        _check(lib().sg_measure(self._h, _ptr(k), len(k), _ptr(out)))
+        return out
+
+    @property
+    def sweeps_done(self) -> int:
+        return int(lib().sg_sweeps_done(self._h))
+
+    def set_sweeps_done(self, n: int):
+        _check(lib().sg_set_sweeps_done(self._h, int(n)))
+
+    def info(self) -> Info:
+        i = Info()
+        _check(lib().sg_get_info(self._h, ctypes.byref(i)))
+        return i
+
+    def results(self) -> dict:
+        return _observables(lambda o: lib().sg_results(self._h, ctypes.byref(o)), self.n_T)
+
+
+def _observables(call, nt: int) -> dict:
+    arrays = {}
+    o = Observables()
+    for name in _OBS_FIELDS:
+        for f in (name, name + "_err"):
+            arrays[f] = np.zeros(nt, dtype=np.float64)
+            setattr(o, f, arrays[f].ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    _check(call(o))
+    return arrays
+
+
+def observables_from_acc(acc: np.ndarray, L: int) -> dict:
+    """Library estimators (host C++) on an accumulator array [S][n_T][40]."""
+    acc = np.ascontiguousarray(acc, dtype=np.float64)
+    S, nt, _ = acc.shape
+    return _observables(lambda o: lib().sg_observables_from_acc(_ptr(acc), S, nt, L,
+                                                                 ctypes.byref(o)), nt)
+
+
+def sweep_batch(ensembles, n: int, use_graph: bool = True):
+    arr = (ctypes.c_void_p * len(ensembles))(*[e.handle.value for e in ensembles])
+    _check(lib().sg_sweep_batch(arr, len(ensembles), int(n), int(bool(use_graph))))

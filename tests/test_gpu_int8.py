@@ -1,0 +1,250 @@
+"""GPU parity of the int8 path against the CPU oracle, through the C ABI.
+
++-J and Gaussian couplings both reproduce the oracle bit for bit: spins,
+energies and every FP64 accumulator (the acceptance rule, RNG layout and
+summation orders are frozen on both sides). Sizes span several work units
+and ragged slot counts; the full-size check samples a few disorder samples of
+the bench workload in the bench's own launch configuration.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_1403_4560_b300 import build as sgbuild
+from paper_1403_4560_b300 import inputs, sgmc
+
+pytestmark = pytest.mark.gpu
+THREADS = max(1, min(16, os.cpu_count() or 1))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA GPU required for the gpu-marked tests")
+    sgbuild.build()
+    torch.cuda.init()
+
+
+def oracle_state(L, T, h, dist, seed, J, s0, **opt):
+    return orc.State(L, T, h, dist == "gauss", seed=seed, J=J, spins=s0,
+                     rng_group=opt.get("rng_group", 1),
+                     exchange_every=opt.get("exchange_every", 1),
+                     measure_every=opt.get("measure_every", 1), n_therm=opt.get("n_therm", 0))
+
+
+def assert_same(ens, st, samples=None):
+    sl = slice(None) if samples is None else samples
+    np.testing.assert_array_equal(ens.spins()[sl], st.spins[sl])
+    B, M = ens.energies()
+    np.testing.assert_array_equal(B[sl], st.B[sl])
+    np.testing.assert_array_equal(M[sl], st.M[sl])
+    np.testing.assert_array_equal(ens.accumulators()[sl], st.acc[sl])
+
+
+def test_library_generated_pmj_instance_matches_oracle_generators():
+    L, S, nt, seed = 4, 16, 8, 1
+    T = inputs.geometric_ladder(0.4, 1.6, nt)
+    with sgmc.Ensemble(L, 0.3, T, "pmj", S, seed) as ens:
+        np.testing.assert_array_equal(ens.couplings(), orc.pmj_couplings(seed, S, L))
+        np.testing.assert_array_equal(ens.spins(), orc.init_spins(seed, S, nt, L))
+        B, M = ens.energies()
+        for s in (0, 7):
+            for r in (0, 1):
+                for t in (0, nt - 1):
+                    b, m = orc.bond_sum(L, False, orc.pmj_couplings(seed, S, L)[s],
+                                        orc.init_spins(seed, S, nt, L)[s, r, t])
+                    assert (B[s, r, t], M[s, r, t]) == (b, m)
+
+
+def test_plain_pmj_config_is_bit_exact():
+    """L=4, +-J, h=0.3, 2 x 8 temperatures geometric 0.4-1.6, exchange every
+    sweep, 16 samples, seed 1 (the small plain configuration), library-drawn
+    instance reproduced by the oracle's own generators."""
+    L, S, nt, seed, h = 4, 16, 8, 1, 0.3
+    T = inputs.geometric_ladder(0.4, 1.6, nt)
+    sweeps, n_therm = 1200, 600
+    with sgmc.Ensemble(L, h, T, "pmj", S, seed, n_therm=n_therm) as ens:
+        ens.sweep(sweeps)
+        ens.synchronize()
+        st = oracle_state(L, T, h, "pmj", seed, orc.pmj_couplings(seed, S, L),
+                          orc.init_spins(seed, S, nt, L), n_therm=n_therm)
+        st.run(sweeps, threads=THREADS)
+        assert_same(ens, st)
+
+
+@pytest.mark.parametrize("L,nt,dist,ee,me,rg", [
+    (2, 3, "pmj", 1, 1, 1), (2, 5, "gauss", 2, 1, 1), (4, 5, "gauss", 1, 2, 1),
+    (6, 6, "pmj", 1, 1, 2), (6, 4, "gauss", 3, 1, 1), (8, 7, "pmj", 2, 3, 1),
+    (8, 9, "gauss", 1, 1, 1), (10, 6, "gauss", 1, 1, 1), (10, 4, "pmj", 0, 1, 1),
+    (12, 5, "pmj", 1, 1, 4), (12, 8, "gauss", 1, 1, 1), (14, 4, "pmj", 1, 1, 1),
+    (16, 4, "gauss", 1, 2, 1), (4, 1, "pmj", 1, 1, 1)])
+def test_int8_paths_are_bit_exact(L, nt, dist, ee, me, rg):
+    S, seed, h = 4, 1234 + L, 0.25
+    T = inputs.geometric_ladder(0.5, 1.6, nt)
+    J, s0 = inputs.make_instance(dist, L, S, nt, seed=L * 100 + nt)
+    sweeps = 60 if L >= 12 else 150
+    opt = dict(exchange_every=ee, measure_every=me, n_therm=sweeps // 3, rng_group=rg)
+    with sgmc.Ensemble(L, h, T, dist, S, seed, J=J, spins=s0, **opt) as ens:
+        ens.sweep(sweeps)
+        ens.synchronize()
+        st = oracle_state(L, T, h, dist, seed, J, s0, **opt)
+        st.run(sweeps, threads=THREADS)
+        assert_same(ens, st)
+
+
+@pytest.mark.parametrize("dist", ["pmj", "gauss"])
+def test_chunking_and_launch_shape_do_not_change_results(dist):
+    L, S, nt = 6, 5, 6
+    T = inputs.geometric_ladder(0.5, 1.5, nt)
+    J, s0 = inputs.make_instance(dist, L, S, nt, seed=3)
+    ref = None
+    for opt in (dict(), dict(sweeps_per_launch=1), dict(sweeps_per_launch=7, threads_per_block=96),
+                dict(threads_per_block=480)):
+        with sgmc.Ensemble(L, 0.1, T, dist, S, 77, J=J, spins=s0, n_therm=5, **opt) as ens:
+            ens.sweep(20)
+            ens.sweep(13)
+            got = (ens.spins(), ens.energies(), ens.accumulators())
+        if ref is None:
+            ref = got
+        else:
+            np.testing.assert_array_equal(got[0], ref[0])
+            np.testing.assert_array_equal(got[1][0], ref[1][0])
+            np.testing.assert_array_equal(got[2], ref[2])
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_batched_uneven_ensembles_match_single_runs(use_graph):
+    specs = [(4, "pmj", 3, 6), (6, "gauss", 2, 5), (8, "gauss", 4, 4)]
+    Ts = {nt: inputs.geometric_ladder(0.5, 1.5, nt) for _, _, _, nt in specs}
+    insts = [inputs.make_instance(d, L, S, nt, seed=L) for L, d, S, nt in specs]
+    singles = []
+    for (L, d, S, nt), (J, s0) in zip(specs, insts):
+        with sgmc.Ensemble(L, 0.2, Ts[nt], d, S, 5, J=J, spins=s0) as e:
+            e.sweep(25)
+            e.sweep(25)
+            singles.append((e.spins(), e.accumulators()))
+    ens = [sgmc.Ensemble(L, 0.2, Ts[nt], d, S, 5, J=J, spins=s0)
+           for (L, d, S, nt), (J, s0) in zip(specs, insts)]
+    try:
+        sgmc.sweep_batch(ens, 25, use_graph=use_graph)
+        sgmc.sweep_batch(ens, 25, use_graph=use_graph)  # second call replays the cached graph
+        for e, (sp, acc) in zip(ens, singles):
+            e.synchronize()
+            assert e.sweeps_done == 50
+            np.testing.assert_array_equal(e.spins(), sp)
+            np.testing.assert_array_equal(e.accumulators(), acc)
+    finally:
+        for e in ens:
+            e.close()
+
+
+@pytest.mark.parametrize("dist", ["pmj", "gauss"])
+def test_standalone_exchange_matches_oracle(dist):
+    L, S, nt = 4, 6, 7
+    T = inputs.geometric_ladder(0.3, 3.0, nt)
+    J, s0 = inputs.make_instance(dist, L, S, nt, seed=11)
+    with sgmc.Ensemble(L, 0.4, T, dist, S, 21, J=J, spins=s0) as ens:
+        st = oracle_state(L, T, 0.4, dist, 21, J, s0)
+        for parity in (0, 1, 1, 0):
+            ens.exchange(parity)
+            st.exchange(parity)
+        np.testing.assert_array_equal(ens.spins(), st.spins)
+        B, M = ens.energies()
+        np.testing.assert_array_equal(B, st.B)
+        np.testing.assert_array_equal(M, st.M)
+
+
+def test_measure_arbitrary_wavevectors():
+    L, S, nt = 6, 3, 4
+    T = inputs.geometric_ladder(0.5, 1.5, nt)
+    J, s0 = inputs.make_instance("pmj", L, S, nt, seed=2)
+    k = np.array([[0, 0, 0], [1, 0, 0], [1, 1, 0], [2, -1, 3]])
+    with sgmc.Ensemble(L, 0.0, T, "pmj", S, 3, J=J, spins=s0) as ens:
+        got = ens.measure(k)
+    coords = np.array([[i % L, (i // L) % L, i // (L * L)] for i in range(L ** 3)])
+    q = s0[:, 0].astype(np.float64) * s0[:, 1]
+    want = (q[..., None] * np.exp(2j * np.pi / L * coords @ k.T)).mean(axis=-2)
+    np.testing.assert_allclose(got[..., 0], want.real, atol=2e-6)
+    np.testing.assert_allclose(got[..., 1], want.imag, atol=2e-6)
+
+
+def test_results_match_oracle_estimators():
+    L, S, nt = 4, 24, 4
+    T = inputs.geometric_ladder(0.6, 1.6, nt)
+    J, s0 = inputs.make_instance("gauss", L, S, nt, seed=8)
+    with sgmc.Ensemble(L, 0.1, T, "gauss", S, 4, J=J, spins=s0, n_therm=50) as ens:
+        ens.sweep(300)
+        got = ens.results()
+        acc = ens.accumulators()
+    want = orc.observables(acc, L)
+    for kl, ko in [("g", "g"), ("chi0", "chi0"), ("chi1", "chi_k1"), ("r12", "r12"), ("e", "e")]:
+        np.testing.assert_allclose(got[kl], want[ko], rtol=1e-10, equal_nan=True)
+        np.testing.assert_allclose(got[kl + "_err"], want["err"][ko], rtol=1e-7, equal_nan=True)
+
+
+@pytest.mark.parametrize("L", [8, 12])
+def test_full_size_gaussian_workload_sampled_parity(L):
+    """512 samples, 2 x 24 temperatures geometric 0.5-1.6, Gaussian couplings,
+    h = 0.2, exchange every sweep, measuring from sweep 0, default (bench)
+    launch configuration; three samples are re-run by the oracle."""
+    S, nt, h, seed, sweeps = 512, 24, 0.2, 2024, 6
+    T = inputs.geometric_ladder(0.5, 1.6, nt)
+    J, s0 = inputs.make_instance("gauss", L, S, nt, seed=31 + L)
+    with sgmc.Ensemble(L, h, T, "gauss", S, seed, J=J, spins=s0) as ens:
+        ens.sweep(sweeps)
+        ens.synchronize()
+        st = oracle_state(L, T, h, "gauss", seed, J, s0)
+        picks = [0, 255, 511]
+        for s in picks:
+            st.run(sweeps, s_range=(s, s + 1))
+        assert_same(ens, st, samples=picks)
+
+
+def test_library_gaussian_couplings_are_standard_normal_on_grid():
+    from scipy import stats
+    L, S = 8, 64
+    with sgmc.Ensemble(L, 0.0, [1.0], "gauss", S, 99) as ens:
+        J = ens.couplings().astype(np.float64).ravel()
+    assert np.all(np.rint(J * 2 ** 17) == J * 2 ** 17)
+    n = J.size
+    assert abs(J.mean()) < 5 / np.sqrt(n)
+    assert abs(J.var() - 1.0) < 5 * np.sqrt(2.0 / n)
+    assert stats.kstest(J, "norm").pvalue > 1e-4
+
+
+def test_edge_cases_and_argument_errors():
+    T = [0.7]
+    with sgmc.Ensemble(2, 0.5, T, "pmj", 1, 3) as ens:   # one sample, one temperature
+        ens.sweep(0)
+        ens.sweep(10)
+        ens.synchronize()
+        st = oracle_state(2, np.array(T), 0.5, "pmj", 3, orc.pmj_couplings(3, 1, 2),
+                          orc.init_spins(3, 1, 1, 2))
+        st.run(10)
+        assert_same(ens, st)
+    for bad in (dict(L=5), dict(L=4, T=[1.0, 0.5]), dict(L=4, T=[0.0, 1.0])):
+        with pytest.raises(sgmc.SgError) as ei:
+            sgmc.Ensemble(bad["L"], 0.1, bad.get("T", [1.0]), "pmj", 2, 1)
+        assert ei.value.status == sgmc.SG_EINVAL
+    J = np.full((1, 3, 64), 0.5, dtype=np.float32)
+    with pytest.raises(sgmc.SgError) as ei:
+        sgmc.Ensemble(4, 0.1, [1.0], "pmj", 1, 1, J=J)
+    assert ei.value.status == sgmc.SG_EINVAL
+
+
+def test_watchdog_stops_a_long_launch_with_a_status():
+    """A launch whose clock budget runs out stops between sweeps and reports
+    SG_ETIMEOUT through the status word; the context stays usable."""
+    L, S, nt = 8, 4, 8
+    T = inputs.geometric_ladder(0.5, 1.5, nt)
+    with sgmc.Ensemble(L, 0.1, T, "gauss", S, 1, watchdog_cycles=20000) as ens:
+        ens.sweep(2000)
+        with pytest.raises(sgmc.SgError) as ei:
+            ens.synchronize()
+        assert ei.value.status == sgmc.SG_ETIMEOUT
+    with sgmc.Ensemble(4, 0.1, [1.0, 2.0], "pmj", 2, 1) as ens:
+        ens.sweep(5)
+        ens.synchronize()
