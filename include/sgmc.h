@@ -231,6 +231,17 @@ sg_status sg_results(sg_ensemble *e, const sg_observables *out);
 sg_status sg_observables_from_acc(const double *acc, int64_t n_samples, int n_T, int L,
                                   const sg_observables *out);
 
+/*
+ * Diagnostics: the device's Metropolis threshold map. out[k] = floor(e^x[k] *
+ * 2^32) saturated to [0, 2^32 - 1], with x clamped to [-64, 0] and e^x from
+ * the library's own FP32 exponential (Cody-Waite reduction, degree-7 Taylor
+ * polynomial): the acceptance rule behind continuous couplings and replica
+ * exchange (paper: methods section, Metropolis updates and parallel
+ * tempering). x and out are host arrays of n entries; runs on the current
+ * device and synchronises it.
+ */
+sg_status sg_threshold_map(const float *x, int n, uint32_t *out);
+
 /* Text for a status code, and the message of the last error on this thread. */
 const char *sg_status_str(sg_status s);
 const char *sg_last_error(void);

@@ -119,56 +119,53 @@ ArenaPlan plan_arena(int L, int nt, int Tp, int64_t S, bool gauss)
 
 int pad_slots(int nt) { return (nt + 3) & ~3; }
 
-// Threads per CTA: a multiple of the per-site word count W = Tp/2 (each
-// thread keeps one 4-slot word for the whole half-sweep), chosen so that the
-// half-sweep work items divide evenly where possible.
-int pick_threads(int L, int Tp, int requested)
-{
-    const int W = Tp / 2;
-    const int H = L / 2;
-    int run = H;
-    while (run % 4) run += H;
-    const int items = (L * L * L / 2) / run * W;
-    const int maxt = int8_max_threads();
-    if (requested > 0) {
-        int t = std::max(W, (requested / W) * W);
-        return std::min(t, (maxt / W) * W);
-    }
-    int best = W, best_score = -1;
-    for (int t = W; t <= maxt; t += W) {
-        if (t < 64 && t + W <= maxt) continue;
-        const int rounds = (items + t - 1) / t;
-        // efficiency of the last round, then prefer 256-384 threads
-        const double eff = (double)items / (double)(rounds * t);
-        const int score = (int)(eff * 1000) - std::abs(t - 320) / 16;
-        if (score > best_score) {
-            best_score = score;
-            best = t;
-        }
-    }
-    return best;
-}
-
+// Launch shape: threads per CTA are a multiple of WR = Tp/4 (each thread
+// keeps one 4-slot group for the whole half-sweep); among the candidates the
+// one with the best product of work balance and resident warps per SM wins,
+// then the largest measurement chunk that keeps that occupancy.
 sg_status configure_launch(sg_ensemble *e)
 {
     const int WR = e->Tp / 4;
-    const int threads = pick_threads(e->L, e->Tp, e->opt.threads_per_block);
-    int best_m = 0, best_occ = 0;
-    for (int m = WR; m >= 1; --m) {
-        const size_t smem = int8_smem_bytes(e->L, e->Tp, e->gauss, m);
-        if (!smem) continue;
-        const int occ = int8_ctas_per_sm(e->L, e->gauss, threads, smem);
-        if (occ > best_occ) {
+    const int L = e->L, H = L / 2;
+    int run = H;
+    while (run % 4) run += H;
+    const int items = (L * L * L / 2) / run * WR;
+    const int maxt = int8_max_threads();
+    double best_score = -1.0;
+    int best_t = 0, best_m = 0, best_occ = 0;
+    for (int t = WR; t <= maxt; t += WR) {
+        if (t < 32) continue;  // the measurement needs one full warp
+        if (e->opt.threads_per_block > 0 && t != std::max(WR, (e->opt.threads_per_block / WR) * WR))
+            continue;
+        int occ = 0, m_for = 0;
+        for (int m = WR; m >= 1; --m) {
+            const size_t smem = int8_smem_bytes(L, e->Tp, e->gauss, m);
+            if (!smem) continue;
+            const int o = int8_ctas_per_sm(L, e->gauss, t, smem);
+            if (o > occ) {
+                occ = o;
+                m_for = m;
+            }
+        }
+        if (!occ) continue;
+        // useful threads per SM: work items in flight per round, over the
+        // resident CTAs; ties go to more CTAs (barriers overlap) and fewer threads
+        const int rounds = (items + t - 1) / t;
+        const double useful = (double)items / rounds * occ;
+        const double score = std::min(useful, 1024.0) + 0.5 * occ - 1e-3 * t;
+        if (score > best_score) {
+            best_score = score;
+            best_t = t;
+            best_m = m_for;
             best_occ = occ;
-            best_m = m;
         }
     }
     if (best_occ == 0)
         return fail(SG_EUNSUPPORTED, "int8 state of one sample does not fit in shared memory "
                                      "(use fewer temperatures or a smaller L)");
     e->mchunk = best_m;
-    e->launch.threads = threads;
-    e->launch.smem = int8_smem_bytes(e->L, e->Tp, e->gauss, best_m);
+    e->launch.threads = best_t;
+    e->launch.smem = int8_smem_bytes(L, e->Tp, e->gauss, best_m);
     const int64_t resident = (int64_t)best_occ * e->num_sms;
     e->launch.grid = (int)std::min<int64_t>(e->S, resident);
     return SG_OK;
@@ -705,6 +702,23 @@ sg_status sg_get_info(const sg_ensemble *e, sg_info *out)
     out->h = e->h_used;
     out->attempts_per_sweep = (int64_t)e->L * e->L * e->L * 2 * e->nt * e->S;
     out->device_bytes = e->bytes;
+    return SG_OK;
+}
+
+sg_status sg_threshold_map(const float *x, int n, uint32_t *out)
+{
+    if (!x || !out || n < 0) return fail(SG_EINVAL, "bad arguments");
+    if (n == 0) return SG_OK;
+    float *xd = nullptr;
+    uint32_t *od = nullptr;
+    SG_CUDA(cudaMalloc(&xd, sizeof(float) * (size_t)n), "cudaMalloc");
+    cudaError_t ce = cudaMalloc(&od, sizeof(uint32_t) * (size_t)n);
+    if (ce == cudaSuccess) ce = cudaMemcpy(xd, x, sizeof(float) * (size_t)n, cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) ce = threshold_map(xd, n, od, 0);
+    if (ce == cudaSuccess) ce = cudaMemcpy(out, od, sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToHost);
+    cudaFree(xd);
+    cudaFree(od);
+    if (ce != cudaSuccess) return cuda_fail(ce, "threshold map");
     return SG_OK;
 }
 

@@ -47,14 +47,19 @@ __device__ __forceinline__ u32x4 philox10(uint32_t k0, uint32_t k1, uint32_t c0,
     return r;
 }
 
-// e^x on [-64, 0] from IEEE basic operations only, so that host and device
-// agree bit for bit: Cody-Waite reduction x = n*ln2 + r with ln2 split into
-// 0.693359375 + (-2.12194440e-4), then e^r by its degree-7 Taylor polynomial
-// (coefficients 1/k! rounded to FP32) in Horner form with fused multiply-adds,
-// and the factor 2^n assembled from exponent bits.
-__device__ __forceinline__ float exp_cw32(float x)
+// e^x * 2^k on [-64, 0] from IEEE basic operations only, so that host and
+// device agree bit for bit: Cody-Waite reduction x = n*ln2 + r with ln2 split
+// into 0.693359375 + (-2.12194440e-4), then e^r by its degree-7 Taylor
+// polynomial (coefficients 1/k! rounded to FP32) in Horner form with fused
+// multiply-adds, and the factor 2^(n+k) assembled from exponent bits.
+// n = rint(x * log2(e)) is taken with the 1.5 * 2^23 shifter: adding it rounds
+// to the nearest integer (ties to even), exactly as rintf does for |t| < 2^22.
+template <int K>
+__device__ __forceinline__ float exp_cw32_scaled(float x)
 {
-    const float n = rintf(__fmul_rn(x, 1.44269502f));
+    const float t = __fmul_rn(x, 1.44269502f);
+    const float sh = __fadd_rn(t, 12582912.0f);
+    const float n = __fadd_rn(sh, -12582912.0f);
     float r = __fmaf_rn(-n, 0.693359375f, x);
     r = __fmaf_rn(-n, -2.12194440e-4f, r);
     float p = 1.0f / 5040.0f;
@@ -65,18 +70,21 @@ __device__ __forceinline__ float exp_cw32(float x)
     p = __fmaf_rn(p, r, 0.5f);
     p = __fmaf_rn(p, r, 1.0f);
     p = __fmaf_rn(p, r, 1.0f);
-    const int ni = __float2int_rn(n);
-    return __fmul_rn(p, __int_as_float((ni + 127) << 23));
+    const int ni = __float_as_int(sh) - 0x4B400000;
+    return __fmul_rn(p, __int_as_float((ni + 127 + K) << 23));
 }
 
-// Acceptance threshold for an FP32 log-probability x <= 0: a uniform 32-bit
-// word r is accepted iff r <= thr, i.e. with probability (thr + 1)/2^32.
+__device__ __forceinline__ float exp_cw32(float x) { return exp_cw32_scaled<0>(x); }
+
+// Acceptance threshold for an FP32 log-probability x: a uniform 32-bit word
+// r is accepted iff r <= thr, i.e. with probability (thr + 1)/2^32; thr is
+// floor(e^x * 2^32) saturated to 0xFFFFFFFF. x >= 0 (an energy decrease)
+// gives 0xFFFFFFFF; x < -64 gives 0 (e^-64 * 2^32 < 1, the clamp changes
+// nothing). The float-to-unsigned conversion saturates at 2^32 - 1.
 __device__ __forceinline__ uint32_t thr_of_logp(float x)
 {
-    const float xc = fmaxf(x, -64.0f);
-    const float v = __fmul_rn(exp_cw32(xc), 4294967296.0f);
-    uint32_t t = v >= 4294967296.0f ? 0xFFFFFFFFu : __float2uint_rz(v);
-    return x < -64.0f ? 0u : t;
+    const float xc = fminf(fmaxf(x, -64.0f), 0.0f);
+    return __float2uint_rz(exp_cw32_scaled<32>(xc));
 }
 
 }  // namespace sg

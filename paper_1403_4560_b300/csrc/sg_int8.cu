@@ -11,16 +11,16 @@
 // bound by the SM's integer / FP32 issue rate rather than by HBM.
 //
 // Shared-memory layout of one sample:
-//   spins  [N][2*Tp] bytes   byte r*Tp + t of site i is replica r, slot t;
-//                            value 0 => +1, 1 => -1. A 32-bit word holds four
-//                            consecutive slots of one replica, so one
-//                            neighbour load serves four chains (SIMD within a
-//                            register).
+//   spins  [N][2*Tp] bytes   per site, Tp/4 groups of 8 bytes: 4 slots of
+//                            replica 0, then the same 4 slots of replica 1;
+//                            value 0 => +1, 1 => -1. One 32-bit word holds
+//                            four chains (SIMD within a register) and one
+//                            64-bit load serves the 8 chains of a group.
 //   +-J    [N][8] bytes      bond bits (+x, -x, +y, -y, +z, -z, 0, 0), 1 => J = -1
 //   Gauss  [3][N] float      J[d][i] joins i and i + e_d
-// Work unit of a half-sweep: (run of RUN = lcm(L/2, 4) consecutive sites of one
-// colour, one 4-slot word). RUN is a multiple of 4, so the Philox calls (four
-// sites each) never straddle two units.
+// Work item of a half-sweep: (run of RUN = lcm(L/2, 4) consecutive sites of
+// one colour, one 4-slot group, both replicas). RUN is a multiple of 4, so
+// the Philox calls (four sites each) never straddle two items.
 #include <cuda_runtime.h>
 
 #include "sg_device.cuh"
@@ -44,6 +44,14 @@ __device__ __forceinline__ void sts32(uint8_t *base, int off, uint32_t v)
     *reinterpret_cast<uint32_t *>(base + off) = v;
 }
 
+// Byte of (replica r, slot t) inside a site's row: slots come in 4-slot
+// words and the two replicas' words of one 4-slot group are adjacent, so one
+// 64-bit load reads 8 chains (4 slots x 2 replicas) of a site.
+__host__ __device__ __forceinline__ int slot_byte(int r, int t)
+{
+    return 8 * (t >> 2) + 4 * r + (t & 3);
+}
+
 struct Smem {
     uint8_t *spins;
     uint8_t *J8;
@@ -54,7 +62,7 @@ struct Smem {
     uint32_t *xflag;            // [2][Tp] exchange stamps
     uint32_t *sel;              // [2][Tp/4][2] byte-permutation selectors
     int *anyswap;               // [2]
-    uint32_t *marg;             // [mchunk][3][L*L] byte counts of q = -1
+    uint32_t *marg;             // [3][L*L][mchunk] byte counts of q = -1
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -83,187 +91,223 @@ __host__ __device__ inline size_t carve(uint8_t *base, int L, int Tp, bool gauss
     s.xflag = reinterpret_cast<uint32_t *>(take((size_t)2 * Tp * 4));
     s.sel = reinterpret_cast<uint32_t *>(take((size_t)2 * (Tp / 4) * 2 * 4));
     s.anyswap = reinterpret_cast<int *>(take(2 * 4));
-    s.marg = reinterpret_cast<uint32_t *>(take((size_t)mchunk * 3 * L * L * 4));
+    s.marg = reinterpret_cast<uint32_t *>(take((size_t)3 * L * L * mchunk * 4));
     if (sm) *sm = s;
     return off;
 }
 
 struct Ctx {
-    int nt, Tp, WR, W, RB;
+    int nt, Tp, WR, RB;
     int64_t s;
     uint32_t k0, k1;  // Metropolis Philox key
     uint32_t seed_lo, seed_hi;
     float hq;         // Gaussian: field on the 2^-17 grid
 };
 
+// Site index and neighbour offsets (in sites) of the colour-COL site with
+// colour-compressed index jj (i = 2*jj + parity, i >> 1 == jj).
+template <int L>
+struct SiteNb {
+    int i, x, dxp, dxm, dyp, dym, dzp, dzm;
+    __device__ __forceinline__ SiteNb(int jj, int COL)
+    {
+        constexpr int H = L / 2;
+        const int row = jj / H;
+        const int x2 = jj - row * H;
+        const int y = row % L;
+        const int z = row / L;
+        x = 2 * x2 + ((COL + y + z) & 1);
+        i = x + L * row;
+        dxp = (x == L - 1) ? -(L - 1) : 1;
+        dxm = (x == 0) ? (L - 1) : -1;
+        dyp = (y == L - 1) ? -(L - 1) * L : L;
+        dym = (y == 0) ? (L - 1) * L : -L;
+        dzp = (z == L - 1) ? -(L - 1) * L * L : L * L;
+        dzm = (z == 0) ? (L - 1) * L * L : -L * L;
+    }
+};
+
+// +-J: Metropolis on 4 chains of one replica word; returns the flip bytes
+// (0x01 per flipped chain) and the unsatisfied-bond counts per byte.
+__device__ __forceinline__ uint32_t pmj_word(uint32_t s, uint32_t nxp, uint32_t nxm,
+                                             uint32_t nyp, uint32_t nym, uint32_t nzp,
+                                             uint32_t nzm, const uint32_t (&m)[6],
+                                             const uint32_t *thr_w, const uint32_t (&rnd)[4][4],
+                                             int lane, uint32_t valid, uint32_t &uw)
+{
+    uw = (s ^ nxp ^ m[0]) + (s ^ nxm ^ m[1]) + (s ^ nyp ^ m[2]) + (s ^ nym ^ m[3]) +
+         (s ^ nzp ^ m[4]) + (s ^ nzm ^ m[5]);
+    const uint32_t idx = (s << 3) | uw;  // per byte: sb*8 + u
+    uint32_t fm = 0;
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+        const uint32_t th = thr_w[kk * 16 + ((idx >> (8 * kk)) & 15u)];
+        fm |= (uint32_t)(rnd[kk][lane] <= th) << (8 * kk);
+    }
+    return fm & valid;
+}
+
+// Gaussian: Metropolis on 4 chains of one replica word. bq[kk] receives
+// s_new * b / qJ for the energy of colour-1 sites.
+template <bool ENERGY>
+__device__ __forceinline__ uint32_t gauss_word(uint32_t s, uint32_t nxp, uint32_t nxm,
+                                               uint32_t nyp, uint32_t nym, uint32_t nzp,
+                                               uint32_t nzm, const float (&j)[6], float hq,
+                                               const float (&nbeta)[4],
+                                               const uint32_t (&rnd)[4][4], int lane,
+                                               uint32_t valid, int (&bq)[4])
+{
+    uint32_t fm = 0;
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+        const int sh = 31 - 8 * kk;
+        // J * s_nb: flip the sign bit of J where the neighbour is -1
+        float b = __int_as_float(__float_as_int(j[0]) ^ ((nxp << sh) & 0x80000000u));
+        b = __fadd_rn(b, __int_as_float(__float_as_int(j[1]) ^ ((nxm << sh) & 0x80000000u)));
+        b = __fadd_rn(b, __int_as_float(__float_as_int(j[2]) ^ ((nyp << sh) & 0x80000000u)));
+        b = __fadd_rn(b, __int_as_float(__float_as_int(j[3]) ^ ((nym << sh) & 0x80000000u)));
+        b = __fadd_rn(b, __int_as_float(__float_as_int(j[4]) ^ ((nzp << sh) & 0x80000000u)));
+        b = __fadd_rn(b, __int_as_float(__float_as_int(j[5]) ^ ((nzm << sh) & 0x80000000u)));
+        const uint32_t sgn = (s << sh) & 0x80000000u;  // own spin -1 => sign bit
+        const float zf = __fadd_rn(b, hq);
+        const float dE = __int_as_float(__float_as_int(__fadd_rn(zf, zf)) ^ sgn);
+        // dE <= 0 gives x >= 0, whose threshold is 0xFFFFFFFF: always accepted
+        const float xl = __fmul_rn(nbeta[kk], dE);
+        const uint32_t flip = (rnd[kk][lane] <= thr_of_logp(xl)) & (valid >> (8 * kk));
+        fm |= flip << (8 * kk);
+        if (ENERGY) {
+            const int q = __float2int_rn(__fmul_rn(b, 131072.0f));
+            bq[kk] = (((s >> (8 * kk)) ^ flip) & 1u) ? -q : q;
+        }
+    }
+    return fm;
+}
+
 // ---------------------------------------------------------------------------
 // One checkerboard half-sweep of colour COL over all chains of the sample.
-// For COL == 1 it also accumulates B and M of the post-sweep configuration:
-// every bond has exactly one colour-1 end, so summing s_i * b_i over colour-1
-// sites counts each bond once; M pairs each colour-1 site with its x^1
-// partner (colour 0, final after the colour-0 half).
+// Work item: (run of RUN colour-COL sites, 4-slot group j) covering both
+// replicas, i.e. 8 chains. For COL == 1 it also accumulates B and M of the
+// post-sweep configuration: every bond has exactly one colour-1 end, so
+// summing s_i * b_i over colour-1 sites counts each bond once; M pairs each
+// colour-1 site with its x^1 partner (colour 0, final after the colour-0 half).
 // ---------------------------------------------------------------------------
-template <int L, bool GAUSS, int COL>
-__device__ __forceinline__ void half_sweep(const Smem &sm, const Ctx &cx, uint32_t n_sweep)
+template <int L, bool GAUSS>
+__device__ __forceinline__ void half_sweep(const Smem &sm, const Ctx &cx, uint32_t n_sweep,
+                                        const int COL)
 {
     constexpr int H = L / 2;
     constexpr int N = L * L * L;
     constexpr int RUN = lcm_c(H, 4);
-    constexpr int R = RUN / H;
+    constexpr int NG = RUN / 4;
     constexpr int U = (N / 2) / RUN;
-    const int W = cx.W, RB = cx.RB;
-    const int w = threadIdx.x % W;  // fixed per thread: blockDim.x is a multiple of W
-    const int r = w / cx.WR;
-    const int t0 = 4 * (w % cx.WR);
-    const int items = U * W;
+    const int WR = cx.WR, RB = cx.RB;
+    const int j = threadIdx.x % WR;  // fixed per thread: blockDim.x is a multiple of WR
+    const int t0 = 4 * j;
+    const int items = U * WR;
 
-    // bytes of real (not padding) slots in this thread's word
-    uint32_t valid = 0;
+    uint32_t valid = 0;  // bytes of real (not padding) slots in this group
 #pragma unroll
     for (int kk = 0; kk < 4; ++kk)
         if (t0 + kk < cx.nt) valid |= 1u << (8 * kk);
 
-    long long bacc[4] = {0, 0, 0, 0};  // +-J: sum of u_new; Gauss: sum s*b/qJ
-    int macc_t[4] = {0, 0, 0, 0};      // count of -1 spins over site + partner
-    int nsites = 0;
-
     float nbeta[4];
-    const uint32_t *thr_t[4];
 #pragma unroll
-    for (int kk = 0; kk < 4; ++kk) {
-        nbeta[kk] = GAUSS ? sm.negbeta[t0 + kk] : 0.0f;
-        thr_t[kk] = GAUSS ? nullptr : sm.thr + (t0 + kk) * 16;
-    }
+    for (int kk = 0; kk < 4; ++kk) nbeta[kk] = GAUSS ? sm.negbeta[t0 + kk] : 0.0f;
+    const uint32_t *thr_w = GAUSS ? nullptr : sm.thr + t0 * 16;
 
     for (int item = threadIdx.x; item < items; item += blockDim.x) {
-        const int u = item / W;
-        uint32_t eacc = 0, macc = 0;  // byte-wise partial sums over this run
-        int bgi[4] = {0, 0, 0, 0};    // Gauss: int32 partial of s*b/qJ
-        uint32_t rnd[4][4];
+        const int u = item / WR;
+        uint32_t eacc0 = 0, eacc1 = 0, macc0 = 0, macc1 = 0;  // byte-wise partial sums
+        int bg[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+        for (int g = 0; g < NG; ++g) {
+            const uint32_t c0 = (uint32_t)(u * NG + g);
+            uint32_t rnd[2][4][4];
 #pragma unroll
-        for (int rho = 0; rho < R; ++rho) {
-            const int row = u * R + rho;
-            const int y = row % L;
-            const int z = row / L;
-            const int par = (COL + y + z) & 1;
-            const int dyp = (y == L - 1) ? -(L - 1) * L : L;
-            const int dym = (y == 0) ? (L - 1) * L : -L;
-            const int dzp = (z == L - 1) ? -(L - 1) * L * L : L * L;
-            const int dzm = (z == 0) ? (L - 1) * L * L : -L * L;
+            for (int r = 0; r < 2; ++r)
 #pragma unroll
-            for (int x2 = 0; x2 < H; ++x2) {
-                const int k = rho * H + x2;
-                if ((k & 3) == 0) {
-                    const uint32_t c0 = (uint32_t)(u * (RUN / 4) + (k >> 2));
-#pragma unroll
-                    for (int kk = 0; kk < 4; ++kk) {
-                        const uint32_t c2 = ((uint32_t)COL << 24) | ((uint32_t)r << 16) |
-                                            (uint32_t)(t0 + kk);
-                        const u32x4 o = philox10(cx.k0, cx.k1, c0, n_sweep, c2, cx.seed_hi);
-                        rnd[kk][0] = o.v[0];
-                        rnd[kk][1] = o.v[1];
-                        rnd[kk][2] = o.v[2];
-                        rnd[kk][3] = o.v[3];
-                    }
+                for (int kk = 0; kk < 4; ++kk) {
+                    const uint32_t c2 = ((uint32_t)COL << 24) | ((uint32_t)r << 16) |
+                                        (uint32_t)(t0 + kk);
+                    const u32x4 o = philox10(cx.k0, cx.k1, c0, n_sweep, c2, cx.seed_hi);
+                    rnd[r][kk][0] = o.v[0];
+                    rnd[r][kk][1] = o.v[1];
+                    rnd[r][kk][2] = o.v[2];
+                    rnd[r][kk][3] = o.v[3];
                 }
-                const int lane = k & 3;
-                const int x = 2 * x2 + par;
-                const int i = x + L * row;
-                const int dxp = (x == L - 1) ? -(L - 1) : 1;
-                const int dxm = (x == 0) ? (L - 1) : -1;
-                const int own = i * RB + 4 * w;
-                const uint32_t s = lds32(sm.spins, own);
-                const uint32_t nxp = lds32(sm.spins, own + dxp * RB);
-                const uint32_t nxm = lds32(sm.spins, own + dxm * RB);
-                const uint32_t nyp = lds32(sm.spins, own + dyp * RB);
-                const uint32_t nym = lds32(sm.spins, own + dym * RB);
-                const uint32_t nzp = lds32(sm.spins, own + dzp * RB);
-                const uint32_t nzm = lds32(sm.spins, own + dzm * RB);
-                uint32_t fm = 0;  // 0x01 in each flipped byte
-                if constexpr (!GAUSS) {
-                    const uint2 jb = *reinterpret_cast<const uint2 *>(sm.J8 + 8 * i);
-                    const uint32_t m0 = __byte_perm(jb.x, jb.y, 0x0000);
-                    const uint32_t m1 = __byte_perm(jb.x, jb.y, 0x1111);
-                    const uint32_t m2 = __byte_perm(jb.x, jb.y, 0x2222);
-                    const uint32_t m3 = __byte_perm(jb.x, jb.y, 0x3333);
-                    const uint32_t m4 = __byte_perm(jb.x, jb.y, 0x4444);
-                    const uint32_t m5 = __byte_perm(jb.x, jb.y, 0x5555);
-                    // unsatisfied-bond count per byte (0..6): s ^ s_nb ^ jbit
-                    const uint32_t uw = (s ^ nxp ^ m0) + (s ^ nxm ^ m1) + (s ^ nyp ^ m2) +
-                                        (s ^ nym ^ m3) + (s ^ nzp ^ m4) + (s ^ nzm ^ m5);
-                    const uint32_t idx = (s << 3) | uw;  // per byte: sb*8 + u
 #pragma unroll
-                    for (int kk = 0; kk < 4; ++kk) {
-                        const uint32_t th = thr_t[kk][(idx >> (8 * kk)) & 15u];
-                        fm |= (uint32_t)(rnd[kk][lane] <= th) << (8 * kk);
-                    }
-                    fm &= valid;
+            for (int lane = 0; lane < 4; ++lane) {
+                const SiteNb<L> st(u * RUN + 4 * g + lane, COL);
+                const int own = st.i * RB + 8 * j;
+                const uint2 s = *reinterpret_cast<const uint2 *>(sm.spins + own);
+                const uint2 nxp = *reinterpret_cast<const uint2 *>(sm.spins + own + st.dxp * RB);
+                const uint2 nxm = *reinterpret_cast<const uint2 *>(sm.spins + own + st.dxm * RB);
+                const uint2 nyp = *reinterpret_cast<const uint2 *>(sm.spins + own + st.dyp * RB);
+                const uint2 nym = *reinterpret_cast<const uint2 *>(sm.spins + own + st.dym * RB);
+                const uint2 nzp = *reinterpret_cast<const uint2 *>(sm.spins + own + st.dzp * RB);
+                const uint2 nzm = *reinterpret_cast<const uint2 *>(sm.spins + own + st.dzm * RB);
+                uint2 fm;
+                if constexpr (!GAUSS) {
+                    const uint2 jb = *reinterpret_cast<const uint2 *>(sm.J8 + 8 * st.i);
+                    const uint32_t m[6] = {__byte_perm(jb.x, jb.y, 0x0000),
+                                           __byte_perm(jb.x, jb.y, 0x1111),
+                                           __byte_perm(jb.x, jb.y, 0x2222),
+                                           __byte_perm(jb.x, jb.y, 0x3333),
+                                           __byte_perm(jb.x, jb.y, 0x4444),
+                                           __byte_perm(jb.x, jb.y, 0x5555)};
+                    uint32_t uw0, uw1;
+                    fm.x = pmj_word(s.x, nxp.x, nxm.x, nyp.x, nym.x, nzp.x, nzm.x, m, thr_w,
+                                    rnd[0], lane, valid, uw0);
+                    fm.y = pmj_word(s.y, nxp.y, nxm.y, nyp.y, nym.y, nzp.y, nzm.y, m, thr_w,
+                                    rnd[1], lane, valid, uw1);
                     if (COL == 1) {
-                        const uint32_t fm8 = fm * 0xFFu;
-                        const uint32_t unew = uw ^ ((uw ^ (0x06060606u - uw)) & fm8);
-                        eacc += unew;
+                        const uint32_t f0 = fm.x * 0xFFu, f1 = fm.y * 0xFFu;
+                        eacc0 += uw0 ^ ((uw0 ^ (0x06060606u - uw0)) & f0);
+                        eacc1 += uw1 ^ ((uw1 ^ (0x06060606u - uw1)) & f1);
                     }
                 } else {
-                    const float j0 = sm.Jg[i];
-                    const float j1 = sm.Jg[i + dxm];
-                    const float j2 = sm.Jg[N + i];
-                    const float j3 = sm.Jg[N + i + dym];
-                    const float j4 = sm.Jg[2 * N + i];
-                    const float j5 = sm.Jg[2 * N + i + dzm];
+                    const float jv[6] = {sm.Jg[st.i], sm.Jg[st.i + st.dxm], sm.Jg[N + st.i],
+                                         sm.Jg[N + st.i + st.dym], sm.Jg[2 * N + st.i],
+                                         sm.Jg[2 * N + st.i + st.dzm]};
+                    int bq0[4], bq1[4];
+                    fm.x = gauss_word<true>(s.x, nxp.x, nxm.x, nyp.x, nym.x, nzp.x, nzm.x, jv,
+                                            cx.hq, nbeta, rnd[0], lane, valid, bq0);
+                    fm.y = gauss_word<true>(s.y, nxp.y, nxm.y, nyp.y, nym.y, nzp.y, nzm.y, jv,
+                                            cx.hq, nbeta, rnd[1], lane, valid, bq1);
+                    if (COL == 1) {
 #pragma unroll
-                    for (int kk = 0; kk < 4; ++kk) {
-                        const int sh = 31 - 8 * kk;
-                        // J * s_nb: flip the sign bit of J where the neighbour is -1
-                        float b = __int_as_float(__float_as_int(j0) ^ ((nxp << sh) & 0x80000000u));
-                        b = __fadd_rn(b, __int_as_float(__float_as_int(j1) ^ ((nxm << sh) & 0x80000000u)));
-                        b = __fadd_rn(b, __int_as_float(__float_as_int(j2) ^ ((nyp << sh) & 0x80000000u)));
-                        b = __fadd_rn(b, __int_as_float(__float_as_int(j3) ^ ((nym << sh) & 0x80000000u)));
-                        b = __fadd_rn(b, __int_as_float(__float_as_int(j4) ^ ((nzp << sh) & 0x80000000u)));
-                        b = __fadd_rn(b, __int_as_float(__float_as_int(j5) ^ ((nzm << sh) & 0x80000000u)));
-                        const uint32_t sgn = (s << sh) & 0x80000000u;  // own spin -1 => sign bit
-                        const float zf = __fadd_rn(b, cx.hq);
-                        const float dE = __int_as_float(__float_as_int(__fadd_rn(zf, zf)) ^ sgn);
-                        const float xl = __fmul_rn(nbeta[kk], dE);
-                        const bool acc = (dE <= 0.0f) || (rnd[kk][lane] <= thr_of_logp(xl));
-                        const uint32_t flip = acc && (valid >> (8 * kk) & 1u);
-                        fm |= flip << (8 * kk);
-                        if (COL == 1) {
-                            const int bq = __float2int_rn(__fmul_rn(b, 131072.0f));
-                            // s_new * b / qJ, s_new = -1 when (old bit) xor flip is 1
-                            bgi[kk] += (((s >> (8 * kk)) ^ flip) & 1u) ? -bq : bq;
+                        for (int kk = 0; kk < 4; ++kk) {
+                            bg[0][kk] += bq0[kk];
+                            bg[1][kk] += bq1[kk];
                         }
                     }
                 }
-                const uint32_t snew = s ^ fm;
-                sts32(sm.spins, own, snew);
+                uint2 sn;
+                sn.x = s.x ^ fm.x;
+                sn.y = s.y ^ fm.y;
+                *reinterpret_cast<uint2 *>(sm.spins + own) = sn;
                 if (COL == 1) {
-                    const uint32_t partner = (x & 1) ? nxm : nxp;
-                    macc += snew + partner;
+                    const uint2 partner = (st.x & 1) ? nxm : nxp;
+                    macc0 += sn.x + partner.x;
+                    macc1 += sn.y + partner.y;
                 }
             }
         }
         if (COL == 1) {
-            nsites += RUN;
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-                if (!GAUSS)
-                    bacc[kk] += (eacc >> (8 * kk)) & 0xFFu;
-                else
-                    bacc[kk] += bgi[kk];
-                macc_t[kk] += (macc >> (8 * kk)) & 0xFFu;
-            }
-        }
-    }
-    if (COL == 1 && nsites > 0) {
+            for (int r = 0; r < 2; ++r)
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-            const int t = t0 + kk;
-            if (t >= cx.nt) continue;
-            // +-J: s b = 6 - 2u per colour-1 site; M: each pair contributes 2 - 2*(#-1)
-            const long long b = GAUSS ? bacc[kk] : 6LL * nsites - 2LL * bacc[kk];
-            const long long m = 2LL * nsites - 2LL * macc_t[kk];
-            atomicAdd(&sm.B[r * cx.Tp + t], (unsigned long long)b);
-            atomicAdd(&sm.M[r * cx.Tp + t], (unsigned long long)m);
+                for (int kk = 0; kk < 4; ++kk) {
+                    const int t = t0 + kk;
+                    if (t >= cx.nt) continue;
+                    const uint32_t ea = r ? eacc1 : eacc0;
+                    const uint32_t ma = r ? macc1 : macc0;
+                    // +-J: s b = 6 - 2u per colour-1 site; M: each pair gives 2 - 2*(#-1)
+                    const long long b = GAUSS ? (long long)bg[r][kk]
+                                              : 6LL * RUN - 2LL * ((ea >> (8 * kk)) & 0xFFu);
+                    const long long mm = 2LL * RUN - 2LL * ((ma >> (8 * kk)) & 0xFFu);
+                    atomicAdd(&sm.B[r * cx.Tp + t], (unsigned long long)b);
+                    atomicAdd(&sm.M[r * cx.Tp + t], (unsigned long long)mm);
+                }
         }
     }
 }
@@ -343,13 +387,13 @@ __device__ __forceinline__ void exchange_apply(const Smem &sm, const Ctx &cx, ui
     for (int id = threadIdx.x; id < 2 * N; id += blockDim.x) {
         const int r = id & 1, site = id >> 1;
         if (!sm.anyswap[r]) continue;
-        uint8_t *row = sm.spins + site * RB + r * Tp;
+        uint8_t *row = sm.spins + site * RB + 4 * r;  // word j at row + 8j
         const uint32_t *sel = sm.sel + r * WR * 2;
         uint32_t prev = 0, cur = lds32(row, 0);
-        for (int j = 0; j < WR; ++j) {
-            const uint32_t next = (j + 1 < WR) ? lds32(row, 4 * (j + 1)) : 0u;
-            const uint32_t tmp = __byte_perm(cur, next, sel[2 * j]);
-            sts32(row, 4 * j, __byte_perm(tmp, prev, sel[2 * j + 1]));
+        for (int jj = 0; jj < WR; ++jj) {
+            const uint32_t next = (jj + 1 < WR) ? lds32(row, 8 * (jj + 1)) : 0u;
+            const uint32_t tmp = __byte_perm(cur, next, sel[2 * jj]);
+            sts32(row, 8 * jj, __byte_perm(tmp, prev, sel[2 * jj + 1]));
             prev = cur;
             cur = next;
         }
@@ -357,27 +401,47 @@ __device__ __forceinline__ void exchange_apply(const Smem &sm, const Ctx &cx, ui
     __syncthreads();
 }
 
+// Counts of q = -1 per phase d of one wave vector, from the 2D marginal
+// pm[(A*L + B)*nw] (byte sh): PAT 0: A = d; 1: B = d; 2: A + B = d;
+// 3: A - B = d (mod L). Fully unrolled: L*L independent loads.
+template <int L, int PAT>
+__device__ __forceinline__ void count_pattern(const uint32_t *pm, int nw, int sh, int (&cs)[L])
+{
+#pragma unroll
+    for (int d = 0; d < L; ++d) {
+        int c = 0;
+#pragma unroll
+        for (int aa = 0; aa < L; ++aa) {
+            const int A = PAT == 0 ? d : aa;
+            const int Bc = PAT == 0 ? aa : PAT == 1 ? d : PAT == 2 ? (d - aa + L) % L : (aa - d + L) % L;
+            c += (pm[(A * L + Bc) * nw] >> sh) & 0xFF;
+        }
+        cs[d] = c;
+    }
+}
+
 // ---------------------------------------------------------------------------
-// Overlap measurement (eq. overlap) for every slot: q = s^(0) s^(1); 2D
-// marginals of the q = -1 counts over the xy, xz and yz planes; the nine
-// projections P_v[d] (v over the k1 and k2 orbits); FP32 DFT of each
-// projection; FP64 accumulation.
+// Overlap measurement (eq. overlap) for every slot: q = s^(0) s^(1);
+// (A) 2D marginals of the q = -1 counts over the xy, xz and yz planes,
+// (B) per (slot, v): the integer projections P_v[d] (v over the k1 and k2
+// orbits), the FP32 DFT in ascending d and the FP64 accumulation,
+// together with Q, E and M. Processed mchunk 4-slot groups at a time.
 // ---------------------------------------------------------------------------
 template <int L>
 __device__ __forceinline__ void measure_step(const Smem &sm, const Ctx &cx, const Int8Args &a)
 {
-    constexpr int N = L * L * L;
     constexpr int LL = L * L;
     const int WR = cx.WR, RB = cx.RB, Tp = cx.Tp, nt = cx.nt;
     double *accs = a.acc + (size_t)cx.s * nt * SG_NACC;
     for (int j0 = 0; j0 < WR; j0 += a.mchunk) {
         const int nw = min(a.mchunk, WR - j0);
-        for (int id = threadIdx.x; id < nw * 3 * LL; id += blockDim.x) {
-            const int jj = id / (3 * LL);
-            const int rem = id % (3 * LL);
-            const int plane = rem / LL;
-            const int ab = rem % LL;
-            const int A = ab / L, Bc = ab % L;
+        // (A) marginals; the group index varies fastest across lanes
+        for (int id = threadIdx.x; id < 3 * LL * nw; id += blockDim.x) {
+            const int jj = id % nw;
+            const int rest = id / nw;
+            const int ab = rest % LL;
+            const int plane = rest / LL;
+            const int A = ab % L, Bc = ab / L;  // A varies fastest
             int base, step;
             if (plane == 0) {        // (x=A, y=Bc), over z
                 base = A + L * Bc;
@@ -389,30 +453,46 @@ __device__ __forceinline__ void measure_step(const Smem &sm, const Ctx &cx, cons
                 base = L * A + LL * Bc;
                 step = 1;
             }
-            const int woff = 4 * (j0 + jj);
+            const int woff = 8 * (j0 + jj);
             uint32_t cnt = 0;
 #pragma unroll 4
             for (int m = 0; m < L; ++m) {
-                const int off = (base + m * step) * RB + woff;
-                cnt += lds32(sm.spins, off) ^ lds32(sm.spins, off + Tp);
+                const uint2 w = *reinterpret_cast<const uint2 *>(sm.spins + (base + m * step) * RB + woff);
+                cnt += w.x ^ w.y;
             }
-            sm.marg[id] = cnt;
+            sm.marg[(plane * LL + A * L + Bc) * nw + jj] = cnt;
         }
         __syncthreads();
-        for (int id = threadIdx.x; id < nw * 4 * 10; id += blockDim.x) {
+        // (B) one thread per (slot, v): the L projections P_v[d] from L*L
+        // independent loads, then the FP32 DFT in ascending d and the FP64
+        // accumulation; v == 9 handles Q, E and M
+        for (int id = threadIdx.x; id < 4 * nw * 10; id += blockDim.x) {
             const int v = id % 10;
-            const int rest = id / 10;
-            const int kk = rest % 4;
-            const int jj = rest / 4;
-            const int t = 4 * (j0 + jj) + kk;
+            const int sl = id / 10;  // 4*jj + kk
+            const int t = 4 * j0 + sl;
             if (t >= nt) continue;
-            const uint32_t *mg = sm.marg + jj * 3 * LL;
-            const int sh = 8 * kk;
+            const int jj = sl >> 2, sh = 8 * (sl & 3);
             double *ac = accs + (size_t)t * SG_NACC;
+            int cs[L];
+            if (v == 9 || v == 0)
+                count_pattern<L, 0>(sm.marg + jj, nw, sh, cs);
+            else if (v == 1)
+                count_pattern<L, 1>(sm.marg + jj, nw, sh, cs);
+            else if (v == 2)
+                count_pattern<L, 1>(sm.marg + LL * nw + jj, nw, sh, cs);
+            else {
+                const int plane = (v == 3 || v == 4) ? 0 : (v == 5 || v == 6) ? 1 : 2;
+                const uint32_t *pm = sm.marg + plane * LL * nw + jj;
+                if (v == 3 || v == 5 || v == 7)
+                    count_pattern<L, 2>(pm, nw, sh, cs);
+                else
+                    count_pattern<L, 3>(pm, nw, sh, cs);
+            }
             if (v == 9) {
-                int cq = 0;
-                for (int e = 0; e < LL; ++e) cq += (mg[e] >> sh) & 0xFF;
-                const double Q = (double)(N - 2 * cq);
+                int Qi = 0;
+#pragma unroll
+                for (int d = 0; d < L; ++d) Qi += LL - 2 * cs[d];
+                const double Q = (double)Qi;
                 const double Q2 = __dmul_rn(Q, Q);
                 ac[0] = __dadd_rn(ac[0], 1.0);
                 ac[1] = __dadd_rn(ac[1], Q);
@@ -434,33 +514,18 @@ __device__ __forceinline__ void measure_step(const Smem &sm, const Ctx &cx, cons
                 }
                 continue;
             }
-            // plane and index map of the projection for wave vector v
-            const int plane = (v == 0 || v == 1 || v == 3 || v == 4) ? 0
-                              : (v == 2 || v == 5 || v == 6)         ? 1
-                                                                     : 2;
-            const uint32_t *pm = mg + plane * LL;
             float re = 0.0f, im = 0.0f;
+#pragma unroll
             for (int d = 0; d < L; ++d) {
-                int cs = 0;
-                for (int aa = 0; aa < L; ++aa) {
-                    int A, Bc;
-                    switch (v) {
-                    case 0: A = d; Bc = aa; break;                 // x = d
-                    case 1: A = aa; Bc = d; break;                 // y = d
-                    case 2: A = aa; Bc = d; break;                 // z = d (xz plane)
-                    case 3: case 5: case 7: A = aa; Bc = (d - aa + L) % L; break;  // a + b = d
-                    default: A = aa; Bc = (aa - d + L) % L; break;                 // a - b = d
-                    }
-                    cs += (pm[A * L + Bc] >> sh) & 0xFF;
-                }
-                const float P = (float)(LL - 2 * cs);
-                re = __fmaf_rn(P, sm.twid[d], re);
-                im = __fmaf_rn(P, sm.twid[L + d], im);
+                const float Pf = (float)(LL - 2 * cs[d]);
+                re = __fmaf_rn(Pf, sm.twid[d], re);
+                im = __fmaf_rn(Pf, sm.twid[L + d], im);
             }
             const double dr = (double)re, di = (double)im;
             ac[9 + 3 * v] = __dadd_rn(ac[9 + 3 * v], dr);
             ac[10 + 3 * v] = __dadd_rn(ac[10 + 3 * v], di);
-            ac[11 + 3 * v] = __dadd_rn(ac[11 + 3 * v], __dadd_rn(__dmul_rn(dr, dr), __dmul_rn(di, di)));
+            ac[11 + 3 * v] =
+                __dadd_rn(ac[11 + 3 * v], __dadd_rn(__dmul_rn(dr, dr), __dmul_rn(di, di)));
         }
         __syncthreads();
     }
@@ -488,7 +553,6 @@ __global__ void __launch_bounds__(kMaxThreads) int8_run_kernel(const Int8Args a)
     cx.nt = a.nt;
     cx.Tp = a.Tp;
     cx.WR = a.Tp / 4;
-    cx.W = a.Tp / 2;
     cx.RB = 2 * a.Tp;
     cx.seed_lo = a.seed_lo;
     cx.seed_hi = a.seed_hi;
@@ -538,14 +602,17 @@ __global__ void __launch_bounds__(kMaxThreads) int8_run_kernel(const Int8Args a)
                 stop = __syncthreads_or(why != 0);
                 if (stop) break;
             }
-            half_sweep<L, GAUSS, 0>(sm, cx, (uint32_t)n);
-            for (int k = threadIdx.x; k < 2 * a.Tp; k += blockDim.x) {
-                sm.B[k] = 0;
-                sm.M[k] = 0;
+            // one code path for both colours keeps the instruction footprint small
+#pragma unroll 1
+            for (int col = 0; col < 2; ++col) {
+                half_sweep<L, GAUSS>(sm, cx, (uint32_t)n, col);
+                if (col == 0)
+                    for (int k = threadIdx.x; k < 2 * a.Tp; k += blockDim.x) {
+                        sm.B[k] = 0;
+                        sm.M[k] = 0;
+                    }
+                __syncthreads();
             }
-            __syncthreads();
-            half_sweep<L, GAUSS, 1>(sm, cx, (uint32_t)n);
-            __syncthreads();
             if (a.exchange_every > 0 && (n + 1) % a.exchange_every == 0) {
                 const int64_t e = (n + 1) / a.exchange_every - 1;
                 ++stamp;
@@ -643,7 +710,7 @@ __global__ void gen_spins_kernel(uint8_t *spins, int64_t S, int L, int nt, int T
         const int64_t s = g / ((int64_t)N * RB);
         const int i = (int)((g / RB) % N);
         const int rb = (int)(g % RB);
-        const int r = rb / Tp, t = rb % Tp;
+        const int r = (rb & 7) >> 2, t = 4 * (rb >> 3) + (rb & 3);
         uint8_t v = 0;
         if (t < nt) {
             const u32x4 o = philox10(slo ^ kTagInit, (uint32_t)s, (uint32_t)(i >> 7),
@@ -705,7 +772,7 @@ __global__ void import_spins_kernel(uint8_t *spins, const int8_t *c, int64_t S, 
         const int64_t s = g / ((int64_t)N * RB);
         const int i = (int)((g / RB) % N);
         const int rb = (int)(g % RB);
-        const int r = rb / Tp, t = rb % Tp;
+        const int r = (rb & 7) >> 2, t = 4 * (rb >> 3) + (rb & 3);
         spins[g] = t < nt ? (uint8_t)(c[((s * 2 + r) * nt + t) * N + i] < 0) : (uint8_t)0;
     }
 }
@@ -721,7 +788,7 @@ __global__ void export_spins_kernel(int8_t *c, const uint8_t *spins, int64_t S, 
         const int t = (int)((g / N) % nt);
         const int r = (int)((g / ((int64_t)N * nt)) % 2);
         const int64_t s = g / ((int64_t)2 * nt * N);
-        c[g] = spins[(s * N + i) * (2 * Tp) + r * Tp + t] ? -1 : 1;
+        c[g] = spins[(s * N + i) * (2 * Tp) + slot_byte(r, t)] ? -1 : 1;
     }
 }
 
@@ -732,7 +799,7 @@ __device__ void chain_energy(const Int8Args &a, int L, bool gauss, int64_t s, in
 {
     const int N = L * L * L;
     const int RB = 2 * a.Tp;
-    const uint8_t *sp = a.spins + (size_t)s * N * RB + r * a.Tp + t;
+    const uint8_t *sp = a.spins + (size_t)s * N * RB + slot_byte(r, t);
     long long b = 0, m = 0;
     for (int i = 0; i < N; ++i) {
         const int si = sp[(size_t)i * RB] ? -1 : 1;
@@ -808,10 +875,10 @@ __global__ void exchange_kernel(const Int8Args a, int L, int parity, uint32_t ca
             const int r = rest % 2;
             const int p = parity + 2 * (rest / 2);
             if (p + 1 >= nt || !accept[r][p]) continue;
-            uint8_t *row = sp + (size_t)i * RB + r * Tp;
-            const uint8_t tv = row[p];
-            row[p] = row[p + 1];
-            row[p + 1] = tv;
+            uint8_t *row = sp + (size_t)i * RB;
+            const uint8_t tv = row[slot_byte(r, p)];
+            row[slot_byte(r, p)] = row[slot_byte(r, p + 1)];
+            row[slot_byte(r, p + 1)] = tv;
         }
     }
 }
@@ -831,7 +898,7 @@ __global__ void measure_k_kernel(const Int8Args a, int L, const int *kv, int nk,
         float re = 0.0f, im = 0.0f;
         for (int i = 0; i < N; ++i) {
             const int x = i % L, y = (i / L) % L, z = i / (L * L);
-            const int q = (sp[(size_t)i * RB + t] ^ sp[(size_t)i * RB + a.Tp + t]) ? -1 : 1;
+            const int q = (sp[(size_t)i * RB + slot_byte(0, t)] ^ sp[(size_t)i * RB + slot_byte(1, t)]) ? -1 : 1;
             int ph = (kv[3 * j] * x + kv[3 * j + 1] * y + kv[3 * j + 2] * z) % L;
             if (ph < 0) ph += L;
             float sn, cs;
@@ -842,6 +909,12 @@ __global__ void measure_k_kernel(const Int8Args a, int L, const int *kv, int nk,
         out[2 * g] = re / (float)N;
         out[2 * g + 1] = im / (float)N;
     }
+}
+
+__global__ void thr_map_kernel(const float *x, int n, uint32_t *out)
+{
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+        out[k] = thr_of_logp(x[k]);
 }
 
 __global__ void advance_kernel(int64_t *ctr, int64_t n)
@@ -985,6 +1058,12 @@ cudaError_t int8_exchange(const Int8Args &a, int L, bool gauss, int parity, uint
     if (e != cudaSuccess) return e;
     const int64_t n = a.s_end - a.s_begin;
     exchange_kernel<<<(int)(n < 148 * 16 ? n : 148 * 16), 256, 0, st>>>(a, L, parity & 1, call_id);
+    return cudaGetLastError();
+}
+
+cudaError_t threshold_map(const float *x, int n, uint32_t *out, cudaStream_t st)
+{
+    thr_map_kernel<<<grid_for(n, 256), 256, 0, st>>>(x, n, out);
     return cudaGetLastError();
 }
 

@@ -72,6 +72,7 @@ cudaError_t int8_export_spins(int8_t *canon, const uint8_t *spins, int64_t S, in
 cudaError_t int8_energies(const Int8Args &a, int L, bool gauss, cudaStream_t st);
 cudaError_t int8_exchange(const Int8Args &a, int L, bool gauss, int parity, uint32_t call_id,
                           cudaStream_t st);
+cudaError_t threshold_map(const float *x, int n, uint32_t *out, cudaStream_t st);
 cudaError_t advance_counter(int64_t *ctr, int64_t n, cudaStream_t st);
 cudaError_t int8_measure_k(const Int8Args &a, int L, const int *k_dev, int nk, float *out,
                            cudaStream_t st);

@@ -85,6 +85,7 @@ def lib() -> ctypes.CDLL:
         "sg_get_info": (st, [P, P]),
         "sg_results": (st, [P, P]),
         "sg_observables_from_acc": (st, [P, i64, i32, i32, P]),
+        "sg_threshold_map": (st, [P, i32, P]),
         "sg_status_str": (ctypes.c_char_p, [i32]),
         "sg_last_error": (ctypes.c_char_p, []),
     }
@@ -261,6 +262,14 @@ def observables_from_acc(acc: np.ndarray, L: int) -> dict:
     S, nt, _ = acc.shape
     return _observables(lambda o: lib().sg_observables_from_acc(_ptr(acc), S, nt, L,
                                                                  ctypes.byref(o)), nt)
+
+
+def threshold_map(x) -> np.ndarray:
+    """Device Metropolis threshold map on an FP32 array (diagnostics)."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    out = np.zeros(x.shape, dtype=np.uint32)
+    _check(lib().sg_threshold_map(_ptr(x), x.size, _ptr(out)))
+    return out
 
 
 def sweep_batch(ensembles, n: int, use_graph: bool = True):

@@ -248,3 +248,18 @@ def test_watchdog_stops_a_long_launch_with_a_status():
     with sgmc.Ensemble(4, 0.1, [1.0, 2.0], "pmj", 2, 1) as ens:
         ens.sweep(5)
         ens.synchronize()
+
+
+def test_device_threshold_map_matches_oracle_bit_for_bit():
+    """The device exponential/threshold map equals the oracle's on a dense grid
+    (all FP32 values in [-1, 0] of one binade sample, and a uniform grid over
+    [-70, 1])."""
+    rng = np.random.default_rng(0)
+    x = np.concatenate([np.linspace(-70.0, 1.0, 400001, dtype=np.float32),
+                        -rng.random(200000).astype(np.float32),
+                        -(rng.random(100000) * 23).astype(np.float32),
+                        np.array([0.0, -0.0, -1e-30, -64.0, -64.0001, -22.18, -22.19],
+                                 dtype=np.float32)])
+    got = sgmc.threshold_map(x)
+    want = np.array([orc.t32(float(v)) if v < 0 else 0xFFFFFFFF for v in x], dtype=np.uint32)
+    np.testing.assert_array_equal(got, want)
