@@ -174,6 +174,31 @@ sg_status sg_exchange(sg_ensemble *e, int parity);
  */
 sg_status sg_measure(sg_ensemble *e, const int *k, int nk, float *out);
 
+/*
+ * sg_measure without any device allocation. The paper has no counterpart;
+ * this exists for callers that cannot call cudaMalloc when they measure: code
+ * running while a stream is being captured into a CUDA graph, serving loops
+ * that keep the allocator off their latency path, and hosts whose device
+ * memory belongs to another framework's pool.
+ *   Same arguments and output as sg_measure. The k vectors and the output are
+ *   staged in one library-owned static device array of
+ *   4096 + 4 * SG_MEASURE_NOALLOC_MAX_FLOATS bytes that every GPU which loads
+ *   the library holds until the process exits.
+ *   Limits: nk <= SG_MEASURE_NOALLOC_MAX_K and
+ *   n_samples * n_T * nk * 2 <= SG_MEASURE_NOALLOC_MAX_FLOATS; larger requests
+ *   return SG_EINVAL without touching the device.
+ *   The first call on a device looks up the array's device address (once per
+ *   device, with that device current); make that first call before any
+ *   stream capture begins.
+ *   All calls share the one array and it keeps the last call's contents:
+ *   calls whose work overlaps on the GPU (other host threads, other streams)
+ *   race on it and must be serialised by the caller. The call synchronises
+ *   the ensemble's stream before it returns.
+ */
+#define SG_MEASURE_NOALLOC_MAX_K 256
+#define SG_MEASURE_NOALLOC_MAX_FLOATS (1 << 20)
+sg_status sg_measure_noalloc(sg_ensemble *e, const int *k, int nk, float *out);
+
 /* Copy the accumulators (canonical layout) to a host array. */
 sg_status sg_get_accumulators(sg_ensemble *e, double *acc_out);
 /* Zero the accumulators. */

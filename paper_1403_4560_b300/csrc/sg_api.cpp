@@ -580,6 +580,20 @@ sg_status sg_measure(sg_ensemble *e, const int *k, int nk, float *out)
     return SG_OK;
 }
 
+sg_status sg_measure_noalloc(sg_ensemble *e, const int *k, int nk, float *out)
+{
+    if (!e || !k || nk < 1 || !out) return fail(SG_EINVAL, "bad measure arguments");
+    if (nk > SG_MEASURE_NOALLOC_MAX_K)
+        return fail(SG_EINVAL, "sg_measure_noalloc: more than SG_MEASURE_NOALLOC_MAX_K wave vectors");
+    const size_t floats = (size_t)e->S * e->nt * nk * 2;
+    if (floats > (size_t)SG_MEASURE_NOALLOC_MAX_FLOATS)
+        return fail(SG_EINVAL, "sg_measure_noalloc: n_samples * n_T * nk * 2 exceeds "
+                               "SG_MEASURE_NOALLOC_MAX_FLOATS");
+    SG_CUDA(int8_measure_k_noalloc(make_args(e), e->L, k, nk, out, floats, e->stream),
+            "measure (no allocation)");
+    return SG_OK;
+}
+
 sg_status sg_get_accumulators(sg_ensemble *e, double *out)
 {
     if (!e || !out) return fail(SG_EINVAL, "bad arguments");

@@ -23,6 +23,8 @@
 // the Philox calls (four sites each) never straddle two items.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "sg_device.cuh"
 #include "sg_internal.h"
 
@@ -1079,6 +1081,73 @@ cudaError_t int8_measure_k(const Int8Args &a, int L, const int *k_dev, int nk, f
     measure_k_kernel<<<grid_for((a.s_end - a.s_begin) * a.nt * nk, 128), 128, 0, st>>>(a, L, k_dev,
                                                                                         nk, out);
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the arbitrary-k overlap measurement.
+//
+// Some callers cannot allocate device memory at the point where they want a
+// measurement: code running while a stream is being captured into a CUDA
+// graph (cudaMalloc is not allowed there), serving loops that must not touch
+// the allocator on their latency path, and hosts whose memory pool belongs to
+// another framework. For them the k-vector and output staging live in this
+// file-scope device array instead of cudaMalloc'd buffers. Every device that
+// loads the library holds the array until the process exits.
+//
+// In host code the array's name is only a host-side stand-in, never a device
+// address: the device address comes from cudaGetSymbolAddress, taken once per
+// device with that device current (on the first call made on that device).
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoAllocKBytes = 4096;  // room for SG_MEASURE_NOALLOC_MAX_K vectors
+constexpr size_t kNoAllocBytes = kNoAllocKBytes + (size_t)SG_MEASURE_NOALLOC_MAX_FLOATS * 4;
+static_assert(3 * sizeof(int) * SG_MEASURE_NOALLOC_MAX_K <= kNoAllocKBytes, "k staging");
+
+__device__ __align__(256) unsigned char g_measure_scratch[kNoAllocBytes];
+
+constexpr int kMaxDevices = 64;
+unsigned char *g_scratch_ptr[kMaxDevices];
+std::mutex g_scratch_mu;
+
+// Device address of g_measure_scratch on the current device (set up once).
+cudaError_t scratch_for_current_device(unsigned char **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    if (!g_scratch_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_measure_scratch);
+        if (e != cudaSuccess) return e;
+        g_scratch_ptr[dev] = static_cast<unsigned char *>(p);
+    }
+    *out = g_scratch_ptr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t int8_measure_k_noalloc(const Int8Args &a, int L, const int *k_host, int nk,
+                                   float *out_host, size_t out_floats, cudaStream_t st)
+{
+    unsigned char *scratch = nullptr;
+    cudaError_t e = scratch_for_current_device(&scratch);
+    if (e != cudaSuccess) return e;
+    int *kd = reinterpret_cast<int *>(scratch);
+    float *od = reinterpret_cast<float *>(scratch + kNoAllocKBytes);
+    e = cudaMemcpyAsync(kd, k_host, sizeof(int) * 3 * (size_t)nk, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+    // every output element is written by the kernel, so nothing needs clearing
+    measure_k_kernel<<<grid_for((a.s_end - a.s_begin) * a.nt * nk, 128), 128, 0, st>>>(a, L, kd,
+                                                                                        nk, od);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(out_host, od, sizeof(float) * out_floats, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(st);
 }
 
 }  // namespace sg

@@ -74,6 +74,8 @@ cudaError_t int8_exchange(const Int8Args &a, int L, bool gauss, int parity, uint
                           cudaStream_t st);
 cudaError_t threshold_map(const float *x, int n, uint32_t *out, cudaStream_t st);
 cudaError_t advance_counter(int64_t *ctr, int64_t n, cudaStream_t st);
+cudaError_t int8_measure_k_noalloc(const Int8Args &a, int L, const int *k_host, int nk,
+                                   float *out_host, size_t out_floats, cudaStream_t st);
 cudaError_t int8_measure_k(const Int8Args &a, int L, const int *k_dev, int nk, float *out,
                            cudaStream_t st);
 

@@ -72,6 +72,7 @@ def lib() -> ctypes.CDLL:
         "sg_sweep_batch": (st, [P, i32, i64, i32]),
         "sg_exchange": (st, [P, i32]),
         "sg_measure": (st, [P, P, i32, P]),
+        "sg_measure_noalloc": (st, [P, P, i32, P]),
         "sg_get_accumulators": (st, [P, P]),
         "sg_set_accumulators": (st, [P, P]),
         "sg_reset_accumulators": (st, [P]),
@@ -227,6 +228,14 @@ class Ensemble:
         k = np.ascontiguousarray(k, dtype=np.int32).reshape(-1, 3)
         out = np.zeros((self.n_samples, self.n_T, len(k), 2), dtype=np.float32)
         _check(lib().sg_measure(self._h, _ptr(k), len(k), _ptr(out)))
+        return out
+
+    def measure_noalloc(self, k) -> np.ndarray:
+        """sg_measure_noalloc: the same result, staged in the library's static
+        device array instead of freshly allocated device memory."""
+        k = np.ascontiguousarray(k, dtype=np.int32).reshape(-1, 3)
+        out = np.zeros((self.n_samples, self.n_T, len(k), 2), dtype=np.float32)
+        _check(lib().sg_measure_noalloc(self._h, _ptr(k), len(k), _ptr(out)))
         return out
 
     @property
