@@ -76,8 +76,8 @@ def lib():
         L.orc_mc_exp32.restype = f32
         L.orc_t32.argtypes = [f32]
         L.orc_t32.restype = u32
-        L.orc_init_spins.argtypes = [u64, i64, i32, i32, P]
-        L.orc_pmj_couplings.argtypes = [u64, i64, i32, P]
+        L.orc_init_spins.argtypes = [u64, i64, i64, i32, i32, P]
+        L.orc_pmj_couplings.argtypes = [u64, i64, i64, i32, P]
         L.orc_bond_sum.argtypes = [i32, i32, P, P, P, P]
         L.orc_site_threshold.argtypes = [i32, i32, f64, f64, P, P, P, i32]
         L.orc_site_threshold.restype = u32
@@ -85,9 +85,10 @@ def lib():
         L.orc_delta_e.restype = f64
         L.orc_overlap.argtypes = [i32, P, P, P, P, P]
         L.orc_run.argtypes = [i32, i32, i32, f64, P, u64, i32, i32, i32, i64, i64, i64,
-                              i64, i64, P, P, P, P, P]
+                              i64, i64, i64, P, P, P, P, P]
         L.orc_run.restype = i32
-        L.orc_exchange.argtypes = [i32, i32, i32, f64, P, u64, i64, i32, i64, i64, P, P, P, P]
+        L.orc_exchange.argtypes = [i32, i32, i32, f64, P, u64, i64, i32, i64, i64, i64, P, P,
+                                   P, P]
         L.orc_exchange.restype = i32
         _lib = L
     return _lib
@@ -124,15 +125,17 @@ def t32(x: float) -> int:
     return lib().orc_t32(float(x))
 
 
-def init_spins(seed: int, S: int, n_t: int, L: int) -> np.ndarray:
+def init_spins(seed: int, S: int, n_t: int, L: int, s_base: int = 0) -> np.ndarray:
+    """Seed-drawn initial spins of samples s_base .. s_base + S - 1."""
     out = np.zeros((S, 2, n_t, L ** 3), dtype=np.int8)
-    lib().orc_init_spins(seed, S, n_t, L, _p(out))
+    lib().orc_init_spins(seed, s_base, S, n_t, L, _p(out))
     return out
 
 
-def pmj_couplings(seed: int, S: int, L: int) -> np.ndarray:
+def pmj_couplings(seed: int, S: int, L: int, s_base: int = 0) -> np.ndarray:
+    """Seed-drawn +-J couplings of samples s_base .. s_base + S - 1."""
     out = np.zeros((S, 3, L ** 3), dtype=np.float32)
-    lib().orc_pmj_couplings(seed, S, L, _p(out))
+    lib().orc_pmj_couplings(seed, s_base, S, L, _p(out))
     return out
 
 
@@ -173,7 +176,9 @@ class State:
     """Host-side state of one oracle ensemble (canonical layouts)."""
 
     def __init__(self, L, T, h, gauss, seed, J, spins, rng_group=1, exchange_every=1,
-                 measure_every=1, n_therm=0):
+                 measure_every=1, n_therm=0, s_base=0):
+        """Local sample k is the global sample s_base + k (its RNG key)."""
+        self.s_base = int(s_base)
         self.L, self.h, self.gauss, self.seed = L, float(h), bool(gauss), int(seed)
         self.T = np.ascontiguousarray(T, dtype=np.float64)
         self.nt = len(self.T)
@@ -196,7 +201,7 @@ class State:
         def work(a, b):
             rc = L.orc_run(self.L, self.nt, int(self.gauss), self.h, _p(self.T), self.seed,
                            self.rng_group, self.exchange_every, self.measure_every,
-                           self.n_therm, self.sweeps_done, n_sweeps, a, b, _p(self.J),
+                           self.n_therm, self.sweeps_done, n_sweeps, self.s_base, a, b, _p(self.J),
                            _p(self.spins), _p(self.B), _p(self.M), _p(self.acc))
             if rc != 0:
                 raise ValueError("oracle rejected its arguments")
@@ -212,7 +217,7 @@ class State:
 
     def exchange(self, parity: int):
         rc = lib().orc_exchange(self.L, self.nt, int(self.gauss), self.h, _p(self.T), self.seed,
-                                self.exchanges_done, parity, 0, self.S, _p(self.J),
+                                self.exchanges_done, parity, self.s_base, 0, self.S, _p(self.J),
                                 _p(self.spins), _p(self.B), _p(self.M))
         if rc != 0:
             raise ValueError("oracle rejected its arguments")

@@ -153,11 +153,13 @@ uint32_t orc_t32(float x)
 /* ---------------------------------------------------------------------- */
 /* Instance helpers reproducing the library's own Philox-keyed draws.     */
 /* ---------------------------------------------------------------------- */
-void orc_init_spins(uint64_t seed, int64_t S, int nt, int L, int8_t *spins)
+/* Initial spins of samples s_base .. s_base + S - 1 (stored from index 0). */
+void orc_init_spins(uint64_t seed, int64_t s_base, int64_t S, int nt, int L, int8_t *spins)
 {
     int N = L * L * L;
     uint32_t slo = (uint32_t)seed, shi = (uint32_t)(seed >> 32);
-    for (int64_t s = 0; s < S; ++s)
+    for (int64_t sl = 0; sl < S; ++sl) {
+        int64_t s = s_base + sl;
         for (int r = 0; r < 2; ++r)
             for (int t = 0; t < nt; ++t)
                 for (int i = 0; i < N; ++i) {
@@ -165,22 +167,26 @@ void orc_init_spins(uint64_t seed, int64_t S, int nt, int L, int8_t *spins)
                                              ((uint32_t)r << 16) | (uint32_t)t, 0u, shi,
                                              (i >> 5) & 3);
                     int bit = (w >> (i & 31)) & 1;
-                    spins[((s * 2 + r) * nt + t) * (int64_t)N + i] = (int8_t)(bit ? -1 : 1);
+                    spins[((sl * 2 + r) * nt + t) * (int64_t)N + i] = (int8_t)(bit ? -1 : 1);
                 }
+    }
 }
 
-void orc_pmj_couplings(uint64_t seed, int64_t S, int L, float *J)
+/* +-J couplings of samples s_base .. s_base + S - 1 (stored from index 0). */
+void orc_pmj_couplings(uint64_t seed, int64_t s_base, int64_t S, int L, float *J)
 {
     int N = L * L * L;
     uint32_t slo = (uint32_t)seed, shi = (uint32_t)(seed >> 32);
-    for (int64_t s = 0; s < S; ++s)
+    for (int64_t sl = 0; sl < S; ++sl) {
+        int64_t s = s_base + sl;
         for (int d = 0; d < 3; ++d)
             for (int i = 0; i < N; ++i) {
                 uint32_t w = philox_lane(slo ^ TAG_BOND, (uint32_t)s, (uint32_t)(i >> 7),
                                          (uint32_t)d, 0u, shi, (i >> 5) & 3);
                 int bit = (w >> (i & 31)) & 1;
-                J[(s * 3 + d) * (int64_t)N + i] = bit ? -1.0f : 1.0f;
+                J[(sl * 3 + d) * (int64_t)N + i] = bit ? -1.0f : 1.0f;
             }
+    }
 }
 
 /* ---------------------------------------------------------------------- */
@@ -431,14 +437,16 @@ static void make_params(chain_params *cp, int L, int nt, int gauss, double h,
 }
 
 /*
- * Run sweeps sweep0 .. sweep0 + n_sweeps - 1 for samples [s_begin, s_end).
+ * Run sweeps sweep0 .. sweep0 + n_sweeps - 1 for the local samples
+ * [s_begin, s_end); local sample k is the global sample s_base + k (the index
+ * that keys its random numbers).
  * J [S][3][N] float; spins [S][2][nt][N] int8 in/out; B, M [S][2][nt] out
  * (state after the last sweep); acc [S][nt][40] in/out.
  * Returns 0, or -1 for invalid arguments.
  */
 int orc_run(int L, int nt, int gauss, double h, const double *T, uint64_t seed,
             int rng_group, int exchange_every, int measure_every, int64_t n_therm,
-            int64_t sweep0, int64_t n_sweeps, int64_t s_begin, int64_t s_end,
+            int64_t sweep0, int64_t n_sweeps, int64_t s_base, int64_t s_begin, int64_t s_end,
             const float *J, int8_t *spins, int64_t *B, int64_t *M, double *acc)
 {
     if (L < 2 || (L & 1) || nt < 1 || nt > 4096 || rng_group < 1 || measure_every < 1 ||
@@ -457,11 +465,11 @@ int orc_run(int L, int nt, int gauss, double h, const double *T, uint64_t seed,
         double *as = acc + s * (int64_t)nt * ORC_NACC;
         energies(&cp, Js, sp, Bs, Ms);
         for (int64_t n = sweep0; n < sweep0 + n_sweeps; ++n) {
-            one_sweep_metropolis(&cp, s, n, Js, sp);
+            one_sweep_metropolis(&cp, s_base + s, n, Js, sp);
             energies(&cp, Js, sp, Bs, Ms);
             if (exchange_every > 0 && (n + 1) % exchange_every == 0) {
                 int64_t e = (n + 1) / exchange_every - 1;
-                exchange_step(&cp, s, (int)(e & 1), (uint32_t)n, 0u, Js, sp, Bs, Ms);
+                exchange_step(&cp, s_base + s, (int)(e & 1), (uint32_t)n, 0u, Js, sp, Bs, Ms);
             }
             if (n >= n_therm && (n - n_therm) % measure_every == 0)
                 measure(&cp, sp, Bs, Ms, as);
@@ -475,8 +483,8 @@ int orc_run(int L, int nt, int gauss, double h, const double *T, uint64_t seed,
 /* Standalone exchange call number k with the given pair parity (not part of
  * the sweep schedule; its random numbers are keyed apart from it). */
 int orc_exchange(int L, int nt, int gauss, double h, const double *T, uint64_t seed,
-                 int64_t k, int parity, int64_t s_begin, int64_t s_end, const float *J,
-                 int8_t *spins, int64_t *B, int64_t *M)
+                 int64_t k, int parity, int64_t s_base, int64_t s_begin, int64_t s_end,
+                 const float *J, int8_t *spins, int64_t *B, int64_t *M)
 {
     if (L < 2 || (L & 1) || nt < 1) return -1;
     int N = L * L * L;
@@ -489,7 +497,7 @@ int orc_exchange(int L, int nt, int gauss, double h, const double *T, uint64_t s
         int8_t *sp = spins + s * 2 * (int64_t)nt * N;
         int64_t *Bs = B + s * 2 * nt, *Ms = M + s * 2 * nt;
         energies(&cp, Js, sp, Bs, Ms);
-        exchange_step(&cp, s, parity & 1, (uint32_t)k, 0x100u, Js, sp, Bs, Ms);
+        exchange_step(&cp, s_base + s, parity & 1, (uint32_t)k, 0x100u, Js, sp, Bs, Ms);
     }
     free(thr);
     free(db_f);

@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "sg_internal.h"
+#include "sg_msc.h"
 
 using namespace sg;
 
@@ -73,6 +74,9 @@ struct sg_ensemble {
     std::vector<double> T;
     Int8Launch launch{};
     int mchunk = 1;
+    // multispin-coded +-J layout
+    bool msc = false;
+    uint64_t *W = nullptr, *Jw = nullptr, *masks = nullptr;
 };
 
 namespace {
@@ -101,18 +105,24 @@ struct ArenaPlan {
     size_t spins, J, BM, acc, thr, tab, twid, misc, total;
 };
 
-ArenaPlan plan_arena(int L, int nt, int Tp, int64_t S, bool gauss)
+ArenaPlan plan_arena(int L, int nt, int Tp, int64_t S, bool gauss, bool msc)
 {
     const size_t N = (size_t)L * L * L;
     ArenaPlan p;
-    p.spins = align256((size_t)S * N * 2 * Tp);
-    p.J = align256(gauss ? (size_t)S * 3 * N * sizeof(float) : (size_t)S * N * 8);
+    if (msc) {
+        // 64 samples per word: W [S/64][nt][2][N], Jw [S/64][3][N], masks [S/64][2][nt]
+        p.spins = align256((size_t)(S / 64) * nt * 2 * N * 8);
+        p.J = align256((size_t)(S / 64) * 3 * N * 8);
+    } else {
+        p.spins = align256((size_t)S * N * 2 * Tp);
+        p.J = align256(gauss ? (size_t)S * 3 * N * sizeof(float) : (size_t)S * N * 8);
+    }
     p.BM = align256((size_t)S * 2 * Tp * sizeof(int64_t));
     p.acc = align256((size_t)S * nt * SG_NACC * sizeof(double));
     p.thr = align256((size_t)Tp * 16 * sizeof(uint32_t));
     p.tab = align256((size_t)Tp * sizeof(float));
     p.twid = align256((size_t)2 * L * sizeof(float));
-    p.misc = 256;
+    p.misc = 256 + (msc ? align256((size_t)(S / 64) * 2 * nt * 8) : 0);
     p.total = p.spins + p.J + 2 * p.BM + p.acc + p.thr + 2 * p.tab + p.twid + p.misc;
     return p;
 }
@@ -209,6 +219,32 @@ Int8Args make_args(sg_ensemble *e)
     return a;
 }
 
+MscArgs make_msc_args(sg_ensemble *e)
+{
+    MscArgs a{};
+    a.W = e->W;
+    a.Jw = e->Jw;
+    a.B = e->B;
+    a.M = e->M;
+    a.acc = e->acc;
+    a.thr = e->thr;
+    a.dbeta = e->dbeta;
+    a.twid = e->twid;
+    a.G = e->S / 64;
+    a.nt = e->nt;
+    a.h_f = (float)e->h_used;
+    a.h_d = e->h_used;
+    a.seed_lo = (uint32_t)e->seed;
+    a.seed_hi = (uint32_t)(e->seed >> 32);
+    a.sweep0 = e->sweeps_done;
+    a.sweep0_dev = nullptr;
+    a.sweep_offset = 0;
+    a.exchange_every = e->opt.exchange_every;
+    a.measure_every = e->opt.measure_every;
+    a.n_therm = e->opt.n_therm;
+    return a;
+}
+
 // Host tables: +-J thresholds (FP64 exp of the C library), FP32 -beta and
 // beta differences, FP32 twiddles of the DFT.
 void host_tables(const sg_ensemble *e, std::vector<uint32_t> &thr, std::vector<float> &nb,
@@ -261,8 +297,12 @@ sg_status validate(int L, const double *T, int nt, sg_coupling dist, int64_t S,
     if (o.measure_every < 1) return fail(SG_EINVAL, "measure_every must be >= 1");
     if (o.layout != SG_LAYOUT_INT8 && o.layout != SG_LAYOUT_MSC64)
         return fail(SG_EINVAL, "unknown layout");
-    if (o.layout == SG_LAYOUT_MSC64)
-        return fail(SG_EUNSUPPORTED, "the MSC64 layout is not available in this build");
+    if (o.layout == SG_LAYOUT_MSC64) {
+        if (dist != SG_PM_J) return fail(SG_EINVAL, "the MSC64 layout needs +-J couplings");
+        if (S % 64) return fail(SG_EINVAL, "the MSC64 layout needs n_samples % 64 == 0");
+        if (!msc_supported_L(L))
+            return fail(SG_EUNSUPPORTED, "the MSC64 layout supports even L <= 16");
+    }
     return SG_OK;
 }
 
@@ -305,7 +345,8 @@ size_t sg_ensemble_bytes(int L, int nt, int64_t S, sg_coupling dist, const sg_op
     std::vector<double> T((size_t)std::max(nt, 1));
     for (size_t k = 0; k < T.size(); ++k) T[k] = 1.0 + (double)k;
     if (validate(L, T.data(), nt, dist, S, o) != SG_OK) return 0;
-    return plan_arena(L, nt, pad_slots(nt), S, dist == SG_GAUSS).total;
+    const bool msc = o.layout == SG_LAYOUT_MSC64;
+    return plan_arena(L, nt, msc ? nt : pad_slots(nt), S, dist == SG_GAUSS, msc).total;
 }
 
 sg_status sg_create_ensemble(int L, double h, const double *T, int nt, sg_coupling dist,
@@ -345,7 +386,9 @@ sg_status sg_create_ensemble(int L, double h, const double *T, int nt, sg_coupli
     sg_ensemble *e = new sg_ensemble();
     e->L = L;
     e->nt = nt;
-    e->Tp = pad_slots(nt);
+    e->msc = o.layout == SG_LAYOUT_MSC64;
+    e->Tp = e->msc ? nt : pad_slots(nt);  // MSC: B and M are [S][2][nt]
+    if (e->msc) o.rng_group = 64;         // the 64 samples of a word share Metropolis numbers
     e->layout = o.layout;
     e->gauss = gauss;
     e->S = S;
@@ -362,17 +405,22 @@ sg_status sg_create_ensemble(int L, double h, const double *T, int nt, sg_coupli
     cudaError_t ce = cudaGetDevice(&e->device);
     if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaGetDevice"));
     cudaDeviceGetAttribute(&e->num_sms, cudaDevAttrMultiProcessorCount, e->device);
-    if ((st = configure_launch(e)) != SG_OK) return bail(st);
+    if (!e->msc && (st = configure_launch(e)) != SG_OK) return bail(st);
 
-    const ArenaPlan p = plan_arena(L, nt, e->Tp, S, gauss);
+    const ArenaPlan p = plan_arena(L, nt, e->Tp, S, gauss, e->msc);
     ce = cudaMalloc(&e->arena, p.total);
     if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaMalloc(ensemble)"));
     e->bytes = p.total;
     uint8_t *base = (uint8_t *)e->arena;
     size_t off = 0;
-    e->spins = base + off; off += p.spins;
-    if (gauss) e->Jg = (float *)(base + off); else e->J8 = base + off;
-    off += p.J;
+    if (e->msc) {
+        e->W = (uint64_t *)(base + off); off += p.spins;
+        e->Jw = (uint64_t *)(base + off); off += p.J;
+    } else {
+        e->spins = base + off; off += p.spins;
+        if (gauss) e->Jg = (float *)(base + off); else e->J8 = base + off;
+        off += p.J;
+    }
     e->B = (int64_t *)(base + off); off += p.BM;
     e->M = (int64_t *)(base + off); off += p.BM;
     e->acc = (double *)(base + off); off += p.acc;
@@ -382,6 +430,7 @@ sg_status sg_create_ensemble(int L, double h, const double *T, int nt, sg_coupli
     e->twid = (float *)(base + off); off += p.twid;
     e->status = (int *)(base + off);
     e->sweep_ctr = (int64_t *)(base + off + 64);
+    if (e->msc) e->masks = (uint64_t *)(base + off + 256);
 
     ce = cudaStreamCreateWithFlags(&e->branch, cudaStreamNonBlocking);
     if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaStreamCreate"));
@@ -406,12 +455,17 @@ sg_status sg_create_ensemble(int L, double h, const double *T, int nt, sg_coupli
             const size_t bytes = (size_t)S * 3 * N * sizeof(float);
             if ((r = cudaMalloc(&stage, bytes)) != cudaSuccess) return r;
             r = cudaMemcpyAsync(stage, J_host, bytes, cudaMemcpyHostToDevice, s);
-            if (r == cudaSuccess) r = int8_import_J(e->J8, e->Jg, stage, S, L, gauss, s);
+            if (r == cudaSuccess)
+                r = e->msc ? msc_import_J(e->Jw, stage, S / 64, L, s)
+                           : int8_import_J(e->J8, e->Jg, stage, S, L, gauss, s);
             if (r == cudaSuccess) r = cudaStreamSynchronize(s);
             cudaFree(stage);
             if (r != cudaSuccess) return r;
         } else {
-            r = gauss ? int8_gen_gauss(e->Jg, S, L, slo, shi, s) : int8_gen_pmj(e->J8, S, L, slo, shi, s);
+            if (e->msc)
+                r = msc_generate(e->Jw, e->W, S / 64, L, nt, slo, shi, s);
+            else
+                r = gauss ? int8_gen_gauss(e->Jg, S, L, slo, shi, s) : int8_gen_pmj(e->J8, S, L, slo, shi, s);
             if (r != cudaSuccess) return r;
         }
         if (spins_host) {
@@ -419,15 +473,21 @@ sg_status sg_create_ensemble(int L, double h, const double *T, int nt, sg_coupli
             const size_t bytes = (size_t)S * 2 * nt * N;
             if ((r = cudaMalloc(&stage, bytes)) != cudaSuccess) return r;
             r = cudaMemcpyAsync(stage, spins_host, bytes, cudaMemcpyHostToDevice, s);
-            if (r == cudaSuccess) r = int8_import_spins(e->spins, stage, S, L, nt, e->Tp, s);
+            if (r == cudaSuccess)
+                r = e->msc ? msc_import_spins(e->W, stage, S / 64, L, nt, s)
+                           : int8_import_spins(e->spins, stage, S, L, nt, e->Tp, s);
             if (r == cudaSuccess) r = cudaStreamSynchronize(s);
             cudaFree(stage);
             if (r != cudaSuccess) return r;
-        } else {
+        } else if (!e->msc) {
             if ((r = int8_gen_spins(e->spins, S, L, nt, e->Tp, slo, shi, s)) != cudaSuccess) return r;
         }
-        Int8Args a = make_args(e);
-        if ((r = int8_energies(a, L, gauss, s)) != cudaSuccess) return r;
+        if (e->msc) {
+            if ((r = msc_energies(make_msc_args(e), L, s)) != cudaSuccess) return r;
+        } else {
+            Int8Args a = make_args(e);
+            if ((r = int8_energies(a, L, gauss, s)) != cudaSuccess) return r;
+        }
         return cudaStreamSynchronize(s);
     };
     ce = run();
@@ -450,6 +510,17 @@ void sg_destroy(sg_ensemble *e)
 
 static sg_status launch_sweeps(sg_ensemble *e, int64_t n, cudaStream_t s, bool device_counter)
 {
+    if (e->msc) {
+        // one launch per sweep: the exchange pairing alternates between sweeps
+        MscArgs a = make_msc_args(e);
+        if (device_counter) a.sweep0_dev = e->sweep_ctr;
+        for (int64_t k = 0; k < n; ++k) {
+            a.sweep_offset = (int)k;
+            SG_CUDA(msc_sweep(a, e->L, s), "MSC sweep kernel launch");
+        }
+        if (device_counter) SG_CUDA(advance_counter(e->sweep_ctr, n, s), "counter");
+        return SG_OK;
+    }
     int64_t chunk = e->opt.sweeps_per_launch > 0 ? e->opt.sweeps_per_launch : n;
     if (chunk < 1) chunk = 1;
     chunk = std::min<int64_t>(chunk, 1 << 30);
@@ -555,9 +626,16 @@ sg_status sg_sweep_batch(sg_ensemble *const *es, int n_ens, int64_t n, int use_g
 sg_status sg_exchange(sg_ensemble *e, int parity)
 {
     if (!e) return fail(SG_EINVAL, "ensemble is NULL");
-    Int8Args a = make_args(e);
-    SG_CUDA(int8_exchange(a, e->L, e->gauss, parity & 1, (uint32_t)e->exchanges_done, e->stream),
-            "exchange");
+    if (e->msc) {
+        SG_CUDA(msc_exchange(make_msc_args(e), e->L, parity & 1, (uint32_t)e->exchanges_done,
+                             e->masks, e->stream),
+                "exchange");
+    } else {
+        Int8Args a = make_args(e);
+        SG_CUDA(int8_exchange(a, e->L, e->gauss, parity & 1, (uint32_t)e->exchanges_done,
+                              e->stream),
+                "exchange");
+    }
     ++e->exchanges_done;
     return SG_OK;
 }
@@ -571,7 +649,9 @@ sg_status sg_measure(sg_ensemble *e, const int *k, int nk, float *out)
     SG_CUDA(cudaMalloc(&kd, sizeof(int) * 3 * nk), "cudaMalloc");
     cudaError_t ce = cudaMalloc(&od, ob);
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(kd, k, sizeof(int) * 3 * nk, cudaMemcpyHostToDevice, e->stream);
-    if (ce == cudaSuccess) ce = int8_measure_k(make_args(e), e->L, kd, nk, od, e->stream);
+    if (ce == cudaSuccess)
+        ce = e->msc ? msc_measure_k(make_msc_args(e), e->L, kd, nk, od, e->stream)
+                    : int8_measure_k(make_args(e), e->L, kd, nk, od, e->stream);
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(out, od, ob, cudaMemcpyDeviceToHost, e->stream);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(e->stream);
     cudaFree(kd);
@@ -583,6 +663,7 @@ sg_status sg_measure(sg_ensemble *e, const int *k, int nk, float *out)
 sg_status sg_measure_noalloc(sg_ensemble *e, const int *k, int nk, float *out)
 {
     if (!e || !k || nk < 1 || !out) return fail(SG_EINVAL, "bad measure arguments");
+    if (e->msc) return fail(SG_EUNSUPPORTED, "sg_measure_noalloc serves the int8 layout");
     if (nk > SG_MEASURE_NOALLOC_MAX_K)
         return fail(SG_EINVAL, "sg_measure_noalloc: more than SG_MEASURE_NOALLOC_MAX_K wave vectors");
     const size_t floats = (size_t)e->S * e->nt * nk * 2;
@@ -626,7 +707,8 @@ sg_status sg_get_spins(sg_ensemble *e, int8_t *out)
     const size_t bytes = (size_t)e->S * 2 * e->nt * e->L * e->L * e->L;
     int8_t *d = nullptr;
     SG_CUDA(cudaMalloc(&d, bytes), "cudaMalloc");
-    cudaError_t ce = int8_export_spins(d, e->spins, e->S, e->L, e->nt, e->Tp, e->stream);
+    cudaError_t ce = e->msc ? msc_export_spins(d, e->W, e->S / 64, e->L, e->nt, e->stream)
+                            : int8_export_spins(d, e->spins, e->S, e->L, e->nt, e->Tp, e->stream);
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(out, d, bytes, cudaMemcpyDeviceToHost, e->stream);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(e->stream);
     cudaFree(d);
@@ -643,8 +725,12 @@ sg_status sg_set_spins(sg_ensemble *e, const int8_t *in)
     int8_t *d = nullptr;
     SG_CUDA(cudaMalloc(&d, bytes), "cudaMalloc");
     cudaError_t ce = cudaMemcpyAsync(d, in, bytes, cudaMemcpyHostToDevice, e->stream);
-    if (ce == cudaSuccess) ce = int8_import_spins(e->spins, d, e->S, e->L, e->nt, e->Tp, e->stream);
-    if (ce == cudaSuccess) ce = int8_energies(make_args(e), e->L, e->gauss, e->stream);
+    if (ce == cudaSuccess)
+        ce = e->msc ? msc_import_spins(e->W, d, e->S / 64, e->L, e->nt, e->stream)
+                    : int8_import_spins(e->spins, d, e->S, e->L, e->nt, e->Tp, e->stream);
+    if (ce == cudaSuccess)
+        ce = e->msc ? msc_energies(make_msc_args(e), e->L, e->stream)
+                    : int8_energies(make_args(e), e->L, e->gauss, e->stream);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(e->stream);
     cudaFree(d);
     if (ce != cudaSuccess) return cuda_fail(ce, "set spins");
@@ -675,7 +761,8 @@ sg_status sg_get_couplings(sg_ensemble *e, float *out)
     const size_t bytes = (size_t)e->S * 3 * e->L * e->L * e->L * sizeof(float);
     float *d = nullptr;
     SG_CUDA(cudaMalloc(&d, bytes), "cudaMalloc");
-    cudaError_t ce = int8_export_J(d, e->J8, e->Jg, e->S, e->L, e->gauss, e->stream);
+    cudaError_t ce = e->msc ? msc_export_J(d, e->Jw, e->S / 64, e->L, e->stream)
+                            : int8_export_J(d, e->J8, e->Jg, e->S, e->L, e->gauss, e->stream);
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(out, d, bytes, cudaMemcpyDeviceToHost, e->stream);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(e->stream);
     cudaFree(d);

@@ -1,0 +1,793 @@
+// sg_msc.cu -- multispin-coded +-J path of the EA spin-glass engine (sm_103a).
+//
+// Multispin coding (paper: methods section, where the replicas of one sample
+// were packed into the bits of shared-memory words) is used here across
+// disorder samples: bit b of a 64-bit word belongs to sample 64*g + b of word
+// group g, so one logical operation updates 64 independent samples. The 64
+// samples of a word share the Metropolis random word of each (site, chain,
+// sweep) -- the RNG group G = 64 of the frozen random-number layout -- while
+// every sample draws its own replica-exchange numbers; the path therefore
+// reproduces, bit for bit, the int8 chain run with G = 64.
+//
+// Device layout (global memory):
+//   W   [G][n_T][2][N] uint64   chain (t, r) of word group g; bit 1 => spin -1
+//   Jw  [G][3][N] uint64        J[d][i] for the 64 samples; bit 1 => J = -1
+//   B,M [S][2][n_T] int64       bond sum and magnetisation per sample and chain
+// One launch is one sweep. Its CTAs each own one exchange unit -- a pair of
+// neighbouring slots (p, p+1) of the sweep's exchange parity, or a single
+// edge slot -- for both replicas, i.e. up to four chains in shared memory:
+// both half-sweeps, the per-sample energies, the pair's exchange (a masked
+// bit swap) and the overlap measurement of its slots all happen in one CTA.
+#include <cuda_runtime.h>
+
+#include "sg_device.cuh"
+#include "sg_msc.h"
+
+namespace sg {
+
+namespace {
+
+constexpr int kMscThreads = 512;
+constexpr int kDU = 9;  // bit planes of the per-thread unsatisfied-bond counter
+constexpr int kDM = 8;  // bit planes of the per-thread (-1 spin) counter
+constexpr int kDP = 9;  // bit planes of a projection (<= L^2 <= 256 sites)
+constexpr int kDG = 5;  // bit planes of a 2D marginal entry (<= L <= 16 sites)
+
+__device__ __forceinline__ uint64_t ldg64(const uint64_t *p) { return __ldg(p); }
+
+// Bit-sliced ripple add of a K-plane number into a D-plane counter.
+template <int D, int K>
+__device__ __forceinline__ void bs_add(uint64_t (&c)[D], const uint64_t (&x)[K])
+{
+    uint64_t carry = 0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        const uint64_t a = c[k];
+        const uint64_t b = k < K ? x[k] : 0ull;
+        c[k] = a ^ b ^ carry;
+        carry = (a & b) | (carry & (a ^ b));
+    }
+}
+
+// Column counts over the 32 lanes of a warp: lane l receives
+// sum over lanes of bit l of x (a 32x32 bit transpose by shuffles, then popc).
+__device__ __forceinline__ int warp_column_popc(uint32_t x)
+{
+    const int lane = threadIdx.x & 31;
+    uint32_t m = 0x0000FFFFu;
+#pragma unroll
+    for (int k = 16; k >= 1; k >>= 1, m ^= m << k) {
+        const uint32_t y = __shfl_xor_sync(0xFFFFFFFFu, x, k);
+        x = (lane & k) ? ((x & ~m) | ((y & ~m) >> k)) : ((x & m) | ((y & m) << k));
+    }
+    return __popc(x);
+}
+
+struct MscSmem {
+    uint64_t *w;        // [4][N]   chains: index q = 2*k + r (k = slot in unit)
+    uint32_t *thr;      // [2][16]  +-J thresholds of the unit's slots (sb*8 + u)
+    long long *B, *M;   // [4][64]  per-sample energies of the unit's chains
+    uint64_t *swap;     // [2]      exchange masks per replica
+    uint64_t *marg;     // [3][L*L][kDG] bit-sliced 2D marginal counts of q = -1
+    uint64_t *proj;     // [9][L][kDP] bit-sliced projection counts of q = -1
+};
+
+__host__ __device__ inline size_t a16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+__host__ __device__ inline size_t msc_carve(uint8_t *base, int L, MscSmem *sm)
+{
+    const size_t N = (size_t)L * L * L;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        uint8_t *p = base ? base + off : nullptr;
+        off = a16(off + bytes);
+        return p;
+    };
+    MscSmem s;
+    s.w = reinterpret_cast<uint64_t *>(take(4 * N * 8));
+    s.thr = reinterpret_cast<uint32_t *>(take(2 * 16 * 4));
+    s.B = reinterpret_cast<long long *>(take(4 * 64 * 8));
+    s.M = reinterpret_cast<long long *>(take(4 * 64 * 8));
+    s.swap = reinterpret_cast<uint64_t *>(take(2 * 8));
+    s.marg = reinterpret_cast<uint64_t *>(take((size_t)3 * L * L * kDG * 8));
+    s.proj = reinterpret_cast<uint64_t *>(take((size_t)9 * L * kDP * 8));
+    if (sm) *sm = s;
+    return off;
+}
+
+// Exchange unit u of parity par: first slot and slot count (1 or 2).
+__device__ __forceinline__ bool unit_slots(int u, int par, int nt, int *t0, int *cnt)
+{
+    if (par == 0) {
+        *t0 = 2 * u;
+    } else {
+        if (u == 0) {
+            *t0 = 0;
+            *cnt = 1;
+            return nt >= 1;
+        }
+        *t0 = 2 * u - 1;
+    }
+    if (*t0 >= nt) return false;
+    *cnt = (*t0 + 1 < nt) ? 2 : 1;
+    return true;
+}
+
+// u >= c for a bit-sliced 3-bit u and a scalar c in 0..7.
+__device__ __forceinline__ uint64_t ge_const(uint64_t u0, uint64_t u1, uint64_t u2, int c)
+{
+    const uint64_t C0 = (c & 1) ? ~0ull : 0ull;
+    const uint64_t C1 = (c & 2) ? ~0ull : 0ull;
+    const uint64_t C2 = (c & 4) ? ~0ull : 0ull;
+    const uint64_t a0 = ~u0 & C0;
+    const uint64_t a1 = (~u1 & C1) | (~(u1 ^ C1) & a0);
+    const uint64_t lt = (~u2 & C2) | (~(u2 ^ C2) & a1);
+    return ~lt;
+}
+
+// Number of unsatisfied-bond classes whose threshold rejects r: since the
+// threshold grows with u (the energy change falls), r <= thr[u] exactly for
+// u >= ustar.
+__device__ __forceinline__ int ustar_of(const uint32_t *thr_sb, uint32_t r)
+{
+    int c = 0;
+#pragma unroll
+    for (int u = 0; u < 7; ++u) c += r > thr_sb[u];
+    return c;
+}
+
+// Site index and neighbour offsets of the colour-c site with
+// colour-compressed index jj.
+template <int L>
+struct MscSite {
+    int i, x, dxp, dxm, dyp, dym, dzp, dzm;
+    __device__ __forceinline__ MscSite(int jj, int c)
+    {
+        constexpr int H = L / 2;
+        const int row = jj / H;
+        const int x2 = jj - row * H;
+        const int y = row % L;
+        const int z = row / L;
+        x = 2 * x2 + ((c + y + z) & 1);
+        i = x + L * row;
+        dxp = (x == L - 1) ? -(L - 1) : 1;
+        dxm = (x == 0) ? (L - 1) : -1;
+        dyp = (y == L - 1) ? -(L - 1) * L : L;
+        dym = (y == 0) ? (L - 1) * L : -L;
+        dzp = (z == L - 1) ? -(L - 1) * L * L : L * L;
+        dzm = (z == 0) ? (L - 1) * L * L : -L * L;
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Half-sweep of colour c for chain q (slot t, replica r) held in sm.w[q].
+// Thread team: the threads with (threadIdx.x / tpc) == q, tpc threads per
+// chain. For c == 1 the team also accumulates the per-sample unsatisfied-bond
+// and (-1)-spin counts of the post-sweep configuration into sm.B / sm.M
+// (raw counts; converted to B and M afterwards).
+// ---------------------------------------------------------------------------
+template <int L>
+__device__ __forceinline__ void msc_half(const MscSmem &sm, const MscArgs &a, int g, int q, int t,
+                                         int r, int tpc, int c, uint32_t n_sweep)
+{
+    constexpr int N = L * L * L;
+    constexpr int NG = (N / 2) / 4;  // Philox groups of four colour-c sites
+    const int tid = threadIdx.x % tpc;
+    uint64_t *w = sm.w + (size_t)q * N;
+    const uint64_t *J = a.Jw + (size_t)g * 3 * N;
+    const uint32_t *thr = sm.thr + (q >> 1) * 16;
+    uint64_t cu[kDU], cm[kDM];
+#pragma unroll
+    for (int k = 0; k < kDU; ++k) cu[k] = 0;
+#pragma unroll
+    for (int k = 0; k < kDM; ++k) cm[k] = 0;
+    const uint32_t c2 = ((uint32_t)c << 24) | ((uint32_t)r << 16) | (uint32_t)t;
+    for (int grp = tid; grp < NG; grp += tpc) {
+        const u32x4 rnd = philox10(a.seed_lo ^ kTagMet, (uint32_t)g, (uint32_t)grp, n_sweep, c2,
+                                   a.seed_hi);
+#pragma unroll
+        for (int lane = 0; lane < 4; ++lane) {
+            const MscSite<L> st(4 * grp + lane, c);
+            const int i = st.i;
+            const uint64_t s = w[i];
+            const uint64_t n0 = w[i + st.dxp], n1 = w[i + st.dxm];
+            const uint64_t n2 = w[i + st.dyp], n3 = w[i + st.dym];
+            const uint64_t n4 = w[i + st.dzp], n5 = w[i + st.dzm];
+            // unsatisfied bonds: s ^ s_nb ^ jbit
+            const uint64_t d0 = s ^ n0 ^ ldg64(J + i);
+            const uint64_t d1 = s ^ n1 ^ ldg64(J + i + st.dxm);
+            const uint64_t d2 = s ^ n2 ^ ldg64(J + N + i);
+            const uint64_t d3 = s ^ n3 ^ ldg64(J + N + i + st.dym);
+            const uint64_t d4 = s ^ n4 ^ ldg64(J + 2 * N + i);
+            const uint64_t d5 = s ^ n5 ^ ldg64(J + 2 * N + i + st.dzm);
+            // 3-bit count u of the six: two full adders and a carry merge
+            const uint64_t sa = d0 ^ d1 ^ d2, ca = (d0 & d1) | (d2 & (d0 ^ d1));
+            const uint64_t sb = d3 ^ d4 ^ d5, cb = (d3 & d4) | (d5 & (d3 ^ d4));
+            const uint64_t u0 = sa ^ sb, cc = sa & sb;
+            const uint64_t u1 = ca ^ cb ^ cc, u2 = (ca & cb) | (cc & (ca ^ cb));
+            const uint32_t rr = rnd.v[lane];
+            const uint64_t acc0 = ge_const(u0, u1, u2, ustar_of(thr, rr));      // s = +1
+            const uint64_t acc1 = ge_const(u0, u1, u2, ustar_of(thr + 8, rr));  // s = -1
+            const uint64_t f = (~s & acc0) | (s & acc1);
+            const uint64_t sn = s ^ f;
+            w[i] = sn;
+            if (c == 1) {
+                // u after the flip: 6 - u where flipped
+                const uint64_t n1b = ~(u1 ^ u0);
+                const uint64_t n2b = ~u2 & ~(u1 & u0);
+                const uint64_t un[3] = {u0, (u1 & ~f) | (n1b & f), (u2 & ~f) | (n2b & f)};
+                bs_add<kDU, 3>(cu, un);
+                const uint64_t partner = (st.x & 1) ? n1 : n0;
+                const uint64_t mm[2] = {sn ^ partner, sn & partner};
+                bs_add<kDM, 2>(cm, mm);
+            }
+        }
+    }
+    if (c == 1) {
+        // per-sample column counts: warp transpose-popc of every plane half
+        const int lane = threadIdx.x & 31;
+        long long vu_lo = 0, vu_hi = 0, vm_lo = 0, vm_hi = 0;
+#pragma unroll
+        for (int k = 0; k < kDU; ++k) {
+            vu_lo += (long long)warp_column_popc((uint32_t)cu[k]) << k;
+            vu_hi += (long long)warp_column_popc((uint32_t)(cu[k] >> 32)) << k;
+        }
+#pragma unroll
+        for (int k = 0; k < kDM; ++k) {
+            vm_lo += (long long)warp_column_popc((uint32_t)cm[k]) << k;
+            vm_hi += (long long)warp_column_popc((uint32_t)(cm[k] >> 32)) << k;
+        }
+        atomicAdd((unsigned long long *)&sm.B[q * 64 + lane], (unsigned long long)vu_lo);
+        atomicAdd((unsigned long long *)&sm.B[q * 64 + 32 + lane], (unsigned long long)vu_hi);
+        atomicAdd((unsigned long long *)&sm.M[q * 64 + lane], (unsigned long long)vm_lo);
+        atomicAdd((unsigned long long *)&sm.M[q * 64 + 32 + lane], (unsigned long long)vm_hi);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Overlap measurement of slot k of the unit for the 64 samples (eq. overlap):
+// bit-sliced 2D marginals, bit-sliced projections, then per sample the
+// integer projections, the FP32 DFT and the FP64 accumulation.
+// ---------------------------------------------------------------------------
+template <int L>
+__device__ __forceinline__ void msc_measure(const MscSmem &sm, const MscArgs &a, int g, int k,
+                                            int t)
+{
+    constexpr int N = L * L * L;
+    constexpr int LL = L * L;
+    const uint64_t *w0 = sm.w + (size_t)(2 * k) * N;
+    const uint64_t *w1 = w0 + N;
+    // (A) marginal counts of q = -1 (bit set) over the summed axis
+    for (int id = threadIdx.x; id < 3 * LL; id += blockDim.x) {
+        const int plane = id / LL, ab = id % LL;
+        const int A = ab / L, Bc = ab % L;
+        int base, step;
+        if (plane == 0) {        // (x=A, y=Bc), over z
+            base = A + L * Bc;
+            step = LL;
+        } else if (plane == 1) { // (x=A, z=Bc), over y
+            base = A + LL * Bc;
+            step = L;
+        } else {                 // (y=A, z=Bc), over x
+            base = L * A + LL * Bc;
+            step = 1;
+        }
+        uint64_t cnt[kDG];
+#pragma unroll
+        for (int p = 0; p < kDG; ++p) cnt[p] = 0;
+#pragma unroll 4
+        for (int m = 0; m < L; ++m) {
+            const int i = base + m * step;
+            const uint64_t qb[1] = {w0[i] ^ w1[i]};
+            bs_add<kDG, 1>(cnt, qb);
+        }
+#pragma unroll
+        for (int p = 0; p < kDG; ++p) sm.marg[(size_t)id * kDG + p] = cnt[p];
+    }
+    __syncthreads();
+    // (B) projection counts: sum of L marginal entries per (v, d)
+    for (int id = threadIdx.x; id < 9 * L; id += blockDim.x) {
+        const int v = id / L, d = id % L;
+        const int plane = (v == 0 || v == 1 || v == 3 || v == 4) ? 0 : (v == 2 || v == 5 || v == 6) ? 1 : 2;
+        uint64_t acc[kDP];
+#pragma unroll
+        for (int p = 0; p < kDP; ++p) acc[p] = 0;
+        for (int aa = 0; aa < L; ++aa) {
+            int A, Bc;
+            if (v == 0) {
+                A = d; Bc = aa;
+            } else if (v == 1 || v == 2) {
+                A = aa; Bc = d;
+            } else if (v == 3 || v == 5 || v == 7) {
+                A = aa; Bc = (d - aa + L) % L;
+            } else {
+                A = aa; Bc = (aa - d + L) % L;
+            }
+            const uint64_t *m = sm.marg + ((size_t)plane * LL + A * L + Bc) * kDG;
+            const uint64_t x[kDG] = {m[0], m[1], m[2], m[3], m[4]};
+            bs_add<kDP, kDG>(acc, x);
+        }
+#pragma unroll
+        for (int p = 0; p < kDP; ++p) sm.proj[(size_t)id * kDP + p] = acc[p];
+    }
+    __syncthreads();
+    // (C) per sample b and wave vector v (v == 9: Q, E and M)
+    for (int id = threadIdx.x; id < 64 * 10; id += blockDim.x) {
+        const int b = id % 64, v = id / 64;
+        const int64_t s = 64 * (int64_t)g + b;
+        double *ac = a.acc + ((size_t)s * a.nt + t) * SG_NACC;
+        const int vv = v == 9 ? 0 : v;
+        float re = 0.0f, im = 0.0f;
+        int Qi = 0;
+        for (int d = 0; d < L; ++d) {
+            const uint64_t *p = sm.proj + ((size_t)vv * L + d) * kDP;
+            int cnt = 0;
+#pragma unroll
+            for (int k2 = 0; k2 < kDP; ++k2) cnt |= (int)((p[k2] >> b) & 1ull) << k2;
+            const int P = LL - 2 * cnt;
+            Qi += P;
+            re = __fmaf_rn((float)P, a.twid[d], re);
+            im = __fmaf_rn((float)P, a.twid[L + d], im);
+        }
+        if (v == 9) {
+            const double Q = (double)Qi;
+            const double Q2 = __dmul_rn(Q, Q);
+            ac[0] = __dadd_rn(ac[0], 1.0);
+            ac[1] = __dadd_rn(ac[1], Q);
+            ac[2] = __dadd_rn(ac[2], Q2);
+            ac[3] = __dadd_rn(ac[3], __dmul_rn(Q2, Q));
+            ac[4] = __dadd_rn(ac[4], __dmul_rn(Q2, Q2));
+            for (int r = 0; r < 2; ++r) {
+                const long long Bv = sm.B[(2 * k + r) * 64 + b];
+                const long long Mv = sm.M[(2 * k + r) * 64 + b];
+                const double e = -__dadd_rn((double)Bv, __dmul_rn(a.h_d, (double)Mv));
+                ac[5] = __dadd_rn(ac[5], e);
+                ac[6] = __dadd_rn(ac[6], __dmul_rn(e, e));
+            }
+            for (int r = 0; r < 2; ++r) {
+                const double m = (double)sm.M[(2 * k + r) * 64 + b];
+                ac[7] = __dadd_rn(ac[7], m);
+                ac[8] = __dadd_rn(ac[8], __dmul_rn(m, m));
+            }
+        } else {
+            const double dr = (double)re, di = (double)im;
+            ac[9 + 3 * v] = __dadd_rn(ac[9 + 3 * v], dr);
+            ac[10 + 3 * v] = __dadd_rn(ac[10 + 3 * v], di);
+            ac[11 + 3 * v] =
+                __dadd_rn(ac[11 + 3 * v], __dadd_rn(__dmul_rn(dr, dr), __dmul_rn(di, di)));
+        }
+    }
+    __syncthreads();
+}
+
+template <int L>
+__global__ void __launch_bounds__(kMscThreads) msc_sweep_kernel(const MscArgs a)
+{
+    constexpr int N = L * L * L;
+    extern __shared__ __align__(16) uint8_t msc_smem[];
+    MscSmem sm;
+    msc_carve(msc_smem, L, &sm);
+    const int g = blockIdx.y;
+    const int64_t n = (a.sweep0_dev ? *a.sweep0_dev : a.sweep0) + a.sweep_offset;
+    const bool xchg = a.exchange_every > 0 && (n + 1) % a.exchange_every == 0;
+    const int par = xchg ? (int)(((n + 1) / a.exchange_every - 1) & 1) : 0;
+    int t0, cnt;
+    if (!unit_slots(blockIdx.x, par, a.nt, &t0, &cnt)) return;
+    const bool meas = n >= a.n_therm && (n - a.n_therm) % a.measure_every == 0;
+    const int nq = 2 * cnt;
+
+    // load the unit's chains (index q = 2k + r is contiguous in W) and tables
+    const uint64_t *src = a.W + ((size_t)g * a.nt + t0) * 2 * N;
+    for (int k = threadIdx.x; k < nq * N; k += blockDim.x) sm.w[k] = src[k];
+    for (int k = threadIdx.x; k < cnt * 16; k += blockDim.x) sm.thr[k] = a.thr[t0 * 16 + k];
+    for (int k = threadIdx.x; k < 4 * 64; k += blockDim.x) {
+        sm.B[k] = 0;
+        sm.M[k] = 0;
+    }
+    __syncthreads();
+
+    const int tpc = blockDim.x / nq;  // threads per chain
+    const int q = threadIdx.x / tpc;
+    for (int c = 0; c < 2; ++c) {
+        if (q < nq) msc_half<L>(sm, a, g, q, t0 + (q >> 1), q & 1, tpc, c, (uint32_t)n);
+        __syncthreads();
+    }
+    // raw counts -> B = 3N - 2 * (unsatisfied bonds), M = N - 2 * (#-1 spins)
+    for (int k = threadIdx.x; k < nq * 64; k += blockDim.x) {
+        sm.B[k] = 3LL * N - 2 * sm.B[k];
+        sm.M[k] = (long long)N - 2 * sm.M[k];
+    }
+    if (threadIdx.x < 2) sm.swap[threadIdx.x] = 0;
+    __syncthreads();
+
+    if (xchg && cnt == 2) {
+        // one thread per (replica, sample): Metropolis on the pair (t0, t0+1)
+        if (threadIdx.x < 128) {
+            const int r = threadIdx.x >> 6, b = threadIdx.x & 63;
+            const int64_t s = 64 * (int64_t)g + b;
+            const long long dB = sm.B[(0 + r) * 64 + b] - sm.B[(2 + r) * 64 + b];
+            const long long dM = sm.M[(0 + r) * 64 + b] - sm.M[(2 + r) * 64 + b];
+            const float t1 = __fmul_rn(__ll2float_rn(dB), 1.0f);
+            const float t2 = __fmul_rn(a.h_f, __ll2float_rn(dM));
+            const float dE = -__fadd_rn(t1, t2);
+            const float D = __fmul_rn(a.dbeta[t0], dE);
+            const u32x4 o = philox10(a.seed_lo ^ kTagExc, (uint32_t)s, (uint32_t)t0, (uint32_t)n,
+                                     (uint32_t)r, a.seed_hi);
+            const bool acc = (D >= 0.0f) || (o.v[0] <= thr_of_logp(D));
+            const unsigned bal = __ballot_sync(0xFFFFFFFFu, acc);
+            if ((threadIdx.x & 31) == 0)
+                atomicOr((unsigned long long *)&sm.swap[r],
+                         (unsigned long long)bal << (threadIdx.x & 32));
+            if (acc) {
+                const long long tb = sm.B[r * 64 + b];
+                sm.B[r * 64 + b] = sm.B[(2 + r) * 64 + b];
+                sm.B[(2 + r) * 64 + b] = tb;
+                const long long tm = sm.M[r * 64 + b];
+                sm.M[r * 64 + b] = sm.M[(2 + r) * 64 + b];
+                sm.M[(2 + r) * 64 + b] = tm;
+            }
+        }
+        __syncthreads();
+        for (int id = threadIdx.x; id < 2 * N; id += blockDim.x) {
+            const int r = id / N, i = id % N;
+            const uint64_t m = sm.swap[r];
+            if (!m) continue;
+            uint64_t *pa = sm.w + (size_t)r * N + i;         // slot t0
+            uint64_t *pb = sm.w + (size_t)(2 + r) * N + i;   // slot t0 + 1
+            const uint64_t x = (*pa ^ *pb) & m;
+            *pa ^= x;
+            *pb ^= x;
+        }
+        __syncthreads();
+    }
+    if (meas)
+        for (int k = 0; k < cnt; ++k) msc_measure<L>(sm, a, g, k, t0 + k);
+
+    uint64_t *dst = a.W + ((size_t)g * a.nt + t0) * 2 * N;
+    for (int k = threadIdx.x; k < nq * N; k += blockDim.x) dst[k] = sm.w[k];
+    for (int k = threadIdx.x; k < nq * 64; k += blockDim.x) {
+        const int qq = k / 64, b = k % 64;
+        const int64_t s = 64 * (int64_t)g + b;
+        const size_t o = ((size_t)s * 2 + (qq & 1)) * a.nt + t0 + (qq >> 1);
+        a.B[o] = sm.B[k];
+        a.M[o] = sm.M[k];
+    }
+}
+
+// ---- conversion, generation and standalone kernels ------------------------
+
+__device__ __forceinline__ int nb_site(int L, int i, int d, int step)
+{
+    int x = i % L, y = (i / L) % L, z = i / (L * L);
+    if (d == 0) x = (x + step + L) % L;
+    if (d == 1) y = (y + step + L) % L;
+    if (d == 2) z = (z + step + L) % L;
+    return x + L * (y + L * z);
+}
+
+// canonical int8 [S][2][nt][N] -> W [G][nt][2][N]
+__global__ void msc_import_spins_kernel(uint64_t *W, const int8_t *c, int64_t G, int L, int nt)
+{
+    const int N = L * L * L;
+    const int64_t total = G * nt * 2 * (int64_t)N;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % N);
+        const int r = (int)((e / N) % 2);
+        const int t = (int)((e / (2 * (int64_t)N)) % nt);
+        const int64_t g = e / (2 * (int64_t)N * nt);
+        uint64_t w = 0;
+        for (int b = 0; b < 64; ++b) {
+            const int64_t s = 64 * g + b;
+            if (c[((s * 2 + r) * nt + t) * N + i] < 0) w |= 1ull << b;
+        }
+        W[e] = w;
+    }
+}
+
+__global__ void msc_export_spins_kernel(int8_t *c, const uint64_t *W, int64_t S, int L, int nt)
+{
+    const int N = L * L * L;
+    const int64_t total = S * 2 * (int64_t)nt * N;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % N);
+        const int t = (int)((e / N) % nt);
+        const int r = (int)((e / ((int64_t)N * nt)) % 2);
+        const int64_t s = e / ((int64_t)2 * nt * N);
+        const int64_t g = s / 64;
+        const int b = (int)(s % 64);
+        const uint64_t w = W[((g * nt + t) * 2 + r) * N + i];
+        c[e] = ((w >> b) & 1ull) ? -1 : 1;
+    }
+}
+
+// canonical float [S][3][N] (+-1) -> Jw [G][3][N]
+__global__ void msc_import_J_kernel(uint64_t *Jw, const float *Jc, int64_t G, int L)
+{
+    const int N = L * L * L;
+    const int64_t total = G * 3 * (int64_t)N;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % N);
+        const int d = (int)((e / N) % 3);
+        const int64_t g = e / (3 * (int64_t)N);
+        uint64_t w = 0;
+        for (int b = 0; b < 64; ++b)
+            if (Jc[((64 * g + b) * 3 + d) * N + i] < 0.0f) w |= 1ull << b;
+        Jw[e] = w;
+    }
+}
+
+__global__ void msc_export_J_kernel(float *Jc, const uint64_t *Jw, int64_t S, int L)
+{
+    const int N = L * L * L;
+    const int64_t total = S * 3 * (int64_t)N;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % N);
+        const int d = (int)((e / N) % 3);
+        const int64_t s = e / (3 * (int64_t)N);
+        Jc[e] = ((Jw[((s / 64) * 3 + d) * N + i] >> (s % 64)) & 1ull) ? -1.0f : 1.0f;
+    }
+}
+
+// +-J bonds and initial spins drawn from the seed (same draws as the int8 path)
+__global__ void msc_gen_kernel(uint64_t *Jw, uint64_t *W, int64_t G, int L, int nt, uint32_t slo,
+                               uint32_t shi)
+{
+    const int N = L * L * L;
+    const int64_t nJ = G * 3 * (int64_t)N, nW = G * nt * 2 * (int64_t)N;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nJ + nW;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t w = 0;
+        if (e < nJ) {
+            const int i = (int)(e % N);
+            const int d = (int)((e / N) % 3);
+            const int64_t g = e / (3 * (int64_t)N);
+            for (int b = 0; b < 64; ++b) {
+                const u32x4 o = philox10(slo ^ kTagBond, (uint32_t)(64 * g + b), (uint32_t)(i >> 7),
+                                         (uint32_t)d, 0u, shi);
+                w |= (uint64_t)((o.v[(i >> 5) & 3] >> (i & 31)) & 1u) << b;
+            }
+            Jw[e] = w;
+        } else {
+            const int64_t f = e - nJ;
+            const int i = (int)(f % N);
+            const int r = (int)((f / N) % 2);
+            const int t = (int)((f / (2 * (int64_t)N)) % nt);
+            const int64_t g = f / (2 * (int64_t)N * nt);
+            for (int b = 0; b < 64; ++b) {
+                const u32x4 o = philox10(slo ^ kTagInit, (uint32_t)(64 * g + b), (uint32_t)(i >> 7),
+                                         ((uint32_t)r << 16) | (uint32_t)t, 0u, shi);
+                w |= (uint64_t)((o.v[(i >> 5) & 3] >> (i & 31)) & 1u) << b;
+            }
+            W[f] = w;
+        }
+    }
+}
+
+// B and M of every sample and chain straight from the bond sum.
+__global__ void msc_energies_kernel(const MscArgs a, int L)
+{
+    const int N = L * L * L;
+    const int64_t S = a.G * 64;
+    const int64_t total = S * 2 * a.nt;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int t = (int)(e % a.nt);
+        const int r = (int)((e / a.nt) % 2);
+        const int64_t s = e / (2 * a.nt);
+        const int64_t g = s / 64;
+        const int b = (int)(s % 64);
+        const uint64_t *w = a.W + ((g * a.nt + t) * 2 + r) * N;
+        const uint64_t *J = a.Jw + g * 3 * N;
+        long long B = 0, M = 0;
+        for (int i = 0; i < N; ++i) {
+            const int si = ((w[i] >> b) & 1ull) ? -1 : 1;
+            M += si;
+            for (int d = 0; d < 3; ++d) {
+                const int j = nb_site(L, i, d, +1);
+                const int sj = ((w[j] >> b) & 1ull) ? -1 : 1;
+                const int jb = ((J[d * N + i] >> b) & 1ull) ? -1 : 1;
+                B += jb * si * sj;
+            }
+        }
+        a.B[e] = B;
+        a.M[e] = M;
+    }
+}
+
+// Standalone exchange: one thread per (sample, replica, pair), then the
+// masked swaps, on the global-memory state (call after msc_energies_kernel).
+__global__ void msc_exchange_decide_kernel(const MscArgs a, int parity, uint32_t call_id,
+                                           uint64_t *masks /* [G][2][nt] */)
+{
+    const int64_t S = a.G * 64;
+    const int np = (a.nt - parity) / 2;
+    const int64_t total = S * 2 * (int64_t)np;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int m = (int)(e % np);
+        const int r = (int)((e / np) % 2);
+        const int64_t s = e / (2 * (int64_t)np);
+        const int p = parity + 2 * m;
+        int64_t *Bp = a.B + (s * 2 + r) * a.nt + p;
+        int64_t *Mp = a.M + (s * 2 + r) * a.nt + p;
+        const long long dB = Bp[0] - Bp[1], dM = Mp[0] - Mp[1];
+        const float t1 = __fmul_rn(__ll2float_rn(dB), 1.0f);
+        const float t2 = __fmul_rn(a.h_f, __ll2float_rn(dM));
+        const float dE = -__fadd_rn(t1, t2);
+        const float D = __fmul_rn(a.dbeta[p], dE);
+        const u32x4 o = philox10(a.seed_lo ^ kTagExc, (uint32_t)s, (uint32_t)p, call_id,
+                                 (uint32_t)r | 0x100u, a.seed_hi);
+        if ((D >= 0.0f) || (o.v[0] <= thr_of_logp(D))) {
+            const int64_t tb = Bp[0]; Bp[0] = Bp[1]; Bp[1] = tb;
+            const int64_t tm = Mp[0]; Mp[0] = Mp[1]; Mp[1] = tm;
+            atomicOr((unsigned long long *)&masks[((s / 64) * 2 + r) * a.nt + p],
+                     1ull << (s % 64));
+        }
+    }
+}
+
+__global__ void msc_exchange_apply_kernel(const MscArgs a, int L, const uint64_t *masks)
+{
+    const int N = L * L * L;
+    const int64_t total = a.G * 2 * (int64_t)a.nt * N;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % N);
+        const int p = (int)((e / N) % a.nt);
+        const int r = (int)((e / ((int64_t)N * a.nt)) % 2);
+        const int64_t g = e / (2 * (int64_t)N * a.nt);
+        const uint64_t m = masks[(g * 2 + r) * a.nt + p];
+        if (!m || p + 1 >= a.nt) continue;
+        uint64_t *pa = a.W + ((g * a.nt + p) * 2 + r) * N + i;
+        uint64_t *pb = a.W + ((g * a.nt + p + 1) * 2 + r) * N + i;
+        const uint64_t x = (*pa ^ *pb) & m;
+        *pa ^= x;
+        *pb ^= x;
+    }
+}
+
+// q(k) for arbitrary integer k, one thread per (sample, slot, k).
+__global__ void msc_measure_k_kernel(const MscArgs a, int L, const int *kv, int nk, float *out)
+{
+    const int N = L * L * L;
+    const int64_t S = a.G * 64;
+    const int64_t total = S * a.nt * (int64_t)nk;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int j = (int)(e % nk);
+        const int t = (int)((e / nk) % a.nt);
+        const int64_t s = e / ((int64_t)nk * a.nt);
+        const int64_t g = s / 64;
+        const int b = (int)(s % 64);
+        const uint64_t *w0 = a.W + ((g * a.nt + t) * 2 + 0) * N;
+        const uint64_t *w1 = w0 + N;
+        float re = 0.0f, im = 0.0f;
+        for (int i = 0; i < N; ++i) {
+            const int x = i % L, y = (i / L) % L, z = i / (L * L);
+            const int q = (((w0[i] ^ w1[i]) >> b) & 1ull) ? -1 : 1;
+            int ph = (kv[3 * j] * x + kv[3 * j + 1] * y + kv[3 * j + 2] * z) % L;
+            if (ph < 0) ph += L;
+            float sn, cs;
+            sincospif(2.0f * (float)ph / (float)L, &sn, &cs);
+            re += q * cs;
+            im += q * sn;
+        }
+        out[2 * e] = re / (float)N;
+        out[2 * e + 1] = im / (float)N;
+    }
+}
+
+inline int gridn(int64_t work, int threads)
+{
+    int64_t b = (work + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > 148 * 32) b = 148 * 32;
+    return (int)b;
+}
+
+constexpr int kMscMaxSmem = 227 * 1024;
+
+template <int L>
+cudaError_t msc_launch_t(const MscArgs &a, cudaStream_t st)
+{
+    static cudaError_t attr = cudaFuncSetAttribute(
+        msc_sweep_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMscMaxSmem);
+    if (attr != cudaSuccess) return attr;
+    const size_t smem = msc_carve(nullptr, L, nullptr);
+    dim3 grid((unsigned)(a.nt / 2 + 1), (unsigned)a.G);
+    msc_sweep_kernel<L><<<grid, kMscThreads, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+#define SG_MSC_FOR_EACH_L(X) X(2) X(4) X(6) X(8) X(10) X(12) X(14) X(16)
+
+}  // namespace
+
+size_t msc_smem_bytes(int L)
+{
+    const size_t b = msc_carve(nullptr, L, nullptr);
+    return b <= (size_t)kMscMaxSmem ? b : 0;
+}
+
+bool msc_supported_L(int L)
+{
+#define X(LL) if (L == LL) return msc_smem_bytes(L) > 0;
+    SG_MSC_FOR_EACH_L(X)
+#undef X
+    return false;
+}
+
+cudaError_t msc_sweep(const MscArgs &a, int L, cudaStream_t st)
+{
+#define X(LL) if (L == LL) return msc_launch_t<LL>(a, st);
+    SG_MSC_FOR_EACH_L(X)
+#undef X
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t msc_import_spins(uint64_t *W, const int8_t *c, int64_t G, int L, int nt, cudaStream_t st)
+{
+    msc_import_spins_kernel<<<gridn(G * nt * 2 * L * L * L, 256), 256, 0, st>>>(W, c, G, L, nt);
+    return cudaGetLastError();
+}
+
+cudaError_t msc_export_spins(int8_t *c, const uint64_t *W, int64_t G, int L, int nt, cudaStream_t st)
+{
+    msc_export_spins_kernel<<<gridn(G * 64 * 2 * nt * L * L * L, 256), 256, 0, st>>>(c, W, G * 64, L,
+                                                                                    nt);
+    return cudaGetLastError();
+}
+
+cudaError_t msc_import_J(uint64_t *Jw, const float *Jc, int64_t G, int L, cudaStream_t st)
+{
+    msc_import_J_kernel<<<gridn(G * 3 * L * L * L, 256), 256, 0, st>>>(Jw, Jc, G, L);
+    return cudaGetLastError();
+}
+
+cudaError_t msc_export_J(float *Jc, const uint64_t *Jw, int64_t G, int L, cudaStream_t st)
+{
+    msc_export_J_kernel<<<gridn(G * 64 * 3 * L * L * L, 256), 256, 0, st>>>(Jc, Jw, G * 64, L);
+    return cudaGetLastError();
+}
+
+cudaError_t msc_generate(uint64_t *Jw, uint64_t *W, int64_t G, int L, int nt, uint32_t slo,
+                         uint32_t shi, cudaStream_t st)
+{
+    msc_gen_kernel<<<gridn(G * (3 + 2 * nt) * L * L * L, 128), 128, 0, st>>>(Jw, W, G, L, nt, slo,
+                                                                              shi);
+    return cudaGetLastError();
+}
+
+cudaError_t msc_energies(const MscArgs &a, int L, cudaStream_t st)
+{
+    msc_energies_kernel<<<gridn(a.G * 64 * 2 * a.nt, 128), 128, 0, st>>>(a, L);
+    return cudaGetLastError();
+}
+
+cudaError_t msc_exchange(const MscArgs &a, int L, int parity, uint32_t call_id, uint64_t *masks,
+                         cudaStream_t st)
+{
+    cudaError_t e = msc_energies(a, L, st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(masks, 0, sizeof(uint64_t) * a.G * 2 * a.nt, st);
+    if (e != cudaSuccess) return e;
+    const int np = (a.nt - parity) / 2;
+    msc_exchange_decide_kernel<<<gridn(a.G * 64 * 2 * (np > 0 ? np : 1), 128), 128, 0, st>>>(
+        a, parity, call_id, masks);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    msc_exchange_apply_kernel<<<gridn(a.G * 2 * a.nt * L * L * L, 256), 256, 0, st>>>(a, L, masks);
+    return cudaGetLastError();
+}
+
+cudaError_t msc_measure_k(const MscArgs &a, int L, const int *k_dev, int nk, float *out,
+                          cudaStream_t st)
+{
+    msc_measure_k_kernel<<<gridn(a.G * 64 * a.nt * nk, 128), 128, 0, st>>>(a, L, k_dev, nk, out);
+    return cudaGetLastError();
+}
+
+}  // namespace sg

@@ -1,0 +1,48 @@
+// sg_msc.h -- internal interface of the multispin-coded +-J path.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/sgmc.h"
+
+namespace sg {
+
+struct MscArgs {
+    uint64_t *W;          // [G][nt][2][N] spin words, bit b = sample 64g + b
+    const uint64_t *Jw;   // [G][3][N] coupling words, bit 1 => J = -1
+    int64_t *B, *M;       // [S][2][nt]
+    double *acc;          // [S][nt][40]
+    const uint32_t *thr;  // [nt][16] thresholds, entry sb*8 + u
+    const float *dbeta;   // [nt] (float)(beta_t - beta_{t+1})
+    const float *twid;    // [2][L] FP32 cos, sin of 2 pi d / L
+    int64_t G;            // word groups (S / 64)
+    int nt;
+    float h_f;
+    double h_d;
+    uint32_t seed_lo, seed_hi;
+    int64_t sweep0;
+    const int64_t *sweep0_dev;  // if set, the base sweep index is read here
+    int sweep_offset;           // this launch's sweep = base + sweep_offset
+    int exchange_every, measure_every;
+    int64_t n_therm;
+};
+
+size_t msc_smem_bytes(int L);
+bool msc_supported_L(int L);
+cudaError_t msc_sweep(const MscArgs &a, int L, cudaStream_t st);
+cudaError_t msc_import_spins(uint64_t *W, const int8_t *canon, int64_t G, int L, int nt,
+                             cudaStream_t st);
+cudaError_t msc_export_spins(int8_t *canon, const uint64_t *W, int64_t G, int L, int nt,
+                             cudaStream_t st);
+cudaError_t msc_import_J(uint64_t *Jw, const float *Jc, int64_t G, int L, cudaStream_t st);
+cudaError_t msc_export_J(float *Jc, const uint64_t *Jw, int64_t G, int L, cudaStream_t st);
+cudaError_t msc_generate(uint64_t *Jw, uint64_t *W, int64_t G, int L, int nt, uint32_t slo,
+                         uint32_t shi, cudaStream_t st);
+cudaError_t msc_energies(const MscArgs &a, int L, cudaStream_t st);
+cudaError_t msc_exchange(const MscArgs &a, int L, int parity, uint32_t call_id, uint64_t *masks,
+                         cudaStream_t st);
+cudaError_t msc_measure_k(const MscArgs &a, int L, const int *k_dev, int nk, float *out,
+                          cudaStream_t st);
+
+}  // namespace sg
