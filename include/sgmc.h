@@ -111,7 +111,7 @@ size_t sg_ensemble_bytes(int L, int n_T, int64_t n_samples, sg_coupling dist,
 
 /*
  * Create an ensemble of n_samples disorder samples on the current device.
- *   L        even, 2 <= L <= 32 (even L keeps the two-colour checkerboard a
+ *   L        even, 2 <= L <= 24 (even L keeps the two-colour checkerboard a
  *            proper colouring under periodic boundaries)
  *   h        uniform field (eq. Hamiltonian); rounded to the 2^-17 grid when
  *            dist == SG_GAUSS

@@ -8,6 +8,7 @@ import hashlib
 import os
 import subprocess
 import sys
+from concurrent.futures import ThreadPoolExecutor
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
@@ -48,17 +49,18 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB
     os.makedirs(OBJ, exist_ok=True)
     cu, cpp = _sources()
-    objs = []
+    jobs = []
     for f in cu:
         o = os.path.join(OBJ, f + ".o")
-        cmd = [NVCC] + NVCC_FLAGS + (["-Xptxas", "-v"] if verbose else []) + \
-            ["-c", os.path.join(CSRC, f), "-o", o]
-        subprocess.check_call(cmd)
-        objs.append(o)
+        jobs.append(([NVCC] + NVCC_FLAGS + (["-Xptxas", "-v"] if verbose else []) +
+                     ["-c", os.path.join(CSRC, f), "-o", o], o))
     for f in cpp:
         o = os.path.join(OBJ, f + ".o")
-        subprocess.check_call(["g++"] + CXX_FLAGS + ["-c", os.path.join(CSRC, f), "-o", o])
-        objs.append(o)
+        jobs.append((["g++"] + CXX_FLAGS + ["-c", os.path.join(CSRC, f), "-o", o], o))
+    # translation units compile in parallel
+    with ThreadPoolExecutor(max(1, min(len(jobs), os.cpu_count() or 1))) as ex:
+        list(ex.map(lambda j: subprocess.check_call(j[0]), jobs))
+    objs = [o for _, o in jobs]
     tmp = LIB + f".tmp{os.getpid()}"
     subprocess.check_call([NVCC] + ARCH + ["-shared", "-o", tmp] + objs +
                           ["-cudart", "static", "-lpthread", "-ldl", "-lrt"])

@@ -141,44 +141,50 @@ sg_status configure_launch(sg_ensemble *e)
     while (run % 4) run += H;
     const int items = (L * L * L / 2) / run * WR;
     const int maxt = int8_max_threads();
-    double best_score = -1.0;
-    int best_t = 0, best_m = 0, best_occ = 0;
-    for (int t = WR; t <= maxt; t += WR) {
-        if (t < 32) continue;  // the measurement needs one full warp
-        if (e->opt.threads_per_block > 0 && t != std::max(WR, (e->opt.threads_per_block / WR) * WR))
-            continue;
-        int occ = 0, m_for = 0;
-        for (int m = WR; m >= 1; --m) {
-            const size_t smem = int8_smem_bytes(L, e->Tp, e->gauss, m);
-            if (!smem) continue;
-            const int o = int8_ctas_per_sm(L, e->gauss, t, smem);
-            if (o > occ) {
-                occ = o;
-                m_for = m;
+    // shared-memory residency first; the global-memory variant when the
+    // sample's state does not fit (large L or many temperatures)
+    for (int pass = 0; pass < 2; ++pass) {
+        const bool gst = pass == 1;
+        double best_score = -1.0;
+        int best_t = 0, best_m = 0, best_occ = 0;
+        for (int t = WR; t <= maxt; t += WR) {
+            if (t < 32) continue;  // the measurement needs one full warp
+            if (e->opt.threads_per_block > 0 &&
+                t != std::max(WR, (e->opt.threads_per_block / WR) * WR))
+                continue;
+            int occ = 0, m_for = 0;
+            for (int m = WR; m >= 1; --m) {
+                const size_t smem = int8_smem_bytes(L, e->Tp, e->gauss, m, gst);
+                if (!smem) continue;
+                const int o = int8_ctas_per_sm(L, e->gauss, t, smem, gst);
+                if (o > occ) {
+                    occ = o;
+                    m_for = m;
+                }
+            }
+            if (!occ) continue;
+            // useful threads per SM: work items in flight per round, over the
+            // resident CTAs; ties go to more CTAs (barriers overlap) and fewer threads
+            const int rounds = (items + t - 1) / t;
+            const double useful = (double)items / rounds * occ;
+            const double score = std::min(useful, 1024.0) + 0.5 * occ - 1e-3 * t;
+            if (score > best_score) {
+                best_score = score;
+                best_t = t;
+                best_m = m_for;
+                best_occ = occ;
             }
         }
-        if (!occ) continue;
-        // useful threads per SM: work items in flight per round, over the
-        // resident CTAs; ties go to more CTAs (barriers overlap) and fewer threads
-        const int rounds = (items + t - 1) / t;
-        const double useful = (double)items / rounds * occ;
-        const double score = std::min(useful, 1024.0) + 0.5 * occ - 1e-3 * t;
-        if (score > best_score) {
-            best_score = score;
-            best_t = t;
-            best_m = m_for;
-            best_occ = occ;
-        }
+        if (best_occ == 0) continue;
+        e->mchunk = best_m;
+        e->launch.threads = best_t;
+        e->launch.gst = gst;
+        e->launch.smem = int8_smem_bytes(L, e->Tp, e->gauss, best_m, gst);
+        const int64_t resident = (int64_t)best_occ * e->num_sms;
+        e->launch.grid = (int)std::min<int64_t>(e->S, resident);
+        return SG_OK;
     }
-    if (best_occ == 0)
-        return fail(SG_EUNSUPPORTED, "int8 state of one sample does not fit in shared memory "
-                                     "(use fewer temperatures or a smaller L)");
-    e->mchunk = best_m;
-    e->launch.threads = best_t;
-    e->launch.smem = int8_smem_bytes(L, e->Tp, e->gauss, best_m);
-    const int64_t resident = (int64_t)best_occ * e->num_sms;
-    e->launch.grid = (int)std::min<int64_t>(e->S, resident);
-    return SG_OK;
+    return fail(SG_EUNSUPPORTED, "no int8 kernel serves this lattice size");
 }
 
 Int8Args make_args(sg_ensemble *e)
@@ -281,7 +287,7 @@ void host_tables(const sg_ensemble *e, std::vector<uint32_t> &thr, std::vector<f
 sg_status validate(int L, const double *T, int nt, sg_coupling dist, int64_t S,
                    const sg_options &o)
 {
-    if (L < 2 || (L & 1) || L > 32) return fail(SG_EINVAL, "L must be even and in [2, 32]");
+    if (L < 2 || (L & 1) || L > 24) return fail(SG_EINVAL, "L must be even and in [2, 24]");
     if (nt < 1 || nt > 64) return fail(SG_EINVAL, "n_T must be in [1, 64]");
     if (!T) return fail(SG_EINVAL, "temperature array is NULL");
     for (int t = 0; t < nt; ++t) {

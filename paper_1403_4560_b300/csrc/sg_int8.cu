@@ -70,8 +70,10 @@ struct Smem {
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 // Carve the dynamic shared memory; returns the bytes used.
+// gst: the sample's spins and couplings stay in global memory (large L);
+// only the small tables are carved.
 __host__ __device__ inline size_t carve(uint8_t *base, int L, int Tp, bool gauss, int mchunk,
-                                        Smem *sm)
+                                        Smem *sm, bool gst = false)
 {
     const size_t N = (size_t)L * L * L;
     size_t off = 0;
@@ -81,9 +83,9 @@ __host__ __device__ inline size_t carve(uint8_t *base, int L, int Tp, bool gauss
         return p;
     };
     Smem s;
-    s.spins = take(N * 2 * Tp);
-    s.J8 = gauss ? nullptr : take(N * 8);
-    s.Jg = gauss ? reinterpret_cast<float *>(take(N * 3 * sizeof(float))) : nullptr;
+    s.spins = gst ? nullptr : take(N * 2 * Tp);
+    s.J8 = (gauss || gst) ? nullptr : take(N * 8);
+    s.Jg = (gauss && !gst) ? reinterpret_cast<float *>(take(N * 3 * sizeof(float))) : nullptr;
     s.thr = gauss ? nullptr : reinterpret_cast<uint32_t *>(take((size_t)Tp * 16 * 4));
     s.negbeta = reinterpret_cast<float *>(take((size_t)Tp * 4));
     s.dbeta = reinterpret_cast<float *>(take((size_t)Tp * 4));
@@ -221,6 +223,9 @@ __device__ __forceinline__ void half_sweep(const Smem &sm, const Ctx &cx, uint32
         const int u = item / WR;
         uint32_t eacc0 = 0, eacc1 = 0, macc0 = 0, macc1 = 0;  // byte-wise partial sums
         int bg[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+        // long runs would overflow the byte-wise sums of unsatisfied bonds
+        // (6 per site): those are flushed into bg after every group of 4 sites
+        constexpr bool kFlushU = 6 * RUN > 255;
         for (int g = 0; g < NG; ++g) {
             const uint32_t c0 = (uint32_t)(u * NG + g);
             uint32_t rnd[2][4][4];
@@ -293,6 +298,14 @@ __device__ __forceinline__ void half_sweep(const Smem &sm, const Ctx &cx, uint32
                     macc1 += sn.y + partner.y;
                 }
             }
+            if (kFlushU && !GAUSS && COL == 1) {
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {
+                    bg[0][kk] += (eacc0 >> (8 * kk)) & 0xFFu;
+                    bg[1][kk] += (eacc1 >> (8 * kk)) & 0xFFu;
+                }
+                eacc0 = eacc1 = 0;
+            }
         }
         if (COL == 1) {
 #pragma unroll
@@ -304,8 +317,8 @@ __device__ __forceinline__ void half_sweep(const Smem &sm, const Ctx &cx, uint32
                     const uint32_t ea = r ? eacc1 : eacc0;
                     const uint32_t ma = r ? macc1 : macc0;
                     // +-J: s b = 6 - 2u per colour-1 site; M: each pair gives 2 - 2*(#-1)
-                    const long long b = GAUSS ? (long long)bg[r][kk]
-                                              : 6LL * RUN - 2LL * ((ea >> (8 * kk)) & 0xFFu);
+                    const long long usum = (long long)((ea >> (8 * kk)) & 0xFFu) + (kFlushU ? bg[r][kk] : 0);
+                    const long long b = GAUSS ? (long long)bg[r][kk] : 6LL * RUN - 2LL * usum;
                     const long long mm = 2LL * RUN - 2LL * ((ma >> (8 * kk)) & 0xFFu);
                     atomicAdd(&sm.B[r * cx.Tp + t], (unsigned long long)b);
                     atomicAdd(&sm.M[r * cx.Tp + t], (unsigned long long)mm);
@@ -405,14 +418,14 @@ __device__ __forceinline__ void exchange_apply(const Smem &sm, const Ctx &cx, ui
 
 // Counts of q = -1 per phase d of one wave vector, from the 2D marginal
 // pm[(A*L + B)*nw] (byte sh): PAT 0: A = d; 1: B = d; 2: A + B = d;
-// 3: A - B = d (mod L). Fully unrolled: L*L independent loads.
+// 3: A - B = d (mod L). The L sums are independent load chains.
 template <int L, int PAT>
 __device__ __forceinline__ void count_pattern(const uint32_t *pm, int nw, int sh, int (&cs)[L])
 {
 #pragma unroll
     for (int d = 0; d < L; ++d) {
         int c = 0;
-#pragma unroll
+#pragma unroll 4
         for (int aa = 0; aa < L; ++aa) {
             const int A = PAT == 0 ? d : aa;
             const int Bc = PAT == 0 ? aa : PAT == 1 ? d : PAT == 2 ? (d - aa + L) % L : (aa - d + L) % L;
@@ -544,13 +557,13 @@ __device__ __forceinline__ void copy16(void *dst, const void *src, size_t bytes)
 // The fused kernel: for each sample of this CTA, load, run n_sweeps sweeps
 // (half-sweeps, energies, exchange, measurement), store.
 // ---------------------------------------------------------------------------
-template <int L, bool GAUSS>
+template <int L, bool GAUSS, bool GST>
 __global__ void __launch_bounds__(kMaxThreads) int8_run_kernel(const Int8Args a)
 {
     constexpr int N = L * L * L;
     extern __shared__ __align__(16) uint8_t smem_raw[];
     Smem sm;
-    carve(smem_raw, L, a.Tp, GAUSS, a.mchunk, &sm);
+    carve(smem_raw, L, a.Tp, GAUSS, a.mchunk, &sm, GST);
     Ctx cx;
     cx.nt = a.nt;
     cx.Tp = a.Tp;
@@ -575,11 +588,20 @@ __global__ void __launch_bounds__(kMaxThreads) int8_run_kernel(const Int8Args a)
         cx.k0 = a.seed_lo ^ kTagMet;
         cx.k1 = (uint32_t)(s / a.rng_group);
         __syncthreads();
-        copy16(sm.spins, a.spins + (size_t)s * N * cx.RB, (size_t)N * cx.RB);
-        if (!GAUSS)
-            copy16(sm.J8, a.J8 + (size_t)s * N * 8, (size_t)N * 8);
-        else
-            copy16(sm.Jg, a.Jg + (size_t)s * 3 * N, (size_t)3 * N * sizeof(float));
+        if (GST) {
+            // large lattices: the CTA works on the sample's state in place
+            sm.spins = a.spins + (size_t)s * N * cx.RB;
+            if (!GAUSS)
+                sm.J8 = const_cast<uint8_t *>(a.J8) + (size_t)s * N * 8;
+            else
+                sm.Jg = const_cast<float *>(a.Jg) + (size_t)s * 3 * N;
+        } else {
+            copy16(sm.spins, a.spins + (size_t)s * N * cx.RB, (size_t)N * cx.RB);
+            if (!GAUSS)
+                copy16(sm.J8, a.J8 + (size_t)s * N * 8, (size_t)N * 8);
+            else
+                copy16(sm.Jg, a.Jg + (size_t)s * 3 * N, (size_t)3 * N * sizeof(float));
+        }
         for (int k = threadIdx.x; k < 2 * a.Tp; k += blockDim.x) {
             sm.xflag[k] = 0;
             sm.B[k] = (unsigned long long)a.B[s * 2 * a.Tp + k];
@@ -625,7 +647,7 @@ __global__ void __launch_bounds__(kMaxThreads) int8_run_kernel(const Int8Args a)
             if (n >= a.n_therm && (n - a.n_therm) % a.measure_every == 0) measure_step<L>(sm, cx, a);
         }
         __syncthreads();
-        copy16(a.spins + (size_t)s * N * cx.RB, sm.spins, (size_t)N * cx.RB);
+        if (!GST) copy16(a.spins + (size_t)s * N * cx.RB, sm.spins, (size_t)N * cx.RB);
         for (int k = threadIdx.x; k < 2 * a.Tp; k += blockDim.x) {
             a.B[s * 2 * a.Tp + k] = (int64_t)sm.B[k];
             a.M[s * 2 * a.Tp + k] = (int64_t)sm.M[k];
@@ -935,28 +957,28 @@ inline int grid_for(int64_t work, int threads)
 constexpr int kMaxSmem = 227 * 1024;
 
 // Raise the kernel's dynamic shared-memory limit once (before any capture).
-template <int L, bool G>
+template <int L, bool G, bool GST>
 cudaError_t ensure_attr()
 {
     static cudaError_t done = cudaFuncSetAttribute(
-        int8_run_kernel<L, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+        int8_run_kernel<L, G, GST>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
     return done;
 }
 
-template <int L, bool G>
+template <int L, bool G, bool GST>
 cudaError_t launch_t(const Int8Args &a, const Int8Launch &c, cudaStream_t st)
 {
-    cudaError_t e = ensure_attr<L, G>();
+    cudaError_t e = ensure_attr<L, G, GST>();
     if (e != cudaSuccess) return e;
-    int8_run_kernel<L, G><<<c.grid, c.threads, c.smem, st>>>(a);
+    int8_run_kernel<L, G, GST><<<c.grid, c.threads, c.smem, st>>>(a);
     return cudaGetLastError();
 }
 
-template <int L, bool G>
+template <int L, bool G, bool GST>
 int occ_t(int threads, size_t smem)
 {
-    auto k = int8_run_kernel<L, G>;
-    if (ensure_attr<L, G>() != cudaSuccess) return 0;
+    auto k = int8_run_kernel<L, G, GST>;
+    if (ensure_attr<L, G, GST>() != cudaSuccess) return 0;
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, threads, smem) != cudaSuccess)
         return 0;
@@ -964,12 +986,18 @@ int occ_t(int threads, size_t smem)
 }
 
 #define SG_FOR_EACH_L(X) X(2) X(4) X(6) X(8) X(10) X(12) X(14) X(16)
+#define SG_FOR_EACH_GST_L(X) X(10) X(12) X(14) X(16) X(18) X(20) X(22) X(24)
 
 }  // namespace
 
-size_t int8_smem_bytes(int L, int Tp, bool gauss, int mchunk)
+size_t int8_smem_bytes(int L, int Tp, bool gauss, int mchunk, bool gst)
 {
-    size_t b = carve(nullptr, L, Tp, gauss, mchunk, nullptr);
+    bool ok = false;
+#define X(LL) ok |= (L == LL);
+    if (gst) { SG_FOR_EACH_GST_L(X) } else { SG_FOR_EACH_L(X) }
+#undef X
+    if (!ok) return 0;
+    size_t b = carve(nullptr, L, Tp, gauss, mchunk, nullptr, gst);
     return b <= (size_t)kMaxSmem ? b : 0;
 }
 
@@ -978,19 +1006,35 @@ int int8_max_threads() { return kMaxThreads; }
 cudaError_t int8_launch(int L, bool gauss, const Int8Args &a, const Int8Launch &cfg,
                         cudaStream_t st)
 {
-#define X(LL)                                                                           \
-    if (L == LL) return gauss ? launch_t<LL, true>(a, cfg, st) : launch_t<LL, false>(a, cfg, st);
-    SG_FOR_EACH_L(X)
+    if (cfg.gst) {
+#define X(LL)                                                                         \
+        if (L == LL)                                                                  \
+            return gauss ? launch_t<LL, true, true>(a, cfg, st) : launch_t<LL, false, true>(a, cfg, st);
+        SG_FOR_EACH_GST_L(X)
 #undef X
+    } else {
+#define X(LL)                                                                          \
+        if (L == LL)                                                                   \
+            return gauss ? launch_t<LL, true, false>(a, cfg, st) : launch_t<LL, false, false>(a, cfg, st);
+        SG_FOR_EACH_L(X)
+#undef X
+    }
     return cudaErrorInvalidValue;
 }
 
-int int8_ctas_per_sm(int L, bool gauss, int threads, size_t smem)
+int int8_ctas_per_sm(int L, bool gauss, int threads, size_t smem, bool gst)
 {
+    if (gst) {
 #define X(LL) \
-    if (L == LL) return gauss ? occ_t<LL, true>(threads, smem) : occ_t<LL, false>(threads, smem);
-    SG_FOR_EACH_L(X)
+        if (L == LL) return gauss ? occ_t<LL, true, true>(threads, smem) : occ_t<LL, false, true>(threads, smem);
+        SG_FOR_EACH_GST_L(X)
 #undef X
+    } else {
+#define X(LL) \
+        if (L == LL) return gauss ? occ_t<LL, true, false>(threads, smem) : occ_t<LL, false, false>(threads, smem);
+        SG_FOR_EACH_L(X)
+#undef X
+    }
     return 0;
 }
 

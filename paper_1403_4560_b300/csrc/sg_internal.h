@@ -43,16 +43,18 @@ struct Int8Args {
 struct Int8Launch {
     int threads, grid;
     size_t smem;
+    bool gst;  // state kept in global memory (large L) instead of shared memory
 };
 
-// Shared-memory bytes of the fused kernel, or 0 when the state does not fit.
-size_t int8_smem_bytes(int L, int Tp, bool gauss, int mchunk);
+// Shared-memory bytes of the fused kernel, or 0 when the state does not fit
+// (or no kernel is built for that L and mode).
+size_t int8_smem_bytes(int L, int Tp, bool gauss, int mchunk, bool gst);
 int int8_max_threads();
 // Configure and launch the fused kernel.
 cudaError_t int8_launch(int L, bool gauss, const Int8Args &a, const Int8Launch &cfg,
                         cudaStream_t st);
 // Occupancy of the fused kernel (CTAs per SM), 0 if it cannot launch.
-int int8_ctas_per_sm(int L, bool gauss, int threads, size_t smem);
+int int8_ctas_per_sm(int L, bool gauss, int threads, size_t smem, bool gst);
 
 // Instance preparation and state conversion kernels.
 cudaError_t int8_gen_pmj(uint8_t *J8, int64_t S, int L, uint32_t seed_lo, uint32_t seed_hi,

@@ -80,12 +80,15 @@ def test_plain_pmj_config_is_bit_exact():
     (6, 6, "pmj", 1, 1, 2), (6, 4, "gauss", 3, 1, 1), (8, 7, "pmj", 2, 3, 1),
     (8, 9, "gauss", 1, 1, 1), (10, 6, "gauss", 1, 1, 1), (10, 4, "pmj", 0, 1, 1),
     (12, 5, "pmj", 1, 1, 4), (12, 8, "gauss", 1, 1, 1), (14, 4, "pmj", 1, 1, 1),
-    (16, 4, "gauss", 1, 2, 1), (4, 1, "pmj", 1, 1, 1)])
+    (16, 4, "gauss", 1, 2, 1), (4, 1, "pmj", 1, 1, 1),
+    # state kept in global memory: large L, or too many slots for shared memory
+    (18, 3, "pmj", 1, 1, 1), (20, 2, "gauss", 1, 1, 1), (22, 2, "pmj", 1, 1, 1),
+    (24, 2, "gauss", 1, 1, 1), (12, 64, "gauss", 1, 1, 1)])
 def test_int8_paths_are_bit_exact(L, nt, dist, ee, me, rg):
     S, seed, h = 4, 1234 + L, 0.25
     T = inputs.geometric_ladder(0.5, 1.6, nt)
     J, s0 = inputs.make_instance(dist, L, S, nt, seed=L * 100 + nt)
-    sweeps = 60 if L >= 12 else 150
+    sweeps = 12 if (L >= 18 or nt > 32) else 60 if L >= 12 else 150
     opt = dict(exchange_every=ee, measure_every=me, n_therm=sweeps // 3, rng_group=rg)
     with sgmc.Ensemble(L, h, T, dist, S, seed, J=J, spins=s0, **opt) as ens:
         ens.sweep(sweeps)
