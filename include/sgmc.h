@@ -271,6 +271,72 @@ sg_status sg_threshold_map(const float *x, int n, uint32_t *out);
 const char *sg_status_str(sg_status s);
 const char *sg_last_error(void);
 
+
+/* ------------------------------------------------------------------------
+ * Serving: a request loop with continuous batching on one GPU.
+ * The paper has no serving layer; this is the engine's way of running many
+ * independent simulation requests (each a full run of the method above)
+ * that arrive over time. A worker thread admits queued requests while their
+ * ensembles fit the device-memory budget, keeps admitted ensembles resident
+ * (lattices, couplings, accumulators, sweep counters), advances all of them
+ * together in batching rounds (sg_sweep_batch) and releases finished ones.
+ * A result does not depend on what else ran beside it.
+ * ------------------------------------------------------------------------ */
+typedef struct sg_server sg_server;
+
+typedef struct {
+    size_t memory_budget;  /* device bytes for resident ensembles; 0 = 80% of
+                              the free memory when the server starts        */
+    int32_t max_active;    /* cap on resident ensembles; 0 = budget only    */
+    int64_t chunk_sweeps;  /* sweeps per batching round (default 256)       */
+    int32_t use_graph;     /* run rounds through cached CUDA graphs         */
+} sg_server_options;
+
+typedef struct {
+    int32_t L;              /* as sg_create_ensemble                        */
+    double h;
+    const double *T;        /* copied at submission                         */
+    int32_t n_T;
+    int32_t dist;           /* sg_coupling                                  */
+    int64_t n_samples;
+    uint64_t seed;
+    int64_t n_sweeps;       /* total sweeps of the run                      */
+    int64_t n_therm;        /* -1: first half thermalises (Table I caption) */
+    int32_t layout;         /* -1: MSC64 for +-J with n_samples % 64 == 0
+                               and L <= 16, else INT8                       */
+    int32_t exchange_every; /* <= 0: every sweep                            */
+    int32_t measure_every;  /* <= 0: every sweep                            */
+} sg_request;
+
+typedef struct {
+    int64_t completed, queued, active, rounds;
+    double attempts;        /* spin-flip attempts done by all rounds        */
+    double busy_seconds;    /* wall time spent in rounds                    */
+    size_t device_bytes_in_use;
+    double latency_p50, latency_p99; /* submit-to-result seconds, completed */
+} sg_server_stats;
+
+void sg_server_options_default(sg_server_options *opt);
+void sg_request_default(sg_request *req);
+/* Start a server on the current device; all its work runs on `stream`. */
+sg_status sg_server_create(const sg_server_options *opt, void *stream, sg_server **out);
+/* Queue a request (thread-safe, returns at once); *id receives its handle. */
+sg_status sg_server_submit(sg_server *sv, const sg_request *req, int64_t *id);
+/* Wait until request id has finished (done, failed or cancelled); a
+ * negative timeout waits forever; SG_ETIMEOUT if it has not finished.
+ * *state (may be NULL): 0 queued, 1 running, 2 done, 3 failed, 4 cancelled. */
+sg_status sg_server_wait(sg_server *sv, int64_t id, double timeout_s, int *state);
+/* Accumulators ([n_samples][n_T][40]) and latency of a finished request;
+ * SG_EBUSY while it runs, its error code if it failed, SG_ECANCELLED. */
+sg_status sg_server_result(sg_server *sv, int64_t id, double *acc_out, double *latency_s);
+/* Ask to drop a request; it leaves at the next round boundary. */
+sg_status sg_server_cancel(sg_server *sv, int64_t id);
+/* Forget a finished request and its stored result. */
+sg_status sg_server_release(sg_server *sv, int64_t id);
+sg_status sg_server_get_stats(sg_server *sv, sg_server_stats *out);
+/* Stop the worker (running requests are cancelled) and free everything. */
+void sg_server_destroy(sg_server *sv);
+
 #ifdef __cplusplus
 }
 #endif

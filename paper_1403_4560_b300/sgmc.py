@@ -41,6 +41,28 @@ class Info(ctypes.Structure):
                 ("attempts_per_sweep", ctypes.c_int64), ("device_bytes", ctypes.c_size_t)]
 
 
+class ServerOptions(ctypes.Structure):
+    _fields_ = [("memory_budget", ctypes.c_size_t), ("max_active", ctypes.c_int32),
+                ("chunk_sweeps", ctypes.c_int64), ("use_graph", ctypes.c_int32)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int32), ("h", ctypes.c_double),
+                ("T", ctypes.POINTER(ctypes.c_double)), ("n_T", ctypes.c_int32),
+                ("dist", ctypes.c_int32), ("n_samples", ctypes.c_int64),
+                ("seed", ctypes.c_uint64), ("n_sweeps", ctypes.c_int64),
+                ("n_therm", ctypes.c_int64), ("layout", ctypes.c_int32),
+                ("exchange_every", ctypes.c_int32), ("measure_every", ctypes.c_int32)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_int64), ("queued", ctypes.c_int64),
+                ("active", ctypes.c_int64), ("rounds", ctypes.c_int64),
+                ("attempts", ctypes.c_double), ("busy_seconds", ctypes.c_double),
+                ("device_bytes_in_use", ctypes.c_size_t), ("latency_p50", ctypes.c_double),
+                ("latency_p99", ctypes.c_double)]
+
+
 _OBS_FIELDS = ["g", "chi0", "chi1", "chi2", "xi", "r12", "e", "q2", "q4"]
 
 
@@ -87,6 +109,16 @@ def lib() -> ctypes.CDLL:
         "sg_results": (st, [P, P]),
         "sg_observables_from_acc": (st, [P, i64, i32, i32, P]),
         "sg_threshold_map": (st, [P, i32, P]),
+        "sg_server_options_default": (None, [P]),
+        "sg_request_default": (None, [P]),
+        "sg_server_create": (st, [P, P, P]),
+        "sg_server_submit": (st, [P, P, P]),
+        "sg_server_wait": (st, [P, i64, f64, P]),
+        "sg_server_result": (st, [P, i64, P, P]),
+        "sg_server_cancel": (st, [P, i64]),
+        "sg_server_release": (st, [P, i64]),
+        "sg_server_get_stats": (st, [P, P]),
+        "sg_server_destroy": (None, [P]),
         "sg_status_str": (ctypes.c_char_p, [i32]),
         "sg_last_error": (ctypes.c_char_p, []),
     }
@@ -284,3 +316,76 @@ def threshold_map(x) -> np.ndarray:
 def sweep_batch(ensembles, n: int, use_graph: bool = True):
     arr = (ctypes.c_void_p * len(ensembles))(*[e.handle.value for e in ensembles])
     _check(lib().sg_sweep_batch(arr, len(ensembles), int(n), int(bool(use_graph))))
+
+
+class Server:
+    """Request loop with continuous batching (sg_server_*)."""
+
+    def __init__(self, memory_budget: int = 0, max_active: int = 0, chunk_sweeps: int = 256,
+                 use_graph: bool = False, stream=None):
+        o = ServerOptions()
+        lib().sg_server_options_default(ctypes.byref(o))
+        o.memory_budget, o.max_active = int(memory_budget), int(max_active)
+        o.chunk_sweeps, o.use_graph = int(chunk_sweeps), int(bool(use_graph))
+        h = ctypes.c_void_p()
+        _check(lib().sg_server_create(ctypes.byref(o), ctypes.c_void_p(_stream_handle(stream)),
+                                      ctypes.byref(h)))
+        self._h = h
+        self._meta = {}
+
+    def submit(self, L, h, T, dist="pmj", n_samples=64, seed=1, n_sweeps=256, n_therm=-1,
+               layout=-1, exchange_every=1, measure_every=1) -> int:
+        r = Request()
+        lib().sg_request_default(ctypes.byref(r))
+        T = np.ascontiguousarray(T, dtype=np.float64)
+        r.L, r.h, r.n_T = int(L), float(h), len(T)
+        r.T = T.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        r.dist = SG_GAUSS if dist in ("gauss", SG_GAUSS) else SG_PM_J
+        r.n_samples, r.seed, r.n_sweeps = int(n_samples), int(seed), int(n_sweeps)
+        r.n_therm, r.layout = int(n_therm), int(layout)
+        r.exchange_every, r.measure_every = int(exchange_every), int(measure_every)
+        rid = ctypes.c_int64()
+        _check(lib().sg_server_submit(self._h, ctypes.byref(r), ctypes.byref(rid)))
+        self._meta[rid.value] = (int(n_samples), len(T))
+        return rid.value
+
+    def wait(self, rid: int, timeout: float = -1.0) -> int:
+        state = ctypes.c_int()
+        _check(lib().sg_server_wait(self._h, int(rid), float(timeout), ctypes.byref(state)))
+        return state.value
+
+    def result(self, rid: int):
+        S, nt = self._meta[rid]
+        acc = np.zeros((S, nt, NACC), dtype=np.float64)
+        lat = ctypes.c_double()
+        _check(lib().sg_server_result(self._h, int(rid), _ptr(acc), ctypes.byref(lat)))
+        return acc, lat.value
+
+    def cancel(self, rid: int):
+        _check(lib().sg_server_cancel(self._h, int(rid)))
+
+    def release(self, rid: int):
+        _check(lib().sg_server_release(self._h, int(rid)))
+        self._meta.pop(rid, None)
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(lib().sg_server_get_stats(self._h, ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in ServerStats._fields_}
+
+    def close(self):
+        if self._h is not None and _lib is not None:
+            _lib.sg_server_destroy(self._h)
+        self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
