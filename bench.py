@@ -57,6 +57,8 @@ def parse_args():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the secondary workloads (uneven batch, MSC, serving)")
     return ap.parse_args()
 
 
@@ -151,16 +153,17 @@ def cpu_baseline(budget_s: float):
     T = inputs.geometric_ladder(T_MIN, T_MAX, N_T)
     J, s0 = inputs.make_instance("gauss", L, cores, N_T, seed=99)
     st = orc.State(L, T, 0.2, True, seed=99, J=J, spins=s0, n_therm=0)
+    st.run(1, threads=cores)  # warm-up (library load, thread start)
     t0 = time.perf_counter()
     st.run(1, threads=cores)
     t1 = time.perf_counter() - t0
     n = max(1, min(500, int(budget_s / max(t1, 1e-3)) - 1))
     t0 = time.perf_counter()
     st.run(n, threads=cores)
-    dt = time.perf_counter() - t0
-    att = L ** 3 * 2 * N_T * cores * n
+    dt = time.perf_counter() - t0 + t1
+    att = L ** 3 * 2 * N_T * cores * (n + 1)
     return {"value": att / (dt * 1e9), "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"L=12 gaussian, 2x24 T, h=0.2, {cores} samples x {n} sweeps "
+            "sample": f"L=12 gaussian, 2x24 T, h=0.2, {cores} samples x {n + 1} sweeps "
                       f"(exchange+measure every sweep), {dt:.1f} s"}
 
 
@@ -195,6 +198,111 @@ def run_reference(args, rank):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+CFG4 = [(6, 2048), (8, 1024), (10, 1024), (12, 512), (16, 256)]
+
+
+def extra_uneven_batch(sgmc, inputs, stream, torch):
+    """Uneven-L Gaussian ensemble (L = 6..16 with 2048..256 samples, h = 0.2,
+    2 x 20 T in 0.5-1.5): autotuned, batched through one CUDA graph per step,
+    against plain per-sweep launches of the ensembles one after another."""
+    T = inputs.geometric_ladder(0.5, 1.5, 20)
+    insts = [inputs.make_instance("gauss", L, S, 20, seed=40 + L) for L, S in CFG4]
+    att_sweep = sum(L ** 3 * 40 * S for L, S in CFG4)
+    ens = [sgmc.Ensemble(L, 0.2, T, "gauss", S, 40 + L, J=J, spins=s0, stream=stream, n_therm=0)
+           for (L, S), (J, s0) in zip(CFG4, insts)]
+    tune = {f"L{e.L}": e.autotune(trial_sweeps=4)["threads_per_block"] for e in ens}
+    n = 64
+    sgmc.sweep_batch(ens, n, use_graph=True)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record(stream)
+    for _ in range(2):
+        sgmc.sweep_batch(ens, n, use_graph=True)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    batched = att_sweep * 2 * n / (ev[0].elapsed_time(ev[1]) * 1e6)
+    for e in ens:
+        e.close()
+    pens = [sgmc.Ensemble(L, 0.2, T, "gauss", S, 40 + L, J=J, spins=s0, stream=stream,
+                          n_therm=0, sweeps_per_launch=1)
+            for (L, S), (J, s0) in zip(CFG4, insts)]
+    for e in pens:
+        e.sweep(1)
+    torch.cuda.synchronize()
+    npl = 16
+    ev[0].record(stream)
+    for e in pens:
+        e.sweep(npl)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    plain = att_sweep * npl / (ev[0].elapsed_time(ev[1]) * 1e6)
+    for e in pens:
+        e.close()
+    return {"batched": batched, "plain": plain, "unit": UNIT, "tuned_threads": tune,
+            "workload": "gaussian, L=6,8,10,12,16 x 2048,1024,1024,512,256 samples, h=0.2, "
+                        "2x20 T 0.5-1.5, exchange+measure every sweep"}
+
+
+def extra_msc(sgmc, stream, torch):
+    """+-J multispin-coded path: L = 16, 4096 samples (64 words), h = 0.1,
+    2 x 32 T in 0.4-1.5; one launch per sweep (graph-captured batch)."""
+    from paper_1403_4560_b300 import inputs
+    T = inputs.geometric_ladder(0.4, 1.5, 32)
+    out = {}
+    for name, n_therm in (("measuring", 0), ("thermalising", 10 ** 9)):
+        with sgmc.Ensemble(16, 0.1, T, "pmj", 4096, 5, stream=stream, n_therm=n_therm,
+                           layout=sgmc.SG_LAYOUT_MSC64) as e:
+            sgmc.sweep_batch([e], 4, use_graph=True)
+            torch.cuda.synchronize()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            ev[0].record(stream)
+            for _ in range(4):
+                sgmc.sweep_batch([e], 4, use_graph=True)
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            out[name] = e.info().attempts_per_sweep * 16 / (ev[0].elapsed_time(ev[1]) * 1e6)
+    out["unit"] = UNIT
+    return out
+
+
+def extra_serving(sgmc, stream, n_req=24, rate=50.0, sweeps=256):
+    """A finite Poisson stream (mean 50 requests/s, seed 1) of requests drawn
+    uniformly from L in {8,12,16,20,24}, h in {0.05,...,0.40}, 16-32
+    temperatures geometric in 0.5-1.6, 64-1024 samples (multiples of 64),
+    +-J or Gaussian couplings; each request runs `sweeps` sweeps (truncated
+    from the full 2^14 so the stream ends within seconds)."""
+    from paper_1403_4560_b300 import inputs
+    rng = np.random.default_rng(1)
+    reqs = []
+    t = 0.0
+    for _ in range(n_req):
+        t += rng.exponential(1.0 / rate)
+        reqs.append(dict(at=t, L=int(rng.choice([8, 12, 16, 20, 24])),
+                         h=float(rng.choice(np.arange(1, 9) * 0.05)),
+                         nt=int(rng.integers(16, 33)), S=int(64 * rng.integers(1, 17)),
+                         dist=str(rng.choice(["pmj", "gauss"]))))
+    att_total = sum(r["L"] ** 3 * 2 * r["nt"] * r["S"] * sweeps for r in reqs)
+    with sgmc.Server(chunk_sweeps=64, stream=stream) as sv:
+        t0 = time.perf_counter()
+        ids = []
+        for k, r in enumerate(reqs):
+            delay = r["at"] - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            ids.append(sv.submit(r["L"], r["h"], inputs.geometric_ladder(0.5, 1.6, r["nt"]),
+                                 r["dist"], r["S"], seed=1000 + k, n_sweeps=sweeps))
+        for rid in ids:
+            sv.wait(rid)
+        wall = time.perf_counter() - t0
+        lat = [sv.result(rid)[1] for rid in ids]
+        st = sv.stats()
+    return {"requests": n_req, "rate_per_s": rate, "sweeps_per_request": sweeps,
+            "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "attempts_per_ns_wall": att_total / (wall * 1e9),
+            "attempts_per_ns_busy": st["attempts"] / (st["busy_seconds"] * 1e9),
+            "unit": UNIT}
 
 
 def main():
@@ -325,6 +433,12 @@ def main():
                "how": "per step: sg_set_spins from pinned host spins for all 6 ensembles, "
                       "batched sweeps, sg_get_accumulators to host"}
 
+    extras = None
+    if rank == 0 and not args.no_extras:
+        extras = {"uneven_batch": extra_uneven_batch(sgmc, inputs, stream, torch),
+                  "msc_L16": extra_msc(sgmc, stream, torch),
+                  "serving": extra_serving(sgmc, stream)}
+
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cb = cpu_baseline(args.cpu_seconds)
@@ -340,7 +454,7 @@ def main():
                            "batched": "one CUDA graph per step, 6 parallel branches"},
                 "gpu_launches": n_launch_per_step * K,
                 "roofline": roofline, "plain": plain, "e2e": e2e, "cpu_baseline": cb,
-                "clocks": clk.summary()}
+                "clocks": clk.summary(), "extras": extras}
         print(json.dumps(line), flush=True)
     for e in ens:
         e.close()

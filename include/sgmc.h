@@ -220,6 +220,23 @@ sg_status sg_set_sweeps_done(sg_ensemble *e, int64_t n);
 /* Replace the accumulators from a host array (checkpoint restore). */
 sg_status sg_set_accumulators(sg_ensemble *e, const double *acc_host);
 
+/*
+ * Autotuner (the paper has no counterpart; it picks launch shapes for this
+ * GPU). Times up to 13 candidate launch shapes of the int8 kernel (threads
+ * per CTA, measurement chunk) for trial_sweeps sweeps each on the ensemble's
+ * own data, restores the state afterwards (spins, energies, accumulators and
+ * sweep counter are as before the call, so results do not change), keeps the
+ * fastest shape for this ensemble and caches it per (L, slots, distribution,
+ * memory mode) for ensembles created later in the process. Synchronises the
+ * stream; allocates a device copy of the state while it runs. The
+ * multispin-coded layout has one fixed shape (reported, nothing timed).
+ */
+typedef struct {
+    int32_t threads_per_block, mchunk, n_candidates;
+    double best_ms_per_sweep, default_ms_per_sweep;
+} sg_tune_report;
+sg_status sg_autotune(sg_ensemble *e, int64_t trial_sweeps, sg_tune_report *report);
+
 /* Wait for the ensemble's stream and report the first device-side error. */
 sg_status sg_synchronize(sg_ensemble *e);
 

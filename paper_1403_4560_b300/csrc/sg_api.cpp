@@ -129,6 +129,16 @@ ArenaPlan plan_arena(int L, int nt, int Tp, int64_t S, bool gauss, bool msc)
 
 int pad_slots(int nt) { return (nt + 3) & ~3; }
 
+// Autotuned launch shapes per problem shape (L, slots, distribution, mode).
+std::mutex g_tune_mu;
+std::map<std::string, std::pair<int, int>> g_tuned;  // -> (threads, mchunk)
+
+std::string tune_key(const sg_ensemble *e, bool gst)
+{
+    return std::to_string(e->L) + ":" + std::to_string(e->Tp) + ":" + (e->gauss ? "g" : "j") +
+           (gst ? ":gst" : ":smem");
+}
+
 // Launch shape: threads per CTA are a multiple of WR = Tp/4 (each thread
 // keeps one 4-slot group for the whole half-sweep); among the candidates the
 // one with the best product of work balance and resident warps per SM wins,
@@ -176,6 +186,19 @@ sg_status configure_launch(sg_ensemble *e)
             }
         }
         if (best_occ == 0) continue;
+        if (e->opt.threads_per_block <= 0) {  // a tuned shape for this problem wins
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            auto it = g_tuned.find(tune_key(e, gst));
+            if (it != g_tuned.end()) {
+                const size_t smem = int8_smem_bytes(L, e->Tp, e->gauss, it->second.second, gst);
+                const int occ = smem ? int8_ctas_per_sm(L, e->gauss, it->second.first, smem, gst) : 0;
+                if (occ > 0) {
+                    best_t = it->second.first;
+                    best_m = it->second.second;
+                    best_occ = occ;
+                }
+            }
+        }
         e->mchunk = best_m;
         e->launch.threads = best_t;
         e->launch.gst = gst;
@@ -826,6 +849,125 @@ sg_status sg_threshold_map(const float *x, int n, uint32_t *out)
     cudaFree(xd);
     cudaFree(od);
     if (ce != cudaSuccess) return cuda_fail(ce, "threshold map");
+    return SG_OK;
+}
+
+sg_status sg_autotune(sg_ensemble *e, int64_t trial_sweeps, sg_tune_report *rep)
+{
+    if (!e || trial_sweeps < 1) return fail(SG_EINVAL, "bad autotune arguments");
+    sg_tune_report r{};
+    if (e->msc) {  // one fixed shape (a CTA per exchange unit, 512 threads)
+        r.threads_per_block = 512;
+        r.n_candidates = 1;
+        if (rep) *rep = r;
+        return SG_OK;
+    }
+    const size_t N = (size_t)e->L * e->L * e->L;
+    const size_t sp_bytes = (size_t)e->S * N * 2 * e->Tp;
+    const size_t bm_bytes = (size_t)e->S * 2 * e->Tp * sizeof(int64_t);
+    const size_t acc_bytes = (size_t)e->S * e->nt * SG_NACC * sizeof(double);
+    uint8_t *backup = nullptr;
+    SG_CUDA(cudaMalloc(&backup, sp_bytes + 2 * bm_bytes + acc_bytes), "autotune backup");
+    auto save = [&](bool restore) {
+        const cudaMemcpyKind k = cudaMemcpyDeviceToDevice;
+        uint8_t *b = backup;
+        cudaError_t ce = restore ? cudaMemcpyAsync(e->spins, b, sp_bytes, k, e->stream)
+                                 : cudaMemcpyAsync(b, e->spins, sp_bytes, k, e->stream);
+        b += sp_bytes;
+        if (ce == cudaSuccess)
+            ce = restore ? cudaMemcpyAsync(e->B, b, bm_bytes, k, e->stream)
+                         : cudaMemcpyAsync(b, e->B, bm_bytes, k, e->stream);
+        b += bm_bytes;
+        if (ce == cudaSuccess)
+            ce = restore ? cudaMemcpyAsync(e->M, b, bm_bytes, k, e->stream)
+                         : cudaMemcpyAsync(b, e->M, bm_bytes, k, e->stream);
+        b += bm_bytes;
+        if (ce == cudaSuccess)
+            ce = restore ? cudaMemcpyAsync(e->acc, b, acc_bytes, k, e->stream)
+                         : cudaMemcpyAsync(b, e->acc, acc_bytes, k, e->stream);
+        return ce;
+    };
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const Int8Launch orig_launch = e->launch;
+    const int orig_m = e->mchunk;
+    const sg_options orig_opt = e->opt;
+    e->opt.sweeps_per_launch = 0;
+    const int WR = e->Tp / 4;
+    double best_ms = 1e300, default_ms = 0.0;
+    int best_t = orig_launch.threads, best_m = orig_m, ncand = 0;
+    cudaError_t ce = save(false);
+    std::vector<std::pair<int, int>> cands;
+    cands.push_back({orig_launch.threads, orig_m});
+    for (int t = ((32 + WR - 1) / WR) * WR; t <= int8_max_threads(); t += WR) {
+        int best_occ = 0, m_for = 0;
+        for (int m = WR; m >= 1; --m) {
+            const size_t smem = int8_smem_bytes(e->L, e->Tp, e->gauss, m, orig_launch.gst);
+            const int o = smem ? int8_ctas_per_sm(e->L, e->gauss, t, smem, orig_launch.gst) : 0;
+            if (o > best_occ) {
+                best_occ = o;
+                m_for = m;
+            }
+        }
+        if (best_occ > 0 && !(t == orig_launch.threads && m_for == orig_m)) cands.push_back({t, m_for});
+    }
+    // at most 12 shapes besides the default: spread over the range
+    if (cands.size() > 13) {
+        std::vector<std::pair<int, int>> pick{cands[0]};
+        for (int k = 1; k <= 12; ++k) pick.push_back(cands[1 + (k - 1) * (cands.size() - 2) / 11]);
+        cands = pick;
+    }
+    for (size_t c = 0; c < cands.size() && ce == cudaSuccess; ++c) {
+        e->launch.threads = cands[c].first;
+        e->mchunk = cands[c].second;
+        e->launch.smem = int8_smem_bytes(e->L, e->Tp, e->gauss, e->mchunk, orig_launch.gst);
+        const int occ = int8_ctas_per_sm(e->L, e->gauss, e->launch.threads, e->launch.smem,
+                                         orig_launch.gst);
+        e->launch.grid = (int)std::min<int64_t>(e->S, (int64_t)occ * e->num_sms);
+        if (launch_sweeps(e, 1, e->stream, false) != SG_OK) break;  // warm-up
+        cudaEventRecord(e0, e->stream);
+        if (launch_sweeps(e, trial_sweeps, e->stream, false) != SG_OK) break;
+        cudaEventRecord(e1, e->stream);
+        ce = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double per = ms / (double)trial_sweeps;
+        if (c == 0) default_ms = per;
+        if (per < best_ms) {
+            best_ms = per;
+            best_t = cands[c].first;
+            best_m = cands[c].second;
+        }
+        ++ncand;
+        if (ce == cudaSuccess) ce = save(true);
+    }
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(e->stream);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(backup);
+    e->opt = orig_opt;
+    if (ce != cudaSuccess) {
+        e->launch = orig_launch;
+        e->mchunk = orig_m;
+        return cuda_fail(ce, "autotune");
+    }
+    e->launch = orig_launch;
+    e->launch.threads = best_t;
+    e->mchunk = best_m;
+    e->launch.smem = int8_smem_bytes(e->L, e->Tp, e->gauss, best_m, orig_launch.gst);
+    const int occ = int8_ctas_per_sm(e->L, e->gauss, best_t, e->launch.smem, orig_launch.gst);
+    e->launch.grid = (int)std::min<int64_t>(e->S, (int64_t)occ * e->num_sms);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tuned[tune_key(e, orig_launch.gst)] = {best_t, best_m};
+    }
+    r.threads_per_block = best_t;
+    r.mchunk = best_m;
+    r.n_candidates = ncand;
+    r.best_ms_per_sweep = best_ms;
+    r.default_ms_per_sweep = default_ms;
+    if (rep) *rep = r;
     return SG_OK;
 }
 

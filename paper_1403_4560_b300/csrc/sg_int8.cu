@@ -480,14 +480,22 @@ __device__ __forceinline__ void measure_step(const Smem &sm, const Ctx &cx, cons
         __syncthreads();
         // (B) one thread per (slot, v): the L projections P_v[d] from L*L
         // independent loads, then the FP32 DFT in ascending d and the FP64
-        // accumulation; v == 9 handles Q, E and M
+        // accumulation; v == 9 handles Q, E and M. The task's accumulators are
+        // loaded first so that their global-memory latency overlaps the counting.
+        // the slot varies fastest across lanes: one wave vector (one code path)
+        // per warp, adjacent marginal words per lane
         for (int id = threadIdx.x; id < 4 * nw * 10; id += blockDim.x) {
-            const int v = id % 10;
-            const int sl = id / 10;  // 4*jj + kk
+            const int sl = id % (4 * nw);  // 4*jj + kk
+            const int v = id / (4 * nw);
             const int t = 4 * j0 + sl;
             if (t >= nt) continue;
             const int jj = sl >> 2, sh = 8 * (sl & 3);
             double *ac = accs + (size_t)t * SG_NACC;
+            double *acv = ac + (v == 9 ? 0 : 9 + 3 * v);
+            const int nacc = v == 9 ? 9 : 3;
+            double old[9];
+#pragma unroll
+            for (int q = 0; q < 9; ++q) old[q] = q < nacc ? acv[q] : 0.0;
             int cs[L];
             if (v == 9 || v == 0)
                 count_pattern<L, 0>(sm.marg + jj, nw, sh, cs);
@@ -509,38 +517,40 @@ __device__ __forceinline__ void measure_step(const Smem &sm, const Ctx &cx, cons
                 for (int d = 0; d < L; ++d) Qi += LL - 2 * cs[d];
                 const double Q = (double)Qi;
                 const double Q2 = __dmul_rn(Q, Q);
-                ac[0] = __dadd_rn(ac[0], 1.0);
-                ac[1] = __dadd_rn(ac[1], Q);
-                ac[2] = __dadd_rn(ac[2], Q2);
-                ac[3] = __dadd_rn(ac[3], __dmul_rn(Q2, Q));
-                ac[4] = __dadd_rn(ac[4], __dmul_rn(Q2, Q2));
+                old[0] = __dadd_rn(old[0], 1.0);
+                old[1] = __dadd_rn(old[1], Q);
+                old[2] = __dadd_rn(old[2], Q2);
+                old[3] = __dadd_rn(old[3], __dmul_rn(Q2, Q));
+                old[4] = __dadd_rn(old[4], __dmul_rn(Q2, Q2));
                 for (int r = 0; r < 2; ++r) {
                     const long long Bv = (long long)sm.B[r * Tp + t];
                     const long long Mv = (long long)sm.M[r * Tp + t];
                     const double e = -__dadd_rn(__dmul_rn((double)Bv, a.qJ_d),
                                                 __dmul_rn(a.h_d, (double)Mv));
-                    ac[5] = __dadd_rn(ac[5], e);
-                    ac[6] = __dadd_rn(ac[6], __dmul_rn(e, e));
+                    old[5] = __dadd_rn(old[5], e);
+                    old[6] = __dadd_rn(old[6], __dmul_rn(e, e));
                 }
                 for (int r = 0; r < 2; ++r) {
                     const double m = (double)(long long)sm.M[r * Tp + t];
-                    ac[7] = __dadd_rn(ac[7], m);
-                    ac[8] = __dadd_rn(ac[8], __dmul_rn(m, m));
+                    old[7] = __dadd_rn(old[7], m);
+                    old[8] = __dadd_rn(old[8], __dmul_rn(m, m));
                 }
-                continue;
-            }
-            float re = 0.0f, im = 0.0f;
+            } else {
+                float re = 0.0f, im = 0.0f;
 #pragma unroll
-            for (int d = 0; d < L; ++d) {
-                const float Pf = (float)(LL - 2 * cs[d]);
-                re = __fmaf_rn(Pf, sm.twid[d], re);
-                im = __fmaf_rn(Pf, sm.twid[L + d], im);
+                for (int d = 0; d < L; ++d) {
+                    const float Pf = (float)(LL - 2 * cs[d]);
+                    re = __fmaf_rn(Pf, sm.twid[d], re);
+                    im = __fmaf_rn(Pf, sm.twid[L + d], im);
+                }
+                const double dr = (double)re, di = (double)im;
+                old[0] = __dadd_rn(old[0], dr);
+                old[1] = __dadd_rn(old[1], di);
+                old[2] = __dadd_rn(old[2], __dadd_rn(__dmul_rn(dr, dr), __dmul_rn(di, di)));
             }
-            const double dr = (double)re, di = (double)im;
-            ac[9 + 3 * v] = __dadd_rn(ac[9 + 3 * v], dr);
-            ac[10 + 3 * v] = __dadd_rn(ac[10 + 3 * v], di);
-            ac[11 + 3 * v] =
-                __dadd_rn(ac[11 + 3 * v], __dadd_rn(__dmul_rn(dr, dr), __dmul_rn(di, di)));
+#pragma unroll
+            for (int q = 0; q < 9; ++q)
+                if (q < nacc) acv[q] = old[q];
         }
         __syncthreads();
     }

@@ -316,6 +316,12 @@ __device__ __forceinline__ void msc_measure(const MscSmem &sm, const MscArgs &a,
         const int b = id % 64, v = id / 64;
         const int64_t s = 64 * (int64_t)g + b;
         double *ac = a.acc + ((size_t)s * a.nt + t) * SG_NACC;
+        // the task's accumulators first: their latency overlaps the extraction
+        double *acv = ac + (v == 9 ? 0 : 9 + 3 * v);
+        const int nacc = v == 9 ? 9 : 3;
+        double old[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) old[q] = q < nacc ? acv[q] : 0.0;
         const int vv = v == 9 ? 0 : v;
         float re = 0.0f, im = 0.0f;
         int Qi = 0;
@@ -332,30 +338,32 @@ __device__ __forceinline__ void msc_measure(const MscSmem &sm, const MscArgs &a,
         if (v == 9) {
             const double Q = (double)Qi;
             const double Q2 = __dmul_rn(Q, Q);
-            ac[0] = __dadd_rn(ac[0], 1.0);
-            ac[1] = __dadd_rn(ac[1], Q);
-            ac[2] = __dadd_rn(ac[2], Q2);
-            ac[3] = __dadd_rn(ac[3], __dmul_rn(Q2, Q));
-            ac[4] = __dadd_rn(ac[4], __dmul_rn(Q2, Q2));
+            old[0] = __dadd_rn(old[0], 1.0);
+            old[1] = __dadd_rn(old[1], Q);
+            old[2] = __dadd_rn(old[2], Q2);
+            old[3] = __dadd_rn(old[3], __dmul_rn(Q2, Q));
+            old[4] = __dadd_rn(old[4], __dmul_rn(Q2, Q2));
             for (int r = 0; r < 2; ++r) {
                 const long long Bv = sm.B[(2 * k + r) * 64 + b];
                 const long long Mv = sm.M[(2 * k + r) * 64 + b];
                 const double e = -__dadd_rn((double)Bv, __dmul_rn(a.h_d, (double)Mv));
-                ac[5] = __dadd_rn(ac[5], e);
-                ac[6] = __dadd_rn(ac[6], __dmul_rn(e, e));
+                old[5] = __dadd_rn(old[5], e);
+                old[6] = __dadd_rn(old[6], __dmul_rn(e, e));
             }
             for (int r = 0; r < 2; ++r) {
                 const double m = (double)sm.M[(2 * k + r) * 64 + b];
-                ac[7] = __dadd_rn(ac[7], m);
-                ac[8] = __dadd_rn(ac[8], __dmul_rn(m, m));
+                old[7] = __dadd_rn(old[7], m);
+                old[8] = __dadd_rn(old[8], __dmul_rn(m, m));
             }
         } else {
             const double dr = (double)re, di = (double)im;
-            ac[9 + 3 * v] = __dadd_rn(ac[9 + 3 * v], dr);
-            ac[10 + 3 * v] = __dadd_rn(ac[10 + 3 * v], di);
-            ac[11 + 3 * v] =
-                __dadd_rn(ac[11 + 3 * v], __dadd_rn(__dmul_rn(dr, dr), __dmul_rn(di, di)));
+            old[0] = __dadd_rn(old[0], dr);
+            old[1] = __dadd_rn(old[1], di);
+            old[2] = __dadd_rn(old[2], __dadd_rn(__dmul_rn(dr, dr), __dmul_rn(di, di)));
         }
+#pragma unroll
+        for (int q = 0; q < 9; ++q)
+            if (q < nacc) acv[q] = old[q];
     }
     __syncthreads();
 }

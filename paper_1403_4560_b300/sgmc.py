@@ -41,6 +41,12 @@ class Info(ctypes.Structure):
                 ("attempts_per_sweep", ctypes.c_int64), ("device_bytes", ctypes.c_size_t)]
 
 
+class TuneReport(ctypes.Structure):
+    _fields_ = [("threads_per_block", ctypes.c_int32), ("mchunk", ctypes.c_int32),
+                ("n_candidates", ctypes.c_int32), ("best_ms_per_sweep", ctypes.c_double),
+                ("default_ms_per_sweep", ctypes.c_double)]
+
+
 class ServerOptions(ctypes.Structure):
     _fields_ = [("memory_budget", ctypes.c_size_t), ("max_active", ctypes.c_int32),
                 ("chunk_sweeps", ctypes.c_int64), ("use_graph", ctypes.c_int32)]
@@ -119,6 +125,7 @@ def lib() -> ctypes.CDLL:
         "sg_server_release": (st, [P, i64]),
         "sg_server_get_stats": (st, [P, P]),
         "sg_server_destroy": (None, [P]),
+        "sg_autotune": (st, [P, i64, P]),
         "sg_status_str": (ctypes.c_char_p, [i32]),
         "sg_last_error": (ctypes.c_char_p, []),
     }
@@ -261,6 +268,12 @@ class Ensemble:
         out = np.zeros((self.n_samples, self.n_T, len(k), 2), dtype=np.float32)
         _check(lib().sg_measure(self._h, _ptr(k), len(k), _ptr(out)))
         return out
+
+    def autotune(self, trial_sweeps: int = 8) -> dict:
+        """sg_autotune: pick the fastest launch shape; state is unchanged."""
+        r = TuneReport()
+        _check(lib().sg_autotune(self._h, int(trial_sweeps), ctypes.byref(r)))
+        return {f: getattr(r, f) for f, _ in TuneReport._fields_}
 
     def measure_noalloc(self, k) -> np.ndarray:
         """sg_measure_noalloc: the same result, staged in the library's static

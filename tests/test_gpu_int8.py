@@ -266,3 +266,22 @@ def test_device_threshold_map_matches_oracle_bit_for_bit():
     got = sgmc.threshold_map(x)
     want = np.array([orc.t32(float(v)) if v < 0 else 0xFFFFFFFF for v in x], dtype=np.uint32)
     np.testing.assert_array_equal(got, want)
+
+
+@pytest.mark.parametrize("dist,L,nt", [("gauss", 8, 20), ("pmj", 12, 8)])
+def test_autotune_changes_speed_not_results(dist, L, nt):
+    S = 40
+    T = inputs.geometric_ladder(0.5, 1.5, nt)
+    J, s0 = inputs.make_instance(dist, L, S, nt, seed=6)
+    with sgmc.Ensemble(L, 0.2, T, dist, S, 4, J=J, spins=s0, n_therm=3) as ref:
+        ref.sweep(10)
+        want = (ref.spins(), ref.accumulators(), ref.energies()[0])
+    with sgmc.Ensemble(L, 0.2, T, dist, S, 4, J=J, spins=s0, n_therm=3) as ens:
+        ens.sweep(4)
+        rep = ens.autotune(trial_sweeps=3)
+        assert rep["n_candidates"] > 1 and rep["best_ms_per_sweep"] <= rep["default_ms_per_sweep"]
+        assert ens.sweeps_done == 4
+        ens.sweep(6)
+        np.testing.assert_array_equal(ens.spins(), want[0])
+        np.testing.assert_array_equal(ens.accumulators(), want[1])
+        np.testing.assert_array_equal(ens.energies()[0], want[2])
