@@ -98,6 +98,12 @@ typedef struct {
     uint64_t watchdog_cycles;  /* 0 = no limit; else per-launch clock64 budget
                                   after which kernels stop and report
                                   SG_ETIMEOUT                                 */
+    int64_t sample_base;       /* global index of this ensemble's sample 0: the
+                                  key of every random number of sample s is
+                                  sample_base + s, so an ensemble split into
+                                  shards (one per GPU) reproduces the
+                                  unsplit run exactly; 0 by default; a
+                                  multiple of 64 for MSC64                   */
 } sg_options;
 
 /* Fill *opt with the defaults: INT8 layout, rng_group 1, exchange and

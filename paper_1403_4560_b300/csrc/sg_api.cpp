@@ -245,6 +245,7 @@ Int8Args make_args(sg_ensemble *e)
     a.cancel = nullptr;
     a.s_begin = 0;
     a.s_end = e->S;
+    a.s_key0 = e->opt.sample_base;
     return a;
 }
 
@@ -271,6 +272,7 @@ MscArgs make_msc_args(sg_ensemble *e)
     a.exchange_every = e->opt.exchange_every;
     a.measure_every = e->opt.measure_every;
     a.n_therm = e->opt.n_therm;
+    a.s_key0 = e->opt.sample_base;
     return a;
 }
 
@@ -326,8 +328,11 @@ sg_status validate(int L, const double *T, int nt, sg_coupling dist, int64_t S,
     if (o.measure_every < 1) return fail(SG_EINVAL, "measure_every must be >= 1");
     if (o.layout != SG_LAYOUT_INT8 && o.layout != SG_LAYOUT_MSC64)
         return fail(SG_EINVAL, "unknown layout");
+    if (o.sample_base < 0 || o.sample_base + S > ((int64_t)1 << 32))
+        return fail(SG_EINVAL, "sample_base + n_samples must be in [0, 2^32]");
     if (o.layout == SG_LAYOUT_MSC64) {
         if (dist != SG_PM_J) return fail(SG_EINVAL, "the MSC64 layout needs +-J couplings");
+        if (o.sample_base % 64) return fail(SG_EINVAL, "the MSC64 layout needs sample_base % 64 == 0");
         if (S % 64) return fail(SG_EINVAL, "the MSC64 layout needs n_samples % 64 == 0");
         if (!msc_supported_L(L))
             return fail(SG_EUNSUPPORTED, "the MSC64 layout supports even L <= 16");
@@ -492,9 +497,10 @@ sg_status sg_create_ensemble(int L, double h, const double *T, int nt, sg_coupli
             if (r != cudaSuccess) return r;
         } else {
             if (e->msc)
-                r = msc_generate(e->Jw, e->W, S / 64, L, nt, slo, shi, s);
+                r = msc_generate(e->Jw, e->W, S / 64, L, nt, slo, shi, o.sample_base, s);
             else
-                r = gauss ? int8_gen_gauss(e->Jg, S, L, slo, shi, s) : int8_gen_pmj(e->J8, S, L, slo, shi, s);
+                r = gauss ? int8_gen_gauss(e->Jg, S, L, slo, shi, o.sample_base, s)
+                          : int8_gen_pmj(e->J8, S, L, slo, shi, o.sample_base, s);
             if (r != cudaSuccess) return r;
         }
         if (spins_host) {
@@ -509,7 +515,8 @@ sg_status sg_create_ensemble(int L, double h, const double *T, int nt, sg_coupli
             cudaFree(stage);
             if (r != cudaSuccess) return r;
         } else if (!e->msc) {
-            if ((r = int8_gen_spins(e->spins, S, L, nt, e->Tp, slo, shi, s)) != cudaSuccess) return r;
+            if ((r = int8_gen_spins(e->spins, S, L, nt, e->Tp, slo, shi, o.sample_base, s)) != cudaSuccess)
+                return r;
         }
         if (e->msc) {
             if ((r = msc_energies(make_msc_args(e), L, s)) != cudaSuccess) return r;

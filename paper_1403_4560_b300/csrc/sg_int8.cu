@@ -350,7 +350,7 @@ __device__ __forceinline__ void exchange_decide(const Smem &sm, const Ctx &cx, c
         const float t2 = __fmul_rn(a.h_f, __ll2float_rn(dM));
         const float dE = -__fadd_rn(t1, t2);
         const float D = __fmul_rn(sm.dbeta[p], dE);
-        const u32x4 o = philox10(cx.seed_lo ^ kTagExc, (uint32_t)cx.s, (uint32_t)p, ctr1,
+        const u32x4 o = philox10(cx.seed_lo ^ kTagExc, (uint32_t)(cx.s + a.s_key0), (uint32_t)p, ctr1,
                                  (uint32_t)r | rflag, cx.seed_hi);
         const bool acc = (D >= 0.0f) || (o.v[0] <= thr_of_logp(D));
         if (acc) {
@@ -596,7 +596,7 @@ __global__ void __launch_bounds__(kMaxThreads) int8_run_kernel(const Int8Args a)
     for (int64_t s = a.s_begin + blockIdx.x; s < a.s_end; s += gridDim.x) {
         cx.s = s;
         cx.k0 = a.seed_lo ^ kTagMet;
-        cx.k1 = (uint32_t)(s / a.rng_group);
+        cx.k1 = (uint32_t)((s + a.s_key0) / a.rng_group);
         __syncthreads();
         if (GST) {
             // large lattices: the CTA works on the sample's state in place
@@ -679,7 +679,8 @@ __device__ __forceinline__ int site_nb(int L, int i, int d, int step)
     return x + L * (y + L * z);
 }
 
-__global__ void gen_pmj_kernel(uint8_t *J8, int64_t S, int L, uint32_t slo, uint32_t shi)
+__global__ void gen_pmj_kernel(uint8_t *J8, int64_t S, int L, uint32_t slo, uint32_t shi,
+                               int64_t key0)
 {
     const int N = L * L * L;
     const int64_t total = S * N;
@@ -691,7 +692,7 @@ __global__ void gen_pmj_kernel(uint8_t *J8, int64_t S, int L, uint32_t slo, uint
         for (int d = 0; d < 3; ++d) {
             for (int side = 0; side < 2; ++side) {
                 const int owner = side == 0 ? i : site_nb(L, i, d, -1);  // bond owner site
-                const u32x4 o = philox10(slo ^ kTagBond, (uint32_t)s, (uint32_t)(owner >> 7),
+                const u32x4 o = philox10(slo ^ kTagBond, (uint32_t)(s + key0), (uint32_t)(owner >> 7),
                                          (uint32_t)d, 0u, shi);
                 out[2 * d + side] = (uint8_t)((o.v[(owner >> 5) & 3] >> (owner & 31)) & 1u);
             }
@@ -703,7 +704,8 @@ __global__ void gen_pmj_kernel(uint8_t *J8, int64_t S, int L, uint32_t slo, uint
     }
 }
 
-__global__ void gen_gauss_kernel(float *Jg, int64_t S, int L, uint32_t slo, uint32_t shi)
+__global__ void gen_gauss_kernel(float *Jg, int64_t S, int L, uint32_t slo, uint32_t shi,
+                                 int64_t key0)
 {
     const int N = L * L * L;
     const int64_t pairs = S * 3 * (int64_t)((N + 1) / 2);
@@ -713,7 +715,7 @@ __global__ void gen_gauss_kernel(float *Jg, int64_t S, int L, uint32_t slo, uint
         const int64_t s = g / (3 * half);
         const int d = (int)((g / half) % 3);
         const int m = (int)(g % half);
-        const u32x4 o = philox10(slo ^ kTagBond, (uint32_t)s, (uint32_t)m, (uint32_t)d, 1u, shi);
+        const u32x4 o = philox10(slo ^ kTagBond, (uint32_t)(s + key0), (uint32_t)m, (uint32_t)d, 1u, shi);
         // two uniforms in (0, 1) with 53 bits each, then Box-Muller
         const uint64_t a53 = (((uint64_t)o.v[0] << 21) ^ (o.v[1] >> 11)) & ((1ull << 53) - 1);
         const uint64_t b53 = (((uint64_t)o.v[2] << 21) ^ (o.v[3] >> 11)) & ((1ull << 53) - 1);
@@ -734,7 +736,7 @@ __global__ void gen_gauss_kernel(float *Jg, int64_t S, int L, uint32_t slo, uint
 }
 
 __global__ void gen_spins_kernel(uint8_t *spins, int64_t S, int L, int nt, int Tp, uint32_t slo,
-                                 uint32_t shi)
+                                 uint32_t shi, int64_t key0)
 {
     const int N = L * L * L;
     const int RB = 2 * Tp;
@@ -747,7 +749,7 @@ __global__ void gen_spins_kernel(uint8_t *spins, int64_t S, int L, int nt, int T
         const int r = (rb & 7) >> 2, t = 4 * (rb >> 3) + (rb & 3);
         uint8_t v = 0;
         if (t < nt) {
-            const u32x4 o = philox10(slo ^ kTagInit, (uint32_t)s, (uint32_t)(i >> 7),
+            const u32x4 o = philox10(slo ^ kTagInit, (uint32_t)(s + key0), (uint32_t)(i >> 7),
                                      ((uint32_t)r << 16) | (uint32_t)t, 0u, shi);
             v = (uint8_t)((o.v[(i >> 5) & 3] >> (i & 31)) & 1u);
         }
@@ -889,7 +891,7 @@ __global__ void exchange_kernel(const Int8Args a, int L, int parity, uint32_t ca
             const float t2 = __fmul_rn(a.h_f, __ll2float_rn(dM));
             const float dE = -__fadd_rn(t1, t2);
             const float D = __fmul_rn(a.dbeta[p], dE);
-            const u32x4 o = philox10(a.seed_lo ^ kTagExc, (uint32_t)s, (uint32_t)p, call_id,
+            const u32x4 o = philox10(a.seed_lo ^ kTagExc, (uint32_t)(s + a.s_key0), (uint32_t)p, call_id,
                                      (uint32_t)r | 0x100u, a.seed_hi);
             if ((D >= 0.0f) || (o.v[0] <= thr_of_logp(D))) {
                 accept[r][p] = 1;
@@ -1049,25 +1051,25 @@ int int8_ctas_per_sm(int L, bool gauss, int threads, size_t smem, bool gst)
 }
 
 cudaError_t int8_gen_pmj(uint8_t *J8, int64_t S, int L, uint32_t slo, uint32_t shi,
-                         cudaStream_t st)
+                         int64_t key0, cudaStream_t st)
 {
-    gen_pmj_kernel<<<grid_for(S * L * L * L, 256), 256, 0, st>>>(J8, S, L, slo, shi);
+    gen_pmj_kernel<<<grid_for(S * L * L * L, 256), 256, 0, st>>>(J8, S, L, slo, shi, key0);
     return cudaGetLastError();
 }
 
 cudaError_t int8_gen_gauss(float *Jg, int64_t S, int L, uint32_t slo, uint32_t shi,
-                           cudaStream_t st)
+                           int64_t key0, cudaStream_t st)
 {
     gen_gauss_kernel<<<grid_for(S * 3 * (L * L * L + 1) / 2, 256), 256, 0, st>>>(Jg, S, L, slo,
-                                                                                  shi);
+                                                                                  shi, key0);
     return cudaGetLastError();
 }
 
 cudaError_t int8_gen_spins(uint8_t *spins, int64_t S, int L, int nt, int Tp, uint32_t slo,
-                           uint32_t shi, cudaStream_t st)
+                           uint32_t shi, int64_t key0, cudaStream_t st)
 {
     gen_spins_kernel<<<grid_for(S * L * L * L * 2 * Tp, 256), 256, 0, st>>>(spins, S, L, nt, Tp,
-                                                                             slo, shi);
+                                                                             slo, shi, key0);
     return cudaGetLastError();
 }
 

@@ -38,6 +38,7 @@ struct Int8Args {
     unsigned long long watchdog;
     const volatile int *cancel;  // optional host-mapped cancel flag
     int64_t s_begin, s_end;      // samples handled by this launch
+    int64_t s_key0;              // global index of local sample 0 (RNG keys)
 };
 
 struct Int8Launch {
@@ -58,11 +59,11 @@ int int8_ctas_per_sm(int L, bool gauss, int threads, size_t smem, bool gst);
 
 // Instance preparation and state conversion kernels.
 cudaError_t int8_gen_pmj(uint8_t *J8, int64_t S, int L, uint32_t seed_lo, uint32_t seed_hi,
-                         cudaStream_t st);
+                         int64_t key0, cudaStream_t st);
 cudaError_t int8_gen_gauss(float *Jg, int64_t S, int L, uint32_t seed_lo, uint32_t seed_hi,
-                           cudaStream_t st);
+                           int64_t key0, cudaStream_t st);
 cudaError_t int8_gen_spins(uint8_t *spins, int64_t S, int L, int nt, int Tp, uint32_t seed_lo,
-                           uint32_t seed_hi, cudaStream_t st);
+                           uint32_t seed_hi, int64_t key0, cudaStream_t st);
 cudaError_t int8_import_J(uint8_t *J8, float *Jg, const float *Jcanon, int64_t S, int L,
                           bool gauss, cudaStream_t st);
 cudaError_t int8_export_J(float *Jcanon, const uint8_t *J8, const float *Jg, int64_t S, int L,

@@ -183,7 +183,7 @@ __device__ __forceinline__ void msc_half(const MscSmem &sm, const MscArgs &a, in
     for (int k = 0; k < kDM; ++k) cm[k] = 0;
     const uint32_t c2 = ((uint32_t)c << 24) | ((uint32_t)r << 16) | (uint32_t)t;
     for (int grp = tid; grp < NG; grp += tpc) {
-        const u32x4 rnd = philox10(a.seed_lo ^ kTagMet, (uint32_t)g, (uint32_t)grp, n_sweep, c2,
+        const u32x4 rnd = philox10(a.seed_lo ^ kTagMet, (uint32_t)(g + a.s_key0 / 64), (uint32_t)grp, n_sweep, c2,
                                    a.seed_hi);
 #pragma unroll
         for (int lane = 0; lane < 4; ++lane) {
@@ -419,7 +419,7 @@ __global__ void __launch_bounds__(kMscThreads) msc_sweep_kernel(const MscArgs a)
             const float t2 = __fmul_rn(a.h_f, __ll2float_rn(dM));
             const float dE = -__fadd_rn(t1, t2);
             const float D = __fmul_rn(a.dbeta[t0], dE);
-            const u32x4 o = philox10(a.seed_lo ^ kTagExc, (uint32_t)s, (uint32_t)t0, (uint32_t)n,
+            const u32x4 o = philox10(a.seed_lo ^ kTagExc, (uint32_t)(s + a.s_key0), (uint32_t)t0, (uint32_t)n,
                                      (uint32_t)r, a.seed_hi);
             const bool acc = (D >= 0.0f) || (o.v[0] <= thr_of_logp(D));
             const unsigned bal = __ballot_sync(0xFFFFFFFFu, acc);
@@ -542,7 +542,7 @@ __global__ void msc_export_J_kernel(float *Jc, const uint64_t *Jw, int64_t S, in
 
 // +-J bonds and initial spins drawn from the seed (same draws as the int8 path)
 __global__ void msc_gen_kernel(uint64_t *Jw, uint64_t *W, int64_t G, int L, int nt, uint32_t slo,
-                               uint32_t shi)
+                               uint32_t shi, int64_t key0)
 {
     const int N = L * L * L;
     const int64_t nJ = G * 3 * (int64_t)N, nW = G * nt * 2 * (int64_t)N;
@@ -554,7 +554,7 @@ __global__ void msc_gen_kernel(uint64_t *Jw, uint64_t *W, int64_t G, int L, int 
             const int d = (int)((e / N) % 3);
             const int64_t g = e / (3 * (int64_t)N);
             for (int b = 0; b < 64; ++b) {
-                const u32x4 o = philox10(slo ^ kTagBond, (uint32_t)(64 * g + b), (uint32_t)(i >> 7),
+                const u32x4 o = philox10(slo ^ kTagBond, (uint32_t)(64 * g + b + key0), (uint32_t)(i >> 7),
                                          (uint32_t)d, 0u, shi);
                 w |= (uint64_t)((o.v[(i >> 5) & 3] >> (i & 31)) & 1u) << b;
             }
@@ -566,7 +566,7 @@ __global__ void msc_gen_kernel(uint64_t *Jw, uint64_t *W, int64_t G, int L, int 
             const int t = (int)((f / (2 * (int64_t)N)) % nt);
             const int64_t g = f / (2 * (int64_t)N * nt);
             for (int b = 0; b < 64; ++b) {
-                const u32x4 o = philox10(slo ^ kTagInit, (uint32_t)(64 * g + b), (uint32_t)(i >> 7),
+                const u32x4 o = philox10(slo ^ kTagInit, (uint32_t)(64 * g + b + key0), (uint32_t)(i >> 7),
                                          ((uint32_t)r << 16) | (uint32_t)t, 0u, shi);
                 w |= (uint64_t)((o.v[(i >> 5) & 3] >> (i & 31)) & 1u) << b;
             }
@@ -627,7 +627,7 @@ __global__ void msc_exchange_decide_kernel(const MscArgs a, int parity, uint32_t
         const float t2 = __fmul_rn(a.h_f, __ll2float_rn(dM));
         const float dE = -__fadd_rn(t1, t2);
         const float D = __fmul_rn(a.dbeta[p], dE);
-        const u32x4 o = philox10(a.seed_lo ^ kTagExc, (uint32_t)s, (uint32_t)p, call_id,
+        const u32x4 o = philox10(a.seed_lo ^ kTagExc, (uint32_t)(s + a.s_key0), (uint32_t)p, call_id,
                                  (uint32_t)r | 0x100u, a.seed_hi);
         if ((D >= 0.0f) || (o.v[0] <= thr_of_logp(D))) {
             const int64_t tb = Bp[0]; Bp[0] = Bp[1]; Bp[1] = tb;
@@ -763,10 +763,10 @@ cudaError_t msc_export_J(float *Jc, const uint64_t *Jw, int64_t G, int L, cudaSt
 }
 
 cudaError_t msc_generate(uint64_t *Jw, uint64_t *W, int64_t G, int L, int nt, uint32_t slo,
-                         uint32_t shi, cudaStream_t st)
+                         uint32_t shi, int64_t key0, cudaStream_t st)
 {
     msc_gen_kernel<<<gridn(G * (3 + 2 * nt) * L * L * L, 128), 128, 0, st>>>(Jw, W, G, L, nt, slo,
-                                                                              shi);
+                                                                              shi, key0);
     return cudaGetLastError();
 }
 

@@ -26,6 +26,7 @@ struct MscArgs {
     int sweep_offset;           // this launch's sweep = base + sweep_offset
     int exchange_every, measure_every;
     int64_t n_therm;
+    int64_t s_key0;             // global index of local sample 0 (multiple of 64)
 };
 
 size_t msc_smem_bytes(int L);
@@ -38,7 +39,7 @@ cudaError_t msc_export_spins(int8_t *canon, const uint64_t *W, int64_t G, int L,
 cudaError_t msc_import_J(uint64_t *Jw, const float *Jc, int64_t G, int L, cudaStream_t st);
 cudaError_t msc_export_J(float *Jc, const uint64_t *Jw, int64_t G, int L, cudaStream_t st);
 cudaError_t msc_generate(uint64_t *Jw, uint64_t *W, int64_t G, int L, int nt, uint32_t slo,
-                         uint32_t shi, cudaStream_t st);
+                         uint32_t shi, int64_t key0, cudaStream_t st);
 cudaError_t msc_energies(const MscArgs &a, int L, cudaStream_t st);
 cudaError_t msc_exchange(const MscArgs &a, int L, int parity, uint32_t call_id, uint64_t *masks,
                          cudaStream_t st);

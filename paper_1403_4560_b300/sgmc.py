@@ -32,7 +32,8 @@ class Options(ctypes.Structure):
     _fields_ = [("layout", ctypes.c_int32), ("rng_group", ctypes.c_int32),
                 ("exchange_every", ctypes.c_int32), ("measure_every", ctypes.c_int32),
                 ("n_therm", ctypes.c_int64), ("threads_per_block", ctypes.c_int32),
-                ("sweeps_per_launch", ctypes.c_int32), ("watchdog_cycles", ctypes.c_uint64)]
+                ("sweeps_per_launch", ctypes.c_int32), ("watchdog_cycles", ctypes.c_uint64),
+                ("sample_base", ctypes.c_int64)]
 
 
 class Info(ctypes.Structure):

@@ -285,3 +285,43 @@ def test_autotune_changes_speed_not_results(dist, L, nt):
         np.testing.assert_array_equal(ens.spins(), want[0])
         np.testing.assert_array_equal(ens.accumulators(), want[1])
         np.testing.assert_array_equal(ens.energies()[0], want[2])
+
+
+@pytest.mark.parametrize("layout,dist,S,cut,L", [(0, "gauss", 12, 5, 6), (0, "pmj", 9, 4, 8),
+                                                 (1, "pmj", 192, 64, 6)])
+def test_shards_with_sample_base_reproduce_the_unsplit_run(layout, dist, S, cut, L):
+    """Library-drawn instance; one ensemble against two shards whose samples
+    carry their global indices (the multi-GPU split)."""
+    nt, seed = 5, 31
+    T = inputs.geometric_ladder(0.5, 1.5, nt)
+    with sgmc.Ensemble(L, 0.2, T, dist, S, seed, layout=layout, n_therm=4) as whole, \
+            sgmc.Ensemble(L, 0.2, T, dist, cut, seed, layout=layout, n_therm=4) as a, \
+            sgmc.Ensemble(L, 0.2, T, dist, S - cut, seed, layout=layout, n_therm=4,
+                          sample_base=cut) as b:
+        for e in (whole, a, b):
+            e.sweep(20)
+        np.testing.assert_array_equal(np.concatenate([a.couplings(), b.couplings()]),
+                                      whole.couplings())
+        np.testing.assert_array_equal(np.concatenate([a.spins(), b.spins()]), whole.spins())
+        np.testing.assert_array_equal(np.concatenate([a.accumulators(), b.accumulators()]),
+                                      whole.accumulators())
+
+
+@pytest.mark.parametrize("layout,dist,S", [(0, "gauss", 6), (1, "pmj", 64)])
+def test_checkpoint_and_resume_is_bit_exact(layout, dist, S):
+    L, nt = 6, 4
+    T = inputs.geometric_ladder(0.5, 1.5, nt)
+    J, s0 = inputs.make_instance(dist, L, S, nt, seed=2)
+    with sgmc.Ensemble(L, 0.1, T, dist, S, 8, J=J, spins=s0, layout=layout, n_therm=5) as ref:
+        ref.sweep(30)
+        want = (ref.spins(), ref.accumulators())
+    with sgmc.Ensemble(L, 0.1, T, dist, S, 8, J=J, spins=s0, layout=layout, n_therm=5) as e:
+        e.sweep(12)
+        ckpt = (e.spins(), e.accumulators(), e.sweeps_done)
+    with sgmc.Ensemble(L, 0.1, T, dist, S, 8, J=J, spins=s0, layout=layout, n_therm=5) as r:
+        r.set_spins(ckpt[0])
+        r.set_accumulators(ckpt[1])
+        r.set_sweeps_done(ckpt[2])
+        r.sweep(18)
+        np.testing.assert_array_equal(r.spins(), want[0])
+        np.testing.assert_array_equal(r.accumulators(), want[1])
