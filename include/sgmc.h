@@ -301,8 +301,11 @@ const char *sg_last_error(void);
  * independent simulation requests (each a full run of the method above)
  * that arrive over time. A worker thread admits queued requests while their
  * ensembles fit the device-memory budget, keeps admitted ensembles resident
- * (lattices, couplings, accumulators, sweep counters), advances all of them
- * together in batching rounds (sg_sweep_batch) and releases finished ones.
+ * (lattices, couplings, accumulators, sweep counters), advances each on its
+ * own stream in chunks of at most chunk_sweeps sweeps and about 2e9
+ * spin-flip attempts (all resident requests share the GPU; streams of
+ * smaller requests get higher priority), and releases each as soon as its
+ * last chunk completes.
  * A result does not depend on what else ran beside it.
  * ------------------------------------------------------------------------ */
 typedef struct sg_server sg_server;
@@ -311,8 +314,8 @@ typedef struct {
     size_t memory_budget;  /* device bytes for resident ensembles; 0 = 80% of
                               the free memory when the server starts        */
     int32_t max_active;    /* cap on resident ensembles; 0 = budget only    */
-    int64_t chunk_sweeps;  /* sweeps per batching round (default 256)       */
-    int32_t use_graph;     /* run rounds through cached CUDA graphs         */
+    int64_t chunk_sweeps;  /* sweeps per chunk of a request (default 256)   */
+    int32_t use_graph;     /* run chunks through cached CUDA graphs         */
 } sg_server_options;
 
 typedef struct {
@@ -332,16 +335,17 @@ typedef struct {
 } sg_request;
 
 typedef struct {
-    int64_t completed, queued, active, rounds;
-    double attempts;        /* spin-flip attempts done by all rounds        */
-    double busy_seconds;    /* wall time spent in rounds                    */
+    int64_t completed, queued, active, rounds; /* rounds = chunks launched */
+    double attempts;        /* spin-flip attempts of all completed chunks   */
+    double busy_seconds;    /* wall time with at least one request resident */
     size_t device_bytes_in_use;
     double latency_p50, latency_p99; /* submit-to-result seconds, completed */
 } sg_server_stats;
 
 void sg_server_options_default(sg_server_options *opt);
 void sg_request_default(sg_request *req);
-/* Start a server on the current device; all its work runs on `stream`. */
+/* Start a server on the current device. `stream` is unused (each request
+ * gets its own stream); it is kept for ABI stability and may be NULL. */
 sg_status sg_server_create(const sg_server_options *opt, void *stream, sg_server **out);
 /* Queue a request (thread-safe, returns at once); *id receives its handle. */
 sg_status sg_server_submit(sg_server *sv, const sg_request *req, int64_t *id);

@@ -4,12 +4,13 @@
 // seed, sweeps) arrive at any time from any host thread. One worker thread
 // owns the device work: it admits queued requests while their ensembles fit
 // the device-memory budget, keeps every admitted ensemble (lattices, couplings,
-// accumulators, sweep counters) resident on the device, and advances all
-// active ensembles together in rounds of batched sweeps. A request that
-// arrives while others run joins at the next round; a finished one leaves at
-// the end of its round, its accumulators are copied out and its memory is
-// released for the queue. Results do not depend on the mix: each ensemble's
-// chain is keyed by its own seed and sweep index.
+// accumulators, sweep counters) resident on the device, and advances each on
+// its own stream in chunks of sweeps, so the kernels of all resident requests
+// share the GPU. A request that arrives while others run starts at once if
+// memory allows; a finished one leaves as soon as its last chunk completes,
+// its accumulators are copied out and its memory is released for the queue.
+// Results do not depend on the mix: each ensemble's chain is keyed by its own
+// seed and sweep index.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -35,6 +36,10 @@ double now_s()
 
 enum { RQ_QUEUED = 0, RQ_RUNNING = 1, RQ_DONE = 2, RQ_FAILED = 3, RQ_CANCELLED = 4 };
 
+// A chunk is at most this many spin-flip attempts (~10 ms of GPU time), so a
+// large request never holds the SMs long enough to stall the small ones.
+constexpr double kChunkAttempts = 2.0e9;
+
 struct Request {
     sg_request r{};
     std::vector<double> T;
@@ -42,6 +47,11 @@ struct Request {
     sg_status err = SG_OK;
     std::string err_msg;
     sg_ensemble *e = nullptr;
+    cudaStream_t st = nullptr;  // the request's own stream
+    cudaEvent_t ev = nullptr;   // completion of its chunk in flight
+    bool inflight = false;
+    int64_t chunk = 0;
+    double chunk_attempts = 0;
     size_t bytes = 0;
     int64_t remaining = 0;
     bool cancel = false;
@@ -62,12 +72,13 @@ struct sg_server {
     std::deque<int64_t> queue;
     std::map<int64_t, Request> reqs;
     std::vector<int64_t> active;
-    bool stop = false;
+    bool stop = false;  // set by destroy
     size_t used = 0;
     int64_t next_id = 1;
     // statistics
     int64_t completed = 0, rounds = 0;
     double attempts = 0, busy_s = 0;
+    double busy_since = -1.0;  // start of the current busy interval, or -1
     std::vector<double> latencies;
 };
 
@@ -87,15 +98,29 @@ sg_options request_options(const sg_request &r)
     return o;
 }
 
+// Release a request's device resources (called without the lock).
+void release_request(Request &q)
+{
+    if (q.e) sg_destroy(q.e);
+    if (q.ev) cudaEventDestroy(q.ev);
+    if (q.st) cudaStreamDestroy(q.st);
+    q.e = nullptr;
+    q.ev = nullptr;
+    q.st = nullptr;
+}
+
+// Worker: admission, then every resident request advances on its own stream
+// chunk by chunk; finished chunks are found by polling their events, so a
+// short request leaves as soon as its own work is done and a new one starts
+// at once (continuous batching).
 void worker_loop(sg_server *sv)
 {
     cudaSetDevice(sv->device);
     std::unique_lock<std::mutex> lk(sv->mu);
+    double &busy_since = sv->busy_since;
     for (;;) {
         // ---- admission: queued requests while their ensembles fit the budget
-        bool admitted_any = true;
-        while (admitted_any && !sv->queue.empty() && !sv->stop) {
-            admitted_any = false;
+        while (!sv->queue.empty() && !sv->stop) {
             const int64_t id = sv->queue.front();
             Request &q = sv->reqs[id];
             if (q.cancel) {
@@ -103,109 +128,137 @@ void worker_loop(sg_server *sv)
                 q.state = RQ_CANCELLED;
                 q.t_done = now_s();
                 sv->done_cv.notify_all();
-                admitted_any = true;
                 continue;
             }
             if (sv->opt.max_active > 0 && (int)sv->active.size() >= sv->opt.max_active) break;
             const sg_options o = request_options(q.r);
-            const size_t need = sg_ensemble_bytes(q.r.L, q.r.n_T, q.r.n_samples, (sg_coupling)q.r.dist, &o);
-            if (need == 0) {
+            const size_t need =
+                sg_ensemble_bytes(q.r.L, q.r.n_T, q.r.n_samples, (sg_coupling)q.r.dist, &o);
+            if (need == 0 || (sv->used + need > sv->opt.memory_budget && sv->active.empty())) {
                 sv->queue.pop_front();
                 q.state = RQ_FAILED;
-                q.err = SG_EINVAL;
-                q.err_msg = "request rejected by sg_ensemble_bytes";
+                q.err = need == 0 ? SG_EINVAL : SG_ENOMEM;
+                q.err_msg = need == 0 ? "request rejected by sg_ensemble_bytes"
+                                      : "request larger than the server's memory budget";
                 q.t_done = now_s();
                 sv->done_cv.notify_all();
-                admitted_any = true;
                 continue;
             }
-            if (sv->used + need > sv->opt.memory_budget) {
-                if (sv->active.empty()) {  // would never fit
-                    sv->queue.pop_front();
-                    q.state = RQ_FAILED;
-                    q.err = SG_ENOMEM;
-                    q.err_msg = "request larger than the server's memory budget";
-                    q.t_done = now_s();
-                    sv->done_cv.notify_all();
-                    admitted_any = true;
-                }
-                break;  // first in, first admitted: wait for memory
-            }
+            if (sv->used + need > sv->opt.memory_budget) break;  // wait for memory, in order
             sv->queue.pop_front();
             const sg_request r = q.r;
             const std::vector<double> T = q.T;
             lk.unlock();
+            cudaStream_t st = nullptr;
+            cudaEvent_t ev = nullptr;
             sg_ensemble *e = nullptr;
-            const sg_status st = sg_create_ensemble(r.L, r.h, T.data(), r.n_T, (sg_coupling)r.dist, r.n_samples,
-                                                    r.seed, &o, nullptr, nullptr, sv->stream, &e);
-            const std::string msg = st == SG_OK ? "" : sg_last_error();
+            sg_status rc = SG_OK;
+            // smaller requests get higher-priority streams: when SMs free up,
+            // the scheduler prefers their CTAs (shortest work first)
+            int least = 0, greatest = 0;
+            cudaDeviceGetStreamPriorityRange(&least, &greatest);
+            const double work = (double)r.L * r.L * r.L * 2.0 * r.n_T * (double)r.n_samples *
+                                (double)std::max<int64_t>(r.n_sweeps, 1);
+            int bucket = (int)std::floor(std::log10(std::max(work, 1.0))) - 9;
+            bucket = std::max(0, bucket);
+            const int prio = std::min(least, greatest + bucket);
+            if (cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, prio) != cudaSuccess ||
+                cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
+                rc = SG_ECUDA;
+            if (rc == SG_OK)
+                rc = sg_create_ensemble(r.L, r.h, T.data(), r.n_T, (sg_coupling)r.dist,
+                                        r.n_samples, r.seed, &o, nullptr, nullptr, st, &e);
+            const std::string msg = rc == SG_OK ? "" : sg_last_error();
             lk.lock();
             Request &q2 = sv->reqs[id];
-            if (st != SG_OK) {
-                if (st == SG_ENOMEM && !sv->active.empty()) {
+            q2.st = st;
+            q2.ev = ev;
+            if (rc != SG_OK) {
+                lk.unlock();
+                release_request(q2);
+                lk.lock();
+                if (rc == SG_ENOMEM && !sv->active.empty()) {
                     sv->queue.push_front(id);  // retry once memory frees up
                     break;
                 }
                 q2.state = RQ_FAILED;
-                q2.err = st;
+                q2.err = rc;
                 q2.err_msg = msg;
                 q2.t_done = now_s();
                 sv->done_cv.notify_all();
-            } else {
-                q2.e = e;
-                q2.bytes = need;
-                q2.remaining = r.n_sweeps;
-                q2.state = RQ_RUNNING;
-                q2.t_start = now_s();
-                sv->used += need;
-                sv->active.push_back(id);
+                continue;
             }
-            admitted_any = true;
+            q2.e = e;
+            q2.bytes = need;
+            q2.remaining = r.n_sweeps;
+            q2.state = RQ_RUNNING;
+            q2.t_start = now_s();
+            sv->used += need;
+            sv->active.push_back(id);
         }
         if (sv->stop) break;
         if (sv->active.empty()) {
+            if (busy_since >= 0) {
+                sv->busy_s += now_s() - busy_since;
+                busy_since = -1.0;
+            }
             sv->cv.wait(lk, [&] { return sv->stop || !sv->queue.empty(); });
             if (sv->stop) break;
             continue;
         }
-        // ---- one batching round over every active ensemble
-        std::vector<sg_ensemble *> es;
-        std::vector<int64_t> ids;
-        int64_t n = sv->opt.chunk_sweeps > 0 ? sv->opt.chunk_sweeps : 256;
-        double att = 0;
+        if (busy_since < 0) busy_since = now_s();
+        // ---- launch the next chunk of every idle request
+        const int64_t chunk = sv->opt.chunk_sweeps > 0 ? sv->opt.chunk_sweeps : 256;
         for (int64_t id : sv->active) {
             Request &q = sv->reqs[id];
-            if (q.remaining > 0) {
-                n = std::min(n, q.remaining);
-                es.push_back(q.e);
-                ids.push_back(id);
-            }
-        }
-        for (int64_t id : ids) {
+            if (q.inflight || q.cancel || q.remaining <= 0) continue;
             sg_info inf;
-            sg_get_info(sv->reqs[id].e, &inf);
-            att += (double)inf.attempts_per_sweep * (double)n;
+            sg_get_info(q.e, &inf);
+            const int64_t cap = std::max<int64_t>(
+                1, (int64_t)(kChunkAttempts / (double)std::max<int64_t>(inf.attempts_per_sweep, 1)));
+            const int64_t n = std::min(std::min(chunk, cap), q.remaining);
+            sg_ensemble *e = q.e;
+            lk.unlock();
+            sg_status rc = sv->opt.use_graph ? sg_sweep_batch(&e, 1, n, 1) : sg_sweep(e, n);
+            cudaError_t ce = rc == SG_OK ? cudaEventRecord(q.ev, q.st) : cudaSuccess;
+            lk.lock();
+            if (rc != SG_OK || ce != cudaSuccess) {
+                q.state = RQ_FAILED;
+                q.err = rc != SG_OK ? rc : SG_ECUDA;
+                q.err_msg = rc != SG_OK ? sg_last_error() : cudaGetErrorString(ce);
+                q.cancel = true;  // retired below
+                continue;
+            }
+            q.inflight = true;
+            q.chunk = n;
+            q.chunk_attempts = (double)inf.attempts_per_sweep * (double)n;
+            sv->rounds += 1;
         }
-        lk.unlock();
-        const double t0 = now_s();
-        sg_status st = es.empty() ? SG_OK : sg_sweep_batch(es.data(), (int)es.size(), n, sv->opt.use_graph);
-        cudaError_t ce = cudaStreamSynchronize(sv->stream);
-        const double t1 = now_s();
-        lk.lock();
-        sv->busy_s += t1 - t0;
-        sv->rounds += 1;
-        if (st == SG_OK && ce == cudaSuccess) sv->attempts += att;
         // ---- retire finished, failed and cancelled requests
+        bool progressed = false;
         std::vector<int64_t> keep;
         for (int64_t id : sv->active) {
             Request &q = sv->reqs[id];
-            const bool in_round = std::find(ids.begin(), ids.end(), id) != ids.end();
-            if (in_round && st == SG_OK && ce == cudaSuccess) q.remaining -= n;
+            if (q.inflight) {
+                const cudaError_t qe = cudaEventQuery(q.ev);
+                if (qe == cudaErrorNotReady) {
+                    keep.push_back(id);
+                    continue;
+                }
+                q.inflight = false;
+                progressed = true;
+                if (qe != cudaSuccess) {
+                    q.state = RQ_FAILED;
+                    q.err = SG_ECUDA;
+                    q.err_msg = cudaGetErrorString(qe);
+                    q.cancel = true;
+                } else {
+                    q.remaining -= q.chunk;
+                    sv->attempts += q.chunk_attempts;
+                }
+            }
             bool finish = false;
-            if (st != SG_OK || ce != cudaSuccess) {
-                q.state = RQ_FAILED;
-                q.err = st != SG_OK ? st : SG_ECUDA;
-                q.err_msg = st != SG_OK ? sg_last_error() : cudaGetErrorString(ce);
+            if (q.state == RQ_FAILED) {
                 finish = true;
             } else if (q.cancel) {
                 q.state = RQ_CANCELLED;
@@ -214,15 +267,12 @@ void worker_loop(sg_server *sv)
                 sg_info inf;
                 sg_get_info(q.e, &inf);
                 q.acc.assign((size_t)inf.n_samples * inf.n_T * SG_NACC, 0.0);
+                sg_ensemble *e = q.e;
                 lk.unlock();
-                const sg_status gs = sg_get_accumulators(q.e, q.acc.data());
+                const sg_status gs = sg_get_accumulators(e, q.acc.data());
                 lk.lock();
-                if (gs != SG_OK) {
-                    q.state = RQ_FAILED;
-                    q.err = gs;
-                } else {
-                    q.state = RQ_DONE;
-                }
+                q.state = gs == SG_OK ? RQ_DONE : RQ_FAILED;
+                q.err = gs;
                 finish = true;
             }
             if (finish) {
@@ -231,26 +281,29 @@ void worker_loop(sg_server *sv)
                     sv->completed += 1;
                     sv->latencies.push_back(q.t_done - q.t_submit);
                 }
-                sg_ensemble *e = q.e;
-                q.e = nullptr;
                 sv->used -= q.bytes;
+                q.bytes = 0;
                 lk.unlock();
-                sg_destroy(e);
+                release_request(q);
                 lk.lock();
                 sv->done_cv.notify_all();
+                progressed = true;
             } else {
                 keep.push_back(id);
             }
         }
         sv->active = keep;
+        if (!progressed) {  // nothing finished: give the GPU a moment
+            lk.unlock();
+            std::this_thread::sleep_for(std::chrono::microseconds(100));
+            lk.lock();
+        }
     }
-    // shutdown: release what is still resident
+    // shutdown: wait for in-flight work and release what is still resident
     for (int64_t id : sv->active) {
         Request &q = sv->reqs[id];
-        if (q.e) {
-            sg_destroy(q.e);
-            q.e = nullptr;
-        }
+        if (q.st) cudaStreamSynchronize(q.st);
+        release_request(q);
         q.state = RQ_CANCELLED;
     }
     sv->active.clear();
@@ -396,7 +449,7 @@ sg_status sg_server_get_stats(sg_server *sv, sg_server_stats *out)
     out->active = (int64_t)sv->active.size();
     out->rounds = sv->rounds;
     out->attempts = sv->attempts;
-    out->busy_seconds = sv->busy_s;
+    out->busy_seconds = sv->busy_s + (sv->busy_since >= 0 ? now_s() - sv->busy_since : 0.0);
     out->device_bytes_in_use = sv->used;
     out->latency_p50 = percentile(sv->latencies, 0.50);
     out->latency_p99 = percentile(sv->latencies, 0.99);
