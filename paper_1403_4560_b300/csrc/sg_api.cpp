@@ -150,7 +150,7 @@ sg_status configure_launch(sg_ensemble *e)
     int run = H;
     while (run % 4) run += H;
     const int items = (L * L * L / 2) / run * WR;
-    const int maxt = int8_max_threads();
+    const int maxt = int8_max_threads(e->L);
     // shared-memory residency first; the global-memory variant when the
     // sample's state does not fit (large L or many temperatures)
     for (int pass = 0; pass < 2; ++pass) {
@@ -159,8 +159,8 @@ sg_status configure_launch(sg_ensemble *e)
         int best_t = 0, best_m = 0, best_occ = 0;
         for (int t = WR; t <= maxt; t += WR) {
             if (t < 32) continue;  // the measurement needs one full warp
-            if (e->opt.threads_per_block > 0 &&
-                t != std::max(WR, (e->opt.threads_per_block / WR) * WR))
+            if (e->opt.threads_per_block > 0 &&  // a request is clamped to what the kernel allows
+                t != std::max(WR, (std::min(e->opt.threads_per_block, maxt) / WR) * WR))
                 continue;
             int occ = 0, m_for = 0;
             for (int m = WR; m >= 1; --m) {
@@ -907,7 +907,7 @@ sg_status sg_autotune(sg_ensemble *e, int64_t trial_sweeps, sg_tune_report *rep)
     cudaError_t ce = save(false);
     std::vector<std::pair<int, int>> cands;
     cands.push_back({orig_launch.threads, orig_m});
-    for (int t = ((32 + WR - 1) / WR) * WR; t <= int8_max_threads(); t += WR) {
+    for (int t = ((32 + WR - 1) / WR) * WR; t <= int8_max_threads(e->L); t += WR) {
         int best_occ = 0, m_for = 0;
         for (int m = WR; m >= 1; --m) {
             const size_t smem = int8_smem_bytes(e->L, e->Tp, e->gauss, m, orig_launch.gst);

@@ -165,13 +165,16 @@ __device__ __forceinline__ uint32_t gauss_word(uint32_t s, uint32_t nxp, uint32_
 #pragma unroll
     for (int kk = 0; kk < 4; ++kk) {
         const int sh = 31 - 8 * kk;
-        // J * s_nb: flip the sign bit of J where the neighbour is -1
-        float b = __int_as_float(__float_as_int(j[0]) ^ ((nxp << sh) & 0x80000000u));
-        b = __fadd_rn(b, __int_as_float(__float_as_int(j[1]) ^ ((nxm << sh) & 0x80000000u)));
-        b = __fadd_rn(b, __int_as_float(__float_as_int(j[2]) ^ ((nyp << sh) & 0x80000000u)));
-        b = __fadd_rn(b, __int_as_float(__float_as_int(j[3]) ^ ((nym << sh) & 0x80000000u)));
-        b = __fadd_rn(b, __int_as_float(__float_as_int(j[4]) ^ ((nzp << sh) & 0x80000000u)));
-        b = __fadd_rn(b, __int_as_float(__float_as_int(j[5]) ^ ((nzm << sh) & 0x80000000u)));
+        // J * s_nb: flip the sign bit of J where the neighbour is -1; the sum
+        // is exact on the 2^-17 grid, so a balanced tree (short dependency
+        // chain) gives the same value as any other order
+        const float t0 = __int_as_float(__float_as_int(j[0]) ^ ((nxp << sh) & 0x80000000u));
+        const float t1 = __int_as_float(__float_as_int(j[1]) ^ ((nxm << sh) & 0x80000000u));
+        const float t2 = __int_as_float(__float_as_int(j[2]) ^ ((nyp << sh) & 0x80000000u));
+        const float t3 = __int_as_float(__float_as_int(j[3]) ^ ((nym << sh) & 0x80000000u));
+        const float t4 = __int_as_float(__float_as_int(j[4]) ^ ((nzp << sh) & 0x80000000u));
+        const float t5 = __int_as_float(__float_as_int(j[5]) ^ ((nzm << sh) & 0x80000000u));
+        const float b = __fadd_rn(__fadd_rn(__fadd_rn(t0, t1), __fadd_rn(t2, t3)), __fadd_rn(t4, t5));
         const uint32_t sgn = (s << sh) & 0x80000000u;  // own spin -1 => sign bit
         const float zf = __fadd_rn(b, hq);
         const float dE = __int_as_float(__float_as_int(__fadd_rn(zf, zf)) ^ sgn);
@@ -336,9 +339,12 @@ __device__ __forceinline__ void exchange_decide(const Smem &sm, const Ctx &cx, c
                                                 int parity, uint32_t ctr1, uint32_t rflag,
                                                 uint32_t stamp)
 {
-    const int nt = cx.nt, Tp = cx.Tp;
+    // warp 0 only: the pair decisions, then the byte-permutation selectors
+    const int lane = threadIdx.x;
+    const int nt = cx.nt, Tp = cx.Tp, WR = cx.WR;
     const int np = (nt - parity) / 2;
-    for (int id = threadIdx.x; id < 2 * np; id += blockDim.x) {
+    if (lane < 2) sm.anyswap[lane] = 0;
+    for (int id = lane; id < 2 * np; id += 32) {
         const int r = id / np;
         const int p = parity + 2 * (id % np);
         if (p + 1 >= nt) continue;
@@ -363,16 +369,8 @@ __device__ __forceinline__ void exchange_decide(const Smem &sm, const Ctx &cx, c
             sm.xflag[r * Tp + p] = stamp;
         }
     }
-}
-
-template <int L>
-__device__ __forceinline__ void exchange_apply(const Smem &sm, const Ctx &cx, uint32_t stamp)
-{
-    constexpr int N = L * L * L;
-    const int nt = cx.nt, Tp = cx.Tp, WR = cx.WR;
-    if (threadIdx.x < 2) sm.anyswap[threadIdx.x] = 0;
-    __syncthreads();
-    for (int id = threadIdx.x; id < 2 * WR; id += blockDim.x) {
+    __syncwarp();
+    for (int id = lane; id < 2 * WR; id += 32) {
         const int r = id / WR, j = id % WR;
         const uint32_t *fl = sm.xflag + r * Tp;
         uint32_t s1 = 0, s2 = 0;
@@ -397,8 +395,15 @@ __device__ __forceinline__ void exchange_apply(const Smem &sm, const Ctx &cx, ui
         sm.sel[(r * WR + j) * 2 + 1] = s2;
         if (any) atomicOr(&sm.anyswap[r], 1);
     }
-    __syncthreads();
-    const int RB = cx.RB;
+}
+
+// All threads: apply the accepted swaps row by row (after a block barrier
+// that publishes the selectors).
+template <int L>
+__device__ __forceinline__ void exchange_apply(const Smem &sm, const Ctx &cx)
+{
+    constexpr int N = L * L * L;
+    const int WR = cx.WR, RB = cx.RB;
     for (int id = threadIdx.x; id < 2 * N; id += blockDim.x) {
         const int r = id & 1, site = id >> 1;
         if (!sm.anyswap[r]) continue;
@@ -413,7 +418,6 @@ __device__ __forceinline__ void exchange_apply(const Smem &sm, const Ctx &cx, ui
             cur = next;
         }
     }
-    __syncthreads();
 }
 
 // Counts of q = -1 per phase d of one wave vector, from the 2D marginal
@@ -448,6 +452,28 @@ __device__ __forceinline__ void measure_step(const Smem &sm, const Ctx &cx, cons
     constexpr int LL = L * L;
     const int WR = cx.WR, RB = cx.RB, Tp = cx.Tp, nt = cx.nt;
     double *accs = a.acc + (size_t)cx.s * nt * SG_NACC;
+    // energies and magnetisations first (one thread per slot), so that the
+    // projection phase reads nothing the next sweep overwrites
+    for (int t = threadIdx.x; t < nt; t += blockDim.x) {
+        double *ac = accs + (size_t)t * SG_NACC;
+        double o5 = ac[5], o6 = ac[6], o7 = ac[7], o8 = ac[8];
+        for (int r = 0; r < 2; ++r) {
+            const long long Bv = (long long)sm.B[r * Tp + t];
+            const long long Mv = (long long)sm.M[r * Tp + t];
+            const double e = -__dadd_rn(__dmul_rn((double)Bv, a.qJ_d), __dmul_rn(a.h_d, (double)Mv));
+            o5 = __dadd_rn(o5, e);
+            o6 = __dadd_rn(o6, __dmul_rn(e, e));
+        }
+        for (int r = 0; r < 2; ++r) {
+            const double m = (double)(long long)sm.M[r * Tp + t];
+            o7 = __dadd_rn(o7, m);
+            o8 = __dadd_rn(o8, __dmul_rn(m, m));
+        }
+        ac[5] = o5;
+        ac[6] = o6;
+        ac[7] = o7;
+        ac[8] = o8;
+    }
     for (int j0 = 0; j0 < WR; j0 += a.mchunk) {
         const int nw = min(a.mchunk, WR - j0);
         // (A) marginals; the group index varies fastest across lanes
@@ -492,7 +518,7 @@ __device__ __forceinline__ void measure_step(const Smem &sm, const Ctx &cx, cons
             const int jj = sl >> 2, sh = 8 * (sl & 3);
             double *ac = accs + (size_t)t * SG_NACC;
             double *acv = ac + (v == 9 ? 0 : 9 + 3 * v);
-            const int nacc = v == 9 ? 9 : 3;
+            const int nacc = v == 9 ? 5 : 3;
             double old[9];
 #pragma unroll
             for (int q = 0; q < 9; ++q) old[q] = q < nacc ? acv[q] : 0.0;
@@ -522,19 +548,6 @@ __device__ __forceinline__ void measure_step(const Smem &sm, const Ctx &cx, cons
                 old[2] = __dadd_rn(old[2], Q2);
                 old[3] = __dadd_rn(old[3], __dmul_rn(Q2, Q));
                 old[4] = __dadd_rn(old[4], __dmul_rn(Q2, Q2));
-                for (int r = 0; r < 2; ++r) {
-                    const long long Bv = (long long)sm.B[r * Tp + t];
-                    const long long Mv = (long long)sm.M[r * Tp + t];
-                    const double e = -__dadd_rn(__dmul_rn((double)Bv, a.qJ_d),
-                                                __dmul_rn(a.h_d, (double)Mv));
-                    old[5] = __dadd_rn(old[5], e);
-                    old[6] = __dadd_rn(old[6], __dmul_rn(e, e));
-                }
-                for (int r = 0; r < 2; ++r) {
-                    const double m = (double)(long long)sm.M[r * Tp + t];
-                    old[7] = __dadd_rn(old[7], m);
-                    old[8] = __dadd_rn(old[8], __dmul_rn(m, m));
-                }
             } else {
                 float re = 0.0f, im = 0.0f;
 #pragma unroll
@@ -552,7 +565,10 @@ __device__ __forceinline__ void measure_step(const Smem &sm, const Ctx &cx, cons
             for (int q = 0; q < 9; ++q)
                 if (q < nacc) acv[q] = old[q];
         }
-        __syncthreads();
+        // the next chunk's marginals overwrite this chunk's; after the last
+        // chunk the next sweep touches nothing this phase reads (spins, B and
+        // M are not read here), so no barrier is needed
+        if (j0 + a.mchunk < WR) __syncthreads();
     }
 }
 
@@ -650,9 +666,10 @@ __global__ void __launch_bounds__(kMaxThreads) int8_run_kernel(const Int8Args a)
             if (a.exchange_every > 0 && (n + 1) % a.exchange_every == 0) {
                 const int64_t e = (n + 1) / a.exchange_every - 1;
                 ++stamp;
-                exchange_decide(sm, cx, a, (int)(e & 1), (uint32_t)n, 0u, stamp);
+                if (threadIdx.x < 32) exchange_decide(sm, cx, a, (int)(e & 1), (uint32_t)n, 0u, stamp);
                 __syncthreads();
-                exchange_apply<L>(sm, cx, stamp);
+                exchange_apply<L>(sm, cx);
+                __syncthreads();
             }
             if (n >= a.n_therm && (n - a.n_therm) % a.measure_every == 0) measure_step<L>(sm, cx, a);
         }
@@ -1013,7 +1030,7 @@ size_t int8_smem_bytes(int L, int Tp, bool gauss, int mchunk, bool gst)
     return b <= (size_t)kMaxSmem ? b : 0;
 }
 
-int int8_max_threads() { return kMaxThreads; }
+int int8_max_threads(int) { return kMaxThreads; }
 
 cudaError_t int8_launch(int L, bool gauss, const Int8Args &a, const Int8Launch &cfg,
                         cudaStream_t st)

@@ -50,7 +50,7 @@ struct Int8Launch {
 // Shared-memory bytes of the fused kernel, or 0 when the state does not fit
 // (or no kernel is built for that L and mode).
 size_t int8_smem_bytes(int L, int Tp, bool gauss, int mchunk, bool gst);
-int int8_max_threads();
+int int8_max_threads(int L);
 // Configure and launch the fused kernel.
 cudaError_t int8_launch(int L, bool gauss, const Int8Args &a, const Int8Launch &cfg,
                         cudaStream_t st);
