@@ -49,9 +49,46 @@ __device__ __forceinline__ void bs_add(uint64_t (&c)[D], const uint64_t (&x)[K])
     }
 }
 
-// Column counts over the 32 lanes of a warp: lane l receives
-// sum over lanes of bit l of x (a 32x32 bit transpose by shuffles, then popc).
-__device__ __forceinline__ int warp_column_popc(uint32_t x)
+// Carry-save adder: three words in, their bitwise sum as (sum, carry).
+__device__ __forceinline__ void csa(uint64_t &h, uint64_t &l, uint64_t a, uint64_t b, uint64_t c)
+{
+    const uint64_t u = a ^ b;
+    h = (a & b) | (u & c);
+    l = u ^ c;
+}
+
+// Bit-sliced population count of 16 words (bitwise, 64 lanes): a carry-save
+// adder tree giving the five bit planes of the per-lane count 0..16.
+__device__ __forceinline__ void count16(const uint64_t (&x)[16], uint64_t (&c)[5])
+{
+    uint64_t s1, c1, s2, c2, s3, c3, s4, c4, s5, c5;
+    csa(c1, s1, x[0], x[1], x[2]);
+    csa(c2, s2, x[3], x[4], x[5]);
+    csa(c3, s3, x[6], x[7], x[8]);
+    csa(c4, s4, x[9], x[10], x[11]);
+    csa(c5, s5, x[12], x[13], x[14]);
+    uint64_t s6, c6, s7, c7;
+    csa(c6, s6, s1, s2, s3);
+    csa(c7, s7, s4, s5, x[15]);
+    c[0] = s6 ^ s7;
+    const uint64_t c8 = s6 & s7;
+    uint64_t t1, d1, t2, d2, t3, d3;  // weight 2: c1..c8
+    csa(d1, t1, c1, c2, c3);
+    csa(d2, t2, c4, c5, c6);
+    csa(d3, t3, c7, c8, t1);
+    c[1] = t2 ^ t3;
+    const uint64_t d4 = t2 & t3;
+    uint64_t f1, e1;  // weight 4: d1..d4
+    csa(e1, f1, d1, d2, d3);
+    c[2] = f1 ^ d4;
+    const uint64_t e2 = f1 & d4;
+    c[3] = e1 ^ e2;  // weight 8
+    c[4] = e1 & e2;  // weight 16
+}
+
+// 32x32 bit transpose across a warp by five shuffle stages: afterwards bit k
+// of lane l's word is bit l of lane k's word before.
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x)
 {
     const int lane = threadIdx.x & 31;
     uint32_t m = 0x0000FFFFu;
@@ -60,8 +97,12 @@ __device__ __forceinline__ int warp_column_popc(uint32_t x)
         const uint32_t y = __shfl_xor_sync(0xFFFFFFFFu, x, k);
         x = (lane & k) ? ((x & ~m) | ((y & ~m) >> k)) : ((x & m) | ((y & m) << k));
     }
-    return __popc(x);
+    return x;
 }
+
+// Column counts over the 32 lanes of a warp: lane l receives the number of
+// lanes whose word has bit l set.
+__device__ __forceinline__ int warp_column_popc(uint32_t x) { return __popc(warp_transpose32(x)); }
 
 struct MscSmem {
     uint64_t *w;        // [4][N]   chains: index q = 2*k + r (k = slot in unit)
@@ -260,7 +301,7 @@ __device__ __forceinline__ void msc_measure(const MscSmem &sm, const MscArgs &a,
     // (A) marginal counts of q = -1 (bit set) over the summed axis
     for (int id = threadIdx.x; id < 3 * LL; id += blockDim.x) {
         const int plane = id / LL, ab = id % LL;
-        const int A = ab / L, Bc = ab % L;
+        const int A = ab % L, Bc = ab / L;  // consecutive lanes: consecutive A
         int base, step;
         if (plane == 0) {        // (x=A, y=Bc), over z
             base = A + L * Bc;
@@ -272,17 +313,21 @@ __device__ __forceinline__ void msc_measure(const MscSmem &sm, const MscArgs &a,
             base = L * A + LL * Bc;
             step = 1;
         }
-        uint64_t cnt[kDG];
+        // along x (plane 2) lanes would hit one bank: each lane starts the
+        // (order-free) column sum at its own offset
+        const int rot = plane == 2 ? (threadIdx.x % L) : 0;
+        uint64_t qs[16];
 #pragma unroll
-        for (int p = 0; p < kDG; ++p) cnt[p] = 0;
-#pragma unroll 4
-        for (int m = 0; m < L; ++m) {
-            const int i = base + m * step;
-            const uint64_t qb[1] = {w0[i] ^ w1[i]};
-            bs_add<kDG, 1>(cnt, qb);
+        for (int m = 0; m < 16; ++m) {
+            int mm = m + rot;
+            if (mm >= L) mm -= L;
+            const int i = base + mm * step;
+            qs[m] = m < L ? (w0[i] ^ w1[i]) : 0ull;
         }
+        uint64_t cnt[kDG];
+        count16(qs, cnt);
 #pragma unroll
-        for (int p = 0; p < kDG; ++p) sm.marg[(size_t)id * kDG + p] = cnt[p];
+        for (int p = 0; p < kDG; ++p) sm.marg[((size_t)plane * LL + A * L + Bc) * kDG + p] = cnt[p];
     }
     __syncthreads();
     // (B) projection counts: sum of L marginal entries per (v, d)
@@ -311,59 +356,64 @@ __device__ __forceinline__ void msc_measure(const MscSmem &sm, const MscArgs &a,
         for (int p = 0; p < kDP; ++p) sm.proj[(size_t)id * kDP + p] = acc[p];
     }
     __syncthreads();
-    // (C) per sample b and wave vector v (v == 9: Q, E and M)
-    for (int id = threadIdx.x; id < 64 * 10; id += blockDim.x) {
-        const int b = id % 64, v = id / 64;
-        const int64_t s = 64 * (int64_t)g + b;
-        double *ac = a.acc + ((size_t)s * a.nt + t) * SG_NACC;
-        // the task's accumulators first: their latency overlaps the extraction
-        double *acv = ac + (v == 9 ? 0 : 9 + 3 * v);
-        const int nacc = v == 9 ? 9 : 3;
-        double old[9];
+    // (C) one warp per (wave vector v, half of the word): lanes 0..8 load the
+    // nine planes of P_v[d] and a bit transpose hands lane b the count of
+    // sample 32*half + b; the lane then runs the FP32 DFT over d in ascending
+    // order and the FP64 accumulation. The v = 0 tasks also produce Q, and
+    // E and M are added straight from the per-sample energies.
+    {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+        for (int task = warp; task < 2 * 9; task += nwarps) {
+            const int v = task >> 1, half = task & 1;
+            const int b = 32 * half + lane;
+            const int64_t s = 64 * (int64_t)g + b;
+            double *ac = a.acc + ((size_t)s * a.nt + t) * SG_NACC;
+            double *acv = ac + 9 + 3 * v;
+            double o0 = acv[0], o1 = acv[1], o2 = acv[2];
+            double q[9];
+            if (v == 0) {
 #pragma unroll
-        for (int q = 0; q < 9; ++q) old[q] = q < nacc ? acv[q] : 0.0;
-        const int vv = v == 9 ? 0 : v;
-        float re = 0.0f, im = 0.0f;
-        int Qi = 0;
-        for (int d = 0; d < L; ++d) {
-            const uint64_t *p = sm.proj + ((size_t)vv * L + d) * kDP;
-            int cnt = 0;
-#pragma unroll
-            for (int k2 = 0; k2 < kDP; ++k2) cnt |= (int)((p[k2] >> b) & 1ull) << k2;
-            const int P = LL - 2 * cnt;
-            Qi += P;
-            re = __fmaf_rn((float)P, a.twid[d], re);
-            im = __fmaf_rn((float)P, a.twid[L + d], im);
-        }
-        if (v == 9) {
-            const double Q = (double)Qi;
-            const double Q2 = __dmul_rn(Q, Q);
-            old[0] = __dadd_rn(old[0], 1.0);
-            old[1] = __dadd_rn(old[1], Q);
-            old[2] = __dadd_rn(old[2], Q2);
-            old[3] = __dadd_rn(old[3], __dmul_rn(Q2, Q));
-            old[4] = __dadd_rn(old[4], __dmul_rn(Q2, Q2));
-            for (int r = 0; r < 2; ++r) {
-                const long long Bv = sm.B[(2 * k + r) * 64 + b];
-                const long long Mv = sm.M[(2 * k + r) * 64 + b];
-                const double e = -__dadd_rn((double)Bv, __dmul_rn(a.h_d, (double)Mv));
-                old[5] = __dadd_rn(old[5], e);
-                old[6] = __dadd_rn(old[6], __dmul_rn(e, e));
+                for (int k2 = 0; k2 < 9; ++k2) q[k2] = ac[k2];
             }
-            for (int r = 0; r < 2; ++r) {
-                const double m = (double)sm.M[(2 * k + r) * 64 + b];
-                old[7] = __dadd_rn(old[7], m);
-                old[8] = __dadd_rn(old[8], __dmul_rn(m, m));
+            float re = 0.0f, im = 0.0f;
+            int Qi = 0;
+            for (int d = 0; d < L; ++d) {
+                const uint64_t *p = sm.proj + ((size_t)v * L + d) * kDP;
+                const uint32_t row = lane < kDP ? (uint32_t)(p[lane] >> (32 * half)) : 0u;
+                const int cnt = (int)(warp_transpose32(row) & ((1u << kDP) - 1));
+                const int P = LL - 2 * cnt;
+                Qi += P;
+                re = __fmaf_rn((float)P, a.twid[d], re);
+                im = __fmaf_rn((float)P, a.twid[L + d], im);
             }
-        } else {
             const double dr = (double)re, di = (double)im;
-            old[0] = __dadd_rn(old[0], dr);
-            old[1] = __dadd_rn(old[1], di);
-            old[2] = __dadd_rn(old[2], __dadd_rn(__dmul_rn(dr, dr), __dmul_rn(di, di)));
-        }
+            acv[0] = __dadd_rn(o0, dr);
+            acv[1] = __dadd_rn(o1, di);
+            acv[2] = __dadd_rn(o2, __dadd_rn(__dmul_rn(dr, dr), __dmul_rn(di, di)));
+            if (v == 0) {
+                const double Q = (double)Qi;
+                const double Q2 = __dmul_rn(Q, Q);
+                q[0] = __dadd_rn(q[0], 1.0);
+                q[1] = __dadd_rn(q[1], Q);
+                q[2] = __dadd_rn(q[2], Q2);
+                q[3] = __dadd_rn(q[3], __dmul_rn(Q2, Q));
+                q[4] = __dadd_rn(q[4], __dmul_rn(Q2, Q2));
+                for (int r = 0; r < 2; ++r) {
+                    const long long Bv = sm.B[(2 * k + r) * 64 + b];
+                    const long long Mv = sm.M[(2 * k + r) * 64 + b];
+                    const double e = -__dadd_rn((double)Bv, __dmul_rn(a.h_d, (double)Mv));
+                    q[5] = __dadd_rn(q[5], e);
+                    q[6] = __dadd_rn(q[6], __dmul_rn(e, e));
+                }
+                for (int r = 0; r < 2; ++r) {
+                    const double m = (double)sm.M[(2 * k + r) * 64 + b];
+                    q[7] = __dadd_rn(q[7], m);
+                    q[8] = __dadd_rn(q[8], __dmul_rn(m, m));
+                }
 #pragma unroll
-        for (int q = 0; q < 9; ++q)
-            if (q < nacc) acv[q] = old[q];
+                for (int k2 = 0; k2 < 9; ++k2) ac[k2] = q[k2];
+            }
+        }
     }
     __syncthreads();
 }
