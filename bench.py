@@ -44,6 +44,11 @@ B_ALG_CONST = 2.0     # int8 spin read + write per attempt, bytes
 B_ALG_COUPLING = 12.0  # three FP32 bonds per site, shared by the 2*N_T chains
 WORKLOAD = ("gaussian EA 3D, L=8 and 12 x h=0.1,0.2,0.3, 512 samples each, "
             "2 replicas x 24 T geometric 0.5-1.6, exchange+measure every sweep")
+# DRAM bytes (read + write) of one launch of the dominant kernel in this
+# workload (L = 12, 512 samples, 256 sweeps), from the one-pass ncu capture
+# summarised in profiles/dram_int8_run_kernel_L12_bench.md. Must be reset to
+# None whenever the kernel changes, until it is captured again.
+TRAFFIC_BYTES_PER_LAUNCH = 58.7e6
 
 
 def parse_args():
@@ -383,7 +388,8 @@ def main():
     achieved = b_alg * dom_att / (dom_ms * 1e6)  # GB/s
     peak, peak_kind = peaks()
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": TRAFFIC_BYTES_PER_LAUNCH,
+                "algorithmic_bytes_per_launch": b_alg * dom_att,
                 "kernel": "int8_run_kernel<L=12, gauss>",
                 "b_alg_bytes_per_attempt": b_alg, "peak_kind": peak_kind,
                 "attempts_per_ns": dom_att / (dom_ms * 1e6)}

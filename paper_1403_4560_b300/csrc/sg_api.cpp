@@ -44,6 +44,24 @@ sg_status cuda_fail(cudaError_t e, const char *where)
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// True when every byte is +1 (0x01) or -1 (0xFF); eight bytes per test:
+// x = w ^ 0x01.. has bytes 0x00 or 0xFE exactly when the spins are valid.
+bool spins_valid(const int8_t *p, size_t n)
+{
+    const uint64_t ones = 0x0101010101010101ull;
+    size_t k = 0;
+    for (; k + 8 <= n; k += 8) {
+        uint64_t w;
+        std::memcpy(&w, p + k, 8);
+        const uint64_t x = w ^ ones;
+        const uint64_t z = (x >> 1) & 0x7F7F7F7F7F7F7F7Full;  // 0x00 or 0x7F per byte
+        if ((x & ones) | ((z + ones) & 0x7E7E7E7E7E7E7E7Eull)) return false;
+    }
+    for (; k < n; ++k)
+        if (p[k] != 1 && p[k] != -1) return false;
+    return true;
+}
+
 }  // namespace
 
 struct sg_ensemble {
@@ -77,6 +95,9 @@ struct sg_ensemble {
     // multispin-coded +-J layout
     bool msc = false;
     uint64_t *W = nullptr, *Jw = nullptr, *masks = nullptr;
+    // device staging of canonical host arrays, allocated on first use
+    void *stage = nullptr;
+    size_t stage_bytes = 0;
 };
 
 namespace {
@@ -276,6 +297,24 @@ MscArgs make_msc_args(sg_ensemble *e)
     return a;
 }
 
+// Staging buffer of at least `bytes` for host <-> canonical-layout copies;
+// grows on demand (after the stream has drained) and lives with the ensemble.
+cudaError_t stage_buffer(sg_ensemble *e, size_t bytes, void **out)
+{
+    if (e->stage_bytes < bytes) {
+        cudaError_t ce = cudaStreamSynchronize(e->stream);
+        if (ce != cudaSuccess) return ce;
+        if (e->stage) cudaFree(e->stage);
+        e->stage = nullptr;
+        e->stage_bytes = 0;
+        ce = cudaMalloc(&e->stage, bytes);
+        if (ce != cudaSuccess) return ce;
+        e->stage_bytes = bytes;
+    }
+    *out = e->stage;
+    return cudaSuccess;
+}
+
 // Host tables: +-J thresholds (FP64 exp of the C library), FP32 -beta and
 // beta differences, FP32 twiddles of the DFT.
 void host_tables(const sg_ensemble *e, std::vector<uint32_t> &thr, std::vector<float> &nb,
@@ -410,12 +449,8 @@ sg_status sg_create_ensemble(int L, double h, const double *T, int nt, sg_coupli
             }
         }
     }
-    if (spins_host) {
-        const size_t ns = (size_t)S * 2 * nt * N;
-        for (size_t k = 0; k < ns; ++k)
-            if (spins_host[k] != 1 && spins_host[k] != -1)
-                return fail(SG_EINVAL, "spins must be +1 or -1");
-    }
+    if (spins_host && !spins_valid(spins_host, (size_t)S * 2 * nt * N))
+        return fail(SG_EINVAL, "spins must be +1 or -1");
 
     sg_ensemble *e = new sg_ensemble();
     e->L = L;
@@ -539,6 +574,7 @@ void sg_destroy(sg_ensemble *e)
     if (e->stream || e->arena) cudaStreamSynchronize(e->stream);
     if (e->branch) cudaStreamSynchronize(e->branch);
     if (e->arena) cudaFree(e->arena);
+    if (e->stage) cudaFree(e->stage);
     if (e->branch) cudaStreamDestroy(e->branch);
     if (e->ev) cudaEventDestroy(e->ev);
     delete e;
@@ -742,12 +778,11 @@ sg_status sg_get_spins(sg_ensemble *e, int8_t *out)
     if (!e || !out) return fail(SG_EINVAL, "bad arguments");
     const size_t bytes = (size_t)e->S * 2 * e->nt * e->L * e->L * e->L;
     int8_t *d = nullptr;
-    SG_CUDA(cudaMalloc(&d, bytes), "cudaMalloc");
+    SG_CUDA(stage_buffer(e, bytes, (void **)&d), "staging buffer");
     cudaError_t ce = e->msc ? msc_export_spins(d, e->W, e->S / 64, e->L, e->nt, e->stream)
                             : int8_export_spins(d, e->spins, e->S, e->L, e->nt, e->Tp, e->stream);
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(out, d, bytes, cudaMemcpyDeviceToHost, e->stream);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(e->stream);
-    cudaFree(d);
     if (ce != cudaSuccess) return cuda_fail(ce, "get spins");
     return SG_OK;
 }
@@ -756,10 +791,9 @@ sg_status sg_set_spins(sg_ensemble *e, const int8_t *in)
 {
     if (!e || !in) return fail(SG_EINVAL, "bad arguments");
     const size_t bytes = (size_t)e->S * 2 * e->nt * e->L * e->L * e->L;
-    for (size_t k = 0; k < bytes; ++k)
-        if (in[k] != 1 && in[k] != -1) return fail(SG_EINVAL, "spins must be +1 or -1");
+    if (!spins_valid(in, bytes)) return fail(SG_EINVAL, "spins must be +1 or -1");
     int8_t *d = nullptr;
-    SG_CUDA(cudaMalloc(&d, bytes), "cudaMalloc");
+    SG_CUDA(stage_buffer(e, bytes, (void **)&d), "staging buffer");
     cudaError_t ce = cudaMemcpyAsync(d, in, bytes, cudaMemcpyHostToDevice, e->stream);
     if (ce == cudaSuccess)
         ce = e->msc ? msc_import_spins(e->W, d, e->S / 64, e->L, e->nt, e->stream)
@@ -768,7 +802,6 @@ sg_status sg_set_spins(sg_ensemble *e, const int8_t *in)
         ce = e->msc ? msc_energies(make_msc_args(e), e->L, e->stream)
                     : int8_energies(make_args(e), e->L, e->gauss, e->stream);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(e->stream);
-    cudaFree(d);
     if (ce != cudaSuccess) return cuda_fail(ce, "set spins");
     return SG_OK;
 }
