@@ -49,6 +49,13 @@ WORKLOAD = ("gaussian EA 3D, L=8 and 12 x h=0.1,0.2,0.3, 512 samples each, "
 # summarised in profiles/dram_int8_run_kernel_L12_bench.md. Must be reset to
 # None whenever the kernel changes, until it is captured again.
 TRAFFIC_BYTES_PER_LAUNCH = 58.7e6
+# Thread instructions per attempt of the same kernel (ncu, smsp__inst_executed
+# x threads per instruction over the launch's attempts; profiles/
+# int8_run_kernel_L12_gauss.md). Reset to None whenever the kernel changes.
+INSTR_PER_ATTEMPT = 86.0
+# SM issue peak: 148 SMs x 4 schedulers x 1 warp instruction per cycle x 32
+# threads x 2.032 GHz (maximum SM clock), in thread instructions per second.
+ISSUE_PEAK = 148 * 4 * 32 * 2.032e9
 
 
 def parse_args():
@@ -393,6 +400,13 @@ def main():
                 "kernel": "int8_run_kernel<L=12, gauss>",
                 "b_alg_bytes_per_attempt": b_alg, "peak_kind": peak_kind,
                 "attempts_per_ns": dom_att / (dom_ms * 1e6)}
+    alu = None
+    if INSTR_PER_ATTEMPT:
+        inst = INSTR_PER_ATTEMPT * dom_att / (dom_ms * 1e-3) / 1e12
+        alu = {"bound": "alu", "achieved": inst, "peak": ISSUE_PEAK / 1e12,
+               "unit": "T thread-instructions/s", "frac": inst / (ISSUE_PEAK / 1e12),
+               "instructions_per_attempt": INSTR_PER_ATTEMPT,
+               "kernel": "int8_run_kernel<L=12, gauss>"}
 
     plain = None
     if not args.no_plain and rank == 0:
@@ -459,7 +473,8 @@ def main():
                            "l2": "state+couplings 206 MB per GPU, larger than L2",
                            "batched": "one CUDA graph per step, 6 parallel branches"},
                 "gpu_launches": n_launch_per_step * K,
-                "roofline": roofline, "plain": plain, "e2e": e2e, "cpu_baseline": cb,
+                "roofline": roofline, "roofline_alu": alu, "plain": plain, "e2e": e2e,
+                "cpu_baseline": cb,
                 "clocks": clk.summary(), "extras": extras}
         print(json.dumps(line), flush=True)
     for e in ens:
