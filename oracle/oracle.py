@@ -85,7 +85,7 @@ def lib():
         L.orc_delta_e.restype = f64
         L.orc_overlap.argtypes = [i32, P, P, P, P, P]
         L.orc_run.argtypes = [i32, i32, i32, f64, P, u64, i32, i32, i32, i64, i64, i64,
-                              i64, i64, i64, P, P, P, P, P]
+                              i64, i64, i64, P, P, P, P, i32, P, P]
         L.orc_run.restype = i32
         L.orc_exchange.argtypes = [i32, i32, i32, f64, P, u64, i64, i32, i64, i64, i64, P, P,
                                    P, P]
@@ -176,8 +176,13 @@ class State:
     """Host-side state of one oracle ensemble (canonical layouts)."""
 
     def __init__(self, L, T, h, gauss, seed, J, spins, rng_group=1, exchange_every=1,
-                 measure_every=1, n_therm=0, s_base=0):
-        """Local sample k is the global sample s_base + k (its RNG key)."""
+                 measure_every=1, n_therm=0, s_base=0, log_bins=1, pq_hist=False):
+        """Local sample k is the global sample s_base + k (its RNG key).
+
+        log_bins: accumulators per logarithmic sweep bin (acc then has shape
+        [S][n_T][log_bins][40]; 1 keeps [S][n_T][40]). pq_hist: also count
+        the overlap histogram hist[n_T][log_bins][N+1] (entry k: replicas
+        agree on k sites)."""
         self.s_base = int(s_base)
         self.L, self.h, self.gauss, self.seed = L, float(h), bool(gauss), int(seed)
         self.T = np.ascontiguousarray(T, dtype=np.float64)
@@ -189,7 +194,12 @@ class State:
         self.measure_every, self.n_therm = measure_every, n_therm
         self.B = np.zeros((self.S, 2, self.nt), dtype=np.int64)
         self.M = np.zeros((self.S, 2, self.nt), dtype=np.int64)
-        self.acc = np.zeros((self.S, self.nt, NACC), dtype=np.float64)
+        self.log_bins = int(log_bins)
+        shape = (self.S, self.nt, NACC) if self.log_bins == 1 else (self.S, self.nt, self.log_bins, NACC)
+        self.acc = np.zeros(shape, dtype=np.float64)
+        N = L ** 3
+        self.hist = (np.zeros((self.nt, self.log_bins, N + 1), dtype=np.uint64) if pq_hist
+                     else None)
         self.sweeps_done = 0
         self.exchanges_done = 0
 
@@ -199,19 +209,27 @@ class State:
         L = lib()
 
         def work(a, b):
+            # each call counts into its own histogram; the parts are summed below
+            h = None if self.hist is None else np.zeros_like(self.hist)
             rc = L.orc_run(self.L, self.nt, int(self.gauss), self.h, _p(self.T), self.seed,
                            self.rng_group, self.exchange_every, self.measure_every,
                            self.n_therm, self.sweeps_done, n_sweeps, self.s_base, a, b, _p(self.J),
-                           _p(self.spins), _p(self.B), _p(self.M), _p(self.acc))
+                           _p(self.spins), _p(self.B), _p(self.M), self.log_bins, _p(self.acc),
+                           None if h is None else _p(h))
             if rc != 0:
                 raise ValueError("oracle rejected its arguments")
+            return h
 
         if threads <= 1:
-            work(s0, s1)
+            parts = [work(s0, s1)]
         else:
             cuts = np.linspace(s0, s1, threads + 1).astype(np.int64)
             with ThreadPoolExecutor(threads) as ex:
-                list(ex.map(lambda ab: work(int(ab[0]), int(ab[1])), zip(cuts[:-1], cuts[1:])))
+                parts = list(ex.map(lambda ab: work(int(ab[0]), int(ab[1])),
+                                    zip(cuts[:-1], cuts[1:])))
+        if self.hist is not None:
+            for h in parts:
+                self.hist += h
         if s_range is None:
             self.sweeps_done += n_sweeps
 

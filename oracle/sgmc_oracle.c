@@ -13,7 +13,10 @@
  *   simple cubic lattice, bimodal couplings);
  *   overlap q(k), eq. (overlap);
  *   parallel tempering with two replicas per temperature (methods section);
- *   thermalise-then-measure split (Table I caption).
+ *   thermalise-then-measure split (Table I caption);
+ *   the logarithmic-binning equilibration test (caption of the figure of R12
+ *   against the number of sweeps) and the distribution P(q) of the overlap
+ *   (conclusion).
  *
  * Parity pins (tests/): L = 2 exact enumeration of Boltzmann averages and of
  * the one-sweep transition matrix, gauge and global-flip symmetries,
@@ -374,19 +377,39 @@ static void exchange_step(const chain_params *cp, int64_t s, int parity, uint32_
         }
 }
 
+/* Logarithmic bin of the measurement taken at global sweep n (0-based):
+ * floor(log2(n + 1)), the last bin also holding every later sweep. Bin b
+ * thus covers sweeps 2^b - 1 ... 2^(b+1) - 2, the second half of a run of
+ * 2^(b+1) sweeps. */
+static int log_bin(int64_t n, int n_bins)
+{
+    int b = 0;
+    while (b + 1 < n_bins && ((n + 1) >> (b + 1)) != 0) ++b;
+    return b;
+}
+
+/* One measurement of every slot of one sample at sweep n. acc is the
+ * sample's [nt][n_bins][40] block; hist (may be NULL) is [nt][n_bins][N+1]
+ * and entry k of a (slot, bin) counts measurements whose replicas agree on
+ * exactly k sites, i.e. whose overlap is q = (2k - N) / N. */
 static void measure(const chain_params *cp, const int8_t *sp, const int64_t *B,
-                    const int64_t *M, double *acc /* [nt][40] */)
+                    const int64_t *M, int n_bins, int bin, double *acc, uint64_t *hist)
 {
     int L = cp->L, N = L * L * L, nt = cp->nt;
     double qJ = cp->gauss ? (1.0 / 131072.0) : 1.0;
     double h = cp->gauss ? gauss_field(cp->h) : cp->h;
     for (int t = 0; t < nt; ++t) {
-        double *a = acc + (size_t)t * ORC_NACC;
+        double *a = acc + ((size_t)t * n_bins + bin) * ORC_NACC;
         const int8_t *s0 = sp + ((int64_t)0 * nt + t) * N;
         const int8_t *s1 = sp + ((int64_t)1 * nt + t) * N;
         int64_t Q;
         float re[9], im[9];
         orc_overlap(L, s0, s1, &Q, re, im);
+        if (hist) {
+            int64_t agree = 0;
+            for (int i = 0; i < N; ++i) agree += s0[i] == s1[i];
+            hist[((size_t)t * n_bins + bin) * (N + 1) + agree] += 1;
+        }
         double q = (double)Q;
         a[0] += 1.0;
         a[1] += q;
@@ -441,16 +464,20 @@ static void make_params(chain_params *cp, int L, int nt, int gauss, double h,
  * [s_begin, s_end); local sample k is the global sample s_base + k (the index
  * that keys its random numbers).
  * J [S][3][N] float; spins [S][2][nt][N] int8 in/out; B, M [S][2][nt] out
- * (state after the last sweep); acc [S][nt][40] in/out.
+ * (state after the last sweep); acc [S][nt][n_bins][40] in/out, a sweep's
+ * measurement going to its logarithmic bin (n_bins = 1: one bin); hist
+ * [nt][n_bins][N+1] in/out or NULL, summed over the samples run here (the
+ * caller gives concurrent calls separate arrays).
  * Returns 0, or -1 for invalid arguments.
  */
 int orc_run(int L, int nt, int gauss, double h, const double *T, uint64_t seed,
             int rng_group, int exchange_every, int measure_every, int64_t n_therm,
             int64_t sweep0, int64_t n_sweeps, int64_t s_base, int64_t s_begin, int64_t s_end,
-            const float *J, int8_t *spins, int64_t *B, int64_t *M, double *acc)
+            const float *J, int8_t *spins, int64_t *B, int64_t *M, int n_bins, double *acc,
+            uint64_t *hist)
 {
     if (L < 2 || (L & 1) || nt < 1 || nt > 4096 || rng_group < 1 || measure_every < 1 ||
-        exchange_every < 0)
+        exchange_every < 0 || n_bins < 1 || n_bins > 64)
         return -1;
     int N = L * L * L;
     uint32_t *thr = (uint32_t *)malloc(sizeof(uint32_t) * 14 * (size_t)nt);
@@ -462,7 +489,7 @@ int orc_run(int L, int nt, int gauss, double h, const double *T, uint64_t seed,
         const float *Js = J + s * 3 * (int64_t)N;
         int8_t *sp = spins + s * 2 * (int64_t)nt * N;
         int64_t *Bs = B + s * 2 * nt, *Ms = M + s * 2 * nt;
-        double *as = acc + s * (int64_t)nt * ORC_NACC;
+        double *as = acc + s * (int64_t)nt * n_bins * ORC_NACC;
         energies(&cp, Js, sp, Bs, Ms);
         for (int64_t n = sweep0; n < sweep0 + n_sweeps; ++n) {
             one_sweep_metropolis(&cp, s_base + s, n, Js, sp);
@@ -472,7 +499,7 @@ int orc_run(int L, int nt, int gauss, double h, const double *T, uint64_t seed,
                 exchange_step(&cp, s_base + s, (int)(e & 1), (uint32_t)n, 0u, Js, sp, Bs, Ms);
             }
             if (n >= n_therm && (n - n_therm) % measure_every == 0)
-                measure(&cp, sp, Bs, Ms, as);
+                measure(&cp, sp, Bs, Ms, n_bins, log_bin(n, n_bins), as, hist);
         }
     }
     free(thr);
