@@ -21,9 +21,15 @@
  *       energies   int64  [S][2][n_T]    B = sum_bonds (J/qJ) s s (qJ = 1 for
  *                                        +-J, 2^-17 for Gaussian couplings);
  *                                        M = sum_i s_i;  E = -(qJ*B + h*M)
- *       accumulators double [S][n_T][40] sweep sums of the measurements; the
- *                                        index table is listed at
- *                                        SG_ACC_* below
+ *       accumulators double [S][n_T][B][40] sweep sums of the measurements
+ *                                        per logarithmic sweep bin (B =
+ *                                        sg_options.log_bins, 1 by default,
+ *                                        which is [S][n_T][40]); the index
+ *                                        table is listed at SG_ACC_* below
+ *       histogram  uint64 [n_T][B][N+1]  optional overlap histogram: entry k
+ *                                        counts measurements (all samples)
+ *                                        whose two replicas agree on k sites,
+ *                                        i.e. q = (2k - N) / N
  *   - Every call that launches work is asynchronous on the ensemble's CUDA
  *     stream (the cudaStream_t passed at creation, 0 = legacy default
  *     stream). Calls that return host data synchronise that stream first.
@@ -104,10 +110,22 @@ typedef struct {
                                   shards (one per GPU) reproduces the
                                   unsplit run exactly; 0 by default; a
                                   multiple of 64 for MSC64                   */
+    int32_t log_bins;          /* accumulator bins B over the global sweep
+                                  index n: 0 or 1 = one bin; B >= 2 sends the
+                                  measurement of sweep n to bin
+                                  min(floor(log2(n + 1)), B - 1), so bin b
+                                  holds sweeps 2^b - 1 .. 2^(b+1) - 2, the
+                                  second half of a run of 2^(b+1) sweeps (the
+                                  logarithmic-binning equilibration test of
+                                  the paper's R12-against-sweeps figure);
+                                  at most 64                                 */
+    int32_t pq_hist;           /* nonzero: also count the overlap histogram
+                                  P(q) per slot and bin (sg_get_histogram)   */
 } sg_options;
 
 /* Fill *opt with the defaults: INT8 layout, rng_group 1, exchange and
- * measure every sweep, n_therm 0, library-chosen launch shape, no watchdog. */
+ * measure every sweep, n_therm 0, library-chosen launch shape, no watchdog,
+ * one accumulator bin, no histogram. */
 void sg_options_default(sg_options *opt);
 
 /* Number of device bytes sg_create_ensemble allocates for this problem
@@ -205,10 +223,22 @@ sg_status sg_measure(sg_ensemble *e, const int *k, int nk, float *out);
 #define SG_MEASURE_NOALLOC_MAX_FLOATS (1 << 20)
 sg_status sg_measure_noalloc(sg_ensemble *e, const int *k, int nk, float *out);
 
-/* Copy the accumulators (canonical layout) to a host array. */
+/* Copy the accumulators (canonical layout, [S][n_T][B][40]) to a host array. */
 sg_status sg_get_accumulators(sg_ensemble *e, double *acc_out);
-/* Zero the accumulators. */
+/* Zero the accumulators and the overlap histogram. */
 sg_status sg_reset_accumulators(sg_ensemble *e);
+/*
+ * Overlap histogram (the distribution P(q) the paper's conclusion proposes
+ * to analyse), counted in the fused measurement when sg_options.pq_hist was
+ * set: host array uint64 [n_T][B][N+1]; entry k of (slot t, bin b) counts the
+ * measurements of every sample at temperature T[t] in sweep bin b whose
+ * replicas agree on k sites (q = (2k - N)/N). Integer counts, so the result
+ * does not depend on the order of the device's atomic additions. SG_EINVAL
+ * if the ensemble keeps no histogram. sg_set_histogram restores one
+ * (checkpoint); shards of one run add their histograms.
+ */
+sg_status sg_get_histogram(sg_ensemble *e, uint64_t *hist_out);
+sg_status sg_set_histogram(sg_ensemble *e, const uint64_t *hist_host);
 /* Copy the current spins (canonical layout, +-1) to a host array. */
 sg_status sg_get_spins(sg_ensemble *e, int8_t *spins_out);
 /* Replace the current spins from a host array (canonical layout, +-1). */
@@ -253,6 +283,8 @@ typedef struct {
     double h;          /* field actually used (rounded for Gaussian)   */
     int64_t attempts_per_sweep; /* N * 2 * n_T * n_samples           */
     size_t device_bytes;
+    int32_t log_bins;  /* accumulator bins B (>= 1)                    */
+    int32_t pq_hist;   /* 1 if the overlap histogram is kept           */
 } sg_info;
 sg_status sg_get_info(const sg_ensemble *e, sg_info *out);
 
@@ -274,8 +306,11 @@ typedef struct {
     double *q4, *q4_err;           /* [<q(0)^4>]                           */
 } sg_observables;
 sg_status sg_results(sg_ensemble *e, const sg_observables *out);
+/* The same for one sweep bin 0 <= bin < B (sg_results uses the last bin);
+ * comparing successive bins is the logarithmic-binning equilibration test. */
+sg_status sg_results_bin(sg_ensemble *e, int bin, const sg_observables *out);
 
-/* The same estimators on a host accumulator array [S][n_T][40]. */
+/* The same estimators on a host accumulator array [S][n_T][40] (one bin). */
 sg_status sg_observables_from_acc(const double *acc, int64_t n_samples, int n_T, int L,
                                   const sg_observables *out);
 

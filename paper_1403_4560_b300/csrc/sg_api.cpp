@@ -83,6 +83,9 @@ struct sg_ensemble {
     float *Jg = nullptr;
     int64_t *B = nullptr, *M = nullptr;
     double *acc = nullptr;
+    unsigned long long *hist = nullptr;  // [nt][n_bins][N+1] or null
+    int n_bins = 1;
+    size_t acc_bytes = 0, hist_bytes = 0;  // acc, then hist right after it
     uint32_t *thr = nullptr;
     float *negbeta = nullptr, *dbeta = nullptr, *twid = nullptr;
     int *status = nullptr;
@@ -123,10 +126,13 @@ void purge_graphs(sg_ensemble *e)
 }
 
 struct ArenaPlan {
-    size_t spins, J, BM, acc, thr, tab, twid, misc, total;
+    size_t spins, J, BM, acc, hist, thr, tab, twid, misc, total;
 };
 
-ArenaPlan plan_arena(int L, int nt, int Tp, int64_t S, bool gauss, bool msc)
+int bins_of(const sg_options &o) { return o.log_bins > 1 ? o.log_bins : 1; }
+
+ArenaPlan plan_arena(int L, int nt, int Tp, int64_t S, bool gauss, bool msc, int n_bins,
+                     bool hist)
 {
     const size_t N = (size_t)L * L * L;
     ArenaPlan p;
@@ -139,12 +145,13 @@ ArenaPlan plan_arena(int L, int nt, int Tp, int64_t S, bool gauss, bool msc)
         p.J = align256(gauss ? (size_t)S * 3 * N * sizeof(float) : (size_t)S * N * 8);
     }
     p.BM = align256((size_t)S * 2 * Tp * sizeof(int64_t));
-    p.acc = align256((size_t)S * nt * SG_NACC * sizeof(double));
+    p.acc = align256((size_t)S * nt * n_bins * SG_NACC * sizeof(double));
+    p.hist = hist ? align256((size_t)nt * n_bins * (N + 1) * sizeof(uint64_t)) : 0;
     p.thr = align256((size_t)Tp * 16 * sizeof(uint32_t));
     p.tab = align256((size_t)Tp * sizeof(float));
     p.twid = align256((size_t)2 * L * sizeof(float));
     p.misc = 256 + (msc ? align256((size_t)(S / 64) * 2 * nt * 8) : 0);
-    p.total = p.spins + p.J + 2 * p.BM + p.acc + p.thr + 2 * p.tab + p.twid + p.misc;
+    p.total = p.spins + p.J + 2 * p.BM + p.acc + p.hist + p.thr + 2 * p.tab + p.twid + p.misc;
     return p;
 }
 
@@ -240,6 +247,8 @@ Int8Args make_args(sg_ensemble *e)
     a.B = e->B;
     a.M = e->M;
     a.acc = e->acc;
+    a.hist = e->hist;
+    a.n_bins = e->n_bins;
     a.thr = e->thr;
     a.negbeta = e->negbeta;
     a.dbeta = e->dbeta;
@@ -278,6 +287,8 @@ MscArgs make_msc_args(sg_ensemble *e)
     a.B = e->B;
     a.M = e->M;
     a.acc = e->acc;
+    a.hist = e->hist;
+    a.n_bins = e->n_bins;
     a.thr = e->thr;
     a.dbeta = e->dbeta;
     a.twid = e->twid;
@@ -369,6 +380,7 @@ sg_status validate(int L, const double *T, int nt, sg_coupling dist, int64_t S,
         return fail(SG_EINVAL, "unknown layout");
     if (o.sample_base < 0 || o.sample_base + S > ((int64_t)1 << 32))
         return fail(SG_EINVAL, "sample_base + n_samples must be in [0, 2^32]");
+    if (o.log_bins < 0 || o.log_bins > 64) return fail(SG_EINVAL, "log_bins must be in [0, 64]");
     if (o.layout == SG_LAYOUT_MSC64) {
         if (dist != SG_PM_J) return fail(SG_EINVAL, "the MSC64 layout needs +-J couplings");
         if (o.sample_base % 64) return fail(SG_EINVAL, "the MSC64 layout needs sample_base % 64 == 0");
@@ -419,7 +431,8 @@ size_t sg_ensemble_bytes(int L, int nt, int64_t S, sg_coupling dist, const sg_op
     for (size_t k = 0; k < T.size(); ++k) T[k] = 1.0 + (double)k;
     if (validate(L, T.data(), nt, dist, S, o) != SG_OK) return 0;
     const bool msc = o.layout == SG_LAYOUT_MSC64;
-    return plan_arena(L, nt, msc ? nt : pad_slots(nt), S, dist == SG_GAUSS, msc).total;
+    return plan_arena(L, nt, msc ? nt : pad_slots(nt), S, dist == SG_GAUSS, msc, bins_of(o),
+                      o.pq_hist != 0).total;
 }
 
 sg_status sg_create_ensemble(int L, double h, const double *T, int nt, sg_coupling dist,
@@ -476,7 +489,8 @@ sg_status sg_create_ensemble(int L, double h, const double *T, int nt, sg_coupli
     cudaDeviceGetAttribute(&e->num_sms, cudaDevAttrMultiProcessorCount, e->device);
     if (!e->msc && (st = configure_launch(e)) != SG_OK) return bail(st);
 
-    const ArenaPlan p = plan_arena(L, nt, e->Tp, S, gauss, e->msc);
+    e->n_bins = bins_of(o);
+    const ArenaPlan p = plan_arena(L, nt, e->Tp, S, gauss, e->msc, e->n_bins, o.pq_hist != 0);
     ce = cudaMalloc(&e->arena, p.total);
     if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaMalloc(ensemble)"));
     e->bytes = p.total;
@@ -493,6 +507,12 @@ sg_status sg_create_ensemble(int L, double h, const double *T, int nt, sg_coupli
     e->B = (int64_t *)(base + off); off += p.BM;
     e->M = (int64_t *)(base + off); off += p.BM;
     e->acc = (double *)(base + off); off += p.acc;
+    e->acc_bytes = (size_t)S * nt * e->n_bins * SG_NACC * sizeof(double);
+    if (p.hist) {
+        e->hist = (unsigned long long *)(base + off);
+        e->hist_bytes = (size_t)nt * e->n_bins * (N + 1) * sizeof(uint64_t);
+    }
+    off += p.hist;
     e->thr = (uint32_t *)(base + off); off += p.thr;
     e->negbeta = (float *)(base + off); off += p.tab;
     e->dbeta = (float *)(base + off); off += p.tab;
@@ -514,7 +534,7 @@ sg_status sg_create_ensemble(int L, double h, const double *T, int nt, sg_coupli
     auto run = [&]() -> cudaError_t {
         cudaError_t r;
         if ((r = cudaMemsetAsync(e->status, 0, 256, s)) != cudaSuccess) return r;
-        if ((r = cudaMemsetAsync(e->acc, 0, p.acc, s)) != cudaSuccess) return r;
+        if ((r = cudaMemsetAsync(e->acc, 0, p.acc + p.hist, s)) != cudaSuccess) return r;
         if ((r = cudaMemcpyAsync(e->thr, thr.data(), thr.size() * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess) return r;
         if ((r = cudaMemcpyAsync(e->negbeta, nb.data(), nb.size() * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess) return r;
         if ((r = cudaMemcpyAsync(e->dbeta, db.data(), db.size() * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess) return r;
@@ -750,8 +770,8 @@ sg_status sg_measure_noalloc(sg_ensemble *e, const int *k, int nk, float *out)
 sg_status sg_get_accumulators(sg_ensemble *e, double *out)
 {
     if (!e || !out) return fail(SG_EINVAL, "bad arguments");
-    SG_CUDA(cudaMemcpyAsync(out, e->acc, (size_t)e->S * e->nt * SG_NACC * sizeof(double),
-                            cudaMemcpyDeviceToHost, e->stream), "copy accumulators");
+    SG_CUDA(cudaMemcpyAsync(out, e->acc, e->acc_bytes, cudaMemcpyDeviceToHost, e->stream),
+            "copy accumulators");
     SG_CUDA(cudaStreamSynchronize(e->stream), "sync");
     return SG_OK;
 }
@@ -759,8 +779,8 @@ sg_status sg_get_accumulators(sg_ensemble *e, double *out)
 sg_status sg_set_accumulators(sg_ensemble *e, const double *in)
 {
     if (!e || !in) return fail(SG_EINVAL, "bad arguments");
-    SG_CUDA(cudaMemcpyAsync(e->acc, in, (size_t)e->S * e->nt * SG_NACC * sizeof(double),
-                            cudaMemcpyHostToDevice, e->stream), "copy accumulators");
+    SG_CUDA(cudaMemcpyAsync(e->acc, in, e->acc_bytes, cudaMemcpyHostToDevice, e->stream),
+            "copy accumulators");
     SG_CUDA(cudaStreamSynchronize(e->stream), "sync");
     return SG_OK;
 }
@@ -768,8 +788,28 @@ sg_status sg_set_accumulators(sg_ensemble *e, const double *in)
 sg_status sg_reset_accumulators(sg_ensemble *e)
 {
     if (!e) return fail(SG_EINVAL, "ensemble is NULL");
-    SG_CUDA(cudaMemsetAsync(e->acc, 0, (size_t)e->S * e->nt * SG_NACC * sizeof(double), e->stream),
-            "memset");
+    SG_CUDA(cudaMemsetAsync(e->acc, 0, e->acc_bytes, e->stream), "memset");
+    if (e->hist) SG_CUDA(cudaMemsetAsync(e->hist, 0, e->hist_bytes, e->stream), "memset");
+    return SG_OK;
+}
+
+sg_status sg_get_histogram(sg_ensemble *e, uint64_t *out)
+{
+    if (!e || !out) return fail(SG_EINVAL, "bad arguments");
+    if (!e->hist) return fail(SG_EINVAL, "the ensemble keeps no overlap histogram (pq_hist)");
+    SG_CUDA(cudaMemcpyAsync(out, e->hist, e->hist_bytes, cudaMemcpyDeviceToHost, e->stream),
+            "copy histogram");
+    SG_CUDA(cudaStreamSynchronize(e->stream), "sync");
+    return SG_OK;
+}
+
+sg_status sg_set_histogram(sg_ensemble *e, const uint64_t *in)
+{
+    if (!e || !in) return fail(SG_EINVAL, "bad arguments");
+    if (!e->hist) return fail(SG_EINVAL, "the ensemble keeps no overlap histogram (pq_hist)");
+    SG_CUDA(cudaMemcpyAsync(e->hist, in, e->hist_bytes, cudaMemcpyHostToDevice, e->stream),
+            "copy histogram");
+    SG_CUDA(cudaStreamSynchronize(e->stream), "sync");
     return SG_OK;
 }
 
@@ -872,6 +912,8 @@ sg_status sg_get_info(const sg_ensemble *e, sg_info *out)
     out->h = e->h_used;
     out->attempts_per_sweep = (int64_t)e->L * e->L * e->L * 2 * e->nt * e->S;
     out->device_bytes = e->bytes;
+    out->log_bins = e->n_bins;
+    out->pq_hist = e->hist ? 1 : 0;
     return SG_OK;
 }
 
@@ -905,7 +947,9 @@ sg_status sg_autotune(sg_ensemble *e, int64_t trial_sweeps, sg_tune_report *rep)
     const size_t N = (size_t)e->L * e->L * e->L;
     const size_t sp_bytes = (size_t)e->S * N * 2 * e->Tp;
     const size_t bm_bytes = (size_t)e->S * 2 * e->Tp * sizeof(int64_t);
-    const size_t acc_bytes = (size_t)e->S * e->nt * SG_NACC * sizeof(double);
+    // the histogram sits right after the accumulators: one copy saves both
+    const size_t acc_bytes = e->hist ? (size_t)((uint8_t *)e->hist - (uint8_t *)e->acc) + e->hist_bytes
+                                     : e->acc_bytes;
     uint8_t *backup = nullptr;
     SG_CUDA(cudaMalloc(&backup, sp_bytes + 2 * bm_bytes + acc_bytes), "autotune backup");
     auto save = [&](bool restore) {
@@ -1011,13 +1055,26 @@ sg_status sg_autotune(sg_ensemble *e, int64_t trial_sweeps, sg_tune_report *rep)
     return SG_OK;
 }
 
-sg_status sg_results(sg_ensemble *e, const sg_observables *out)
+sg_status sg_results_bin(sg_ensemble *e, int bin, const sg_observables *out)
 {
     if (!e || !out) return fail(SG_EINVAL, "bad arguments");
-    std::vector<double> acc((size_t)e->S * e->nt * SG_NACC);
+    if (bin < 0 || bin >= e->n_bins) return fail(SG_EINVAL, "bin out of range");
+    const size_t per = (size_t)e->S * e->nt;
+    std::vector<double> acc(per * e->n_bins * SG_NACC);
     sg_status st = sg_get_accumulators(e, acc.data());
     if (st != SG_OK) return st;
+    if (e->n_bins > 1) {  // gather the bin into [S][n_T][40]
+        for (size_t k = 0; k < per; ++k)
+            std::memmove(acc.data() + k * SG_NACC,
+                         acc.data() + (k * e->n_bins + bin) * SG_NACC, SG_NACC * sizeof(double));
+    }
     return sg_observables_from_acc(acc.data(), e->S, e->nt, e->L, out);
+}
+
+sg_status sg_results(sg_ensemble *e, const sg_observables *out)
+{
+    if (!e) return fail(SG_EINVAL, "ensemble is NULL");
+    return sg_results_bin(e, e->n_bins - 1, out);
 }
 
 }  // extern "C"

@@ -87,4 +87,14 @@ __device__ __forceinline__ uint32_t thr_of_logp(float x)
     return __float2uint_rz(exp_cw32_scaled<32>(xc));
 }
 
+// Logarithmic bin of a measurement taken at global sweep n (0-based):
+// floor(log2(n + 1)), with every later sweep in the last of n_bins bins. Bin b
+// covers sweeps 2^b - 1 .. 2^(b+1) - 2, the second half of a run of 2^(b+1)
+// sweeps (the logarithmic-binning equilibration test).
+__device__ __forceinline__ int log_bin(int64_t n, int n_bins)
+{
+    const int b = 63 - __clzll((long long)(n + 1));
+    return b < n_bins - 1 ? b : n_bins - 1;
+}
+
 }  // namespace sg

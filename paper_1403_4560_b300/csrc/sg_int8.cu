@@ -447,15 +447,18 @@ __device__ __forceinline__ void count_pattern(const uint32_t *pm, int nw, int sh
 // together with Q, E and M. Processed mchunk 4-slot groups at a time.
 // ---------------------------------------------------------------------------
 template <int L>
-__device__ __forceinline__ void measure_step(const Smem &sm, const Ctx &cx, const Int8Args &a)
+__device__ __forceinline__ void measure_step(const Smem &sm, const Ctx &cx, const Int8Args &a,
+                                             int bin)
 {
     constexpr int LL = L * L;
     const int WR = cx.WR, RB = cx.RB, Tp = cx.Tp, nt = cx.nt;
-    double *accs = a.acc + (size_t)cx.s * nt * SG_NACC;
+    // accumulators of (sample, slot t, bin): accs + t * tstride
+    const size_t tstride = (size_t)a.n_bins * SG_NACC;
+    double *accs = a.acc + ((size_t)cx.s * nt * a.n_bins + bin) * SG_NACC;
     // energies and magnetisations first (one thread per slot), so that the
     // projection phase reads nothing the next sweep overwrites
     for (int t = threadIdx.x; t < nt; t += blockDim.x) {
-        double *ac = accs + (size_t)t * SG_NACC;
+        double *ac = accs + (size_t)t * tstride;
         double o5 = ac[5], o6 = ac[6], o7 = ac[7], o8 = ac[8];
         for (int r = 0; r < 2; ++r) {
             const long long Bv = (long long)sm.B[r * Tp + t];
@@ -516,7 +519,7 @@ __device__ __forceinline__ void measure_step(const Smem &sm, const Ctx &cx, cons
             const int t = 4 * j0 + sl;
             if (t >= nt) continue;
             const int jj = sl >> 2, sh = 8 * (sl & 3);
-            double *ac = accs + (size_t)t * SG_NACC;
+            double *ac = accs + (size_t)t * tstride;
             double *acv = ac + (v == 9 ? 0 : 9 + 3 * v);
             const int nacc = v == 9 ? 5 : 3;
             double old[9];
@@ -541,6 +544,9 @@ __device__ __forceinline__ void measure_step(const Smem &sm, const Ctx &cx, cons
                 int Qi = 0;
 #pragma unroll
                 for (int d = 0; d < L; ++d) Qi += LL - 2 * cs[d];
+                if (a.hist)  // P(q): replicas agree on (N + Q) / 2 sites
+                    atomicAdd(a.hist + ((size_t)t * a.n_bins + bin) * (L * LL + 1) + ((L * LL + Qi) >> 1),
+                              1ull);
                 const double Q = (double)Qi;
                 const double Q2 = __dmul_rn(Q, Q);
                 old[0] = __dadd_rn(old[0], 1.0);
@@ -671,7 +677,8 @@ __global__ void __launch_bounds__(kMaxThreads) int8_run_kernel(const Int8Args a)
                 exchange_apply<L>(sm, cx);
                 __syncthreads();
             }
-            if (n >= a.n_therm && (n - a.n_therm) % a.measure_every == 0) measure_step<L>(sm, cx, a);
+            if (n >= a.n_therm && (n - a.n_therm) % a.measure_every == 0)
+                measure_step<L>(sm, cx, a, log_bin(n, a.n_bins));
         }
         __syncthreads();
         if (!GST) copy16(a.spins + (size_t)s * N * cx.RB, sm.spins, (size_t)N * cx.RB);

@@ -17,7 +17,9 @@ struct Int8Args {
     const float *Jg;       // [S][3][N] Gaussian couplings
     int64_t *B;            // [S][2][Tp] bond sums of the current configuration
     int64_t *M;            // [S][2][Tp] magnetisations
-    double *acc;           // [S][nt][40] measurement accumulators
+    double *acc;           // [S][nt][n_bins][40] measurement accumulators
+    unsigned long long *hist;  // [nt][n_bins][N+1] overlap histogram, or null
+    int n_bins;            // logarithmic sweep bins (1 = a single bin)
     const uint32_t *thr;   // [Tp][16] +-J thresholds, entry sb*8 + u
     const float *negbeta;  // [Tp] -(float)beta_t (0 for padding slots)
     const float *dbeta;    // [Tp] (float)(beta_t - beta_{t+1})

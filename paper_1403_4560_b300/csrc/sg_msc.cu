@@ -292,7 +292,7 @@ __device__ __forceinline__ void msc_half(const MscSmem &sm, const MscArgs &a, in
 // ---------------------------------------------------------------------------
 template <int L>
 __device__ __forceinline__ void msc_measure(const MscSmem &sm, const MscArgs &a, int g, int k,
-                                            int t)
+                                            int t, int bin)
 {
     constexpr int N = L * L * L;
     constexpr int LL = L * L;
@@ -367,7 +367,7 @@ __device__ __forceinline__ void msc_measure(const MscSmem &sm, const MscArgs &a,
             const int v = task >> 1, half = task & 1;
             const int b = 32 * half + lane;
             const int64_t s = 64 * (int64_t)g + b;
-            double *ac = a.acc + ((size_t)s * a.nt + t) * SG_NACC;
+            double *ac = a.acc + (((size_t)s * a.nt + t) * a.n_bins + bin) * SG_NACC;
             double *acv = ac + 9 + 3 * v;
             double o0 = acv[0], o1 = acv[1], o2 = acv[2];
             double q[9];
@@ -391,6 +391,8 @@ __device__ __forceinline__ void msc_measure(const MscSmem &sm, const MscArgs &a,
             acv[1] = __dadd_rn(o1, di);
             acv[2] = __dadd_rn(o2, __dadd_rn(__dmul_rn(dr, dr), __dmul_rn(di, di)));
             if (v == 0) {
+                if (a.hist)  // P(q): replicas agree on (N + Q) / 2 sites
+                    atomicAdd(a.hist + ((size_t)t * a.n_bins + bin) * (N + 1) + ((N + Qi) >> 1), 1ull);
                 const double Q = (double)Qi;
                 const double Q2 = __dmul_rn(Q, Q);
                 q[0] = __dadd_rn(q[0], 1.0);
@@ -499,7 +501,7 @@ __global__ void __launch_bounds__(kMscThreads) msc_sweep_kernel(const MscArgs a)
         __syncthreads();
     }
     if (meas)
-        for (int k = 0; k < cnt; ++k) msc_measure<L>(sm, a, g, k, t0 + k);
+        for (int k = 0; k < cnt; ++k) msc_measure<L>(sm, a, g, k, t0 + k, log_bin(n, a.n_bins));
 
     uint64_t *dst = a.W + ((size_t)g * a.nt + t0) * 2 * N;
     for (int k = threadIdx.x; k < nq * N; k += blockDim.x) dst[k] = sm.w[k];

@@ -12,7 +12,9 @@ struct MscArgs {
     uint64_t *W;          // [G][nt][2][N] spin words, bit b = sample 64g + b
     const uint64_t *Jw;   // [G][3][N] coupling words, bit 1 => J = -1
     int64_t *B, *M;       // [S][2][nt]
-    double *acc;          // [S][nt][40]
+    double *acc;          // [S][nt][n_bins][40]
+    unsigned long long *hist;  // [nt][n_bins][N+1] overlap histogram, or null
+    int n_bins;           // logarithmic sweep bins (1 = a single bin)
     const uint32_t *thr;  // [nt][16] thresholds, entry sb*8 + u
     const float *dbeta;   // [nt] (float)(beta_t - beta_{t+1})
     const float *twid;    // [2][L] FP32 cos, sin of 2 pi d / L

@@ -33,13 +33,15 @@ class Options(ctypes.Structure):
                 ("exchange_every", ctypes.c_int32), ("measure_every", ctypes.c_int32),
                 ("n_therm", ctypes.c_int64), ("threads_per_block", ctypes.c_int32),
                 ("sweeps_per_launch", ctypes.c_int32), ("watchdog_cycles", ctypes.c_uint64),
-                ("sample_base", ctypes.c_int64)]
+                ("sample_base", ctypes.c_int64), ("log_bins", ctypes.c_int32),
+                ("pq_hist", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int32), ("n_T", ctypes.c_int32), ("layout", ctypes.c_int32),
                 ("dist", ctypes.c_int32), ("n_samples", ctypes.c_int64), ("h", ctypes.c_double),
-                ("attempts_per_sweep", ctypes.c_int64), ("device_bytes", ctypes.c_size_t)]
+                ("attempts_per_sweep", ctypes.c_int64), ("device_bytes", ctypes.c_size_t),
+                ("log_bins", ctypes.c_int32), ("pq_hist", ctypes.c_int32)]
 
 
 class TuneReport(ctypes.Structure):
@@ -105,6 +107,8 @@ def lib() -> ctypes.CDLL:
         "sg_get_accumulators": (st, [P, P]),
         "sg_set_accumulators": (st, [P, P]),
         "sg_reset_accumulators": (st, [P]),
+        "sg_get_histogram": (st, [P, P]),
+        "sg_set_histogram": (st, [P, P]),
         "sg_get_spins": (st, [P, P]),
         "sg_set_spins": (st, [P, P]),
         "sg_get_energies": (st, [P, P, P]),
@@ -114,6 +118,7 @@ def lib() -> ctypes.CDLL:
         "sg_synchronize": (st, [P]),
         "sg_get_info": (st, [P, P]),
         "sg_results": (st, [P, P]),
+        "sg_results_bin": (st, [P, i32, P]),
         "sg_observables_from_acc": (st, [P, i64, i32, i32, P]),
         "sg_threshold_map": (st, [P, i32, P]),
         "sg_server_options_default": (None, [P]),
@@ -180,6 +185,8 @@ class Ensemble:
         self.n_T = len(self.T)
         self.dist = SG_GAUSS if dist in ("gauss", SG_GAUSS) else SG_PM_J
         self.opt = default_options(**options)
+        self.n_bins = max(int(self.opt.log_bins), 1)
+        self.has_hist = bool(self.opt.pq_hist)
         self._keep = []
         Jp = None
         sp = None
@@ -232,14 +239,35 @@ class Ensemble:
         _check(lib().sg_synchronize(self._h))
 
     # ---- data ------------------------------------------------------------
+    def _acc_shape(self):
+        if self.n_bins == 1:
+            return (self.n_samples, self.n_T, NACC)
+        return (self.n_samples, self.n_T, self.n_bins, NACC)
+
     def accumulators(self) -> np.ndarray:
-        out = np.zeros((self.n_samples, self.n_T, NACC), dtype=np.float64)
+        """[S][n_T][40], or [S][n_T][log_bins][40] with logarithmic bins."""
+        out = np.zeros(self._acc_shape(), dtype=np.float64)
         _check(lib().sg_get_accumulators(self._h, _ptr(out)))
         return out
 
     def set_accumulators(self, acc: np.ndarray):
         acc = np.ascontiguousarray(acc, dtype=np.float64)
+        if acc.shape != self._acc_shape():
+            raise ValueError(f"accumulators must have shape {self._acc_shape()}")
         _check(lib().sg_set_accumulators(self._h, _ptr(acc)))
+
+    def histogram(self) -> np.ndarray:
+        """Overlap histogram uint64 [n_T][log_bins][N+1]: entry k counts the
+        measurements whose replicas agree on k sites (q = (2k - N) / N)."""
+        out = np.zeros((self.n_T, self.n_bins, self.L ** 3 + 1), dtype=np.uint64)
+        _check(lib().sg_get_histogram(self._h, _ptr(out)))
+        return out
+
+    def set_histogram(self, hist: np.ndarray):
+        hist = np.ascontiguousarray(hist, dtype=np.uint64)
+        if hist.shape != (self.n_T, self.n_bins, self.L ** 3 + 1):
+            raise ValueError("histogram must have shape [n_T][log_bins][N+1]")
+        _check(lib().sg_set_histogram(self._h, _ptr(hist)))
 
     def reset_accumulators(self):
         _check(lib().sg_reset_accumulators(self._h))
@@ -296,8 +324,12 @@ class Ensemble:
         _check(lib().sg_get_info(self._h, ctypes.byref(i)))
         return i
 
-    def results(self) -> dict:
-        return _observables(lambda o: lib().sg_results(self._h, ctypes.byref(o)), self.n_T)
+    def results(self, bin: int | None = None) -> dict:
+        """Observables of the last sweep bin, or of bin `bin`."""
+        if bin is None:
+            return _observables(lambda o: lib().sg_results(self._h, ctypes.byref(o)), self.n_T)
+        return _observables(lambda o: lib().sg_results_bin(self._h, int(bin), ctypes.byref(o)),
+                            self.n_T)
 
 
 def _observables(call, nt: int) -> dict:

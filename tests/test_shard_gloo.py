@@ -1,6 +1,7 @@
 """Multi-rank path on CPU (gloo, world size 2): sample shards keyed by their
-global index reproduce the unsplit run, and the accumulator gather rebuilds
-the full array in rank order. The per-shard compute here is the oracle (no
+global index reproduce the unsplit run, the accumulator gather rebuilds the
+full (sweep-binned) array in rank order and the histogram reduction gives the
+unsplit histogram. The per-shard compute here is the oracle (no
 GPU); the sharding and gather logic under test is the product's."""
 import os
 import socket
@@ -12,7 +13,7 @@ import torch.multiprocessing as mp
 from oracle import oracle as orc
 from paper_1403_4560_b300 import inputs, shard
 
-L, S, NT, SEED, SWEEPS = 4, 11, 3, 21, 40
+L, S, NT, SEED, SWEEPS, BINS = 4, 11, 3, 21, 40, 5
 
 
 def _free_port():
@@ -28,11 +29,14 @@ def _worker(rank, world, port, out_path):
     T = inputs.geometric_ladder(0.5, 1.5, NT)
     J, s0 = inputs.make_instance("pmj", L, S, NT, seed=5)
     b, e = shard.shard_bounds(S, world, rank)
-    st = orc.State(L, T, 0.2, False, seed=SEED, J=J[b:e], spins=s0[b:e], s_base=b, n_therm=10)
+    st = orc.State(L, T, 0.2, False, seed=SEED, J=J[b:e], spins=s0[b:e], s_base=b, n_therm=10,
+                   log_bins=BINS, pq_hist=True)
     st.run(SWEEPS)
     full = shard.gather_accumulators(st.acc)
+    hist = shard.reduce_histogram(st.hist)
     if rank == 0:
         np.save(out_path, full)
+        np.save(out_path + ".hist.npy", hist)
     dist.barrier()
     dist.destroy_process_group()
 
@@ -50,6 +54,8 @@ def test_two_gloo_ranks_reproduce_the_single_process_run(tmp_path):
     mp.start_processes(_worker, args=(2, _free_port(), out), nprocs=2, start_method="spawn")
     T = inputs.geometric_ladder(0.5, 1.5, NT)
     J, s0 = inputs.make_instance("pmj", L, S, NT, seed=5)
-    st = orc.State(L, T, 0.2, False, seed=SEED, J=J, spins=s0, n_therm=10)
+    st = orc.State(L, T, 0.2, False, seed=SEED, J=J, spins=s0, n_therm=10, log_bins=BINS,
+                   pq_hist=True)
     st.run(SWEEPS)
     np.testing.assert_array_equal(np.load(out), st.acc)
+    np.testing.assert_array_equal(np.load(out + ".hist.npy"), st.hist)
