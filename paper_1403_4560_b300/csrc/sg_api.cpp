@@ -606,9 +606,10 @@ static sg_status launch_sweeps(sg_ensemble *e, int64_t n, cudaStream_t s, bool d
         // one launch per sweep: the exchange pairing alternates between sweeps
         MscArgs a = make_msc_args(e);
         if (device_counter) a.sweep0_dev = e->sweep_ctr;
+        const int threads = msc_threads(e->L, e->opt.threads_per_block);
         for (int64_t k = 0; k < n; ++k) {
             a.sweep_offset = (int)k;
-            SG_CUDA(msc_sweep(a, e->L, s), "MSC sweep kernel launch");
+            SG_CUDA(msc_sweep(a, e->L, threads, s), "MSC sweep kernel launch");
         }
         if (device_counter) SG_CUDA(advance_counter(e->sweep_ctr, n, s), "counter");
         return SG_OK;
@@ -938,9 +939,64 @@ sg_status sg_autotune(sg_ensemble *e, int64_t trial_sweeps, sg_tune_report *rep)
 {
     if (!e || trial_sweeps < 1) return fail(SG_EINVAL, "bad autotune arguments");
     sg_tune_report r{};
-    if (e->msc) {  // one fixed shape (a CTA per exchange unit, 512 threads)
-        r.threads_per_block = 512;
-        r.n_candidates = 1;
+    if (e->msc) {  // a CTA per exchange unit; time the CTA sizes
+        const size_t wbytes = (size_t)(e->S / 64) * e->nt * 2 * e->L * e->L * e->L * 8;
+        const size_t bm = (size_t)e->S * 2 * e->nt * sizeof(int64_t);
+        const size_t ab = e->hist ? (size_t)((uint8_t *)e->hist - (uint8_t *)e->acc) + e->hist_bytes
+                                  : e->acc_bytes;
+        uint8_t *bk = nullptr;
+        SG_CUDA(cudaMalloc(&bk, wbytes + 2 * bm + ab), "autotune backup");
+        auto save = [&](bool restore) {
+            const cudaMemcpyKind k = cudaMemcpyDeviceToDevice;
+            void *dst[4] = {bk, bk + wbytes, bk + wbytes + bm, bk + wbytes + 2 * bm};
+            void *src[4] = {e->W, e->B, e->M, e->acc};
+            const size_t len[4] = {wbytes, bm, bm, ab};
+            cudaError_t ce = cudaSuccess;
+            for (int q = 0; q < 4 && ce == cudaSuccess; ++q)
+                ce = restore ? cudaMemcpyAsync(src[q], dst[q], len[q], k, e->stream)
+                             : cudaMemcpyAsync(dst[q], src[q], len[q], k, e->stream);
+            return ce;
+        };
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        const sg_options orig = e->opt;
+        const int64_t done0 = e->sweeps_done;
+        double best = 1e300, def = 0.0;
+        int best_t = msc_threads(e->L, 0), nc = 0;
+        cudaError_t ce = save(false);
+        const int cands[3] = {msc_threads(e->L, 0), 128, 512};
+        for (int c = 0; c < 3 && ce == cudaSuccess; ++c) {
+            if (c > 0 && cands[c] == cands[0]) continue;
+            e->opt.threads_per_block = cands[c];
+            if (launch_sweeps(e, 1, e->stream, false) != SG_OK) break;  // warm-up
+            cudaEventRecord(e0, e->stream);
+            if (launch_sweeps(e, trial_sweeps, e->stream, false) != SG_OK) break;
+            cudaEventRecord(e1, e->stream);
+            ce = cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            const double per = ms / (double)trial_sweeps;
+            if (c == 0) def = per;
+            if (per < best) {
+                best = per;
+                best_t = cands[c];
+            }
+            ++nc;
+            if (ce == cudaSuccess) ce = save(true);
+        }
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(e->stream);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cudaFree(bk);
+        e->opt = orig;
+        e->sweeps_done = done0;
+        if (ce != cudaSuccess) return cuda_fail(ce, "autotune");
+        e->opt.threads_per_block = best_t;
+        r.threads_per_block = best_t;
+        r.n_candidates = nc;
+        r.best_ms_per_sweep = best;
+        r.default_ms_per_sweep = def;
         if (rep) *rep = r;
         return SG_OK;
     }

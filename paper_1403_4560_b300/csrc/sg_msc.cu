@@ -420,8 +420,13 @@ __device__ __forceinline__ void msc_measure(const MscSmem &sm, const MscArgs &a,
     __syncthreads();
 }
 
-template <int L>
-__global__ void __launch_bounds__(kMscThreads) msc_sweep_kernel(const MscArgs a)
+// MAXT / MINB: launch bounds of the instance. The narrow instance (128
+// threads, at least 6 CTAs per SM, so at most 80 registers) serves small
+// lattices, where a unit has little work per barrier and several resident
+// CTAs hide each other's barrier and memory waits; the wide one (up to 512
+// threads) serves large lattices.
+template <int L, int MAXT, int MINB>
+__global__ void __launch_bounds__(MAXT, MINB) msc_sweep_kernel(const MscArgs a)
 {
     constexpr int N = L * L * L;
     extern __shared__ __align__(16) uint8_t msc_smem[];
@@ -751,15 +756,23 @@ inline int gridn(int64_t work, int threads)
 
 constexpr int kMscMaxSmem = 227 * 1024;
 
+constexpr int kMscNarrow = 128;
+
 template <int L>
-cudaError_t msc_launch_t(const MscArgs &a, cudaStream_t st)
+cudaError_t msc_launch_t(const MscArgs &a, int threads, cudaStream_t st)
 {
-    static cudaError_t attr = cudaFuncSetAttribute(
-        msc_sweep_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMscMaxSmem);
-    if (attr != cudaSuccess) return attr;
+    static cudaError_t attr_n = cudaFuncSetAttribute(
+        msc_sweep_kernel<L, kMscNarrow, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMscMaxSmem);
+    static cudaError_t attr_w = cudaFuncSetAttribute(
+        msc_sweep_kernel<L, kMscThreads, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMscMaxSmem);
+    if (attr_n != cudaSuccess) return attr_n;
+    if (attr_w != cudaSuccess) return attr_w;
     const size_t smem = msc_carve(nullptr, L, nullptr);
     dim3 grid((unsigned)(a.nt / 2 + 1), (unsigned)a.G);
-    msc_sweep_kernel<L><<<grid, kMscThreads, smem, st>>>(a);
+    if (threads == kMscNarrow)
+        msc_sweep_kernel<L, kMscNarrow, 6><<<grid, threads, smem, st>>>(a);
+    else
+        msc_sweep_kernel<L, kMscThreads, 1><<<grid, threads, smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -781,9 +794,25 @@ bool msc_supported_L(int L)
     return false;
 }
 
-cudaError_t msc_sweep(const MscArgs &a, int L, cudaStream_t st)
+int msc_threads(int L, int requested)
 {
-#define X(LL) if (L == LL) return msc_launch_t<LL>(a, st);
+    // The exchange step uses one thread per (replica, sample), so at least
+    // 128; a multiple of 128 splits into whole warps per chain for both unit
+    // sizes (2 or 4 chains), which the per-warp energy reduction needs.
+    if (requested > 0) {
+        const int t = requested < 128 ? 128 : requested > kMscThreads ? kMscThreads : requested;
+        return t & ~127;
+    }
+    // measured on B300 (+-J, 32-56 temperatures, 4096-8192 samples): small
+    // lattices run fastest with several narrow CTAs per SM, large ones with
+    // one wide CTA
+    return L <= 10 ? 128 : L == 12 ? 256 : kMscThreads;
+}
+
+cudaError_t msc_sweep(const MscArgs &a, int L, int threads, cudaStream_t st)
+{
+    if (threads < 128 || threads > kMscThreads || (threads & 127)) return cudaErrorInvalidValue;
+#define X(LL) if (L == LL) return msc_launch_t<LL>(a, threads, st);
     SG_MSC_FOR_EACH_L(X)
 #undef X
     return cudaErrorInvalidValue;

@@ -33,7 +33,10 @@ struct MscArgs {
 
 size_t msc_smem_bytes(int L);
 bool msc_supported_L(int L);
-cudaError_t msc_sweep(const MscArgs &a, int L, cudaStream_t st);
+// Threads per CTA of the sweep kernel: `requested` (0 = library choice for
+// L) clamped to [128, 512] and rounded down to a multiple of 128.
+int msc_threads(int L, int requested);
+cudaError_t msc_sweep(const MscArgs &a, int L, int threads, cudaStream_t st);
 cudaError_t msc_import_spins(uint64_t *W, const int8_t *canon, int64_t G, int L, int nt,
                              cudaStream_t st);
 cudaError_t msc_export_spins(int8_t *canon, const uint64_t *W, int64_t G, int L, int nt,

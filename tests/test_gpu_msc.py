@@ -144,3 +144,41 @@ def test_msc_argument_checks():
     with pytest.raises(sgmc.SgError) as ei:
         sgmc.Ensemble(20, 0.1, T, "pmj", 64, 1, **MSC)
     assert ei.value.status == sgmc.SG_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("L,nt", [(4, 5), (8, 4), (12, 3)])
+def test_msc_cta_size_changes_speed_not_results(L, nt):
+    """The narrow (128-thread) and wide (256, 512) kernel instances give the
+    same chain, energies, accumulators and histogram bit for bit."""
+    T = inputs.geometric_ladder(0.4, 1.5, nt)
+    J, s0 = inputs.make_instance("pmj", L, 128, nt, seed=3 + L)
+    ref = None
+    for th in (128, 256, 512):
+        with sgmc.Ensemble(L, 0.2, T, "pmj", 128, 17, J=J, spins=s0, threads_per_block=th,
+                           log_bins=4, pq_hist=1, **MSC) as ens:
+            ens.sweep(21)
+            out = (ens.spins(), ens.energies(), ens.accumulators(), ens.histogram())
+        if ref is None:
+            ref = out
+            continue
+        np.testing.assert_array_equal(out[0], ref[0])
+        np.testing.assert_array_equal(out[1][0], ref[1][0])
+        np.testing.assert_array_equal(out[2], ref[2])
+        np.testing.assert_array_equal(out[3], ref[3])
+
+
+def test_msc_autotune_changes_speed_not_results():
+    L, nt, S = 6, 6, 128
+    T = inputs.geometric_ladder(0.4, 1.5, nt)
+    J, s0 = inputs.make_instance("pmj", L, S, nt, seed=12)
+    with sgmc.Ensemble(L, 0.1, T, "pmj", S, 5, J=J, spins=s0, **MSC) as a, \
+            sgmc.Ensemble(L, 0.1, T, "pmj", S, 5, J=J, spins=s0, **MSC) as b:
+        a.sweep(10)
+        b.sweep(10)
+        rep = b.autotune(trial_sweeps=4)
+        assert rep["threads_per_block"] in (128, 256, 512) and rep["n_candidates"] >= 2
+        a.sweep(15)
+        b.sweep(15)
+        np.testing.assert_array_equal(a.spins(), b.spins())
+        np.testing.assert_array_equal(a.accumulators(), b.accumulators())
+        assert a.sweeps_done == b.sweeps_done == 25
