@@ -135,8 +135,10 @@ size_t sg_ensemble_bytes(int L, int n_T, int64_t n_samples, sg_coupling dist,
 
 /*
  * Create an ensemble of n_samples disorder samples on the current device.
- *   L        even, 2 <= L <= 24 (even L keeps the two-colour checkerboard a
- *            proper colouring under periodic boundaries)
+ *   L        even, 2 <= L <= 64 (even L keeps the two-colour checkerboard a
+ *            proper colouring under periodic boundaries). The INT8 layout
+ *            has kernels for every even L up to 32 and for 40, 48 and 64
+ *            (SG_EUNSUPPORTED for the other sizes); MSC64 for L <= 16.
  *   h        uniform field (eq. Hamiltonian); rounded to the 2^-17 grid when
  *            dist == SG_GAUSS
  *   T        host array of n_T temperatures, strictly ascending, > 0 (the

@@ -362,7 +362,7 @@ void host_tables(const sg_ensemble *e, std::vector<uint32_t> &thr, std::vector<f
 sg_status validate(int L, const double *T, int nt, sg_coupling dist, int64_t S,
                    const sg_options &o)
 {
-    if (L < 2 || (L & 1) || L > 24) return fail(SG_EINVAL, "L must be even and in [2, 24]");
+    if (L < 2 || (L & 1) || L > 64) return fail(SG_EINVAL, "L must be even and in [2, 64]");
     if (nt < 1 || nt > 64) return fail(SG_EINVAL, "n_T must be in [1, 64]");
     if (!T) return fail(SG_EINVAL, "temperature array is NULL");
     for (int t = 0; t < nt; ++t) {

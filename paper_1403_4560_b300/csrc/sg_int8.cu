@@ -1,695 +1,16 @@
-// sg_int8.cu -- int8-spin path of the EA spin-glass engine on B300 (sm_103a).
-//
-// One CTA owns one disorder sample at a time and keeps its whole state in
-// shared memory for a chunk of sweeps: the 2 x Tp chains (two replicas, Tp
-// temperature slots padded to a multiple of 4) of every site, the couplings,
-// the threshold table and the energies. The CTA runs the paper's method for
-// that sample (methods section: checkerboard single-spin Metropolis sweeps,
-// parallel tempering between neighbouring temperatures with two replicas per
-// temperature, overlap measurement after thermalisation), then writes the
-// state back. HBM is touched only at chunk boundaries, so the sweep loop is
-// bound by the SM's integer / FP32 issue rate rather than by HBM.
-//
-// Shared-memory layout of one sample:
-//   spins  [N][2*Tp] bytes   per site, Tp/4 groups of 8 bytes: 4 slots of
-//                            replica 0, then the same 4 slots of replica 1;
-//                            value 0 => +1, 1 => -1. One 32-bit word holds
-//                            four chains (SIMD within a register) and one
-//                            64-bit load serves the 8 chains of a group.
-//   +-J    [N][8] bytes      bond bits (+x, -x, +y, -y, +z, -z, 0, 0), 1 => J = -1
-//   Gauss  [3][N] float      J[d][i] joins i and i + e_d
-// Work item of a half-sweep: (run of RUN = lcm(L/2, 4) consecutive sites of
-// one colour, one 4-slot group, both replicas). RUN is a multiple of 4, so
-// the Philox calls (four sites each) never straddle two items.
+// sg_int8.cu -- int8-spin path of the EA spin-glass engine on B300 (sm_103a):
+// shared-memory instances of the fused kernel (the kernel itself is in
+// sg_int8_run.cuh; the large-lattice global-memory instances are in
+// sg_int8_gst.cu), instance preparation, conversion and standalone kernels.
 #include <cuda_runtime.h>
 
 #include <mutex>
 
-#include "sg_device.cuh"
-#include "sg_internal.h"
+#include "sg_int8_run.cuh"
 
 namespace sg {
 
 namespace {
-
-constexpr int kMaxThreads = 512;
-
-__host__ __device__ constexpr int gcd_c(int a, int b) { return b == 0 ? a : gcd_c(b, a % b); }
-__host__ __device__ constexpr int lcm_c(int a, int b) { return a / gcd_c(a, b) * b; }
-
-__device__ __forceinline__ uint32_t lds32(const uint8_t *base, int off)
-{
-    return *reinterpret_cast<const uint32_t *>(base + off);
-}
-__device__ __forceinline__ void sts32(uint8_t *base, int off, uint32_t v)
-{
-    *reinterpret_cast<uint32_t *>(base + off) = v;
-}
-
-// Byte of (replica r, slot t) inside a site's row: slots come in 4-slot
-// words and the two replicas' words of one 4-slot group are adjacent, so one
-// 64-bit load reads 8 chains (4 slots x 2 replicas) of a site.
-__host__ __device__ __forceinline__ int slot_byte(int r, int t)
-{
-    return 8 * (t >> 2) + 4 * r + (t & 3);
-}
-
-struct Smem {
-    uint8_t *spins;
-    uint8_t *J8;
-    float *Jg;
-    uint32_t *thr;
-    float *negbeta, *dbeta, *twid;
-    unsigned long long *B, *M;  // [2][Tp], two's complement int64
-    uint32_t *xflag;            // [2][Tp] exchange stamps
-    uint32_t *sel;              // [2][Tp/4][2] byte-permutation selectors
-    int *anyswap;               // [2]
-    uint32_t *marg;             // [3][L*L][mchunk] byte counts of q = -1
-};
-
-__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
-
-// Carve the dynamic shared memory; returns the bytes used.
-// gst: the sample's spins and couplings stay in global memory (large L);
-// only the small tables are carved.
-__host__ __device__ inline size_t carve(uint8_t *base, int L, int Tp, bool gauss, int mchunk,
-                                        Smem *sm, bool gst = false)
-{
-    const size_t N = (size_t)L * L * L;
-    size_t off = 0;
-    auto take = [&](size_t bytes) {
-        uint8_t *p = base ? base + off : nullptr;
-        off = align16(off + bytes);
-        return p;
-    };
-    Smem s;
-    s.spins = gst ? nullptr : take(N * 2 * Tp);
-    s.J8 = (gauss || gst) ? nullptr : take(N * 8);
-    s.Jg = (gauss && !gst) ? reinterpret_cast<float *>(take(N * 3 * sizeof(float))) : nullptr;
-    s.thr = gauss ? nullptr : reinterpret_cast<uint32_t *>(take((size_t)Tp * 16 * 4));
-    s.negbeta = reinterpret_cast<float *>(take((size_t)Tp * 4));
-    s.dbeta = reinterpret_cast<float *>(take((size_t)Tp * 4));
-    s.twid = reinterpret_cast<float *>(take((size_t)2 * L * 4));
-    s.B = reinterpret_cast<unsigned long long *>(take((size_t)2 * Tp * 8));
-    s.M = reinterpret_cast<unsigned long long *>(take((size_t)2 * Tp * 8));
-    s.xflag = reinterpret_cast<uint32_t *>(take((size_t)2 * Tp * 4));
-    s.sel = reinterpret_cast<uint32_t *>(take((size_t)2 * (Tp / 4) * 2 * 4));
-    s.anyswap = reinterpret_cast<int *>(take(2 * 4));
-    s.marg = reinterpret_cast<uint32_t *>(take((size_t)3 * L * L * mchunk * 4));
-    if (sm) *sm = s;
-    return off;
-}
-
-struct Ctx {
-    int nt, Tp, WR, RB;
-    int64_t s;
-    uint32_t k0, k1;  // Metropolis Philox key
-    uint32_t seed_lo, seed_hi;
-    float hq;         // Gaussian: field on the 2^-17 grid
-};
-
-// Site index and neighbour offsets (in sites) of the colour-COL site with
-// colour-compressed index jj (i = 2*jj + parity, i >> 1 == jj).
-template <int L>
-struct SiteNb {
-    int i, x, dxp, dxm, dyp, dym, dzp, dzm;
-    __device__ __forceinline__ SiteNb(int jj, int COL)
-    {
-        constexpr int H = L / 2;
-        const int row = jj / H;
-        const int x2 = jj - row * H;
-        const int y = row % L;
-        const int z = row / L;
-        x = 2 * x2 + ((COL + y + z) & 1);
-        i = x + L * row;
-        dxp = (x == L - 1) ? -(L - 1) : 1;
-        dxm = (x == 0) ? (L - 1) : -1;
-        dyp = (y == L - 1) ? -(L - 1) * L : L;
-        dym = (y == 0) ? (L - 1) * L : -L;
-        dzp = (z == L - 1) ? -(L - 1) * L * L : L * L;
-        dzm = (z == 0) ? (L - 1) * L * L : -L * L;
-    }
-};
-
-// +-J: Metropolis on 4 chains of one replica word; returns the flip bytes
-// (0x01 per flipped chain) and the unsatisfied-bond counts per byte.
-__device__ __forceinline__ uint32_t pmj_word(uint32_t s, uint32_t nxp, uint32_t nxm,
-                                             uint32_t nyp, uint32_t nym, uint32_t nzp,
-                                             uint32_t nzm, const uint32_t (&m)[6],
-                                             const uint32_t *thr_w, const uint32_t (&rnd)[4][4],
-                                             int lane, uint32_t valid, uint32_t &uw)
-{
-    uw = (s ^ nxp ^ m[0]) + (s ^ nxm ^ m[1]) + (s ^ nyp ^ m[2]) + (s ^ nym ^ m[3]) +
-         (s ^ nzp ^ m[4]) + (s ^ nzm ^ m[5]);
-    const uint32_t idx = (s << 3) | uw;  // per byte: sb*8 + u
-    uint32_t fm = 0;
-#pragma unroll
-    for (int kk = 0; kk < 4; ++kk) {
-        const uint32_t th = thr_w[kk * 16 + ((idx >> (8 * kk)) & 15u)];
-        fm |= (uint32_t)(rnd[kk][lane] <= th) << (8 * kk);
-    }
-    return fm & valid;
-}
-
-// Gaussian: Metropolis on 4 chains of one replica word. bq[kk] receives
-// s_new * b / qJ for the energy of colour-1 sites.
-template <bool ENERGY>
-__device__ __forceinline__ uint32_t gauss_word(uint32_t s, uint32_t nxp, uint32_t nxm,
-                                               uint32_t nyp, uint32_t nym, uint32_t nzp,
-                                               uint32_t nzm, const float (&j)[6], float hq,
-                                               const float (&nbeta)[4],
-                                               const uint32_t (&rnd)[4][4], int lane,
-                                               uint32_t valid, int (&bq)[4])
-{
-    uint32_t fm = 0;
-#pragma unroll
-    for (int kk = 0; kk < 4; ++kk) {
-        const int sh = 31 - 8 * kk;
-        // J * s_nb: flip the sign bit of J where the neighbour is -1; the sum
-        // is exact on the 2^-17 grid, so a balanced tree (short dependency
-        // chain) gives the same value as any other order
-        const float t0 = __int_as_float(__float_as_int(j[0]) ^ ((nxp << sh) & 0x80000000u));
-        const float t1 = __int_as_float(__float_as_int(j[1]) ^ ((nxm << sh) & 0x80000000u));
-        const float t2 = __int_as_float(__float_as_int(j[2]) ^ ((nyp << sh) & 0x80000000u));
-        const float t3 = __int_as_float(__float_as_int(j[3]) ^ ((nym << sh) & 0x80000000u));
-        const float t4 = __int_as_float(__float_as_int(j[4]) ^ ((nzp << sh) & 0x80000000u));
-        const float t5 = __int_as_float(__float_as_int(j[5]) ^ ((nzm << sh) & 0x80000000u));
-        const float b = __fadd_rn(__fadd_rn(__fadd_rn(t0, t1), __fadd_rn(t2, t3)), __fadd_rn(t4, t5));
-        const uint32_t sgn = (s << sh) & 0x80000000u;  // own spin -1 => sign bit
-        const float zf = __fadd_rn(b, hq);
-        const float dE = __int_as_float(__float_as_int(__fadd_rn(zf, zf)) ^ sgn);
-        // dE <= 0 gives x >= 0, whose threshold is 0xFFFFFFFF: always accepted
-        const float xl = __fmul_rn(nbeta[kk], dE);
-        const uint32_t flip = (rnd[kk][lane] <= thr_of_logp(xl)) & (valid >> (8 * kk));
-        fm |= flip << (8 * kk);
-        if (ENERGY) {
-            const int q = __float2int_rn(__fmul_rn(b, 131072.0f));
-            bq[kk] = (((s >> (8 * kk)) ^ flip) & 1u) ? -q : q;
-        }
-    }
-    return fm;
-}
-
-// ---------------------------------------------------------------------------
-// One checkerboard half-sweep of colour COL over all chains of the sample.
-// Work item: (run of RUN colour-COL sites, 4-slot group j) covering both
-// replicas, i.e. 8 chains. For COL == 1 it also accumulates B and M of the
-// post-sweep configuration: every bond has exactly one colour-1 end, so
-// summing s_i * b_i over colour-1 sites counts each bond once; M pairs each
-// colour-1 site with its x^1 partner (colour 0, final after the colour-0 half).
-// ---------------------------------------------------------------------------
-template <int L, bool GAUSS>
-__device__ __forceinline__ void half_sweep(const Smem &sm, const Ctx &cx, uint32_t n_sweep,
-                                        const int COL)
-{
-    constexpr int H = L / 2;
-    constexpr int N = L * L * L;
-    constexpr int RUN = lcm_c(H, 4);
-    constexpr int NG = RUN / 4;
-    constexpr int U = (N / 2) / RUN;
-    const int WR = cx.WR, RB = cx.RB;
-    const int j = threadIdx.x % WR;  // fixed per thread: blockDim.x is a multiple of WR
-    const int t0 = 4 * j;
-    const int items = U * WR;
-
-    uint32_t valid = 0;  // bytes of real (not padding) slots in this group
-#pragma unroll
-    for (int kk = 0; kk < 4; ++kk)
-        if (t0 + kk < cx.nt) valid |= 1u << (8 * kk);
-
-    float nbeta[4];
-#pragma unroll
-    for (int kk = 0; kk < 4; ++kk) nbeta[kk] = GAUSS ? sm.negbeta[t0 + kk] : 0.0f;
-    const uint32_t *thr_w = GAUSS ? nullptr : sm.thr + t0 * 16;
-
-    for (int item = threadIdx.x; item < items; item += blockDim.x) {
-        const int u = item / WR;
-        uint32_t eacc0 = 0, eacc1 = 0, macc0 = 0, macc1 = 0;  // byte-wise partial sums
-        int bg[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
-        // long runs would overflow the byte-wise sums of unsatisfied bonds
-        // (6 per site): those are flushed into bg after every group of 4 sites
-        constexpr bool kFlushU = 6 * RUN > 255;
-        for (int g = 0; g < NG; ++g) {
-            const uint32_t c0 = (uint32_t)(u * NG + g);
-            uint32_t rnd[2][4][4];
-#pragma unroll
-            for (int r = 0; r < 2; ++r)
-#pragma unroll
-                for (int kk = 0; kk < 4; ++kk) {
-                    const uint32_t c2 = ((uint32_t)COL << 24) | ((uint32_t)r << 16) |
-                                        (uint32_t)(t0 + kk);
-                    const u32x4 o = philox10(cx.k0, cx.k1, c0, n_sweep, c2, cx.seed_hi);
-                    rnd[r][kk][0] = o.v[0];
-                    rnd[r][kk][1] = o.v[1];
-                    rnd[r][kk][2] = o.v[2];
-                    rnd[r][kk][3] = o.v[3];
-                }
-#pragma unroll
-            for (int lane = 0; lane < 4; ++lane) {
-                const SiteNb<L> st(u * RUN + 4 * g + lane, COL);
-                const int own = st.i * RB + 8 * j;
-                const uint2 s = *reinterpret_cast<const uint2 *>(sm.spins + own);
-                const uint2 nxp = *reinterpret_cast<const uint2 *>(sm.spins + own + st.dxp * RB);
-                const uint2 nxm = *reinterpret_cast<const uint2 *>(sm.spins + own + st.dxm * RB);
-                const uint2 nyp = *reinterpret_cast<const uint2 *>(sm.spins + own + st.dyp * RB);
-                const uint2 nym = *reinterpret_cast<const uint2 *>(sm.spins + own + st.dym * RB);
-                const uint2 nzp = *reinterpret_cast<const uint2 *>(sm.spins + own + st.dzp * RB);
-                const uint2 nzm = *reinterpret_cast<const uint2 *>(sm.spins + own + st.dzm * RB);
-                uint2 fm;
-                if constexpr (!GAUSS) {
-                    const uint2 jb = *reinterpret_cast<const uint2 *>(sm.J8 + 8 * st.i);
-                    const uint32_t m[6] = {__byte_perm(jb.x, jb.y, 0x0000),
-                                           __byte_perm(jb.x, jb.y, 0x1111),
-                                           __byte_perm(jb.x, jb.y, 0x2222),
-                                           __byte_perm(jb.x, jb.y, 0x3333),
-                                           __byte_perm(jb.x, jb.y, 0x4444),
-                                           __byte_perm(jb.x, jb.y, 0x5555)};
-                    uint32_t uw0, uw1;
-                    fm.x = pmj_word(s.x, nxp.x, nxm.x, nyp.x, nym.x, nzp.x, nzm.x, m, thr_w,
-                                    rnd[0], lane, valid, uw0);
-                    fm.y = pmj_word(s.y, nxp.y, nxm.y, nyp.y, nym.y, nzp.y, nzm.y, m, thr_w,
-                                    rnd[1], lane, valid, uw1);
-                    if (COL == 1) {
-                        const uint32_t f0 = fm.x * 0xFFu, f1 = fm.y * 0xFFu;
-                        eacc0 += uw0 ^ ((uw0 ^ (0x06060606u - uw0)) & f0);
-                        eacc1 += uw1 ^ ((uw1 ^ (0x06060606u - uw1)) & f1);
-                    }
-                } else {
-                    const float jv[6] = {sm.Jg[st.i], sm.Jg[st.i + st.dxm], sm.Jg[N + st.i],
-                                         sm.Jg[N + st.i + st.dym], sm.Jg[2 * N + st.i],
-                                         sm.Jg[2 * N + st.i + st.dzm]};
-                    int bq0[4], bq1[4];
-                    fm.x = gauss_word<true>(s.x, nxp.x, nxm.x, nyp.x, nym.x, nzp.x, nzm.x, jv,
-                                            cx.hq, nbeta, rnd[0], lane, valid, bq0);
-                    fm.y = gauss_word<true>(s.y, nxp.y, nxm.y, nyp.y, nym.y, nzp.y, nzm.y, jv,
-                                            cx.hq, nbeta, rnd[1], lane, valid, bq1);
-                    if (COL == 1) {
-#pragma unroll
-                        for (int kk = 0; kk < 4; ++kk) {
-                            bg[0][kk] += bq0[kk];
-                            bg[1][kk] += bq1[kk];
-                        }
-                    }
-                }
-                uint2 sn;
-                sn.x = s.x ^ fm.x;
-                sn.y = s.y ^ fm.y;
-                *reinterpret_cast<uint2 *>(sm.spins + own) = sn;
-                if (COL == 1) {
-                    const uint2 partner = (st.x & 1) ? nxm : nxp;
-                    macc0 += sn.x + partner.x;
-                    macc1 += sn.y + partner.y;
-                }
-            }
-            if (kFlushU && !GAUSS && COL == 1) {
-#pragma unroll
-                for (int kk = 0; kk < 4; ++kk) {
-                    bg[0][kk] += (eacc0 >> (8 * kk)) & 0xFFu;
-                    bg[1][kk] += (eacc1 >> (8 * kk)) & 0xFFu;
-                }
-                eacc0 = eacc1 = 0;
-            }
-        }
-        if (COL == 1) {
-#pragma unroll
-            for (int r = 0; r < 2; ++r)
-#pragma unroll
-                for (int kk = 0; kk < 4; ++kk) {
-                    const int t = t0 + kk;
-                    if (t >= cx.nt) continue;
-                    const uint32_t ea = r ? eacc1 : eacc0;
-                    const uint32_t ma = r ? macc1 : macc0;
-                    // +-J: s b = 6 - 2u per colour-1 site; M: each pair gives 2 - 2*(#-1)
-                    const long long usum = (long long)((ea >> (8 * kk)) & 0xFFu) + (kFlushU ? bg[r][kk] : 0);
-                    const long long b = GAUSS ? (long long)bg[r][kk] : 6LL * RUN - 2LL * usum;
-                    const long long mm = 2LL * RUN - 2LL * ((ma >> (8 * kk)) & 0xFFu);
-                    atomicAdd(&sm.B[r * cx.Tp + t], (unsigned long long)b);
-                    atomicAdd(&sm.M[r * cx.Tp + t], (unsigned long long)mm);
-                }
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Replica exchange between slots p and p+1 of each replica (pairs of one
-// parity), then the state swap of accepted pairs as byte permutations of the
-// 4-slot words. stamp identifies this exchange in xflag.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void exchange_decide(const Smem &sm, const Ctx &cx, const Int8Args &a,
-                                                int parity, uint32_t ctr1, uint32_t rflag,
-                                                uint32_t stamp)
-{
-    // warp 0 only: the pair decisions, then the byte-permutation selectors
-    const int lane = threadIdx.x;
-    const int nt = cx.nt, Tp = cx.Tp, WR = cx.WR;
-    const int np = (nt - parity) / 2;
-    if (lane < 2) sm.anyswap[lane] = 0;
-    for (int id = lane; id < 2 * np; id += 32) {
-        const int r = id / np;
-        const int p = parity + 2 * (id % np);
-        if (p + 1 >= nt) continue;
-        unsigned long long *Bp = sm.B + r * Tp + p;
-        unsigned long long *Mp = sm.M + r * Tp + p;
-        const long long dB = (long long)Bp[0] - (long long)Bp[1];
-        const long long dM = (long long)Mp[0] - (long long)Mp[1];
-        const float t1 = __fmul_rn(__ll2float_rn(dB), a.qJ_f);
-        const float t2 = __fmul_rn(a.h_f, __ll2float_rn(dM));
-        const float dE = -__fadd_rn(t1, t2);
-        const float D = __fmul_rn(sm.dbeta[p], dE);
-        const u32x4 o = philox10(cx.seed_lo ^ kTagExc, (uint32_t)(cx.s + a.s_key0), (uint32_t)p, ctr1,
-                                 (uint32_t)r | rflag, cx.seed_hi);
-        const bool acc = (D >= 0.0f) || (o.v[0] <= thr_of_logp(D));
-        if (acc) {
-            const unsigned long long tb = Bp[0];
-            Bp[0] = Bp[1];
-            Bp[1] = tb;
-            const unsigned long long tm = Mp[0];
-            Mp[0] = Mp[1];
-            Mp[1] = tm;
-            sm.xflag[r * Tp + p] = stamp;
-        }
-    }
-    __syncwarp();
-    for (int id = lane; id < 2 * WR; id += 32) {
-        const int r = id / WR, j = id % WR;
-        const uint32_t *fl = sm.xflag + r * Tp;
-        uint32_t s1 = 0, s2 = 0;
-        bool any = false;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int t = 4 * j + k;
-            int src = t;
-            if (t + 1 < nt && fl[t] == stamp) src = t + 1;
-            else if (t >= 1 && t < nt && fl[t - 1] == stamp) src = t - 1;
-            any |= (src != t);
-            // first permutation over {next word : this word}, second brings in
-            // byte 3 of the previous word
-            uint32_t n1 = (uint32_t)k, n2 = (uint32_t)k;
-            if (src >= 4 * j && src < 4 * j + 4) n1 = (uint32_t)(src - 4 * j);
-            else if (src == 4 * j + 4) n1 = 4u;
-            else n2 = 7u;  // src == 4j - 1
-            s1 |= n1 << (4 * k);
-            s2 |= n2 << (4 * k);
-        }
-        sm.sel[(r * WR + j) * 2 + 0] = s1;
-        sm.sel[(r * WR + j) * 2 + 1] = s2;
-        if (any) atomicOr(&sm.anyswap[r], 1);
-    }
-}
-
-// All threads: apply the accepted swaps row by row (after a block barrier
-// that publishes the selectors).
-template <int L>
-__device__ __forceinline__ void exchange_apply(const Smem &sm, const Ctx &cx)
-{
-    constexpr int N = L * L * L;
-    const int WR = cx.WR, RB = cx.RB;
-    for (int id = threadIdx.x; id < 2 * N; id += blockDim.x) {
-        const int r = id & 1, site = id >> 1;
-        if (!sm.anyswap[r]) continue;
-        uint8_t *row = sm.spins + site * RB + 4 * r;  // word j at row + 8j
-        const uint32_t *sel = sm.sel + r * WR * 2;
-        uint32_t prev = 0, cur = lds32(row, 0);
-        for (int jj = 0; jj < WR; ++jj) {
-            const uint32_t next = (jj + 1 < WR) ? lds32(row, 8 * (jj + 1)) : 0u;
-            const uint32_t tmp = __byte_perm(cur, next, sel[2 * jj]);
-            sts32(row, 8 * jj, __byte_perm(tmp, prev, sel[2 * jj + 1]));
-            prev = cur;
-            cur = next;
-        }
-    }
-}
-
-// Counts of q = -1 per phase d of one wave vector, from the 2D marginal
-// pm[(A*L + B)*nw] (byte sh): PAT 0: A = d; 1: B = d; 2: A + B = d;
-// 3: A - B = d (mod L). The L sums are independent load chains.
-template <int L, int PAT>
-__device__ __forceinline__ void count_pattern(const uint32_t *pm, int nw, int sh, int (&cs)[L])
-{
-#pragma unroll
-    for (int d = 0; d < L; ++d) {
-        int c = 0;
-#pragma unroll 4
-        for (int aa = 0; aa < L; ++aa) {
-            const int A = PAT == 0 ? d : aa;
-            const int Bc = PAT == 0 ? aa : PAT == 1 ? d : PAT == 2 ? (d - aa + L) % L : (aa - d + L) % L;
-            c += (pm[(A * L + Bc) * nw] >> sh) & 0xFF;
-        }
-        cs[d] = c;
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Overlap measurement (eq. overlap) for every slot: q = s^(0) s^(1);
-// (A) 2D marginals of the q = -1 counts over the xy, xz and yz planes,
-// (B) per (slot, v): the integer projections P_v[d] (v over the k1 and k2
-// orbits), the FP32 DFT in ascending d and the FP64 accumulation,
-// together with Q, E and M. Processed mchunk 4-slot groups at a time.
-// ---------------------------------------------------------------------------
-template <int L>
-__device__ __forceinline__ void measure_step(const Smem &sm, const Ctx &cx, const Int8Args &a,
-                                             int bin)
-{
-    constexpr int LL = L * L;
-    const int WR = cx.WR, RB = cx.RB, Tp = cx.Tp, nt = cx.nt;
-    // accumulators of (sample, slot t, bin): accs + t * tstride
-    const size_t tstride = (size_t)a.n_bins * SG_NACC;
-    double *accs = a.acc + ((size_t)cx.s * nt * a.n_bins + bin) * SG_NACC;
-    // energies and magnetisations first (one thread per slot), so that the
-    // projection phase reads nothing the next sweep overwrites
-    for (int t = threadIdx.x; t < nt; t += blockDim.x) {
-        double *ac = accs + (size_t)t * tstride;
-        double o5 = ac[5], o6 = ac[6], o7 = ac[7], o8 = ac[8];
-        for (int r = 0; r < 2; ++r) {
-            const long long Bv = (long long)sm.B[r * Tp + t];
-            const long long Mv = (long long)sm.M[r * Tp + t];
-            const double e = -__dadd_rn(__dmul_rn((double)Bv, a.qJ_d), __dmul_rn(a.h_d, (double)Mv));
-            o5 = __dadd_rn(o5, e);
-            o6 = __dadd_rn(o6, __dmul_rn(e, e));
-        }
-        for (int r = 0; r < 2; ++r) {
-            const double m = (double)(long long)sm.M[r * Tp + t];
-            o7 = __dadd_rn(o7, m);
-            o8 = __dadd_rn(o8, __dmul_rn(m, m));
-        }
-        ac[5] = o5;
-        ac[6] = o6;
-        ac[7] = o7;
-        ac[8] = o8;
-    }
-    for (int j0 = 0; j0 < WR; j0 += a.mchunk) {
-        const int nw = min(a.mchunk, WR - j0);
-        // (A) marginals; the group index varies fastest across lanes
-        for (int id = threadIdx.x; id < 3 * LL * nw; id += blockDim.x) {
-            const int jj = id % nw;
-            const int rest = id / nw;
-            const int ab = rest % LL;
-            const int plane = rest / LL;
-            const int A = ab % L, Bc = ab / L;  // A varies fastest
-            int base, step;
-            if (plane == 0) {        // (x=A, y=Bc), over z
-                base = A + L * Bc;
-                step = LL;
-            } else if (plane == 1) { // (x=A, z=Bc), over y
-                base = A + LL * Bc;
-                step = L;
-            } else {                 // (y=A, z=Bc), over x
-                base = L * A + LL * Bc;
-                step = 1;
-            }
-            const int woff = 8 * (j0 + jj);
-            uint32_t cnt = 0;
-#pragma unroll 4
-            for (int m = 0; m < L; ++m) {
-                const uint2 w = *reinterpret_cast<const uint2 *>(sm.spins + (base + m * step) * RB + woff);
-                cnt += w.x ^ w.y;
-            }
-            sm.marg[(plane * LL + A * L + Bc) * nw + jj] = cnt;
-        }
-        __syncthreads();
-        // (B) one thread per (slot, v): the L projections P_v[d] from L*L
-        // independent loads, then the FP32 DFT in ascending d and the FP64
-        // accumulation; v == 9 handles Q, E and M. The task's accumulators are
-        // loaded first so that their global-memory latency overlaps the counting.
-        // the slot varies fastest across lanes: one wave vector (one code path)
-        // per warp, adjacent marginal words per lane
-        for (int id = threadIdx.x; id < 4 * nw * 10; id += blockDim.x) {
-            const int sl = id % (4 * nw);  // 4*jj + kk
-            const int v = id / (4 * nw);
-            const int t = 4 * j0 + sl;
-            if (t >= nt) continue;
-            const int jj = sl >> 2, sh = 8 * (sl & 3);
-            double *ac = accs + (size_t)t * tstride;
-            double *acv = ac + (v == 9 ? 0 : 9 + 3 * v);
-            const int nacc = v == 9 ? 5 : 3;
-            double old[9];
-#pragma unroll
-            for (int q = 0; q < 9; ++q) old[q] = q < nacc ? acv[q] : 0.0;
-            int cs[L];
-            if (v == 9 || v == 0)
-                count_pattern<L, 0>(sm.marg + jj, nw, sh, cs);
-            else if (v == 1)
-                count_pattern<L, 1>(sm.marg + jj, nw, sh, cs);
-            else if (v == 2)
-                count_pattern<L, 1>(sm.marg + LL * nw + jj, nw, sh, cs);
-            else {
-                const int plane = (v == 3 || v == 4) ? 0 : (v == 5 || v == 6) ? 1 : 2;
-                const uint32_t *pm = sm.marg + plane * LL * nw + jj;
-                if (v == 3 || v == 5 || v == 7)
-                    count_pattern<L, 2>(pm, nw, sh, cs);
-                else
-                    count_pattern<L, 3>(pm, nw, sh, cs);
-            }
-            if (v == 9) {
-                int Qi = 0;
-#pragma unroll
-                for (int d = 0; d < L; ++d) Qi += LL - 2 * cs[d];
-                if (a.hist)  // P(q): replicas agree on (N + Q) / 2 sites
-                    atomicAdd(a.hist + ((size_t)t * a.n_bins + bin) * (L * LL + 1) + ((L * LL + Qi) >> 1),
-                              1ull);
-                const double Q = (double)Qi;
-                const double Q2 = __dmul_rn(Q, Q);
-                old[0] = __dadd_rn(old[0], 1.0);
-                old[1] = __dadd_rn(old[1], Q);
-                old[2] = __dadd_rn(old[2], Q2);
-                old[3] = __dadd_rn(old[3], __dmul_rn(Q2, Q));
-                old[4] = __dadd_rn(old[4], __dmul_rn(Q2, Q2));
-            } else {
-                float re = 0.0f, im = 0.0f;
-#pragma unroll
-                for (int d = 0; d < L; ++d) {
-                    const float Pf = (float)(LL - 2 * cs[d]);
-                    re = __fmaf_rn(Pf, sm.twid[d], re);
-                    im = __fmaf_rn(Pf, sm.twid[L + d], im);
-                }
-                const double dr = (double)re, di = (double)im;
-                old[0] = __dadd_rn(old[0], dr);
-                old[1] = __dadd_rn(old[1], di);
-                old[2] = __dadd_rn(old[2], __dadd_rn(__dmul_rn(dr, dr), __dmul_rn(di, di)));
-            }
-#pragma unroll
-            for (int q = 0; q < 9; ++q)
-                if (q < nacc) acv[q] = old[q];
-        }
-        // the next chunk's marginals overwrite this chunk's; after the last
-        // chunk the next sweep touches nothing this phase reads (spins, B and
-        // M are not read here), so no barrier is needed
-        if (j0 + a.mchunk < WR) __syncthreads();
-    }
-}
-
-__device__ __forceinline__ void copy16(void *dst, const void *src, size_t bytes)
-{
-    int4 *d = reinterpret_cast<int4 *>(dst);
-    const int4 *s = reinterpret_cast<const int4 *>(src);
-    for (size_t k = threadIdx.x; k < bytes / 16; k += blockDim.x) d[k] = s[k];
-}
-
-// ---------------------------------------------------------------------------
-// The fused kernel: for each sample of this CTA, load, run n_sweeps sweeps
-// (half-sweeps, energies, exchange, measurement), store.
-// ---------------------------------------------------------------------------
-template <int L, bool GAUSS, bool GST>
-__global__ void __launch_bounds__(kMaxThreads) int8_run_kernel(const Int8Args a)
-{
-    constexpr int N = L * L * L;
-    extern __shared__ __align__(16) uint8_t smem_raw[];
-    Smem sm;
-    carve(smem_raw, L, a.Tp, GAUSS, a.mchunk, &sm, GST);
-    Ctx cx;
-    cx.nt = a.nt;
-    cx.Tp = a.Tp;
-    cx.WR = a.Tp / 4;
-    cx.RB = 2 * a.Tp;
-    cx.seed_lo = a.seed_lo;
-    cx.seed_hi = a.seed_hi;
-    cx.hq = a.h_f;
-    const long long t_start = clock64();
-
-    // per-launch tables
-    for (int k = threadIdx.x; k < a.Tp; k += blockDim.x) {
-        sm.negbeta[k] = a.negbeta[k];
-        sm.dbeta[k] = a.dbeta[k];
-    }
-    for (int k = threadIdx.x; k < 2 * L; k += blockDim.x) sm.twid[k] = a.twid[k];
-    if (!GAUSS)
-        for (int k = threadIdx.x; k < a.Tp * 16; k += blockDim.x) sm.thr[k] = a.thr[k];
-
-    for (int64_t s = a.s_begin + blockIdx.x; s < a.s_end; s += gridDim.x) {
-        cx.s = s;
-        cx.k0 = a.seed_lo ^ kTagMet;
-        cx.k1 = (uint32_t)((s + a.s_key0) / a.rng_group);
-        __syncthreads();
-        if (GST) {
-            // large lattices: the CTA works on the sample's state in place
-            sm.spins = a.spins + (size_t)s * N * cx.RB;
-            if (!GAUSS)
-                sm.J8 = const_cast<uint8_t *>(a.J8) + (size_t)s * N * 8;
-            else
-                sm.Jg = const_cast<float *>(a.Jg) + (size_t)s * 3 * N;
-        } else {
-            copy16(sm.spins, a.spins + (size_t)s * N * cx.RB, (size_t)N * cx.RB);
-            if (!GAUSS)
-                copy16(sm.J8, a.J8 + (size_t)s * N * 8, (size_t)N * 8);
-            else
-                copy16(sm.Jg, a.Jg + (size_t)s * 3 * N, (size_t)3 * N * sizeof(float));
-        }
-        for (int k = threadIdx.x; k < 2 * a.Tp; k += blockDim.x) {
-            sm.xflag[k] = 0;
-            sm.B[k] = (unsigned long long)a.B[s * 2 * a.Tp + k];
-            sm.M[k] = (unsigned long long)a.M[s * 2 * a.Tp + k];
-        }
-        __syncthreads();
-
-        uint32_t stamp = 0;
-        bool stop = false;
-        const int64_t sweep0 = a.sweep0_dev ? *a.sweep0_dev : a.sweep0;
-        for (int it = 0; it < a.n_sweeps; ++it) {
-            const int64_t n = sweep0 + it;
-            if (a.watchdog || a.cancel) {  // launch-uniform branch
-                int why = 0;
-                if (threadIdx.x == 0) {
-                    if (a.watchdog && (unsigned long long)(clock64() - t_start) > a.watchdog)
-                        why = (int)SG_ETIMEOUT;
-                    else if (a.cancel && *a.cancel)
-                        why = (int)SG_ECANCELLED;
-                    if (why) atomicCAS(a.status, 0, why);
-                }
-                stop = __syncthreads_or(why != 0);
-                if (stop) break;
-            }
-            // one code path for both colours keeps the instruction footprint small
-#pragma unroll 1
-            for (int col = 0; col < 2; ++col) {
-                half_sweep<L, GAUSS>(sm, cx, (uint32_t)n, col);
-                if (col == 0)
-                    for (int k = threadIdx.x; k < 2 * a.Tp; k += blockDim.x) {
-                        sm.B[k] = 0;
-                        sm.M[k] = 0;
-                    }
-                __syncthreads();
-            }
-            if (a.exchange_every > 0 && (n + 1) % a.exchange_every == 0) {
-                const int64_t e = (n + 1) / a.exchange_every - 1;
-                ++stamp;
-                if (threadIdx.x < 32) exchange_decide(sm, cx, a, (int)(e & 1), (uint32_t)n, 0u, stamp);
-                __syncthreads();
-                exchange_apply<L>(sm, cx);
-                __syncthreads();
-            }
-            if (n >= a.n_therm && (n - a.n_therm) % a.measure_every == 0)
-                measure_step<L>(sm, cx, a, log_bin(n, a.n_bins));
-        }
-        __syncthreads();
-        if (!GST) copy16(a.spins + (size_t)s * N * cx.RB, sm.spins, (size_t)N * cx.RB);
-        for (int k = threadIdx.x; k < 2 * a.Tp; k += blockDim.x) {
-            a.B[s * 2 * a.Tp + k] = (int64_t)sm.B[k];
-            a.M[s * 2 * a.Tp + k] = (int64_t)sm.M[k];
-        }
-        // a stopped launch leaves later samples untouched; the status word tells
-        if (__syncthreads_or(stop)) break;
-    }
-}
 
 // ---------------------------------------------------------------------------
 // Instance preparation, conversion and standalone kernels (global memory).
@@ -990,39 +311,7 @@ inline int grid_for(int64_t work, int threads)
     return (int)b;
 }
 
-constexpr int kMaxSmem = 227 * 1024;
-
-// Raise the kernel's dynamic shared-memory limit once (before any capture).
-template <int L, bool G, bool GST>
-cudaError_t ensure_attr()
-{
-    static cudaError_t done = cudaFuncSetAttribute(
-        int8_run_kernel<L, G, GST>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
-    return done;
-}
-
-template <int L, bool G, bool GST>
-cudaError_t launch_t(const Int8Args &a, const Int8Launch &c, cudaStream_t st)
-{
-    cudaError_t e = ensure_attr<L, G, GST>();
-    if (e != cudaSuccess) return e;
-    int8_run_kernel<L, G, GST><<<c.grid, c.threads, c.smem, st>>>(a);
-    return cudaGetLastError();
-}
-
-template <int L, bool G, bool GST>
-int occ_t(int threads, size_t smem)
-{
-    auto k = int8_run_kernel<L, G, GST>;
-    if (ensure_attr<L, G, GST>() != cudaSuccess) return 0;
-    int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, threads, smem) != cudaSuccess)
-        return 0;
-    return n;
-}
-
 #define SG_FOR_EACH_L(X) X(2) X(4) X(6) X(8) X(10) X(12) X(14) X(16)
-#define SG_FOR_EACH_GST_L(X) X(10) X(12) X(14) X(16) X(18) X(20) X(22) X(24)
 
 }  // namespace
 
@@ -1030,7 +319,7 @@ size_t int8_smem_bytes(int L, int Tp, bool gauss, int mchunk, bool gst)
 {
     bool ok = false;
 #define X(LL) ok |= (L == LL);
-    if (gst) { SG_FOR_EACH_GST_L(X) } else { SG_FOR_EACH_L(X) }
+    if (gst) ok = int8_gst_has(L); else { SG_FOR_EACH_L(X) }
 #undef X
     if (!ok) return 0;
     size_t b = carve(nullptr, L, Tp, gauss, mchunk, nullptr, gst);
@@ -1042,35 +331,22 @@ int int8_max_threads(int) { return kMaxThreads; }
 cudaError_t int8_launch(int L, bool gauss, const Int8Args &a, const Int8Launch &cfg,
                         cudaStream_t st)
 {
-    if (cfg.gst) {
-#define X(LL)                                                                         \
-        if (L == LL)                                                                  \
-            return gauss ? launch_t<LL, true, true>(a, cfg, st) : launch_t<LL, false, true>(a, cfg, st);
-        SG_FOR_EACH_GST_L(X)
-#undef X
-    } else {
+    if (cfg.gst) return int8_launch_gst(L, gauss, a, cfg, st);
 #define X(LL)                                                                          \
-        if (L == LL)                                                                   \
-            return gauss ? launch_t<LL, true, false>(a, cfg, st) : launch_t<LL, false, false>(a, cfg, st);
-        SG_FOR_EACH_L(X)
+    if (L == LL)                                                                       \
+        return gauss ? launch_t<LL, true, false>(a, cfg, st) : launch_t<LL, false, false>(a, cfg, st);
+    SG_FOR_EACH_L(X)
 #undef X
-    }
     return cudaErrorInvalidValue;
 }
 
 int int8_ctas_per_sm(int L, bool gauss, int threads, size_t smem, bool gst)
 {
-    if (gst) {
+    if (gst) return int8_ctas_per_sm_gst(L, gauss, threads, smem);
 #define X(LL) \
-        if (L == LL) return gauss ? occ_t<LL, true, true>(threads, smem) : occ_t<LL, false, true>(threads, smem);
-        SG_FOR_EACH_GST_L(X)
+    if (L == LL) return gauss ? occ_t<LL, true, false>(threads, smem) : occ_t<LL, false, false>(threads, smem);
+    SG_FOR_EACH_L(X)
 #undef X
-    } else {
-#define X(LL) \
-        if (L == LL) return gauss ? occ_t<LL, true, false>(threads, smem) : occ_t<LL, false, false>(threads, smem);
-        SG_FOR_EACH_L(X)
-#undef X
-    }
     return 0;
 }
 

@@ -58,6 +58,11 @@ cudaError_t int8_launch(int L, bool gauss, const Int8Args &a, const Int8Launch &
                         cudaStream_t st);
 // Occupancy of the fused kernel (CTAs per SM), 0 if it cannot launch.
 int int8_ctas_per_sm(int L, bool gauss, int threads, size_t smem, bool gst);
+// The global-memory (large lattice) instances, in their own translation unit.
+bool int8_gst_has(int L);
+cudaError_t int8_launch_gst(int L, bool gauss, const Int8Args &a, const Int8Launch &cfg,
+                            cudaStream_t st);
+int int8_ctas_per_sm_gst(int L, bool gauss, int threads, size_t smem);
 
 // Instance preparation and state conversion kernels.
 cudaError_t int8_gen_pmj(uint8_t *J8, int64_t S, int L, uint32_t seed_lo, uint32_t seed_hi,

@@ -51,7 +51,8 @@ def test_ensemble_bytes_validates_arguments(lib):
     assert lib.sg_ensemble_bytes(5, 8, 16, 0, None) == 0   # odd L
     assert lib.sg_ensemble_bytes(4, 0, 16, 0, None) == 0   # no temperatures
     assert lib.sg_ensemble_bytes(4, 8, 0, 0, None) == 0    # no samples
-    assert lib.sg_ensemble_bytes(40, 8, 1, 0, None) == 0   # L too large
+    assert lib.sg_ensemble_bytes(66, 8, 1, 0, None) == 0   # L too large
+    assert lib.sg_ensemble_bytes(40, 8, 1, 0, None) > 0    # large L, int8 layout
 
 
 def test_library_estimators_match_oracle_estimators(lib):

@@ -1,0 +1,63 @@
+"""Large lattices (L = 26 .. 64) on the int8 path with the state in global
+memory, against the CPU oracle through the C ABI: spins, energies, binned
+accumulators and the overlap histogram agree bit for bit. L = 26 has the
+longest run of colour sites (lcm(13, 4) = 52), where the byte-wise sums of
+unsatisfied +-J bonds are flushed every four sites."""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_1403_4560_b300 import build as sgbuild
+from paper_1403_4560_b300 import inputs, sgmc
+
+pytestmark = pytest.mark.gpu
+THREADS = max(1, min(16, os.cpu_count() or 1))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA GPU required for the gpu-marked tests")
+    sgbuild.build()
+
+
+@pytest.mark.parametrize("L,nt,dist,S,sweeps", [
+    (26, 3, "pmj", 2, 6), (28, 2, "gauss", 1, 5), (32, 5, "pmj", 2, 4), (32, 2, "gauss", 2, 4),
+    (40, 2, "gauss", 1, 3), (64, 1, "pmj", 1, 2)])
+def test_large_lattice_is_bit_exact(L, nt, dist, S, sweeps):
+    T = inputs.geometric_ladder(0.6, 1.5, nt)
+    J, s0 = inputs.make_instance(dist, L, S, nt, seed=L)
+    opt = dict(log_bins=3, pq_hist=1)
+    with sgmc.Ensemble(L, 0.15, T, dist, S, 100 + L, J=J, spins=s0, **opt) as ens:
+        ens.sweep(sweeps - 1)
+        ens.sweep(1)
+        st = orc.State(L, T, 0.15, dist == "gauss", seed=100 + L, J=J, spins=s0, log_bins=3,
+                       pq_hist=True)
+        st.run(sweeps, threads=THREADS)
+        np.testing.assert_array_equal(ens.spins(), st.spins)
+        B, M = ens.energies()
+        np.testing.assert_array_equal(B, st.B)
+        np.testing.assert_array_equal(M, st.M)
+        np.testing.assert_array_equal(ens.accumulators(), st.acc)
+        np.testing.assert_array_equal(ens.histogram(), st.hist)
+
+
+def test_library_drawn_large_instance_matches_oracle_generators():
+    L, S, nt, seed = 32, 2, 3, 9
+    T = inputs.geometric_ladder(0.6, 1.5, nt)
+    with sgmc.Ensemble(L, 0.2, T, "pmj", S, seed) as ens:
+        np.testing.assert_array_equal(ens.couplings(), orc.pmj_couplings(seed, S, L))
+        np.testing.assert_array_equal(ens.spins(), orc.init_spins(seed, S, nt, L))
+
+
+def test_unbuilt_lattice_sizes_are_rejected():
+    T = inputs.geometric_ladder(0.6, 1.5, 2)
+    with pytest.raises(sgmc.SgError) as ei:
+        sgmc.Ensemble(34, 0.2, T, "pmj", 1, 1)
+    assert ei.value.status == sgmc.SG_EUNSUPPORTED
+    with pytest.raises(sgmc.SgError) as ei:
+        sgmc.Ensemble(66, 0.2, T, "pmj", 1, 1)
+    assert ei.value.status == sgmc.SG_EINVAL
