@@ -202,10 +202,13 @@ sg_status configure_launch(sg_ensemble *e)
             }
             if (!occ) continue;
             // useful threads per SM: work items in flight per round, over the
-            // resident CTAs; ties go to more CTAs (barriers overlap) and fewer threads
+            // CTAs an SM actually gets (one CTA per sample, so never more than
+            // ceil(S / SMs)); ties go to more CTAs (barriers overlap) and fewer threads
+            const int64_t per_sm = (e->S + e->num_sms - 1) / e->num_sms;
+            const int eff = (int)std::min<int64_t>(occ, per_sm);
             const int rounds = (items + t - 1) / t;
-            const double useful = (double)items / rounds * occ;
-            const double score = std::min(useful, 1024.0) + 0.5 * occ - 1e-3 * t;
+            const double useful = (double)items / rounds * eff;
+            const double score = std::min(useful, 1024.0) + 0.5 * eff - 1e-3 * t;
             if (score > best_score) {
                 best_score = score;
                 best_t = t;
