@@ -287,6 +287,10 @@ typedef struct {
     size_t device_bytes;
     int32_t log_bins;  /* accumulator bins B (>= 1)                    */
     int32_t pq_hist;   /* 1 if the overlap histogram is kept           */
+    int32_t threads_per_block;  /* launch shape of the sweep kernel    */
+    int32_t grid;               /* CTAs per sweep launch               */
+    int32_t state_in_shared;    /* 1: state held in shared memory for a
+                                   chunk of sweeps; 0: in global memory */
 } sg_info;
 sg_status sg_get_info(const sg_ensemble *e, sg_info *out);
 

@@ -918,6 +918,15 @@ sg_status sg_get_info(const sg_ensemble *e, sg_info *out)
     out->device_bytes = e->bytes;
     out->log_bins = e->n_bins;
     out->pq_hist = e->hist ? 1 : 0;
+    if (e->msc) {
+        out->threads_per_block = msc_threads(e->L, e->opt.threads_per_block);
+        out->grid = (e->nt / 2 + 1) * (int32_t)(e->S / 64);
+        out->state_in_shared = 1;
+    } else {
+        out->threads_per_block = e->launch.threads;
+        out->grid = e->launch.grid;
+        out->state_in_shared = e->launch.gst ? 0 : 1;
+    }
     return SG_OK;
 }
 

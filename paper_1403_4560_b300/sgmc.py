@@ -41,7 +41,9 @@ class Info(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int32), ("n_T", ctypes.c_int32), ("layout", ctypes.c_int32),
                 ("dist", ctypes.c_int32), ("n_samples", ctypes.c_int64), ("h", ctypes.c_double),
                 ("attempts_per_sweep", ctypes.c_int64), ("device_bytes", ctypes.c_size_t),
-                ("log_bins", ctypes.c_int32), ("pq_hist", ctypes.c_int32)]
+                ("log_bins", ctypes.c_int32), ("pq_hist", ctypes.c_int32),
+                ("threads_per_block", ctypes.c_int32), ("grid", ctypes.c_int32),
+                ("state_in_shared", ctypes.c_int32)]
 
 
 class TuneReport(ctypes.Structure):
