@@ -121,6 +121,12 @@ typedef struct {
                                   at most 64                                 */
     int32_t pq_hist;           /* nonzero: also count the overlap histogram
                                   P(q) per slot and bin (sg_get_histogram)   */
+    int32_t state_mode;        /* INT8 layout: where the sweep kernel keeps a
+                                  sample's state: 0 = library choice (shared
+                                  memory when it fits), 1 = shared memory
+                                  (SG_EUNSUPPORTED if it does not fit), 2 =
+                                  global memory (L >= 10). Results do not
+                                  depend on it.                              */
 } sg_options;
 
 /* Fill *opt with the defaults: INT8 layout, rng_group 1, exchange and

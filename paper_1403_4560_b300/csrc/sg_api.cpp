@@ -183,6 +183,7 @@ sg_status configure_launch(sg_ensemble *e)
     // sample's state does not fit (large L or many temperatures)
     for (int pass = 0; pass < 2; ++pass) {
         const bool gst = pass == 1;
+        if ((e->opt.state_mode == 1 && gst) || (e->opt.state_mode == 2 && !gst)) continue;
         double best_score = -1.0;
         int best_t = 0, best_m = 0, best_occ = 0;
         for (int t = WR; t <= maxt; t += WR) {
@@ -384,6 +385,7 @@ sg_status validate(int L, const double *T, int nt, sg_coupling dist, int64_t S,
     if (o.sample_base < 0 || o.sample_base + S > ((int64_t)1 << 32))
         return fail(SG_EINVAL, "sample_base + n_samples must be in [0, 2^32]");
     if (o.log_bins < 0 || o.log_bins > 64) return fail(SG_EINVAL, "log_bins must be in [0, 64]");
+    if (o.state_mode < 0 || o.state_mode > 2) return fail(SG_EINVAL, "state_mode must be 0, 1 or 2");
     if (o.layout == SG_LAYOUT_MSC64) {
         if (dist != SG_PM_J) return fail(SG_EINVAL, "the MSC64 layout needs +-J couplings");
         if (o.sample_base % 64) return fail(SG_EINVAL, "the MSC64 layout needs sample_base % 64 == 0");

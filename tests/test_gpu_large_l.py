@@ -74,3 +74,31 @@ def test_few_large_samples_get_wide_ctas():
     with sgmc.Ensemble(12, 0.1, inputs.geometric_ladder(0.5, 1.6, 24), "gauss", 512, 1) as ens:
         info = ens.info()
         assert info.state_in_shared == 1 and info.threads_per_block >= 64
+
+
+@pytest.mark.parametrize("L,dist", [(10, "gauss"), (12, "pmj")])
+def test_state_in_shared_or_global_memory_gives_the_same_chain(L, dist):
+    T = inputs.geometric_ladder(0.5, 1.6, 6)
+    J, s0 = inputs.make_instance(dist, L, 5, 6, seed=L)
+    out = []
+    for mode in (1, 2):
+        with sgmc.Ensemble(L, 0.2, T, dist, 5, 3, J=J, spins=s0, state_mode=mode, log_bins=3,
+                           pq_hist=1) as ens:
+            assert ens.info().state_in_shared == (1 if mode == 1 else 0)
+            ens.sweep(25)
+            out.append((ens.spins(), ens.accumulators(), ens.histogram()))
+    for a, b in zip(*out):
+        np.testing.assert_array_equal(a, b)
+
+
+def test_state_mode_requests_that_cannot_be_met_are_rejected():
+    T = inputs.geometric_ladder(0.5, 1.6, 32)
+    with pytest.raises(sgmc.SgError) as ei:  # 262 KB of spins per sample
+        sgmc.Ensemble(16, 0.2, T, "gauss", 4, 1, state_mode=1)
+    assert ei.value.status == sgmc.SG_EUNSUPPORTED
+    with pytest.raises(sgmc.SgError) as ei:  # no global-memory kernel below L = 10
+        sgmc.Ensemble(8, 0.2, T, "gauss", 4, 1, state_mode=2)
+    assert ei.value.status == sgmc.SG_EUNSUPPORTED
+    with pytest.raises(sgmc.SgError) as ei:
+        sgmc.Ensemble(8, 0.2, T, "gauss", 4, 1, state_mode=3)
+    assert ei.value.status == sgmc.SG_EINVAL
