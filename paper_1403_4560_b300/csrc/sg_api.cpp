@@ -837,10 +837,20 @@ sg_status sg_set_spins(sg_ensemble *e, const int8_t *in)
 {
     if (!e || !in) return fail(SG_EINVAL, "bad arguments");
     const size_t bytes = (size_t)e->S * 2 * e->nt * e->L * e->L * e->L;
-    if (!spins_valid(in, bytes)) return fail(SG_EINVAL, "spins must be +1 or -1");
     int8_t *d = nullptr;
     SG_CUDA(stage_buffer(e, bytes, (void **)&d), "staging buffer");
-    cudaError_t ce = cudaMemcpyAsync(d, in, bytes, cudaMemcpyHostToDevice, e->stream);
+    // upload to the staging buffer and check the values there (a pass at HBM
+    // speed instead of one host thread); the state is replaced only if every
+    // value is +1 or -1
+    int *flag = (int *)((uint8_t *)e->status + 128);
+    int bad = 0;
+    cudaError_t ce = cudaMemsetAsync(flag, 0, sizeof(int), e->stream);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(d, in, bytes, cudaMemcpyHostToDevice, e->stream);
+    if (ce == cudaSuccess) ce = check_pm1(d, bytes, flag, e->stream);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(&bad, flag, sizeof(int), cudaMemcpyDeviceToHost, e->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(e->stream);
+    if (ce != cudaSuccess) return cuda_fail(ce, "set spins");
+    if (bad) return fail(SG_EINVAL, "spins must be +1 or -1");
     if (ce == cudaSuccess)
         ce = e->msc ? msc_import_spins(e->W, d, e->S / 64, e->L, e->nt, e->stream)
                     : int8_import_spins(e->spins, d, e->S, e->L, e->nt, e->Tp, e->stream);

@@ -303,6 +303,27 @@ __global__ void advance_kernel(int64_t *ctr, int64_t n)
     if (threadIdx.x == 0 && blockIdx.x == 0) *ctr += n;
 }
 
+// Sets *flag when any of the n bytes is neither +1 nor -1. Eight bytes per
+// step: x = w ^ 0x01.. has every byte 0x00 (for +1) or 0xFE (for -1) exactly
+// when all bytes are valid.
+__global__ void check_pm1_kernel(const int8_t *c, int64_t n, int *flag)
+{
+    const uint64_t ones = 0x0101010101010101ull;
+    const int64_t words = n / 8;
+    const uint64_t *w = reinterpret_cast<const uint64_t *>(c);
+    bool bad = false;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < words;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t x = w[g] ^ ones;
+        const uint64_t z = (x >> 1) & 0x7F7F7F7F7F7F7F7Full;  // 0x00 or 0x7F per valid byte
+        bad |= ((x & ones) | ((z + ones) & 0x7E7E7E7E7E7E7E7Eull)) != 0;
+    }
+    for (int64_t k = 8 * words + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x)
+        bad |= c[k] != 1 && c[k] != -1;
+    if (bad) atomicOr(flag, 1);
+}
+
 inline int grid_for(int64_t work, int threads)
 {
     int64_t b = (work + threads - 1) / threads;
@@ -422,6 +443,13 @@ cudaError_t int8_exchange(const Int8Args &a, int L, bool gauss, int parity, uint
 cudaError_t threshold_map(const float *x, int n, uint32_t *out, cudaStream_t st)
 {
     thr_map_kernel<<<grid_for(n, 256), 256, 0, st>>>(x, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t check_pm1(const int8_t *c, size_t n, int *flag, cudaStream_t st)
+{
+    // c comes from cudaMalloc (8-byte aligned); one 8-byte word per thread step
+    check_pm1_kernel<<<grid_for((int64_t)(n / 8 + 1), 256), 256, 0, st>>>(c, (int64_t)n, flag);
     return cudaGetLastError();
 }
 

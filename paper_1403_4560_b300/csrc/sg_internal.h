@@ -84,6 +84,8 @@ cudaError_t int8_exchange(const Int8Args &a, int L, bool gauss, int parity, uint
                           cudaStream_t st);
 cudaError_t threshold_map(const float *x, int n, uint32_t *out, cudaStream_t st);
 cudaError_t advance_counter(int64_t *ctr, int64_t n, cudaStream_t st);
+// Sets *flag (device) when a byte of c[0..n) (device, 8-byte aligned) is not +-1.
+cudaError_t check_pm1(const int8_t *c, size_t n, int *flag, cudaStream_t st);
 cudaError_t int8_measure_k_noalloc(const Int8Args &a, int L, const int *k_host, int nk,
                                    float *out_host, size_t out_floats, cudaStream_t st);
 cudaError_t int8_measure_k(const Int8Args &a, int L, const int *k_dev, int nk, float *out,

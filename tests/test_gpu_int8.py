@@ -325,3 +325,25 @@ def test_checkpoint_and_resume_is_bit_exact(layout, dist, S):
         r.sweep(18)
         np.testing.assert_array_equal(r.spins(), want[0])
         np.testing.assert_array_equal(r.accumulators(), want[1])
+
+
+@pytest.mark.parametrize("layout", [0, sgmc.SG_LAYOUT_MSC64])
+def test_set_spins_rejects_values_other_than_pm1_and_keeps_the_state(layout):
+    """The values are checked on the device after the upload; a bad array
+    (a 0, a 2, in the middle or in the ragged tail) leaves the state as it was."""
+    L, nt, S = 4, 3, 64
+    T = inputs.geometric_ladder(0.5, 1.5, nt)
+    with sgmc.Ensemble(L, 0.2, T, "pmj", S, 5, layout=layout) as ens:
+        ens.sweep(3)
+        before, (B0, M0) = ens.spins(), ens.energies()
+        for pos, val in ((0, 0), (S * 2 * nt * L ** 3 // 2 + 3, 2), (S * 2 * nt * L ** 3 - 1, 0)):
+            bad = before.copy().reshape(-1)
+            bad[pos] = val
+            with pytest.raises(sgmc.SgError) as ei:
+                ens.set_spins(bad.reshape(before.shape))
+            assert ei.value.status == sgmc.SG_EINVAL
+            np.testing.assert_array_equal(ens.spins(), before)
+            np.testing.assert_array_equal(ens.energies()[0], B0)
+        flipped = -before
+        ens.set_spins(flipped)
+        np.testing.assert_array_equal(ens.spins(), flipped)
