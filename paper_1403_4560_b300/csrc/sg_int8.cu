@@ -347,7 +347,12 @@ size_t int8_smem_bytes(int L, int Tp, bool gauss, int mchunk, bool gst)
     return b <= (size_t)kMaxSmem ? b : 0;
 }
 
-int int8_max_threads(int) { return kMaxThreads; }
+int int8_max_threads(int L)
+{
+    // the shared-memory and global-memory instances of one L share a bound
+    // except below L = 10, where only shared-memory instances exist
+    return L <= 8 ? KernelBounds<8, false>::threads : kMaxThreads;
+}
 
 cudaError_t int8_launch(int L, bool gauss, const Int8Args &a, const Int8Launch &cfg,
                         cudaStream_t st)
