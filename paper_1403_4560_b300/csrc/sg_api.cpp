@@ -167,29 +167,30 @@ std::string tune_key(const sg_ensemble *e, bool gst)
            (gst ? ":gst" : ":smem");
 }
 
-// Launch shape: threads per CTA are a multiple of WR = Tp/4 (each thread
-// keeps one 4-slot group for the whole half-sweep); among the candidates the
+// Launch shape: threads per CTA are a multiple of int8_thread_quantum (each
+// thread keeps one (4-slot group, replica) pair for the whole half-sweep); among the candidates the
 // one with the best product of work balance and resident warps per SM wins,
 // then the largest measurement chunk that keeps that occupancy.
 sg_status configure_launch(sg_ensemble *e)
 {
     const int WR = e->Tp / 4;
+    const int Q = int8_thread_quantum(e->Tp);  // thread counts are multiples of Q
     const int L = e->L, H = L / 2;
     int run = H;
     while (run % 4) run += H;
-    const int items = (L * L * L / 2) / run * WR;
-    const int maxt = int8_max_threads(e->L);
+    const int items = (L * L * L / 2) / run * Q;
     // shared-memory residency first; the global-memory variant when the
     // sample's state does not fit (large L or many temperatures)
     for (int pass = 0; pass < 2; ++pass) {
         const bool gst = pass == 1;
+        const int maxt = int8_max_threads(e->L, gst);
         if ((e->opt.state_mode == 1 && gst) || (e->opt.state_mode == 2 && !gst)) continue;
         double best_score = -1.0;
         int best_t = 0, best_m = 0, best_occ = 0;
-        for (int t = WR; t <= maxt; t += WR) {
+        for (int t = Q; t <= maxt; t += Q) {
             if (t < 32) continue;  // the measurement needs one full warp
             if (e->opt.threads_per_block > 0 &&  // a request is clamped to what the kernel allows
-                t != std::max(WR, (std::min(e->opt.threads_per_block, maxt) / WR) * WR))
+                t != std::max(((32 + Q - 1) / Q) * Q, (std::min(e->opt.threads_per_block, maxt) / Q) * Q))
                 continue;
             int occ = 0, m_for = 0;
             for (int m = WR; m >= 1; --m) {
@@ -1059,12 +1060,13 @@ sg_status sg_autotune(sg_ensemble *e, int64_t trial_sweeps, sg_tune_report *rep)
     const sg_options orig_opt = e->opt;
     e->opt.sweeps_per_launch = 0;
     const int WR = e->Tp / 4;
+    const int Q = int8_thread_quantum(e->Tp);
     double best_ms = 1e300, default_ms = 0.0;
     int best_t = orig_launch.threads, best_m = orig_m, ncand = 0;
     cudaError_t ce = save(false);
     std::vector<std::pair<int, int>> cands;
     cands.push_back({orig_launch.threads, orig_m});
-    for (int t = ((32 + WR - 1) / WR) * WR; t <= int8_max_threads(e->L); t += WR) {
+    for (int t = ((32 + Q - 1) / Q) * Q; t <= int8_max_threads(e->L, orig_launch.gst); t += Q) {
         int best_occ = 0, m_for = 0;
         for (int m = WR; m >= 1; --m) {
             const size_t smem = int8_smem_bytes(e->L, e->Tp, e->gauss, m, orig_launch.gst);

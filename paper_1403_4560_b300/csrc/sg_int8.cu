@@ -347,11 +347,18 @@ size_t int8_smem_bytes(int L, int Tp, bool gauss, int mchunk, bool gst)
     return b <= (size_t)kMaxSmem ? b : 0;
 }
 
-int int8_max_threads(int L)
+int int8_thread_quantum(int Tp)
 {
-    // the shared-memory and global-memory instances of one L share a bound
-    // except below L = 10, where only shared-memory instances exist
-    return L <= 8 ? KernelBounds<8, false>::threads : kMaxThreads;
+    // a half-sweep thread keeps one (4-slot group, replica) pair: Tp/4 * 2
+    return Tp / 2;
+}
+
+int int8_max_threads(int L, bool gst)
+{
+    if (gst) return KernelBounds<10, true>::threads;  // the same for every L
+    if (L <= 8) return KernelBounds<8, false>::threads;
+    if (L <= 12) return KernelBounds<12, false>::threads;
+    return KernelBounds<16, false>::threads;
 }
 
 cudaError_t int8_launch(int L, bool gauss, const Int8Args &a, const Int8Launch &cfg,

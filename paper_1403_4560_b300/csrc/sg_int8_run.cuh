@@ -23,7 +23,7 @@
 //   +-J    [N][8] bytes      bond bits (+x, -x, +y, -y, +z, -z, 0, 0), 1 => J = -1
 //   Gauss  [3][N] float      J[d][i] joins i and i + e_d
 // Work item of a half-sweep: (run of RUN = lcm(L/2, 4) consecutive sites of
-// one colour, one 4-slot group, both replicas). RUN is a multiple of 4, so
+// one colour, one 4-slot group, one replica). RUN is a multiple of 4, so
 // the Philox calls (four sites each) never straddle two items.
 #pragma once
 #include <cuda_runtime.h>
@@ -40,18 +40,21 @@ namespace {
 
 constexpr int kMaxThreads = 512;
 
-// Launch bounds of an instance. Small lattices held in shared memory (L <= 8)
-// fit several samples per SM, so they are compiled for up to 192 threads and
-// four CTAs per SM (at most 80 registers): more resident warps hide the
-// Philox and exponential latency better than the spill-free 128-register
-// build does (B300, L = 8 with 48 chains: 164 vs 147 attempts/ns). Larger
-// lattices keep 128 registers, where the extra spills cost more than the
-// warps gain.
+// Launch bounds of an instance, chosen from B300 measurements of the
+// register / resident-warp trade-off:
+//   L <= 8 in shared memory: several samples fit per SM, so up to 192
+//     threads and four CTAs per SM (at most 80 registers);
+//   L = 10, 12 in shared memory: two samples fit per SM; 320 threads and
+//     two CTAs per SM (at most 96 registers, no spills with one replica per
+//     work item) give up to 20 warps instead of 13.5;
+//   larger lattices (one CTA per SM in shared memory, or global-memory
+//     state): up to 512 threads with 128 registers.
 template <int L, bool GST>
 struct KernelBounds {
     static constexpr bool kSmall = L <= 8 && !GST;
-    static constexpr int threads = kSmall ? 192 : kMaxThreads;
-    static constexpr int min_blocks = kSmall ? 4 : 1;
+    static constexpr bool kMid = (L == 10 || L == 12) && !GST;
+    static constexpr int threads = kSmall ? 192 : kMid ? 320 : kMaxThreads;
+    static constexpr int min_blocks = kSmall ? 4 : kMid ? 2 : 1;
 };
 
 __host__ __device__ constexpr int gcd_c(int a, int b) { return b == 0 ? a : gcd_c(b, a % b); }
@@ -212,11 +215,15 @@ __device__ __forceinline__ uint32_t gauss_word(uint32_t s, uint32_t nxp, uint32_
 
 // ---------------------------------------------------------------------------
 // One checkerboard half-sweep of colour COL over all chains of the sample.
-// Work item: (run of RUN colour-COL sites, 4-slot group j) covering both
-// replicas, i.e. 8 chains. For COL == 1 it also accumulates B and M of the
-// post-sweep configuration: every bond has exactly one colour-1 end, so
-// summing s_i * b_i over colour-1 sites counts each bond once; M pairs each
-// colour-1 site with its x^1 partner (colour 0, final after the colour-0 half).
+// Work item: (run of RUN colour-COL sites, 4-slot group j, replica r), i.e.
+// 4 chains; a thread keeps (j, r) for every item it takes, so its slots'
+// tables are loaded once. One replica per item halves the live random
+// numbers and spin words against an item over both replicas, which keeps
+// the kernel's registers low enough for more resident warps. For COL == 1 it
+// also accumulates B and M of the post-sweep configuration: every bond has
+// exactly one colour-1 end, so summing s_i * b_i over colour-1 sites counts
+// each bond once; M pairs each colour-1 site with its x^1 partner (colour 0,
+// final after the colour-0 half).
 // ---------------------------------------------------------------------------
 template <int L, bool GAUSS>
 __device__ __forceinline__ void half_sweep(const Smem &sm, const Ctx &cx, uint32_t n_sweep,
@@ -228,9 +235,10 @@ __device__ __forceinline__ void half_sweep(const Smem &sm, const Ctx &cx, uint32
     constexpr int NG = RUN / 4;
     constexpr int U = (N / 2) / RUN;
     const int WR = cx.WR, RB = cx.RB;
-    const int j = threadIdx.x % WR;  // fixed per thread: blockDim.x is a multiple of WR
+    const int jr = threadIdx.x % (2 * WR);  // fixed per thread: blockDim.x is a multiple of 2 WR
+    const int j = jr >> 1, r = jr & 1;
     const int t0 = 4 * j;
-    const int items = U * WR;
+    const int items = U * 2 * WR;
 
     uint32_t valid = 0;  // bytes of real (not padding) slots in this group
 #pragma unroll
@@ -241,41 +249,39 @@ __device__ __forceinline__ void half_sweep(const Smem &sm, const Ctx &cx, uint32
 #pragma unroll
     for (int kk = 0; kk < 4; ++kk) nbeta[kk] = GAUSS ? sm.negbeta[t0 + kk] : 0.0f;
     const uint32_t *thr_w = GAUSS ? nullptr : sm.thr + t0 * 16;
+    const int woff = 8 * j + 4 * r;  // byte offset of this (group, replica) word in a site row
 
     for (int item = threadIdx.x; item < items; item += blockDim.x) {
-        const int u = item / WR;
-        uint32_t eacc0 = 0, eacc1 = 0, macc0 = 0, macc1 = 0;  // byte-wise partial sums
-        int bg[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+        const int u = item / (2 * WR);
+        uint32_t eacc = 0, macc = 0;  // byte-wise partial sums
+        int bg[4] = {0, 0, 0, 0};
         // long runs would overflow the byte-wise sums of unsatisfied bonds
         // (6 per site): those are flushed into bg after every group of 4 sites
         constexpr bool kFlushU = 6 * RUN > 255;
         for (int g = 0; g < NG; ++g) {
             const uint32_t c0 = (uint32_t)(u * NG + g);
-            uint32_t rnd[2][4][4];
+            uint32_t rnd[4][4];
 #pragma unroll
-            for (int r = 0; r < 2; ++r)
-#pragma unroll
-                for (int kk = 0; kk < 4; ++kk) {
-                    const uint32_t c2 = ((uint32_t)COL << 24) | ((uint32_t)r << 16) |
-                                        (uint32_t)(t0 + kk);
-                    const u32x4 o = philox10(cx.k0, cx.k1, c0, n_sweep, c2, cx.seed_hi);
-                    rnd[r][kk][0] = o.v[0];
-                    rnd[r][kk][1] = o.v[1];
-                    rnd[r][kk][2] = o.v[2];
-                    rnd[r][kk][3] = o.v[3];
-                }
+            for (int kk = 0; kk < 4; ++kk) {
+                const uint32_t c2 = ((uint32_t)COL << 24) | ((uint32_t)r << 16) | (uint32_t)(t0 + kk);
+                const u32x4 o = philox10(cx.k0, cx.k1, c0, n_sweep, c2, cx.seed_hi);
+                rnd[kk][0] = o.v[0];
+                rnd[kk][1] = o.v[1];
+                rnd[kk][2] = o.v[2];
+                rnd[kk][3] = o.v[3];
+            }
 #pragma unroll
             for (int lane = 0; lane < 4; ++lane) {
                 const SiteNb<L> st(u * RUN + 4 * g + lane, COL);
-                const int own = st.i * RB + 8 * j;
-                const uint2 s = *reinterpret_cast<const uint2 *>(sm.spins + own);
-                const uint2 nxp = *reinterpret_cast<const uint2 *>(sm.spins + own + st.dxp * RB);
-                const uint2 nxm = *reinterpret_cast<const uint2 *>(sm.spins + own + st.dxm * RB);
-                const uint2 nyp = *reinterpret_cast<const uint2 *>(sm.spins + own + st.dyp * RB);
-                const uint2 nym = *reinterpret_cast<const uint2 *>(sm.spins + own + st.dym * RB);
-                const uint2 nzp = *reinterpret_cast<const uint2 *>(sm.spins + own + st.dzp * RB);
-                const uint2 nzm = *reinterpret_cast<const uint2 *>(sm.spins + own + st.dzm * RB);
-                uint2 fm;
+                const int own = st.i * RB + woff;
+                const uint32_t s = lds32(sm.spins, own);
+                const uint32_t nxp = lds32(sm.spins, own + st.dxp * RB);
+                const uint32_t nxm = lds32(sm.spins, own + st.dxm * RB);
+                const uint32_t nyp = lds32(sm.spins, own + st.dyp * RB);
+                const uint32_t nym = lds32(sm.spins, own + st.dym * RB);
+                const uint32_t nzp = lds32(sm.spins, own + st.dzp * RB);
+                const uint32_t nzm = lds32(sm.spins, own + st.dzm * RB);
+                uint32_t fm;
                 if constexpr (!GAUSS) {
                     const uint2 jb = *reinterpret_cast<const uint2 *>(sm.J8 + 8 * st.i);
                     const uint32_t m[6] = {__byte_perm(jb.x, jb.y, 0x0000),
@@ -284,68 +290,49 @@ __device__ __forceinline__ void half_sweep(const Smem &sm, const Ctx &cx, uint32
                                            __byte_perm(jb.x, jb.y, 0x3333),
                                            __byte_perm(jb.x, jb.y, 0x4444),
                                            __byte_perm(jb.x, jb.y, 0x5555)};
-                    uint32_t uw0, uw1;
-                    fm.x = pmj_word(s.x, nxp.x, nxm.x, nyp.x, nym.x, nzp.x, nzm.x, m, thr_w,
-                                    rnd[0], lane, valid, uw0);
-                    fm.y = pmj_word(s.y, nxp.y, nxm.y, nyp.y, nym.y, nzp.y, nzm.y, m, thr_w,
-                                    rnd[1], lane, valid, uw1);
+                    uint32_t uw;
+                    fm = pmj_word(s, nxp, nxm, nyp, nym, nzp, nzm, m, thr_w, rnd, lane, valid, uw);
                     if (COL == 1) {
-                        const uint32_t f0 = fm.x * 0xFFu, f1 = fm.y * 0xFFu;
-                        eacc0 += uw0 ^ ((uw0 ^ (0x06060606u - uw0)) & f0);
-                        eacc1 += uw1 ^ ((uw1 ^ (0x06060606u - uw1)) & f1);
+                        const uint32_t f = fm * 0xFFu;
+                        eacc += uw ^ ((uw ^ (0x06060606u - uw)) & f);
                     }
                 } else {
                     const float jv[6] = {sm.Jg[st.i], sm.Jg[st.i + st.dxm], sm.Jg[N + st.i],
                                          sm.Jg[N + st.i + st.dym], sm.Jg[2 * N + st.i],
                                          sm.Jg[2 * N + st.i + st.dzm]};
-                    int bq0[4], bq1[4];
-                    fm.x = gauss_word<true>(s.x, nxp.x, nxm.x, nyp.x, nym.x, nzp.x, nzm.x, jv,
-                                            cx.hq, nbeta, rnd[0], lane, valid, bq0);
-                    fm.y = gauss_word<true>(s.y, nxp.y, nxm.y, nyp.y, nym.y, nzp.y, nzm.y, jv,
-                                            cx.hq, nbeta, rnd[1], lane, valid, bq1);
+                    int bq[4];
+                    fm = gauss_word<true>(s, nxp, nxm, nyp, nym, nzp, nzm, jv, cx.hq, nbeta, rnd,
+                                          lane, valid, bq);
                     if (COL == 1) {
 #pragma unroll
-                        for (int kk = 0; kk < 4; ++kk) {
-                            bg[0][kk] += bq0[kk];
-                            bg[1][kk] += bq1[kk];
-                        }
+                        for (int kk = 0; kk < 4; ++kk) bg[kk] += bq[kk];
                     }
                 }
-                uint2 sn;
-                sn.x = s.x ^ fm.x;
-                sn.y = s.y ^ fm.y;
-                *reinterpret_cast<uint2 *>(sm.spins + own) = sn;
+                const uint32_t sn = s ^ fm;
+                sts32(sm.spins, own, sn);
                 if (COL == 1) {
-                    const uint2 partner = (st.x & 1) ? nxm : nxp;
-                    macc0 += sn.x + partner.x;
-                    macc1 += sn.y + partner.y;
+                    const uint32_t partner = (st.x & 1) ? nxm : nxp;
+                    macc += sn + partner;
                 }
             }
             if (kFlushU && !GAUSS && COL == 1) {
 #pragma unroll
-                for (int kk = 0; kk < 4; ++kk) {
-                    bg[0][kk] += (eacc0 >> (8 * kk)) & 0xFFu;
-                    bg[1][kk] += (eacc1 >> (8 * kk)) & 0xFFu;
-                }
-                eacc0 = eacc1 = 0;
+                for (int kk = 0; kk < 4; ++kk) bg[kk] += (eacc >> (8 * kk)) & 0xFFu;
+                eacc = 0;
             }
         }
         if (COL == 1) {
 #pragma unroll
-            for (int r = 0; r < 2; ++r)
-#pragma unroll
-                for (int kk = 0; kk < 4; ++kk) {
-                    const int t = t0 + kk;
-                    if (t >= cx.nt) continue;
-                    const uint32_t ea = r ? eacc1 : eacc0;
-                    const uint32_t ma = r ? macc1 : macc0;
-                    // +-J: s b = 6 - 2u per colour-1 site; M: each pair gives 2 - 2*(#-1)
-                    const long long usum = (long long)((ea >> (8 * kk)) & 0xFFu) + (kFlushU ? bg[r][kk] : 0);
-                    const long long b = GAUSS ? (long long)bg[r][kk] : 6LL * RUN - 2LL * usum;
-                    const long long mm = 2LL * RUN - 2LL * ((ma >> (8 * kk)) & 0xFFu);
-                    atomicAdd(&sm.B[r * cx.Tp + t], (unsigned long long)b);
-                    atomicAdd(&sm.M[r * cx.Tp + t], (unsigned long long)mm);
-                }
+            for (int kk = 0; kk < 4; ++kk) {
+                const int t = t0 + kk;
+                if (t >= cx.nt) continue;
+                // +-J: s b = 6 - 2u per colour-1 site; M: each pair gives 2 - 2*(#-1)
+                const long long usum = (long long)((eacc >> (8 * kk)) & 0xFFu) + (kFlushU ? bg[kk] : 0);
+                const long long b = GAUSS ? (long long)bg[kk] : 6LL * RUN - 2LL * usum;
+                const long long mm = 2LL * RUN - 2LL * ((macc >> (8 * kk)) & 0xFFu);
+                atomicAdd(&sm.B[r * cx.Tp + t], (unsigned long long)b);
+                atomicAdd(&sm.M[r * cx.Tp + t], (unsigned long long)mm);
+            }
         }
     }
 }

@@ -52,7 +52,9 @@ struct Int8Launch {
 // Shared-memory bytes of the fused kernel, or 0 when the state does not fit
 // (or no kernel is built for that L and mode).
 size_t int8_smem_bytes(int L, int Tp, bool gauss, int mchunk, bool gst);
-int int8_max_threads(int L);
+int int8_max_threads(int L, bool gst);
+// Launch thread counts must be multiples of this (Tp = padded slot count).
+int int8_thread_quantum(int Tp);
 // Configure and launch the fused kernel.
 cudaError_t int8_launch(int L, bool gauss, const Int8Args &a, const Int8Launch &cfg,
                         cudaStream_t st);
