@@ -24,8 +24,11 @@ from concurrent.futures import ThreadPoolExecutor
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "liboracle.so")
 SRC_PATH = os.path.join(HERE, "sgmc_oracle.c")
+# SGMC_ORACLE_LIB names a prebuilt oracle library to load instead (the
+# mutation tests point the pins at deliberately broken builds this way)
+LIB_OVERRIDE = os.environ.get("SGMC_ORACLE_LIB", "")
+LIB_PATH = LIB_OVERRIDE or os.path.join(HERE, "liboracle.so")
 NACC = 40
 
 # accumulator indices (frozen layout)
@@ -48,14 +51,22 @@ KVECS = np.array([[1, 0, 0], [0, 1, 0], [0, 0, 1], [1, 1, 0], [1, -1, 0],
                   [1, 0, 1], [1, 0, -1], [0, 1, 1], [0, 1, -1]], dtype=np.int64)
 
 
+def compile_oracle(src: str, out: str) -> str:
+    """gcc the oracle source into a shared library (no FP contraction)."""
+    tmp = out + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-ffp-contract=off",
+                           "-fno-fast-math", "-fPIC", "-shared", "-o", tmp, src, "-lm"])
+    os.replace(tmp, out)
+    return out
+
+
 def build(force: bool = False) -> str:
     """Compile sgmc_oracle.c into liboracle.so (plain gcc, no FP contraction)."""
+    if LIB_OVERRIDE:
+        return LIB_PATH
     if force or not os.path.exists(LIB_PATH) or \
             os.path.getmtime(LIB_PATH) < os.path.getmtime(SRC_PATH):
-        tmp = LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-ffp-contract=off",
-                               "-fno-fast-math", "-fPIC", "-shared", "-o", tmp, SRC_PATH, "-lm"])
-        os.replace(tmp, LIB_PATH)
+        compile_oracle(SRC_PATH, LIB_PATH)
     return LIB_PATH
 
 
