@@ -251,6 +251,28 @@ sg_status sg_set_histogram(sg_ensemble *e, const uint64_t *hist_host);
 sg_status sg_get_spins(sg_ensemble *e, int8_t *spins_out);
 /* Replace the current spins from a host array (canonical layout, +-1). */
 sg_status sg_set_spins(sg_ensemble *e, const int8_t *spins_host);
+/*
+ * Stream-ordered variants for pipelined host I/O (the paper has no
+ * counterpart; they let a host feed new initial states and read results
+ * while the GPU sweeps).
+ *
+ * sg_set_spins_async: the same replacement as sg_set_spins, enqueued: the
+ *   host array (canonical layout) is copied on the ensemble's private copy
+ *   stream into a device buffer of its own (allocated on the first call,
+ *   which synchronises the stream; do not make that first call inside a
+ *   stream capture), so the copy overlaps sweeps enqueued before the call;
+ *   the check of the values and the import then run on the ensemble's stream,
+ *   after everything enqueued before the call. The host array must stay
+ *   valid and unchanged until the next sg_synchronize (page-locked memory
+ *   makes the copy truly asynchronous). If a value is not +-1 the state is
+ *   left as it was and the next sg_synchronize returns SG_EINVAL.
+ * sg_get_accumulators_async: enqueues the copy of the accumulators
+ *   ([S][n_T][B][40] doubles) to host memory on the ensemble's stream; the
+ *   values are there after sg_synchronize (or any later synchronising call).
+ */
+sg_status sg_set_spins_async(sg_ensemble *e, const int8_t *spins_host);
+sg_status sg_get_accumulators_async(sg_ensemble *e, double *acc_out);
+
 /* Copy B and M ([S][2][n_T] each) of the configuration after the last sweep
  * or exchange; either pointer may be NULL. */
 sg_status sg_get_energies(sg_ensemble *e, int64_t *B_out, int64_t *M_out);

@@ -101,6 +101,11 @@ struct sg_ensemble {
     // device staging of canonical host arrays, allocated on first use
     void *stage = nullptr;
     size_t stage_bytes = 0;
+    // asynchronous spin uploads: own buffer and copy stream (first use);
+    // up_done: the copy has landed; up_free: the import has read the buffer
+    void *upload = nullptr;
+    cudaStream_t copy = nullptr;
+    cudaEvent_t up_done = nullptr, up_free = nullptr;
 };
 
 namespace {
@@ -599,6 +604,11 @@ void sg_destroy(sg_ensemble *e)
     purge_graphs(e);
     if (e->stream || e->arena) cudaStreamSynchronize(e->stream);
     if (e->branch) cudaStreamSynchronize(e->branch);
+    if (e->copy) cudaStreamSynchronize(e->copy);
+    if (e->upload) cudaFree(e->upload);
+    if (e->copy) cudaStreamDestroy(e->copy);
+    if (e->up_done) cudaEventDestroy(e->up_done);
+    if (e->up_free) cudaEventDestroy(e->up_free);
     if (e->arena) cudaFree(e->arena);
     if (e->stage) cudaFree(e->stage);
     if (e->branch) cudaStreamDestroy(e->branch);
@@ -847,7 +857,7 @@ sg_status sg_set_spins(sg_ensemble *e, const int8_t *in)
     int bad = 0;
     cudaError_t ce = cudaMemsetAsync(flag, 0, sizeof(int), e->stream);
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(d, in, bytes, cudaMemcpyHostToDevice, e->stream);
-    if (ce == cudaSuccess) ce = check_pm1(d, bytes, flag, e->stream);
+    if (ce == cudaSuccess) ce = check_pm1(d, bytes, flag, nullptr, e->stream);
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(&bad, flag, sizeof(int), cudaMemcpyDeviceToHost, e->stream);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(e->stream);
     if (ce != cudaSuccess) return cuda_fail(ce, "set spins");
@@ -860,6 +870,48 @@ sg_status sg_set_spins(sg_ensemble *e, const int8_t *in)
                     : int8_energies(make_args(e), e->L, e->gauss, e->stream);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(e->stream);
     if (ce != cudaSuccess) return cuda_fail(ce, "set spins");
+    return SG_OK;
+}
+
+sg_status sg_set_spins_async(sg_ensemble *e, const int8_t *in)
+{
+    if (!e || !in) return fail(SG_EINVAL, "bad arguments");
+    const size_t bytes = (size_t)e->S * 2 * e->nt * e->L * e->L * e->L;
+    if (!e->copy) {
+        SG_CUDA(cudaStreamSynchronize(e->stream), "sync");
+        SG_CUDA(cudaMalloc(&e->upload, bytes), "upload buffer");
+        SG_CUDA(cudaStreamCreateWithFlags(&e->copy, cudaStreamNonBlocking), "copy stream");
+        SG_CUDA(cudaEventCreateWithFlags(&e->up_done, cudaEventDisableTiming), "event");
+        SG_CUDA(cudaEventCreateWithFlags(&e->up_free, cudaEventDisableTiming), "event");
+        SG_CUDA(cudaEventRecord(e->up_free, e->stream), "event");
+    }
+    int8_t *d = (int8_t *)e->upload;
+    int *flag = (int *)((uint8_t *)e->status + 128);
+    // the copy waits only until the previous upload's import has read the
+    // buffer, so it overlaps the sweeps enqueued since
+    SG_CUDA(cudaStreamWaitEvent(e->copy, e->up_free, 0), "wait");
+    SG_CUDA(cudaMemcpyAsync(d, in, bytes, cudaMemcpyHostToDevice, e->copy), "upload");
+    SG_CUDA(cudaEventRecord(e->up_done, e->copy), "event");
+    // check and import in order with the work already on the ensemble's stream
+    SG_CUDA(cudaStreamWaitEvent(e->stream, e->up_done, 0), "wait");
+    cudaError_t ce = cudaMemsetAsync(flag, 0, sizeof(int), e->stream);
+    if (ce == cudaSuccess) ce = check_pm1(d, bytes, flag, e->status, e->stream);
+    if (ce == cudaSuccess)
+        ce = e->msc ? msc_import_spins(e->W, d, e->S / 64, e->L, e->nt, e->stream, flag)
+                    : int8_import_spins(e->spins, d, e->S, e->L, e->nt, e->Tp, e->stream, flag);
+    if (ce == cudaSuccess)
+        ce = e->msc ? msc_energies(make_msc_args(e), e->L, e->stream)
+                    : int8_energies(make_args(e), e->L, e->gauss, e->stream);
+    if (ce == cudaSuccess) ce = cudaEventRecord(e->up_free, e->stream);
+    if (ce != cudaSuccess) return cuda_fail(ce, "set spins (asynchronous)");
+    return SG_OK;
+}
+
+sg_status sg_get_accumulators_async(sg_ensemble *e, double *out)
+{
+    if (!e || !out) return fail(SG_EINVAL, "bad arguments");
+    SG_CUDA(cudaMemcpyAsync(out, e->acc, e->acc_bytes, cudaMemcpyDeviceToHost, e->stream),
+            "copy accumulators");
     return SG_OK;
 }
 
@@ -913,7 +965,10 @@ sg_status sg_synchronize(sg_ensemble *e)
     SG_CUDA(cudaMemcpy(&status, e->status, sizeof(int), cudaMemcpyDeviceToHost), "status");
     if (status != 0) {
         SG_CUDA(cudaMemset(e->status, 0, sizeof(int)), "status reset");
-        return fail((sg_status)status, "device reported an error");
+        return fail((sg_status)status, status == SG_EINVAL
+                                           ? "an asynchronous spin upload held values other than "
+                                             "+-1; that upload was not applied"
+                                           : "device reported an error");
     }
     return SG_OK;
 }

@@ -143,8 +143,9 @@ __global__ void export_J_kernel(float *Jc, const uint8_t *J8, const float *Jg, i
 }
 
 __global__ void import_spins_kernel(uint8_t *spins, const int8_t *c, int64_t S, int L, int nt,
-                                    int Tp)
+                                    int Tp, const int *skip)
 {
+    if (skip && *skip) return;  // the upload failed its check: keep the state
     const int N = L * L * L;
     const int RB = 2 * Tp;
     const int64_t total = S * N * (int64_t)RB;
@@ -306,7 +307,7 @@ __global__ void advance_kernel(int64_t *ctr, int64_t n)
 // Sets *flag when any of the n bytes is neither +1 nor -1. Eight bytes per
 // step: x = w ^ 0x01.. has every byte 0x00 (for +1) or 0xFE (for -1) exactly
 // when all bytes are valid.
-__global__ void check_pm1_kernel(const int8_t *c, int64_t n, int *flag)
+__global__ void check_pm1_kernel(const int8_t *c, int64_t n, int *flag, int *status)
 {
     const uint64_t ones = 0x0101010101010101ull;
     const int64_t words = n / 8;
@@ -321,7 +322,10 @@ __global__ void check_pm1_kernel(const int8_t *c, int64_t n, int *flag)
     for (int64_t k = 8 * words + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
          k += (int64_t)gridDim.x * blockDim.x)
         bad |= c[k] != 1 && c[k] != -1;
-    if (bad) atomicOr(flag, 1);
+    if (bad) {
+        atomicOr(flag, 1);
+        if (status) atomicCAS(status, 0, (int)SG_EINVAL);
+    }
 }
 
 inline int grid_for(int64_t work, int threads)
@@ -421,10 +425,10 @@ cudaError_t int8_export_J(float *Jc, const uint8_t *J8, const float *Jg, int64_t
 }
 
 cudaError_t int8_import_spins(uint8_t *spins, const int8_t *c, int64_t S, int L, int nt, int Tp,
-                              cudaStream_t st)
+                              cudaStream_t st, const int *skip)
 {
     import_spins_kernel<<<grid_for(S * L * L * L * 2 * Tp, 256), 256, 0, st>>>(spins, c, S, L,
-                                                                                nt, Tp);
+                                                                                nt, Tp, skip);
     return cudaGetLastError();
 }
 
@@ -458,10 +462,11 @@ cudaError_t threshold_map(const float *x, int n, uint32_t *out, cudaStream_t st)
     return cudaGetLastError();
 }
 
-cudaError_t check_pm1(const int8_t *c, size_t n, int *flag, cudaStream_t st)
+cudaError_t check_pm1(const int8_t *c, size_t n, int *flag, int *status, cudaStream_t st)
 {
     // c comes from cudaMalloc (8-byte aligned); one 8-byte word per thread step
-    check_pm1_kernel<<<grid_for((int64_t)(n / 8 + 1), 256), 256, 0, st>>>(c, (int64_t)n, flag);
+    check_pm1_kernel<<<grid_for((int64_t)(n / 8 + 1), 256), 256, 0, st>>>(c, (int64_t)n, flag,
+                                                                         status);
     return cudaGetLastError();
 }
 

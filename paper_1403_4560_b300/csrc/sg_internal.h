@@ -77,8 +77,9 @@ cudaError_t int8_import_J(uint8_t *J8, float *Jg, const float *Jcanon, int64_t S
                           bool gauss, cudaStream_t st);
 cudaError_t int8_export_J(float *Jcanon, const uint8_t *J8, const float *Jg, int64_t S, int L,
                           bool gauss, cudaStream_t st);
+// skip (device, may be null): when *skip is nonzero the import writes nothing
 cudaError_t int8_import_spins(uint8_t *spins, const int8_t *canon, int64_t S, int L, int nt,
-                              int Tp, cudaStream_t st);
+                              int Tp, cudaStream_t st, const int *skip = nullptr);
 cudaError_t int8_export_spins(int8_t *canon, const uint8_t *spins, int64_t S, int L, int nt,
                               int Tp, cudaStream_t st);
 cudaError_t int8_energies(const Int8Args &a, int L, bool gauss, cudaStream_t st);
@@ -86,8 +87,10 @@ cudaError_t int8_exchange(const Int8Args &a, int L, bool gauss, int parity, uint
                           cudaStream_t st);
 cudaError_t threshold_map(const float *x, int n, uint32_t *out, cudaStream_t st);
 cudaError_t advance_counter(int64_t *ctr, int64_t n, cudaStream_t st);
-// Sets *flag (device) when a byte of c[0..n) (device, 8-byte aligned) is not +-1.
-cudaError_t check_pm1(const int8_t *c, size_t n, int *flag, cudaStream_t st);
+// Sets *flag (device) when a byte of c[0..n) (device, 8-byte aligned) is not
+// +-1, and then also sets *status to SG_EINVAL if status is not null and
+// still 0 (asynchronous uploads report through the status word).
+cudaError_t check_pm1(const int8_t *c, size_t n, int *flag, int *status, cudaStream_t st);
 cudaError_t int8_measure_k_noalloc(const Int8Args &a, int L, const int *k_host, int nk,
                                    float *out_host, size_t out_floats, cudaStream_t st);
 cudaError_t int8_measure_k(const Int8Args &a, int L, const int *k_dev, int nk, float *out,

@@ -531,8 +531,10 @@ __device__ __forceinline__ int nb_site(int L, int i, int d, int step)
 }
 
 // canonical int8 [S][2][nt][N] -> W [G][nt][2][N]
-__global__ void msc_import_spins_kernel(uint64_t *W, const int8_t *c, int64_t G, int L, int nt)
+__global__ void msc_import_spins_kernel(uint64_t *W, const int8_t *c, int64_t G, int L, int nt,
+                                        const int *skip)
 {
+    if (skip && *skip) return;  // the upload failed its check: keep the state
     const int N = L * L * L;
     const int64_t total = G * nt * 2 * (int64_t)N;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
@@ -818,9 +820,10 @@ cudaError_t msc_sweep(const MscArgs &a, int L, int threads, cudaStream_t st)
     return cudaErrorInvalidValue;
 }
 
-cudaError_t msc_import_spins(uint64_t *W, const int8_t *c, int64_t G, int L, int nt, cudaStream_t st)
+cudaError_t msc_import_spins(uint64_t *W, const int8_t *c, int64_t G, int L, int nt, cudaStream_t st,
+                             const int *skip)
 {
-    msc_import_spins_kernel<<<gridn(G * nt * 2 * L * L * L, 256), 256, 0, st>>>(W, c, G, L, nt);
+    msc_import_spins_kernel<<<gridn(G * nt * 2 * L * L * L, 256), 256, 0, st>>>(W, c, G, L, nt, skip);
     return cudaGetLastError();
 }
 

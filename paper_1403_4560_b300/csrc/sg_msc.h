@@ -37,8 +37,9 @@ bool msc_supported_L(int L);
 // L) clamped to [128, 512] and rounded down to a multiple of 128.
 int msc_threads(int L, int requested);
 cudaError_t msc_sweep(const MscArgs &a, int L, int threads, cudaStream_t st);
+// skip (device, may be null): when *skip is nonzero the import writes nothing
 cudaError_t msc_import_spins(uint64_t *W, const int8_t *canon, int64_t G, int L, int nt,
-                             cudaStream_t st);
+                             cudaStream_t st, const int *skip = nullptr);
 cudaError_t msc_export_spins(int8_t *canon, const uint64_t *W, int64_t G, int L, int nt,
                              cudaStream_t st);
 cudaError_t msc_import_J(uint64_t *Jw, const float *Jc, int64_t G, int L, cudaStream_t st);

@@ -113,6 +113,8 @@ def lib() -> ctypes.CDLL:
         "sg_set_histogram": (st, [P, P]),
         "sg_get_spins": (st, [P, P]),
         "sg_set_spins": (st, [P, P]),
+        "sg_set_spins_async": (st, [P, P]),
+        "sg_get_accumulators_async": (st, [P, P]),
         "sg_get_energies": (st, [P, P, P]),
         "sg_get_couplings": (st, [P, P]),
         "sg_sweeps_done": (i64, [P]),
@@ -190,6 +192,7 @@ class Ensemble:
         self.n_bins = max(int(self.opt.log_bins), 1)
         self.has_hist = bool(self.opt.pq_hist)
         self._keep = []
+        self._inflight = []  # host arrays of enqueued copies, kept until synchronize
         Jp = None
         sp = None
         if J is not None:
@@ -238,7 +241,10 @@ class Ensemble:
         _check(lib().sg_exchange(self._h, int(parity)))
 
     def synchronize(self):
-        _check(lib().sg_synchronize(self._h))
+        try:
+            _check(lib().sg_synchronize(self._h))
+        finally:
+            self._inflight.clear()
 
     # ---- data ------------------------------------------------------------
     def _acc_shape(self):
@@ -257,6 +263,24 @@ class Ensemble:
         if acc.shape != self._acc_shape():
             raise ValueError(f"accumulators must have shape {self._acc_shape()}")
         _check(lib().sg_set_accumulators(self._h, _ptr(acc)))
+
+    def set_spins_async(self, s: np.ndarray):
+        """sg_set_spins_async: enqueue the replacement of the spins; the array
+        (best page-locked) is kept referenced until synchronize()."""
+        s = np.ascontiguousarray(s, dtype=np.int8)
+        if s.shape != (self.n_samples, 2, self.n_T, self.L ** 3):
+            raise ValueError("spins must have shape [S][2][n_T][N]")
+        self._inflight.append(s)
+        _check(lib().sg_set_spins_async(self._h, _ptr(s)))
+
+    def accumulators_async(self, out: np.ndarray) -> np.ndarray:
+        """sg_get_accumulators_async into `out` (float64, the accumulators'
+        shape, best page-locked); valid after synchronize()."""
+        if out.dtype != np.float64 or out.shape != self._acc_shape() or not out.flags.c_contiguous:
+            raise ValueError(f"out must be a C-contiguous float64 array of shape {self._acc_shape()}")
+        self._inflight.append(out)
+        _check(lib().sg_get_accumulators_async(self._h, _ptr(out)))
+        return out
 
     def histogram(self) -> np.ndarray:
         """Overlap histogram uint64 [n_T][log_bins][N+1]: entry k counts the

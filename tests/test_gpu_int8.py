@@ -347,3 +347,51 @@ def test_set_spins_rejects_values_other_than_pm1_and_keeps_the_state(layout):
         flipped = -before
         ens.set_spins(flipped)
         np.testing.assert_array_equal(ens.spins(), flipped)
+
+
+@pytest.mark.parametrize("layout", [0, sgmc.SG_LAYOUT_MSC64])
+def test_async_uploads_and_downloads_match_the_synchronous_calls(layout):
+    """A pipelined loop (upload the next state while the previous sweeps run,
+    download each step's accumulators) gives the same results bit for bit as
+    the synchronous calls, with a different initial state every step."""
+    import torch
+    L, nt, S, steps, n = 6, 4, 64, 3, 7
+    T = inputs.geometric_ladder(0.5, 1.5, nt)
+    states = [inputs.make_instance("pmj", L, S, nt, seed=20 + k)[1] for k in range(steps)]
+    with sgmc.Ensemble(L, 0.2, T, "pmj", S, 9, layout=layout) as a, \
+            sgmc.Ensemble(L, 0.2, T, "pmj", S, 9, layout=layout) as b:
+        want = []
+        for x in states:
+            a.set_spins(x)
+            a.sweep(n)
+            want.append(a.accumulators())
+        pinned = [torch.from_numpy(x).pin_memory().numpy() for x in states]
+        outs = [torch.zeros(want[0].shape, dtype=torch.float64).pin_memory().numpy()
+                for _ in range(steps)]
+        for x, o in zip(pinned, outs):
+            b.set_spins_async(x)
+            b.sweep(n)
+            b.accumulators_async(o)
+        b.synchronize()
+        for w, o in zip(want, outs):
+            np.testing.assert_array_equal(o, w)
+        np.testing.assert_array_equal(b.spins(), a.spins())
+
+
+@pytest.mark.parametrize("layout", [0, sgmc.SG_LAYOUT_MSC64])
+def test_async_upload_with_bad_values_is_skipped_and_reported(layout):
+    L, nt, S = 4, 3, 64
+    T = inputs.geometric_ladder(0.5, 1.5, nt)
+    with sgmc.Ensemble(L, 0.2, T, "pmj", S, 5, layout=layout) as a, \
+            sgmc.Ensemble(L, 0.2, T, "pmj", S, 5, layout=layout) as ref:
+        bad = a.spins().copy()
+        bad.reshape(-1)[-1] = 0
+        a.set_spins_async(bad)
+        a.sweep(5)
+        with pytest.raises(sgmc.SgError) as ei:
+            a.synchronize()
+        assert ei.value.status == sgmc.SG_EINVAL
+        a.synchronize()  # the status word was reported once and cleared
+        ref.sweep(5)
+        np.testing.assert_array_equal(a.spins(), ref.spins())
+        np.testing.assert_array_equal(a.accumulators(), ref.accumulators())
