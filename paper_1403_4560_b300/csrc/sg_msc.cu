@@ -33,7 +33,6 @@ constexpr int kDM = 8;  // bit planes of the per-thread (-1 spin) counter
 constexpr int kDP = 9;  // bit planes of a projection (<= L^2 <= 256 sites)
 constexpr int kDG = 5;  // bit planes of a 2D marginal entry (<= L <= 16 sites)
 
-__device__ __forceinline__ uint64_t ldg64(const uint64_t *p) { return __ldg(p); }
 
 // Bit-sliced ripple add of a K-plane number into a D-plane counter.
 template <int D, int K>
@@ -104,8 +103,25 @@ __device__ __forceinline__ uint32_t warp_transpose32(uint32_t x)
 // lanes whose word has bit l set.
 __device__ __forceinline__ int warp_column_popc(uint32_t x) { return __popc(warp_transpose32(x)); }
 
+// Small lattices keep the word group's couplings in shared memory too (loaded
+// once per launch): the four chain teams of a unit read each bond word six
+// times per sweep, which through L1 competed with the chain words.
+__host__ __device__ constexpr bool msc_j_shared(int L) { return L <= 8; }
+
+// A coupling word: a plain shared-memory load when the couplings are staged
+// there, else a read-only global load.
+template <int L>
+__device__ __forceinline__ uint64_t ldJ(const uint64_t *p)
+{
+    if constexpr (msc_j_shared(L))
+        return *p;
+    else
+        return __ldg(p);
+}
+
 struct MscSmem {
     uint64_t *w;        // [4][N]   chains: index q = 2*k + r (k = slot in unit)
+    uint64_t *J;        // [3][N]   the word group's couplings (small L), else null
     uint32_t *thr;      // [2][16]  +-J thresholds of the unit's slots (sb*8 + u)
     long long *B, *M;   // [4][64]  per-sample energies of the unit's chains
     uint64_t *swap;     // [2]      exchange masks per replica
@@ -117,6 +133,7 @@ __host__ __device__ inline size_t a16(size_t x) { return (x + 15) & ~(size_t)15;
 
 __host__ __device__ inline size_t msc_carve(uint8_t *base, int L, MscSmem *sm)
 {
+    const bool jshared = msc_j_shared(L);
     const size_t N = (size_t)L * L * L;
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -126,6 +143,7 @@ __host__ __device__ inline size_t msc_carve(uint8_t *base, int L, MscSmem *sm)
     };
     MscSmem s;
     s.w = reinterpret_cast<uint64_t *>(take(4 * N * 8));
+    s.J = jshared ? reinterpret_cast<uint64_t *>(take(3 * N * 8)) : nullptr;
     s.thr = reinterpret_cast<uint32_t *>(take(2 * 16 * 4));
     s.B = reinterpret_cast<long long *>(take(4 * 64 * 8));
     s.M = reinterpret_cast<long long *>(take(4 * 64 * 8));
@@ -215,7 +233,7 @@ __device__ __forceinline__ void msc_half(const MscSmem &sm, const MscArgs &a, in
     constexpr int NG = (N / 2) / 4;  // Philox groups of four colour-c sites
     const int tid = threadIdx.x % tpc;
     uint64_t *w = sm.w + (size_t)q * N;
-    const uint64_t *J = a.Jw + (size_t)g * 3 * N;
+    const uint64_t *J = msc_j_shared(L) ? sm.J : a.Jw + (size_t)g * 3 * N;
     const uint32_t *thr = sm.thr + (q >> 1) * 16;
     uint64_t cu[kDU], cm[kDM];
 #pragma unroll
@@ -235,12 +253,12 @@ __device__ __forceinline__ void msc_half(const MscSmem &sm, const MscArgs &a, in
             const uint64_t n2 = w[i + st.dyp], n3 = w[i + st.dym];
             const uint64_t n4 = w[i + st.dzp], n5 = w[i + st.dzm];
             // unsatisfied bonds: s ^ s_nb ^ jbit
-            const uint64_t d0 = s ^ n0 ^ ldg64(J + i);
-            const uint64_t d1 = s ^ n1 ^ ldg64(J + i + st.dxm);
-            const uint64_t d2 = s ^ n2 ^ ldg64(J + N + i);
-            const uint64_t d3 = s ^ n3 ^ ldg64(J + N + i + st.dym);
-            const uint64_t d4 = s ^ n4 ^ ldg64(J + 2 * N + i);
-            const uint64_t d5 = s ^ n5 ^ ldg64(J + 2 * N + i + st.dzm);
+            const uint64_t d0 = s ^ n0 ^ ldJ<L>(J + i);
+            const uint64_t d1 = s ^ n1 ^ ldJ<L>(J + i + st.dxm);
+            const uint64_t d2 = s ^ n2 ^ ldJ<L>(J + N + i);
+            const uint64_t d3 = s ^ n3 ^ ldJ<L>(J + N + i + st.dym);
+            const uint64_t d4 = s ^ n4 ^ ldJ<L>(J + 2 * N + i);
+            const uint64_t d5 = s ^ n5 ^ ldJ<L>(J + 2 * N + i + st.dzm);
             // 3-bit count u of the six: two full adders and a carry merge
             const uint64_t sa = d0 ^ d1 ^ d2, ca = (d0 & d1) | (d2 & (d0 ^ d1));
             const uint64_t sb = d3 ^ d4 ^ d5, cb = (d3 & d4) | (d5 & (d3 ^ d4));
@@ -444,6 +462,10 @@ __global__ void __launch_bounds__(MAXT, MINB) msc_sweep_kernel(const MscArgs a)
     // load the unit's chains (index q = 2k + r is contiguous in W) and tables
     const uint64_t *src = a.W + ((size_t)g * a.nt + t0) * 2 * N;
     for (int k = threadIdx.x; k < nq * N; k += blockDim.x) sm.w[k] = src[k];
+    if (msc_j_shared(L)) {
+        const uint64_t *jsrc = a.Jw + (size_t)g * 3 * N;
+        for (int k = threadIdx.x; k < 3 * N; k += blockDim.x) sm.J[k] = jsrc[k];
+    }
     for (int k = threadIdx.x; k < cnt * 16; k += blockDim.x) sm.thr[k] = a.thr[t0 * 16 + k];
     for (int k = threadIdx.x; k < 4 * 64; k += blockDim.x) {
         sm.B[k] = 0;
