@@ -142,15 +142,20 @@ class Clocks:
 
 
 def make_ensembles(sgmc, inputs, rank, stream, **opt):
+    """One ensemble per (L, h). Rank r holds the global samples
+    [r * N_SAMPLES, (r + 1) * N_SAMPLES) of each: couplings and initial spins
+    are drawn on the device keyed by the global sample index (sample_base),
+    so N ranks run one N-times-larger ensemble split by samples. The host
+    copy of the initial spins feeds the end-to-end uploads."""
     T = inputs.geometric_ladder(T_MIN, T_MAX, N_T)
     ens, host = [], []
     for li, L in enumerate(LS):
         for hi, h in enumerate(HS):
-            seed = 1000 * rank + 10 * li + hi + 1
-            J, s0 = inputs.make_instance("gauss", L, N_SAMPLES, N_T, seed=seed)
-            ens.append(sgmc.Ensemble(L, h, T, "gauss", N_SAMPLES, seed, J=J, spins=s0,
-                                     stream=stream, n_therm=0, **opt))
-            host.append(s0)
+            seed = 10 * li + hi + 1
+            e = sgmc.Ensemble(L, h, T, "gauss", N_SAMPLES, seed, stream=stream, n_therm=0,
+                              sample_base=rank * N_SAMPLES, **opt)
+            ens.append(e)
+            host.append(e.spins())
     return ens, host
 
 
@@ -487,7 +492,7 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "fp32",
                 "data": "synthetic",
                 "config": {"workload": WORKLOAD, "sweeps_per_step": nsw,
-                           "parallelism": f"independent samples, {world} GPU(s)",
+                           "parallelism": f"sample shards (sample_base), {world} GPU(s), no collective in the timed region",
                            "l2": "state+couplings 206 MB per GPU, larger than L2",
                            "batched": "one CUDA graph per step, 6 parallel branches"},
                 "gpu_launches": n_launch_per_step * K,
