@@ -104,6 +104,7 @@ struct sg_ensemble {
     // asynchronous spin uploads: own buffer and copy stream (first use);
     // up_done: the copy has landed; up_free: the import has read the buffer
     void *upload = nullptr;
+    void *acc_download = nullptr;  // MSC: canonical accumulators for async downloads
     cudaStream_t copy = nullptr;
     cudaEvent_t up_done = nullptr, up_free = nullptr;
 };
@@ -606,6 +607,7 @@ void sg_destroy(sg_ensemble *e)
     if (e->branch) cudaStreamSynchronize(e->branch);
     if (e->copy) cudaStreamSynchronize(e->copy);
     if (e->upload) cudaFree(e->upload);
+    if (e->acc_download) cudaFree(e->acc_download);
     if (e->copy) cudaStreamDestroy(e->copy);
     if (e->up_done) cudaEventDestroy(e->up_done);
     if (e->up_free) cudaEventDestroy(e->up_free);
@@ -787,7 +789,15 @@ sg_status sg_measure_noalloc(sg_ensemble *e, const int *k, int nk, float *out)
 sg_status sg_get_accumulators(sg_ensemble *e, double *out)
 {
     if (!e || !out) return fail(SG_EINVAL, "bad arguments");
-    SG_CUDA(cudaMemcpyAsync(out, e->acc, e->acc_bytes, cudaMemcpyDeviceToHost, e->stream),
+    const double *src = e->acc;
+    if (e->msc) {  // device layout [G][nt][bins][40][64] -> canonical, via the staging buffer
+        double *d = nullptr;
+        SG_CUDA(stage_buffer(e, e->acc_bytes, (void **)&d), "staging buffer");
+        SG_CUDA(msc_acc_layout(d, e->acc, e->S / 64, e->nt, e->n_bins, false, e->stream),
+                "accumulator layout");
+        src = d;
+    }
+    SG_CUDA(cudaMemcpyAsync(out, src, e->acc_bytes, cudaMemcpyDeviceToHost, e->stream),
             "copy accumulators");
     SG_CUDA(cudaStreamSynchronize(e->stream), "sync");
     return SG_OK;
@@ -796,8 +806,17 @@ sg_status sg_get_accumulators(sg_ensemble *e, double *out)
 sg_status sg_set_accumulators(sg_ensemble *e, const double *in)
 {
     if (!e || !in) return fail(SG_EINVAL, "bad arguments");
-    SG_CUDA(cudaMemcpyAsync(e->acc, in, e->acc_bytes, cudaMemcpyHostToDevice, e->stream),
-            "copy accumulators");
+    if (e->msc) {  // canonical -> device layout, via the staging buffer
+        double *d = nullptr;
+        SG_CUDA(stage_buffer(e, e->acc_bytes, (void **)&d), "staging buffer");
+        SG_CUDA(cudaMemcpyAsync(d, in, e->acc_bytes, cudaMemcpyHostToDevice, e->stream),
+                "copy accumulators");
+        SG_CUDA(msc_acc_layout(e->acc, d, e->S / 64, e->nt, e->n_bins, true, e->stream),
+                "accumulator layout");
+    } else {
+        SG_CUDA(cudaMemcpyAsync(e->acc, in, e->acc_bytes, cudaMemcpyHostToDevice, e->stream),
+                "copy accumulators");
+    }
     SG_CUDA(cudaStreamSynchronize(e->stream), "sync");
     return SG_OK;
 }
@@ -910,7 +929,18 @@ sg_status sg_set_spins_async(sg_ensemble *e, const int8_t *in)
 sg_status sg_get_accumulators_async(sg_ensemble *e, double *out)
 {
     if (!e || !out) return fail(SG_EINVAL, "bad arguments");
-    SG_CUDA(cudaMemcpyAsync(out, e->acc, e->acc_bytes, cudaMemcpyDeviceToHost, e->stream),
+    const double *src = e->acc;
+    if (e->msc) {  // canonical copy in a buffer of its own, then the download
+        if (!e->acc_download) {
+            SG_CUDA(cudaStreamSynchronize(e->stream), "sync");
+            SG_CUDA(cudaMalloc(&e->acc_download, e->acc_bytes), "download buffer");
+        }
+        SG_CUDA(msc_acc_layout((double *)e->acc_download, e->acc, e->S / 64, e->nt, e->n_bins,
+                               false, e->stream),
+                "accumulator layout");
+        src = (const double *)e->acc_download;
+    }
+    SG_CUDA(cudaMemcpyAsync(out, src, e->acc_bytes, cudaMemcpyDeviceToHost, e->stream),
             "copy accumulators");
     return SG_OK;
 }

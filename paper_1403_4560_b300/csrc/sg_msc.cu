@@ -383,15 +383,16 @@ __device__ __forceinline__ void msc_measure(const MscSmem &sm, const MscArgs &a,
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
         for (int task = warp; task < 2 * 9; task += nwarps) {
             const int v = task >> 1, half = task & 1;
-            const int b = 32 * half + lane;
-            const int64_t s = 64 * (int64_t)g + b;
-            double *ac = a.acc + (((size_t)s * a.nt + t) * a.n_bins + bin) * SG_NACC;
-            double *acv = ac + 9 + 3 * v;
-            double o0 = acv[0], o1 = acv[1], o2 = acv[2];
+            const int b = 32 * half + lane;  // sample 64 g + b
+            // device layout [G][nt][bins][40][64]: entry k of this sample at
+            // ac[64 k], so the 32 lanes of a warp touch 256 contiguous bytes
+            double *ac = a.acc + (((size_t)g * a.nt + t) * a.n_bins + bin) * SG_NACC * 64 + b;
+            double *acv = ac + 64 * (9 + 3 * v);
+            double o0 = acv[0], o1 = acv[64], o2 = acv[128];
             double q[9];
             if (v == 0) {
 #pragma unroll
-                for (int k2 = 0; k2 < 9; ++k2) q[k2] = ac[k2];
+                for (int k2 = 0; k2 < 9; ++k2) q[k2] = ac[64 * k2];
             }
             float re = 0.0f, im = 0.0f;
             int Qi = 0;
@@ -406,8 +407,8 @@ __device__ __forceinline__ void msc_measure(const MscSmem &sm, const MscArgs &a,
             }
             const double dr = (double)re, di = (double)im;
             acv[0] = __dadd_rn(o0, dr);
-            acv[1] = __dadd_rn(o1, di);
-            acv[2] = __dadd_rn(o2, __dadd_rn(__dmul_rn(dr, dr), __dmul_rn(di, di)));
+            acv[64] = __dadd_rn(o1, di);
+            acv[128] = __dadd_rn(o2, __dadd_rn(__dmul_rn(dr, dr), __dmul_rn(di, di)));
             if (v == 0) {
                 if (a.hist)  // P(q): replicas agree on (N + Q) / 2 sites
                     atomicAdd(a.hist + ((size_t)t * a.n_bins + bin) * (N + 1) + ((N + Qi) >> 1), 1ull);
@@ -431,7 +432,7 @@ __device__ __forceinline__ void msc_measure(const MscSmem &sm, const MscArgs &a,
                     q[8] = __dadd_rn(q[8], __dmul_rn(m, m));
                 }
 #pragma unroll
-                for (int k2 = 0; k2 < 9; ++k2) ac[k2] = q[k2];
+                for (int k2 = 0; k2 < 9; ++k2) ac[64 * k2] = q[k2];
             }
         }
     }
@@ -550,6 +551,26 @@ __device__ __forceinline__ int nb_site(int L, int i, int d, int step)
     if (d == 1) y = (y + step + L) % L;
     if (d == 2) z = (z + step + L) % L;
     return x + L * (y + L * z);
+}
+
+// Accumulators: canonical [S][nt][bins][40] <-> device [G][nt][bins][40][64]
+// (the sample's bit within its word group fastest). to_dev selects the direction.
+__global__ void msc_acc_layout_kernel(double *dst, const double *src, int64_t G, int nt, int nb,
+                                      int to_dev)
+{
+    const int64_t total = G * 64 * (int64_t)nt * nb * SG_NACC;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        // e runs over the canonical index ((s * nt + t) * nb + bin) * 40 + k
+        const int k = (int)(e % SG_NACC);
+        const int64_t tb = (e / SG_NACC) % ((int64_t)nt * nb);  // t * nb + bin
+        const int64_t s = e / ((int64_t)SG_NACC * nt * nb);
+        const int64_t d = (((s / 64) * nt * nb + tb) * SG_NACC + k) * 64 + (s % 64);
+        if (to_dev)
+            dst[d] = src[e];
+        else
+            dst[e] = src[d];
+    }
 }
 
 // canonical int8 [S][2][nt][N] -> W [G][nt][2][N]
@@ -853,6 +874,14 @@ cudaError_t msc_export_spins(int8_t *c, const uint64_t *W, int64_t G, int L, int
 {
     msc_export_spins_kernel<<<gridn(G * 64 * 2 * nt * L * L * L, 256), 256, 0, st>>>(c, W, G * 64, L,
                                                                                     nt);
+    return cudaGetLastError();
+}
+
+cudaError_t msc_acc_layout(double *dst, const double *src, int64_t G, int nt, int nb, bool to_dev,
+                           cudaStream_t st)
+{
+    msc_acc_layout_kernel<<<gridn(G * 64 * nt * nb * SG_NACC, 256), 256, 0, st>>>(dst, src, G, nt, nb,
+                                                                                  to_dev ? 1 : 0);
     return cudaGetLastError();
 }
 

@@ -12,7 +12,7 @@ struct MscArgs {
     uint64_t *W;          // [G][nt][2][N] spin words, bit b = sample 64g + b
     const uint64_t *Jw;   // [G][3][N] coupling words, bit 1 => J = -1
     int64_t *B, *M;       // [S][2][nt]
-    double *acc;          // [S][nt][n_bins][40]
+    double *acc;          // [G][nt][n_bins][40][64] (sample bit fastest)
     unsigned long long *hist;  // [nt][n_bins][N+1] overlap histogram, or null
     int n_bins;           // logarithmic sweep bins (1 = a single bin)
     const uint32_t *thr;  // [nt][16] thresholds, entry sb*8 + u
@@ -42,6 +42,10 @@ cudaError_t msc_import_spins(uint64_t *W, const int8_t *canon, int64_t G, int L,
                              cudaStream_t st, const int *skip = nullptr);
 cudaError_t msc_export_spins(int8_t *canon, const uint64_t *W, int64_t G, int L, int nt,
                              cudaStream_t st);
+// Accumulator layouts: canonical [S][nt][nb][40] <-> device [G][nt][nb][40][64]
+// (to_dev: canonical src to device dst; else device src to canonical dst).
+cudaError_t msc_acc_layout(double *dst, const double *src, int64_t G, int nt, int nb, bool to_dev,
+                           cudaStream_t st);
 cudaError_t msc_import_J(uint64_t *Jw, const float *Jc, int64_t G, int L, cudaStream_t st);
 cudaError_t msc_export_J(float *Jc, const uint64_t *Jw, int64_t G, int L, cudaStream_t st);
 cudaError_t msc_generate(uint64_t *Jw, uint64_t *W, int64_t G, int L, int nt, uint32_t slo,
