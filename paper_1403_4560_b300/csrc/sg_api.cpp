@@ -104,7 +104,7 @@ struct sg_ensemble {
     // asynchronous spin uploads: own buffer and copy stream (first use);
     // up_done: the copy has landed; up_free: the import has read the buffer
     void *upload = nullptr;
-    void *acc_download = nullptr;  // MSC: canonical accumulators for async downloads
+    void *acc_download = nullptr;  // canonical accumulators for async downloads
     cudaStream_t copy = nullptr;
     cudaEvent_t up_done = nullptr, up_free = nullptr;
 };
@@ -786,18 +786,22 @@ sg_status sg_measure_noalloc(sg_ensemble *e, const int *k, int nk, float *out)
     return SG_OK;
 }
 
+// The accumulators' device layouts differ from the canonical one so that the
+// measurement's lanes touch consecutive doubles: int8 [S][bins][40][nt] (slot
+// fastest), MSC64 [G][nt][bins][40][64] (sample bit fastest).
+static cudaError_t acc_layout(sg_ensemble *e, double *dst, const double *src, bool to_dev)
+{
+    return e->msc ? msc_acc_layout(dst, src, e->S / 64, e->nt, e->n_bins, to_dev, e->stream)
+                  : int8_acc_layout(dst, src, e->S, e->nt, e->n_bins, to_dev, e->stream);
+}
+
 sg_status sg_get_accumulators(sg_ensemble *e, double *out)
 {
     if (!e || !out) return fail(SG_EINVAL, "bad arguments");
-    const double *src = e->acc;
-    if (e->msc) {  // device layout [G][nt][bins][40][64] -> canonical, via the staging buffer
-        double *d = nullptr;
-        SG_CUDA(stage_buffer(e, e->acc_bytes, (void **)&d), "staging buffer");
-        SG_CUDA(msc_acc_layout(d, e->acc, e->S / 64, e->nt, e->n_bins, false, e->stream),
-                "accumulator layout");
-        src = d;
-    }
-    SG_CUDA(cudaMemcpyAsync(out, src, e->acc_bytes, cudaMemcpyDeviceToHost, e->stream),
+    double *d = nullptr;  // device layout -> canonical, via the staging buffer
+    SG_CUDA(stage_buffer(e, e->acc_bytes, (void **)&d), "staging buffer");
+    SG_CUDA(acc_layout(e, d, e->acc, false), "accumulator layout");
+    SG_CUDA(cudaMemcpyAsync(out, d, e->acc_bytes, cudaMemcpyDeviceToHost, e->stream),
             "copy accumulators");
     SG_CUDA(cudaStreamSynchronize(e->stream), "sync");
     return SG_OK;
@@ -806,17 +810,11 @@ sg_status sg_get_accumulators(sg_ensemble *e, double *out)
 sg_status sg_set_accumulators(sg_ensemble *e, const double *in)
 {
     if (!e || !in) return fail(SG_EINVAL, "bad arguments");
-    if (e->msc) {  // canonical -> device layout, via the staging buffer
-        double *d = nullptr;
-        SG_CUDA(stage_buffer(e, e->acc_bytes, (void **)&d), "staging buffer");
-        SG_CUDA(cudaMemcpyAsync(d, in, e->acc_bytes, cudaMemcpyHostToDevice, e->stream),
-                "copy accumulators");
-        SG_CUDA(msc_acc_layout(e->acc, d, e->S / 64, e->nt, e->n_bins, true, e->stream),
-                "accumulator layout");
-    } else {
-        SG_CUDA(cudaMemcpyAsync(e->acc, in, e->acc_bytes, cudaMemcpyHostToDevice, e->stream),
-                "copy accumulators");
-    }
+    double *d = nullptr;  // canonical -> device layout, via the staging buffer
+    SG_CUDA(stage_buffer(e, e->acc_bytes, (void **)&d), "staging buffer");
+    SG_CUDA(cudaMemcpyAsync(d, in, e->acc_bytes, cudaMemcpyHostToDevice, e->stream),
+            "copy accumulators");
+    SG_CUDA(acc_layout(e, e->acc, d, true), "accumulator layout");
     SG_CUDA(cudaStreamSynchronize(e->stream), "sync");
     return SG_OK;
 }
@@ -929,18 +927,12 @@ sg_status sg_set_spins_async(sg_ensemble *e, const int8_t *in)
 sg_status sg_get_accumulators_async(sg_ensemble *e, double *out)
 {
     if (!e || !out) return fail(SG_EINVAL, "bad arguments");
-    const double *src = e->acc;
-    if (e->msc) {  // canonical copy in a buffer of its own, then the download
-        if (!e->acc_download) {
-            SG_CUDA(cudaStreamSynchronize(e->stream), "sync");
-            SG_CUDA(cudaMalloc(&e->acc_download, e->acc_bytes), "download buffer");
-        }
-        SG_CUDA(msc_acc_layout((double *)e->acc_download, e->acc, e->S / 64, e->nt, e->n_bins,
-                               false, e->stream),
-                "accumulator layout");
-        src = (const double *)e->acc_download;
+    if (!e->acc_download) {  // canonical copy in a buffer of its own, then the download
+        SG_CUDA(cudaStreamSynchronize(e->stream), "sync");
+        SG_CUDA(cudaMalloc(&e->acc_download, e->acc_bytes), "download buffer");
     }
-    SG_CUDA(cudaMemcpyAsync(out, src, e->acc_bytes, cudaMemcpyDeviceToHost, e->stream),
+    SG_CUDA(acc_layout(e, (double *)e->acc_download, e->acc, false), "accumulator layout");
+    SG_CUDA(cudaMemcpyAsync(out, e->acc_download, e->acc_bytes, cudaMemcpyDeviceToHost, e->stream),
             "copy accumulators");
     return SG_OK;
 }

@@ -304,6 +304,26 @@ __global__ void advance_kernel(int64_t *ctr, int64_t n)
     if (threadIdx.x == 0 && blockIdx.x == 0) *ctr += n;
 }
 
+// Accumulators: canonical [S][nt][nb][40] <-> device [S][nb][40][nt].
+__global__ void acc_layout_kernel(double *dst, const double *src, int64_t S, int nt, int nb,
+                                  int to_dev)
+{
+    const int64_t total = S * (int64_t)nt * nb * SG_NACC;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        // e runs over the canonical index ((s * nt + t) * nb + bin) * 40 + k
+        const int k = (int)(e % SG_NACC);
+        const int bin = (int)((e / SG_NACC) % nb);
+        const int t = (int)((e / ((int64_t)SG_NACC * nb)) % nt);
+        const int64_t s = e / ((int64_t)SG_NACC * nb * nt);
+        const int64_t d = ((s * nb + bin) * SG_NACC + k) * nt + t;
+        if (to_dev)
+            dst[d] = src[e];
+        else
+            dst[e] = src[d];
+    }
+}
+
 // Sets *flag when any of the n bytes is neither +1 nor -1. Eight bytes per
 // step: x = w ^ 0x01.. has every byte 0x00 (for +1) or 0xFE (for -1) exactly
 // when all bytes are valid.
@@ -459,6 +479,14 @@ cudaError_t int8_exchange(const Int8Args &a, int L, bool gauss, int parity, uint
 cudaError_t threshold_map(const float *x, int n, uint32_t *out, cudaStream_t st)
 {
     thr_map_kernel<<<grid_for(n, 256), 256, 0, st>>>(x, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t int8_acc_layout(double *dst, const double *src, int64_t S, int nt, int nb, bool to_dev,
+                            cudaStream_t st)
+{
+    acc_layout_kernel<<<grid_for(S * nt * nb * SG_NACC, 256), 256, 0, st>>>(dst, src, S, nt, nb,
+                                                                            to_dev ? 1 : 0);
     return cudaGetLastError();
 }
 

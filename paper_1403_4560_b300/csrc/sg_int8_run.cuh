@@ -459,14 +459,14 @@ __device__ __forceinline__ void measure_step(const Smem &sm, const Ctx &cx, cons
 {
     constexpr int LL = L * L;
     const int WR = cx.WR, RB = cx.RB, Tp = cx.Tp, nt = cx.nt;
-    // accumulators of (sample, slot t, bin): accs + t * tstride
-    const size_t tstride = (size_t)a.n_bins * SG_NACC;
-    double *accs = a.acc + ((size_t)cx.s * nt * a.n_bins + bin) * SG_NACC;
+    // device layout [S][bins][40][nt]: entry k of slot t at accs[k * nt + t],
+    // so lanes over consecutive slots touch consecutive doubles
+    double *accs = a.acc + ((size_t)cx.s * a.n_bins + bin) * SG_NACC * nt;
     // energies and magnetisations first (one thread per slot), so that the
     // projection phase reads nothing the next sweep overwrites
     for (int t = threadIdx.x; t < nt; t += blockDim.x) {
-        double *ac = accs + (size_t)t * tstride;
-        double o5 = ac[5], o6 = ac[6], o7 = ac[7], o8 = ac[8];
+        double *ac = accs + t;  // entry k at ac[k * nt]
+        double o5 = ac[5 * nt], o6 = ac[6 * nt], o7 = ac[7 * nt], o8 = ac[8 * nt];
         for (int r = 0; r < 2; ++r) {
             const long long Bv = (long long)sm.B[r * Tp + t];
             const long long Mv = (long long)sm.M[r * Tp + t];
@@ -479,10 +479,10 @@ __device__ __forceinline__ void measure_step(const Smem &sm, const Ctx &cx, cons
             o7 = __dadd_rn(o7, m);
             o8 = __dadd_rn(o8, __dmul_rn(m, m));
         }
-        ac[5] = o5;
-        ac[6] = o6;
-        ac[7] = o7;
-        ac[8] = o8;
+        ac[5 * nt] = o5;
+        ac[6 * nt] = o6;
+        ac[7 * nt] = o7;
+        ac[8 * nt] = o8;
     }
     for (int j0 = 0; j0 < WR; j0 += a.mchunk) {
         const int nw = min(a.mchunk, WR - j0);
@@ -526,12 +526,11 @@ __device__ __forceinline__ void measure_step(const Smem &sm, const Ctx &cx, cons
             const int t = 4 * j0 + sl;
             if (t >= nt) continue;
             const int jj = sl >> 2, sh = 8 * (sl & 3);
-            double *ac = accs + (size_t)t * tstride;
-            double *acv = ac + (v == 9 ? 0 : 9 + 3 * v);
+            double *acv = accs + (size_t)(v == 9 ? 0 : 9 + 3 * v) * nt + t;  // entry at acv[q * nt]
             const int nacc = v == 9 ? 5 : 3;
             double old[9];
 #pragma unroll
-            for (int q = 0; q < 9; ++q) old[q] = q < nacc ? acv[q] : 0.0;
+            for (int q = 0; q < 9; ++q) old[q] = q < nacc ? acv[q * nt] : 0.0;
             int cs[L];
             if (v == 9 || v == 0)
                 count_pattern<L, 0>(sm.marg + jj, nw, sh, cs);
@@ -576,7 +575,7 @@ __device__ __forceinline__ void measure_step(const Smem &sm, const Ctx &cx, cons
             }
 #pragma unroll
             for (int q = 0; q < 9; ++q)
-                if (q < nacc) acv[q] = old[q];
+                if (q < nacc) acv[q * nt] = old[q];
         }
         // the next chunk's marginals overwrite this chunk's; after the last
         // chunk the next sweep touches nothing this phase reads (spins, B and

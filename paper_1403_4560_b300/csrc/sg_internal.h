@@ -17,7 +17,7 @@ struct Int8Args {
     const float *Jg;       // [S][3][N] Gaussian couplings
     int64_t *B;            // [S][2][Tp] bond sums of the current configuration
     int64_t *M;            // [S][2][Tp] magnetisations
-    double *acc;           // [S][nt][n_bins][40] measurement accumulators
+    double *acc;           // [S][n_bins][40][nt] measurement accumulators (slot fastest)
     unsigned long long *hist;  // [nt][n_bins][N+1] overlap histogram, or null
     int n_bins;            // logarithmic sweep bins (1 = a single bin)
     const uint32_t *thr;   // [Tp][16] +-J thresholds, entry sb*8 + u
@@ -87,6 +87,10 @@ cudaError_t int8_exchange(const Int8Args &a, int L, bool gauss, int parity, uint
                           cudaStream_t st);
 cudaError_t threshold_map(const float *x, int n, uint32_t *out, cudaStream_t st);
 cudaError_t advance_counter(int64_t *ctr, int64_t n, cudaStream_t st);
+// Accumulator layouts: canonical [S][nt][nb][40] <-> device [S][nb][40][nt]
+// (to_dev: canonical src to device dst; else device src to canonical dst).
+cudaError_t int8_acc_layout(double *dst, const double *src, int64_t S, int nt, int nb, bool to_dev,
+                            cudaStream_t st);
 // Sets *flag (device) when a byte of c[0..n) (device, 8-byte aligned) is not
 // +-1, and then also sets *status to SG_EINVAL if status is not null and
 // still 0 (asynchronous uploads report through the status word).
