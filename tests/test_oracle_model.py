@@ -345,3 +345,44 @@ def test_jackknife_of_a_mean_is_the_standard_error():
     obs = orc.observables(acc, L)
     q2 = Q ** 2 / 64 ** 2
     assert obs["err"]["q2"][0] == pytest.approx(q2.std(ddof=1) / math.sqrt(S), rel=1e-10)
+
+
+@pytest.mark.parametrize("gauss", [False, True])
+def test_high_temperature_energy_follows_the_small_beta_expansion(gauss):
+    """ln Z = N ln 2 + (beta^2 / 2)(sum_bonds J^2 + N h^2) + O(beta^4), so
+    <E>/N = -beta (sum_bonds J^2 / N + h^2) + O(beta^3). At beta = 0.05 and
+    h = 1 the prediction is about -0.2; a sign error, a dropped field term or
+    double-counted bonds miss it by far more than the tolerance."""
+    L, S, beta, h = 4, 32, 0.05, 1.0
+    N = L ** 3
+    J, s0 = inputs.make_instance("gauss" if gauss else "pmj", L, S, 1, seed=17)
+    st = orc.State(L, np.array([1.0 / beta]), h, gauss, seed=17, J=J, spins=s0, n_therm=20)
+    st.run(420, threads=4)
+    tm = orc.thermal_means(st.acc, L)
+    e_per_spin = tm["e1"][:, 0]                      # per sample, both replicas
+    h_used = np.rint(h * 131072.0) / 131072.0 if gauss else h
+    pred = -beta * ((J.astype(np.float64) ** 2).sum(axis=(1, 2)) / N + h_used ** 2)
+    n = st.acc[:, 0, 0]  # measurements per sample
+    # per-measurement spread of E/N, estimated from the accumulated second moment
+    var = tm["e2"][:, 0] - e_per_spin ** 2
+    se = np.sqrt(var.sum() / (2 * n.sum())) / np.sqrt(S)
+    diff = (e_per_spin - pred).mean()
+    assert abs(diff) < 4 * se + 3 * beta ** 3 * (3 + h ** 4) * 4, (diff, se)
+    assert abs(pred.mean() + 0.2) < 0.02
+
+
+def test_zero_field_averages_of_m_and_q_vanish():
+    """At h = 0 the model is symmetric under s -> -s of one replica (for q) and
+    of both (for M): the disorder and thermal averages of M and q(0) vanish
+    within their errors."""
+    L, S, nt = 4, 48, 2
+    T = np.array([1.6, 2.4])
+    J, s0 = inputs.make_instance("pmj", L, S, nt, seed=23)
+    st = orc.State(L, T, 0.0, False, seed=23, J=J, spins=s0, n_therm=100)
+    st.run(1100, threads=4)
+    tm = orc.thermal_means(st.acc, L)
+    for key in ("m1", "q1"):
+        per_sample = tm[key]                          # [S][nt]
+        mean = per_sample.mean(axis=0)
+        se = per_sample.std(axis=0, ddof=1) / np.sqrt(S)
+        assert np.all(np.abs(mean) < 4 * se + 1e-12), (key, mean, se)

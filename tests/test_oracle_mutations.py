@@ -53,6 +53,10 @@ MUTATIONS = [
      "while (b + 1 < n_bins && ((n + 1) >> (b + 1)) != 0) ++b;",
      "while (b + 1 < n_bins && (n >> (b + 1)) != 0) ++b;",
      [BINS + "::test_bin_populations_closed_form"]),
+    ("accumulated energy with the field term's sign reversed",
+     "double e = -((double)B[r * nt + t] * qJ + h * (double)M[r * nt + t]);",
+     "double e = -((double)B[r * nt + t] * qJ - h * (double)M[r * nt + t]);",
+     [MODEL + "::test_high_temperature_energy_follows_the_small_beta_expansion"]),
     ("histogram counts disagreeing sites",
      "agree += s0[i] == s1[i];", "agree += s0[i] != s1[i];",
      [BINS + "::test_strong_field_low_temperature_concentrates_at_q_one"]),
