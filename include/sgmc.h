@@ -135,7 +135,11 @@ typedef struct {
 void sg_options_default(sg_options *opt);
 
 /* Number of device bytes sg_create_ensemble allocates for this problem
- * (state, couplings, accumulators, tables); 0 for invalid arguments. */
+ * (state, couplings, accumulators, histogram, tables); 0 for invalid
+ * arguments. Buffers allocated later on first use come on top: the staging
+ * buffer of the host-array getters and setters (the larger of the canonical
+ * spins, couplings or accumulators) and the buffers of the asynchronous
+ * upload and download (canonical spins, canonical accumulators). */
 size_t sg_ensemble_bytes(int L, int n_T, int64_t n_samples, sg_coupling dist,
                          const sg_options *opt);
 
