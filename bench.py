@@ -171,20 +171,23 @@ def cpu_baseline(budget_s: float):
     J, s0 = inputs.make_instance("gauss", L, cores, N_T, seed=99)
     st = orc.State(L, T, 0.2, True, seed=99, J=J, spins=s0, n_therm=0)
     st.run(1, threads=cores)  # warm-up (library load, thread start)
-    # calibrate on a multi-sweep call: a single-sweep call is dominated by
-    # starting the worker threads
-    n0 = 8
+    # two-point calibration: each call pays a fixed start-up (worker threads),
+    # so the per-sweep cost is the difference of two call lengths
     t0 = time.perf_counter()
-    st.run(n0, threads=cores)
-    t1 = time.perf_counter() - t0
-    n = max(1, min(20000, int(budget_s * n0 / max(t1, 1e-3)) - n0))
+    st.run(4, threads=cores)
+    ta = time.perf_counter() - t0
     t0 = time.perf_counter()
-    st.run(n, threads=cores)
-    dt = time.perf_counter() - t0 + t1
-    att = L ** 3 * 2 * N_T * cores * (n + n0)
+    st.run(20, threads=cores)
+    tb = time.perf_counter() - t0
+    per_sweep = max((tb - ta) / 16, 1e-4)
+    n = max(1, min(20000, int(budget_s / per_sweep)))
+    t0 = time.perf_counter()
+    st.run(n, threads=cores)  # the timed sample: one call
+    dt = time.perf_counter() - t0
+    att = L ** 3 * 2 * N_T * cores * n
     return {"value": att / (dt * 1e9), "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"L=12 gaussian, 2x24 T, h=0.2, {cores} samples x {n + n0} sweeps "
-                      f"(exchange+measure every sweep), {dt:.1f} s"}
+            "sample": f"L=12 gaussian, 2x24 T, h=0.2, {cores} samples x {n} sweeps "
+                      f"(exchange+measure every sweep) in one call, {dt:.1f} s"}
 
 
 def run_reference(args, rank):
@@ -266,14 +269,14 @@ def extra_uneven_batch(sgmc, inputs, stream, torch):
                         "2x20 T 0.5-1.5, exchange+measure every sweep"}
 
 
-def extra_msc(sgmc, stream, torch):
-    """+-J multispin-coded path: L = 16, 4096 samples (64 words), h = 0.1,
-    2 x 32 T in 0.4-1.5; one launch per sweep (graph-captured batch)."""
+def extra_msc(sgmc, stream, torch, L=16, S=4096, T=None, h=0.1):
+    """+-J multispin-coded path, by default L = 16, 4096 samples (64 words),
+    h = 0.1, 2 x 32 T in 0.4-1.5; one launch per sweep (graph-captured batch)."""
     from paper_1403_4560_b300 import inputs
-    T = inputs.geometric_ladder(0.4, 1.5, 32)
+    T = inputs.geometric_ladder(0.4, 1.5, 32) if T is None else T
     out = {}
     for name, n_therm in (("measuring", 0), ("thermalising", 10 ** 9)):
-        with sgmc.Ensemble(16, 0.1, T, "pmj", 4096, 5, stream=stream, n_therm=n_therm,
+        with sgmc.Ensemble(L, h, T, "pmj", S, 5, stream=stream, n_therm=n_therm,
                            layout=sgmc.SG_LAYOUT_MSC64) as e:
             sgmc.sweep_batch([e], 4, use_graph=True)
             torch.cuda.synchronize()
@@ -480,6 +483,12 @@ def main():
     if rank == 0 and not args.no_extras:
         extras = {"uneven_batch": extra_uneven_batch(sgmc, inputs, stream, torch),
                   "msc_L16": extra_msc(sgmc, stream, torch),
+                  # the paper's own geometry (Table I): L = 10, 56 temperatures
+                  # geometric in beta 0.1-1.8, h = 0.1; 8192 samples here
+                  "msc_paper_L10_56T": extra_msc(
+                      sgmc, stream, torch, L=10, S=8192, h=0.1,
+                      T=np.ascontiguousarray(
+                          (1.0 / (0.1 * 18.0 ** (np.arange(56) / 55.0)))[::-1])),
                   "serving": extra_serving(sgmc, stream)}
 
     cb = None
