@@ -894,13 +894,21 @@ sg_status sg_set_spins_async(sg_ensemble *e, const int8_t *in)
 {
     if (!e || !in) return fail(SG_EINVAL, "bad arguments");
     const size_t bytes = (size_t)e->S * 2 * e->nt * e->L * e->L * e->L;
-    if (!e->copy) {
+    if (!e->up_free) {  // first use: each step of the set-up is kept if a later one fails
         SG_CUDA(cudaStreamSynchronize(e->stream), "sync");
-        SG_CUDA(cudaMalloc(&e->upload, bytes), "upload buffer");
-        SG_CUDA(cudaStreamCreateWithFlags(&e->copy, cudaStreamNonBlocking), "copy stream");
-        SG_CUDA(cudaEventCreateWithFlags(&e->up_done, cudaEventDisableTiming), "event");
-        SG_CUDA(cudaEventCreateWithFlags(&e->up_free, cudaEventDisableTiming), "event");
-        SG_CUDA(cudaEventRecord(e->up_free, e->stream), "event");
+        if (!e->upload) SG_CUDA(cudaMalloc(&e->upload, bytes), "upload buffer");
+        if (!e->copy)
+            SG_CUDA(cudaStreamCreateWithFlags(&e->copy, cudaStreamNonBlocking), "copy stream");
+        if (!e->up_done)
+            SG_CUDA(cudaEventCreateWithFlags(&e->up_done, cudaEventDisableTiming), "event");
+        cudaEvent_t ev = nullptr;
+        SG_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "event");
+        const cudaError_t ce = cudaEventRecord(ev, e->stream);
+        if (ce != cudaSuccess) {
+            cudaEventDestroy(ev);
+            return cuda_fail(ce, "event");
+        }
+        e->up_free = ev;  // set last: its presence marks a complete set-up
     }
     int8_t *d = (int8_t *)e->upload;
     int *flag = (int *)((uint8_t *)e->status + 128);
