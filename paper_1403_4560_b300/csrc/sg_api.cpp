@@ -105,6 +105,11 @@ struct sg_ensemble {
     // up_done: the copy has landed; up_free: the import has read the buffer
     void *upload = nullptr;
     void *acc_download = nullptr;  // canonical accumulators for async downloads
+    // int8 with global-memory state: the state is packed (a byte per site and
+    // 4-slot group); other int8 kernels run on this byte-per-chain copy, part
+    // of the arena
+    uint8_t *unpacked = nullptr;
+    size_t spins_bytes = 0;       // bytes of the state in the arena
     cudaStream_t copy = nullptr;
     cudaEvent_t up_done = nullptr, up_free = nullptr;
 };
@@ -132,22 +137,23 @@ void purge_graphs(sg_ensemble *e)
 }
 
 struct ArenaPlan {
-    size_t spins, J, BM, acc, hist, thr, tab, twid, misc, total;
+    size_t spins, unpacked, J, BM, acc, hist, thr, tab, twid, misc, total;
 };
 
 int bins_of(const sg_options &o) { return o.log_bins > 1 ? o.log_bins : 1; }
 
 ArenaPlan plan_arena(int L, int nt, int Tp, int64_t S, bool gauss, bool msc, int n_bins,
-                     bool hist)
+                     bool hist, bool packed)
 {
     const size_t N = (size_t)L * L * L;
-    ArenaPlan p;
+    ArenaPlan p{};
     if (msc) {
         // 64 samples per word: W [S/64][nt][2][N], Jw [S/64][3][N], masks [S/64][2][nt]
         p.spins = align256((size_t)(S / 64) * nt * 2 * N * 8);
         p.J = align256((size_t)(S / 64) * 3 * N * 8);
     } else {
-        p.spins = align256((size_t)S * N * 2 * Tp);
+        p.spins = align256((size_t)S * N * (packed ? Tp / 4 : 2 * Tp));
+        p.unpacked = packed ? align256((size_t)S * N * 2 * Tp) : 0;
         p.J = align256(gauss ? (size_t)S * 3 * N * sizeof(float) : (size_t)S * N * 8);
     }
     p.BM = align256((size_t)S * 2 * Tp * sizeof(int64_t));
@@ -157,7 +163,8 @@ ArenaPlan plan_arena(int L, int nt, int Tp, int64_t S, bool gauss, bool msc, int
     p.tab = align256((size_t)Tp * sizeof(float));
     p.twid = align256((size_t)2 * L * sizeof(float));
     p.misc = 256 + (msc ? align256((size_t)(S / 64) * 2 * nt * 8) : 0);
-    p.total = p.spins + p.J + 2 * p.BM + p.acc + p.hist + p.thr + 2 * p.tab + p.twid + p.misc;
+    p.total = p.spins + p.unpacked + p.J + 2 * p.BM + p.acc + p.hist + p.thr + 2 * p.tab + p.twid +
+              p.misc;
     return p;
 }
 
@@ -180,17 +187,17 @@ std::string tune_key(const sg_ensemble *e, bool gst)
 sg_status configure_launch(sg_ensemble *e)
 {
     const int WR = e->Tp / 4;
-    const int Q = int8_thread_quantum(e->Tp);  // thread counts are multiples of Q
     const int L = e->L, H = L / 2;
     int run = H;
     while (run % 4) run += H;
-    const int items = (L * L * L / 2) / run * Q;
     // shared-memory residency first; the global-memory variant when the
     // sample's state does not fit (large L or many temperatures)
     for (int pass = 0; pass < 2; ++pass) {
         const bool gst = pass == 1;
         const int maxt = int8_max_threads(e->L, gst);
         if ((e->opt.state_mode == 1 && gst) || (e->opt.state_mode == 2 && !gst)) continue;
+        const int Q = int8_thread_quantum(e->Tp, gst);  // thread counts are multiples of Q
+        const int items = (L * L * L / 2) / run * Q;
         double best_score = -1.0;
         int best_t = 0, best_m = 0, best_occ = 0;
         for (int t = Q; t <= maxt; t += Q) {
@@ -337,6 +344,28 @@ cudaError_t stage_buffer(sg_ensemble *e, size_t bytes, void **out)
     return cudaSuccess;
 }
 
+// The int8 state in the byte-per-chain layout every kernel but the fused one
+// works on: the state itself, or (packed state of the global-memory
+// instances) the ensemble's scratch copy, unpacked from the state when fill.
+cudaError_t unpacked_view(sg_ensemble *e, uint8_t **out, bool fill)
+{
+    if (!e->unpacked) {
+        *out = e->spins;
+        return cudaSuccess;
+    }
+    *out = e->unpacked;
+    return fill ? int8_unpack_spins(e->unpacked, e->spins, e->S, e->L, e->Tp, e->stream)
+                : cudaSuccess;
+}
+
+// After the byte-per-chain view was changed: pack it back into the state
+// (a no-op when the view is the state). skip: as for the imports.
+cudaError_t commit_unpacked(sg_ensemble *e, const uint8_t *view, const int *skip)
+{
+    if (view == e->spins) return cudaSuccess;
+    return int8_pack_spins(e->spins, view, e->S, e->L, e->Tp, e->stream, skip);
+}
+
 // Host tables: +-J thresholds (FP64 exp of the C library), FP32 -beta and
 // beta differences, FP32 twiddles of the DFT.
 void host_tables(const sg_ensemble *e, std::vector<uint32_t> &thr, std::vector<float> &nb,
@@ -443,8 +472,11 @@ size_t sg_ensemble_bytes(int L, int nt, int64_t S, sg_coupling dist, const sg_op
     for (size_t k = 0; k < T.size(); ++k) T[k] = 1.0 + (double)k;
     if (validate(L, T.data(), nt, dist, S, o) != SG_OK) return 0;
     const bool msc = o.layout == SG_LAYOUT_MSC64;
-    return plan_arena(L, nt, msc ? nt : pad_slots(nt), S, dist == SG_GAUSS, msc, bins_of(o),
-                      o.pq_hist != 0).total;
+    const int Tp = msc ? nt : pad_slots(nt);
+    // the global-memory instances (packed state) serve what shared memory cannot hold
+    const bool packed = !msc && (o.state_mode == 2 ||
+                                 (o.state_mode == 0 && !int8_smem_bytes(L, Tp, dist == SG_GAUSS, 1, false)));
+    return plan_arena(L, nt, Tp, S, dist == SG_GAUSS, msc, bins_of(o), o.pq_hist != 0, packed).total;
 }
 
 sg_status sg_create_ensemble(int L, double h, const double *T, int nt, sg_coupling dist,
@@ -502,7 +534,10 @@ sg_status sg_create_ensemble(int L, double h, const double *T, int nt, sg_coupli
     if (!e->msc && (st = configure_launch(e)) != SG_OK) return bail(st);
 
     e->n_bins = bins_of(o);
-    const ArenaPlan p = plan_arena(L, nt, e->Tp, S, gauss, e->msc, e->n_bins, o.pq_hist != 0);
+    const ArenaPlan p = plan_arena(L, nt, e->Tp, S, gauss, e->msc, e->n_bins, o.pq_hist != 0,
+                                   !e->msc && e->launch.gst);
+    e->spins_bytes = e->msc ? (size_t)(S / 64) * nt * 2 * N * 8
+                            : (size_t)S * N * (e->launch.gst ? e->Tp / 4 : 2 * e->Tp);
     ce = cudaMalloc(&e->arena, p.total);
     if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaMalloc(ensemble)"));
     e->bytes = p.total;
@@ -513,6 +548,8 @@ sg_status sg_create_ensemble(int L, double h, const double *T, int nt, sg_coupli
         e->Jw = (uint64_t *)(base + off); off += p.J;
     } else {
         e->spins = base + off; off += p.spins;
+        if (p.unpacked) e->unpacked = base + off;
+        off += p.unpacked;
         if (gauss) e->Jg = (float *)(base + off); else e->J8 = base + off;
         off += p.J;
     }
@@ -570,6 +607,8 @@ sg_status sg_create_ensemble(int L, double h, const double *T, int nt, sg_coupli
                           : int8_gen_pmj(e->J8, S, L, slo, shi, o.sample_base, s);
             if (r != cudaSuccess) return r;
         }
+        uint8_t *view = e->spins;  // int8: the byte-per-chain state (or its scratch copy)
+        if (!e->msc && (r = unpacked_view(e, &view, false)) != cudaSuccess) return r;
         if (spins_host) {
             int8_t *stage = nullptr;
             const size_t bytes = (size_t)S * 2 * nt * N;
@@ -577,18 +616,20 @@ sg_status sg_create_ensemble(int L, double h, const double *T, int nt, sg_coupli
             r = cudaMemcpyAsync(stage, spins_host, bytes, cudaMemcpyHostToDevice, s);
             if (r == cudaSuccess)
                 r = e->msc ? msc_import_spins(e->W, stage, S / 64, L, nt, s)
-                           : int8_import_spins(e->spins, stage, S, L, nt, e->Tp, s);
+                           : int8_import_spins(view, stage, S, L, nt, e->Tp, s);
             if (r == cudaSuccess) r = cudaStreamSynchronize(s);
             cudaFree(stage);
             if (r != cudaSuccess) return r;
         } else if (!e->msc) {
-            if ((r = int8_gen_spins(e->spins, S, L, nt, e->Tp, slo, shi, o.sample_base, s)) != cudaSuccess)
+            if ((r = int8_gen_spins(view, S, L, nt, e->Tp, slo, shi, o.sample_base, s)) != cudaSuccess)
                 return r;
         }
         if (e->msc) {
             if ((r = msc_energies(make_msc_args(e), L, s)) != cudaSuccess) return r;
         } else {
+            if ((r = commit_unpacked(e, view, nullptr)) != cudaSuccess) return r;
             Int8Args a = make_args(e);
+            a.spins = view;
             if ((r = int8_energies(a, L, gauss, s)) != cudaSuccess) return r;
         }
         return cudaStreamSynchronize(s);
@@ -743,9 +784,11 @@ sg_status sg_exchange(sg_ensemble *e, int parity)
                 "exchange");
     } else {
         Int8Args a = make_args(e);
+        SG_CUDA(unpacked_view(e, &a.spins, true), "unpack");
         SG_CUDA(int8_exchange(a, e->L, e->gauss, parity & 1, (uint32_t)e->exchanges_done,
                               e->stream),
                 "exchange");
+        SG_CUDA(commit_unpacked(e, a.spins, nullptr), "pack");
     }
     ++e->exchanges_done;
     return SG_OK;
@@ -760,9 +803,15 @@ sg_status sg_measure(sg_ensemble *e, const int *k, int nk, float *out)
     SG_CUDA(cudaMalloc(&kd, sizeof(int) * 3 * nk), "cudaMalloc");
     cudaError_t ce = cudaMalloc(&od, ob);
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(kd, k, sizeof(int) * 3 * nk, cudaMemcpyHostToDevice, e->stream);
-    if (ce == cudaSuccess)
-        ce = e->msc ? msc_measure_k(make_msc_args(e), e->L, kd, nk, od, e->stream)
-                    : int8_measure_k(make_args(e), e->L, kd, nk, od, e->stream);
+    if (ce == cudaSuccess) {
+        if (e->msc) {
+            ce = msc_measure_k(make_msc_args(e), e->L, kd, nk, od, e->stream);
+        } else {
+            Int8Args a = make_args(e);
+            ce = unpacked_view(e, &a.spins, true);
+            if (ce == cudaSuccess) ce = int8_measure_k(a, e->L, kd, nk, od, e->stream);
+        }
+    }
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(out, od, ob, cudaMemcpyDeviceToHost, e->stream);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(e->stream);
     cudaFree(kd);
@@ -781,7 +830,11 @@ sg_status sg_measure_noalloc(sg_ensemble *e, const int *k, int nk, float *out)
     if (floats > (size_t)SG_MEASURE_NOALLOC_MAX_FLOATS)
         return fail(SG_EINVAL, "sg_measure_noalloc: n_samples * n_T * nk * 2 exceeds "
                                "SG_MEASURE_NOALLOC_MAX_FLOATS");
-    SG_CUDA(int8_measure_k_noalloc(make_args(e), e->L, k, nk, out, floats, e->stream),
+    // the packed state of large lattices is read through the ensemble's
+    // unpacked copy (part of its arena: nothing is allocated here)
+    Int8Args a = make_args(e);
+    SG_CUDA(unpacked_view(e, &a.spins, true), "unpack");
+    SG_CUDA(int8_measure_k_noalloc(a, e->L, k, nk, out, floats, e->stream),
             "measure (no allocation)");
     return SG_OK;
 }
@@ -853,8 +906,11 @@ sg_status sg_get_spins(sg_ensemble *e, int8_t *out)
     const size_t bytes = (size_t)e->S * 2 * e->nt * e->L * e->L * e->L;
     int8_t *d = nullptr;
     SG_CUDA(stage_buffer(e, bytes, (void **)&d), "staging buffer");
-    cudaError_t ce = e->msc ? msc_export_spins(d, e->W, e->S / 64, e->L, e->nt, e->stream)
-                            : int8_export_spins(d, e->spins, e->S, e->L, e->nt, e->Tp, e->stream);
+    uint8_t *view = nullptr;
+    cudaError_t ce = e->msc ? cudaSuccess : unpacked_view(e, &view, true);
+    if (ce == cudaSuccess)
+        ce = e->msc ? msc_export_spins(d, e->W, e->S / 64, e->L, e->nt, e->stream)
+                    : int8_export_spins(d, view, e->S, e->L, e->nt, e->Tp, e->stream);
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(out, d, bytes, cudaMemcpyDeviceToHost, e->stream);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(e->stream);
     if (ce != cudaSuccess) return cuda_fail(ce, "get spins");
@@ -879,12 +935,16 @@ sg_status sg_set_spins(sg_ensemble *e, const int8_t *in)
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(e->stream);
     if (ce != cudaSuccess) return cuda_fail(ce, "set spins");
     if (bad) return fail(SG_EINVAL, "spins must be +1 or -1");
-    if (ce == cudaSuccess)
-        ce = e->msc ? msc_import_spins(e->W, d, e->S / 64, e->L, e->nt, e->stream)
-                    : int8_import_spins(e->spins, d, e->S, e->L, e->nt, e->Tp, e->stream);
-    if (ce == cudaSuccess)
-        ce = e->msc ? msc_energies(make_msc_args(e), e->L, e->stream)
-                    : int8_energies(make_args(e), e->L, e->gauss, e->stream);
+    if (e->msc) {
+        ce = msc_import_spins(e->W, d, e->S / 64, e->L, e->nt, e->stream);
+        if (ce == cudaSuccess) ce = msc_energies(make_msc_args(e), e->L, e->stream);
+    } else {
+        Int8Args a = make_args(e);
+        ce = unpacked_view(e, &a.spins, false);
+        if (ce == cudaSuccess) ce = int8_import_spins(a.spins, d, e->S, e->L, e->nt, e->Tp, e->stream);
+        if (ce == cudaSuccess) ce = commit_unpacked(e, a.spins, nullptr);
+        if (ce == cudaSuccess) ce = int8_energies(a, e->L, e->gauss, e->stream);
+    }
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(e->stream);
     if (ce != cudaSuccess) return cuda_fail(ce, "set spins");
     return SG_OK;
@@ -921,12 +981,21 @@ sg_status sg_set_spins_async(sg_ensemble *e, const int8_t *in)
     SG_CUDA(cudaStreamWaitEvent(e->stream, e->up_done, 0), "wait");
     cudaError_t ce = cudaMemsetAsync(flag, 0, sizeof(int), e->stream);
     if (ce == cudaSuccess) ce = check_pm1(d, bytes, flag, e->status, e->stream);
-    if (ce == cudaSuccess)
-        ce = e->msc ? msc_import_spins(e->W, d, e->S / 64, e->L, e->nt, e->stream, flag)
-                    : int8_import_spins(e->spins, d, e->S, e->L, e->nt, e->Tp, e->stream, flag);
-    if (ce == cudaSuccess)
-        ce = e->msc ? msc_energies(make_msc_args(e), e->L, e->stream)
-                    : int8_energies(make_args(e), e->L, e->gauss, e->stream);
+    if (ce == cudaSuccess) {
+        if (e->msc) {
+            ce = msc_import_spins(e->W, d, e->S / 64, e->L, e->nt, e->stream, flag);
+            if (ce == cudaSuccess) ce = msc_energies(make_msc_args(e), e->L, e->stream);
+        } else {
+            // packed state: the copy starts as the current state, so that a
+            // skipped import leaves the energies of the unchanged state
+            Int8Args a = make_args(e);
+            ce = unpacked_view(e, &a.spins, true);
+            if (ce == cudaSuccess)
+                ce = int8_import_spins(a.spins, d, e->S, e->L, e->nt, e->Tp, e->stream, flag);
+            if (ce == cudaSuccess) ce = commit_unpacked(e, a.spins, flag);
+            if (ce == cudaSuccess) ce = int8_energies(a, e->L, e->gauss, e->stream);
+        }
+    }
     if (ce == cudaSuccess) ce = cudaEventRecord(e->up_free, e->stream);
     if (ce != cudaSuccess) return cuda_fail(ce, "set spins (asynchronous)");
     return SG_OK;
@@ -1111,7 +1180,7 @@ sg_status sg_autotune(sg_ensemble *e, int64_t trial_sweeps, sg_tune_report *rep)
         return SG_OK;
     }
     const size_t N = (size_t)e->L * e->L * e->L;
-    const size_t sp_bytes = (size_t)e->S * N * 2 * e->Tp;
+    const size_t sp_bytes = e->spins_bytes;  // the state as kept (packed or not)
     const size_t bm_bytes = (size_t)e->S * 2 * e->Tp * sizeof(int64_t);
     // the histogram sits right after the accumulators: one copy saves both
     const size_t acc_bytes = e->hist ? (size_t)((uint8_t *)e->hist - (uint8_t *)e->acc) + e->hist_bytes
@@ -1145,7 +1214,7 @@ sg_status sg_autotune(sg_ensemble *e, int64_t trial_sweeps, sg_tune_report *rep)
     const sg_options orig_opt = e->opt;
     e->opt.sweeps_per_launch = 0;
     const int WR = e->Tp / 4;
-    const int Q = int8_thread_quantum(e->Tp);
+    const int Q = int8_thread_quantum(e->Tp, orig_launch.gst);
     double best_ms = 1e300, default_ms = 0.0;
     int best_t = orig_launch.threads, best_m = orig_m, ncand = 0;
     cudaError_t ce = save(false);

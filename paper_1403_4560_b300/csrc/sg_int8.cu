@@ -304,6 +304,24 @@ __global__ void advance_kernel(int64_t *ctr, int64_t n)
     if (threadIdx.x == 0 && blockIdx.x == 0) *ctr += n;
 }
 
+// Packed state <-> byte per chain: rows = S * N site rows of WR groups; a
+// packed byte holds one group's 8 chains (see load_packed / store_packed).
+__global__ void pack_spins_kernel(uint8_t *packed, const uint8_t *unpacked, int64_t n_bytes,
+                                  const int *skip)
+{
+    if (skip && *skip) return;  // an upload that failed its check: keep the state
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n_bytes;
+         g += (int64_t)gridDim.x * blockDim.x)
+        store_packed(packed + g, *reinterpret_cast<const uint2 *>(unpacked + 8 * g));
+}
+
+__global__ void unpack_spins_kernel(uint8_t *unpacked, const uint8_t *packed, int64_t n_bytes)
+{
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n_bytes;
+         g += (int64_t)gridDim.x * blockDim.x)
+        *reinterpret_cast<uint2 *>(unpacked + 8 * g) = load_packed(packed + g);
+}
+
 // Accumulators: canonical [S][nt][nb][40] <-> device [S][nb][40][nt].
 __global__ void acc_layout_kernel(double *dst, const double *src, int64_t S, int nt, int nb,
                                   int to_dev)
@@ -371,10 +389,12 @@ size_t int8_smem_bytes(int L, int Tp, bool gauss, int mchunk, bool gst)
     return b <= (size_t)kMaxSmem ? b : 0;
 }
 
-int int8_thread_quantum(int Tp)
+int int8_thread_quantum(int Tp, bool gst)
 {
-    // a half-sweep thread keeps one (4-slot group, replica) pair: Tp/4 * 2
-    return Tp / 2;
+    // a half-sweep thread keeps one (4-slot group, replica) pair, Tp/4 * 2;
+    // on the packed state of the global-memory instances one 4-slot group
+    // with both replicas, Tp/4
+    return gst ? Tp / 4 : Tp / 2;
 }
 
 int int8_max_threads(int L, bool gst)
@@ -479,6 +499,22 @@ cudaError_t int8_exchange(const Int8Args &a, int L, bool gauss, int parity, uint
 cudaError_t threshold_map(const float *x, int n, uint32_t *out, cudaStream_t st)
 {
     thr_map_kernel<<<grid_for(n, 256), 256, 0, st>>>(x, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t int8_pack_spins(uint8_t *packed, const uint8_t *unpacked, int64_t S, int L, int Tp,
+                            cudaStream_t st, const int *skip)
+{
+    const int64_t n = S * L * L * L * (int64_t)(Tp / 4);
+    pack_spins_kernel<<<grid_for(n, 256), 256, 0, st>>>(packed, unpacked, n, skip);
+    return cudaGetLastError();
+}
+
+cudaError_t int8_unpack_spins(uint8_t *unpacked, const uint8_t *packed, int64_t S, int L, int Tp,
+                              cudaStream_t st)
+{
+    const int64_t n = S * L * L * L * (int64_t)(Tp / 4);
+    unpack_spins_kernel<<<grid_for(n, 256), 256, 0, st>>>(unpacked, packed, n);
     return cudaGetLastError();
 }
 

@@ -77,6 +77,30 @@ __host__ __device__ __forceinline__ int slot_byte(int r, int t)
     return 8 * (t >> 2) + 4 * r + (t & 3);
 }
 
+// Packed state (global-memory instances): one byte per (site, 4-slot group)
+// holds the group's 8 chains, bit 4r + k = chain (replica r, slot 4j + k), 1
+// => -1 (the replicas of one sample packed into bits, as the paper's
+// multispin coding does; 8x smaller rows keep a CTA's working planes in L1).
+// The sweep computes on the byte-per-chain form: a nibble expands to four
+// 0/1 bytes and compresses back. Neither product carries between fields.
+__device__ __forceinline__ uint32_t expand4(uint32_t nib)
+{
+    return (nib * 0x00204081u) & 0x01010101u;  // bit k -> byte k
+}
+__device__ __forceinline__ uint32_t compress4(uint32_t w)
+{
+    return (w * 0x01020408u) >> 24;  // byte k (0 or 1) -> bit k
+}
+__device__ __forceinline__ uint2 load_packed(const uint8_t *p)
+{
+    const uint32_t b = *p;
+    return make_uint2(expand4(b & 15u), expand4(b >> 4));
+}
+__device__ __forceinline__ void store_packed(uint8_t *p, uint2 w)
+{
+    *p = (uint8_t)(compress4(w.x) | (compress4(w.y) << 4));
+}
+
 struct Smem {
     uint8_t *spins;
     uint8_t *J8;
@@ -87,6 +111,7 @@ struct Smem {
     uint32_t *xflag;            // [2][Tp] exchange stamps
     uint32_t *sel;              // [2][Tp/4][2] byte-permutation selectors
     int *anyswap;               // [2]
+    unsigned long long *accm;   // [2] accepted pairs per replica (bit p: pair p, p+1)
     uint32_t *marg;             // [3][L*L][mchunk] byte counts of q = -1
 };
 
@@ -118,6 +143,7 @@ __host__ __device__ inline size_t carve(uint8_t *base, int L, int Tp, bool gauss
     s.xflag = reinterpret_cast<uint32_t *>(take((size_t)2 * Tp * 4));
     s.sel = reinterpret_cast<uint32_t *>(take((size_t)2 * (Tp / 4) * 2 * 4));
     s.anyswap = reinterpret_cast<int *>(take(2 * 4));
+    s.accm = reinterpret_cast<unsigned long long *>(take(2 * 8));
     s.marg = reinterpret_cast<uint32_t *>(take((size_t)3 * L * L * mchunk * 4));
     if (sm) *sm = s;
     return off;
@@ -338,6 +364,142 @@ __device__ __forceinline__ void half_sweep(const Smem &sm, const Ctx &cx, uint32
 }
 
 // ---------------------------------------------------------------------------
+// Half-sweep of colour COL on the packed state (global-memory instances).
+// Work item: (run of RUN colour-COL sites, 4-slot group j, both replicas),
+// i.e. the 8 chains of one byte, which this thread alone writes. The rule,
+// random numbers and energy bookkeeping are those of half_sweep; only the
+// storage differs (one byte per site and group, expanded to 0/1 bytes).
+// ---------------------------------------------------------------------------
+template <int L, bool GAUSS>
+__device__ __forceinline__ void half_sweep_packed(const Smem &sm, const Ctx &cx, uint32_t n_sweep,
+                                                  const int COL)
+{
+    constexpr int H = L / 2;
+    constexpr int N = L * L * L;
+    constexpr int RUN = lcm_c(H, 4);
+    constexpr int NG = RUN / 4;
+    constexpr int U = (N / 2) / RUN;
+    const int WR = cx.WR, RB = cx.RB;  // packed: RB == WR bytes per site
+    const int j = threadIdx.x % WR;    // fixed per thread: blockDim.x is a multiple of WR
+    const int t0 = 4 * j;
+    const int items = U * WR;
+
+    uint32_t valid = 0;  // bytes of real (not padding) slots in this group
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk)
+        if (t0 + kk < cx.nt) valid |= 1u << (8 * kk);
+
+    float nbeta[4];
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) nbeta[kk] = GAUSS ? sm.negbeta[t0 + kk] : 0.0f;
+    const uint32_t *thr_w = GAUSS ? nullptr : sm.thr + t0 * 16;
+
+    for (int item = threadIdx.x; item < items; item += blockDim.x) {
+        const int u = item / WR;
+        uint32_t eacc0 = 0, eacc1 = 0, macc0 = 0, macc1 = 0;  // byte-wise partial sums
+        int bg[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+        constexpr bool kFlushU = 6 * RUN > 255;
+        for (int g = 0; g < NG; ++g) {
+            const uint32_t c0 = (uint32_t)(u * NG + g);
+            uint32_t rnd[2][4][4];
+#pragma unroll
+            for (int r = 0; r < 2; ++r)
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {
+                    const uint32_t c2 = ((uint32_t)COL << 24) | ((uint32_t)r << 16) |
+                                        (uint32_t)(t0 + kk);
+                    const u32x4 o = philox10(cx.k0, cx.k1, c0, n_sweep, c2, cx.seed_hi);
+                    rnd[r][kk][0] = o.v[0];
+                    rnd[r][kk][1] = o.v[1];
+                    rnd[r][kk][2] = o.v[2];
+                    rnd[r][kk][3] = o.v[3];
+                }
+#pragma unroll
+            for (int lane = 0; lane < 4; ++lane) {
+                const SiteNb<L> st(u * RUN + 4 * g + lane, COL);
+                const int own = st.i * RB + j;
+                const uint2 s = load_packed(sm.spins + own);
+                const uint2 nxp = load_packed(sm.spins + own + st.dxp * RB);
+                const uint2 nxm = load_packed(sm.spins + own + st.dxm * RB);
+                const uint2 nyp = load_packed(sm.spins + own + st.dyp * RB);
+                const uint2 nym = load_packed(sm.spins + own + st.dym * RB);
+                const uint2 nzp = load_packed(sm.spins + own + st.dzp * RB);
+                const uint2 nzm = load_packed(sm.spins + own + st.dzm * RB);
+                uint2 fm;
+                if constexpr (!GAUSS) {
+                    const uint2 jb = *reinterpret_cast<const uint2 *>(sm.J8 + 8 * st.i);
+                    const uint32_t m[6] = {__byte_perm(jb.x, jb.y, 0x0000),
+                                           __byte_perm(jb.x, jb.y, 0x1111),
+                                           __byte_perm(jb.x, jb.y, 0x2222),
+                                           __byte_perm(jb.x, jb.y, 0x3333),
+                                           __byte_perm(jb.x, jb.y, 0x4444),
+                                           __byte_perm(jb.x, jb.y, 0x5555)};
+                    uint32_t uw0, uw1;
+                    fm.x = pmj_word(s.x, nxp.x, nxm.x, nyp.x, nym.x, nzp.x, nzm.x, m, thr_w,
+                                    rnd[0], lane, valid, uw0);
+                    fm.y = pmj_word(s.y, nxp.y, nxm.y, nyp.y, nym.y, nzp.y, nzm.y, m, thr_w,
+                                    rnd[1], lane, valid, uw1);
+                    if (COL == 1) {
+                        const uint32_t f0 = fm.x * 0xFFu, f1 = fm.y * 0xFFu;
+                        eacc0 += uw0 ^ ((uw0 ^ (0x06060606u - uw0)) & f0);
+                        eacc1 += uw1 ^ ((uw1 ^ (0x06060606u - uw1)) & f1);
+                    }
+                } else {
+                    const float jv[6] = {sm.Jg[st.i], sm.Jg[st.i + st.dxm], sm.Jg[N + st.i],
+                                         sm.Jg[N + st.i + st.dym], sm.Jg[2 * N + st.i],
+                                         sm.Jg[2 * N + st.i + st.dzm]};
+                    int bq0[4], bq1[4];
+                    fm.x = gauss_word<true>(s.x, nxp.x, nxm.x, nyp.x, nym.x, nzp.x, nzm.x, jv,
+                                            cx.hq, nbeta, rnd[0], lane, valid, bq0);
+                    fm.y = gauss_word<true>(s.y, nxp.y, nxm.y, nyp.y, nym.y, nzp.y, nzm.y, jv,
+                                            cx.hq, nbeta, rnd[1], lane, valid, bq1);
+                    if (COL == 1) {
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) {
+                            bg[0][kk] += bq0[kk];
+                            bg[1][kk] += bq1[kk];
+                        }
+                    }
+                }
+                uint2 sn;
+                sn.x = s.x ^ fm.x;
+                sn.y = s.y ^ fm.y;
+                store_packed(sm.spins + own, sn);
+                if (COL == 1) {
+                    const uint2 partner = (st.x & 1) ? nxm : nxp;
+                    macc0 += sn.x + partner.x;
+                    macc1 += sn.y + partner.y;
+                }
+            }
+            if (kFlushU && !GAUSS && COL == 1) {
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {
+                    bg[0][kk] += (eacc0 >> (8 * kk)) & 0xFFu;
+                    bg[1][kk] += (eacc1 >> (8 * kk)) & 0xFFu;
+                }
+                eacc0 = eacc1 = 0;
+            }
+        }
+        if (COL == 1) {
+#pragma unroll
+            for (int r = 0; r < 2; ++r)
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {
+                    const int t = t0 + kk;
+                    if (t >= cx.nt) continue;
+                    const uint32_t ea = r ? eacc1 : eacc0;
+                    const uint32_t ma = r ? macc1 : macc0;
+                    const long long usum = (long long)((ea >> (8 * kk)) & 0xFFu) + (kFlushU ? bg[r][kk] : 0);
+                    const long long b = GAUSS ? (long long)bg[r][kk] : 6LL * RUN - 2LL * usum;
+                    const long long mm = 2LL * RUN - 2LL * ((ma >> (8 * kk)) & 0xFFu);
+                    atomicAdd(&sm.B[r * cx.Tp + t], (unsigned long long)b);
+                    atomicAdd(&sm.M[r * cx.Tp + t], (unsigned long long)mm);
+                }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Replica exchange between slots p and p+1 of each replica (pairs of one
 // parity), then the state swap of accepted pairs as byte permutations of the
 // 4-slot words. stamp identifies this exchange in xflag.
@@ -350,7 +512,11 @@ __device__ __forceinline__ void exchange_decide(const Smem &sm, const Ctx &cx, c
     const int lane = threadIdx.x;
     const int nt = cx.nt, Tp = cx.Tp, WR = cx.WR;
     const int np = (nt - parity) / 2;
-    if (lane < 2) sm.anyswap[lane] = 0;
+    if (lane < 2) {
+        sm.anyswap[lane] = 0;
+        sm.accm[lane] = 0ull;
+    }
+    __syncwarp();
     for (int id = lane; id < 2 * np; id += 32) {
         const int r = id / np;
         const int p = parity + 2 * (id % np);
@@ -374,6 +540,7 @@ __device__ __forceinline__ void exchange_decide(const Smem &sm, const Ctx &cx, c
             Mp[0] = Mp[1];
             Mp[1] = tm;
             sm.xflag[r * Tp + p] = stamp;
+            atomicOr(&sm.accm[r], 1ull << p);
         }
     }
     __syncwarp();
@@ -427,6 +594,33 @@ __device__ __forceinline__ void exchange_apply(const Smem &sm, const Ctx &cx)
     }
 }
 
+// Packed state: per site, each replica's slots as one mask (bit t = slot t);
+// an accepted pair (p, p+1) swaps bits p and p+1. Pairs of one parity are
+// disjoint, so one masked exchange per replica applies them all.
+template <int L>
+__device__ __forceinline__ void exchange_apply_packed(const Smem &sm, const Ctx &cx)
+{
+    constexpr int N = L * L * L;
+    const int WR = cx.WR, RB = cx.RB;
+    const unsigned long long a0 = sm.accm[0], a1 = sm.accm[1];
+    if (!(a0 | a1)) return;
+    for (int site = threadIdx.x; site < N; site += blockDim.x) {
+        uint8_t *row = sm.spins + (size_t)site * RB;
+        unsigned long long w0 = 0, w1 = 0;
+        for (int jj = 0; jj < WR; ++jj) {
+            const unsigned long long b = row[jj];
+            w0 |= (b & 15ull) << (4 * jj);
+            w1 |= (b >> 4) << (4 * jj);
+        }
+        const unsigned long long x0 = (w0 ^ (w0 >> 1)) & a0;
+        const unsigned long long x1 = (w1 ^ (w1 >> 1)) & a1;
+        w0 ^= x0 | (x0 << 1);
+        w1 ^= x1 | (x1 << 1);
+        for (int jj = 0; jj < WR; ++jj)
+            row[jj] = (uint8_t)(((w0 >> (4 * jj)) & 15ull) | (((w1 >> (4 * jj)) & 15ull) << 4));
+    }
+}
+
 // Counts of q = -1 per phase d of one wave vector, from the 2D marginal
 // pm[(A*L + B)*nw] (byte sh): PAT 0: A = d; 1: B = d; 2: A + B = d;
 // 3: A - B = d (mod L). The L sums are independent load chains.
@@ -453,7 +647,7 @@ __device__ __forceinline__ void count_pattern(const uint32_t *pm, int nw, int sh
 // orbits), the FP32 DFT in ascending d and the FP64 accumulation,
 // together with Q, E and M. Processed mchunk 4-slot groups at a time.
 // ---------------------------------------------------------------------------
-template <int L>
+template <int L, bool PACK>
 __device__ __forceinline__ void measure_step(const Smem &sm, const Ctx &cx, const Int8Args &a,
                                              int bin)
 {
@@ -504,12 +698,20 @@ __device__ __forceinline__ void measure_step(const Smem &sm, const Ctx &cx, cons
                 base = L * A + LL * Bc;
                 step = 1;
             }
-            const int woff = 8 * (j0 + jj);
             uint32_t cnt = 0;
+            if constexpr (PACK) {  // q of the group's 4 slots: the two nibbles' xor
 #pragma unroll 4
-            for (int m = 0; m < L; ++m) {
-                const uint2 w = *reinterpret_cast<const uint2 *>(sm.spins + (base + m * step) * RB + woff);
-                cnt += w.x ^ w.y;
+                for (int m = 0; m < L; ++m) {
+                    const uint32_t b = sm.spins[(size_t)(base + m * step) * RB + j0 + jj];
+                    cnt += expand4((b ^ (b >> 4)) & 15u);
+                }
+            } else {
+                const int woff = 8 * (j0 + jj);
+#pragma unroll 4
+                for (int m = 0; m < L; ++m) {
+                    const uint2 w = *reinterpret_cast<const uint2 *>(sm.spins + (base + m * step) * RB + woff);
+                    cnt += w.x ^ w.y;
+                }
             }
             sm.marg[(plane * LL + A * L + Bc) * nw + jj] = cnt;
         }
@@ -606,8 +808,9 @@ __global__ void __launch_bounds__(KernelBounds<L, GST>::threads, KernelBounds<L,
     Ctx cx;
     cx.nt = a.nt;
     cx.Tp = a.Tp;
+    constexpr bool PACK = GST;  // global-memory instances keep the packed state
     cx.WR = a.Tp / 4;
-    cx.RB = 2 * a.Tp;
+    cx.RB = PACK ? a.Tp / 4 : 2 * a.Tp;
     cx.seed_lo = a.seed_lo;
     cx.seed_hi = a.seed_hi;
     cx.hq = a.h_f;
@@ -668,7 +871,10 @@ __global__ void __launch_bounds__(KernelBounds<L, GST>::threads, KernelBounds<L,
             // one code path for both colours keeps the instruction footprint small
 #pragma unroll 1
             for (int col = 0; col < 2; ++col) {
-                half_sweep<L, GAUSS>(sm, cx, (uint32_t)n, col);
+                if constexpr (PACK)
+                    half_sweep_packed<L, GAUSS>(sm, cx, (uint32_t)n, col);
+                else
+                    half_sweep<L, GAUSS>(sm, cx, (uint32_t)n, col);
                 if (col == 0)
                     for (int k = threadIdx.x; k < 2 * a.Tp; k += blockDim.x) {
                         sm.B[k] = 0;
@@ -681,11 +887,14 @@ __global__ void __launch_bounds__(KernelBounds<L, GST>::threads, KernelBounds<L,
                 ++stamp;
                 if (threadIdx.x < 32) exchange_decide(sm, cx, a, (int)(e & 1), (uint32_t)n, 0u, stamp);
                 __syncthreads();
-                exchange_apply<L>(sm, cx);
+                if constexpr (PACK)
+                    exchange_apply_packed<L>(sm, cx);
+                else
+                    exchange_apply<L>(sm, cx);
                 __syncthreads();
             }
             if (n >= a.n_therm && (n - a.n_therm) % a.measure_every == 0)
-                measure_step<L>(sm, cx, a, log_bin(n, a.n_bins));
+                measure_step<L, PACK>(sm, cx, a, log_bin(n, a.n_bins));
         }
         __syncthreads();
         if (!GST) copy16(a.spins + (size_t)s * N * cx.RB, sm.spins, (size_t)N * cx.RB);

@@ -12,7 +12,8 @@ namespace sg {
 // Arguments of the fused int8 sweep kernel (one CTA owns one sample at a time
 // and keeps its whole state -- every replica and slot -- in shared memory).
 struct Int8Args {
-    uint8_t *spins;        // [S][N][2*Tp] bytes, 0 => +1, 1 => -1; byte r*Tp + t
+    uint8_t *spins;        // [S][N][2*Tp] bytes, 0 => +1, 1 => -1 (slot_byte layout);
+                           // global-memory instances: packed [S][N][Tp/4]
     const uint8_t *J8;     // [S][N][8] +-J bond bits (+x,-x,+y,-y,+z,-z,0,0), 1 => J=-1
     const float *Jg;       // [S][3][N] Gaussian couplings
     int64_t *B;            // [S][2][Tp] bond sums of the current configuration
@@ -54,7 +55,14 @@ struct Int8Launch {
 size_t int8_smem_bytes(int L, int Tp, bool gauss, int mchunk, bool gst);
 int int8_max_threads(int L, bool gst);
 // Launch thread counts must be multiples of this (Tp = padded slot count).
-int int8_thread_quantum(int Tp);
+int int8_thread_quantum(int Tp, bool gst);
+// The global-memory instances keep the state packed, one byte per (site,
+// 4-slot group) for the group's 8 chains; every other int8 kernel works on
+// the byte-per-chain layout [S][N][2*Tp]. skip: as for the imports.
+cudaError_t int8_pack_spins(uint8_t *packed, const uint8_t *unpacked, int64_t S, int L, int Tp,
+                            cudaStream_t st, const int *skip = nullptr);
+cudaError_t int8_unpack_spins(uint8_t *unpacked, const uint8_t *packed, int64_t S, int L, int Tp,
+                              cudaStream_t st);
 // Configure and launch the fused kernel.
 cudaError_t int8_launch(int L, bool gauss, const Int8Args &a, const Int8Launch &cfg,
                         cudaStream_t st);
