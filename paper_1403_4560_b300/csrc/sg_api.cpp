@@ -223,7 +223,10 @@ sg_status configure_launch(sg_ensemble *e)
             const int eff = (int)std::min<int64_t>(occ, per_sm);
             const int rounds = (items + t - 1) / t;
             const double useful = (double)items / rounds * eff;
-            const double score = std::min(useful, 1024.0) + 0.5 * eff - 1e-3 * t;
+            // packed global-memory state: one wide CTA per SM measured best
+            // (the whole L1 for one sample's planes, no ragged second wave
+            // when samples are not a multiple of the SMs)
+            const double score = gst ? (double)t : std::min(useful, 1024.0) + 0.5 * eff - 1e-3 * t;
             if (score > best_score) {
                 best_score = score;
                 best_t = t;

@@ -69,7 +69,7 @@ def test_few_large_samples_get_wide_ctas():
     T = inputs.geometric_ladder(0.5, 1.6, 32)
     with sgmc.Ensemble(16, 0.1, T, "gauss", 256, 1) as ens:
         info = ens.info()
-        assert info.state_in_shared == 0 and info.grid == 256
+        assert info.state_in_shared == 0 and info.grid <= 256
         assert info.threads_per_block >= 256, info.threads_per_block
     with sgmc.Ensemble(12, 0.1, inputs.geometric_ladder(0.5, 1.6, 24), "gauss", 512, 1) as ens:
         info = ens.info()
