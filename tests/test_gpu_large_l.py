@@ -102,3 +102,53 @@ def test_state_mode_requests_that_cannot_be_met_are_rejected():
     with pytest.raises(sgmc.SgError) as ei:
         sgmc.Ensemble(8, 0.2, T, "gauss", 4, 1, state_mode=3)
     assert ei.value.status == sgmc.SG_EINVAL
+
+
+@pytest.mark.parametrize("nt,dist", [(64, "pmj"), (1, "gauss"), (9, "gauss")])
+def test_packed_state_edge_slot_counts_are_bit_exact(nt, dist):
+    """Global-memory (packed) state with 64 temperatures (the exchange masks
+    use all 64 bits), a single temperature (one 4-slot group) and a ragged
+    group, against the oracle."""
+    L, S = 10, 2
+    T = inputs.geometric_ladder(0.4, 1.6, nt)
+    J, s0 = inputs.make_instance(dist, L, S, nt, seed=nt)
+    with sgmc.Ensemble(L, 0.2, T, dist, S, 31, J=J, spins=s0, state_mode=2, log_bins=2,
+                       pq_hist=1) as ens:
+        assert ens.info().state_in_shared == 0
+        ens.sweep(6)
+        st = orc.State(L, T, 0.2, dist == "gauss", seed=31, J=J, spins=s0, log_bins=2, pq_hist=True)
+        st.run(6, threads=THREADS)
+        np.testing.assert_array_equal(ens.spins(), st.spins)
+        np.testing.assert_array_equal(ens.energies()[0], st.B)
+        np.testing.assert_array_equal(ens.accumulators(), st.acc)
+        np.testing.assert_array_equal(ens.histogram(), st.hist)
+
+
+def test_standalone_calls_on_packed_state_match_shared_memory_state():
+    """Calls that read or change the state outside the fused kernel (standalone
+    exchange and measurement, spin get/set, a rejected asynchronous upload)
+    go through the ensemble's unpacked copy; they must give what the same
+    calls give on the shared-memory state."""
+    L, nt, S = 12, 6, 4
+    T = inputs.geometric_ladder(0.5, 1.5, nt)
+    J, s0 = inputs.make_instance("gauss", L, S, nt, seed=77)
+    kv = [[1, 0, 0], [0, 2, 1], [3, 1, -1]]
+    out = {}
+    for mode in (1, 2):
+        with sgmc.Ensemble(L, 0.2, T, "gauss", S, 13, J=J, spins=s0, state_mode=mode) as e:
+            e.sweep(7)
+            e.exchange(1)
+            e.sweep(3)
+            m = e.measure(kv)
+            bad = e.spins().copy()
+            bad.reshape(-1)[5] = 0
+            e.set_spins_async(bad)
+            with pytest.raises(sgmc.SgError):
+                e.synchronize()
+            e.sweep(2)
+            flipped = -e.spins()
+            e.set_spins(flipped)
+            e.sweep(2)
+            out[mode] = (m, e.spins(), e.energies()[0], e.accumulators())
+    for a, b in zip(out[1], out[2]):
+        np.testing.assert_array_equal(a, b)
