@@ -25,6 +25,12 @@
 // Work item of a half-sweep: (run of RUN = lcm(L/2, 4) consecutive sites of
 // one colour, one 4-slot group, one replica). RUN is a multiple of 4, so
 // the Philox calls (four sites each) never straddle two items.
+//
+// Global-memory instances (large lattices, or many temperatures): the CTA
+// sweeps its sample's state in place in global memory, packed to one byte
+// per (site, 4-slot group) -- bit 4r + k is chain (replica r, slot 4j + k) --
+// so that rows are 8x smaller and stay in L1; their work item covers both
+// replicas of a group (one thread per byte), see half_sweep_packed.
 #pragma once
 #include <cuda_runtime.h>
 
