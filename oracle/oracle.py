@@ -317,6 +317,7 @@ def observables(acc: np.ndarray, L: int, jackknife: bool = True) -> dict:
     err = {}
     for k in est:
         th = np.stack([r[k] for r in reps], axis=0)
-        err[k] = np.sqrt((S - 1) / S * ((th - th.mean(axis=0)) ** 2).sum(axis=0))
+        with np.errstate(invalid="ignore"):  # xi is NaN where chi0/chi1 < 1; its error too
+            err[k] = np.sqrt((S - 1) / S * ((th - th.mean(axis=0)) ** 2).sum(axis=0))
     est["err"] = err
     return est
