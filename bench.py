@@ -201,7 +201,7 @@ def run_reference(args, rank):
     T = inputs.geometric_ladder(T_MIN, T_MAX, N_T)
     J, s0 = inputs.make_instance("gauss", 12, cores, N_T, seed=5)
     st = orc.State(12, T, 0.2, True, seed=5, J=J, spins=s0, n_therm=0)
-    per_step = 4  # sweeps per step: one call, so thread start-up is amortised
+    per_step = 16  # sweeps per step: one call, so thread start-up is amortised
     for _ in range(args.warmup):
         st.run(per_step, threads=cores)
     for _ in range(args.steps):
