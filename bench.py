@@ -291,6 +291,23 @@ def extra_msc(sgmc, stream, torch, L=16, S=4096, T=None, h=0.1):
     return out
 
 
+def extra_int8(sgmc, stream, torch, L, S, T, h, dist="gauss", sweeps=32):
+    """The fused int8 path on one ensemble (measurement every sweep), timed
+    over `sweeps` sweeps after a warm-up launch."""
+    with sgmc.Ensemble(L, h, T, dist, S, 7, stream=stream, n_therm=0) as e:
+        e.sweep(4)
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(stream)
+        e.sweep(sweeps)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        info = e.info()
+        return {"value": info.attempts_per_sweep * sweeps / (ev[0].elapsed_time(ev[1]) * 1e6),
+                "unit": UNIT, "threads": info.threads_per_block, "grid": info.grid,
+                "workload": f"{dist}, L={L}, {S} samples, 2x{len(T)} T, h={h}"}
+
+
 def extra_serving(sgmc, stream, n_req=24, rate=50.0, sweeps=256):
     """A finite Poisson stream (mean 50 requests/s, seed 1) of requests drawn
     uniformly from L in {8,12,16,20,24}, h in {0.05,...,0.40}, 16-32
@@ -490,14 +507,16 @@ def main():
 
     extras = None
     if rank == 0 and not args.no_extras:
+        # the paper's own geometry (Table I): L = 10, 56 temperatures
+        # geometric in beta 0.1-1.8, h = 0.1
+        t_paper = np.ascontiguousarray((1.0 / (0.1 * 18.0 ** (np.arange(56) / 55.0)))[::-1])
         extras = {"uneven_batch": extra_uneven_batch(sgmc, inputs, stream, torch),
                   "msc_L16": extra_msc(sgmc, stream, torch),
-                  # the paper's own geometry (Table I): L = 10, 56 temperatures
-                  # geometric in beta 0.1-1.8, h = 0.1; 8192 samples here
-                  "msc_paper_L10_56T": extra_msc(
-                      sgmc, stream, torch, L=10, S=8192, h=0.1,
-                      T=np.ascontiguousarray(
-                          (1.0 / (0.1 * 18.0 ** (np.arange(56) / 55.0)))[::-1])),
+                  "msc_paper_L10_56T": extra_msc(sgmc, stream, torch, L=10, S=8192, h=0.1,
+                                                 T=t_paper),
+                  # the same geometry with Gaussian couplings on the int8 path
+                  "int8_paper_L10_56T_gauss": extra_int8(sgmc, stream, torch, L=10, S=1184,
+                                                         T=t_paper, h=0.1),
                   "serving": extra_serving(sgmc, stream)}
 
     cb = None

@@ -99,7 +99,10 @@ typedef struct {
     int32_t measure_every;     /* measure every k-th sweep once measuring     */
     int64_t n_therm;           /* first measured sweep (global sweep index);
                                   the paper thermalises for the first half   */
-    int32_t threads_per_block; /* 0 = library choice (autotuned where known)  */
+    int32_t threads_per_block; /* 0 = library choice (autotuned where known);
+                                  else rounded down to a multiple of the work
+                                  quantum and clamped to the kernel's bound
+                                  (int8: 192 for L <= 8, 512 otherwise) */
     int32_t sweeps_per_launch; /* 0 = library choice                          */
     uint64_t watchdog_cycles;  /* 0 = no limit; else per-launch clock64 budget
                                   after which kernels stop and report

@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -174,10 +175,10 @@ int pad_slots(int nt) { return (nt + 3) & ~3; }
 std::mutex g_tune_mu;
 std::map<std::string, std::pair<int, int>> g_tuned;  // -> (threads, mchunk)
 
-std::string tune_key(const sg_ensemble *e, bool gst)
+std::string tune_key(const sg_ensemble *e, const Int8Launch &c)
 {
     return std::to_string(e->L) + ":" + std::to_string(e->Tp) + ":" + (e->gauss ? "g" : "j") +
-           (gst ? ":gst" : ":smem");
+           (c.gst ? ":gst" : c.wide ? ":wide" : ":smem");
 }
 
 // Launch shape: threads per CTA are a multiple of int8_thread_quantum (each
@@ -194,55 +195,73 @@ sg_status configure_launch(sg_ensemble *e)
     // sample's state does not fit (large L or many temperatures)
     for (int pass = 0; pass < 2; ++pass) {
         const bool gst = pass == 1;
-        const int maxt = int8_max_threads(e->L, gst);
         if ((e->opt.state_mode == 1 && gst) || (e->opt.state_mode == 2 && !gst)) continue;
         const int Q = int8_thread_quantum(e->Tp, gst);  // thread counts are multiples of Q
         const int items = (L * L * L / 2) / run * Q;
-        double best_score = -1.0;
+        double best_score = -1e300;  // scores of requested sizes are negative
         int best_t = 0, best_m = 0, best_occ = 0;
-        for (int t = Q; t <= maxt; t += Q) {
-            if (t < 32) continue;  // the measurement needs one full warp
-            if (e->opt.threads_per_block > 0 &&  // a request is clamped to what the kernel allows
-                t != std::max(((32 + Q - 1) / Q) * Q, (std::min(e->opt.threads_per_block, maxt) / Q) * Q))
-                continue;
-            int occ = 0, m_for = 0;
-            for (int m = WR; m >= 1; --m) {
-                const size_t smem = int8_smem_bytes(L, e->Tp, e->gauss, m, gst);
-                if (!smem) continue;
-                const int o = int8_ctas_per_sm(L, e->gauss, t, smem, gst);
-                if (o > occ) {
-                    occ = o;
-                    m_for = m;
+        bool best_wide = false;
+        // in shared memory, L = 10 and 12 have two instances: two CTAs per SM
+        // of up to 320 threads, or one of up to 512 (many temperatures, or
+        // fewer samples than twice the SMs); the same score picks between them
+        for (int v = 0; v < (gst ? 1 : 2); ++v) {
+            const bool wide = v == 1;
+            if (wide && !int8_wide_has(L)) continue;
+            const int maxt = int8_max_threads(e->L, gst, wide);
+            for (int t = Q; t <= maxt; t += Q) {
+                if (t < 32) continue;  // the measurement needs one full warp
+                // a request is clamped to what the instance allows
+                const int req = (std::min(e->opt.threads_per_block, maxt) / Q) * Q;
+                if (e->opt.threads_per_block > 0 && t != std::max(((32 + Q - 1) / Q) * Q, req))
+                    continue;
+                int occ = 0, m_for = 0;
+                for (int m = WR; m >= 1; --m) {
+                    const size_t smem = int8_smem_bytes(L, e->Tp, e->gauss, m, gst);
+                    if (!smem) continue;
+                    const int o = int8_ctas_per_sm(L, e->gauss, t, smem, gst, wide);
+                    if (o > occ) {
+                        occ = o;
+                        m_for = m;
+                    }
                 }
-            }
-            if (!occ) continue;
-            // useful threads per SM: work items in flight per round, over the
-            // CTAs an SM actually gets (one CTA per sample, so never more than
-            // ceil(S / SMs)); ties go to wider CTAs, i.e. fewer rounds of work
-            // items between barriers (measured on B300: +-J, L = 14, 16 T,
-            // 392 x 1 CTA at 305 attempts/ns against 200 x 2 at 163)
-            const int64_t per_sm = (e->S + e->num_sms - 1) / e->num_sms;
-            const int eff = (int)std::min<int64_t>(occ, per_sm);
-            const int rounds = (items + t - 1) / t;
-            const double useful = (double)items / rounds * eff;
-            // packed global-memory state: one wide CTA per SM measured best
-            // (the whole L1 for one sample's planes, no ragged second wave
-            // when samples are not a multiple of the SMs)
-            const double score = gst ? (double)t : std::min(useful, 1024.0) + 1e-3 * t;
-            if (score > best_score) {
-                best_score = score;
-                best_t = t;
-                best_m = m_for;
-                best_occ = occ;
+                if (!occ) continue;
+                // useful threads per SM: work items in flight per round, over the
+                // CTAs an SM actually gets (one CTA per sample, so never more than
+                // ceil(S / SMs)); ties go to wider CTAs, i.e. fewer rounds of work
+                // items between barriers (measured on B300: +-J, L = 14, 16 T,
+                // 392 x 1 CTA at 305 attempts/ns against 200 x 2 at 163)
+                const int64_t per_sm = (e->S + e->num_sms - 1) / e->num_sms;
+                const int eff = (int)std::min<int64_t>(occ, per_sm);
+                const int rounds = (items + t - 1) / t;
+                const double useful = (double)items / rounds * eff;
+                // packed global-memory state: one wide CTA per SM measured best
+                // (the whole L1 for one sample's planes, no ragged second wave
+                // when samples are not a multiple of the SMs)
+                // a requested CTA size: the instance that comes closest to it
+                const double score =
+                    gst                              ? (double)t
+                    : e->opt.threads_per_block > 0 ? -std::abs(t - e->opt.threads_per_block) + 1e-6 * useful
+                                                     : std::min(useful, 1024.0) + 1e-3 * t;
+                if (score > best_score) {
+                    best_score = score;
+                    best_t = t;
+                    best_m = m_for;
+                    best_occ = occ;
+                    best_wide = wide;
+                }
             }
         }
         if (best_occ == 0) continue;
+        Int8Launch cand{};
+        cand.gst = gst;
+        cand.wide = best_wide;
         if (e->opt.threads_per_block <= 0) {  // a tuned shape for this problem wins
             std::lock_guard<std::mutex> lk(g_tune_mu);
-            auto it = g_tuned.find(tune_key(e, gst));
+            auto it = g_tuned.find(tune_key(e, cand));
             if (it != g_tuned.end()) {
                 const size_t smem = int8_smem_bytes(L, e->Tp, e->gauss, it->second.second, gst);
-                const int occ = smem ? int8_ctas_per_sm(L, e->gauss, it->second.first, smem, gst) : 0;
+                const int occ =
+                    smem ? int8_ctas_per_sm(L, e->gauss, it->second.first, smem, gst, best_wide) : 0;
                 if (occ > 0) {
                     best_t = it->second.first;
                     best_m = it->second.second;
@@ -253,6 +272,7 @@ sg_status configure_launch(sg_ensemble *e)
         e->mchunk = best_m;
         e->launch.threads = best_t;
         e->launch.gst = gst;
+        e->launch.wide = best_wide;
         e->launch.smem = int8_smem_bytes(L, e->Tp, e->gauss, best_m, gst);
         const int64_t resident = (int64_t)best_occ * e->num_sms;
         e->launch.grid = (int)std::min<int64_t>(e->S, resident);
@@ -1225,11 +1245,13 @@ sg_status sg_autotune(sg_ensemble *e, int64_t trial_sweeps, sg_tune_report *rep)
     cudaError_t ce = save(false);
     std::vector<std::pair<int, int>> cands;
     cands.push_back({orig_launch.threads, orig_m});
-    for (int t = ((32 + Q - 1) / Q) * Q; t <= int8_max_threads(e->L, orig_launch.gst); t += Q) {
+    for (int t = ((32 + Q - 1) / Q) * Q; t <= int8_max_threads(e->L, orig_launch.gst, orig_launch.wide);
+         t += Q) {
         int best_occ = 0, m_for = 0;
         for (int m = WR; m >= 1; --m) {
             const size_t smem = int8_smem_bytes(e->L, e->Tp, e->gauss, m, orig_launch.gst);
-            const int o = smem ? int8_ctas_per_sm(e->L, e->gauss, t, smem, orig_launch.gst) : 0;
+            const int o =
+                smem ? int8_ctas_per_sm(e->L, e->gauss, t, smem, orig_launch.gst, orig_launch.wide) : 0;
             if (o > best_occ) {
                 best_occ = o;
                 m_for = m;
@@ -1248,7 +1270,7 @@ sg_status sg_autotune(sg_ensemble *e, int64_t trial_sweeps, sg_tune_report *rep)
         e->mchunk = cands[c].second;
         e->launch.smem = int8_smem_bytes(e->L, e->Tp, e->gauss, e->mchunk, orig_launch.gst);
         const int occ = int8_ctas_per_sm(e->L, e->gauss, e->launch.threads, e->launch.smem,
-                                         orig_launch.gst);
+                                         orig_launch.gst, orig_launch.wide);
         e->launch.grid = (int)std::min<int64_t>(e->S, (int64_t)occ * e->num_sms);
         if (launch_sweeps(e, 1, e->stream, false) != SG_OK) break;  // warm-up
         cudaEventRecord(e0, e->stream);
@@ -1281,11 +1303,12 @@ sg_status sg_autotune(sg_ensemble *e, int64_t trial_sweeps, sg_tune_report *rep)
     e->launch.threads = best_t;
     e->mchunk = best_m;
     e->launch.smem = int8_smem_bytes(e->L, e->Tp, e->gauss, best_m, orig_launch.gst);
-    const int occ = int8_ctas_per_sm(e->L, e->gauss, best_t, e->launch.smem, orig_launch.gst);
+    const int occ =
+        int8_ctas_per_sm(e->L, e->gauss, best_t, e->launch.smem, orig_launch.gst, orig_launch.wide);
     e->launch.grid = (int)std::min<int64_t>(e->S, (int64_t)occ * e->num_sms);
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tuned[tune_key(e, orig_launch.gst)] = {best_t, best_m};
+        g_tuned[tune_key(e, orig_launch)] = {best_t, best_m};
     }
     r.threads_per_block = best_t;
     r.mchunk = best_m;

@@ -397,9 +397,10 @@ int int8_thread_quantum(int Tp, bool gst)
     return gst ? Tp / 4 : Tp / 2;
 }
 
-int int8_max_threads(int L, bool gst)
+int int8_max_threads(int L, bool gst, bool wide)
 {
     if (gst) return KernelBounds<10, true>::threads;  // the same for every L
+    if (wide) return int8_wide_has(L) ? KernelBounds<12, false, true>::threads : 0;
     if (L <= 8) return KernelBounds<8, false>::threads;
     if (L <= 12) return KernelBounds<12, false>::threads;
     return KernelBounds<16, false>::threads;
@@ -409,6 +410,7 @@ cudaError_t int8_launch(int L, bool gauss, const Int8Args &a, const Int8Launch &
                         cudaStream_t st)
 {
     if (cfg.gst) return int8_launch_gst(L, gauss, a, cfg, st);
+    if (cfg.wide) return int8_launch_wide(L, gauss, a, cfg, st);
 #define X(LL)                                                                          \
     if (L == LL)                                                                       \
         return gauss ? launch_t<LL, true, false>(a, cfg, st) : launch_t<LL, false, false>(a, cfg, st);
@@ -417,9 +419,10 @@ cudaError_t int8_launch(int L, bool gauss, const Int8Args &a, const Int8Launch &
     return cudaErrorInvalidValue;
 }
 
-int int8_ctas_per_sm(int L, bool gauss, int threads, size_t smem, bool gst)
+int int8_ctas_per_sm(int L, bool gauss, int threads, size_t smem, bool gst, bool wide)
 {
     if (gst) return int8_ctas_per_sm_gst(L, gauss, threads, smem);
+    if (wide) return int8_ctas_per_sm_wide(L, gauss, threads, smem);
 #define X(LL) \
     if (L == LL) return gauss ? occ_t<LL, true, false>(threads, smem) : occ_t<LL, false, false>(threads, smem);
     SG_FOR_EACH_L(X)

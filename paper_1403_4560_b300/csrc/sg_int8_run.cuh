@@ -53,12 +53,13 @@ constexpr int kMaxThreads = 512;
 //   L = 10, 12 in shared memory: two samples fit per SM; 320 threads and
 //     two CTAs per SM (at most 96 registers, no spills with one replica per
 //     work item) give up to 20 warps instead of 13.5;
-//   larger lattices (one CTA per SM in shared memory, or global-memory
-//     state): up to 512 threads with 128 registers.
-template <int L, bool GST>
+//   the same lattices with many temperatures (one sample per SM: WIDE),
+//     larger lattices (one CTA per SM in shared memory), and the
+//     global-memory state: up to 512 threads with 128 registers.
+template <int L, bool GST, bool WIDE = false>
 struct KernelBounds {
     static constexpr bool kSmall = L <= 8 && !GST;
-    static constexpr bool kMid = (L == 10 || L == 12) && !GST;
+    static constexpr bool kMid = (L == 10 || L == 12) && !GST && !WIDE;
     static constexpr int threads = kSmall ? 192 : kMid ? 320 : kMaxThreads;
     static constexpr int min_blocks = kSmall ? 4 : kMid ? 2 : 1;
 };
@@ -803,8 +804,9 @@ __device__ __forceinline__ void copy16(void *dst, const void *src, size_t bytes)
 // The fused kernel: for each sample of this CTA, load, run n_sweeps sweeps
 // (half-sweeps, energies, exchange, measurement), store.
 // ---------------------------------------------------------------------------
-template <int L, bool GAUSS, bool GST>
-__global__ void __launch_bounds__(KernelBounds<L, GST>::threads, KernelBounds<L, GST>::min_blocks)
+template <int L, bool GAUSS, bool GST, bool WIDE = false>
+__global__ void __launch_bounds__(KernelBounds<L, GST, WIDE>::threads,
+                                  KernelBounds<L, GST, WIDE>::min_blocks)
     int8_run_kernel(const Int8Args a)
 {
     constexpr int N = L * L * L;
@@ -916,28 +918,28 @@ __global__ void __launch_bounds__(KernelBounds<L, GST>::threads, KernelBounds<L,
 constexpr int kMaxSmem = 227 * 1024;
 
 // Raise the kernel's dynamic shared-memory limit once (before any capture).
-template <int L, bool G, bool GST>
+template <int L, bool G, bool GST, bool WIDE = false>
 cudaError_t ensure_attr()
 {
     static cudaError_t done = cudaFuncSetAttribute(
-        int8_run_kernel<L, G, GST>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+        int8_run_kernel<L, G, GST, WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
     return done;
 }
 
-template <int L, bool G, bool GST>
+template <int L, bool G, bool GST, bool WIDE = false>
 cudaError_t launch_t(const Int8Args &a, const Int8Launch &c, cudaStream_t st)
 {
-    cudaError_t e = ensure_attr<L, G, GST>();
+    cudaError_t e = ensure_attr<L, G, GST, WIDE>();
     if (e != cudaSuccess) return e;
-    int8_run_kernel<L, G, GST><<<c.grid, c.threads, c.smem, st>>>(a);
+    int8_run_kernel<L, G, GST, WIDE><<<c.grid, c.threads, c.smem, st>>>(a);
     return cudaGetLastError();
 }
 
-template <int L, bool G, bool GST>
+template <int L, bool G, bool GST, bool WIDE = false>
 int occ_t(int threads, size_t smem)
 {
-    auto k = int8_run_kernel<L, G, GST>;
-    if (ensure_attr<L, G, GST>() != cudaSuccess) return 0;
+    auto k = int8_run_kernel<L, G, GST, WIDE>;
+    if (ensure_attr<L, G, GST, WIDE>() != cudaSuccess) return 0;
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, threads, smem) != cudaSuccess)
         return 0;

@@ -47,13 +47,14 @@ struct Int8Args {
 struct Int8Launch {
     int threads, grid;
     size_t smem;
-    bool gst;  // state kept in global memory (large L) instead of shared memory
+    bool gst;   // state kept in global memory (large L) instead of shared memory
+    bool wide;  // shared-memory state, one CTA of up to 512 threads per SM (L = 10, 12)
 };
 
 // Shared-memory bytes of the fused kernel, or 0 when the state does not fit
 // (or no kernel is built for that L and mode).
 size_t int8_smem_bytes(int L, int Tp, bool gauss, int mchunk, bool gst);
-int int8_max_threads(int L, bool gst);
+int int8_max_threads(int L, bool gst, bool wide = false);
 // Launch thread counts must be multiples of this (Tp = padded slot count).
 int int8_thread_quantum(int Tp, bool gst);
 // The global-memory instances keep the state packed, one byte per (site,
@@ -67,12 +68,19 @@ cudaError_t int8_unpack_spins(uint8_t *unpacked, const uint8_t *packed, int64_t 
 cudaError_t int8_launch(int L, bool gauss, const Int8Args &a, const Int8Launch &cfg,
                         cudaStream_t st);
 // Occupancy of the fused kernel (CTAs per SM), 0 if it cannot launch.
-int int8_ctas_per_sm(int L, bool gauss, int threads, size_t smem, bool gst);
+int int8_ctas_per_sm(int L, bool gauss, int threads, size_t smem, bool gst, bool wide = false);
 // The global-memory (large lattice) instances, in their own translation unit.
 bool int8_gst_has(int L);
 cudaError_t int8_launch_gst(int L, bool gauss, const Int8Args &a, const Int8Launch &cfg,
                             cudaStream_t st);
 int int8_ctas_per_sm_gst(int L, bool gauss, int threads, size_t smem);
+// The wide shared-memory instances (one sample per SM with up to 512
+// threads), for the lattice sizes whose narrow instance is bounded at two
+// CTAs per SM; in their own translation unit.
+bool int8_wide_has(int L);
+cudaError_t int8_launch_wide(int L, bool gauss, const Int8Args &a, const Int8Launch &cfg,
+                             cudaStream_t st);
+int int8_ctas_per_sm_wide(int L, bool gauss, int threads, size_t smem);
 
 // Instance preparation and state conversion kernels.
 cudaError_t int8_gen_pmj(uint8_t *J8, int64_t S, int L, uint32_t seed_lo, uint32_t seed_hi,

@@ -76,6 +76,56 @@ def test_few_large_samples_get_wide_ctas():
         assert info.state_in_shared == 1 and info.threads_per_block >= 64
 
 
+# the narrow shared-memory instance of L = 10, 12 is bounded at 320 threads
+NARROW_MAX = 320
+
+
+@pytest.mark.parametrize("L,nt,dist,S", [(10, 56, "gauss", 3), (10, 56, "pmj", 2), (12, 40, "pmj", 2),
+                                         (12, 24, "gauss", 2)])
+def test_wide_shared_memory_instance_is_bit_exact(L, nt, dist, S):
+    """Many temperatures (one sample per SM's shared memory) or fewer samples
+    than SMs: L = 10, 12 run the wide instance (one CTA of up to 512 threads
+    per SM), which must give the oracle's chain bit for bit."""
+    T = inputs.geometric_ladder(0.5, 1.6, nt)
+    J, s0 = inputs.make_instance(dist, L, S, nt, seed=L + nt)
+    with sgmc.Ensemble(L, 0.2, T, dist, S, 31, J=J, spins=s0, state_mode=1, log_bins=2,
+                       pq_hist=1) as ens:
+        info = ens.info()
+        assert info.state_in_shared == 1 and info.threads_per_block > NARROW_MAX, info.threads_per_block
+        ens.sweep(3)
+        ens.sweep(2)
+        st = orc.State(L, T, 0.2, dist == "gauss", seed=31, J=J, spins=s0, log_bins=2, pq_hist=True)
+        st.run(5, threads=THREADS)
+        np.testing.assert_array_equal(ens.spins(), st.spins)
+        B, M = ens.energies()
+        np.testing.assert_array_equal(B, st.B)
+        np.testing.assert_array_equal(M, st.M)
+        np.testing.assert_array_equal(ens.accumulators(), st.acc)
+        np.testing.assert_array_equal(ens.histogram(), st.hist)
+
+
+def test_instance_choice_follows_occupancy_and_requests():
+    """Many samples with few temperatures keep two narrow CTAs per SM; many
+    temperatures (one sample per SM) take the wide instance; a requested CTA
+    size above the narrow bound selects the wide instance, and both give the
+    same chain."""
+    many = inputs.geometric_ladder(0.5, 1.6, 56)
+    few = inputs.geometric_ladder(0.5, 1.6, 24)
+    with sgmc.Ensemble(12, 0.1, few, "gauss", 1024, 1) as ens:
+        assert ens.info().threads_per_block <= NARROW_MAX
+    with sgmc.Ensemble(10, 0.1, many, "gauss", 1024, 1) as ens:
+        assert ens.info().threads_per_block > NARROW_MAX
+    J, s0 = inputs.make_instance("gauss", 12, 3, 24, seed=5)
+    got = []
+    for req in (120, 480):
+        with sgmc.Ensemble(12, 0.1, few, "gauss", 3, 8, J=J, spins=s0, threads_per_block=req) as ens:
+            assert ens.info().threads_per_block == req
+            ens.sweep(6)
+            got.append((ens.spins(), ens.accumulators()))
+    np.testing.assert_array_equal(got[0][0], got[1][0])
+    np.testing.assert_array_equal(got[0][1], got[1][1])
+
+
 @pytest.mark.parametrize("L,dist", [(10, "gauss"), (12, "pmj")])
 def test_state_in_shared_or_global_memory_gives_the_same_chain(L, dist):
     T = inputs.geometric_ladder(0.5, 1.6, 6)
