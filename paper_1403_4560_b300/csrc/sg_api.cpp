@@ -188,16 +188,14 @@ std::string tune_key(const sg_ensemble *e, const Int8Launch &c)
 sg_status configure_launch(sg_ensemble *e)
 {
     const int WR = e->Tp / 4;
-    const int L = e->L, H = L / 2;
-    int run = H;
-    while (run % 4) run += H;
+    const int L = e->L;
     // shared-memory residency first; the global-memory variant when the
     // sample's state does not fit (large L or many temperatures)
     for (int pass = 0; pass < 2; ++pass) {
         const bool gst = pass == 1;
         if ((e->opt.state_mode == 1 && gst) || (e->opt.state_mode == 2 && !gst)) continue;
         const int Q = int8_thread_quantum(e->Tp, gst);  // thread counts are multiples of Q
-        const int items = (L * L * L / 2) / run * Q;
+        const int items = (L * L * L / 2) / int8_site_run(L, gst) * Q;
         double best_score = -1e300;  // scores of requested sizes are negative
         int best_t = 0, best_m = 0, best_occ = 0;
         bool best_wide = false;

@@ -45,14 +45,16 @@ namespace {
 
 
 constexpr int kMaxThreads = 512;
+// colour sites per work item of the shared-memory half-sweep
+constexpr int kSiteRun = 4;
 
 // Launch bounds of an instance, chosen from B300 measurements of the
 // register / resident-warp trade-off:
 //   L <= 8 in shared memory: several samples fit per SM, so up to 192
 //     threads and four CTAs per SM (at most 80 registers);
-//   L = 10, 12 in shared memory: two samples fit per SM; 320 threads and
+//   L = 10, 12 in shared memory: two samples fit per SM; 336 threads and
 //     two CTAs per SM (at most 96 registers, no spills with one replica per
-//     work item) give up to 20 warps instead of 13.5;
+//     work item) give up to 21 warps instead of 13.5;
 //   the same lattices with many temperatures (one sample per SM: WIDE),
 //     larger lattices (one CTA per SM in shared memory), and the
 //     global-memory state: up to 512 threads with 128 registers.
@@ -248,30 +250,35 @@ __device__ __forceinline__ uint32_t gauss_word(uint32_t s, uint32_t nxp, uint32_
 
 // ---------------------------------------------------------------------------
 // One checkerboard half-sweep of colour COL over all chains of the sample.
-// Work item: (run of RUN colour-COL sites, 4-slot group j, replica r), i.e.
-// 4 chains; a thread keeps (j, r) for every item it takes, so its slots'
-// tables are loaded once. One replica per item halves the live random
-// numbers and spin words against an item over both replicas, which keeps
-// the kernel's registers low enough for more resident warps. For COL == 1 it
+// Work item: (4 consecutive colour-COL sites, i.e. one Philox counter group;
+// 4-slot group j; replica r): 16 attempts. A thread keeps (j, r) for every
+// item it takes, so its slots' tables are loaded once. One replica per item
+// halves the live random numbers and spin words against an item over both
+// replicas, which keeps the kernel's registers low enough for more resident
+// warps. Short items balance the threads' shares (L = 14, 24 temperatures,
+// 504 threads: 4116 items in 8.2 rounds, against 588 items in 1.2 rounds
+// with items a row long), so fewer warps idle at the barrier that ends the
+// half-sweep, and the partial energy sums of many items share one flush to
+// shared memory (B300: L = 8 +14 %, L = 14 +14 %, L = 12 +2 %). For COL == 1 it
 // also accumulates B and M of the post-sweep configuration: every bond has
 // exactly one colour-1 end, so summing s_i * b_i over colour-1 sites counts
 // each bond once; M pairs each colour-1 site with its x^1 partner (colour 0,
-// final after the colour-0 half).
+// final after the colour-0 half). The byte-wise partial sums run over the
+// thread's successive items and go to shared memory every kFlushSites sites.
 // ---------------------------------------------------------------------------
 template <int L, bool GAUSS>
 __device__ __forceinline__ void half_sweep(const Smem &sm, const Ctx &cx, uint32_t n_sweep,
                                         const int COL)
 {
-    constexpr int H = L / 2;
     constexpr int N = L * L * L;
-    constexpr int RUN = lcm_c(H, 4);
-    constexpr int NG = RUN / 4;
+    constexpr int RUN = kSiteRun;
     constexpr int U = (N / 2) / RUN;
+    // byte-wise sums: at most 6 unsatisfied bonds and 2 for M per site
+    constexpr int kFlushSites = 40;
     const int WR = cx.WR, RB = cx.RB;
     const int jr = threadIdx.x % (2 * WR);  // fixed per thread: blockDim.x is a multiple of 2 WR
     const int j = jr >> 1, r = jr & 1;
     const int t0 = 4 * j;
-    const int items = U * 2 * WR;
 
     uint32_t valid = 0;  // bytes of real (not padding) slots in this group
 #pragma unroll
@@ -284,15 +291,36 @@ __device__ __forceinline__ void half_sweep(const Smem &sm, const Ctx &cx, uint32
     const uint32_t *thr_w = GAUSS ? nullptr : sm.thr + t0 * 16;
     const int woff = 8 * j + 4 * r;  // byte offset of this (group, replica) word in a site row
 
-    for (int item = threadIdx.x; item < items; item += blockDim.x) {
-        const int u = item / (2 * WR);
-        uint32_t eacc = 0, macc = 0;  // byte-wise partial sums
-        int bg[4] = {0, 0, 0, 0};
-        // long runs would overflow the byte-wise sums of unsatisfied bonds
-        // (6 per site): those are flushed into bg after every group of 4 sites
-        constexpr bool kFlushU = 6 * RUN > 255;
-        for (int g = 0; g < NG; ++g) {
-            const uint32_t c0 = (uint32_t)(u * NG + g);
+    uint32_t eacc = 0, macc = 0;  // byte-wise partial sums
+    int bg[4] = {0, 0, 0, 0};
+    int nsites = 0;               // colour-1 sites in the partial sums
+    // partial sums to shared memory, per slot of this thread's group
+    auto flush = [&]() {
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+            const int t = t0 + kk;
+            if (t < cx.nt) {
+                // +-J: s b = 6 - 2u per colour-1 site; M: each pair gives 2 - 2*(#-1)
+                const long long usum = (long long)((eacc >> (8 * kk)) & 0xFFu);
+                const long long b = GAUSS ? (long long)bg[kk] : 6LL * nsites - 2LL * usum;
+                const long long mm = 2LL * nsites - 2LL * ((macc >> (8 * kk)) & 0xFFu);
+                atomicAdd(&sm.B[r * cx.Tp + t], (unsigned long long)b);
+                atomicAdd(&sm.M[r * cx.Tp + t], (unsigned long long)mm);
+            }
+            bg[kk] = 0;
+        }
+        eacc = 0;
+        macc = 0;
+        nsites = 0;
+    };
+
+    // item = u * 2 WR + jr: blockDim.x is a multiple of 2 WR, so a thread's
+    // successive items advance u by a fixed step (no division per item)
+    const int du = blockDim.x / (2 * WR);
+    for (int u = threadIdx.x / (2 * WR); u < U; u += du) {
+        if (COL == 1 && nsites + RUN > kFlushSites) flush();
+        {
+            const uint32_t c0 = (uint32_t)u;
             uint32_t rnd[4][4];
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk) {
@@ -305,7 +333,7 @@ __device__ __forceinline__ void half_sweep(const Smem &sm, const Ctx &cx, uint32
             }
 #pragma unroll
             for (int lane = 0; lane < 4; ++lane) {
-                const SiteNb<L> st(u * RUN + 4 * g + lane, COL);
+                const SiteNb<L> st(u * RUN + lane, COL);
                 const int own = st.i * RB + woff;
                 const uint32_t s = lds32(sm.spins, own);
                 const uint32_t nxp = lds32(sm.spins, own + st.dxp * RB);
@@ -348,26 +376,10 @@ __device__ __forceinline__ void half_sweep(const Smem &sm, const Ctx &cx, uint32
                     macc += sn + partner;
                 }
             }
-            if (kFlushU && !GAUSS && COL == 1) {
-#pragma unroll
-                for (int kk = 0; kk < 4; ++kk) bg[kk] += (eacc >> (8 * kk)) & 0xFFu;
-                eacc = 0;
-            }
         }
-        if (COL == 1) {
-#pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-                const int t = t0 + kk;
-                if (t >= cx.nt) continue;
-                // +-J: s b = 6 - 2u per colour-1 site; M: each pair gives 2 - 2*(#-1)
-                const long long usum = (long long)((eacc >> (8 * kk)) & 0xFFu) + (kFlushU ? bg[kk] : 0);
-                const long long b = GAUSS ? (long long)bg[kk] : 6LL * RUN - 2LL * usum;
-                const long long mm = 2LL * RUN - 2LL * ((macc >> (8 * kk)) & 0xFFu);
-                atomicAdd(&sm.B[r * cx.Tp + t], (unsigned long long)b);
-                atomicAdd(&sm.M[r * cx.Tp + t], (unsigned long long)mm);
-            }
-        }
+        nsites += RUN;
     }
+    if (COL == 1 && nsites > 0) flush();
 }
 
 // ---------------------------------------------------------------------------

@@ -55,6 +55,8 @@ struct Int8Launch {
 // (or no kernel is built for that L and mode).
 size_t int8_smem_bytes(int L, int Tp, bool gauss, int mchunk, bool gst);
 int int8_max_threads(int L, bool gst, bool wide = false);
+// Colour sites per half-sweep work item (items = (L^3 / 2) / run * quantum).
+int int8_site_run(int L, bool gst);
 // Launch thread counts must be multiples of this (Tp = padded slot count).
 int int8_thread_quantum(int Tp, bool gst);
 // The global-memory instances keep the state packed, one byte per (site,
