@@ -397,11 +397,9 @@ int int8_thread_quantum(int Tp, bool gst)
     return gst ? Tp / 4 : Tp / 2;
 }
 
-int int8_site_run(int L, bool gst)
+int int8_site_run(int, bool)
 {
-    // packed items run along rows (lcm(L/2, 4) colour sites); shared-memory
-    // items are one Philox group
-    return gst ? lcm_c(L / 2, 4) : kSiteRun;
+    return kSiteRun;  // one Philox group, in both state layouts
 }
 
 int int8_max_threads(int L, bool gst, bool wide)

@@ -66,8 +66,6 @@ struct KernelBounds {
     static constexpr int min_blocks = kSmall ? 4 : kMid ? 2 : 1;
 };
 
-__host__ __device__ constexpr int gcd_c(int a, int b) { return b == 0 ? a : gcd_c(b, a % b); }
-__host__ __device__ constexpr int lcm_c(int a, int b) { return a / gcd_c(a, b) * b; }
 
 __device__ __forceinline__ uint32_t lds32(const uint8_t *base, int off)
 {
@@ -384,24 +382,23 @@ __device__ __forceinline__ void half_sweep(const Smem &sm, const Ctx &cx, uint32
 
 // ---------------------------------------------------------------------------
 // Half-sweep of colour COL on the packed state (global-memory instances).
-// Work item: (run of RUN colour-COL sites, 4-slot group j, both replicas),
-// i.e. the 8 chains of one byte, which this thread alone writes. The rule,
-// random numbers and energy bookkeeping are those of half_sweep; only the
-// storage differs (one byte per site and group, expanded to 0/1 bytes).
+// Work item: (4 colour-COL sites = one Philox group, 4-slot group j, both
+// replicas), i.e. the 8 chains of one byte, which this thread alone writes.
+// The rule, random numbers, item order and energy bookkeeping are those of
+// half_sweep; only the storage differs (one byte per site and group,
+// expanded to 0/1 bytes).
 // ---------------------------------------------------------------------------
 template <int L, bool GAUSS>
 __device__ __forceinline__ void half_sweep_packed(const Smem &sm, const Ctx &cx, uint32_t n_sweep,
                                                   const int COL)
 {
-    constexpr int H = L / 2;
     constexpr int N = L * L * L;
-    constexpr int RUN = lcm_c(H, 4);
-    constexpr int NG = RUN / 4;
+    constexpr int RUN = kSiteRun;
     constexpr int U = (N / 2) / RUN;
+    constexpr int kFlushSites = 40;    // byte-wise sums: 6 (bonds) and 2 (M) per site
     const int WR = cx.WR, RB = cx.RB;  // packed: RB == WR bytes per site
     const int j = threadIdx.x % WR;    // fixed per thread: blockDim.x is a multiple of WR
     const int t0 = 4 * j;
-    const int items = U * WR;
 
     uint32_t valid = 0;  // bytes of real (not padding) slots in this group
 #pragma unroll
@@ -413,13 +410,36 @@ __device__ __forceinline__ void half_sweep_packed(const Smem &sm, const Ctx &cx,
     for (int kk = 0; kk < 4; ++kk) nbeta[kk] = GAUSS ? sm.negbeta[t0 + kk] : 0.0f;
     const uint32_t *thr_w = GAUSS ? nullptr : sm.thr + t0 * 16;
 
-    for (int item = threadIdx.x; item < items; item += blockDim.x) {
-        const int u = item / WR;
-        uint32_t eacc0 = 0, eacc1 = 0, macc0 = 0, macc1 = 0;  // byte-wise partial sums
-        int bg[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
-        constexpr bool kFlushU = 6 * RUN > 255;
-        for (int g = 0; g < NG; ++g) {
-            const uint32_t c0 = (uint32_t)(u * NG + g);
+    uint32_t eacc0 = 0, eacc1 = 0, macc0 = 0, macc1 = 0;  // byte-wise partial sums
+    int bg[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+    int nsites = 0;  // colour-1 sites in the partial sums
+    auto flush = [&]() {
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                const int t = t0 + kk;
+                if (t < cx.nt) {
+                    const uint32_t ea = r ? eacc1 : eacc0;
+                    const uint32_t ma = r ? macc1 : macc0;
+                    const long long usum = (long long)((ea >> (8 * kk)) & 0xFFu);
+                    const long long b = GAUSS ? (long long)bg[r][kk] : 6LL * nsites - 2LL * usum;
+                    const long long mm = 2LL * nsites - 2LL * ((ma >> (8 * kk)) & 0xFFu);
+                    atomicAdd(&sm.B[r * cx.Tp + t], (unsigned long long)b);
+                    atomicAdd(&sm.M[r * cx.Tp + t], (unsigned long long)mm);
+                }
+                bg[r][kk] = 0;
+            }
+        eacc0 = eacc1 = macc0 = macc1 = 0;
+        nsites = 0;
+    };
+
+    // item = u * WR + j with a fixed step of u per thread (no division per item)
+    const int du = blockDim.x / WR;
+    for (int u = threadIdx.x / WR; u < U; u += du) {
+        if (COL == 1 && nsites + RUN > kFlushSites) flush();
+        {
+            const uint32_t c0 = (uint32_t)u;
             uint32_t rnd[2][4][4];
 #pragma unroll
             for (int r = 0; r < 2; ++r)
@@ -435,7 +455,7 @@ __device__ __forceinline__ void half_sweep_packed(const Smem &sm, const Ctx &cx,
                 }
 #pragma unroll
             for (int lane = 0; lane < 4; ++lane) {
-                const SiteNb<L> st(u * RUN + 4 * g + lane, COL);
+                const SiteNb<L> st(u * RUN + lane, COL);
                 const int own = st.i * RB + j;
                 const uint2 s = load_packed(sm.spins + own);
                 const uint2 nxp = load_packed(sm.spins + own + st.dxp * RB);
@@ -490,32 +510,10 @@ __device__ __forceinline__ void half_sweep_packed(const Smem &sm, const Ctx &cx,
                     macc1 += sn.y + partner.y;
                 }
             }
-            if (kFlushU && !GAUSS && COL == 1) {
-#pragma unroll
-                for (int kk = 0; kk < 4; ++kk) {
-                    bg[0][kk] += (eacc0 >> (8 * kk)) & 0xFFu;
-                    bg[1][kk] += (eacc1 >> (8 * kk)) & 0xFFu;
-                }
-                eacc0 = eacc1 = 0;
-            }
         }
-        if (COL == 1) {
-#pragma unroll
-            for (int r = 0; r < 2; ++r)
-#pragma unroll
-                for (int kk = 0; kk < 4; ++kk) {
-                    const int t = t0 + kk;
-                    if (t >= cx.nt) continue;
-                    const uint32_t ea = r ? eacc1 : eacc0;
-                    const uint32_t ma = r ? macc1 : macc0;
-                    const long long usum = (long long)((ea >> (8 * kk)) & 0xFFu) + (kFlushU ? bg[r][kk] : 0);
-                    const long long b = GAUSS ? (long long)bg[r][kk] : 6LL * RUN - 2LL * usum;
-                    const long long mm = 2LL * RUN - 2LL * ((ma >> (8 * kk)) & 0xFFu);
-                    atomicAdd(&sm.B[r * cx.Tp + t], (unsigned long long)b);
-                    atomicAdd(&sm.M[r * cx.Tp + t], (unsigned long long)mm);
-                }
-        }
+        nsites += RUN;
     }
+    if (COL == 1 && nsites > 0) flush();
 }
 
 // ---------------------------------------------------------------------------
