@@ -638,22 +638,45 @@ __device__ __forceinline__ void exchange_apply_packed(const Smem &sm, const Ctx 
     }
 }
 
-// Counts of q = -1 per phase d of one wave vector, from the 2D marginal
-// pm[(A*L + B)*nw] (byte sh): PAT 0: A = d; 1: B = d; 2: A + B = d;
-// 3: A - B = d (mod L). The L sums are independent load chains.
+// Counts of q = -1 per phase d of one wave vector, for the 4 slots of a
+// marginal word at once, from the 2D marginal pm[(A*L + B)*nw]: PAT 0: A = d;
+// 1: B = d; 2: A + B = d; 3: A - B = d (mod L). This lane takes the phases
+// d = part + 4k; the sums stay in byte lanes (one per slot) while L*L <= 255,
+// otherwise in two words of 16-bit lanes (lo: slots 0, 2; hi: slots 1, 3).
 template <int L, int PAT>
-__device__ __forceinline__ void count_pattern(const uint32_t *pm, int nw, int sh, int (&cs)[L])
+__device__ __forceinline__ void count_phases(const uint32_t *pm, int nw, int part,
+                                             uint32_t (&lo)[(L + 3) / 4],
+                                             uint32_t (&hi)[(L + 3) / 4])
 {
+    constexpr bool kWide = L * L > 255;
 #pragma unroll
-    for (int d = 0; d < L; ++d) {
-        int c = 0;
+    for (int k = 0; k < (L + 3) / 4; ++k) {
+        const int d = part + 4 * k;
+        uint32_t a = 0, b = 0;
+        if (d < L) {
 #pragma unroll 4
-        for (int aa = 0; aa < L; ++aa) {
-            const int A = PAT == 0 ? d : aa;
-            const int Bc = PAT == 0 ? aa : PAT == 1 ? d : PAT == 2 ? (d - aa + L) % L : (aa - d + L) % L;
-            c += (pm[(A * L + Bc) * nw] >> sh) & 0xFF;
+            for (int aa = 0; aa < L; ++aa) {
+                int A = aa, Bc;
+                if (PAT == 0) {
+                    A = d;
+                    Bc = aa;
+                } else if (PAT == 1) {
+                    Bc = d;
+                } else {
+                    Bc = PAT == 2 ? d - aa : aa - d;
+                    Bc += (Bc >> 31) & L;  // mod L of a value in (-L, L)
+                }
+                const uint32_t w = pm[(A * L + Bc) * nw];
+                if (kWide) {
+                    a += w & 0x00FF00FFu;
+                    b += (w >> 8) & 0x00FF00FFu;
+                } else {
+                    a += w;
+                }
+            }
         }
-        cs[d] = c;
+        lo[k] = a;
+        hi[k] = b;
     }
 }
 
@@ -662,7 +685,8 @@ __device__ __forceinline__ void count_pattern(const uint32_t *pm, int nw, int sh
 // (A) 2D marginals of the q = -1 counts over the xy, xz and yz planes,
 // (B) per (slot, v): the integer projections P_v[d] (v over the k1 and k2
 // orbits), the FP32 DFT in ascending d and the FP64 accumulation,
-// together with Q, E and M. Processed mchunk 4-slot groups at a time.
+// together with Q; E and M per slot before both. Processed mchunk 4-slot
+// groups at a time.
 // ---------------------------------------------------------------------------
 template <int L, bool PACK>
 __device__ __forceinline__ void measure_step(const Smem &sm, const Ctx &cx, const Int8Args &a,
@@ -733,68 +757,96 @@ __device__ __forceinline__ void measure_step(const Smem &sm, const Ctx &cx, cons
             sm.marg[(plane * LL + A * L + Bc) * nw + jj] = cnt;
         }
         __syncthreads();
-        // (B) one thread per (slot, v): the L projections P_v[d] from L*L
-        // independent loads, then the FP32 DFT in ascending d and the FP64
-        // accumulation; v == 9 handles Q, E and M. The task's accumulators are
-        // loaded first so that their global-memory latency overlaps the counting.
-        // the slot varies fastest across lanes: one wave vector (one code path)
-        // per warp, adjacent marginal words per lane
-        for (int id = threadIdx.x; id < 4 * nw * 10; id += blockDim.x) {
-            const int sl = id % (4 * nw);  // 4*jj + kk
-            const int v = id / (4 * nw);
-            const int t = 4 * j0 + sl;
-            if (t >= nt) continue;
-            const int jj = sl >> 2, sh = 8 * (sl & 3);
-            double *acv = accs + (size_t)(v == 9 ? 0 : 9 + 3 * v) * nt + t;  // entry at acv[q * nt]
-            const int nacc = v == 9 ? 5 : 3;
-            double old[9];
+        // (B) one warp per wave vector v (v = 0..8; the v = 0 warp also takes
+        // Q, whose count is the sum of its phases). Lane = 4 * (word jj) +
+        // part: the part counts its phases for the word's 4 slots at once,
+        // shuffles then give each lane every phase of slot 4 * jj + part, and
+        // the lane runs the FP32 DFT in ascending d and the FP64 accumulation.
+        // The accumulators are loaded first, so that their global-memory
+        // latency overlaps the counting.
+        {
+            constexpr int ND = (L + 3) / 4;
+            constexpr bool kWide = L * L > 255;
+            const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+            const int nwarp = blockDim.x >> 5;  // full warps (shuffles need all lanes)
+            const int part = lane & 3;
+            for (int v = warp; v < 9 && warp < nwarp; v += nwarp) {
+                for (int jb = 0; jb < nw; jb += 8) {
+                    const int jj = jb + (lane >> 2);
+                    const int t = 4 * (j0 + jj) + part;
+                    const bool live = jj < nw && t < nt;
+                    const int jc = jj < nw ? jj : 0;  // lanes past the chunk count a real word
+                    double *acv = accs + (size_t)(9 + 3 * v) * nt + t;  // entry at acv[q * nt]
+                    double *acq = accs + t;                            // Q: entries 0..4
+                    double old[3] = {0.0, 0.0, 0.0};
+                    if (live) {
 #pragma unroll
-            for (int q = 0; q < 9; ++q) old[q] = q < nacc ? acv[q * nt] : 0.0;
-            int cs[L];
-            if (v == 9 || v == 0)
-                count_pattern<L, 0>(sm.marg + jj, nw, sh, cs);
-            else if (v == 1)
-                count_pattern<L, 1>(sm.marg + jj, nw, sh, cs);
-            else if (v == 2)
-                count_pattern<L, 1>(sm.marg + LL * nw + jj, nw, sh, cs);
-            else {
-                const int plane = (v == 3 || v == 4) ? 0 : (v == 5 || v == 6) ? 1 : 2;
-                const uint32_t *pm = sm.marg + plane * LL * nw + jj;
-                if (v == 3 || v == 5 || v == 7)
-                    count_pattern<L, 2>(pm, nw, sh, cs);
-                else
-                    count_pattern<L, 3>(pm, nw, sh, cs);
-            }
-            if (v == 9) {
-                int Qi = 0;
+                        for (int q = 0; q < 3; ++q) old[q] = acv[q * nt];
+                    }
+                    uint32_t lo[ND], hi[ND];
+                    const uint32_t *pm0 = sm.marg + jc;
+                    if (v == 0)
+                        count_phases<L, 0>(pm0, nw, part, lo, hi);
+                    else if (v == 1)
+                        count_phases<L, 1>(pm0, nw, part, lo, hi);
+                    else if (v == 2)
+                        count_phases<L, 1>(pm0 + LL * nw, nw, part, lo, hi);
+                    else {
+                        const int plane = (v == 3 || v == 4) ? 0 : (v == 5 || v == 6) ? 1 : 2;
+                        const uint32_t *pm = pm0 + plane * LL * nw;
+                        if (v == 3 || v == 5 || v == 7)
+                            count_phases<L, 2>(pm, nw, part, lo, hi);
+                        else
+                            count_phases<L, 3>(pm, nw, part, lo, hi);
+                    }
+                    float re = 0.0f, im = 0.0f;
+                    int Qi = 0;
+                    const int src0 = lane & ~3;
 #pragma unroll
-                for (int d = 0; d < L; ++d) Qi += LL - 2 * cs[d];
-                if (a.hist)  // P(q): replicas agree on (N + Q) / 2 sites
-                    atomicAdd(a.hist + ((size_t)t * a.n_bins + bin) * (L * LL + 1) + ((L * LL + Qi) >> 1),
-                              1ull);
-                const double Q = (double)Qi;
-                const double Q2 = __dmul_rn(Q, Q);
-                old[0] = __dadd_rn(old[0], 1.0);
-                old[1] = __dadd_rn(old[1], Q);
-                old[2] = __dadd_rn(old[2], Q2);
-                old[3] = __dadd_rn(old[3], __dmul_rn(Q2, Q));
-                old[4] = __dadd_rn(old[4], __dmul_rn(Q2, Q2));
-            } else {
-                float re = 0.0f, im = 0.0f;
+                    for (int d = 0; d < L; ++d) {
+                        // phase d lives in lane part d & 3, sum index d >> 2
+                        const uint32_t xl = __shfl_sync(0xFFFFFFFFu, lo[d >> 2], src0 | (d & 3));
+                        int c;
+                        if (kWide) {
+                            const uint32_t xh = __shfl_sync(0xFFFFFFFFu, hi[d >> 2], src0 | (d & 3));
+                            const uint32_t x = (part & 1) ? xh : xl;
+                            c = (int)((part & 2) ? (x >> 16) : (x & 0xFFFFu));
+                        } else {
+                            c = (int)((xl >> (8 * part)) & 0xFFu);
+                        }
+                        const int P = LL - 2 * c;
+                        Qi += P;
+                        const float Pf = (float)P;
+                        re = __fmaf_rn(Pf, sm.twid[d], re);
+                        im = __fmaf_rn(Pf, sm.twid[L + d], im);
+                    }
+                    if (!live) continue;
+                    const double dr = (double)re, di = (double)im;
+                    old[0] = __dadd_rn(old[0], dr);
+                    old[1] = __dadd_rn(old[1], di);
+                    old[2] = __dadd_rn(old[2], __dadd_rn(__dmul_rn(dr, dr), __dmul_rn(di, di)));
 #pragma unroll
-                for (int d = 0; d < L; ++d) {
-                    const float Pf = (float)(LL - 2 * cs[d]);
-                    re = __fmaf_rn(Pf, sm.twid[d], re);
-                    im = __fmaf_rn(Pf, sm.twid[L + d], im);
+                    for (int q = 0; q < 3; ++q) acv[q * nt] = old[q];
+                    if (v == 0) {
+                        if (a.hist)  // P(q): replicas agree on (N + Q) / 2 sites
+                            atomicAdd(a.hist + ((size_t)t * a.n_bins + bin) * (L * LL + 1) +
+                                          ((L * LL + Qi) >> 1),
+                                      1ull);
+                        double oq[5];
+#pragma unroll
+                        for (int q = 0; q < 5; ++q) oq[q] = acq[q * nt];
+                        const double Q = (double)Qi;
+                        const double Q2 = __dmul_rn(Q, Q);
+                        oq[0] = __dadd_rn(oq[0], 1.0);
+                        oq[1] = __dadd_rn(oq[1], Q);
+                        oq[2] = __dadd_rn(oq[2], Q2);
+                        oq[3] = __dadd_rn(oq[3], __dmul_rn(Q2, Q));
+                        oq[4] = __dadd_rn(oq[4], __dmul_rn(Q2, Q2));
+#pragma unroll
+                        for (int q = 0; q < 5; ++q) acq[q * nt] = oq[q];
+                    }
                 }
-                const double dr = (double)re, di = (double)im;
-                old[0] = __dadd_rn(old[0], dr);
-                old[1] = __dadd_rn(old[1], di);
-                old[2] = __dadd_rn(old[2], __dadd_rn(__dmul_rn(dr, dr), __dmul_rn(di, di)));
             }
-#pragma unroll
-            for (int q = 0; q < 9; ++q)
-                if (q < nacc) acv[q * nt] = old[q];
         }
         // the next chunk's marginals overwrite this chunk's; after the last
         // chunk the next sweep touches nothing this phase reads (spins, B and
