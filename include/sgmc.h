@@ -366,6 +366,18 @@ sg_status sg_observables_from_acc(const double *acc, int64_t n_samples, int n_T,
  */
 sg_status sg_threshold_map(const float *x, int n, uint32_t *out);
 
+/*
+ * Diagnostics: the Gaussian sweep's Metropolis decision for n pairs (x[k],
+ * r[k]), x = -beta dE (FP32) and r a uniform 32-bit word. The decision is
+ * r[k] <= the threshold of sg_threshold_map (paper: methods section,
+ * Metropolis updates); the sweep reaches it through a screen against the
+ * hardware 2^x with a 2^-12 relative guard band and takes the exact threshold
+ * only for draws inside the band. out[k] bit 0: accepted; bit 1: the screen
+ * was undecided and the exact threshold decided. x, r and out are host
+ * arrays of n entries; runs on the current device and synchronises it.
+ */
+sg_status sg_accept_map(const float *x, const uint32_t *r, int n, uint8_t *out);
+
 /* Text for a status code, and the message of the last error on this thread. */
 const char *sg_status_str(sg_status s);
 const char *sg_last_error(void);

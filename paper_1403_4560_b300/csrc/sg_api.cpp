@@ -1137,6 +1137,27 @@ sg_status sg_threshold_map(const float *x, int n, uint32_t *out)
     return SG_OK;
 }
 
+sg_status sg_accept_map(const float *x, const uint32_t *r, int n, uint8_t *out)
+{
+    if (!x || !r || !out || n < 0) return fail(SG_EINVAL, "bad arguments");
+    if (n == 0) return SG_OK;
+    float *xd = nullptr;
+    uint32_t *rd = nullptr;
+    uint8_t *od = nullptr;
+    SG_CUDA(cudaMalloc(&xd, sizeof(float) * (size_t)n), "cudaMalloc");
+    cudaError_t ce = cudaMalloc(&rd, sizeof(uint32_t) * (size_t)n);
+    if (ce == cudaSuccess) ce = cudaMalloc(&od, (size_t)n);
+    if (ce == cudaSuccess) ce = cudaMemcpy(xd, x, sizeof(float) * (size_t)n, cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) ce = cudaMemcpy(rd, r, sizeof(uint32_t) * (size_t)n, cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) ce = accept_map(xd, rd, n, od, 0);
+    if (ce == cudaSuccess) ce = cudaMemcpy(out, od, (size_t)n, cudaMemcpyDeviceToHost);
+    cudaFree(xd);
+    cudaFree(rd);
+    cudaFree(od);
+    if (ce != cudaSuccess) return cuda_fail(ce, "accept map");
+    return SG_OK;
+}
+
 sg_status sg_autotune(sg_ensemble *e, int64_t trial_sweeps, sg_tune_report *rep)
 {
     if (!e || trial_sweeps < 1) return fail(SG_EINVAL, "bad autotune arguments");

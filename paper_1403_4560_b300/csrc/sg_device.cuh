@@ -87,6 +87,29 @@ __device__ __forceinline__ uint32_t thr_of_logp(float x)
     return __float2uint_rz(exp_cw32_scaled<32>(xc));
 }
 
+// Screen of the Metropolis test r <= thr_of_logp(x) that skips the
+// exponential for almost every draw. Accepting iff r <= thr_of_logp(x) is
+// accepting iff r <= F(x), with F = exp_cw32_scaled<32>(clamped x) (r is an
+// integer, and F >= 2^32 saturates the threshold). A = 2^(x log2(e) + 32) from
+// the hardware ex2.approx is within 2^-18 (relative) of e^x 2^32 for
+// x in [-64, 0], counting the rounding of the exponent; F is within 2^-21 of
+// it and the float image of r within 2^-24 of r. So whenever
+// |fl(r) - A| > 2^-12 A the sign of fl(r) - A is the sign of r - F, and the
+// screen decides exactly as the threshold would; x >= 0 (A >= 2^32) never
+// screens as a rejection, and x < -64 leaves only r = 0 accepted, as the clamp
+// does. Draws inside the band (probability below 2^-11 per attempt) set amb,
+// and the caller redoes them with thr_of_logp. Returns fl(r) - A, whose sign
+// bit is the screen's decision (set = accept).
+__device__ __forceinline__ float screen_logp(float x, uint32_t r, bool &amb)
+{
+    const float y = __fmaf_rn(x, 1.44269502f, 32.0f);
+    float a;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(a) : "f"(y));
+    const float u = __fsub_rn(__uint2float_rn(r), a);
+    amb |= fabsf(u) <= __fmul_rn(a, 2.44140625e-4f);  // 2^-12 A
+    return u;
+}
+
 // Logarithmic bin of a measurement taken at global sweep n (0-based):
 // floor(log2(n + 1)), with every later sweep in the last of n_bins bins. Bin b
 // covers sweeps 2^b - 1 .. 2^(b+1) - 2, the second half of a run of 2^(b+1)

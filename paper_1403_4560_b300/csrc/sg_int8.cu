@@ -299,6 +299,19 @@ __global__ void thr_map_kernel(const float *x, int n, uint32_t *out)
         out[k] = thr_of_logp(x[k]);
 }
 
+// Metropolis decision of the Gaussian sweep for (x, r) pairs: the screen,
+// and the exact threshold where the screen is undecided. out bit 0: accept;
+// bit 1: the screen was undecided.
+__global__ void accept_map_kernel(const float *x, const uint32_t *r, int n, uint8_t *out)
+{
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        bool amb = false;
+        const float u = screen_logp(x[k], r[k], amb);
+        const bool acc = amb ? (r[k] <= thr_of_logp(x[k])) : (__float_as_uint(u) >> 31) != 0u;
+        out[k] = (uint8_t)((acc ? 1 : 0) | (amb ? 2 : 0));
+    }
+}
+
 __global__ void advance_kernel(int64_t *ctr, int64_t n)
 {
     if (threadIdx.x == 0 && blockIdx.x == 0) *ctr += n;
@@ -507,6 +520,12 @@ cudaError_t int8_exchange(const Int8Args &a, int L, bool gauss, int parity, uint
 cudaError_t threshold_map(const float *x, int n, uint32_t *out, cudaStream_t st)
 {
     thr_map_kernel<<<grid_for(n, 256), 256, 0, st>>>(x, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t accept_map(const float *x, const uint32_t *r, int n, uint8_t *out, cudaStream_t st)
+{
+    accept_map_kernel<<<grid_for(n, 256), 256, 0, st>>>(x, r, n, out);
     return cudaGetLastError();
 }
 

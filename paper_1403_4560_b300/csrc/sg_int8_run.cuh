@@ -207,43 +207,74 @@ __device__ __forceinline__ uint32_t pmj_word(uint32_t s, uint32_t nxp, uint32_t 
     return fm & valid;
 }
 
-// Gaussian: Metropolis on 4 chains of one replica word. bq[kk] receives
-// s_new * b / qJ for the energy of colour-1 sites.
+// Local field b = sum of J * s_nb of chain kk of a replica word: the sign bit
+// of J flips where the neighbour is -1. The sum is exact on the 2^-17 grid,
+// so a balanced tree (short dependency chain) gives the same value as any
+// other order.
+__device__ __forceinline__ float gauss_field(int kk, uint32_t nxp, uint32_t nxm, uint32_t nyp,
+                                             uint32_t nym, uint32_t nzp, uint32_t nzm,
+                                             const float (&j)[6])
+{
+    const int sh = 31 - 8 * kk;
+    const float t0 = __int_as_float(__float_as_int(j[0]) ^ ((nxp << sh) & 0x80000000u));
+    const float t1 = __int_as_float(__float_as_int(j[1]) ^ ((nxm << sh) & 0x80000000u));
+    const float t2 = __int_as_float(__float_as_int(j[2]) ^ ((nyp << sh) & 0x80000000u));
+    const float t3 = __int_as_float(__float_as_int(j[3]) ^ ((nym << sh) & 0x80000000u));
+    const float t4 = __int_as_float(__float_as_int(j[4]) ^ ((nzp << sh) & 0x80000000u));
+    const float t5 = __int_as_float(__float_as_int(j[5]) ^ ((nzm << sh) & 0x80000000u));
+    return __fadd_rn(__fadd_rn(__fadd_rn(t0, t1), __fadd_rn(t2, t3)), __fadd_rn(t4, t5));
+}
+
+// x = -beta dE of chain kk, dE = 2 s (b + h). nbeta2 = -2 beta (exact), so
+// nbeta2 * (s (b + h)) is the same single rounding of the same product as
+// -beta * dE.
+__device__ __forceinline__ float gauss_logp(int kk, uint32_t s, float b, float hq, float nbeta2)
+{
+    const uint32_t sgn = (s << (31 - 8 * kk)) & 0x80000000u;  // own spin -1 => sign bit
+    const float zf = __fadd_rn(b, hq);
+    return __fmul_rn(nbeta2, __int_as_float(__float_as_int(zf) ^ sgn));
+}
+
+// Gaussian: Metropolis on 4 chains of one replica word; nbeta2[kk] = -2 beta
+// of the chain's slot. bq[kk] receives s_new * b / qJ for the energy of
+// colour-1 sites. The four decisions come from screen_logp; if any draw of
+// the word falls in the screen's band, all four are redone with the exact
+// threshold (dE <= 0 gives x >= 0, whose threshold is 0xFFFFFFFF).
 template <bool ENERGY>
 __device__ __forceinline__ uint32_t gauss_word(uint32_t s, uint32_t nxp, uint32_t nxm,
                                                uint32_t nyp, uint32_t nym, uint32_t nzp,
                                                uint32_t nzm, const float (&j)[6], float hq,
-                                               const float (&nbeta)[4],
+                                               const float (&nbeta2)[4],
                                                const uint32_t (&rnd)[4][4], int lane,
                                                uint32_t valid, int (&bq)[4])
 {
     uint32_t fm = 0;
+    bool amb = false;
 #pragma unroll
     for (int kk = 0; kk < 4; ++kk) {
-        const int sh = 31 - 8 * kk;
-        // J * s_nb: flip the sign bit of J where the neighbour is -1; the sum
-        // is exact on the 2^-17 grid, so a balanced tree (short dependency
-        // chain) gives the same value as any other order
-        const float t0 = __int_as_float(__float_as_int(j[0]) ^ ((nxp << sh) & 0x80000000u));
-        const float t1 = __int_as_float(__float_as_int(j[1]) ^ ((nxm << sh) & 0x80000000u));
-        const float t2 = __int_as_float(__float_as_int(j[2]) ^ ((nyp << sh) & 0x80000000u));
-        const float t3 = __int_as_float(__float_as_int(j[3]) ^ ((nym << sh) & 0x80000000u));
-        const float t4 = __int_as_float(__float_as_int(j[4]) ^ ((nzp << sh) & 0x80000000u));
-        const float t5 = __int_as_float(__float_as_int(j[5]) ^ ((nzm << sh) & 0x80000000u));
-        const float b = __fadd_rn(__fadd_rn(__fadd_rn(t0, t1), __fadd_rn(t2, t3)), __fadd_rn(t4, t5));
-        const uint32_t sgn = (s << sh) & 0x80000000u;  // own spin -1 => sign bit
-        const float zf = __fadd_rn(b, hq);
-        const float dE = __int_as_float(__float_as_int(__fadd_rn(zf, zf)) ^ sgn);
-        // dE <= 0 gives x >= 0, whose threshold is 0xFFFFFFFF: always accepted
-        const float xl = __fmul_rn(nbeta[kk], dE);
-        const uint32_t flip = (rnd[kk][lane] <= thr_of_logp(xl)) & (valid >> (8 * kk));
-        fm |= flip << (8 * kk);
+        const float b = gauss_field(kk, nxp, nxm, nyp, nym, nzp, nzm, j);
+        const float u = screen_logp(gauss_logp(kk, s, b, hq, nbeta2[kk]), rnd[kk][lane], amb);
+        fm |= (__float_as_uint(u) >> (31 - 8 * kk)) & (1u << (8 * kk));
         if (ENERGY) {
             const int q = __float2int_rn(__fmul_rn(b, 131072.0f));
-            bq[kk] = (((s >> (8 * kk)) ^ flip) & 1u) ? -q : q;
+            bq[kk] = (((s ^ fm) >> (8 * kk)) & 1u) ? -q : q;
         }
     }
-    return fm;
+    if (amb) {
+        fm = 0;
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+            const float b = gauss_field(kk, nxp, nxm, nyp, nym, nzp, nzm, j);
+            const uint32_t flip =
+                rnd[kk][lane] <= thr_of_logp(gauss_logp(kk, s, b, hq, nbeta2[kk])) ? 1u : 0u;
+            fm |= flip << (8 * kk);
+            if (ENERGY) {
+                const int q = __float2int_rn(__fmul_rn(b, 131072.0f));
+                bq[kk] = (((s >> (8 * kk)) ^ flip) & 1u) ? -q : q;
+            }
+        }
+    }
+    return fm & valid;
 }
 
 // ---------------------------------------------------------------------------
@@ -283,9 +314,9 @@ __device__ __forceinline__ void half_sweep(const Smem &sm, const Ctx &cx, uint32
     for (int kk = 0; kk < 4; ++kk)
         if (t0 + kk < cx.nt) valid |= 1u << (8 * kk);
 
-    float nbeta[4];
+    float nbeta2[4];  // -2 beta per slot (exact)
 #pragma unroll
-    for (int kk = 0; kk < 4; ++kk) nbeta[kk] = GAUSS ? sm.negbeta[t0 + kk] : 0.0f;
+    for (int kk = 0; kk < 4; ++kk) nbeta2[kk] = GAUSS ? __fmul_rn(2.0f, sm.negbeta[t0 + kk]) : 0.0f;
     const uint32_t *thr_w = GAUSS ? nullptr : sm.thr + t0 * 16;
     const int woff = 8 * j + 4 * r;  // byte offset of this (group, replica) word in a site row
 
@@ -360,7 +391,7 @@ __device__ __forceinline__ void half_sweep(const Smem &sm, const Ctx &cx, uint32
                                          sm.Jg[N + st.i + st.dym], sm.Jg[2 * N + st.i],
                                          sm.Jg[2 * N + st.i + st.dzm]};
                     int bq[4];
-                    fm = gauss_word<true>(s, nxp, nxm, nyp, nym, nzp, nzm, jv, cx.hq, nbeta, rnd,
+                    fm = gauss_word<true>(s, nxp, nxm, nyp, nym, nzp, nzm, jv, cx.hq, nbeta2, rnd,
                                           lane, valid, bq);
                     if (COL == 1) {
 #pragma unroll
@@ -405,9 +436,9 @@ __device__ __forceinline__ void half_sweep_packed(const Smem &sm, const Ctx &cx,
     for (int kk = 0; kk < 4; ++kk)
         if (t0 + kk < cx.nt) valid |= 1u << (8 * kk);
 
-    float nbeta[4];
+    float nbeta2[4];  // -2 beta per slot (exact)
 #pragma unroll
-    for (int kk = 0; kk < 4; ++kk) nbeta[kk] = GAUSS ? sm.negbeta[t0 + kk] : 0.0f;
+    for (int kk = 0; kk < 4; ++kk) nbeta2[kk] = GAUSS ? __fmul_rn(2.0f, sm.negbeta[t0 + kk]) : 0.0f;
     const uint32_t *thr_w = GAUSS ? nullptr : sm.thr + t0 * 16;
 
     uint32_t eacc0 = 0, eacc1 = 0, macc0 = 0, macc1 = 0;  // byte-wise partial sums
@@ -489,9 +520,9 @@ __device__ __forceinline__ void half_sweep_packed(const Smem &sm, const Ctx &cx,
                                          sm.Jg[2 * N + st.i + st.dzm]};
                     int bq0[4], bq1[4];
                     fm.x = gauss_word<true>(s.x, nxp.x, nxm.x, nyp.x, nym.x, nzp.x, nzm.x, jv,
-                                            cx.hq, nbeta, rnd[0], lane, valid, bq0);
+                                            cx.hq, nbeta2, rnd[0], lane, valid, bq0);
                     fm.y = gauss_word<true>(s.y, nxp.y, nxm.y, nyp.y, nym.y, nzp.y, nzm.y, jv,
-                                            cx.hq, nbeta, rnd[1], lane, valid, bq1);
+                                            cx.hq, nbeta2, rnd[1], lane, valid, bq1);
                     if (COL == 1) {
 #pragma unroll
                         for (int kk = 0; kk < 4; ++kk) {

@@ -104,6 +104,7 @@ cudaError_t int8_energies(const Int8Args &a, int L, bool gauss, cudaStream_t st)
 cudaError_t int8_exchange(const Int8Args &a, int L, bool gauss, int parity, uint32_t call_id,
                           cudaStream_t st);
 cudaError_t threshold_map(const float *x, int n, uint32_t *out, cudaStream_t st);
+cudaError_t accept_map(const float *x, const uint32_t *r, int n, uint8_t *out, cudaStream_t st);
 cudaError_t advance_counter(int64_t *ctr, int64_t n, cudaStream_t st);
 // Accumulator layouts: canonical [S][nt][nb][40] <-> device [S][nb][40][nt]
 // (to_dev: canonical src to device dst; else device src to canonical dst).

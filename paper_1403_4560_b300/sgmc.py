@@ -125,6 +125,7 @@ def lib() -> ctypes.CDLL:
         "sg_results_bin": (st, [P, i32, P]),
         "sg_observables_from_acc": (st, [P, i64, i32, i32, P]),
         "sg_threshold_map": (st, [P, i32, P]),
+        "sg_accept_map": (st, [P, P, i32, P]),
         "sg_server_options_default": (None, [P]),
         "sg_request_default": (None, [P]),
         "sg_server_create": (st, [P, P, P]),
@@ -382,6 +383,18 @@ def threshold_map(x) -> np.ndarray:
     x = np.ascontiguousarray(x, dtype=np.float32)
     out = np.zeros(x.shape, dtype=np.uint32)
     _check(lib().sg_threshold_map(_ptr(x), x.size, _ptr(out)))
+    return out
+
+
+def accept_map(x, r) -> np.ndarray:
+    """Device Metropolis decision of the Gaussian sweep for (x, r) pairs
+    (diagnostics): bit 0 accept, bit 1 decided by the exact threshold."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    r = np.ascontiguousarray(r, dtype=np.uint32)
+    if x.shape != r.shape:
+        raise ValueError("x and r must have the same shape")
+    out = np.zeros(x.shape, dtype=np.uint8)
+    _check(lib().sg_accept_map(_ptr(x), _ptr(r), x.size, _ptr(out)))
     return out
 
 

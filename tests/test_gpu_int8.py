@@ -268,6 +268,33 @@ def test_device_threshold_map_matches_oracle_bit_for_bit():
     np.testing.assert_array_equal(got, want)
 
 
+def test_screened_metropolis_decision_is_the_threshold_rule():
+    """The Gaussian sweep decides r <= t32(x) through a screen (hardware 2^x
+    with a 2^-12 guard band) and the exact threshold inside the band. Its
+    decisions equal the oracle's rule at every threshold, one above and one
+    below it, and on uniform draws; draws at the threshold of a large
+    threshold must go to the exact path, uniform draws almost never do."""
+    rng = np.random.default_rng(11)
+    x = np.concatenate([np.linspace(-70.0, 2.0, 150001, dtype=np.float32),
+                        -(rng.random(100000) * 23).astype(np.float32),
+                        -rng.random(50000).astype(np.float32) * 1e-3,
+                        np.array([0.0, -0.0, 1e-30, -1e-30, -64.0, -64.0001, -22.18, -22.19,
+                                  -88.0, -100.0, 5.0, 60.0], dtype=np.float32)])
+    thr = np.array([orc.t32(float(v)) if v < 0 else 0xFFFFFFFF for v in x], dtype=np.int64)
+    uniform = rng.integers(0, 2 ** 32, x.size, dtype=np.int64)
+    for name, r in (("at", thr), ("above", thr + 1), ("below", thr - 1), ("uniform", uniform),
+                    ("zero", np.zeros_like(thr)), ("max", np.full_like(thr, 2 ** 32 - 1))):
+        r = np.clip(r, 0, 2 ** 32 - 1)
+        got = sgmc.accept_map(x, r.astype(np.uint32))
+        np.testing.assert_array_equal(got & 1, (r <= thr).astype(np.uint8), err_msg=name)
+        if name == "at":
+            # the band is wider than one unit of r (x > 0 screens as a sure accept)
+            big = (thr >= 2 ** 14) & (x <= 0)
+            assert np.all(got[big] & 2), "draws at a large threshold skipped the exact path"
+        if name == "uniform":
+            assert np.mean(got & 2) / 2 < 2.0 ** -10
+
+
 @pytest.mark.parametrize("dist,L,nt", [("gauss", 8, 20), ("pmj", 12, 8)])
 def test_autotune_changes_speed_not_results(dist, L, nt):
     S = 40
