@@ -236,7 +236,7 @@ def extra_uneven_batch(sgmc, inputs, stream, torch):
     att_sweep = sum(L ** 3 * 40 * S for L, S in CFG4)
     ens = [sgmc.Ensemble(L, 0.2, T, "gauss", S, 40 + L, J=J, spins=s0, stream=stream, n_therm=0)
            for (L, S), (J, s0) in zip(CFG4, insts)]
-    tune = {f"L{e.L}": e.autotune(trial_sweeps=4)["threads_per_block"] for e in ens}
+    tune = {f"L{e.L}": e.autotune(trial_sweeps=16)["threads_per_block"] for e in ens}
     n = 64
     sgmc.sweep_batch(ens, n, use_graph=True)
     torch.cuda.synchronize()

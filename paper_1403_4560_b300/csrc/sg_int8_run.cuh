@@ -66,6 +66,20 @@ struct KernelBounds {
     static constexpr int min_blocks = kSmall ? 4 : kMid ? 2 : 1;
 };
 
+// Whether the sweep loop gets one code path per colour (the colour, and so
+// the energy bookkeeping of colour 1 only, known at compile time) or one
+// path for both colours (half the instruction footprint). From B300
+// measurements with the screened Metropolis test: separate paths gained
+// 2-6 % for L = 10, 14, 16 and the wide and global-memory instances
+// (+-J and Gaussian), but cost 3-5 % for the Gaussian instances bounded at
+// 80 registers (L <= 8, where they spill) and nothing for Gaussian L = 12
+// at two CTAs per SM.
+template <int L, bool GAUSS, bool GST, bool WIDE>
+__host__ __device__ constexpr bool unroll_colours()
+{
+    return !(GAUSS && !GST && !WIDE && (L <= 8 || L == 12));
+}
+
 
 __device__ __forceinline__ uint32_t lds32(const uint8_t *base, int off)
 {
@@ -969,9 +983,7 @@ __global__ void __launch_bounds__(KernelBounds<L, GST, WIDE>::threads,
                 stop = __syncthreads_or(why != 0);
                 if (stop) break;
             }
-            // one code path for both colours keeps the instruction footprint small
-#pragma unroll 1
-            for (int col = 0; col < 2; ++col) {
+            auto colour = [&](const int col) {
                 if constexpr (PACK)
                     half_sweep_packed<L, GAUSS>(sm, cx, (uint32_t)n, col);
                 else
@@ -982,6 +994,13 @@ __global__ void __launch_bounds__(KernelBounds<L, GST, WIDE>::threads,
                         sm.M[k] = 0;
                     }
                 __syncthreads();
+            };
+            if constexpr (unroll_colours<L, GAUSS, GST, WIDE>()) {
+                colour(0);
+                colour(1);
+            } else {
+#pragma unroll 1
+                for (int col = 0; col < 2; ++col) colour(col);
             }
             if (a.exchange_every > 0 && (n + 1) % a.exchange_every == 0) {
                 const int64_t e = (n + 1) / a.exchange_every - 1;
