@@ -125,13 +125,15 @@ struct MscSmem {
     uint32_t *thr;      // [2][16]  +-J thresholds of the unit's slots (sb*8 + u)
     long long *B, *M;   // [4][64]  per-sample energies of the unit's chains
     uint64_t *swap;     // [2]      exchange masks per replica
-    uint64_t *marg;     // [3][L*L][kDG] bit-sliced 2D marginal counts of q = -1
-    uint64_t *proj;     // [9][L][kDP] bit-sliced projection counts of q = -1
+    uint64_t *marg;     // [ms][3][L*L][kDG] bit-sliced 2D marginal counts of q = -1
+    uint64_t *proj;     // [ms][9][L][kDP] bit-sliced projection counts of q = -1
 };
 
 __host__ __device__ inline size_t a16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-__host__ __device__ inline size_t msc_carve(uint8_t *base, int L, MscSmem *sm)
+// ms: slots whose overlap is measured in one pass (1, or 2 for the wide
+// instance, which measures both slots of its unit together).
+__host__ __device__ inline size_t msc_carve(uint8_t *base, int L, MscSmem *sm, int ms)
 {
     const bool jshared = msc_j_shared(L);
     const size_t N = (size_t)L * L * L;
@@ -148,8 +150,8 @@ __host__ __device__ inline size_t msc_carve(uint8_t *base, int L, MscSmem *sm)
     s.B = reinterpret_cast<long long *>(take(4 * 64 * 8));
     s.M = reinterpret_cast<long long *>(take(4 * 64 * 8));
     s.swap = reinterpret_cast<uint64_t *>(take(2 * 8));
-    s.marg = reinterpret_cast<uint64_t *>(take((size_t)3 * L * L * kDG * 8));
-    s.proj = reinterpret_cast<uint64_t *>(take((size_t)9 * L * kDP * 8));
+    s.marg = reinterpret_cast<uint64_t *>(take((size_t)ms * 3 * L * L * kDG * 8));
+    s.proj = reinterpret_cast<uint64_t *>(take((size_t)ms * 9 * L * kDP * 8));
     if (sm) *sm = s;
     return off;
 }
@@ -308,17 +310,25 @@ __device__ __forceinline__ void msc_half(const MscSmem &sm, const MscArgs &a, in
 // bit-sliced 2D marginals, bit-sliced projections, then per sample the
 // integer projections, the FP32 DFT and the FP64 accumulation.
 // ---------------------------------------------------------------------------
-template <int L>
-__device__ __forceinline__ void msc_measure(const MscSmem &sm, const MscArgs &a, int g, int k,
-                                            int t, int bin)
+template <int L, bool WIDE>
+__device__ __forceinline__ void msc_measure(const MscSmem &sm, const MscArgs &a, int g, int k0,
+                                            int nk, int t0, int bin)
 {
     constexpr int N = L * L * L;
     constexpr int LL = L * L;
-    const uint64_t *w0 = sm.w + (size_t)(2 * k) * N;
-    const uint64_t *w1 = w0 + N;
+    // the unit's slots k0 .. k0 + nk - 1 (temperatures t0 ..) in one pass: one
+    // barrier per phase for all of them, and more independent tasks per phase.
+    // The wide instance unrolls the serial loops of (B) and (C) so their
+    // independent steps overlap (B300, +-J, 2 x 32 T, 4096 samples: L = 16
+    // 1988 -> 2134 attempts/ns with the one-pass slots); the narrow
+    // 80-register instance keeps the compiler's choice, which measured faster.
     // (A) marginal counts of q = -1 (bit set) over the summed axis
-    for (int id = threadIdx.x; id < 3 * LL; id += blockDim.x) {
-        const int plane = id / LL, ab = id % LL;
+    for (int id = threadIdx.x; id < nk * 3 * LL; id += blockDim.x) {
+        const int kk = id / (3 * LL), pid = id - kk * (3 * LL);
+        const uint64_t *w0 = sm.w + (size_t)(2 * (k0 + kk)) * N;
+        const uint64_t *w1 = w0 + N;
+        uint64_t *margk = sm.marg + (size_t)kk * 3 * LL * kDG;
+        const int plane = pid / LL, ab = pid % LL;
         const int A = ab % L, Bc = ab / L;  // consecutive lanes: consecutive A
         int base, step;
         if (plane == 0) {        // (x=A, y=Bc), over z
@@ -345,17 +355,19 @@ __device__ __forceinline__ void msc_measure(const MscSmem &sm, const MscArgs &a,
         uint64_t cnt[kDG];
         count16(qs, cnt);
 #pragma unroll
-        for (int p = 0; p < kDG; ++p) sm.marg[((size_t)plane * LL + A * L + Bc) * kDG + p] = cnt[p];
+        for (int p = 0; p < kDG; ++p) margk[((size_t)plane * LL + A * L + Bc) * kDG + p] = cnt[p];
     }
     __syncthreads();
     // (B) projection counts: sum of L marginal entries per (v, d)
-    for (int id = threadIdx.x; id < 9 * L; id += blockDim.x) {
-        const int v = id / L, d = id % L;
+    for (int id = threadIdx.x; id < nk * 9 * L; id += blockDim.x) {
+        const int kk = id / (9 * L), pid = id - kk * (9 * L);
+        const uint64_t *margk = sm.marg + (size_t)kk * 3 * LL * kDG;
+        const int v = pid / L, d = pid % L;
         const int plane = (v == 0 || v == 1 || v == 3 || v == 4) ? 0 : (v == 2 || v == 5 || v == 6) ? 1 : 2;
         uint64_t acc[kDP];
 #pragma unroll
         for (int p = 0; p < kDP; ++p) acc[p] = 0;
-        for (int aa = 0; aa < L; ++aa) {
+        auto add_entry = [&](int aa) {
             int A, Bc;
             if (v == 0) {
                 A = d; Bc = aa;
@@ -366,12 +378,18 @@ __device__ __forceinline__ void msc_measure(const MscSmem &sm, const MscArgs &a,
             } else {
                 A = aa; Bc = (aa - d + L) % L;
             }
-            const uint64_t *m = sm.marg + ((size_t)plane * LL + A * L + Bc) * kDG;
+            const uint64_t *m = margk + ((size_t)plane * LL + A * L + Bc) * kDG;
             const uint64_t x[kDG] = {m[0], m[1], m[2], m[3], m[4]};
             bs_add<kDP, kDG>(acc, x);
+        };
+        if constexpr (WIDE) {
+#pragma unroll
+            for (int aa = 0; aa < L; ++aa) add_entry(aa);
+        } else {
+            for (int aa = 0; aa < L; ++aa) add_entry(aa);
         }
 #pragma unroll
-        for (int p = 0; p < kDP; ++p) sm.proj[(size_t)id * kDP + p] = acc[p];
+        for (int p = 0; p < kDP; ++p) sm.proj[(size_t)id * kDP + p] = acc[p];  // [kk][v][d]
     }
     __syncthreads();
     // (C) one warp per (wave vector v, half of the word): lanes 0..8 load the
@@ -381,8 +399,9 @@ __device__ __forceinline__ void msc_measure(const MscSmem &sm, const MscArgs &a,
     // E and M are added straight from the per-sample energies.
     {
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-        for (int task = warp; task < 2 * 9; task += nwarps) {
-            const int v = task >> 1, half = task & 1;
+        for (int task = warp; task < nk * 2 * 9; task += nwarps) {
+            const int kk = task / 18, v = (task % 18) >> 1, half = task & 1;
+            const int k = k0 + kk, t = t0 + kk;
             const int b = 32 * half + lane;  // sample 64 g + b
             // device layout [G][nt][bins][40][64]: entry k of this sample at
             // ac[64 k], so the 32 lanes of a warp touch 256 contiguous bytes
@@ -396,14 +415,20 @@ __device__ __forceinline__ void msc_measure(const MscSmem &sm, const MscArgs &a,
             }
             float re = 0.0f, im = 0.0f;
             int Qi = 0;
-            for (int d = 0; d < L; ++d) {
-                const uint64_t *p = sm.proj + ((size_t)v * L + d) * kDP;
+            auto add_phase = [&](int d) {
+                const uint64_t *p = sm.proj + (((size_t)kk * 9 + v) * L + d) * kDP;
                 const uint32_t row = lane < kDP ? (uint32_t)(p[lane] >> (32 * half)) : 0u;
                 const int cnt = (int)(warp_transpose32(row) & ((1u << kDP) - 1));
                 const int P = LL - 2 * cnt;
                 Qi += P;
                 re = __fmaf_rn((float)P, a.twid[d], re);
                 im = __fmaf_rn((float)P, a.twid[L + d], im);
+            };
+            if constexpr (WIDE) {
+#pragma unroll
+                for (int d = 0; d < L; ++d) add_phase(d);
+            } else {
+                for (int d = 0; d < L; ++d) add_phase(d);
             }
             const double dr = (double)re, di = (double)im;
             acv[0] = __dadd_rn(o0, dr);
@@ -449,8 +474,9 @@ __global__ void __launch_bounds__(MAXT, MINB) msc_sweep_kernel(const MscArgs a)
 {
     constexpr int N = L * L * L;
     extern __shared__ __align__(16) uint8_t msc_smem[];
+    constexpr bool WIDE = MAXT == kMscThreads;
     MscSmem sm;
-    msc_carve(msc_smem, L, &sm);
+    msc_carve(msc_smem, L, &sm, WIDE ? 2 : 1);
     const int g = blockIdx.y;
     const int64_t n = (a.sweep0_dev ? *a.sweep0_dev : a.sweep0) + a.sweep_offset;
     const bool xchg = a.exchange_every > 0 && (n + 1) % a.exchange_every == 0;
@@ -528,8 +554,12 @@ __global__ void __launch_bounds__(MAXT, MINB) msc_sweep_kernel(const MscArgs a)
         }
         __syncthreads();
     }
-    if (meas)
-        for (int k = 0; k < cnt; ++k) msc_measure<L>(sm, a, g, k, t0 + k, log_bin(n, a.n_bins));
+    if (meas) {
+        if constexpr (WIDE)
+            msc_measure<L, true>(sm, a, g, 0, cnt, t0, log_bin(n, a.n_bins));
+        else
+            for (int k = 0; k < cnt; ++k) msc_measure<L, false>(sm, a, g, k, 1, t0 + k, log_bin(n, a.n_bins));
+    }
 
     uint64_t *dst = a.W + ((size_t)g * a.nt + t0) * 2 * N;
     for (int k = threadIdx.x; k < nq * N; k += blockDim.x) dst[k] = sm.w[k];
@@ -812,7 +842,7 @@ cudaError_t msc_launch_t(const MscArgs &a, int threads, cudaStream_t st)
         msc_sweep_kernel<L, kMscThreads, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMscMaxSmem);
     if (attr_n != cudaSuccess) return attr_n;
     if (attr_w != cudaSuccess) return attr_w;
-    const size_t smem = msc_carve(nullptr, L, nullptr);
+    const size_t smem = msc_carve(nullptr, L, nullptr, threads == kMscNarrow ? 1 : 2);
     dim3 grid((unsigned)(a.nt / 2 + 1), (unsigned)a.G);
     if (threads == kMscNarrow)
         msc_sweep_kernel<L, kMscNarrow, 6><<<grid, threads, smem, st>>>(a);
@@ -827,7 +857,7 @@ cudaError_t msc_launch_t(const MscArgs &a, int threads, cudaStream_t st)
 
 size_t msc_smem_bytes(int L)
 {
-    const size_t b = msc_carve(nullptr, L, nullptr);
+    const size_t b = msc_carve(nullptr, L, nullptr, 2);  // the wide instance's (the larger)
     return b <= (size_t)kMscMaxSmem ? b : 0;
 }
 
