@@ -131,6 +131,17 @@ struct MscSmem {
 
 __host__ __device__ inline size_t a16(size_t x) { return (x + 15) & ~(size_t)15; }
 
+// Whether the projections of a two-slot measurement live in the chains'
+// space: the wide instance writes its chains back to global memory once the
+// marginals are counted, so the projection phase can reuse that space. This
+// keeps the L = 16 instance at 197 KB of shared memory, inside the 196 KB
+// carveout that leaves L1 room for the couplings it reads through the
+// cache (at 217 KB the sweeps ran 5 % slower).
+__host__ __device__ constexpr bool msc_proj_in_w(int L, int ms)
+{
+    return ms == 2 && (size_t)2 * 9 * L * kDP <= (size_t)4 * L * L * L;
+}
+
 // ms: slots whose overlap is measured in one pass (1, or 2 for the wide
 // instance, which measures both slots of its unit together).
 __host__ __device__ inline size_t msc_carve(uint8_t *base, int L, MscSmem *sm, int ms)
@@ -151,7 +162,8 @@ __host__ __device__ inline size_t msc_carve(uint8_t *base, int L, MscSmem *sm, i
     s.M = reinterpret_cast<long long *>(take(4 * 64 * 8));
     s.swap = reinterpret_cast<uint64_t *>(take(2 * 8));
     s.marg = reinterpret_cast<uint64_t *>(take((size_t)ms * 3 * L * L * kDG * 8));
-    s.proj = reinterpret_cast<uint64_t *>(take((size_t)ms * 9 * L * kDP * 8));
+    s.proj = msc_proj_in_w(L, ms) ? s.w
+                                  : reinterpret_cast<uint64_t *>(take((size_t)ms * 9 * L * kDP * 8));
     if (sm) *sm = s;
     return off;
 }
@@ -312,7 +324,7 @@ __device__ __forceinline__ void msc_half(const MscSmem &sm, const MscArgs &a, in
 // ---------------------------------------------------------------------------
 template <int L, bool WIDE>
 __device__ __forceinline__ void msc_measure(const MscSmem &sm, const MscArgs &a, int g, int k0,
-                                            int nk, int t0, int bin)
+                                            int nk, int t0, int bin, uint64_t *w_dst, int nw)
 {
     constexpr int N = L * L * L;
     constexpr int LL = L * L;
@@ -358,6 +370,11 @@ __device__ __forceinline__ void msc_measure(const MscSmem &sm, const MscArgs &a,
         for (int p = 0; p < kDG; ++p) margk[((size_t)plane * LL + A * L + Bc) * kDG + p] = cnt[p];
     }
     __syncthreads();
+    if constexpr (msc_proj_in_w(L, WIDE ? 2 : 1)) {
+        // the chains are final: store them now, their space takes the projections
+        for (int k = threadIdx.x; k < nw; k += blockDim.x) w_dst[k] = sm.w[k];
+        __syncthreads();
+    }
     // (B) projection counts: sum of L marginal entries per (v, d)
     for (int id = threadIdx.x; id < nk * 9 * L; id += blockDim.x) {
         const int kk = id / (9 * L), pid = id - kk * (9 * L);
@@ -554,15 +571,18 @@ __global__ void __launch_bounds__(MAXT, MINB) msc_sweep_kernel(const MscArgs a)
         }
         __syncthreads();
     }
+    uint64_t *dst = a.W + ((size_t)g * a.nt + t0) * 2 * N;
     if (meas) {
         if constexpr (WIDE)
-            msc_measure<L, true>(sm, a, g, 0, cnt, t0, log_bin(n, a.n_bins));
+            msc_measure<L, true>(sm, a, g, 0, cnt, t0, log_bin(n, a.n_bins), dst, nq * N);
         else
-            for (int k = 0; k < cnt; ++k) msc_measure<L, false>(sm, a, g, k, 1, t0 + k, log_bin(n, a.n_bins));
+            for (int k = 0; k < cnt; ++k)
+                msc_measure<L, false>(sm, a, g, k, 1, t0 + k, log_bin(n, a.n_bins), dst, nq * N);
     }
-
-    uint64_t *dst = a.W + ((size_t)g * a.nt + t0) * 2 * N;
-    for (int k = threadIdx.x; k < nq * N; k += blockDim.x) dst[k] = sm.w[k];
+    // (a measuring wide instance whose projections reuse the chains' space
+    // has stored the chains already)
+    if (!(meas && msc_proj_in_w(L, WIDE ? 2 : 1)))
+        for (int k = threadIdx.x; k < nq * N; k += blockDim.x) dst[k] = sm.w[k];
     for (int k = threadIdx.x; k < nq * 64; k += blockDim.x) {
         const int qq = k / 64, b = k % 64;
         const int64_t s = 64 * (int64_t)g + b;
