@@ -112,3 +112,31 @@ def test_t32_threshold_properties():
         prev = v
         ref = math.exp(float(np.float32(x))) * 2.0 ** 32
         assert abs(v - ref) <= max(2.0, ref * 5e-7)
+
+
+def test_screen_guard_band_absorbs_the_approximation_errors():
+    """The Gaussian sweep screens r <= T32(x) by the sign of fl(r) - A, with
+    A ~ e^x 2^32 from a fast 2^x, deciding only outside |fl(r) - A| <= 2^-12 A
+    (the device test checks the hardware). Here A is e^x 2^32 moved by a
+    relative error of +-2^-16, four times the bound the design states, and
+    every decision the screen would take outside the band must equal the
+    oracle's r <= T32(x) at and around each threshold and on random draws."""
+    rng = np.random.default_rng(5)
+    xs = np.concatenate([np.linspace(-64.0, 0.0, 4001, dtype=np.float32),
+                         -(rng.random(2000) * 23).astype(np.float32)])
+    band = 2.0 ** -12
+    decided = 0
+    for x in xs:
+        thr = orc.t32(float(x)) if x < 0 else 0xFFFFFFFF
+        exact = math.exp(float(x)) * 2.0 ** 32
+        rs = {thr, max(thr - 1, 0), min(thr + 1, 2 ** 32 - 1), min(thr + 2, 2 ** 32 - 1),
+              int(rng.integers(0, 2 ** 32)), 0, 2 ** 32 - 1}
+        for eps in (-2.0 ** -16, 2.0 ** -16):
+            a = float(np.float32(exact * (1.0 + eps)))
+            for r in rs:
+                fr = float(np.float32(r))
+                u = float(np.float32(fr - a))
+                if abs(u) > band * a:
+                    decided += 1
+                    assert (u < 0) == (r <= thr), (float(x), r, thr, eps)
+    assert decided > 0.5 * len(xs) * 2 * 5
