@@ -80,7 +80,7 @@ def test_plain_pmj_config_is_bit_exact():
     (6, 6, "pmj", 1, 1, 2), (6, 4, "gauss", 3, 1, 1), (8, 7, "pmj", 2, 3, 1),
     (8, 9, "gauss", 1, 1, 1), (10, 6, "gauss", 1, 1, 1), (10, 4, "pmj", 0, 1, 1),
     (12, 5, "pmj", 1, 1, 4), (12, 8, "gauss", 1, 1, 1), (14, 4, "pmj", 1, 1, 1),
-    (16, 4, "gauss", 1, 2, 1), (4, 1, "pmj", 1, 1, 1),
+    (16, 4, "gauss", 1, 2, 1), (4, 1, "pmj", 1, 1, 1), (14, 5, "gauss", 1, 1, 1),
     # state kept in global memory: large L, or too many slots for shared memory
     (18, 3, "pmj", 1, 1, 1), (20, 2, "gauss", 1, 1, 1), (22, 2, "pmj", 1, 1, 1),
     (24, 2, "gauss", 1, 1, 1), (12, 64, "gauss", 1, 1, 1)])

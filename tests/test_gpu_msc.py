@@ -42,7 +42,10 @@ def assert_same(ens, st, samples=None):
 @pytest.mark.parametrize("L,nt,h,ee,me,S", [
     (2, 3, 0.3, 1, 1, 64), (4, 4, 0.3, 1, 1, 64), (4, 5, 0.0, 2, 3, 128),
     (6, 1, 0.5, 1, 1, 64), (6, 6, 0.1, 1, 2, 64), (8, 4, 0.2, 0, 1, 64),
-    (10, 3, 0.7, 1, 1, 64), (12, 2, 0.3, 1, 1, 64), (16, 2, 0.05, 1, 1, 64)])
+    (10, 3, 0.7, 1, 1, 64), (12, 2, 0.3, 1, 1, 64), (16, 2, 0.05, 1, 1, 64),
+    # wide instance, both slots of a unit measured in one pass: several units,
+    # single-slot edge units and two word groups
+    (14, 3, 0.2, 1, 1, 64), (16, 5, 0.15, 1, 1, 128)])
 def test_msc_is_bit_exact_against_int8_oracle_with_rng_group_64(L, nt, h, ee, me, S):
     T = inputs.geometric_ladder(0.4, 1.5, nt)
     J, s0 = inputs.make_instance("pmj", L, S, nt, seed=100 + L + nt)
