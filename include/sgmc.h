@@ -130,6 +130,16 @@ typedef struct {
                                   (SG_EUNSUPPORTED if it does not fit), 2 =
                                   global memory (L >= 10). Results do not
                                   depend on it.                              */
+    int32_t segments;          /* INT8 state in shared memory: each launch's
+                                  sweeps are split into this many segments per
+                                  sample, and the CTAs claim (segment, sample)
+                                  units in order, a segment starting once the
+                                  sample's previous one is stored, so samples
+                                  beyond one wave of CTAs do not leave SMs idle
+                                  at the end of a launch. 0 = library choice
+                                  (split when there are more samples than
+                                  resident CTAs), 1 = one CTA runs all of a
+                                  sample's sweeps. Results do not depend on it. */
 } sg_options;
 
 /* Fill *opt with the defaults: INT8 layout, rng_group 1, exchange and

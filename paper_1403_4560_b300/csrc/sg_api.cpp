@@ -91,6 +91,7 @@ struct sg_ensemble {
     float *negbeta = nullptr, *dbeta = nullptr, *twid = nullptr;
     int *status = nullptr;
     int64_t *sweep_ctr = nullptr;
+    unsigned int *work = nullptr;  // int8: segmented-launch counters [1 + S]
     int64_t sweeps_done = 0;
     int64_t exchanges_done = 0;
     std::vector<double> T;
@@ -163,7 +164,9 @@ ArenaPlan plan_arena(int L, int nt, int Tp, int64_t S, bool gauss, bool msc, int
     p.thr = align256((size_t)Tp * 16 * sizeof(uint32_t));
     p.tab = align256((size_t)Tp * sizeof(float));
     p.twid = align256((size_t)2 * L * sizeof(float));
-    p.misc = 256 + (msc ? align256((size_t)(S / 64) * 2 * nt * 8) : 0);
+    // int8: the segmented launch's unit counter and per-sample progress
+    p.misc = 256 + (msc ? align256((size_t)(S / 64) * 2 * nt * 8)
+                        : align256((size_t)(1 + S) * sizeof(unsigned int)));
     p.total = p.spins + p.unpacked + p.J + 2 * p.BM + p.acc + p.hist + p.thr + 2 * p.tab + p.twid +
               p.misc;
     return p;
@@ -317,6 +320,8 @@ Int8Args make_args(sg_ensemble *e)
     a.s_begin = 0;
     a.s_end = e->S;
     a.s_key0 = e->opt.sample_base;
+    a.work = e->work;
+    a.n_seg = 1;
     return a;
 }
 
@@ -445,6 +450,7 @@ sg_status validate(int L, const double *T, int nt, sg_coupling dist, int64_t S,
         return fail(SG_EINVAL, "sample_base + n_samples must be in [0, 2^32]");
     if (o.log_bins < 0 || o.log_bins > 64) return fail(SG_EINVAL, "log_bins must be in [0, 64]");
     if (o.state_mode < 0 || o.state_mode > 2) return fail(SG_EINVAL, "state_mode must be 0, 1 or 2");
+    if (o.segments < 0) return fail(SG_EINVAL, "segments must be >= 0");
     if (o.layout == SG_LAYOUT_MSC64) {
         if (dist != SG_PM_J) return fail(SG_EINVAL, "the MSC64 layout needs +-J couplings");
         if (o.sample_base % 64) return fail(SG_EINVAL, "the MSC64 layout needs sample_base % 64 == 0");
@@ -592,6 +598,7 @@ sg_status sg_create_ensemble(int L, double h, const double *T, int nt, sg_coupli
     e->status = (int *)(base + off);
     e->sweep_ctr = (int64_t *)(base + off + 64);
     if (e->msc) e->masks = (uint64_t *)(base + off + 256);
+    else e->work = (unsigned int *)(base + off + 256);
 
     ce = cudaStreamCreateWithFlags(&e->branch, cudaStreamNonBlocking);
     if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaStreamCreate"));
@@ -682,6 +689,32 @@ void sg_destroy(sg_ensemble *e)
     delete e;
 }
 
+// Segments per sample of an int8 launch of n_sweeps sweeps. Splitting pays
+// only when the samples outnumber the resident CTAs (else every sample has a
+// CTA to itself) and only for the shared-memory state (the global-memory
+// instances read the state through L1, which is not coherent across SMs).
+// The library's choice aims at >= 8 units per CTA with segments of 16-64
+// sweeps; the cost is one more load and store of the sample's state per
+// segment.
+static int int8_segments(const sg_ensemble *e, int n_sweeps)
+{
+    if (e->launch.gst || n_sweeps < 2) return 1;
+    int64_t want;
+    if (e->opt.segments > 0) {
+        want = e->opt.segments;
+    } else {
+        if (e->S <= e->launch.grid || n_sweeps < 32) return 1;
+        const int64_t by_balance = (8 * (int64_t)e->launch.grid + e->S - 1) / e->S;
+        const int64_t by_length = (n_sweeps + 63) / 64;
+        want = std::max(by_balance, by_length);
+        want = std::min<int64_t>(want, std::max(1, n_sweeps / 16));
+    }
+    want = std::min<int64_t>(want, n_sweeps);
+    // (segment, sample) units are counted in 32 bits
+    while (want > 1 && want * e->S >= (int64_t)1 << 31) --want;
+    return (int)std::max<int64_t>(want, 1);
+}
+
 static sg_status launch_sweeps(sg_ensemble *e, int64_t n, cudaStream_t s, bool device_counter)
 {
     if (e->msc) {
@@ -704,6 +737,10 @@ static sg_status launch_sweeps(sg_ensemble *e, int64_t n, cudaStream_t s, bool d
         a.n_sweeps = (int)std::min<int64_t>(chunk, n - done);
         a.sweep0 = e->sweeps_done + done;
         if (device_counter) a.sweep0_dev = e->sweep_ctr;
+        a.n_seg = int8_segments(e, a.n_sweeps);
+        if (a.n_seg > 1)
+            SG_CUDA(cudaMemsetAsync(e->work, 0, (size_t)(1 + e->S) * sizeof(unsigned int), s),
+                    "segment counters");
         SG_CUDA(int8_launch(e->L, e->gauss, a, e->launch, s), "sweep kernel launch");
         if (device_counter) SG_CUDA(advance_counter(e->sweep_ctr, a.n_sweeps, s), "counter");
     }

@@ -134,6 +134,7 @@ struct Smem {
     int *anyswap;               // [2]
     unsigned long long *accm;   // [2] accepted pairs per replica (bit p: pair p, p+1)
     uint32_t *marg;             // [3][L*L][mchunk] byte counts of q = -1
+    int *ctl;                   // [2] the CTA's current unit and a wait-failure flag
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -166,6 +167,7 @@ __host__ __device__ inline size_t carve(uint8_t *base, int L, int Tp, bool gauss
     s.anyswap = reinterpret_cast<int *>(take(2 * 4));
     s.accm = reinterpret_cast<unsigned long long *>(take(2 * 8));
     s.marg = reinterpret_cast<uint32_t *>(take((size_t)3 * L * L * mchunk * 4));
+    s.ctl = reinterpret_cast<int *>(take(2 * 4));
     if (sm) *sm = s;
     return off;
 }
@@ -733,12 +735,22 @@ __device__ __forceinline__ void count_phases(const uint32_t *pm, int nw, int par
 // together with Q; E and M per slot before both. Processed mchunk 4-slot
 // groups at a time.
 // ---------------------------------------------------------------------------
+// Per-sample state that another CTA may have written in the same launch (a
+// segmented launch hands a sample's segments to whichever CTA is free) is
+// read from L2: L1 is not coherent across SMs, and a CTA that ran an earlier
+// segment of the sample could still hold its lines.
+__device__ __forceinline__ double ld_acc(const double *p, bool seg)
+{
+    return seg ? __ldcg(p) : *p;
+}
+
 template <int L, bool PACK>
 __device__ __forceinline__ void measure_step(const Smem &sm, const Ctx &cx, const Int8Args &a,
                                              int bin)
 {
     constexpr int LL = L * L;
     const int WR = cx.WR, RB = cx.RB, Tp = cx.Tp, nt = cx.nt;
+    const bool seg = a.n_seg > 1;  // the accumulators may come from another SM
     // device layout [S][bins][40][nt]: entry k of slot t at accs[k * nt + t],
     // so lanes over consecutive slots touch consecutive doubles
     double *accs = a.acc + ((size_t)cx.s * a.n_bins + bin) * SG_NACC * nt;
@@ -746,7 +758,8 @@ __device__ __forceinline__ void measure_step(const Smem &sm, const Ctx &cx, cons
     // projection phase reads nothing the next sweep overwrites
     for (int t = threadIdx.x; t < nt; t += blockDim.x) {
         double *ac = accs + t;  // entry k at ac[k * nt]
-        double o5 = ac[5 * nt], o6 = ac[6 * nt], o7 = ac[7 * nt], o8 = ac[8 * nt];
+        double o5 = ld_acc(ac + 5 * nt, seg), o6 = ld_acc(ac + 6 * nt, seg);
+        double o7 = ld_acc(ac + 7 * nt, seg), o8 = ld_acc(ac + 8 * nt, seg);
         for (int r = 0; r < 2; ++r) {
             const long long Bv = (long long)sm.B[r * Tp + t];
             const long long Mv = (long long)sm.M[r * Tp + t];
@@ -826,7 +839,7 @@ __device__ __forceinline__ void measure_step(const Smem &sm, const Ctx &cx, cons
                     double old[3] = {0.0, 0.0, 0.0};
                     if (live) {
 #pragma unroll
-                        for (int q = 0; q < 3; ++q) old[q] = acv[q * nt];
+                        for (int q = 0; q < 3; ++q) old[q] = ld_acc(acv + q * nt, seg);
                     }
                     uint32_t lo[ND], hi[ND];
                     const uint32_t *pm0 = sm.marg + jc;
@@ -879,7 +892,7 @@ __device__ __forceinline__ void measure_step(const Smem &sm, const Ctx &cx, cons
                                       1ull);
                         double oq[5];
 #pragma unroll
-                        for (int q = 0; q < 5; ++q) oq[q] = acq[q * nt];
+                        for (int q = 0; q < 5; ++q) oq[q] = ld_acc(acq + q * nt, seg);
                         const double Q = (double)Qi;
                         const double Q2 = __dmul_rn(Q, Q);
                         oq[0] = __dadd_rn(oq[0], 1.0);
@@ -906,6 +919,20 @@ __device__ __forceinline__ void copy16(void *dst, const void *src, size_t bytes)
     const int4 *s = reinterpret_cast<const int4 *>(src);
     for (size_t k = threadIdx.x; k < bytes / 16; k += blockDim.x) d[k] = s[k];
 }
+
+// The same from global memory through L2 only (state another SM may have
+// stored in this launch).
+__device__ __forceinline__ void copy16_cg(void *dst, const void *src, size_t bytes)
+{
+    int4 *d = reinterpret_cast<int4 *>(dst);
+    const int4 *s = reinterpret_cast<const int4 *>(src);
+    for (size_t k = threadIdx.x; k < bytes / 16; k += blockDim.x) d[k] = __ldcg(s + k);
+}
+
+// Longest wait for a sample's previous segment (clock64 cycles) when no
+// watchdog budget is set: far beyond any segment the library chooses (at
+// most 64 sweeps), after which the launch stops with SG_ETIMEOUT.
+constexpr unsigned long long kSegWaitCycles = 1ull << 36;
 
 // ---------------------------------------------------------------------------
 // The fused kernel: for each sample of this CTA, load, run n_sweeps sweeps
@@ -940,7 +967,50 @@ __global__ void __launch_bounds__(KernelBounds<L, GST, WIDE>::threads,
     if (!GAUSS)
         for (int k = threadIdx.x; k < a.Tp * 16; k += blockDim.x) sm.thr[k] = a.thr[k];
 
-    for (int64_t s = a.s_begin + blockIdx.x; s < a.s_end; s += gridDim.x) {
+    // units (segment, sample), segment-major: a plain launch (n_seg = 1) takes
+    // samples blockIdx.x, + gridDim.x, ...; a segmented one claims units from
+    // a counter, and a segment starts once the sample's previous one is
+    // stored, so a sample's sweeps still run in order, one CTA at a time
+    // (the host keeps n_seg * samples below 2^31)
+    const int nS = (int)(a.s_end - a.s_begin);
+    const bool segd = a.n_seg > 1;
+    int &unit_sh = sm.ctl[0], &wait_fail = sm.ctl[1];
+    if (threadIdx.x == 0) unit_sh = blockIdx.x;
+    for (;;) {
+        __syncthreads();  // every thread has read the previous unit
+        if (threadIdx.x == 0 && segd) unit_sh = (int)atomicAdd(a.work, 1u);
+        __syncthreads();
+        const int unit = unit_sh;
+        if (unit >= nS * a.n_seg) break;
+        const int segk = unit / nS;
+        const int64_t s = a.s_begin + (unit - segk * nS);
+        const int seg_len = (a.n_sweeps + a.n_seg - 1) / a.n_seg;
+        const int it_begin = segk * seg_len;
+        const int n_it = min(seg_len, a.n_sweeps - it_begin);
+        if (segk > 0) {
+            if (threadIdx.x == 0) {
+                int fail = 0;
+                const volatile unsigned int *done = a.work + 1 + (s - a.s_begin);
+                const unsigned long long limit = a.watchdog ? a.watchdog : kSegWaitCycles;
+                const long long w0 = clock64();
+                while (*done < (unsigned int)segk) {
+                    if (*(const volatile int *)a.status != 0) {  // stopped elsewhere
+                        fail = 1;
+                        break;
+                    }
+                    if ((unsigned long long)(clock64() - w0) > limit) {
+                        atomicCAS(a.status, 0, (int)SG_ETIMEOUT);
+                        fail = 1;
+                        break;
+                    }
+                    __nanosleep(256);
+                }
+                __threadfence();
+                wait_fail = fail;
+            }
+            __syncthreads();
+            if (wait_fail) break;
+        }
         cx.s = s;
         cx.k0 = a.seed_lo ^ kTagMet;
         cx.k1 = (uint32_t)((s + a.s_key0) / a.rng_group);
@@ -953,7 +1023,10 @@ __global__ void __launch_bounds__(KernelBounds<L, GST, WIDE>::threads,
             else
                 sm.Jg = const_cast<float *>(a.Jg) + (size_t)s * 3 * N;
         } else {
-            copy16(sm.spins, a.spins + (size_t)s * N * cx.RB, (size_t)N * cx.RB);
+            if (segd)
+                copy16_cg(sm.spins, a.spins + (size_t)s * N * cx.RB, (size_t)N * cx.RB);
+            else
+                copy16(sm.spins, a.spins + (size_t)s * N * cx.RB, (size_t)N * cx.RB);
             if (!GAUSS)
                 copy16(sm.J8, a.J8 + (size_t)s * N * 8, (size_t)N * 8);
             else
@@ -961,15 +1034,16 @@ __global__ void __launch_bounds__(KernelBounds<L, GST, WIDE>::threads,
         }
         for (int k = threadIdx.x; k < 2 * a.Tp; k += blockDim.x) {
             sm.xflag[k] = 0;
-            sm.B[k] = (unsigned long long)a.B[s * 2 * a.Tp + k];
-            sm.M[k] = (unsigned long long)a.M[s * 2 * a.Tp + k];
+            const int64_t *pb = a.B + s * 2 * a.Tp + k, *pm = a.M + s * 2 * a.Tp + k;
+            sm.B[k] = (unsigned long long)(segd ? __ldcg((const long long *)pb) : *pb);
+            sm.M[k] = (unsigned long long)(segd ? __ldcg((const long long *)pm) : *pm);
         }
         __syncthreads();
 
         uint32_t stamp = 0;
         bool stop = false;
-        const int64_t sweep0 = a.sweep0_dev ? *a.sweep0_dev : a.sweep0;
-        for (int it = 0; it < a.n_sweeps; ++it) {
+        const int64_t sweep0 = (a.sweep0_dev ? *a.sweep0_dev : a.sweep0) + it_begin;
+        for (int it = 0; it < n_it; ++it) {
             const int64_t n = sweep0 + it;
             if (a.watchdog || a.cancel) {  // launch-uniform branch
                 int why = 0;
@@ -1024,6 +1098,13 @@ __global__ void __launch_bounds__(KernelBounds<L, GST, WIDE>::threads,
         }
         // a stopped launch leaves later samples untouched; the status word tells
         if (__syncthreads_or(stop)) break;
+        if (segd) {  // publish the stored segment (the barrier above ordered the stores)
+            __threadfence();
+            __syncthreads();
+            if (threadIdx.x == 0) atomicAdd(a.work + 1 + (s - a.s_begin), 1u);
+        } else if (threadIdx.x == 0) {
+            unit_sh += gridDim.x;
+        }
     }
 }
 

@@ -42,6 +42,12 @@ struct Int8Args {
     const volatile int *cancel;  // optional host-mapped cancel flag
     int64_t s_begin, s_end;      // samples handled by this launch
     int64_t s_key0;              // global index of local sample 0 (RNG keys)
+    // segmented launch (shared-memory state): n_seg segments of the launch's
+    // sweeps per sample; work[0] hands out (segment, sample) units in order,
+    // work[1 + s - s_begin] counts the segments of sample s already stored.
+    // Zeroed before every launch with n_seg > 1.
+    unsigned int *work;
+    int n_seg;
 };
 
 struct Int8Launch {

@@ -34,7 +34,8 @@ class Options(ctypes.Structure):
                 ("n_therm", ctypes.c_int64), ("threads_per_block", ctypes.c_int32),
                 ("sweeps_per_launch", ctypes.c_int32), ("watchdog_cycles", ctypes.c_uint64),
                 ("sample_base", ctypes.c_int64), ("log_bins", ctypes.c_int32),
-                ("pq_hist", ctypes.c_int32), ("state_mode", ctypes.c_int32)]
+                ("pq_hist", ctypes.c_int32), ("state_mode", ctypes.c_int32),
+                ("segments", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):

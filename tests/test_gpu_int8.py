@@ -206,6 +206,37 @@ def test_full_size_gaussian_workload_sampled_parity(L):
         assert_same(ens, st, samples=picks)
 
 
+@pytest.mark.parametrize("L,dist,S,nt", [(8, "gauss", 700, 8), (12, "pmj", 400, 8),
+                                         (6, "gauss", 90, 5)])
+def test_segmented_launches_match_one_cta_per_sample(L, dist, S, nt):
+    """Launches whose sweeps are split into segments that the CTAs claim one
+    by one (consecutive segments of a sample may run on different SMs, each
+    waiting for the previous one to be stored) give the chain of one CTA per
+    sample bit for bit: library choice (more samples than resident CTAs) and
+    a forced split; the oracle agrees on sampled samples."""
+    T = inputs.geometric_ladder(0.5, 1.6, nt)
+    J, s0 = inputs.make_instance(dist, L, S, nt, seed=50 + L)
+    opt = dict(n_therm=10, log_bins=3, pq_hist=1)
+    outs = []
+    for seg in (1, 0, 5):
+        with sgmc.Ensemble(L, 0.2, T, dist, S, 8, J=J, spins=s0, segments=seg, **opt) as ens:
+            ens.sweep(48)
+            ens.sweep(40)
+            ens.synchronize()
+            outs.append((ens.spins(), ens.energies()[0], ens.energies()[1], ens.accumulators(),
+                         ens.histogram()))
+    for out in outs[1:]:
+        for got, want in zip(out, outs[0]):
+            np.testing.assert_array_equal(got, want)
+    st = oracle_state(L, T, 0.2, dist, 8, J, s0, n_therm=10)
+    picks = [0, S // 2, S - 1]
+    for s in picks:
+        st.run(88, s_range=(s, s + 1))
+    np.testing.assert_array_equal(outs[0][0][picks], st.spins[picks])
+    with pytest.raises(sgmc.SgError):
+        sgmc.Ensemble(L, 0.2, T, dist, 4, 8, segments=-1)
+
+
 def test_library_gaussian_couplings_are_standard_normal_on_grid():
     from scipy import stats
     L, S = 8, 64
