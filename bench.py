@@ -48,11 +48,11 @@ WORKLOAD = ("gaussian EA 3D, L=8 and 12 x h=0.1,0.2,0.3, 512 samples each, "
 # workload (L = 12, 512 samples, 256 sweeps), from the one-pass ncu capture
 # summarised in profiles/dram_int8_run_kernel_L12_bench.md. Must be reset to
 # None whenever the kernel changes, until it is captured again.
-TRAFFIC_BYTES_PER_LAUNCH = None
+TRAFFIC_BYTES_PER_LAUNCH = 62.1e6
 # Thread instructions per attempt of the same kernel (ncu thread_inst_executed
 # over the launch's attempts; profiles/int8_run_kernel_L12_gauss.md). Reset to
 # None whenever the kernel changes.
-INSTR_PER_ATTEMPT = None
+INSTR_PER_ATTEMPT = 85.2
 # SM issue peak: 148 SMs x 4 schedulers x 1 warp instruction per cycle x 32
 # threads x 2.032 GHz (maximum SM clock), in thread instructions per second.
 ISSUE_PEAK = 148 * 4 * 32 * 2.032e9
