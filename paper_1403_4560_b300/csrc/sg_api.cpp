@@ -694,8 +694,9 @@ void sg_destroy(sg_ensemble *e)
 // CTA to itself) and only for the shared-memory state (the global-memory
 // instances read the state through L1, which is not coherent across SMs).
 // The library's choice aims at >= 8 units per CTA with segments of 16-64
-// sweeps; the cost is one more load and store of the sample's state per
-// segment.
+// sweeps, and splits only when the last wave of samples would leave more
+// than 3 % of the CTA slots idle; the cost is one more load and store of
+// the sample's state per segment.
 static int int8_segments(const sg_ensemble *e, int n_sweeps)
 {
     if (e->launch.gst || n_sweeps < 2) return 1;
@@ -704,6 +705,10 @@ static int int8_segments(const sg_ensemble *e, int n_sweeps)
         want = e->opt.segments;
     } else {
         if (e->S <= e->launch.grid || n_sweeps < 32) return 1;
+        // whole waves of samples (e.g. 1184 samples on 148 CTAs) leave no
+        // idle tail: splitting would only add state reloads
+        const int64_t waves = (e->S + e->launch.grid - 1) / e->launch.grid;
+        if ((double)e->S / ((double)waves * e->launch.grid) > 0.97) return 1;
         const int64_t by_balance = (8 * (int64_t)e->launch.grid + e->S - 1) / e->S;
         const int64_t by_length = (n_sweeps + 63) / 64;
         want = std::max(by_balance, by_length);
