@@ -137,9 +137,12 @@ typedef struct {
                                   sample's previous one is stored, so samples
                                   beyond one wave of CTAs do not leave SMs idle
                                   at the end of a launch. 0 = library choice
-                                  (split when there are more samples than
-                                  resident CTAs), 1 = one CTA runs all of a
-                                  sample's sweeps. Results do not depend on it. */
+                                  (split into segments of 16-64 sweeps when
+                                  the samples outnumber the resident CTAs and
+                                  the last wave would leave slots idle), 1 =
+                                  one CTA runs all of a sample's sweeps; the
+                                  global-memory state is never split. Results
+                                  do not depend on it.                       */
 } sg_options;
 
 /* Fill *opt with the defaults: INT8 layout, rng_group 1, exchange and
