@@ -132,7 +132,7 @@ struct MscSmem {
 __host__ __device__ inline size_t a16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 // Whether the projections of a two-slot measurement live in the chains'
-// space: the wide instance writes its chains back to global memory once the
+// space: the measuring CTA writes its chains back to global memory once the
 // marginals are counted, so the projection phase can reuse that space. This
 // keeps the L = 16 instance at 197 KB of shared memory, inside the 196 KB
 // carveout that leaves L1 room for the couplings it reads through the
@@ -142,8 +142,15 @@ __host__ __device__ constexpr bool msc_proj_in_w(int L, int ms)
     return ms == 2 && (size_t)2 * 9 * L * kDP <= (size_t)4 * L * L * L;
 }
 
-// ms: slots whose overlap is measured in one pass (1, or 2 for the wide
-// instance, which measures both slots of its unit together).
+// Slots whose overlap one measurement pass covers: both slots of the unit
+// for the wide instance, and for the narrow one at L <= 8, where the extra
+// shared memory leaves its CTAs per SM unchanged; one slot at a time else.
+__host__ __device__ constexpr int msc_measured_slots(int L, bool wide)
+{
+    return (wide || L <= 8) ? 2 : 1;
+}
+
+// ms: slots whose overlap is measured in one pass (msc_measured_slots).
 __host__ __device__ inline size_t msc_carve(uint8_t *base, int L, MscSmem *sm, int ms)
 {
     const bool jshared = msc_j_shared(L);
@@ -370,7 +377,7 @@ __device__ __forceinline__ void msc_measure(const MscSmem &sm, const MscArgs &a,
         for (int p = 0; p < kDG; ++p) margk[((size_t)plane * LL + A * L + Bc) * kDG + p] = cnt[p];
     }
     __syncthreads();
-    if constexpr (msc_proj_in_w(L, WIDE ? 2 : 1)) {
+    if constexpr (msc_proj_in_w(L, msc_measured_slots(L, WIDE))) {
         // the chains are final: store them now, their space takes the projections
         for (int k = threadIdx.x; k < nw; k += blockDim.x) w_dst[k] = sm.w[k];
         __syncthreads();
@@ -492,8 +499,9 @@ __global__ void __launch_bounds__(MAXT, MINB) msc_sweep_kernel(const MscArgs a)
     constexpr int N = L * L * L;
     extern __shared__ __align__(16) uint8_t msc_smem[];
     constexpr bool WIDE = MAXT == kMscThreads;
+    constexpr int MS = msc_measured_slots(L, WIDE);
     MscSmem sm;
-    msc_carve(msc_smem, L, &sm, WIDE ? 2 : 1);
+    msc_carve(msc_smem, L, &sm, MS);
     const int g = blockIdx.y;
     const int64_t n = (a.sweep0_dev ? *a.sweep0_dev : a.sweep0) + a.sweep_offset;
     const bool xchg = a.exchange_every > 0 && (n + 1) % a.exchange_every == 0;
@@ -573,15 +581,15 @@ __global__ void __launch_bounds__(MAXT, MINB) msc_sweep_kernel(const MscArgs a)
     }
     uint64_t *dst = a.W + ((size_t)g * a.nt + t0) * 2 * N;
     if (meas) {
-        if constexpr (WIDE)
-            msc_measure<L, true>(sm, a, g, 0, cnt, t0, log_bin(n, a.n_bins), dst, nq * N);
+        if constexpr (MS == 2)
+            msc_measure<L, WIDE>(sm, a, g, 0, cnt, t0, log_bin(n, a.n_bins), dst, nq * N);
         else
             for (int k = 0; k < cnt; ++k)
-                msc_measure<L, false>(sm, a, g, k, 1, t0 + k, log_bin(n, a.n_bins), dst, nq * N);
+                msc_measure<L, WIDE>(sm, a, g, k, 1, t0 + k, log_bin(n, a.n_bins), dst, nq * N);
     }
-    // (a measuring wide instance whose projections reuse the chains' space
-    // has stored the chains already)
-    if (!(meas && msc_proj_in_w(L, WIDE ? 2 : 1)))
+    // (a measuring two-slot instance whose projections reuse the chains'
+    // space has stored the chains already)
+    if (!(meas && msc_proj_in_w(L, MS)))
         for (int k = threadIdx.x; k < nq * N; k += blockDim.x) dst[k] = sm.w[k];
     for (int k = threadIdx.x; k < nq * 64; k += blockDim.x) {
         const int qq = k / 64, b = k % 64;
@@ -862,7 +870,7 @@ cudaError_t msc_launch_t(const MscArgs &a, int threads, cudaStream_t st)
         msc_sweep_kernel<L, kMscThreads, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMscMaxSmem);
     if (attr_n != cudaSuccess) return attr_n;
     if (attr_w != cudaSuccess) return attr_w;
-    const size_t smem = msc_carve(nullptr, L, nullptr, threads == kMscNarrow ? 1 : 2);
+    const size_t smem = msc_carve(nullptr, L, nullptr, msc_measured_slots(L, threads != kMscNarrow));
     dim3 grid((unsigned)(a.nt / 2 + 1), (unsigned)a.G);
     if (threads == kMscNarrow)
         msc_sweep_kernel<L, kMscNarrow, 6><<<grid, threads, smem, st>>>(a);
