@@ -237,6 +237,33 @@ def test_segmented_launches_match_one_cta_per_sample(L, dist, S, nt):
         sgmc.Ensemble(L, 0.2, T, dist, 4, 8, segments=-1)
 
 
+def test_segmented_launches_in_a_replayed_graph_match_single_runs():
+    """Ensembles with more samples than resident CTAs, batched through one
+    CUDA graph (counters zeroed by captured memset nodes, the sweep index from
+    the device counter) and the graph replayed, equal single runs with one CTA
+    per sample bit for bit."""
+    specs = [(8, "gauss", 700, 8), (12, "pmj", 400, 8)]
+    T = inputs.geometric_ladder(0.5, 1.6, 8)
+    insts = [inputs.make_instance(d, L, S, nt, seed=70 + L) for L, d, S, nt in specs]
+    singles = []
+    for (L, d, S, nt), (J, s0) in zip(specs, insts):
+        with sgmc.Ensemble(L, 0.3, T, d, S, 6, J=J, spins=s0, n_therm=5, segments=1) as e:
+            e.sweep(96)
+            singles.append((e.spins(), e.accumulators()))
+    ens = [sgmc.Ensemble(L, 0.3, T, d, S, 6, J=J, spins=s0, n_therm=5)
+           for (L, d, S, nt), (J, s0) in zip(specs, insts)]
+    try:
+        sgmc.sweep_batch(ens, 48, use_graph=True)
+        sgmc.sweep_batch(ens, 48, use_graph=True)
+        for e, (sp, acc) in zip(ens, singles):
+            e.synchronize()
+            np.testing.assert_array_equal(e.spins(), sp)
+            np.testing.assert_array_equal(e.accumulators(), acc)
+    finally:
+        for e in ens:
+            e.close()
+
+
 def test_library_gaussian_couplings_are_standard_normal_on_grid():
     from scipy import stats
     L, S = 8, 64
