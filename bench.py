@@ -433,8 +433,8 @@ def main():
            "b_alg_bytes_per_attempt": b_alg, "peak_kind": peak_kind,
            "attempts_per_ns": dom_att / (dom_ms * 1e6)}
     # the binding resource: the kernel keeps the state on chip and is bound by
-    # instruction issue (ncu: ~70 % of issue slots, DRAM at ~11 % of the
-    # HBM-equivalent bytes), so the primary roofline is the issue rate
+    # instruction issue (ncu: ~74 % of issue slots; DRAM moves under 5 % of
+    # the HBM-equivalent bytes), so the primary roofline is the issue rate
     roofline = hbm
     if INSTR_PER_ATTEMPT:
         inst = INSTR_PER_ATTEMPT * dom_att / (dom_ms * 1e-3) / 1e12
