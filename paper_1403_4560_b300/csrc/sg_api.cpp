@@ -697,19 +697,34 @@ void sg_destroy(sg_ensemble *e)
 // sweeps, and splits only when the last wave of samples would leave more
 // than 3 % of the CTA slots idle; the cost is one more load and store of
 // the sample's state per segment.
-static int int8_segments(const sg_ensemble *e, int n_sweeps)
+static int int8_segments(const sg_ensemble *e, int n_sweeps, int *grid)
 {
+    *grid = e->launch.grid;
     if (e->launch.gst || n_sweeps < 2) return 1;
     int64_t want;
     if (e->opt.segments > 0) {
         want = e->opt.segments;
     } else {
-        if (e->S <= e->launch.grid || n_sweeps < 32) return 1;
-        // whole waves of samples (e.g. 1184 samples on 148 CTAs) leave no
-        // idle tail: splitting would only add state reloads
-        const int64_t waves = (e->S + e->launch.grid - 1) / e->launch.grid;
-        if ((double)e->S / ((double)waves * e->launch.grid) > 0.97) return 1;
-        const int64_t by_balance = (8 * (int64_t)e->launch.grid + e->S - 1) / e->S;
+        if (n_sweeps < 32) return 1;
+        if (e->S <= e->launch.grid) {
+            // one wave: S CTAs over the SMs leave some SMs one CTA more than
+            // others (512 samples: 68 SMs with 4, 80 with 3); k CTAs on every
+            // SM that share the samples' segments keep all SMs busy to the end
+            // (k >= 3: with fewer CTAs an SM issues too little to win back
+            // the extra samples; B300, Gaussian L = 8, 400 samples: 3/2 CTAs
+            // per SM 253, 2 per SM with segments 249 attempts/ns)
+            const int64_t k = e->S / e->num_sms;
+            if (k < 3 || e->S % e->num_sms == 0) return 1;
+            const double even = (double)e->S / ((double)(k + 1) * e->num_sms);
+            if (even > 0.97) return 1;
+            *grid = (int)(k * e->num_sms);
+        } else {
+            // whole waves of samples (e.g. 1184 samples on 148 CTAs) leave no
+            // idle tail: splitting would only add state reloads
+            const int64_t waves = (e->S + e->launch.grid - 1) / e->launch.grid;
+            if ((double)e->S / ((double)waves * e->launch.grid) > 0.97) return 1;
+        }
+        const int64_t by_balance = (8 * (int64_t)*grid + e->S - 1) / e->S;
         const int64_t by_length = (n_sweeps + 63) / 64;
         want = std::max(by_balance, by_length);
         want = std::min<int64_t>(want, std::max(1, n_sweeps / 16));
@@ -742,11 +757,12 @@ static sg_status launch_sweeps(sg_ensemble *e, int64_t n, cudaStream_t s, bool d
         a.n_sweeps = (int)std::min<int64_t>(chunk, n - done);
         a.sweep0 = e->sweeps_done + done;
         if (device_counter) a.sweep0_dev = e->sweep_ctr;
-        a.n_seg = int8_segments(e, a.n_sweeps);
+        Int8Launch cfg = e->launch;
+        a.n_seg = int8_segments(e, a.n_sweeps, &cfg.grid);
         if (a.n_seg > 1)
             SG_CUDA(cudaMemsetAsync(e->work, 0, (size_t)(1 + e->S) * sizeof(unsigned int), s),
                     "segment counters");
-        SG_CUDA(int8_launch(e->L, e->gauss, a, e->launch, s), "sweep kernel launch");
+        SG_CUDA(int8_launch(e->L, e->gauss, a, cfg, s), "sweep kernel launch");
         if (device_counter) SG_CUDA(advance_counter(e->sweep_ctr, a.n_sweeps, s), "counter");
     }
     return SG_OK;

@@ -207,13 +207,15 @@ def test_full_size_gaussian_workload_sampled_parity(L):
 
 
 @pytest.mark.parametrize("L,dist,S,nt", [(8, "gauss", 700, 8), (12, "pmj", 400, 8),
-                                         (6, "gauss", 90, 5)])
+                                         (6, "gauss", 90, 5), (8, "gauss", 520, 8)])
 def test_segmented_launches_match_one_cta_per_sample(L, dist, S, nt):
     """Launches whose sweeps are split into segments that the CTAs claim one
     by one (consecutive segments of a sample may run on different SMs, each
     waiting for the previous one to be stored) give the chain of one CTA per
-    sample bit for bit: library choice (more samples than resident CTAs) and
-    a forced split; the oracle agrees on sampled samples."""
+    sample bit for bit: library choice (more samples than resident CTAs, or
+    one wave that would load some SMs with one CTA more than others, here
+    520 samples as 3 CTAs on every SM) and a forced split; the oracle agrees
+    on sampled samples."""
     T = inputs.geometric_ladder(0.5, 1.6, nt)
     J, s0 = inputs.make_instance(dist, L, S, nt, seed=50 + L)
     opt = dict(n_therm=10, log_bins=3, pq_hist=1)
