@@ -19,6 +19,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 MODEL = "tests/test_oracle_model.py"
 RNG = "tests/test_oracle_rng_exp.py"
 BINS = "tests/test_oracle_bins_hist.py"
+CONV = "tests/test_oracle_conventions.py"
 
 # (name, original fragment, planted mistake, pins that must fail)
 MUTATIONS = [
@@ -57,6 +58,27 @@ MUTATIONS = [
      "double e = -((double)B[r * nt + t] * qJ + h * (double)M[r * nt + t]);",
      "double e = -((double)B[r * nt + t] * qJ - h * (double)M[r * nt + t]);",
      [MODEL + "::test_high_temperature_energy_follows_the_small_beta_expansion"]),
+    ("Metropolis counter without the colour field",
+     "((uint32_t)c << 24) | ((uint32_t)r << 16) | (uint32_t)t,",
+     "((uint32_t)r << 16) | (uint32_t)t,",
+     [CONV + "::test_metropolis_words_differ_between_colours_replicas_slots_and_sites"]),
+    ("Metropolis word taken from lane 0 for all four sites of a counter",
+     "shi, j & 3);", "shi, 0);",
+     [CONV + "::test_metropolis_words_differ_between_colours_replicas_slots_and_sites"]),
+    ("Metropolis counter without the replica field",
+     "((uint32_t)c << 24) | ((uint32_t)r << 16) | (uint32_t)t,",
+     "((uint32_t)c << 24) | (uint32_t)t,",
+     [CONV + "::test_metropolis_words_differ_between_colours_replicas_slots_and_sites"]),
+    ("exchange always offers the even pairs",
+     "exchange_step(&cp, s_base + s, (int)(e & 1), (uint32_t)n,",
+     "exchange_step(&cp, s_base + s, 0, (uint32_t)n,",
+     [CONV + "::test_exchange_pair_schedule_trace"]),
+    ("+-J couplings read lane 0 for every site of a counter",
+     "(uint32_t)d, 0u, shi, (i >> 5) & 3);", "(uint32_t)d, 0u, shi, 0);",
+     [CONV + "::test_pmj_couplings_are_balanced_and_independent"]),
+    ("initial spins drawn without the replica field",
+     "((uint32_t)r << 16) | (uint32_t)t, 0u, shi,", "(uint32_t)t, 0u, shi,",
+     [CONV + "::test_initial_spins_are_balanced_and_independent"]),
     ("histogram counts disagreeing sites",
      "agree += s0[i] == s1[i];", "agree += s0[i] != s1[i];",
      [BINS + "::test_strong_field_low_temperature_concentrates_at_q_one"]),
