@@ -137,12 +137,17 @@ typedef struct {
                                   sample's previous one is stored, so samples
                                   beyond one wave of CTAs do not leave SMs idle
                                   at the end of a launch. 0 = library choice
-                                  (split into segments of 16-64 sweeps when
-                                  the samples outnumber the resident CTAs and
-                                  the last wave would leave slots idle), 1 =
-                                  one CTA runs all of a sample's sweeps; the
-                                  global-memory state is never split. Results
-                                  do not depend on it.                       */
+                                  for launches of >= 32 sweeps: segments of
+                                  16-64 sweeps when the samples outnumber the
+                                  resident CTAs and the last wave would leave
+                                  more than 3 % of the slots idle, or, when
+                                  one wave would give some SMs one CTA more
+                                  than others, k = floor(S / SMs) >= 3 CTAs on
+                                  every SM sharing the segments (the launch
+                                  then runs k * SMs CTAs: sg_launch_plan);
+                                  1 = one CTA runs all of a sample's sweeps;
+                                  the global-memory state is never split.
+                                  Results do not depend on it.               */
 } sg_options;
 
 /* Fill *opt with the defaults: INT8 layout, rng_group 1, exchange and
@@ -228,24 +233,28 @@ sg_status sg_measure(sg_ensemble *e, const int *k, int nk, float *out);
 
 /*
  * sg_measure without any device allocation. The paper has no counterpart;
- * this exists for callers that cannot call cudaMalloc when they measure: code
- * running while a stream is being captured into a CUDA graph, serving loops
- * that keep the allocator off their latency path, and hosts whose device
- * memory belongs to another framework's pool.
- *   Same arguments and output as sg_measure. The k vectors and the output are
- *   staged in one library-owned static device array of
+ * this exists for callers that cannot call cudaMalloc when they measure:
+ * serving loops that keep the allocator (and the device-wide synchronisation
+ * it can bring) off their latency path, and hosts whose device memory
+ * belongs to another framework's pool.
+ *   Same arguments and output as sg_measure, for the INT8 layout; MSC64
+ *   ensembles get SG_EUNSUPPORTED. The k vectors and the output are staged
+ *   in one library-owned static device array of
  *   4096 + 4 * SG_MEASURE_NOALLOC_MAX_FLOATS bytes that every GPU which loads
  *   the library holds until the process exits.
  *   Limits: nk <= SG_MEASURE_NOALLOC_MAX_K and
  *   n_samples * n_T * nk * 2 <= SG_MEASURE_NOALLOC_MAX_FLOATS; larger requests
  *   return SG_EINVAL without touching the device.
- *   The first call on a device looks up the array's device address (once per
- *   device, with that device current); make that first call before any
- *   stream capture begins.
+ *   The ensemble's device must be the current device (SG_EINVAL otherwise):
+ *   the first call on a device looks up the array's device address, once per
+ *   device, with that device current.
+ *   The call copies from and to pageable host memory and synchronises the
+ *   ensemble's stream before it returns, so it cannot be captured: while the
+ *   stream is being captured it returns SG_EUNSUPPORTED before any stream
+ *   work, and the capture stays valid.
  *   All calls share the one array and it keeps the last call's contents:
  *   calls whose work overlaps on the GPU (other host threads, other streams)
- *   race on it and must be serialised by the caller. The call synchronises
- *   the ensemble's stream before it returns.
+ *   race on it and must be serialised by the caller.
  */
 #define SG_MEASURE_NOALLOC_MAX_K 256
 #define SG_MEASURE_NOALLOC_MAX_FLOATS (1 << 20)
@@ -336,11 +345,29 @@ typedef struct {
     int32_t log_bins;  /* accumulator bins B (>= 1)                    */
     int32_t pq_hist;   /* 1 if the overlap histogram is kept           */
     int32_t threads_per_block;  /* launch shape of the sweep kernel    */
-    int32_t grid;               /* CTAs per sweep launch               */
+    int32_t grid;               /* CTAs of an unsplit sweep launch (a
+                                   segmented launch may run more:
+                                   sg_launch_plan)                     */
     int32_t state_in_shared;    /* 1: state held in shared memory for a
                                    chunk of sweeps; 0: in global memory */
 } sg_info;
 sg_status sg_get_info(const sg_ensemble *e, sg_info *out);
+
+/*
+ * The launch shape sg_sweep(e, n_sweeps) would use (the paper has no
+ * counterpart; it documents what runs). sg_info.grid is the unsplit shape;
+ * a launch may run a different number of CTAs: when the samples outnumber
+ * the resident CTAs and the last wave would leave slots idle, or when one
+ * wave would give some SMs one CTA more than others (then k >= 3 CTAs on
+ * every SM), each sample's sweeps are split into segments that the CTAs
+ * claim in order (sg_options.segments). MSC64 runs one launch per sweep.
+ *   grid      CTAs of each launch (may be NULL)
+ *   segments  segments per sample of the first launch, 1 = unsplit (may be NULL)
+ *   launches  fused-kernel launches of the call (may be NULL)
+ * SG_EINVAL for a NULL ensemble or n_sweeps < 0. Touches no device state.
+ */
+sg_status sg_launch_plan(const sg_ensemble *e, int64_t n_sweeps, int32_t *grid,
+                         int32_t *segments, int32_t *launches);
 
 /*
  * Disorder-averaged observables per slot from the accumulators (paper:

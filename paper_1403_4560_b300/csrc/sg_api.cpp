@@ -322,6 +322,7 @@ Int8Args make_args(sg_ensemble *e)
     a.s_key0 = e->opt.sample_base;
     a.work = e->work;
     a.n_seg = 1;
+    a.seg_wait = 1ull << 30;
     return a;
 }
 
@@ -735,6 +736,21 @@ static int int8_segments(const sg_ensemble *e, int n_sweeps, int *grid)
     return (int)std::max<int64_t>(want, 1);
 }
 
+// Longest wait of a segment for its sample's previous one. A waited-on unit
+// is always held by a running CTA (units are claimed segment-major), so a
+// wait lasts at most about two segments: the bound allows 64 clock cycles
+// per attempt of a segment (the fused kernel takes about 2 per attempt and
+// CTA on B300, more when other kernels share the SMs), at least 2^24 and at
+// most 2^30 cycles (about half a second at 2 GHz), so that a lost unit
+// cannot hold the GPU for long before the launch reports SG_ETIMEOUT.
+static unsigned long long segment_wait_cycles(const sg_ensemble *e, int n_sweeps, int n_seg)
+{
+    const unsigned long long seg_len = (unsigned long long)((n_sweeps + n_seg - 1) / n_seg);
+    const unsigned long long per_sweep = (unsigned long long)e->L * e->L * e->L * 2 * e->Tp;
+    const unsigned long long want = 64ull * per_sweep * seg_len;
+    return std::min(std::max(want, 1ull << 24), 1ull << 30);
+}
+
 static sg_status launch_sweeps(sg_ensemble *e, int64_t n, cudaStream_t s, bool device_counter)
 {
     if (e->msc) {
@@ -759,6 +775,7 @@ static sg_status launch_sweeps(sg_ensemble *e, int64_t n, cudaStream_t s, bool d
         if (device_counter) a.sweep0_dev = e->sweep_ctr;
         Int8Launch cfg = e->launch;
         a.n_seg = int8_segments(e, a.n_sweeps, &cfg.grid);
+        a.seg_wait = segment_wait_cycles(e, a.n_sweeps, a.n_seg);
         if (a.n_seg > 1)
             SG_CUDA(cudaMemsetAsync(e->work, 0, (size_t)(1 + e->S) * sizeof(unsigned int), s),
                     "segment counters");
@@ -905,6 +922,20 @@ sg_status sg_measure_noalloc(sg_ensemble *e, const int *k, int nk, float *out)
 {
     if (!e || !k || nk < 1 || !out) return fail(SG_EINVAL, "bad measure arguments");
     if (e->msc) return fail(SG_EUNSUPPORTED, "sg_measure_noalloc serves the int8 layout");
+    // the call copies to and from pageable host memory and waits for the
+    // stream, none of which a stream capture accepts: refuse before touching
+    // the stream, so that the caller's capture stays valid
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    SG_CUDA(cudaStreamIsCapturing(e->stream, &cap), "capture status");
+    if (cap != cudaStreamCaptureStatusNone)
+        return fail(SG_EUNSUPPORTED, "sg_measure_noalloc cannot run while the ensemble's stream "
+                                     "is being captured");
+    // the static array's address is per device: the ensemble's device must be
+    // the current one
+    int cur = -1;
+    SG_CUDA(cudaGetDevice(&cur), "current device");
+    if (cur != e->device)
+        return fail(SG_EINVAL, "sg_measure_noalloc: the ensemble's device is not the current device");
     if (nk > SG_MEASURE_NOALLOC_MAX_K)
         return fail(SG_EINVAL, "sg_measure_noalloc: more than SG_MEASURE_NOALLOC_MAX_K wave vectors");
     const size_t floats = (size_t)e->S * e->nt * nk * 2;
@@ -1175,6 +1206,28 @@ sg_status sg_get_info(const sg_ensemble *e, sg_info *out)
         out->grid = e->launch.grid;
         out->state_in_shared = e->launch.gst ? 0 : 1;
     }
+    return SG_OK;
+}
+
+sg_status sg_launch_plan(const sg_ensemble *e, int64_t n_sweeps, int32_t *grid, int32_t *segments,
+                         int32_t *launches)
+{
+    if (!e || n_sweeps < 0) return fail(SG_EINVAL, "bad arguments");
+    int g = 0, seg = 1, nl = 0;
+    if (e->msc) {
+        g = (e->nt / 2 + 1) * (int)(e->S / 64);
+        nl = (int)std::min<int64_t>(n_sweeps, INT32_MAX);
+    } else if (n_sweeps > 0) {
+        int64_t chunk = e->opt.sweeps_per_launch > 0 ? e->opt.sweeps_per_launch : n_sweeps;
+        chunk = std::min<int64_t>(std::max<int64_t>(chunk, 1), 1 << 30);
+        nl = (int)std::min<int64_t>((n_sweeps + chunk - 1) / chunk, INT32_MAX);
+        seg = int8_segments(e, (int)std::min<int64_t>(chunk, n_sweeps), &g);
+    } else {
+        g = e->launch.grid;
+    }
+    if (grid) *grid = g;
+    if (segments) *segments = seg;
+    if (launches) *launches = nl;
     return SG_OK;
 }
 

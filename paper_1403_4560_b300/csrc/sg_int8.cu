@@ -579,16 +579,17 @@ cudaError_t int8_measure_k(const Int8Args &a, int L, const int *k_dev, int nk, f
 // Allocation-free variant of the arbitrary-k overlap measurement.
 //
 // Some callers cannot allocate device memory at the point where they want a
-// measurement: code running while a stream is being captured into a CUDA
-// graph (cudaMalloc is not allowed there), serving loops that must not touch
-// the allocator on their latency path, and hosts whose memory pool belongs to
-// another framework. For them the k-vector and output staging live in this
-// file-scope device array instead of cudaMalloc'd buffers. Every device that
-// loads the library holds the array until the process exits.
+// measurement: serving loops that must not touch the allocator (and its
+// device-wide synchronisation) on their latency path, and hosts whose device
+// memory belongs to another framework's pool, where a stray cudaMalloc
+// competes with that pool. For them the k-vector and output staging live in
+// this file-scope device array instead of cudaMalloc'd buffers. Every device
+// that loads the library holds the array until the process exits.
 //
 // In host code the array's name is only a host-side stand-in, never a device
 // address: the device address comes from cudaGetSymbolAddress, taken once per
-// device with that device current (on the first call made on that device).
+// device with that device current (on the first call made on that device;
+// the caller has checked that the ensemble's device is the current one).
 // ---------------------------------------------------------------------------
 namespace {
 

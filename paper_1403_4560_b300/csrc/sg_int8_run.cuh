@@ -929,10 +929,6 @@ __device__ __forceinline__ void copy16_cg(void *dst, const void *src, size_t byt
     for (size_t k = threadIdx.x; k < bytes / 16; k += blockDim.x) d[k] = __ldcg(s + k);
 }
 
-// Longest wait for a sample's previous segment (clock64 cycles) when no
-// watchdog budget is set: far beyond any segment the library chooses (at
-// most 64 sweeps), after which the launch stops with SG_ETIMEOUT.
-constexpr unsigned long long kSegWaitCycles = 1ull << 36;
 
 // ---------------------------------------------------------------------------
 // The fused kernel: for each sample of this CTA, load, run n_sweeps sweeps
@@ -991,7 +987,7 @@ __global__ void __launch_bounds__(KernelBounds<L, GST, WIDE>::threads,
             if (threadIdx.x == 0) {
                 int fail = 0;
                 const volatile unsigned int *done = a.work + 1 + (s - a.s_begin);
-                const unsigned long long limit = a.watchdog ? a.watchdog : kSegWaitCycles;
+                const unsigned long long limit = a.watchdog ? a.watchdog : a.seg_wait;
                 const long long w0 = clock64();
                 while (*done < (unsigned int)segk) {
                     if (*(const volatile int *)a.status != 0) {  // stopped elsewhere

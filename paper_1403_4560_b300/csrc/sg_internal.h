@@ -48,6 +48,9 @@ struct Int8Args {
     // Zeroed before every launch with n_seg > 1.
     unsigned int *work;
     int n_seg;
+    // longest wait (clock64 cycles) for a sample's previous segment when no
+    // watchdog budget is set; the launch then stops with SG_ETIMEOUT
+    unsigned long long seg_wait;
 };
 
 struct Int8Launch {

@@ -122,6 +122,7 @@ def lib() -> ctypes.CDLL:
         "sg_set_sweeps_done": (st, [P, i64]),
         "sg_synchronize": (st, [P]),
         "sg_get_info": (st, [P, P]),
+        "sg_launch_plan": (st, [P, i64, P, P, P]),
         "sg_results": (st, [P, P]),
         "sg_results_bin": (st, [P, i32, P]),
         "sg_observables_from_acc": (st, [P, i64, i32, i32, P]),
@@ -351,6 +352,13 @@ class Ensemble:
         i = Info()
         _check(lib().sg_get_info(self._h, ctypes.byref(i)))
         return i
+
+    def launch_plan(self, n_sweeps: int) -> dict:
+        """sg_launch_plan: grid, segments per sample and launches of sg_sweep(n_sweeps)."""
+        g, seg, nl = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().sg_launch_plan(self._h, int(n_sweeps), ctypes.byref(g), ctypes.byref(seg),
+                                    ctypes.byref(nl)))
+        return {"grid": g.value, "segments": seg.value, "launches": nl.value}
 
     def results(self, bin: int | None = None) -> dict:
         """Observables of the last sweep bin, or of bin `bin`."""

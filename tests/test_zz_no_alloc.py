@@ -1,12 +1,12 @@
 """The allocation-free measurement entry point, through the C ABI.
 
 sg_measure_noalloc is for callers that cannot call cudaMalloc when they
-measure (stream capture in progress, allocator kept off a serving loop's
-latency path, device memory owned by another framework's pool). It must give
-what sg_measure gives, call after call, although every call reuses the same
-static device array. This file is collected last so that a run stopping at
-its first failure has already run every other test; it also passes alone in
-a fresh process.
+measure (a serving loop that keeps the allocator off its latency path, a host
+whose device memory belongs to another framework's pool). It must give what
+sg_measure gives, call after call, although every call reuses the same static
+device array; it refuses a capturing stream without spoiling the capture.
+This file is collected last so that a run stopping at its first failure has
+already run every other test; it also passes alone in a fresh process.
 """
 import numpy as np
 import pytest
@@ -61,3 +61,32 @@ def test_noalloc_measure_rejects_requests_beyond_its_array():
         with pytest.raises(sgmc.SgError) as ei:
             big.measure_noalloc(np.zeros((65, 3), dtype=np.int32))
         assert ei.value.status == sgmc.SG_EINVAL
+
+
+def test_noalloc_measure_status_for_msc_and_for_a_capturing_stream():
+    """The multispin-coded layout is not served (SG_EUNSUPPORTED). A call
+    made while the ensemble's stream is being captured returns
+    SG_EUNSUPPORTED before it touches the stream: the capture completes and
+    replays, and the next call outside the capture measures as before."""
+    import torch
+    T = inputs.geometric_ladder(0.5, 1.5, 4)
+    with sgmc.Ensemble(4, 0.1, T, "pmj", 64, 3, layout=sgmc.SG_LAYOUT_MSC64) as msc:
+        with pytest.raises(sgmc.SgError) as ei:
+            msc.measure_noalloc(np.array([[1, 0, 0]]))
+        assert ei.value.status == sgmc.SG_EUNSUPPORTED
+    side = torch.cuda.Stream()
+    k = np.array([[1, 0, 0], [0, 1, 1]])
+    with sgmc.Ensemble(4, 0.1, T, "pmj", 3, 3, stream=side) as ens:
+        want = ens.measure(k)
+        np.testing.assert_allclose(ens.measure_noalloc(k), want, atol=ATOL, rtol=0)
+        x = torch.zeros(16, device="cuda")
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=side):
+            with pytest.raises(sgmc.SgError) as ei:
+                ens.measure_noalloc(k)
+            y = x + 1.0
+        assert ei.value.status == sgmc.SG_EUNSUPPORTED
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(y, torch.ones(16, device="cuda"))
+        np.testing.assert_allclose(ens.measure_noalloc(k), want, atol=ATOL, rtol=0)
