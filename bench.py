@@ -49,10 +49,11 @@ WORKLOAD = ("gaussian EA 3D, L=8 and 12 x h=0.1,0.2,0.3, 512 samples each, "
 # summarised in profiles/dram_int8_run_kernel_L12_bench.md. Must be reset to
 # None whenever the kernel changes, until it is captured again.
 TRAFFIC_BYTES_PER_LAUNCH = 62.1e6
-# Thread instructions per attempt of the same kernel (ncu thread_inst_executed
-# over the launch's attempts; profiles/int8_run_kernel_L12_gauss.md). Reset to
-# None whenever the kernel changes.
-INSTR_PER_ATTEMPT = 85.2
+# Thread instructions per attempt of the same kernel in the same launch shape
+# (ncu smsp__thread_inst_executed.sum over the launch's attempts, captured on
+# the bench's own 512-sample, 256-sweep segmented launch). Reset to None
+# whenever the kernel changes, until it is captured again.
+INSTR_PER_ATTEMPT = None
 # SM issue peak: 148 SMs x 4 schedulers x 1 warp instruction per cycle x 32
 # threads x 2.032 GHz (maximum SM clock), in thread instructions per second.
 ISSUE_PEAK = 148 * 4 * 32 * 2.032e9
@@ -185,9 +186,21 @@ def cpu_baseline(budget_s: float):
     st.run(n, threads=cores)  # the timed sample: one call
     dt = time.perf_counter() - t0
     att = L ** 3 * 2 * N_T * cores * n
+    # one core: one sample in the calling thread, a quarter of the budget
+    one = orc.State(L, T, 0.2, True, seed=99, J=J[:1], spins=s0[:1], n_therm=0)
+    t0 = time.perf_counter()
+    one.run(2)
+    per1 = max((time.perf_counter() - t0) / 2, 1e-4)
+    n1 = max(1, min(20000, int(0.25 * budget_s / per1)))
+    t0 = time.perf_counter()
+    one.run(n1)
+    dt1 = time.perf_counter() - t0
+    v1 = L ** 3 * 2 * N_T * n1 / (dt1 * 1e9)
     return {"value": att / (dt * 1e9), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "value_1core": v1,
             "sample": f"L=12 gaussian, 2x24 T, h=0.2, {cores} samples x {n} sweeps "
-                      f"(exchange+measure every sweep) in one call, {dt:.1f} s"}
+                      f"(exchange+measure every sweep) in one call, {dt:.1f} s; 1 core: "
+                      f"1 sample x {n1} sweeps, {dt1:.1f} s"}
 
 
 def run_reference(args, rank):
@@ -432,19 +445,23 @@ def main():
            "kernel": "int8_run_kernel<L=12, gauss>",
            "b_alg_bytes_per_attempt": b_alg, "peak_kind": peak_kind,
            "attempts_per_ns": dom_att / (dom_ms * 1e6)}
-    # the binding resource: the kernel keeps the state on chip and is bound by
-    # instruction issue (ncu: ~74 % of issue slots; DRAM moves under 5 % of
-    # the HBM-equivalent bytes), so the primary roofline is the issue rate
+    # The roofline is the HBM-equivalent one above (B_alg x attempts / time
+    # against the measured copy bandwidth). What binds is instruction issue:
+    # the state stays on chip, so at I thread instructions per attempt the
+    # kernel cannot pass ISSUE_PEAK / I attempts/s. That ceiling, and the
+    # share of it reached, are reported beside the roofline.
     roofline = hbm
+    issue = None
     if INSTR_PER_ATTEMPT:
         inst = INSTR_PER_ATTEMPT * dom_att / (dom_ms * 1e-3) / 1e12
-        roofline = {"bound": "alu", "achieved": inst, "peak": ISSUE_PEAK / 1e12,
-                    "unit": "T thread-instructions/s", "frac": inst / (ISSUE_PEAK / 1e12),
-                    "traffic": TRAFFIC_BYTES_PER_LAUNCH,
-                    "instructions_per_attempt": INSTR_PER_ATTEMPT,
-                    "peak_kind": "derived: 148 SMs x 4 schedulers x 32 lanes x 2.032 GHz",
-                    "kernel": "int8_run_kernel<L=12, gauss>",
-                    "attempts_per_ns": dom_att / (dom_ms * 1e6)}
+        ceiling = ISSUE_PEAK / INSTR_PER_ATTEMPT / 1e9  # attempts/ns at 100 % issue
+        issue = {"bound": "alu", "achieved": inst, "peak": ISSUE_PEAK / 1e12,
+                 "unit": "T thread-instructions/s", "frac": inst / (ISSUE_PEAK / 1e12),
+                 "instructions_per_attempt": INSTR_PER_ATTEMPT,
+                 "issue_ceiling_attempts_per_ns": ceiling,
+                 "issue_ceiling_hbm_frac": ceiling * b_alg / peak,
+                 "peak_kind": "derived: 148 SMs x 4 schedulers x 32 lanes x 2.032 GHz",
+                 "kernel": "int8_run_kernel<L=12, gauss>"}
 
     plain = None
     if not args.no_plain and rank == 0:
@@ -533,7 +550,7 @@ def main():
                            "l2": "state+couplings 206 MB per GPU, larger than L2",
                            "batched": "one CUDA graph per step, 6 parallel branches"},
                 "gpu_launches": n_launch_per_step * K,
-                "roofline": roofline, "roofline_hbm": hbm, "plain": plain, "e2e": e2e,
+                "roofline": roofline, "issue": issue, "plain": plain, "e2e": e2e,
                 "cpu_baseline": cb,
                 "clocks": clk.summary(), "extras": extras}
         print(json.dumps(line), flush=True)

@@ -332,6 +332,31 @@ typedef struct {
 } sg_tune_report;
 sg_status sg_autotune(sg_ensemble *e, int64_t trial_sweeps, sg_tune_report *report);
 
+/*
+ * Schedule tuner (opt-in; the paper does not say how often to offer
+ * replica exchanges, methods section). Times trial_sweeps sweeps of the
+ * ensemble, on its own data, for each candidate exchange_every value
+ * (sweeps per parallel-tempering exchange, 0 = never; up to
+ * SG_SCHEDULE_MAX_CANDIDATES values), restores the state afterwards
+ * (spins, energies, accumulators, histogram and sweep counter as before),
+ * and sets the ensemble's exchange_every to the most frequent exchange whose
+ * time per sweep is at most (1 + tolerance) times the fastest candidate's.
+ * Results from then on equal the oracle's run with that exchange_every
+ * (the exchange numbering follows the global sweep index, methods section).
+ * Cached CUDA graphs of the ensemble are dropped. Synchronises the stream;
+ * allocates a device copy of the state while it runs. SG_EINVAL for a
+ * negative candidate, no candidates, too many or tolerance < 0.
+ */
+#define SG_SCHEDULE_MAX_CANDIDATES 16
+typedef struct {
+    int32_t exchange_every;     /* the value chosen and applied               */
+    int32_t n_candidates;
+    double fastest_ms_per_sweep;
+    double ms_per_sweep[SG_SCHEDULE_MAX_CANDIDATES]; /* per candidate, in order */
+} sg_schedule_report;
+sg_status sg_autotune_schedule(sg_ensemble *e, int64_t trial_sweeps, const int32_t *exchange_every,
+                               int n_candidates, double tolerance, sg_schedule_report *report);
+
 /* Wait for the ensemble's stream and report the first device-side error. */
 sg_status sg_synchronize(sg_ensemble *e);
 

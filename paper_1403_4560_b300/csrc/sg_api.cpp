@@ -1449,6 +1449,99 @@ sg_status sg_autotune(sg_ensemble *e, int64_t trial_sweeps, sg_tune_report *rep)
     return SG_OK;
 }
 
+// Device bytes of an ensemble's evolving state (spins as kept, B, M, the
+// accumulators and the histogram right after them), for the tuners' backup.
+static size_t state_backup_bytes(const sg_ensemble *e, size_t part[4])
+{
+    const size_t N = (size_t)e->L * e->L * e->L;
+    part[0] = e->msc ? (size_t)(e->S / 64) * e->nt * 2 * N * 8 : e->spins_bytes;
+    part[1] = part[2] = (size_t)e->S * 2 * (e->msc ? e->nt : e->Tp) * sizeof(int64_t);
+    part[3] = e->hist ? (size_t)((uint8_t *)e->hist - (uint8_t *)e->acc) + e->hist_bytes
+                      : e->acc_bytes;
+    return part[0] + part[1] + part[2] + part[3];
+}
+
+static cudaError_t state_backup(sg_ensemble *e, uint8_t *buf, bool restore)
+{
+    size_t part[4];
+    state_backup_bytes(e, part);
+    void *dev[4] = {e->msc ? (void *)e->W : (void *)e->spins, e->B, e->M, e->acc};
+    cudaError_t ce = cudaSuccess;
+    for (int q = 0; q < 4 && ce == cudaSuccess; ++q) {
+        ce = restore ? cudaMemcpyAsync(dev[q], buf, part[q], cudaMemcpyDeviceToDevice, e->stream)
+                     : cudaMemcpyAsync(buf, dev[q], part[q], cudaMemcpyDeviceToDevice, e->stream);
+        buf += part[q];
+    }
+    return ce;
+}
+
+sg_status sg_autotune_schedule(sg_ensemble *e, int64_t trial_sweeps, const int32_t *exchange_every,
+                               int n_candidates, double tolerance, sg_schedule_report *rep)
+{
+    if (!e || trial_sweeps < 1 || !exchange_every || n_candidates < 1 ||
+        n_candidates > SG_SCHEDULE_MAX_CANDIDATES || !(tolerance >= 0.0))
+        return fail(SG_EINVAL, "bad schedule-tuner arguments");
+    for (int c = 0; c < n_candidates; ++c)
+        if (exchange_every[c] < 0) return fail(SG_EINVAL, "exchange_every candidates must be >= 0");
+    size_t part[4];
+    const size_t bytes = state_backup_bytes(e, part);
+    uint8_t *bk = nullptr;
+    SG_CUDA(cudaMalloc(&bk, bytes), "schedule tuner backup");
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const sg_options orig = e->opt;
+    const int64_t done0 = e->sweeps_done;
+    sg_schedule_report r{};
+    cudaError_t ce = state_backup(e, bk, false);
+    sg_status st = SG_OK;
+    for (int c = 0; c < n_candidates && ce == cudaSuccess && st == SG_OK; ++c) {
+        e->opt.exchange_every = exchange_every[c];
+        st = launch_sweeps(e, 1, e->stream, false);  // warm-up
+        if (st != SG_OK) break;
+        cudaEventRecord(e0, e->stream);
+        st = launch_sweeps(e, trial_sweeps, e->stream, false);
+        if (st != SG_OK) break;
+        cudaEventRecord(e1, e->stream);
+        ce = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        r.ms_per_sweep[c] = ms / (double)trial_sweeps;
+        if (ce == cudaSuccess) ce = state_backup(e, bk, true);
+    }
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(e->stream);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(bk);
+    e->opt = orig;
+    e->sweeps_done = done0;
+    if (st != SG_OK) return st;
+    if (ce != cudaSuccess) return cuda_fail(ce, "schedule tuner");
+    // the most frequent exchange whose sweeps cost at most (1 + tolerance)
+    // times the fastest candidate's; never-exchange (0) only if nothing else
+    // qualifies
+    double fastest = 1e300;
+    for (int c = 0; c < n_candidates; ++c) fastest = std::min(fastest, r.ms_per_sweep[c]);
+    int pick = -1;
+    for (int c = 0; c < n_candidates; ++c) {
+        if (r.ms_per_sweep[c] > fastest * (1.0 + tolerance)) continue;
+        const int32_t v = exchange_every[c];
+        if (pick < 0) {
+            pick = c;
+            continue;
+        }
+        const int32_t w = exchange_every[pick];
+        if ((v > 0 && (w == 0 || v < w))) pick = c;
+    }
+    e->opt.exchange_every = exchange_every[pick];
+    purge_graphs(e);  // captured launches carry the old schedule
+    r.exchange_every = exchange_every[pick];
+    r.n_candidates = n_candidates;
+    r.fastest_ms_per_sweep = fastest;
+    if (rep) *rep = r;
+    return SG_OK;
+}
+
 sg_status sg_results_bin(sg_ensemble *e, int bin, const sg_observables *out)
 {
     if (!e || !out) return fail(SG_EINVAL, "bad arguments");

@@ -53,6 +53,12 @@ class TuneReport(ctypes.Structure):
                 ("default_ms_per_sweep", ctypes.c_double)]
 
 
+class ScheduleReport(ctypes.Structure):
+    _fields_ = [("exchange_every", ctypes.c_int32), ("n_candidates", ctypes.c_int32),
+                ("fastest_ms_per_sweep", ctypes.c_double),
+                ("ms_per_sweep", ctypes.c_double * 16)]
+
+
 class ServerOptions(ctypes.Structure):
     _fields_ = [("memory_budget", ctypes.c_size_t), ("max_active", ctypes.c_int32),
                 ("chunk_sweeps", ctypes.c_int64), ("use_graph", ctypes.c_int32)]
@@ -139,6 +145,7 @@ def lib() -> ctypes.CDLL:
         "sg_server_get_stats": (st, [P, P]),
         "sg_server_destroy": (None, [P]),
         "sg_autotune": (st, [P, i64, P]),
+        "sg_autotune_schedule": (st, [P, i64, P, i32, f64, P]),
         "sg_status_str": (ctypes.c_char_p, [i32]),
         "sg_last_error": (ctypes.c_char_p, []),
     }
@@ -332,6 +339,18 @@ class Ensemble:
         r = TuneReport()
         _check(lib().sg_autotune(self._h, int(trial_sweeps), ctypes.byref(r)))
         return {f: getattr(r, f) for f, _ in TuneReport._fields_}
+
+    def autotune_schedule(self, exchange_every, trial_sweeps: int = 8,
+                          tolerance: float = 0.03) -> dict:
+        """sg_autotune_schedule: time each exchange_every candidate and apply
+        the most frequent exchange within `tolerance` of the fastest."""
+        c = np.ascontiguousarray(exchange_every, dtype=np.int32)
+        r = ScheduleReport()
+        _check(lib().sg_autotune_schedule(self._h, int(trial_sweeps), _ptr(c), len(c),
+                                          float(tolerance), ctypes.byref(r)))
+        self.opt.exchange_every = r.exchange_every
+        return {"exchange_every": r.exchange_every, "fastest_ms_per_sweep": r.fastest_ms_per_sweep,
+                "ms_per_sweep": list(r.ms_per_sweep[:len(c)])}
 
     def measure_noalloc(self, k) -> np.ndarray:
         """sg_measure_noalloc: the same result, staged in the library's static

@@ -167,3 +167,37 @@ def test_served_requests_match_oracle(use_graph):
                        n_therm=sweeps // 2)
         st.run(sweeps, threads=THREADS)
         np.testing.assert_array_equal(acc, st.acc, err_msg=f"served request {k} (L={L})")
+
+
+@pytest.mark.parametrize("dist,layout", [("gauss", 0), ("pmj", 1)])
+def test_schedule_tuner_applies_its_choice_and_matches_oracle(dist, layout):
+    """sg_autotune_schedule times each sweeps-per-exchange candidate on the
+    ensemble's own data, restores the state, and applies its pick: with a
+    wide tolerance the most frequent exchange (3 of {0, 3, 8}); the run that
+    follows equals the oracle's at that schedule, bit for bit."""
+    L, nt, S, sweeps = 6, 6, 64, 40
+    T = inputs.geometric_ladder(0.5, 1.6, nt)
+    J, s0 = inputs.make_instance(dist, L, S, nt, seed=12)
+    extra = dict(layout=sgmc.SG_LAYOUT_MSC64) if layout else {}
+    with sgmc.Ensemble(L, 0.2, T, dist, S, 13, J=J, spins=s0, n_therm=10, **extra) as ens:
+        rep = ens.autotune_schedule([0, 3, 8], trial_sweeps=4, tolerance=10.0)
+        assert rep["exchange_every"] == 3
+        assert all(v > 0 for v in rep["ms_per_sweep"])
+        assert ens.sweeps_done == 0
+        np.testing.assert_array_equal(ens.spins(), s0)
+        assert not ens.accumulators().any()
+        ens.sweep(sweeps)
+        ens.synchronize()
+        st = orc.State(L, T, 0.2, dist == "gauss", seed=13, J=J, spins=s0, n_therm=10,
+                       exchange_every=3, rng_group=64 if layout else 1)
+        st.run(sweeps, threads=THREADS)
+        np.testing.assert_array_equal(ens.spins(), st.spins)
+        np.testing.assert_array_equal(ens.accumulators(), st.acc)
+        # tolerance 0: the fastest candidate wins; bad arguments are refused
+        rep0 = ens.autotune_schedule([1, 4], trial_sweeps=2, tolerance=0.0)
+        best = [1, 4][int(np.argmin(rep0["ms_per_sweep"]))]
+        assert rep0["exchange_every"] == best
+        for bad in ([], [-1, 2]):
+            with pytest.raises(sgmc.SgError) as ei:
+                ens.autotune_schedule(bad)
+            assert ei.value.status == sgmc.SG_EINVAL
