@@ -46,14 +46,15 @@ WORKLOAD = ("gaussian EA 3D, L=8 and 12 x h=0.1,0.2,0.3, 512 samples each, "
             "2 replicas x 24 T geometric 0.5-1.6, exchange+measure every sweep")
 # DRAM bytes (read + write) of one launch of the dominant kernel in this
 # workload (L = 12, 512 samples, 256 sweeps), from the one-pass ncu capture
-# summarised in profiles/dram_int8_run_kernel_L12_bench.md. Must be reset to
+# summarised under profiles/. Must be reset to
 # None whenever the kernel changes, until it is captured again.
 TRAFFIC_BYTES_PER_LAUNCH = 62.1e6
 # Thread instructions per attempt of the same kernel in the same launch shape
 # (ncu smsp__thread_inst_executed.sum over the launch's attempts, captured on
-# the bench's own 512-sample, 256-sweep segmented launch). Reset to None
-# whenever the kernel changes, until it is captured again.
-INSTR_PER_ATTEMPT = None
+# the bench's own 512-sample, 256-sweep segmented launch;
+# its ncu summary is kept under profiles/). Reset to None whenever
+# the kernel changes, until it is captured again.
+INSTR_PER_ATTEMPT = 85.1
 # SM issue peak: 148 SMs x 4 schedulers x 1 warp instruction per cycle x 32
 # threads x 2.032 GHz (maximum SM clock), in thread instructions per second.
 ISSUE_PEAK = 148 * 4 * 32 * 2.032e9
@@ -321,42 +322,16 @@ def extra_int8(sgmc, stream, torch, L, S, T, h, dist="gauss", sweeps=32):
                 "workload": f"{dist}, L={L}, {S} samples, 2x{len(T)} T, h={h}"}
 
 
-def extra_serving(sgmc, stream, n_req=24, rate=50.0, sweeps=256):
+def extra_serving(stream, n_req=24, rate=50.0, sweeps=256):
     """A finite Poisson stream (mean 50 requests/s, seed 1) of requests drawn
     uniformly from L in {8,12,16,20,24}, h in {0.05,...,0.40}, 16-32
     temperatures geometric in 0.5-1.6, 64-1024 samples (multiples of 64),
-    +-J or Gaussian couplings; each request runs `sweeps` sweeps (truncated
-    from the full 2^14 so the stream ends within seconds)."""
-    from paper_1403_4560_b300 import inputs
-    rng = np.random.default_rng(1)
-    reqs = []
-    t = 0.0
-    for _ in range(n_req):
-        t += rng.exponential(1.0 / rate)
-        reqs.append(dict(at=t, L=int(rng.choice([8, 12, 16, 20, 24])),
-                         h=float(rng.choice(np.arange(1, 9) * 0.05)),
-                         nt=int(rng.integers(16, 33)), S=int(64 * rng.integers(1, 17)),
-                         dist=str(rng.choice(["pmj", "gauss"]))))
-    att_total = sum(r["L"] ** 3 * 2 * r["nt"] * r["S"] * sweeps for r in reqs)
-    with sgmc.Server(chunk_sweeps=64, stream=stream) as sv:
-        t0 = time.perf_counter()
-        ids = []
-        for k, r in enumerate(reqs):
-            delay = r["at"] - (time.perf_counter() - t0)
-            if delay > 0:
-                time.sleep(delay)
-            ids.append(sv.submit(r["L"], r["h"], inputs.geometric_ladder(0.5, 1.6, r["nt"]),
-                                 r["dist"], r["S"], seed=1000 + k, n_sweeps=sweeps))
-        for rid in ids:
-            sv.wait(rid)
-        wall = time.perf_counter() - t0
-        lat = [sv.result(rid)[1] for rid in ids]
-        st = sv.stats()
-    return {"requests": n_req, "rate_per_s": rate, "sweeps_per_request": sweeps,
-            "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
-            "attempts_per_ns_wall": att_total / (wall * 1e9),
-            "attempts_per_ns_busy": st["attempts"] / (st["busy_seconds"] * 1e9),
-            "unit": UNIT}
+    +-J or Gaussian couplings; each request runs `sweeps` sweeps (the full
+    2^14-sweep stream takes minutes: python -m
+    paper_1403_4560_b300.serving_run, results committed separately)."""
+    from paper_1403_4560_b300 import serving_run
+    return serving_run.run_stream(serving_run.draw_requests(n_req, rate, seed=1), sweeps,
+                                  chunk_sweeps=64, stream=stream)
 
 
 def main():
@@ -534,7 +509,7 @@ def main():
                   # the same geometry with Gaussian couplings on the int8 path
                   "int8_paper_L10_56T_gauss": extra_int8(sgmc, stream, torch, L=10, S=1184,
                                                          T=t_paper, h=0.1),
-                  "serving": extra_serving(sgmc, stream)}
+                  "serving": extra_serving(stream)}
 
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu:
