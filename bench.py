@@ -322,6 +322,33 @@ def extra_int8(sgmc, stream, torch, L, S, T, h, dist="gauss", sweeps=32):
                 "workload": f"{dist}, L={L}, {S} samples, 2x{len(T)} T, h={h}"}
 
 
+def extra_cluster(sgmc, stream, torch, sweeps=16):
+    """Large lattices with fewer samples than SMs (64 samples, Gaussian, 2 x
+    16 temperatures geometric 0.5-1.6, h = 0.2, measuring every sweep): each
+    sample swept by a thread-block cluster (library choice) against one CTA
+    per sample."""
+    from paper_1403_4560_b300 import inputs
+    T = inputs.geometric_ladder(0.5, 1.6, 16)
+    out = {"unit": UNIT}
+    for L in (24, 32):
+        row = {}
+        for name, cl in (("cluster", 0), ("k2", 2), ("k4", 4), ("one_cta_per_sample", 1)):
+            with sgmc.Ensemble(L, 0.2, T, "gauss", 64, 11, stream=stream, n_therm=0,
+                               cluster=cl) as e:
+                e.sweep(2)
+                torch.cuda.synchronize()
+                ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+                ev[0].record(stream)
+                e.sweep(sweeps)
+                ev[1].record(stream)
+                torch.cuda.synchronize()
+                row[name] = e.info().attempts_per_sweep * sweeps / (ev[0].elapsed_time(ev[1]) * 1e6)
+                if cl == 0:
+                    row["ctas_per_sample"] = e.info().cluster
+        out[f"L{L}_64_samples"] = row
+    return out
+
+
 def extra_serving(stream, n_req=24, rate=50.0, sweeps=256):
     """A finite Poisson stream (mean 50 requests/s, seed 1) of requests drawn
     uniformly from L in {8,12,16,20,24}, h in {0.05,...,0.40}, 16-32
@@ -509,6 +536,7 @@ def main():
                   # the same geometry with Gaussian couplings on the int8 path
                   "int8_paper_L10_56T_gauss": extra_int8(sgmc, stream, torch, L=10, S=1184,
                                                          T=t_paper, h=0.1),
+                  "cluster": extra_cluster(sgmc, stream, torch),
                   "serving": extra_serving(stream)}
 
     cb = None

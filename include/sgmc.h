@@ -148,6 +148,15 @@ typedef struct {
                                   1 = one CTA runs all of a sample's sweeps;
                                   the global-memory state is never split.
                                   Results do not depend on it.               */
+    int32_t cluster;           /* INT8 state in global memory, L = 20, 24, 28
+                                  or 32: CTAs per sample, each sweeping L/k of
+                                  the z-planes as one thread-block cluster.
+                                  0 = library choice (k = 2, 4 or 8 when the
+                                  samples are fewer than the SMs and the split
+                                  keeps more SMs busy), 1 = one CTA per
+                                  sample, 2 / 4 / 8 = that cluster size
+                                  (SG_EUNSUPPORTED if it cannot run). Results
+                                  do not depend on it.                       */
 } sg_options;
 
 /* Fill *opt with the defaults: INT8 layout, rng_group 1, exchange and
@@ -375,6 +384,8 @@ typedef struct {
                                    sg_launch_plan)                     */
     int32_t state_in_shared;    /* 1: state held in shared memory for a
                                    chunk of sweeps; 0: in global memory */
+    int32_t cluster;            /* CTAs sweeping one sample together (1
+                                   unless sg_options.cluster applies)   */
 } sg_info;
 sg_status sg_get_info(const sg_ensemble *e, sg_info *out);
 

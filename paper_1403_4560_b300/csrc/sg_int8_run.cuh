@@ -117,6 +117,14 @@ __device__ __forceinline__ uint2 load_packed(const uint8_t *p)
     const uint32_t b = *p;
     return make_uint2(expand4(b & 15u), expand4(b >> 4));
 }
+// The same through L2 only: a byte another SM stores during the launch (the
+// boundary planes of a neighbouring CTA of the same cluster), which this
+// SM's L1 could still hold from before.
+__device__ __forceinline__ uint2 load_packed_cg(const uint8_t *p)
+{
+    const uint32_t b = __ldcg(p);
+    return make_uint2(expand4(b & 15u), expand4(b >> 4));
+}
 __device__ __forceinline__ void store_packed(uint8_t *p, uint2 w)
 {
     *p = (uint8_t)(compress4(w.x) | (compress4(w.y) << 4));
@@ -178,20 +186,23 @@ struct Ctx {
     uint32_t k0, k1;  // Metropolis Philox key
     uint32_t seed_lo, seed_hi;
     float hq;         // Gaussian: field on the 2^-17 grid
+    // cluster instances: this CTA's slab of z-planes [z0, z1) and its work
+    // items [u0, u1) of each colour
+    int z0, z1, u0, u1;
 };
 
 // Site index and neighbour offsets (in sites) of the colour-COL site with
 // colour-compressed index jj (i = 2*jj + parity, i >> 1 == jj).
 template <int L>
 struct SiteNb {
-    int i, x, dxp, dxm, dyp, dym, dzp, dzm;
+    int i, x, z, dxp, dxm, dyp, dym, dzp, dzm;
     __device__ __forceinline__ SiteNb(int jj, int COL)
     {
         constexpr int H = L / 2;
         const int row = jj / H;
         const int x2 = jj - row * H;
         const int y = row % L;
-        const int z = row / L;
+        z = row / L;
         x = 2 * x2 + ((COL + y + z) & 1);
         i = x + L * row;
         dxp = (x == L - 1) ? -(L - 1) : 1;
@@ -435,7 +446,10 @@ __device__ __forceinline__ void half_sweep(const Smem &sm, const Ctx &cx, uint32
 // half_sweep; only the storage differs (one byte per site and group,
 // expanded to 0/1 bytes).
 // ---------------------------------------------------------------------------
-template <int L, bool GAUSS>
+// SLAB (cluster instances): only the items [cx.u0, cx.u1) of this CTA's
+// z-slab, and the z-neighbours in the next or previous slab are read through
+// L2 (another CTA of the cluster wrote them).
+template <int L, bool GAUSS, bool SLAB = false>
 __device__ __forceinline__ void half_sweep_packed(const Smem &sm, const Ctx &cx, uint32_t n_sweep,
                                                   const int COL)
 {
@@ -483,7 +497,8 @@ __device__ __forceinline__ void half_sweep_packed(const Smem &sm, const Ctx &cx,
 
     // item = u * WR + j with a fixed step of u per thread (no division per item)
     const int du = blockDim.x / WR;
-    for (int u = threadIdx.x / WR; u < U; u += du) {
+    const int u_end = SLAB ? cx.u1 : U;
+    for (int u = (SLAB ? cx.u0 : 0) + threadIdx.x / WR; u < u_end; u += du) {
         if (COL == 1 && nsites + RUN > kFlushSites) flush();
         {
             const uint32_t c0 = (uint32_t)u;
@@ -509,8 +524,15 @@ __device__ __forceinline__ void half_sweep_packed(const Smem &sm, const Ctx &cx,
                 const uint2 nxm = load_packed(sm.spins + own + st.dxm * RB);
                 const uint2 nyp = load_packed(sm.spins + own + st.dyp * RB);
                 const uint2 nym = load_packed(sm.spins + own + st.dym * RB);
-                const uint2 nzp = load_packed(sm.spins + own + st.dzp * RB);
-                const uint2 nzm = load_packed(sm.spins + own + st.dzm * RB);
+                uint2 nzp, nzm;
+                if (SLAB && st.z == cx.z1 - 1)
+                    nzp = load_packed_cg(sm.spins + own + st.dzp * RB);
+                else
+                    nzp = load_packed(sm.spins + own + st.dzp * RB);
+                if (SLAB && st.z == cx.z0)
+                    nzm = load_packed_cg(sm.spins + own + st.dzm * RB);
+                else
+                    nzm = load_packed(sm.spins + own + st.dzm * RB);
                 uint2 fm;
                 if constexpr (!GAUSS) {
                     const uint2 jb = *reinterpret_cast<const uint2 *>(sm.J8 + 8 * st.i);
@@ -661,14 +683,15 @@ __device__ __forceinline__ void exchange_apply(const Smem &sm, const Ctx &cx)
 // Packed state: per site, each replica's slots as one mask (bit t = slot t);
 // an accepted pair (p, p+1) swaps bits p and p+1. Pairs of one parity are
 // disjoint, so one masked exchange per replica applies them all.
+// Sites [site0, site1) (a cluster CTA's slab; the whole lattice by default).
 template <int L>
-__device__ __forceinline__ void exchange_apply_packed(const Smem &sm, const Ctx &cx)
+__device__ __forceinline__ void exchange_apply_packed(const Smem &sm, const Ctx &cx, int site0 = 0,
+                                                      int site1 = L * L * L)
 {
-    constexpr int N = L * L * L;
     const int WR = cx.WR, RB = cx.RB;
     const unsigned long long a0 = sm.accm[0], a1 = sm.accm[1];
     if (!(a0 | a1)) return;
-    for (int site = threadIdx.x; site < N; site += blockDim.x) {
+    for (int site = site0 + threadIdx.x; site < site1; site += blockDim.x) {
         uint8_t *row = sm.spins + (size_t)site * RB;
         unsigned long long w0 = 0, w1 = 0;
         for (int jj = 0; jj < WR; ++jj) {
@@ -744,18 +767,15 @@ __device__ __forceinline__ double ld_acc(const double *p, bool seg)
     return seg ? __ldcg(p) : *p;
 }
 
-template <int L, bool PACK>
-__device__ __forceinline__ void measure_step(const Smem &sm, const Ctx &cx, const Int8Args &a,
-                                             int bin)
+// Energies and magnetisations of every slot (one thread per slot).
+__device__ __forceinline__ void measure_energies(const Smem &sm, const Ctx &cx, const Int8Args &a,
+                                                 int bin)
 {
-    constexpr int LL = L * L;
-    const int WR = cx.WR, RB = cx.RB, Tp = cx.Tp, nt = cx.nt;
+    const int Tp = cx.Tp, nt = cx.nt;
     const bool seg = a.n_seg > 1;  // the accumulators may come from another SM
     // device layout [S][bins][40][nt]: entry k of slot t at accs[k * nt + t],
     // so lanes over consecutive slots touch consecutive doubles
     double *accs = a.acc + ((size_t)cx.s * a.n_bins + bin) * SG_NACC * nt;
-    // energies and magnetisations first (one thread per slot), so that the
-    // projection phase reads nothing the next sweep overwrites
     for (int t = threadIdx.x; t < nt; t += blockDim.x) {
         double *ac = accs + t;  // entry k at ac[k * nt]
         double o5 = ld_acc(ac + 5 * nt, seg), o6 = ld_acc(ac + 6 * nt, seg);
@@ -777,9 +797,19 @@ __device__ __forceinline__ void measure_step(const Smem &sm, const Ctx &cx, cons
         ac[7 * nt] = o7;
         ac[8 * nt] = o8;
     }
-    for (int j0 = 0; j0 < WR; j0 += a.mchunk) {
-        const int nw = min(a.mchunk, WR - j0);
-        // (A) marginals; the group index varies fastest across lanes
+}
+
+// (A) 2D marginals of the q = -1 counts of the words j0 .. j0 + nw - 1 into
+// sm.marg; the group index varies fastest across lanes. SLAB (cluster
+// instances): only the sites of this CTA's z-planes [cx.z0, cx.z1), i.e.
+// the partial xy marginal over those planes and the complete xz and yz lines
+// inside them (the other lines count 0).
+template <int L, bool PACK, bool SLAB = false>
+__device__ __forceinline__ void measure_marginals(const Smem &sm, const Ctx &cx, int j0, int nw)
+{
+    constexpr int LL = L * L;
+    const int RB = cx.RB;
+    {
         for (int id = threadIdx.x; id < 3 * LL * nw; id += blockDim.x) {
             const int jj = id % nw;
             const int rest = id / nw;
@@ -798,7 +828,14 @@ __device__ __forceinline__ void measure_step(const Smem &sm, const Ctx &cx, cons
                 step = 1;
             }
             uint32_t cnt = 0;
-            if constexpr (PACK) {  // q of the group's 4 slots: the two nibbles' xor
+            if constexpr (SLAB) {  // packed state, this CTA's planes only
+                const bool in = plane == 0 || (Bc >= cx.z0 && Bc < cx.z1);
+                const int m0 = plane == 0 ? cx.z0 : 0, m1 = !in ? 0 : plane == 0 ? cx.z1 : L;
+                for (int m = m0; m < m1; ++m) {
+                    const uint32_t b = sm.spins[(size_t)(base + m * step) * RB + j0 + jj];
+                    cnt += expand4((b ^ (b >> 4)) & 15u);
+                }
+            } else if constexpr (PACK) {  // q of the group's 4 slots: the two nibbles' xor
 #pragma unroll 4
                 for (int m = 0; m < L; ++m) {
                     const uint32_t b = sm.spins[(size_t)(base + m * step) * RB + j0 + jj];
@@ -814,7 +851,20 @@ __device__ __forceinline__ void measure_step(const Smem &sm, const Ctx &cx, cons
             }
             sm.marg[(plane * LL + A * L + Bc) * nw + jj] = cnt;
         }
-        __syncthreads();
+    }
+}
+
+// (B) projections, FP32 DFT and FP64 accumulation of the words j0 .. j0 +
+// nw - 1 from the marginals in sm.marg.
+template <int L>
+__device__ __forceinline__ void measure_projections(const Smem &sm, const Ctx &cx,
+                                                    const Int8Args &a, int bin, int j0, int nw)
+{
+    constexpr int LL = L * L;
+    const int nt = cx.nt;
+    const bool seg = a.n_seg > 1;
+    double *accs = a.acc + ((size_t)cx.s * a.n_bins + bin) * SG_NACC * nt;
+    {
         // (B) one warp per wave vector v (v = 0..8; the v = 0 warp also takes
         // Q, whose count is the sum of its phases). Lane = 4 * (word jj) +
         // part: the part counts its phases for the word's 4 slots at once,
@@ -906,10 +956,25 @@ __device__ __forceinline__ void measure_step(const Smem &sm, const Ctx &cx, cons
                 }
             }
         }
+    }
+}
+
+template <int L, bool PACK>
+__device__ __forceinline__ void measure_step(const Smem &sm, const Ctx &cx, const Int8Args &a,
+                                             int bin)
+{
+    // energies and magnetisations first, so that the projection phase reads
+    // nothing the next sweep overwrites
+    measure_energies(sm, cx, a, bin);
+    for (int j0 = 0; j0 < cx.WR; j0 += a.mchunk) {
+        const int nw = min(a.mchunk, cx.WR - j0);
+        measure_marginals<L, PACK>(sm, cx, j0, nw);
+        __syncthreads();
+        measure_projections<L>(sm, cx, a, bin, j0, nw);
         // the next chunk's marginals overwrite this chunk's; after the last
         // chunk the next sweep touches nothing this phase reads (spins, B and
         // M are not read here), so no barrier is needed
-        if (j0 + a.mchunk < WR) __syncthreads();
+        if (j0 + a.mchunk < cx.WR) __syncthreads();
     }
 }
 

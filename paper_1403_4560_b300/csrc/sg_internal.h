@@ -58,6 +58,7 @@ struct Int8Launch {
     size_t smem;
     bool gst;   // state kept in global memory (large L) instead of shared memory
     bool wide;  // shared-memory state, one CTA of up to 512 threads per SM (L = 10, 12)
+    int cluster;  // > 1: global-memory state, each sample swept by a cluster of this many CTAs
 };
 
 // Shared-memory bytes of the fused kernel, or 0 when the state does not fit
@@ -85,6 +86,15 @@ bool int8_gst_has(int L);
 cudaError_t int8_launch_gst(int L, bool gauss, const Int8Args &a, const Int8Launch &cfg,
                             cudaStream_t st);
 int int8_ctas_per_sm_gst(int L, bool gauss, int threads, size_t smem);
+// The cluster instances (one sample per thread-block cluster of k = 2, 4 or
+// 8 CTAs, each sweeping L/k z-planes of the packed global-memory state), for
+// L = 20, 24, 28, 32; in their own translation unit. cfg.grid must be a
+// multiple of cfg.cluster and L a multiple of it.
+bool int8_cluster_has(int L);
+cudaError_t int8_launch_cluster(int L, bool gauss, const Int8Args &a, const Int8Launch &cfg,
+                                cudaStream_t st);
+// Clusters of k CTAs that can be resident at once (0 if the shape cannot launch).
+int int8_active_clusters(int L, bool gauss, int threads, size_t smem, int k);
 // The wide shared-memory instances (one sample per SM with up to 512
 // threads), for the lattice sizes whose narrow instance is bounded at two
 // CTAs per SM; in their own translation unit.
