@@ -96,7 +96,7 @@ def lib():
         L.orc_delta_e.restype = f64
         L.orc_overlap.argtypes = [i32, P, P, P, P, P]
         L.orc_run.argtypes = [i32, i32, i32, f64, P, u64, i32, i32, i32, i64, i64, i64,
-                              i64, i64, i64, P, P, P, P, i32, P, P]
+                              i64, i64, i64, P, P, P, P, i32, P, P, i32]
         L.orc_run.restype = i32
         L.orc_exchange.argtypes = [i32, i32, i32, f64, P, u64, i64, i32, i64, i64, i64, P, P,
                                    P, P]
@@ -187,8 +187,14 @@ class State:
     """Host-side state of one oracle ensemble (canonical layouts)."""
 
     def __init__(self, L, T, h, gauss, seed, J, spins, rng_group=1, exchange_every=1,
-                 measure_every=1, n_therm=0, s_base=0, log_bins=1, pq_hist=False):
+                 measure_every=1, n_therm=0, s_base=0, log_bins=1, pq_hist=False,
+                 slot_shared=False):
         """Local sample k is the global sample s_base + k (its RNG key).
+
+        slot_shared: the temperature slots of a replica share each Metropolis
+        random word (the slot field of the counter is 0), as when the N_T
+        copies of a sample are packed in the bits of one word (methods
+        section, multispin coding).
 
         log_bins: accumulators per logarithmic sweep bin (acc then has shape
         [S][n_T][log_bins][40]; 1 keeps [S][n_T][40]). pq_hist: also count
@@ -203,6 +209,7 @@ class State:
         self.S = self.spins.shape[0]
         self.rng_group, self.exchange_every = rng_group, exchange_every
         self.measure_every, self.n_therm = measure_every, n_therm
+        self.slot_shared = bool(slot_shared)
         self.B = np.zeros((self.S, 2, self.nt), dtype=np.int64)
         self.M = np.zeros((self.S, 2, self.nt), dtype=np.int64)
         self.log_bins = int(log_bins)
@@ -226,7 +233,7 @@ class State:
                            self.rng_group, self.exchange_every, self.measure_every,
                            self.n_therm, self.sweeps_done, n_sweeps, self.s_base, a, b, _p(self.J),
                            _p(self.spins), _p(self.B), _p(self.M), self.log_bins, _p(self.acc),
-                           None if h is None else _p(h))
+                           None if h is None else _p(h), int(self.slot_shared))
             if rc != 0:
                 raise ValueError("oracle rejected its arguments")
             return h

@@ -311,6 +311,7 @@ void orc_overlap(int L, const int8_t *sa, const int8_t *sb, int64_t *Q_out,
 /* ---------------------------------------------------------------------- */
 typedef struct {
     int L, nt, gauss, rng_group, exchange_every, measure_every;
+    int slot_shared;       /* 1: the slots of a replica share each Metropolis word */
     int64_t n_therm;
     double h;
     uint64_t seed;
@@ -329,6 +330,11 @@ static void one_sweep_metropolis(const chain_params *cp, int64_t s, int64_t n,
         for (int r = 0; r < 2; ++r)
             for (int t = 0; t < nt; ++t) {
                 int8_t *cfg = sp + ((int64_t)r * nt + t) * N;
+                /* the slot field of the counter; with shared slot words every
+                 * temperature of the replica reads the word of slot 0, as the
+                 * N_T copies packed in the bits of one word share one random
+                 * number per site (methods section, multispin coding) */
+                uint32_t tw = cp->slot_shared ? 0u : (uint32_t)t;
                 for (int i = 0; i < N; ++i) {
                     int x, y, z;
                     coords_of(L, i, &x, &y, &z);
@@ -336,7 +342,7 @@ static void one_sweep_metropolis(const chain_params *cp, int64_t s, int64_t n,
                     int j = i >> 1;
                     uint32_t rnd = philox_lane(slo ^ TAG_MET, group, (uint32_t)(j >> 2),
                                                (uint32_t)n,
-                                               ((uint32_t)c << 24) | ((uint32_t)r << 16) | (uint32_t)t,
+                                               ((uint32_t)c << 24) | ((uint32_t)r << 16) | tw,
                                                shi, j & 3);
                     uint32_t thr = orc_site_threshold(L, cp->gauss, cp->h, cp->T[t],
                                                       cp->thr + (size_t)t * 14, J, cfg, i);
@@ -451,6 +457,7 @@ static void make_params(chain_params *cp, int L, int nt, int gauss, double h,
 {
     cp->L = L; cp->nt = nt; cp->gauss = gauss; cp->h = h; cp->T = T; cp->seed = seed;
     cp->rng_group = rng_group; cp->exchange_every = ee; cp->measure_every = me;
+    cp->slot_shared = 0;
     cp->n_therm = n_therm;
     orc_thresholds(h, T, nt, thr);
     for (int t = 0; t < nt; ++t)
@@ -467,14 +474,16 @@ static void make_params(chain_params *cp, int L, int nt, int gauss, double h,
  * (state after the last sweep); acc [S][nt][n_bins][40] in/out, a sweep's
  * measurement going to its logarithmic bin (n_bins = 1: one bin); hist
  * [nt][n_bins][N+1] in/out or NULL, summed over the samples run here (the
- * caller gives concurrent calls separate arrays).
+ * caller gives concurrent calls separate arrays). slot_shared: 0 = every
+ * (replica, slot) chain draws its own Metropolis words; 1 = the slots of a
+ * replica share them (the slot field of the counter is 0).
  * Returns 0, or -1 for invalid arguments.
  */
 int orc_run(int L, int nt, int gauss, double h, const double *T, uint64_t seed,
             int rng_group, int exchange_every, int measure_every, int64_t n_therm,
             int64_t sweep0, int64_t n_sweeps, int64_t s_base, int64_t s_begin, int64_t s_end,
             const float *J, int8_t *spins, int64_t *B, int64_t *M, int n_bins, double *acc,
-            uint64_t *hist)
+            uint64_t *hist, int slot_shared)
 {
     if (L < 2 || (L & 1) || nt < 1 || nt > 4096 || rng_group < 1 || measure_every < 1 ||
         exchange_every < 0 || n_bins < 1 || n_bins > 64)
@@ -485,6 +494,7 @@ int orc_run(int L, int nt, int gauss, double h, const double *T, uint64_t seed,
     chain_params cp;
     make_params(&cp, L, nt, gauss, h, T, seed, rng_group, exchange_every, measure_every,
                 n_therm, thr, db_f);
+    cp.slot_shared = slot_shared ? 1 : 0;
     for (int64_t s = s_begin; s < s_end; ++s) {
         const float *Js = J + s * 3 * (int64_t)N;
         int8_t *sp = spins + s * 2 * (int64_t)nt * N;

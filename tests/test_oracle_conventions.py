@@ -178,3 +178,58 @@ def test_metropolis_words_differ_between_colours_replicas_slots_and_sites():
     # samples of one RNG group share every Metropolis word
     grouped = _twins(L=L, rng_group=2)
     np.testing.assert_array_equal(grouped[0], grouped[1])
+
+
+def test_slot_shared_words_keep_the_slots_of_a_replica_together():
+    """Shared slot words (the N_T temperatures of a replica packed in the
+    bits of one word draw one random number per site; methods section,
+    multispin coding): chains of one replica at equal temperatures, started
+    equal, stay identical forever, while the two replicas (separate words)
+    still decorrelate and the stationary +1 fraction is unchanged."""
+    L, nt, S = 6, 4, 2
+    N = L ** 3
+    J = np.zeros((S, 3, N), dtype=np.float32)
+    s0 = np.ones((S, 2, nt, N), dtype=np.int8)
+    st = orc.State(L, np.full(nt, 1.0), 0.5, True, seed=9, J=J, spins=s0, exchange_every=0,
+                   slot_shared=True)
+    st.run(20)
+    sp = st.spins
+    for t in range(1, nt):
+        np.testing.assert_array_equal(sp[:, :, t], sp[:, :, 0])
+    p = 1.0 / (1.0 + np.exp(-1.0))
+    assert _agree(sp[:, 0], sp[:, 1]) < p * p + (1 - p) ** 2 + 0.12
+    assert _agree(sp[0], sp[1]) < p * p + (1 - p) ** 2 + 0.12
+    assert abs((sp > 0).mean() - p) < 0.06
+
+
+@pytest.mark.slow
+def test_shared_slot_words_bias_parallel_tempering():
+    """Why every chain draws its own Metropolis words. Packing the N_T
+    temperatures of a replica into the bits of one word and updating them
+    with one random number per site (the cheap reading of the methods
+    section's multispin coding) couples the slots' moves: each slot's sweep
+    still leaves its own Boltzmann law invariant, but the joint law of
+    neighbouring slots is no longer the product that the replica-exchange
+    rule assumes, and exchange then moves the slots' marginals away from
+    equilibrium. At L = 2 (exact enumeration), 96 chains over 2000 sweeps:
+    with independent words every temperature's energy agrees within 3
+    standard errors; with shared words at least one is off by more than 10."""
+    import math
+    import sys
+    import os
+    sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+    from paper_1403_4560_b300 import inputs
+    from test_oracle_model import _exact_l2
+    L, S, h = 2, 96, 0.3
+    T = inputs.geometric_ladder(0.5, 2.0, 4)
+    J, s0 = inputs.make_instance("pmj", L, S, len(T), seed=33, same_couplings=True)
+    exact = _exact_l2(J[0], h, T, False)
+    z = {}
+    for shared in (False, True):
+        st = orc.State(L, T, h, False, seed=77, J=J, spins=s0, n_therm=200, slot_shared=shared)
+        st.run(2200, threads=4)
+        tm = orc.thermal_means(st.acc, L)
+        z[shared] = [abs(tm["e1"][:, t].mean() - exact[t]["e"]) /
+                     (tm["e1"][:, t].std(ddof=1) / math.sqrt(S)) for t in range(len(T))]
+    assert max(z[False]) < 3.0, z[False]
+    assert max(z[True]) > 10.0, z[True]

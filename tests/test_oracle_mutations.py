@@ -59,15 +59,15 @@ MUTATIONS = [
      "double e = -((double)B[r * nt + t] * qJ - h * (double)M[r * nt + t]);",
      [MODEL + "::test_high_temperature_energy_follows_the_small_beta_expansion"]),
     ("Metropolis counter without the colour field",
-     "((uint32_t)c << 24) | ((uint32_t)r << 16) | (uint32_t)t,",
-     "((uint32_t)r << 16) | (uint32_t)t,",
+     "((uint32_t)c << 24) | ((uint32_t)r << 16) | tw,",
+     "((uint32_t)r << 16) | tw,",
      [CONV + "::test_metropolis_words_differ_between_colours_replicas_slots_and_sites"]),
     ("Metropolis word taken from lane 0 for all four sites of a counter",
      "shi, j & 3);", "shi, 0);",
      [CONV + "::test_metropolis_words_differ_between_colours_replicas_slots_and_sites"]),
     ("Metropolis counter without the replica field",
-     "((uint32_t)c << 24) | ((uint32_t)r << 16) | (uint32_t)t,",
-     "((uint32_t)c << 24) | (uint32_t)t,",
+     "((uint32_t)c << 24) | ((uint32_t)r << 16) | tw,",
+     "((uint32_t)c << 24) | tw,",
      [CONV + "::test_metropolis_words_differ_between_colours_replicas_slots_and_sites"]),
     ("exchange always offers the even pairs",
      "exchange_step(&cp, s_base + s, (int)(e & 1), (uint32_t)n,",
@@ -79,6 +79,9 @@ MUTATIONS = [
     ("initial spins drawn without the replica field",
      "((uint32_t)r << 16) | (uint32_t)t, 0u, shi,", "(uint32_t)t, 0u, shi,",
      [CONV + "::test_initial_spins_are_balanced_and_independent"]),
+    ("shared slot words keep the slot field",
+     "uint32_t tw = cp->slot_shared ? 0u : (uint32_t)t;", "uint32_t tw = (uint32_t)t;",
+     [CONV + "::test_slot_shared_words_keep_the_slots_of_a_replica_together"]),
     ("histogram counts disagreeing sites",
      "agree += s0[i] == s1[i];", "agree += s0[i] != s1[i];",
      [BINS + "::test_strong_field_low_temperature_concentrates_at_q_one"]),
