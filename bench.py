@@ -305,10 +305,10 @@ def extra_msc(sgmc, stream, torch, L=16, S=4096, T=None, h=0.1):
     return out
 
 
-def extra_int8(sgmc, stream, torch, L, S, T, h, dist="gauss", sweeps=32):
+def extra_int8(sgmc, stream, torch, L, S, T, h, dist="gauss", sweeps=32, **opt):
     """The fused int8 path on one ensemble (measurement every sweep), timed
     over `sweeps` sweeps after a warm-up launch."""
-    with sgmc.Ensemble(L, h, T, dist, S, 7, stream=stream, n_therm=0) as e:
+    with sgmc.Ensemble(L, h, T, dist, S, 7, stream=stream, n_therm=0, **opt) as e:
         e.sweep(4)
         torch.cuda.synchronize()
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
@@ -536,6 +536,14 @@ def main():
                   # the same geometry with Gaussian couplings on the int8 path
                   "int8_paper_L10_56T_gauss": extra_int8(sgmc, stream, torch, L=10, S=1184,
                                                          T=t_paper, h=0.1),
+                  # +-J at the same geometry: a byte per chain, and one bit per
+                  # chain swept bit-parallel (each chain its own random words)
+                  "int8_paper_L10_56T_pmj": extra_int8(sgmc, stream, torch, L=10, S=1184,
+                                                       T=t_paper, h=0.1, dist="pmj",
+                                                       state_mode=1),
+                  "bits_paper_L10_56T_pmj": extra_int8(sgmc, stream, torch, L=10, S=1184,
+                                                       T=t_paper, h=0.1, dist="pmj",
+                                                       state_mode=3),
                   "cluster": extra_cluster(sgmc, stream, torch),
                   "serving": extra_serving(stream)}
 

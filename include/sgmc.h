@@ -126,10 +126,19 @@ typedef struct {
                                   P(q) per slot and bin (sg_get_histogram)   */
     int32_t state_mode;        /* INT8 layout: where the sweep kernel keeps a
                                   sample's state: 0 = library choice (shared
-                                  memory when it fits), 1 = shared memory
+                                  memory when it fits; for +-J couplings one
+                                  bit per chain as in 3 at L >= 14, or at
+                                  L >= 10 with more than 16 temperatures,
+                                  where it measured faster), 1 = shared
+                                  memory, a byte per chain
                                   (SG_EUNSUPPORTED if it does not fit), 2 =
-                                  global memory (L >= 10). Results do not
-                                  depend on it.                              */
+                                  global memory (L >= 10), 3 = shared memory,
+                                  one bit per chain, swept bit-parallel
+                                  (+-J couplings, at most 64 temperatures,
+                                  L = 4..16 even; the paper's multispin
+                                  coding of a sample's replicas, each chain
+                                  still drawing its own random numbers).
+                                  Results do not depend on it.               */
     int32_t segments;          /* INT8 state in shared memory: each launch's
                                   sweeps are split into this many segments per
                                   sample, and the CTAs claim (segment, sample)

@@ -173,6 +173,27 @@ ArenaPlan plan_arena(int L, int nt, int Tp, int64_t S, bool gauss, bool msc, int
 }
 
 int pad_slots(int nt) { return (nt + 3) & ~3; }
+// Whether the +-J chains are kept one bit each in shared memory and swept
+// bit-parallel (sg_options.state_mode 3, or the library's choice where it
+// measured faster than a byte per chain on B300: L >= 14, or L >= 10 with
+// more than 16 temperatures; +-J, 1184 samples, attempts/ns byte -> bit:
+// L = 10, 24 / 56 T 395 -> 445 / 398 -> 480; L = 12, 24 / 56 T 435 -> 444 /
+// 433 -> 463; L = 14, 8 / 56 T 217 -> 259 / 398 -> 501; L = 16, 24 T 388 ->
+// 550; slower at L <= 8 and with 8 temperatures below L = 14). The random
+// numbers are the same either way, so results do not depend on it.
+bool use_bits(int L, int nt, sg_coupling dist, const sg_options &o)
+{
+    if (o.state_mode == 3) return true;
+    return o.state_mode == 0 && o.layout == SG_LAYOUT_INT8 && dist == SG_PM_J && nt <= 64 &&
+           int8_bits_has(L) && (L >= 14 || (L >= 10 && nt > 16));
+}
+
+// Slots as stored: 4-slot groups, or for the bit-parallel state whole 64-bit
+// words of a site row (32 slots of both replicas).
+int stored_slots(int L, int nt, sg_coupling dist, const sg_options &o)
+{
+    return use_bits(L, nt, dist, o) ? (nt + 31) & ~31 : pad_slots(nt);
+}
 
 // Autotuned launch shapes per problem shape (L, slots, distribution, mode).
 std::mutex g_tune_mu;
@@ -191,9 +212,9 @@ std::string tune_key(const sg_ensemble *e, const Int8Launch &c)
 // library picks the k in {2, 4, 8} (L % k == 0) with the most effective CTAs
 // S * k / ceil(S / C), the smallest on ties (fewer barriers and halo planes
 // per sweep), and only when that beats one CTA per sample. (B300, Gaussian,
-// 64 samples, 2 x 16 temperatures: k = 4 leaves a ragged second wave of 27
-// clusters and ran 179 / 231 attempts/ns at L = 24 / 32, against 148 / 159
-// with one CTA per sample.)
+// 64 samples, 2 x 16 temperatures, attempts/ns at L = 24 / 32: one CTA per
+// sample 148 / 158; k = 2 (74 resident clusters) 245 / 273; k = 4, whose 37
+// resident clusters leave a ragged second wave, 179 / 231.)
 sg_status configure_cluster(sg_ensemble *e, int64_t resident)
 {
     const int want = e->opt.cluster;
@@ -230,8 +251,41 @@ sg_status configure_cluster(sg_ensemble *e, int64_t resident)
 // thread keeps one (4-slot group, replica) pair for the whole half-sweep); among the candidates the
 // one with the best product of work balance and resident warps per SM wins,
 // then the largest measurement chunk that keeps that occupancy.
+// The bit-parallel instances: one warp per task (32 work items of one word
+// of the site row), at most 8 warps per CTA, so that small lattices run more
+// CTAs per SM rather than idle warps; the measurement chunk that keeps the
+// most CTAs per SM.
+sg_status configure_bits(sg_ensemble *e)
+{
+    const int L = e->L;
+    if (!int8_bits_has(L)) return fail(SG_EUNSUPPORTED, "no bit-parallel kernel for this lattice size");
+    const int items = (L * L * L / 2) / int8_site_run(L, false);
+    const int tasks = ((items + 31) / 32) * (e->Tp / 32);
+    const int t = 32 * std::min(tasks, 8);
+    int occ = 0, m_for = 0;
+    for (int m = e->Tp / 4; m >= 1; --m) {
+        const size_t smem = int8_smem_bytes_bits(L, e->Tp, m);
+        if (!smem) continue;
+        const int o = int8_ctas_per_sm_bits(L, t, smem);
+        if (o > occ) {
+            occ = o;
+            m_for = m;
+        }
+    }
+    if (!occ) return fail(SG_EUNSUPPORTED, "the bit-parallel state does not fit shared memory");
+    e->mchunk = m_for;
+    e->launch = Int8Launch{};
+    e->launch.threads = t;
+    e->launch.bits = true;
+    e->launch.cluster = 1;
+    e->launch.smem = int8_smem_bytes_bits(L, e->Tp, m_for);
+    e->launch.grid = (int)std::min<int64_t>(e->S, (int64_t)occ * e->num_sms);
+    return SG_OK;
+}
+
 sg_status configure_launch(sg_ensemble *e)
 {
+    if (use_bits(e->L, e->nt, e->gauss ? SG_GAUSS : SG_PM_J, e->opt)) return configure_bits(e);
     const int WR = e->Tp / 4;
     const int L = e->L;
     // shared-memory residency first; the global-memory variant when the
@@ -316,6 +370,7 @@ sg_status configure_launch(sg_ensemble *e)
         e->launch.threads = best_t;
         e->launch.gst = gst;
         e->launch.wide = best_wide;
+        e->launch.bits = false;
         e->launch.cluster = 1;
         e->launch.smem = int8_smem_bytes(L, e->Tp, e->gauss, best_m, gst);
         const int64_t resident = (int64_t)best_occ * e->num_sms;
@@ -493,7 +548,10 @@ sg_status validate(int L, const double *T, int nt, sg_coupling dist, int64_t S,
     if (o.sample_base < 0 || o.sample_base + S > ((int64_t)1 << 32))
         return fail(SG_EINVAL, "sample_base + n_samples must be in [0, 2^32]");
     if (o.log_bins < 0 || o.log_bins > 64) return fail(SG_EINVAL, "log_bins must be in [0, 64]");
-    if (o.state_mode < 0 || o.state_mode > 2) return fail(SG_EINVAL, "state_mode must be 0, 1 or 2");
+    if (o.state_mode < 0 || o.state_mode > 3) return fail(SG_EINVAL, "state_mode must be 0, 1, 2 or 3");
+    if (o.state_mode == 3 && (o.layout != SG_LAYOUT_INT8 || dist != SG_PM_J || nt > 64))
+        return fail(SG_EINVAL, "state_mode 3 (bit-parallel) needs the INT8 layout, +-J couplings "
+                               "and at most 64 temperatures");
     if (o.segments < 0) return fail(SG_EINVAL, "segments must be >= 0");
     if (o.cluster < 0 || o.cluster == 3 || (o.cluster > 4 && o.cluster != 8))
         return fail(SG_EINVAL, "cluster must be 0, 1, 2, 4 or 8");
@@ -547,9 +605,10 @@ size_t sg_ensemble_bytes(int L, int nt, int64_t S, sg_coupling dist, const sg_op
     for (size_t k = 0; k < T.size(); ++k) T[k] = 1.0 + (double)k;
     if (validate(L, T.data(), nt, dist, S, o) != SG_OK) return 0;
     const bool msc = o.layout == SG_LAYOUT_MSC64;
-    const int Tp = msc ? nt : pad_slots(nt);
-    // the global-memory instances (packed state) serve what shared memory cannot hold
-    const bool packed = !msc && (o.state_mode == 2 ||
+    const int Tp = msc ? nt : stored_slots(L, nt, dist, o);
+    // the global-memory instances (packed state) serve what shared memory
+    // cannot hold; the bit-parallel ones keep the packed state too
+    const bool packed = !msc && (o.state_mode >= 2 || use_bits(L, nt, dist, o) ||
                                  (o.state_mode == 0 && !int8_smem_bytes(L, Tp, dist == SG_GAUSS, 1, false)));
     return plan_arena(L, nt, Tp, S, dist == SG_GAUSS, msc, bins_of(o), o.pq_hist != 0, packed).total;
 }
@@ -588,7 +647,7 @@ sg_status sg_create_ensemble(int L, double h, const double *T, int nt, sg_coupli
     e->L = L;
     e->nt = nt;
     e->msc = o.layout == SG_LAYOUT_MSC64;
-    e->Tp = e->msc ? nt : pad_slots(nt);  // MSC: B and M are [S][2][nt]
+    e->Tp = e->msc ? nt : stored_slots(L, nt, dist, o);  // MSC: B and M are [S][2][nt]
     if (e->msc) o.rng_group = 64;         // the 64 samples of a word share Metropolis numbers
     e->layout = o.layout;
     e->gauss = gauss;
@@ -609,10 +668,11 @@ sg_status sg_create_ensemble(int L, double h, const double *T, int nt, sg_coupli
     if (!e->msc && (st = configure_launch(e)) != SG_OK) return bail(st);
 
     e->n_bins = bins_of(o);
+    const bool packed = !e->msc && (e->launch.gst || e->launch.bits);
     const ArenaPlan p = plan_arena(L, nt, e->Tp, S, gauss, e->msc, e->n_bins, o.pq_hist != 0,
-                                   !e->msc && e->launch.gst);
+                                   packed);
     e->spins_bytes = e->msc ? (size_t)(S / 64) * nt * 2 * N * 8
-                            : (size_t)S * N * (e->launch.gst ? e->Tp / 4 : 2 * e->Tp);
+                            : (size_t)S * N * (packed ? e->Tp / 4 : 2 * e->Tp);
     ce = cudaMalloc(&e->arena, p.total);
     if (ce != cudaSuccess) return bail(cuda_fail(ce, "cudaMalloc(ensemble)"));
     e->bytes = p.total;
@@ -796,6 +856,13 @@ static unsigned long long segment_wait_cycles(const sg_ensemble *e, int n_sweeps
     return std::min(std::max(want, 1ull << 24), 1ull << 30);
 }
 
+// Whether the next n sweeps of e (global indices sweeps_done ..) are all
+// before n_therm, i.e. none is measured.
+static bool msc_thermalising(const sg_ensemble *e, int64_t n)
+{
+    return e->sweeps_done + n <= e->opt.n_therm;
+}
+
 static sg_status launch_sweeps(sg_ensemble *e, int64_t n, cudaStream_t s, bool device_counter)
 {
     if (e->msc) {
@@ -803,9 +870,10 @@ static sg_status launch_sweeps(sg_ensemble *e, int64_t n, cudaStream_t s, bool d
         MscArgs a = make_msc_args(e);
         if (device_counter) a.sweep0_dev = e->sweep_ctr;
         const int threads = msc_threads(e->L, e->opt.threads_per_block);
+        const bool split = msc_split(e->L, e->opt.threads_per_block) && msc_thermalising(e, n);
         for (int64_t k = 0; k < n; ++k) {
             a.sweep_offset = (int)k;
-            SG_CUDA(msc_sweep(a, e->L, threads, s), "MSC sweep kernel launch");
+            SG_CUDA(msc_sweep(a, e->L, threads, s, split), "MSC sweep kernel launch");
         }
         if (device_counter) SG_CUDA(advance_counter(e->sweep_ctr, n, s), "counter");
         return SG_OK;
@@ -869,10 +937,13 @@ sg_status sg_sweep_batch(sg_ensemble *const *es, int n_ens, int64_t n, int use_g
     }
     // graph path: the sweep index comes from a device counter, so one
     // instantiated graph serves every call with the same ensembles and n
+    // the key holds each ensemble's kernel choice that depends on the sweep
+    // index (multispin-coded launches without a measured sweep run split)
     std::string key = std::to_string(n);
     for (int k = 0; k < n_ens; ++k) {
-        char buf[32];
-        std::snprintf(buf, sizeof buf, ":%p", (void *)es[k]);
+        char buf[40];
+        std::snprintf(buf, sizeof buf, ":%p%s", (void *)es[k],
+                      es[k]->msc && msc_thermalising(es[k], n) ? "t" : "");
         key += buf;
     }
     cudaGraphExec_t exec = nullptr;
@@ -1243,6 +1314,8 @@ sg_status sg_get_info(const sg_ensemble *e, sg_info *out)
     out->log_bins = e->n_bins;
     out->pq_hist = e->hist ? 1 : 0;
     if (e->msc) {
+        // the measuring (fused) shape; thermalising launches of L >= 12 run
+        // split by replica (sg_launch_plan)
         out->threads_per_block = msc_threads(e->L, e->opt.threads_per_block);
         out->grid = (e->nt / 2 + 1) * (int32_t)(e->S / 64);
         out->state_in_shared = 1;
@@ -1261,7 +1334,8 @@ sg_status sg_launch_plan(const sg_ensemble *e, int64_t n_sweeps, int32_t *grid, 
     if (!e || n_sweeps < 0) return fail(SG_EINVAL, "bad arguments");
     int g = 0, seg = 1, nl = 0;
     if (e->msc) {
-        g = (e->nt / 2 + 1) * (int)(e->S / 64);
+        const bool split = msc_split(e->L, e->opt.threads_per_block) && msc_thermalising(e, n_sweeps);
+        g = (e->nt / 2 + 1) * (int)(e->S / 64) * (split ? 2 : 1);
         nl = (int)std::min<int64_t>(n_sweeps, INT32_MAX);
     } else if (n_sweeps > 0) {
         int64_t chunk = e->opt.sweeps_per_launch > 0 ? e->opt.sweeps_per_launch : n_sweeps;
@@ -1343,11 +1417,13 @@ sg_status sg_autotune(sg_ensemble *e, int64_t trial_sweeps, sg_tune_report *rep)
         const sg_options orig = e->opt;
         const int64_t done0 = e->sweeps_done;
         double best = 1e300, def = 0.0;
-        int best_t = msc_threads(e->L, 0), nc = 0;
+        // candidates: the library choice (0: split by replica for L >= 12),
+        // then fused CTAs of 128, 256 and 512 threads
+        int best_t = 0, nc = 0;
         cudaError_t ce = save(false);
-        const int cands[3] = {msc_threads(e->L, 0), 128, 512};
-        for (int c = 0; c < 3 && ce == cudaSuccess; ++c) {
-            if (c > 0 && cands[c] == cands[0]) continue;
+        const int cands[4] = {0, 128, 256, 512};
+        for (int c = 0; c < 4 && ce == cudaSuccess; ++c) {
+            if (c > 0 && !msc_split(e->L, 0) && cands[c] == msc_threads(e->L, 0)) continue;
             e->opt.threads_per_block = cands[c];
             if (launch_sweeps(e, 1, e->stream, false) != SG_OK) break;  // warm-up
             cudaEventRecord(e0, e->stream);
@@ -1372,15 +1448,15 @@ sg_status sg_autotune(sg_ensemble *e, int64_t trial_sweeps, sg_tune_report *rep)
         e->opt = orig;
         e->sweeps_done = done0;
         if (ce != cudaSuccess) return cuda_fail(ce, "autotune");
-        e->opt.threads_per_block = best_t;
-        r.threads_per_block = best_t;
+        e->opt.threads_per_block = best_t;  // 0: the library's choice
+        r.threads_per_block = best_t ? best_t : msc_threads(e->L, 0);
         r.n_candidates = nc;
         r.best_ms_per_sweep = best;
         r.default_ms_per_sweep = def;
         if (rep) *rep = r;
         return SG_OK;
     }
-    if (e->launch.cluster > 1) {  // the cluster shape is fixed: report it, time nothing
+    if (e->launch.cluster > 1 || e->launch.bits) {  // a fixed shape: report it, time nothing
         r.threads_per_block = e->launch.threads;
         r.mchunk = e->mchunk;
         r.n_candidates = 1;

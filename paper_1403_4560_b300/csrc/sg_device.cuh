@@ -120,4 +120,37 @@ __device__ __forceinline__ int log_bin(int64_t n, int n_bins)
     return b < n_bins - 1 ? b : n_bins - 1;
 }
 
+// Bit-sliced ripple add of a K-plane number into a D-plane counter (64
+// independent lanes, plane k holding bit k of every lane's count).
+template <int D, int K>
+__device__ __forceinline__ void bs_add(uint64_t (&c)[D], const uint64_t (&x)[K])
+{
+    uint64_t carry = 0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        const uint64_t a = c[k];
+        const uint64_t b = k < K ? x[k] : 0ull;
+        c[k] = a ^ b ^ carry;
+        carry = (a & b) | (carry & (a ^ b));
+    }
+}
+
+// 32x32 bit transpose across a warp by five shuffle stages: afterwards bit k
+// of lane l's word is bit l of lane k's word before.
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x)
+{
+    const int lane = threadIdx.x & 31;
+    uint32_t m = 0x0000FFFFu;
+#pragma unroll
+    for (int k = 16; k >= 1; k >>= 1, m ^= m << k) {
+        const uint32_t y = __shfl_xor_sync(0xFFFFFFFFu, x, k);
+        x = (lane & k) ? ((x & ~m) | ((y & ~m) >> k)) : ((x & m) | ((y & m) << k));
+    }
+    return x;
+}
+
+// Column counts over the 32 lanes of a warp: lane l receives the number of
+// lanes whose word has bit l set.
+__device__ __forceinline__ int warp_column_popc(uint32_t x) { return __popc(warp_transpose32(x)); }
+
 }  // namespace sg

@@ -45,6 +45,7 @@ namespace {
 
 
 constexpr int kMaxThreads = 512;
+constexpr int kBitsThreads = 256;  // bit-parallel instances: up to 8 warps, 2 CTAs per SM
 // colour sites per work item of the shared-memory half-sweep
 constexpr int kSiteRun = 4;
 
@@ -150,8 +151,9 @@ __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t
 // Carve the dynamic shared memory; returns the bytes used.
 // gst: the sample's spins and couplings stay in global memory (large L);
 // only the small tables are carved.
+// bits: the packed state (one bit per chain) held in shared memory.
 __host__ __device__ inline size_t carve(uint8_t *base, int L, int Tp, bool gauss, int mchunk,
-                                        Smem *sm, bool gst = false)
+                                        Smem *sm, bool gst = false, bool bits = false)
 {
     const size_t N = (size_t)L * L * L;
     size_t off = 0;
@@ -161,7 +163,7 @@ __host__ __device__ inline size_t carve(uint8_t *base, int L, int Tp, bool gauss
         return p;
     };
     Smem s;
-    s.spins = gst ? nullptr : take(N * 2 * Tp);
+    s.spins = gst ? nullptr : take(bits ? N * (Tp / 4) : N * 2 * Tp);
     s.J8 = (gauss || gst) ? nullptr : take(N * 8);
     s.Jg = (gauss && !gst) ? reinterpret_cast<float *>(take(N * 3 * sizeof(float))) : nullptr;
     s.thr = gauss ? nullptr : reinterpret_cast<uint32_t *>(take((size_t)Tp * 16 * 4));
@@ -586,6 +588,168 @@ __device__ __forceinline__ void half_sweep_packed(const Smem &sm, const Ctx &cx,
 }
 
 // ---------------------------------------------------------------------------
+// Half-sweep of colour COL on the packed state held in shared memory, bit
+// parallel (+-J; the paper's multispin coding of one sample's replicas,
+// methods section). The site row is read as 64-bit words: word w holds
+// the 4-slot groups 8w .. 8w + 7, i.e. slots 32w .. 32w + 31 of both
+// replicas, one bit per chain (bit 8g + 4r + k = replica r, slot 4(8w + g)
+// + k). For a site the unsatisfied-bond count of all 64 chains is one
+// bit-sliced 3-bit add of the six words s ^ s_nb ^ J; then every chain draws
+// its own Metropolis word (the random-number layout of half_sweep: Philox
+// counter (site group, sweep, colour | replica | slot), lane = site of the
+// group) and is accepted iff r <= thr[t][sb][u], the class (sb, u) read off
+// the bit planes. Chains never share a random word: sharing one among the
+// temperatures of a replica would couple the slots and bias the replica
+// exchange.
+// Work: a warp task is 32 work items (4 consecutive colour sites each) of
+// one word w, so that the lanes' per-chain energy counts (bit-sliced, per
+// item) reduce by warp transposes; the host sizes the CTA to the number of
+// tasks (at most 8 warps), so small lattices run more, smaller CTAs per SM.
+// (Splitting a word's chains over several warps, which then combine their
+// flips with shared-memory atomics, measured slower on B300: L = 10, 24
+// temperatures 409 -> 362 attempts/ns, L = 12, 56 temperatures 462 -> 300.)
+// For COL == 1 the bond sums and magnetisations of the post-sweep
+// configuration go to sm.B and sm.M, which start the half-sweep at 3N and N
+// (each of the N/2 colour-1 sites gives 6 - 2 u; its x-pair gives 2 - 2 n(-1)).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t lds64(const uint8_t *base, int off)
+{
+    return *reinterpret_cast<const uint64_t *>(base + off);
+}
+
+template <int L>
+__device__ __forceinline__ void half_sweep_bits(const Smem &sm, const Ctx &cx, uint32_t n_sweep,
+                                                const int COL)
+{
+    constexpr int N = L * L * L;
+    constexpr int U = (N / 2) / kSiteRun;
+    constexpr int NUB = (U + 31) / 32;  // blocks of 32 work items
+    constexpr int DU = 5, DM = 4;       // counter planes: per item at most 24 and 8
+    const int RB = cx.RB;               // bytes per site, a multiple of 8
+    const int NW = RB >> 3;             // 64-bit words per site
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nwarp = blockDim.x >> 5;
+    const int nt = cx.nt;
+    for (int tk = warp; tk < NUB * NW; tk += nwarp) {
+        const int ub = tk / NW, w = tk % NW;
+        const int u = ub * 32 + lane;
+        uint64_t cu[DU], cm[DM];
+#pragma unroll
+        for (int k = 0; k < DU; ++k) cu[k] = 0;
+#pragma unroll
+        for (int k = 0; k < DM; ++k) cm[k] = 0;
+        if (u < U) {
+            uint64_t s[4], u0[4], u1[4], u2[4], part[4];
+            int own[4];
+#pragma unroll
+            for (int l = 0; l < 4; ++l) {
+                const SiteNb<L> st(u * kSiteRun + l, COL);
+                own[l] = st.i * RB + 8 * w;
+                s[l] = lds64(sm.spins, own[l]);
+                const uint64_t nxp = lds64(sm.spins, own[l] + st.dxp * RB);
+                const uint64_t nxm = lds64(sm.spins, own[l] + st.dxm * RB);
+                const uint64_t nyp = lds64(sm.spins, own[l] + st.dyp * RB);
+                const uint64_t nym = lds64(sm.spins, own[l] + st.dym * RB);
+                const uint64_t nzp = lds64(sm.spins, own[l] + st.dzp * RB);
+                const uint64_t nzm = lds64(sm.spins, own[l] + st.dzm * RB);
+                const uint2 jb = *reinterpret_cast<const uint2 *>(sm.J8 + 8 * st.i);
+                // bond bit 1 (J = -1) -> all-ones mask
+                auto jm = [](uint32_t word, int byte) {
+                    return (uint64_t)0 - (uint64_t)((word >> (8 * byte)) & 1u);
+                };
+                const uint64_t d0 = s[l] ^ nxp ^ jm(jb.x, 0), d1 = s[l] ^ nxm ^ jm(jb.x, 1);
+                const uint64_t d2 = s[l] ^ nyp ^ jm(jb.x, 2), d3 = s[l] ^ nym ^ jm(jb.x, 3);
+                const uint64_t d4 = s[l] ^ nzp ^ jm(jb.y, 0), d5 = s[l] ^ nzm ^ jm(jb.y, 1);
+                // u = number of unsatisfied bonds: two full adders and a carry merge
+                const uint64_t sa = d0 ^ d1 ^ d2, ca = (d0 & d1) | (d2 & (d0 ^ d1));
+                const uint64_t sb = d3 ^ d4 ^ d5, cb = (d3 & d4) | (d5 & (d3 ^ d4));
+                u0[l] = sa ^ sb;
+                const uint64_t cc = sa & sb;
+                u1[l] = ca ^ cb ^ cc;
+                u2[l] = (ca & cb) | (cc & (ca ^ cb));
+                part[l] = (st.x & 1) ? nxm : nxp;
+            }
+            uint64_t fl[4] = {0, 0, 0, 0};
+            for (int g = 0; g < 8; ++g) {
+                const int j = 8 * w + g;  // 4-slot group
+                if (4 * j >= nt) break;   // padding groups (the same for the whole warp)
+                // per site, the group's class planes as bytes: s | u2 | u1 | u0
+                uint32_t X[4];
+#pragma unroll
+                for (int l = 0; l < 4; ++l) {
+                    const int sh = 8 * g;
+                    const uint32_t bs = (uint32_t)(s[l] >> sh) & 0xFFu;
+                    const uint32_t b2 = (uint32_t)(u2[l] >> sh) & 0xFFu;
+                    const uint32_t b1 = (uint32_t)(u1[l] >> sh) & 0xFFu;
+                    const uint32_t b0 = (uint32_t)(u0[l] >> sh) & 0xFFu;
+                    X[l] = bs | (b2 << 8) | (b1 << 16) | (b0 << 24);
+                }
+                uint32_t fb[4] = {0, 0, 0, 0};
+#pragma unroll
+                for (int k8 = 0; k8 < 8; ++k8) {
+                    const int t = 4 * j + (k8 & 3), r = k8 >> 2;
+                    if (t >= nt) continue;  // padding slots: never flipped
+                    const uint32_t c2 = ((uint32_t)COL << 24) | ((uint32_t)r << 16) | (uint32_t)t;
+                    const u32x4 o = philox10(cx.k0, cx.k1, (uint32_t)u, n_sweep, c2, cx.seed_hi);
+                    const uint32_t *thr_t = sm.thr + t * 16;
+#pragma unroll
+                    for (int l = 0; l < 4; ++l) {
+                        // bit k8 of the four planes gathered into the class
+                        // index sb * 8 + u: the four bits sit in bit 0 of the
+                        // bytes, and one product moves them to bits 27..24
+                        // (no other partial product reaches those bits)
+                        const uint32_t v = (X[l] >> k8) & 0x01010101u;
+                        const uint32_t idx = (v * 0x08040201u) >> 24;
+                        fb[l] |= (uint32_t)(o.v[l] <= thr_t[idx]) << k8;
+                    }
+                }
+#pragma unroll
+                for (int l = 0; l < 4; ++l) fl[l] |= (uint64_t)fb[l] << (8 * g);
+            }
+#pragma unroll
+            for (int l = 0; l < 4; ++l) {
+                const uint64_t sn = s[l] ^ fl[l];
+                *reinterpret_cast<uint64_t *>(sm.spins + own[l]) = sn;
+                if (COL == 1) {
+                    // unsatisfied bonds after the flip: 6 - u where flipped
+                    const uint64_t f = fl[l];
+                    const uint64_t n1b = ~(u1[l] ^ u0[l]);
+                    const uint64_t n2b = ~u2[l] & ~(u1[l] & u0[l]);
+                    const uint64_t un[3] = {u0[l], (u1[l] & ~f) | (n1b & f), (u2[l] & ~f) | (n2b & f)};
+                    bs_add<DU, 3>(cu, un);
+                    const uint64_t mm[2] = {sn ^ part[l], sn & part[l]};
+                    bs_add<DM, 2>(cm, mm);
+                }
+            }
+        }
+        if (COL == 1) {
+            // per chain, the warp's counts: transposes hand lane b the counts
+            // of chain bits b (low word) and 32 + b (high word)
+            long long vu[2] = {0, 0}, vm[2] = {0, 0};
+#pragma unroll
+            for (int k = 0; k < DU; ++k) {
+                vu[0] += (long long)warp_column_popc((uint32_t)cu[k]) << k;
+                vu[1] += (long long)warp_column_popc((uint32_t)(cu[k] >> 32)) << k;
+            }
+#pragma unroll
+            for (int k = 0; k < DM; ++k) {
+                vm[0] += (long long)warp_column_popc((uint32_t)cm[k]) << k;
+                vm[1] += (long long)warp_column_popc((uint32_t)(cm[k] >> 32)) << k;
+            }
+#pragma unroll
+            for (int hf = 0; hf < 2; ++hf) {
+                const int b = 32 * hf + lane;
+                const int t = 4 * (8 * w + (b >> 3)) + (b & 3), r = (b >> 2) & 1;
+                if (t < nt) {
+                    atomicAdd(&sm.B[r * cx.Tp + t], (unsigned long long)(-2 * vu[hf]));
+                    atomicAdd(&sm.M[r * cx.Tp + t], (unsigned long long)(-2 * vm[hf]));
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Replica exchange between slots p and p+1 of each replica (pairs of one
 // parity), then the state swap of accepted pairs as byte permutations of the
 // 4-slot words. stamp identifies this exchange in xflag.
@@ -999,19 +1163,27 @@ __device__ __forceinline__ void copy16_cg(void *dst, const void *src, size_t byt
 // The fused kernel: for each sample of this CTA, load, run n_sweeps sweeps
 // (half-sweeps, energies, exchange, measurement), store.
 // ---------------------------------------------------------------------------
-template <int L, bool GAUSS, bool GST, bool WIDE = false>
-__global__ void __launch_bounds__(KernelBounds<L, GST, WIDE>::threads,
-                                  KernelBounds<L, GST, WIDE>::min_blocks)
+// BITS: the packed state in shared memory, swept bit-parallel (+-J).
+template <int L, bool GST, bool WIDE, bool BITS>
+struct Bounds {
+    static constexpr int threads = BITS ? kBitsThreads : KernelBounds<L, GST, WIDE>::threads;
+    static constexpr int min_blocks = BITS ? 2 : KernelBounds<L, GST, WIDE>::min_blocks;
+};
+
+template <int L, bool GAUSS, bool GST, bool WIDE = false, bool BITS = false>
+__global__ void __launch_bounds__(Bounds<L, GST, WIDE, BITS>::threads,
+                                  Bounds<L, GST, WIDE, BITS>::min_blocks)
     int8_run_kernel(const Int8Args a)
 {
     constexpr int N = L * L * L;
     extern __shared__ __align__(16) uint8_t smem_raw[];
     Smem sm;
-    carve(smem_raw, L, a.Tp, GAUSS, a.mchunk, &sm, GST);
+    carve(smem_raw, L, a.Tp, GAUSS, a.mchunk, &sm, GST, BITS);
     Ctx cx;
     cx.nt = a.nt;
     cx.Tp = a.Tp;
-    constexpr bool PACK = GST;  // global-memory instances keep the packed state
+    // global-memory instances and the bit-parallel ones keep the packed state
+    constexpr bool PACK = GST || BITS;
     cx.WR = a.Tp / 4;
     cx.RB = PACK ? a.Tp / 4 : 2 * a.Tp;
     cx.seed_lo = a.seed_lo;
@@ -1119,18 +1291,20 @@ __global__ void __launch_bounds__(KernelBounds<L, GST, WIDE>::threads,
                 if (stop) break;
             }
             auto colour = [&](const int col) {
-                if constexpr (PACK)
+                if constexpr (BITS)
+                    half_sweep_bits<L>(sm, cx, (uint32_t)n, col);
+                else if constexpr (PACK)
                     half_sweep_packed<L, GAUSS>(sm, cx, (uint32_t)n, col);
                 else
                     half_sweep<L, GAUSS>(sm, cx, (uint32_t)n, col);
-                if (col == 0)
+                if (col == 0)  // the bit-parallel sweep subtracts from 3N and N
                     for (int k = threadIdx.x; k < 2 * a.Tp; k += blockDim.x) {
-                        sm.B[k] = 0;
-                        sm.M[k] = 0;
+                        sm.B[k] = BITS ? 3ull * N : 0ull;
+                        sm.M[k] = BITS ? (unsigned long long)N : 0ull;
                     }
                 __syncthreads();
             };
-            if constexpr (unroll_colours<L, GAUSS, GST, WIDE>()) {
+            if constexpr (BITS || unroll_colours<L, GAUSS, GST, WIDE>()) {
                 colour(0);
                 colour(1);
             } else {
@@ -1172,28 +1346,29 @@ __global__ void __launch_bounds__(KernelBounds<L, GST, WIDE>::threads,
 constexpr int kMaxSmem = 227 * 1024;
 
 // Raise the kernel's dynamic shared-memory limit once (before any capture).
-template <int L, bool G, bool GST, bool WIDE = false>
+template <int L, bool G, bool GST, bool WIDE = false, bool BITS = false>
 cudaError_t ensure_attr()
 {
-    static cudaError_t done = cudaFuncSetAttribute(
-        int8_run_kernel<L, G, GST, WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+    static cudaError_t done = cudaFuncSetAttribute(int8_run_kernel<L, G, GST, WIDE, BITS>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   kMaxSmem);
     return done;
 }
 
-template <int L, bool G, bool GST, bool WIDE = false>
+template <int L, bool G, bool GST, bool WIDE = false, bool BITS = false>
 cudaError_t launch_t(const Int8Args &a, const Int8Launch &c, cudaStream_t st)
 {
-    cudaError_t e = ensure_attr<L, G, GST, WIDE>();
+    cudaError_t e = ensure_attr<L, G, GST, WIDE, BITS>();
     if (e != cudaSuccess) return e;
-    int8_run_kernel<L, G, GST, WIDE><<<c.grid, c.threads, c.smem, st>>>(a);
+    int8_run_kernel<L, G, GST, WIDE, BITS><<<c.grid, c.threads, c.smem, st>>>(a);
     return cudaGetLastError();
 }
 
-template <int L, bool G, bool GST, bool WIDE = false>
+template <int L, bool G, bool GST, bool WIDE = false, bool BITS = false>
 int occ_t(int threads, size_t smem)
 {
-    auto k = int8_run_kernel<L, G, GST, WIDE>;
-    if (ensure_attr<L, G, GST, WIDE>() != cudaSuccess) return 0;
+    auto k = int8_run_kernel<L, G, GST, WIDE, BITS>;
+    if (ensure_attr<L, G, GST, WIDE, BITS>() != cudaSuccess) return 0;
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, threads, smem) != cudaSuccess)
         return 0;

@@ -34,19 +34,6 @@ constexpr int kDP = 9;  // bit planes of a projection (<= L^2 <= 256 sites)
 constexpr int kDG = 5;  // bit planes of a 2D marginal entry (<= L <= 16 sites)
 
 
-// Bit-sliced ripple add of a K-plane number into a D-plane counter.
-template <int D, int K>
-__device__ __forceinline__ void bs_add(uint64_t (&c)[D], const uint64_t (&x)[K])
-{
-    uint64_t carry = 0;
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-        const uint64_t a = c[k];
-        const uint64_t b = k < K ? x[k] : 0ull;
-        c[k] = a ^ b ^ carry;
-        carry = (a & b) | (carry & (a ^ b));
-    }
-}
 
 // Carry-save adder: three words in, their bitwise sum as (sum, carry).
 __device__ __forceinline__ void csa(uint64_t &h, uint64_t &l, uint64_t a, uint64_t b, uint64_t c)
@@ -85,23 +72,6 @@ __device__ __forceinline__ void count16(const uint64_t (&x)[16], uint64_t (&c)[5
     c[4] = e1 & e2;  // weight 16
 }
 
-// 32x32 bit transpose across a warp by five shuffle stages: afterwards bit k
-// of lane l's word is bit l of lane k's word before.
-__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x)
-{
-    const int lane = threadIdx.x & 31;
-    uint32_t m = 0x0000FFFFu;
-#pragma unroll
-    for (int k = 16; k >= 1; k >>= 1, m ^= m << k) {
-        const uint32_t y = __shfl_xor_sync(0xFFFFFFFFu, x, k);
-        x = (lane & k) ? ((x & ~m) | ((y & ~m) >> k)) : ((x & m) | ((y & m) << k));
-    }
-    return x;
-}
-
-// Column counts over the 32 lanes of a warp: lane l receives the number of
-// lanes whose word has bit l set.
-__device__ __forceinline__ int warp_column_popc(uint32_t x) { return __popc(warp_transpose32(x)); }
 
 // Small lattices keep the word group's couplings in shared memory too (loaded
 // once per launch): the four chain teams of a unit read each bond word six
@@ -246,16 +216,17 @@ struct MscSite {
 // and (-1)-spin counts of the post-sweep configuration into sm.B / sm.M
 // (raw counts; converted to B and M afterwards).
 // ---------------------------------------------------------------------------
+// w: the chain's words; thr: its slot's 16 thresholds; bm: its row of
+// sm.B / sm.M.
 template <int L>
-__device__ __forceinline__ void msc_half(const MscSmem &sm, const MscArgs &a, int g, int q, int t,
-                                         int r, int tpc, int c, uint32_t n_sweep)
+__device__ __forceinline__ void msc_half(const MscSmem &sm, const MscArgs &a, int g, uint64_t *w,
+                                         const uint32_t *thr, int bm, int t, int r, int tpc, int c,
+                                         uint32_t n_sweep)
 {
     constexpr int N = L * L * L;
     constexpr int NG = (N / 2) / 4;  // Philox groups of four colour-c sites
     const int tid = threadIdx.x % tpc;
-    uint64_t *w = sm.w + (size_t)q * N;
     const uint64_t *J = msc_j_shared(L) ? sm.J : a.Jw + (size_t)g * 3 * N;
-    const uint32_t *thr = sm.thr + (q >> 1) * 16;
     uint64_t cu[kDU], cm[kDM];
 #pragma unroll
     for (int k = 0; k < kDU; ++k) cu[k] = 0;
@@ -317,10 +288,10 @@ __device__ __forceinline__ void msc_half(const MscSmem &sm, const MscArgs &a, in
             vm_lo += (long long)warp_column_popc((uint32_t)cm[k]) << k;
             vm_hi += (long long)warp_column_popc((uint32_t)(cm[k] >> 32)) << k;
         }
-        atomicAdd((unsigned long long *)&sm.B[q * 64 + lane], (unsigned long long)vu_lo);
-        atomicAdd((unsigned long long *)&sm.B[q * 64 + 32 + lane], (unsigned long long)vu_hi);
-        atomicAdd((unsigned long long *)&sm.M[q * 64 + lane], (unsigned long long)vm_lo);
-        atomicAdd((unsigned long long *)&sm.M[q * 64 + 32 + lane], (unsigned long long)vm_hi);
+        atomicAdd((unsigned long long *)&sm.B[bm * 64 + lane], (unsigned long long)vu_lo);
+        atomicAdd((unsigned long long *)&sm.B[bm * 64 + 32 + lane], (unsigned long long)vu_hi);
+        atomicAdd((unsigned long long *)&sm.M[bm * 64 + lane], (unsigned long long)vm_lo);
+        atomicAdd((unsigned long long *)&sm.M[bm * 64 + 32 + lane], (unsigned long long)vm_hi);
     }
 }
 
@@ -378,8 +349,10 @@ __device__ __forceinline__ void msc_measure(const MscSmem &sm, const MscArgs &a,
     }
     __syncthreads();
     if constexpr (msc_proj_in_w(L, msc_measured_slots(L, WIDE))) {
-        // the chains are final: store them now, their space takes the projections
-        for (int k = threadIdx.x; k < nw; k += blockDim.x) w_dst[k] = sm.w[k];
+        // the chains are final: store them now (unless they are stored
+        // already), their space takes the projections
+        if (w_dst)
+            for (int k = threadIdx.x; k < nw; k += blockDim.x) w_dst[k] = sm.w[k];
         __syncthreads();
     }
     // (B) projection counts: sum of L marginal entries per (v, d)
@@ -528,7 +501,9 @@ __global__ void __launch_bounds__(MAXT, MINB) msc_sweep_kernel(const MscArgs a)
     const int tpc = blockDim.x / nq;  // threads per chain
     const int q = threadIdx.x / tpc;
     for (int c = 0; c < 2; ++c) {
-        if (q < nq) msc_half<L>(sm, a, g, q, t0 + (q >> 1), q & 1, tpc, c, (uint32_t)n);
+        if (q < nq)
+            msc_half<L>(sm, a, g, sm.w + (size_t)q * N, sm.thr + (q >> 1) * 16, q, t0 + (q >> 1),
+                        q & 1, tpc, c, (uint32_t)n);
         __syncthreads();
     }
     // raw counts -> B = 3N - 2 * (unsatisfied bonds), M = N - 2 * (#-1 spins)
@@ -597,6 +572,134 @@ __global__ void __launch_bounds__(MAXT, MINB) msc_sweep_kernel(const MscArgs a)
         const size_t o = ((size_t)s * 2 + (qq & 1)) * a.nt + t0 + (qq >> 1);
         a.B[o] = sm.B[k];
         a.M[o] = sm.M[k];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Thermalising sweeps of large lattices (L >= 12): the exchange unit split by
+// replica. A CTA holds one replica's chains of the unit (the sweep and the
+// exchange never mix replicas: methods section, each replica has its own
+// tempering ladder), so at L = 16 it needs 64 KB of shared memory instead of
+// 197 KB and three CTAs share an SM. It does not measure (the overlap needs
+// both replicas): the host uses it only for launches whose sweeps all lie
+// before n_therm. Same random numbers, decisions and order as
+// msc_sweep_kernel: the results are identical. (B300, +-J, 4096 samples,
+// 2 x 32 temperatures, thermalising attempts/ns fused -> split: L = 12
+// 2200 -> 2478, L = 14 2436 -> 2848, L = 16 2969 -> 3077; with a separate
+// measurement kernel after it, measuring sweeps ran up to 5 % slower than
+// the fused kernel, so those stay fused.)
+// ---------------------------------------------------------------------------
+constexpr int kMscSplitThreads = 256;
+
+__host__ __device__ inline size_t msc_carve_split(uint8_t *base, int L, MscSmem *sm)
+{
+    const size_t N = (size_t)L * L * L;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        uint8_t *p = base ? base + off : nullptr;
+        off = a16(off + bytes);
+        return p;
+    };
+    MscSmem s{};
+    s.w = reinterpret_cast<uint64_t *>(take(2 * N * 8));
+    s.J = nullptr;  // L >= 12: the couplings are read through L1
+    s.thr = reinterpret_cast<uint32_t *>(take(2 * 16 * 4));
+    s.B = reinterpret_cast<long long *>(take(2 * 64 * 8));
+    s.M = reinterpret_cast<long long *>(take(2 * 64 * 8));
+    s.swap = reinterpret_cast<uint64_t *>(take(2 * 8));
+    if (sm) *sm = s;
+    return off;
+}
+
+template <int L>
+__global__ void __launch_bounds__(kMscSplitThreads, 3) msc_split_sweep_kernel(const MscArgs a)
+{
+    static_assert(!msc_j_shared(L), "the split kernel reads the couplings through L1");
+    constexpr int N = L * L * L;
+    extern __shared__ __align__(16) uint8_t msc_smem[];
+    MscSmem sm;
+    msc_carve_split(msc_smem, L, &sm);
+    const int g = blockIdx.y, r = blockIdx.z;
+    const int64_t n = (a.sweep0_dev ? *a.sweep0_dev : a.sweep0) + a.sweep_offset;
+    const bool xchg = a.exchange_every > 0 && (n + 1) % a.exchange_every == 0;
+    const int par = xchg ? (int)(((n + 1) / a.exchange_every - 1) & 1) : 0;
+    int t0, cnt;
+    if (!unit_slots(blockIdx.x, par, a.nt, &t0, &cnt)) return;
+
+    // chain k of this CTA: slot t0 + k of replica r
+    for (int k = 0; k < cnt; ++k) {
+        const uint64_t *src = a.W + (((size_t)g * a.nt + t0 + k) * 2 + r) * N;
+        for (int i = threadIdx.x; i < N; i += blockDim.x) sm.w[(size_t)k * N + i] = src[i];
+    }
+    for (int k = threadIdx.x; k < cnt * 16; k += blockDim.x) sm.thr[k] = a.thr[t0 * 16 + k];
+    for (int k = threadIdx.x; k < 2 * 64; k += blockDim.x) {
+        sm.B[k] = 0;
+        sm.M[k] = 0;
+    }
+    if (threadIdx.x == 0) sm.swap[0] = 0;
+    __syncthreads();
+
+    const int tpc = blockDim.x / cnt;  // threads per chain: whole warps
+    const int k = threadIdx.x / tpc;
+    for (int c = 0; c < 2; ++c) {
+        if (k < cnt)
+            msc_half<L>(sm, a, g, sm.w + (size_t)k * N, sm.thr + k * 16, k, t0 + k, r, tpc, c,
+                        (uint32_t)n);
+        __syncthreads();
+    }
+    // raw counts -> B = 3N - 2 * (unsatisfied bonds), M = N - 2 * (#-1 spins)
+    for (int q = threadIdx.x; q < cnt * 64; q += blockDim.x) {
+        sm.B[q] = 3LL * N - 2 * sm.B[q];
+        sm.M[q] = (long long)N - 2 * sm.M[q];
+    }
+    __syncthreads();
+
+    if (xchg && cnt == 2) {
+        // one thread per sample: Metropolis on the pair (t0, t0 + 1) of replica r
+        if (threadIdx.x < 64) {
+            const int b = threadIdx.x;
+            const int64_t s = 64 * (int64_t)g + b;
+            const long long dB = sm.B[b] - sm.B[64 + b];
+            const long long dM = sm.M[b] - sm.M[64 + b];
+            const float t1 = __fmul_rn(__ll2float_rn(dB), 1.0f);
+            const float t2 = __fmul_rn(a.h_f, __ll2float_rn(dM));
+            const float dE = -__fadd_rn(t1, t2);
+            const float D = __fmul_rn(a.dbeta[t0], dE);
+            const u32x4 o = philox10(a.seed_lo ^ kTagExc, (uint32_t)(s + a.s_key0), (uint32_t)t0,
+                                     (uint32_t)n, (uint32_t)r, a.seed_hi);
+            const bool acc = (D >= 0.0f) || (o.v[0] <= thr_of_logp(D));
+            const unsigned bal = __ballot_sync(0xFFFFFFFFu, acc);
+            if ((threadIdx.x & 31) == 0)
+                atomicOr((unsigned long long *)&sm.swap[0], (unsigned long long)bal << (threadIdx.x & 32));
+            if (acc) {
+                const long long tb = sm.B[b];
+                sm.B[b] = sm.B[64 + b];
+                sm.B[64 + b] = tb;
+                const long long tm = sm.M[b];
+                sm.M[b] = sm.M[64 + b];
+                sm.M[64 + b] = tm;
+            }
+        }
+        __syncthreads();
+        const uint64_t m = sm.swap[0];
+        if (m)
+            for (int i = threadIdx.x; i < N; i += blockDim.x) {
+                const uint64_t x = (sm.w[i] ^ sm.w[N + i]) & m;
+                sm.w[i] ^= x;
+                sm.w[N + i] ^= x;
+            }
+        __syncthreads();
+    }
+    for (int kk = 0; kk < cnt; ++kk) {
+        uint64_t *dst = a.W + (((size_t)g * a.nt + t0 + kk) * 2 + r) * N;
+        for (int i = threadIdx.x; i < N; i += blockDim.x) dst[i] = sm.w[(size_t)kk * N + i];
+    }
+    for (int q = threadIdx.x; q < cnt * 64; q += blockDim.x) {
+        const int kk = q / 64, b = q % 64;
+        const int64_t s = 64 * (int64_t)g + b;
+        const size_t o = ((size_t)s * 2 + r) * a.nt + t0 + kk;
+        a.B[o] = sm.B[q];
+        a.M[o] = sm.M[q];
     }
 }
 
@@ -862,6 +965,21 @@ constexpr int kMscMaxSmem = 227 * 1024;
 constexpr int kMscNarrow = 128;
 
 template <int L>
+cudaError_t msc_split_launch_t(const MscArgs &a, cudaStream_t st)
+{
+    if constexpr (msc_j_shared(L)) {
+        return cudaErrorInvalidValue;
+    } else {
+        static cudaError_t attr_s = cudaFuncSetAttribute(
+            msc_split_sweep_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMscMaxSmem);
+        if (attr_s != cudaSuccess) return attr_s;
+        const dim3 grid((unsigned)(a.nt / 2 + 1), (unsigned)a.G, 2u);
+        msc_split_sweep_kernel<L><<<grid, kMscSplitThreads, msc_carve_split(nullptr, L, nullptr), st>>>(a);
+        return cudaGetLastError();
+    }
+}
+
+template <int L>
 cudaError_t msc_launch_t(const MscArgs &a, int threads, cudaStream_t st)
 {
     static cudaError_t attr_n = cudaFuncSetAttribute(
@@ -912,8 +1030,17 @@ int msc_threads(int L, int requested)
     return L <= 10 ? 128 : L == 12 ? 256 : kMscThreads;
 }
 
-cudaError_t msc_sweep(const MscArgs &a, int L, int threads, cudaStream_t st)
+bool msc_split(int L, int requested) { return requested <= 0 && L >= 12 && msc_supported_L(L); }
+int msc_split_threads() { return kMscSplitThreads; }
+
+cudaError_t msc_sweep(const MscArgs &a, int L, int threads, cudaStream_t st, bool split)
 {
+    if (split) {
+#define X(LL) if (L == LL) return msc_split_launch_t<LL>(a, st);
+        SG_MSC_FOR_EACH_L(X)
+#undef X
+        return cudaErrorInvalidValue;
+    }
     if (threads < 128 || threads > kMscThreads || (threads & 127)) return cudaErrorInvalidValue;
 #define X(LL) if (L == LL) return msc_launch_t<LL>(a, threads, st);
     SG_MSC_FOR_EACH_L(X)

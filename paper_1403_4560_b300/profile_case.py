@@ -32,6 +32,9 @@ def main():
     ap.add_argument("--n-therm", type=int, default=0)
     ap.add_argument("--exchange-every", type=int, default=1)
     ap.add_argument("--measure-every", type=int, default=1)
+    ap.add_argument("--state-mode", type=int, default=0)
+    ap.add_argument("--cluster", type=int, default=0)
+    ap.add_argument("--h", type=float, default=0.2)
     args = ap.parse_args()
 
     import torch
@@ -42,10 +45,11 @@ def main():
     J, s0 = inputs.make_instance(args.dist, args.L, args.samples, args.nt, seed=7)
     stream = torch.cuda.current_stream()
     opt = dict(threads_per_block=args.threads, layout=args.layout, n_therm=args.n_therm,
-               exchange_every=args.exchange_every, measure_every=args.measure_every)
+               exchange_every=args.exchange_every, measure_every=args.measure_every,
+               state_mode=args.state_mode, cluster=args.cluster)
     if args.layout == sgmc.SG_LAYOUT_MSC64:
         opt["rng_group"] = 64
-    with sgmc.Ensemble(args.L, 0.2, T, args.dist, args.samples, 7, J=J, spins=s0,
+    with sgmc.Ensemble(args.L, args.h, T, args.dist, args.samples, 7, J=J, spins=s0,
                        stream=stream, **opt) as ens:
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
         for c in range(args.chunks):
@@ -59,7 +63,8 @@ def main():
         print(json.dumps({"L": args.L, "dist": args.dist, "samples": args.samples,
                           "nt": args.nt, "sweeps": args.sweeps, "n_therm": args.n_therm,
                           "exchange_every": args.exchange_every,
-                          "threads": args.threads, "ms": ms,
+                          "threads": args.threads, "state_mode": args.state_mode,
+                          "ms": ms,
                           "attempts_per_ns": att / (ms * 1e6)}))
 
 

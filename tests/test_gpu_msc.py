@@ -185,3 +185,39 @@ def test_msc_autotune_changes_speed_not_results():
         np.testing.assert_array_equal(a.spins(), b.spins())
         np.testing.assert_array_equal(a.accumulators(), b.accumulators())
         assert a.sweeps_done == b.sweeps_done == 25
+
+
+@pytest.mark.parametrize("L,nt,ee,me,S", [(12, 5, 1, 1, 128), (14, 6, 2, 3, 64), (16, 4, 1, 1, 64),
+                                          (16, 3, 0, 2, 128)])
+def test_replica_split_sweep_equals_fused_kernel_and_oracle(L, nt, ee, me, S):
+    """At L >= 12 launches whose sweeps all thermalise run split by replica
+    (one replica's chains of an exchange unit per CTA); the measuring ones
+    run fused. A run of a thermalising then a measuring launch must equal the
+    fused kernel throughout (an explicit CTA size selects it) bit for bit,
+    through plain launches and a replayed CUDA graph (one graph per phase),
+    and the oracle on sample 0."""
+    T = inputs.geometric_ladder(0.4, 1.5, nt)
+    J, s0 = inputs.make_instance("pmj", L, S, nt, seed=300 + L + nt)
+    opt = dict(exchange_every=ee, measure_every=me, n_therm=9, log_bins=3, pq_hist=1)
+    outs = []
+    for tpb, graph in ((0, False), (0, True), (512, False)):
+        with sgmc.Ensemble(L, 0.2, T, "pmj", S, 4, J=J, spins=s0, threads_per_block=tpb, **MSC,
+                           **opt) as e:
+            split_grid = e.launch_plan(9)["grid"]
+            assert split_grid == (2 if tpb == 0 else 1) * e.info().grid
+            if graph:
+                sgmc.sweep_batch([e], 9, use_graph=True)
+                sgmc.sweep_batch([e], 9, use_graph=True)
+            else:
+                e.sweep(9)
+                e.sweep(9)
+            e.synchronize()
+            outs.append((e.spins(), e.energies()[0], e.energies()[1], e.accumulators(),
+                         e.histogram()))
+    for other in outs[1:]:
+        for a, b in zip(outs[0], other):
+            np.testing.assert_array_equal(a, b)
+    st = oracle_state(L, T, 0.2, 4, J[:1], s0[:1], exchange_every=ee, measure_every=me, n_therm=9)
+    st.run(18)
+    np.testing.assert_array_equal(outs[0][0][:1], st.spins)
+    np.testing.assert_array_equal(outs[0][1][:1], st.B)
