@@ -48,13 +48,13 @@ WORKLOAD = ("gaussian EA 3D, L=8 and 12 x h=0.1,0.2,0.3, 512 samples each, "
 # workload (L = 12, 512 samples, 256 sweeps), from the one-pass ncu capture
 # summarised under profiles/. Must be reset to
 # None whenever the kernel changes, until it is captured again.
-TRAFFIC_BYTES_PER_LAUNCH = 62.1e6
+TRAFFIC_BYTES_PER_LAUNCH = 62.0e6
 # Thread instructions per attempt of the same kernel in the same launch shape
 # (ncu smsp__thread_inst_executed.sum over the launch's attempts, captured on
 # the bench's own 512-sample, 256-sweep segmented launch;
 # its ncu summary is kept under profiles/). Reset to None whenever
 # the kernel changes, until it is captured again.
-INSTR_PER_ATTEMPT = 85.1
+INSTR_PER_ATTEMPT = 84.6
 # SM issue peak: 148 SMs x 4 schedulers x 1 warp instruction per cycle x 32
 # threads x 2.032 GHz (maximum SM clock), in thread instructions per second.
 ISSUE_PEAK = 148 * 4 * 32 * 2.032e9
@@ -189,9 +189,10 @@ def cpu_baseline(budget_s: float):
     att = L ** 3 * 2 * N_T * cores * n
     # one core: one sample in the calling thread, a quarter of the budget
     one = orc.State(L, T, 0.2, True, seed=99, J=J[:1], spins=s0[:1], n_therm=0)
+    one.run(1)  # warm-up
     t0 = time.perf_counter()
-    one.run(2)
-    per1 = max((time.perf_counter() - t0) / 2, 1e-4)
+    one.run(4)
+    per1 = max((time.perf_counter() - t0) / 4, 1e-4)
     n1 = max(1, min(20000, int(0.25 * budget_s / per1)))
     t0 = time.perf_counter()
     one.run(n1)
@@ -251,6 +252,9 @@ def extra_uneven_batch(sgmc, inputs, stream, torch):
     ens = [sgmc.Ensemble(L, 0.2, T, "gauss", S, 40 + L, J=J, spins=s0, stream=stream, n_therm=0)
            for (L, S), (J, s0) in zip(CFG4, insts)]
     tune = {f"L{e.L}": e.autotune(trial_sweeps=16)["threads_per_block"] for e in ens}
+    # sweeps per exchange: the most frequent exchange within 3 % of the fastest
+    sched = {f"L{e.L}": e.autotune_schedule([1, 2, 4], trial_sweeps=8,
+                                            tolerance=0.03)["exchange_every"] for e in ens}
     n = 64
     sgmc.sweep_batch(ens, n, use_graph=True)
     torch.cuda.synchronize()
@@ -264,7 +268,7 @@ def extra_uneven_batch(sgmc, inputs, stream, torch):
     for e in ens:
         e.close()
     pens = [sgmc.Ensemble(L, 0.2, T, "gauss", S, 40 + L, J=J, spins=s0, stream=stream,
-                          n_therm=0, sweeps_per_launch=1)
+                          n_therm=0, sweeps_per_launch=1, exchange_every=sched[f"L{L}"])
             for (L, S), (J, s0) in zip(CFG4, insts)]
     for e in pens:
         e.sweep(1)
@@ -279,6 +283,7 @@ def extra_uneven_batch(sgmc, inputs, stream, torch):
     for e in pens:
         e.close()
     return {"batched": batched, "plain": plain, "unit": UNIT, "tuned_threads": tune,
+            "tuned_exchange_every": sched,
             "workload": "gaussian, L=6,8,10,12,16 x 2048,1024,1024,512,256 samples, h=0.2, "
                         "2x20 T 0.5-1.5, exchange+measure every sweep"}
 

@@ -421,6 +421,7 @@ Int8Args make_args(sg_ensemble *e)
     a.work = e->work;
     a.n_seg = 1;
     a.seg_wait = 1ull << 30;
+    for (int r = 0; r < 10; ++r) a.k0r[r] = (a.seed_lo ^ 0x4D455452u) + (uint32_t)r * 0x9E3779B9u;
     return a;
 }
 

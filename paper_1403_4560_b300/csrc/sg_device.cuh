@@ -47,6 +47,32 @@ __device__ __forceinline__ u32x4 philox10(uint32_t k0, uint32_t k1, uint32_t c0,
     return r;
 }
 
+// The same with the round keys of k0 given (k0r[r] = k0 + r * 0x9E3779B9):
+// when k0 is fixed for a launch, the table lives in the kernel's parameters
+// and each round's xor takes its key as a constant operand.
+__device__ __forceinline__ u32x4 philox10_rk(const uint32_t *k0r, uint32_t k1, uint32_t c0,
+                                             uint32_t c1, uint32_t c2, uint32_t c3)
+{
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint64_t pa = (uint64_t)0xD2511F53u * c0;
+        const uint64_t pb = (uint64_t)0xCD9E8D57u * c2;
+        const uint32_t n0 = (uint32_t)(pb >> 32) ^ c1 ^ k0r[round];
+        const uint32_t n2 = (uint32_t)(pa >> 32) ^ c3 ^ k1;
+        c1 = (uint32_t)pb;
+        c3 = (uint32_t)pa;
+        c0 = n0;
+        c2 = n2;
+        k1 += 0xBB67AE85u;
+    }
+    u32x4 r;
+    r.v[0] = c0;
+    r.v[1] = c1;
+    r.v[2] = c2;
+    r.v[3] = c3;
+    return r;
+}
+
 // e^x * 2^k on [-64, 0] from IEEE basic operations only, so that host and
 // device agree bit for bit: Cody-Waite reduction x = n*ln2 + r with ln2 split
 // into 0.693359375 + (-2.12194440e-4), then e^r by its degree-7 Taylor

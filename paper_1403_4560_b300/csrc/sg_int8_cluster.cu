@@ -76,7 +76,7 @@ __device__ __forceinline__ void measure_cluster(cg::cluster_group &cl, const Sme
 
 template <int L, bool GAUSS>
 __global__ void __launch_bounds__(KernelBounds<L, true>::threads, 1)
-    int8_cluster_kernel(const Int8Args a)
+    int8_cluster_kernel(const __grid_constant__ Int8Args a)
 {
     constexpr int N = L * L * L;
     constexpr int H = L / 2;
@@ -86,6 +86,7 @@ __global__ void __launch_bounds__(KernelBounds<L, true>::threads, 1)
     Smem sm;
     carve(smem_raw, L, a.Tp, GAUSS, a.mchunk, &sm, true);
     Ctx cx;
+    cx.k0r = a.k0r;
     cx.nt = a.nt;
     cx.Tp = a.Tp;
     cx.WR = a.Tp / 4;

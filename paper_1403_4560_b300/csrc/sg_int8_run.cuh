@@ -191,6 +191,7 @@ struct Ctx {
     // cluster instances: this CTA's slab of z-planes [z0, z1) and its work
     // items [u0, u1) of each colour
     int z0, z1, u0, u1;
+    const uint32_t *k0r;  // round keys of k0, in the kernel's parameters
 };
 
 // Site index and neighbour offsets (in sites) of the colour-COL site with
@@ -383,7 +384,7 @@ __device__ __forceinline__ void half_sweep(const Smem &sm, const Ctx &cx, uint32
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk) {
                 const uint32_t c2 = ((uint32_t)COL << 24) | ((uint32_t)r << 16) | (uint32_t)(t0 + kk);
-                const u32x4 o = philox10(cx.k0, cx.k1, c0, n_sweep, c2, cx.seed_hi);
+                const u32x4 o = philox10_rk(cx.k0r, cx.k1, c0, n_sweep, c2, cx.seed_hi);
                 rnd[kk][0] = o.v[0];
                 rnd[kk][1] = o.v[1];
                 rnd[kk][2] = o.v[2];
@@ -511,7 +512,7 @@ __device__ __forceinline__ void half_sweep_packed(const Smem &sm, const Ctx &cx,
                 for (int kk = 0; kk < 4; ++kk) {
                     const uint32_t c2 = ((uint32_t)COL << 24) | ((uint32_t)r << 16) |
                                         (uint32_t)(t0 + kk);
-                    const u32x4 o = philox10(cx.k0, cx.k1, c0, n_sweep, c2, cx.seed_hi);
+                    const u32x4 o = philox10_rk(cx.k0r, cx.k1, c0, n_sweep, c2, cx.seed_hi);
                     rnd[r][kk][0] = o.v[0];
                     rnd[r][kk][1] = o.v[1];
                     rnd[r][kk][2] = o.v[2];
@@ -690,7 +691,7 @@ __device__ __forceinline__ void half_sweep_bits(const Smem &sm, const Ctx &cx, u
                     const int t = 4 * j + (k8 & 3), r = k8 >> 2;
                     if (t >= nt) continue;  // padding slots: never flipped
                     const uint32_t c2 = ((uint32_t)COL << 24) | ((uint32_t)r << 16) | (uint32_t)t;
-                    const u32x4 o = philox10(cx.k0, cx.k1, (uint32_t)u, n_sweep, c2, cx.seed_hi);
+                    const u32x4 o = philox10_rk(cx.k0r, cx.k1, (uint32_t)u, n_sweep, c2, cx.seed_hi);
                     const uint32_t *thr_t = sm.thr + t * 16;
 #pragma unroll
                     for (int l = 0; l < 4; ++l) {
@@ -1173,13 +1174,14 @@ struct Bounds {
 template <int L, bool GAUSS, bool GST, bool WIDE = false, bool BITS = false>
 __global__ void __launch_bounds__(Bounds<L, GST, WIDE, BITS>::threads,
                                   Bounds<L, GST, WIDE, BITS>::min_blocks)
-    int8_run_kernel(const Int8Args a)
+    int8_run_kernel(const __grid_constant__ Int8Args a)
 {
     constexpr int N = L * L * L;
     extern __shared__ __align__(16) uint8_t smem_raw[];
     Smem sm;
     carve(smem_raw, L, a.Tp, GAUSS, a.mchunk, &sm, GST, BITS);
     Ctx cx;
+    cx.k0r = a.k0r;
     cx.nt = a.nt;
     cx.Tp = a.Tp;
     // global-memory instances and the bit-parallel ones keep the packed state

@@ -51,6 +51,10 @@ struct Int8Args {
     // longest wait (clock64 cycles) for a sample's previous segment when no
     // watchdog budget is set; the launch then stops with SG_ETIMEOUT
     unsigned long long seg_wait;
+    // round keys of the Metropolis Philox key word k0 = seed_lo ^ MET:
+    // k0r[r] = k0 + r * 0x9E3779B9, fixed per launch, read as constant
+    // operands instead of the per-round key increment
+    uint32_t k0r[10];
 };
 
 struct Int8Launch {
