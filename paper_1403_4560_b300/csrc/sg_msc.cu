@@ -585,9 +585,11 @@ __global__ void __launch_bounds__(MAXT, MINB) msc_sweep_kernel(const MscArgs a)
 // before n_therm. Same random numbers, decisions and order as
 // msc_sweep_kernel: the results are identical. (B300, +-J, 4096 samples,
 // 2 x 32 temperatures, thermalising attempts/ns fused -> split: L = 12
-// 2200 -> 2478, L = 14 2436 -> 2848, L = 16 2969 -> 3077; with a separate
-// measurement kernel after it, measuring sweeps ran up to 5 % slower than
-// the fused kernel, so those stay fused.)
+// 2200 -> 2478, L = 14 2436 -> 2848, L = 16 2969 -> 3077. Measuring sweeps
+// stay fused: a separate measurement kernel after the split sweep ran them up
+// to 5 % slower, and the replica pair run as a cluster, each CTA measuring one
+// slot through the peer's shared memory, slower still: measuring at L = 12 /
+// 14 / 16 1549 / 1800 / 2057 against 1911 / 1831 / 2199 fused.)
 // ---------------------------------------------------------------------------
 constexpr int kMscSplitThreads = 256;
 
