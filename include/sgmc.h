@@ -157,8 +157,9 @@ typedef struct {
                                   1 = one CTA runs all of a sample's sweeps;
                                   the global-memory state is never split.
                                   Results do not depend on it.               */
-    int32_t cluster;           /* INT8 state in global memory, L = 20, 24, 28
-                                  or 32: CTAs per sample, each sweeping L/k of
+    int32_t cluster;           /* INT8 state in global memory, L = 20, 24, 28,
+                                  32, 40, 48 or 64: CTAs per sample, each
+                                  sweeping L/k of
                                   the z-planes as one thread-block cluster.
                                   0 = library choice (k = 2, 4 or 8 when the
                                   samples are fewer than the SMs and the split

@@ -37,7 +37,7 @@ namespace {
 
 namespace cg = cooperative_groups;
 
-#define SG_FOR_EACH_CLUSTER_L(X) X(20) X(24) X(28) X(32)
+#define SG_FOR_EACH_CLUSTER_L(X) X(20) X(24) X(28) X(32) X(40) X(48) X(64)
 
 template <typename T>
 __device__ __forceinline__ T *rank0(cg::cluster_group &cl, T *p)

@@ -101,7 +101,7 @@ cudaError_t int8_launch_bits(int L, const Int8Args &a, const Int8Launch &cfg, cu
 int int8_ctas_per_sm_bits(int L, int threads, size_t smem);
 // The cluster instances (one sample per thread-block cluster of k = 2, 4 or
 // 8 CTAs, each sweeping L/k z-planes of the packed global-memory state), for
-// L = 20, 24, 28, 32; in their own translation unit. cfg.grid must be a
+// L = 20, 24, 28, 32, 40, 48, 64; in their own translation unit. cfg.grid must be a
 // multiple of cfg.cluster and L a multiple of it.
 bool int8_cluster_has(int L);
 cudaError_t int8_launch_cluster(int L, bool gauss, const Int8Args &a, const Int8Launch &cfg,

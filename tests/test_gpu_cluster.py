@@ -38,7 +38,8 @@ def snapshot(e):
 
 @pytest.mark.parametrize("L,k,dist,nt", [(24, 2, "gauss", 4), (24, 4, "pmj", 5), (24, 8, "gauss", 3),
                                          (32, 2, "pmj", 4), (32, 4, "gauss", 6), (32, 8, "pmj", 2),
-                                         (20, 4, "gauss", 9), (28, 2, "pmj", 4)])
+                                         (20, 4, "gauss", 9), (28, 2, "pmj", 4),
+                                         (40, 8, "gauss", 2), (48, 4, "pmj", 3)])
 def test_cluster_split_is_bit_exact_against_oracle(L, k, dist, nt):
     S, h, seed, sweeps = 3, 0.15, 40 + L + k, 10
     T = inputs.geometric_ladder(0.5, 1.6, nt)
@@ -59,6 +60,26 @@ def test_cluster_split_is_bit_exact_against_oracle(L, k, dist, nt):
     np.testing.assert_array_equal(got[2], st.M)
     np.testing.assert_array_equal(got[3], st.acc)
     np.testing.assert_array_equal(got[4], st.hist)
+
+
+def test_cluster_measurement_in_several_chunks_matches_oracle():
+    """L = 64 with 24 temperatures: the overlap marginals of a sample's six
+    4-slot words do not fit one CTA's shared memory at once, so each
+    measurement runs in chunks, every chunk's partial marginals gathered at
+    rank 0 between cluster barriers; one sample over 4 CTAs, against the
+    oracle bit for bit."""
+    L, S, nt, h, seed, sweeps = 64, 1, 24, 0.1, 3, 2
+    T = inputs.geometric_ladder(0.5, 1.6, nt)
+    J, s0 = inputs.make_instance("pmj", L, S, nt, seed=64)
+    with sgmc.Ensemble(L, h, T, "pmj", S, seed, J=J, spins=s0, cluster=4) as ens:
+        assert ens.info().cluster == 4
+        ens.sweep(sweeps)
+        got = snapshot(ens)
+    st = orc.State(L, T, h, False, seed=seed, J=J, spins=s0)
+    st.run(sweeps)
+    np.testing.assert_array_equal(got[0], st.spins)
+    np.testing.assert_array_equal(got[1], st.B)
+    np.testing.assert_array_equal(got[3], st.acc)
 
 
 def test_library_picks_a_cluster_for_few_samples_and_results_do_not_change():
