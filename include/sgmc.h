@@ -406,7 +406,10 @@ sg_status sg_get_info(const sg_ensemble *e, sg_info *out);
  * the resident CTAs and the last wave would leave slots idle, or when one
  * wave would give some SMs one CTA more than others (then k >= 3 CTAs on
  * every SM), each sample's sweeps are split into segments that the CTAs
- * claim in order (sg_options.segments). MSC64 runs one launch per sweep.
+ * claim in order (sg_options.segments). MSC64 runs one launch per sweep;
+ * at L >= 12 a call whose sweeps all thermalise (global sweep index below
+ * n_therm) runs each exchange unit as two CTAs, one per replica (twice the
+ * grid), and calls with a measured sweep run the fused unit CTAs.
  *   grid      CTAs of each launch (may be NULL)
  *   segments  segments per sample of the first launch, 1 = unsplit (may be NULL)
  *   launches  fused-kernel launches of the call (may be NULL)
