@@ -285,7 +285,8 @@ def extra_uneven_batch(sgmc, inputs, stream, torch):
     return {"batched": batched, "plain": plain, "unit": UNIT, "tuned_threads": tune,
             "tuned_exchange_every": sched,
             "workload": "gaussian, L=6,8,10,12,16 x 2048,1024,1024,512,256 samples, h=0.2, "
-                        "2x20 T 0.5-1.5, exchange+measure every sweep"}
+                        "2x20 T 0.5-1.5, measure every sweep, exchange every "
+                        "tuned_exchange_every sweeps (both arms)"}
 
 
 def extra_msc(sgmc, stream, torch, L=16, S=4096, T=None, h=0.1):

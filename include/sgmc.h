@@ -407,7 +407,7 @@ sg_status sg_get_info(const sg_ensemble *e, sg_info *out);
  * wave would give some SMs one CTA more than others (then k >= 3 CTAs on
  * every SM), each sample's sweeps are split into segments that the CTAs
  * claim in order (sg_options.segments). MSC64 runs one launch per sweep;
- * at L >= 12 a call whose sweeps all thermalise (global sweep index below
+ * at L >= 14 a call whose sweeps all thermalise (global sweep index below
  * n_therm) runs each exchange unit as two CTAs, one per replica (twice the
  * grid), and calls with a measured sweep run the fused unit CTAs.
  *   grid      CTAs of each launch (may be NULL)

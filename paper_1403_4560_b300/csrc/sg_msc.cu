@@ -576,7 +576,7 @@ __global__ void __launch_bounds__(MAXT, MINB) msc_sweep_kernel(const MscArgs a)
 }
 
 // ---------------------------------------------------------------------------
-// Thermalising sweeps of large lattices (L >= 12): the exchange unit split by
+// Thermalising sweeps of large lattices (L >= 14): the exchange unit split by
 // replica. A CTA holds one replica's chains of the unit (the sweep and the
 // exchange never mix replicas: methods section, each replica has its own
 // tempering ladder), so at L = 16 it needs 64 KB of shared memory instead of
@@ -584,8 +584,9 @@ __global__ void __launch_bounds__(MAXT, MINB) msc_sweep_kernel(const MscArgs a)
 // both replicas): the host uses it only for launches whose sweeps all lie
 // before n_therm. Same random numbers, decisions and order as
 // msc_sweep_kernel: the results are identical. (B300, +-J, 4096 samples,
-// 2 x 32 temperatures, thermalising attempts/ns fused -> split: L = 12
-// 2200 -> 2478, L = 14 2436 -> 2848, L = 16 2969 -> 3077. Measuring sweeps
+// 2 x 32 temperatures, thermalising attempts/ns, the library's fused shape
+// -> split: L = 14 2436 -> 2886, L = 16 2969 -> 3117; at L = 12 the fused
+// 256-thread CTA stays ahead, 2661 against 2541. Measuring sweeps
 // stay fused: a separate measurement kernel after the split sweep ran them up
 // to 5 % slower, and the replica pair run as a cluster, each CTA measuring one
 // slot through the peer's shared memory, slower still: measuring at L = 12 /
@@ -1032,7 +1033,7 @@ int msc_threads(int L, int requested)
     return L <= 10 ? 128 : L == 12 ? 256 : kMscThreads;
 }
 
-bool msc_split(int L, int requested) { return requested <= 0 && L >= 12 && msc_supported_L(L); }
+bool msc_split(int L, int requested) { return requested <= 0 && L >= 14 && msc_supported_L(L); }
 int msc_split_threads() { return kMscSplitThreads; }
 
 cudaError_t msc_sweep(const MscArgs &a, int L, int threads, cudaStream_t st, bool split)

@@ -187,10 +187,10 @@ def test_msc_autotune_changes_speed_not_results():
         assert a.sweeps_done == b.sweeps_done == 25
 
 
-@pytest.mark.parametrize("L,nt,ee,me,S", [(12, 5, 1, 1, 128), (14, 6, 2, 3, 64), (16, 4, 1, 1, 64),
+@pytest.mark.parametrize("L,nt,ee,me,S", [(14, 5, 1, 1, 128), (14, 6, 2, 3, 64), (16, 4, 1, 1, 64),
                                           (16, 3, 0, 2, 128)])
 def test_replica_split_sweep_equals_fused_kernel_and_oracle(L, nt, ee, me, S):
-    """At L >= 12 launches whose sweeps all thermalise run split by replica
+    """At L >= 14 launches whose sweeps all thermalise run split by replica
     (one replica's chains of an exchange unit per CTA); the measuring ones
     run fused. A run of a thermalising then a measuring launch must equal the
     fused kernel throughout (an explicit CTA size selects it) bit for bit,
