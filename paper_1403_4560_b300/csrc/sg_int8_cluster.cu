@@ -117,7 +117,6 @@ __global__ void __launch_bounds__(KernelBounds<L, true>::threads, 1)
     bool stop = false;
     for (int64_t s = a.s_begin + c; s < a.s_end && !stop; s += n_clusters) {
         cx.s = s;
-        cx.k0 = a.seed_lo ^ kTagMet;
         cx.k1 = (uint32_t)((s + a.s_key0) / a.rng_group);
         sm.spins = a.spins + (size_t)s * N * cx.RB;
         if (!GAUSS)

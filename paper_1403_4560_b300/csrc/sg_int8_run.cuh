@@ -185,7 +185,7 @@ __host__ __device__ inline size_t carve(uint8_t *base, int L, int Tp, bool gauss
 struct Ctx {
     int nt, Tp, WR, RB;
     int64_t s;
-    uint32_t k0, k1;  // Metropolis Philox key
+    uint32_t k1;      // Metropolis Philox key word of the sample (k0 is in k0r)
     uint32_t seed_lo, seed_hi;
     float hq;         // Gaussian: field on the 2^-17 grid
     // cluster instances: this CTA's slab of z-planes [z0, z1) and its work
@@ -1247,7 +1247,6 @@ __global__ void __launch_bounds__(Bounds<L, GST, WIDE, BITS>::threads,
             if (wait_fail) break;
         }
         cx.s = s;
-        cx.k0 = a.seed_lo ^ kTagMet;
         cx.k1 = (uint32_t)((s + a.s_key0) / a.rng_group);
         __syncthreads();
         if (GST) {

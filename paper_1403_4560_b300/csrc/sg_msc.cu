@@ -1034,7 +1034,6 @@ int msc_threads(int L, int requested)
 }
 
 bool msc_split(int L, int requested) { return requested <= 0 && L >= 14 && msc_supported_L(L); }
-int msc_split_threads() { return kMscSplitThreads; }
 
 cudaError_t msc_sweep(const MscArgs &a, int L, int threads, cudaStream_t st, bool split)
 {

@@ -38,11 +38,10 @@ bool msc_supported_L(int L);
 int msc_threads(int L, int requested);
 // Whether thermalising sweeps run split by replica (L >= 14 and no requested
 // CTA size): msc_split_sweep_kernel, one replica's chains of an exchange unit
-// per CTA (msc_split_threads() threads), which does not measure; the caller
+// per CTA (256 threads), which does not measure; the caller
 // passes split only for launches without measured sweeps; else the fused
 // msc_sweep_kernel with `threads` threads.
 bool msc_split(int L, int requested);
-int msc_split_threads();
 cudaError_t msc_sweep(const MscArgs &a, int L, int threads, cudaStream_t st, bool split);
 // skip (device, may be null): when *skip is nonzero the import writes nothing
 cudaError_t msc_import_spins(uint64_t *W, const int8_t *canon, int64_t G, int L, int nt,
