@@ -107,6 +107,31 @@ def test_library_picks_a_cluster_for_few_samples_and_results_do_not_change():
         np.testing.assert_array_equal(outs[0][3][s], st.acc[0])
 
 
+def test_clusters_taking_several_samples_each_match_one_cta_per_sample():
+    """More samples than resident clusters (L = 24, 180 samples, clusters of
+    2 CTAs, at most ~74 resident): each cluster loops over several samples,
+    rank 0's shared sums and flags reused between them; the run equals one
+    CTA per sample bit for bit, and the last sample equals the oracle."""
+    L, S, nt, h, seed, sweeps = 24, 180, 2, 0.3, 9, 4
+    T = inputs.geometric_ladder(0.5, 1.6, nt)
+    J, s0 = inputs.make_instance("pmj", L, S, nt, seed=180)
+    outs = []
+    for cl in (2, 1):
+        with sgmc.Ensemble(L, h, T, "pmj", S, seed, J=J, spins=s0, cluster=cl, n_therm=1) as e:
+            if cl == 2:
+                assert e.info().grid < 2 * S  # fewer clusters than samples
+            e.sweep(sweeps)
+            outs.append(snapshot(e)[:4])
+    for a, b in zip(*outs):
+        np.testing.assert_array_equal(a, b)
+    s = S - 1
+    st = orc.State(L, T, h, False, seed=seed, J=J[s:s + 1], spins=s0[s:s + 1], s_base=s,
+                   n_therm=1)
+    st.run(sweeps)
+    np.testing.assert_array_equal(outs[0][0][s], st.spins[0])
+    np.testing.assert_array_equal(outs[0][3][s], st.acc[0])
+
+
 def test_cluster_options_are_checked():
     T = inputs.geometric_ladder(0.5, 1.6, 4)
     for bad in (3, 5, -1):
