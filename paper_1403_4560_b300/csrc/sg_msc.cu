@@ -30,7 +30,13 @@ namespace {
 constexpr int kMscThreads = 512;
 constexpr int kDU = 9;  // bit planes of the per-thread unsatisfied-bond counter
 constexpr int kDM = 8;  // bit planes of the per-thread (-1 spin) counter
-constexpr int kDP = 9;  // bit planes of a projection (<= L^2 <= 256 sites)
+// Bit planes of a projection count (0..L^2): the fewest with 2^planes > L^2,
+// 9 at L = 16. Fewer planes make the carry chain of the projection sums
+// shorter and let more phases share one warp transpose.
+__host__ __device__ constexpr int msc_dp(int L)
+{
+    return L * L < 32 ? 5 : L * L < 64 ? 6 : L * L < 128 ? 7 : L * L < 256 ? 8 : 9;
+}
 constexpr int kDG = 5;  // bit planes of a 2D marginal entry (<= L <= 16 sites)
 
 
@@ -96,7 +102,7 @@ struct MscSmem {
     long long *B, *M;   // [4][64]  per-sample energies of the unit's chains
     uint64_t *swap;     // [2]      exchange masks per replica
     uint64_t *marg;     // [ms][3][L*L][kDG] bit-sliced 2D marginal counts of q = -1
-    uint64_t *proj;     // [ms][9][L][kDP] bit-sliced projection counts of q = -1
+    uint64_t *proj;     // [ms][9][L][msc_dp(L)] bit-sliced projection counts of q = -1
 };
 
 __host__ __device__ inline size_t a16(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -109,7 +115,7 @@ __host__ __device__ inline size_t a16(size_t x) { return (x + 15) & ~(size_t)15;
 // cache (at 217 KB the sweeps ran 5 % slower).
 __host__ __device__ constexpr bool msc_proj_in_w(int L, int ms)
 {
-    return ms == 2 && (size_t)2 * 9 * L * kDP <= (size_t)4 * L * L * L;
+    return ms == 2 && (size_t)2 * 9 * L * msc_dp(L) <= (size_t)4 * L * L * L;
 }
 
 // Slots whose overlap one measurement pass covers: both slots of the unit
@@ -140,7 +146,7 @@ __host__ __device__ inline size_t msc_carve(uint8_t *base, int L, MscSmem *sm, i
     s.swap = reinterpret_cast<uint64_t *>(take(2 * 8));
     s.marg = reinterpret_cast<uint64_t *>(take((size_t)ms * 3 * L * L * kDG * 8));
     s.proj = msc_proj_in_w(L, ms) ? s.w
-                                  : reinterpret_cast<uint64_t *>(take((size_t)ms * 9 * L * kDP * 8));
+                                  : reinterpret_cast<uint64_t *>(take((size_t)ms * 9 * L * msc_dp(L) * 8));
     if (sm) *sm = s;
     return off;
 }
@@ -356,14 +362,15 @@ __device__ __forceinline__ void msc_measure(const MscSmem &sm, const MscArgs &a,
         __syncthreads();
     }
     // (B) projection counts: sum of L marginal entries per (v, d)
+    constexpr int DP = msc_dp(L);
     for (int id = threadIdx.x; id < nk * 9 * L; id += blockDim.x) {
         const int kk = id / (9 * L), pid = id - kk * (9 * L);
         const uint64_t *margk = sm.marg + (size_t)kk * 3 * LL * kDG;
         const int v = pid / L, d = pid % L;
         const int plane = (v == 0 || v == 1 || v == 3 || v == 4) ? 0 : (v == 2 || v == 5 || v == 6) ? 1 : 2;
-        uint64_t acc[kDP];
+        uint64_t acc[DP];
 #pragma unroll
-        for (int p = 0; p < kDP; ++p) acc[p] = 0;
+        for (int p = 0; p < DP; ++p) acc[p] = 0;
         auto add_entry = [&](int aa) {
             int A, Bc;
             if (v == 0) {
@@ -377,7 +384,7 @@ __device__ __forceinline__ void msc_measure(const MscSmem &sm, const MscArgs &a,
             }
             const uint64_t *m = margk + ((size_t)plane * LL + A * L + Bc) * kDG;
             const uint64_t x[kDG] = {m[0], m[1], m[2], m[3], m[4]};
-            bs_add<kDP, kDG>(acc, x);
+            bs_add<DP, kDG>(acc, x);
         };
         if constexpr (WIDE) {
 #pragma unroll
@@ -386,16 +393,19 @@ __device__ __forceinline__ void msc_measure(const MscSmem &sm, const MscArgs &a,
             for (int aa = 0; aa < L; ++aa) add_entry(aa);
         }
 #pragma unroll
-        for (int p = 0; p < kDP; ++p) sm.proj[(size_t)id * kDP + p] = acc[p];  // [kk][v][d]
+        for (int p = 0; p < DP; ++p) sm.proj[(size_t)id * DP + p] = acc[p];  // [kk][v][d]
     }
     __syncthreads();
-    // (C) one warp per (wave vector v, half of the word): lanes 0..8 load the
-    // nine planes of P_v[d] and a bit transpose hands lane b the count of
-    // sample 32*half + b; the lane then runs the FP32 DFT over d in ascending
+    // (C) one warp per (wave vector v, half of the word): lanes j*DP + p load
+    // plane p of P_v[d0 + j] for the G = 32 / DP phases of a group, and one
+    // bit transpose hands lane b the G counts of sample 32*half + b, packed
+    // DP bits each; the lane then runs the FP32 DFT over d in ascending
     // order and the FP64 accumulation. The v = 0 tasks also produce Q, and
     // E and M are added straight from the per-sample energies.
     {
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+        constexpr int G = 32 / DP;
+        const int lj = lane / DP, lp = lane - lj * DP;
         for (int task = warp; task < nk * 2 * 9; task += nwarps) {
             const int kk = task / 18, v = (task % 18) >> 1, half = task & 1;
             const int k = k0 + kk, t = t0 + kk;
@@ -412,20 +422,27 @@ __device__ __forceinline__ void msc_measure(const MscSmem &sm, const MscArgs &a,
             }
             float re = 0.0f, im = 0.0f;
             int Qi = 0;
-            auto add_phase = [&](int d) {
-                const uint64_t *p = sm.proj + (((size_t)kk * 9 + v) * L + d) * kDP;
-                const uint32_t row = lane < kDP ? (uint32_t)(p[lane] >> (32 * half)) : 0u;
-                const int cnt = (int)(warp_transpose32(row) & ((1u << kDP) - 1));
-                const int P = LL - 2 * cnt;
-                Qi += P;
-                re = __fmaf_rn((float)P, a.twid[d], re);
-                im = __fmaf_rn((float)P, a.twid[L + d], im);
+            const uint64_t *pv = sm.proj + ((size_t)kk * 9 + v) * L * DP;
+            auto add_group = [&](int d0) {
+                const int dl = d0 + lj;
+                const uint32_t row = (lj < G && dl < L) ? (uint32_t)(pv[dl * DP + lp] >> (32 * half)) : 0u;
+                const uint32_t cnts = warp_transpose32(row);
+#pragma unroll
+                for (int j = 0; j < G; ++j) {
+                    const int d = d0 + j;
+                    if (d < L) {
+                        const int P = LL - 2 * (int)((cnts >> (j * DP)) & ((1u << DP) - 1));
+                        Qi += P;
+                        re = __fmaf_rn((float)P, a.twid[d], re);
+                        im = __fmaf_rn((float)P, a.twid[L + d], im);
+                    }
+                }
             };
             if constexpr (WIDE) {
 #pragma unroll
-                for (int d = 0; d < L; ++d) add_phase(d);
+                for (int d0 = 0; d0 < L; d0 += G) add_group(d0);
             } else {
-                for (int d = 0; d < L; ++d) add_phase(d);
+                for (int d0 = 0; d0 < L; d0 += G) add_group(d0);
             }
             const double dr = (double)re, di = (double)im;
             acv[0] = __dadd_rn(o0, dr);
