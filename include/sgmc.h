@@ -133,11 +133,12 @@ typedef struct {
                                   memory, a byte per chain
                                   (SG_EUNSUPPORTED if it does not fit), 2 =
                                   global memory (L >= 10), 3 = shared memory,
-                                  one bit per chain, swept bit-parallel
-                                  (+-J couplings, at most 64 temperatures,
-                                  L = 4..16 even; the paper's multispin
-                                  coding of a sample's replicas, each chain
-                                  still drawing its own random numbers).
+                                  one bit per chain (at most 64
+                                  temperatures, L = 4..16 even; the paper's
+                                  multispin coding of a sample's replicas,
+                                  each chain still drawing its own random
+                                  numbers): +-J swept bit-parallel, Gaussian
+                                  couplings by chain sets (chain_set).
                                   Results do not depend on it.               */
     int32_t segments;          /* INT8 state in shared memory: each launch's
                                   sweeps are split into this many segments per
@@ -167,6 +168,14 @@ typedef struct {
                                   sample, 2 / 4 / 8 = that cluster size
                                   (SG_EUNSUPPORTED if it cannot run). Results
                                   do not depend on it.                       */
+    int32_t chain_set;         /* one bit per chain (state_mode 3) with
+                                  Gaussian couplings: 4-slot groups (8 chains
+                                  each) in the chain set of one warp task of
+                                  the sweep, 1, 2 or 4: larger sets share a
+                                  task's per-site work among more chains,
+                                  smaller ones balance the warps; 0 = library
+                                  choice (sg_info.chain_set). Results do not
+                                  depend on it.                              */
 } sg_options;
 
 /* Fill *opt with the defaults: INT8 layout, rng_group 1, exchange and
@@ -396,6 +405,8 @@ typedef struct {
                                    chunk of sweeps; 0: in global memory */
     int32_t cluster;            /* CTAs sweeping one sample together (1
                                    unless sg_options.cluster applies)   */
+    int32_t chain_set;          /* bit-parallel Gaussian sweep: 4-slot
+                                   groups per warp task (0 otherwise)   */
 } sg_info;
 sg_status sg_get_info(const sg_ensemble *e, sg_info *out);
 

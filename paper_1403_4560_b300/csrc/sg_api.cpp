@@ -255,30 +255,104 @@ sg_status configure_cluster(sg_ensemble *e, int64_t resident)
 // of the site row), at most 8 warps per CTA, so that small lattices run more
 // CTAs per SM rather than idle warps; the measurement chunk that keeps the
 // most CTAs per SM.
+// The most CTAs per SM over the measurement chunks, and that chunk.
+static int bits_occupancy(const sg_ensemble *e, int threads, int *m_for)
+{
+    int occ = 0;
+    *m_for = 0;
+    for (int m = e->Tp / 4; m >= 1; --m) {
+        const size_t smem = int8_smem_bytes_bits(e->L, e->Tp, m, e->gauss);
+        if (!smem) continue;
+        const int o = int8_ctas_per_sm_bits(e->L, e->gauss, threads, smem);
+        if (o > occ) {
+            occ = o;
+            *m_for = m;
+        }
+    }
+    return occ;
+}
+
+// Gaussian couplings on the bit-per-chain state: a warp task is 32 work
+// items times a chain set of csb 4-slot groups (1, 2 or 4). Larger sets share
+// the per-site work of a task (indices, 13 loads per site) among more chains;
+// smaller ones make more tasks, which balance the warps of a CTA better. The
+// model: a task costs kSetup + (its chains) chain units, warps take tasks
+// round-robin, and a shape scores its balance (work over warps x the
+// longest warp) x the chain share of the work x the resident warps per SM
+// (up to 16, enough to keep the schedulers issuing). A requested
+// threads_per_block fixes the warps.
+static void bits_gauss_shape(const sg_ensemble *e, int *csb_out, int *warps_out)
+{
+    constexpr double kSetup = 1.5;
+    const int L = e->L, nt = e->nt;
+    const int items = (L * L * L / 2) / int8_site_run(L, false);
+    const int nub = (items + 31) / 32, ngrp = (nt + 3) / 4;
+    const int64_t per_sm = (e->S + e->num_sms - 1) / e->num_sms;
+    const int want_w = e->opt.threads_per_block > 0
+                           ? std::max(1, std::min(8, e->opt.threads_per_block / 32)) : 0;
+    double best = -1.0;
+    *csb_out = 1;
+    *warps_out = 1;
+    for (int csb = 4; csb >= 1; csb /= 2) {
+        if (e->opt.chain_set > 0 && csb != e->opt.chain_set) continue;
+        const int ncs = (ngrp + csb - 1) / csb;
+        std::vector<double> cost((size_t)nub * ncs);
+        double work = 0.0, chains = 0.0;
+        for (int tk = 0; tk < nub * ncs; ++tk) {
+            const int cs = tk % ncs;
+            const int t0 = 4 * cs * csb, t1 = std::min(nt, 4 * (cs + 1) * csb);
+            const double ch = 2.0 * (t1 - t0);
+            cost[tk] = kSetup + ch;
+            work += cost[tk];
+            chains += ch;
+        }
+        for (int w = 1; w <= 8; ++w) {
+            if (want_w && w != want_w) continue;
+            double longest = 0.0;
+            for (int k = 0; k < w; ++k) {
+                double c = 0.0;
+                for (int tk = k; tk < nub * ncs; tk += w) c += cost[tk];
+                longest = std::max(longest, c);
+            }
+            int m = 0;
+            const int occ = bits_occupancy(e, 32 * w, &m);
+            if (!occ) continue;
+            const double resident = (double)std::min<int64_t>(occ, per_sm) * w;
+            const double score =
+                work / (w * longest) * (chains / work) * std::min(resident, 16.0);
+            if (score > best * 1.0001) {
+                best = score;
+                *csb_out = csb;
+                *warps_out = w;
+            }
+        }
+    }
+}
+
 sg_status configure_bits(sg_ensemble *e)
 {
     const int L = e->L;
     if (!int8_bits_has(L)) return fail(SG_EUNSUPPORTED, "no bit-parallel kernel for this lattice size");
-    const int items = (L * L * L / 2) / int8_site_run(L, false);
-    const int tasks = ((items + 31) / 32) * (e->Tp / 32);
-    const int t = 32 * std::min(tasks, 8);
-    int occ = 0, m_for = 0;
-    for (int m = e->Tp / 4; m >= 1; --m) {
-        const size_t smem = int8_smem_bytes_bits(L, e->Tp, m);
-        if (!smem) continue;
-        const int o = int8_ctas_per_sm_bits(L, t, smem);
-        if (o > occ) {
-            occ = o;
-            m_for = m;
-        }
+    int t, csb = 0;
+    if (e->gauss) {
+        int w = 1;
+        bits_gauss_shape(e, &csb, &w);
+        t = 32 * w;
+    } else {
+        const int items = (L * L * L / 2) / int8_site_run(L, false);
+        const int tasks = ((items + 31) / 32) * (e->Tp / 32);
+        t = 32 * std::min(tasks, 8);
     }
+    int m_for = 0;
+    const int occ = bits_occupancy(e, t, &m_for);
     if (!occ) return fail(SG_EUNSUPPORTED, "the bit-parallel state does not fit shared memory");
     e->mchunk = m_for;
     e->launch = Int8Launch{};
     e->launch.threads = t;
     e->launch.bits = true;
+    e->launch.csb = csb;
     e->launch.cluster = 1;
-    e->launch.smem = int8_smem_bytes_bits(L, e->Tp, m_for);
+    e->launch.smem = int8_smem_bytes_bits(L, e->Tp, m_for, e->gauss);
     e->launch.grid = (int)std::min<int64_t>(e->S, (int64_t)occ * e->num_sms);
     return SG_OK;
 }
@@ -422,6 +496,7 @@ Int8Args make_args(sg_ensemble *e)
     a.n_seg = 1;
     a.seg_wait = 1ull << 30;
     for (int r = 0; r < 10; ++r) a.k0r[r] = (a.seed_lo ^ 0x4D455452u) + (uint32_t)r * 0x9E3779B9u;
+    a.csb = e->launch.csb;
     return a;
 }
 
@@ -550,10 +625,12 @@ sg_status validate(int L, const double *T, int nt, sg_coupling dist, int64_t S,
         return fail(SG_EINVAL, "sample_base + n_samples must be in [0, 2^32]");
     if (o.log_bins < 0 || o.log_bins > 64) return fail(SG_EINVAL, "log_bins must be in [0, 64]");
     if (o.state_mode < 0 || o.state_mode > 3) return fail(SG_EINVAL, "state_mode must be 0, 1, 2 or 3");
-    if (o.state_mode == 3 && (o.layout != SG_LAYOUT_INT8 || dist != SG_PM_J || nt > 64))
-        return fail(SG_EINVAL, "state_mode 3 (bit-parallel) needs the INT8 layout, +-J couplings "
-                               "and at most 64 temperatures");
+    if (o.state_mode == 3 && (o.layout != SG_LAYOUT_INT8 || nt > 64))
+        return fail(SG_EINVAL, "state_mode 3 (bit-parallel) needs the INT8 layout and at most 64 "
+                               "temperatures");
     if (o.segments < 0) return fail(SG_EINVAL, "segments must be >= 0");
+    if (o.chain_set < 0 || o.chain_set == 3 || o.chain_set > 4)
+        return fail(SG_EINVAL, "chain_set must be 0, 1, 2 or 4");
     if (o.cluster < 0 || o.cluster == 3 || (o.cluster > 4 && o.cluster != 8))
         return fail(SG_EINVAL, "cluster must be 0, 1, 2, 4 or 8");
     if (o.layout == SG_LAYOUT_MSC64) {
@@ -1326,6 +1403,7 @@ sg_status sg_get_info(const sg_ensemble *e, sg_info *out)
         out->state_in_shared = e->launch.gst ? 0 : 1;
     }
     out->cluster = e->msc ? 1 : std::max(e->launch.cluster, 1);
+    out->chain_set = e->msc ? 0 : e->launch.csb;
     return SG_OK;
 }
 

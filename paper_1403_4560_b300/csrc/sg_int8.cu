@@ -427,7 +427,7 @@ int int8_max_threads(int L, bool gst, bool wide)
 cudaError_t int8_launch(int L, bool gauss, const Int8Args &a, const Int8Launch &cfg,
                         cudaStream_t st)
 {
-    if (cfg.bits) return gauss ? cudaErrorInvalidValue : int8_launch_bits(L, a, cfg, st);
+    if (cfg.bits) return int8_launch_bits(L, gauss, a, cfg, st);
     if (cfg.gst && cfg.cluster > 1) return int8_launch_cluster(L, gauss, a, cfg, st);
     if (cfg.gst) return int8_launch_gst(L, gauss, a, cfg, st);
     if (cfg.wide) return int8_launch_wide(L, gauss, a, cfg, st);

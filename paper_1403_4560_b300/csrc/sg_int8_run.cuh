@@ -148,6 +148,18 @@ struct Smem {
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
+// Skewed shared-memory layout of the Gaussian bit-parallel state: site i's
+// row of RB bytes starts at bits_row(i) = i RB + 4 floor(i / 8), and its
+// couplings at index bits_jidx(i) = i + floor(i / 8) of each of the three
+// planes (planes N + N/8 floats apart). The lanes of a warp task take work
+// items 8 sites apart, which without the skew would all fall in two banks.
+template <bool SKEW>
+__host__ __device__ __forceinline__ int bits_row(int i, int RB)
+{
+    return SKEW ? i * RB + ((i >> 1) & ~3) : i * RB;
+}
+__host__ __device__ __forceinline__ int bits_jidx(int i) { return i + (i >> 3); }
+
 // Carve the dynamic shared memory; returns the bytes used.
 // gst: the sample's spins and couplings stay in global memory (large L);
 // only the small tables are carved.
@@ -163,9 +175,13 @@ __host__ __device__ inline size_t carve(uint8_t *base, int L, int Tp, bool gauss
         return p;
     };
     Smem s;
-    s.spins = gst ? nullptr : take(bits ? N * (Tp / 4) : N * 2 * Tp);
+    // Gaussian bit-parallel state: rows and coupling planes skewed (bits_row, bits_jidx)
+    const bool skew = bits && gauss;
+    s.spins = gst ? nullptr : take(bits ? N * (Tp / 4) + (skew ? N / 2 : 0) : N * 2 * Tp);
     s.J8 = (gauss || gst) ? nullptr : take(N * 8);
-    s.Jg = (gauss && !gst) ? reinterpret_cast<float *>(take(N * 3 * sizeof(float))) : nullptr;
+    s.Jg = (gauss && !gst)
+               ? reinterpret_cast<float *>(take((skew ? N + N / 8 : N) * 3 * sizeof(float)))
+               : nullptr;
     s.thr = gauss ? nullptr : reinterpret_cast<uint32_t *>(take((size_t)Tp * 16 * 4));
     s.negbeta = reinterpret_cast<float *>(take((size_t)Tp * 4));
     s.dbeta = reinterpret_cast<float *>(take((size_t)Tp * 4));
@@ -237,71 +253,118 @@ __device__ __forceinline__ uint32_t pmj_word(uint32_t s, uint32_t nxp, uint32_t 
     return fm & valid;
 }
 
-// Local field b = sum of J * s_nb of chain kk of a replica word: the sign bit
-// of J flips where the neighbour is -1. The sum is exact on the 2^-17 grid,
-// so a balanced tree (short dependency chain) gives the same value as any
-// other order.
-__device__ __forceinline__ float gauss_field(int kk, uint32_t nxp, uint32_t nxm, uint32_t nyp,
-                                             uint32_t nym, uint32_t nzp, uint32_t nzm,
-                                             const float (&j)[6])
+// Two FP32 values in one 64-bit register pair, and the packed FP32
+// arithmetic of sm_100-class GPUs on them: one instruction rounds both
+// lanes exactly as the scalar operation would (IEEE round to nearest even,
+// no flush to zero), so pairs of chains share an issue slot.
+__device__ __forceinline__ unsigned long long f2_pack(float lo, float hi)
 {
-    const int sh = 31 - 8 * kk;
-    const float t0 = __int_as_float(__float_as_int(j[0]) ^ ((nxp << sh) & 0x80000000u));
-    const float t1 = __int_as_float(__float_as_int(j[1]) ^ ((nxm << sh) & 0x80000000u));
-    const float t2 = __int_as_float(__float_as_int(j[2]) ^ ((nyp << sh) & 0x80000000u));
-    const float t3 = __int_as_float(__float_as_int(j[3]) ^ ((nym << sh) & 0x80000000u));
-    const float t4 = __int_as_float(__float_as_int(j[4]) ^ ((nzp << sh) & 0x80000000u));
-    const float t5 = __int_as_float(__float_as_int(j[5]) ^ ((nzm << sh) & 0x80000000u));
-    return __fadd_rn(__fadd_rn(__fadd_rn(t0, t1), __fadd_rn(t2, t3)), __fadd_rn(t4, t5));
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
 }
-
-// x = -beta dE of chain kk, dE = 2 s (b + h). nbeta2 = -2 beta (exact), so
-// nbeta2 * (s (b + h)) is the same single rounding of the same product as
-// -beta * dE.
-__device__ __forceinline__ float gauss_logp(int kk, uint32_t s, float b, float hq, float nbeta2)
+__device__ __forceinline__ void f2_unpack(unsigned long long v, float &lo, float &hi)
 {
-    const uint32_t sgn = (s << (31 - 8 * kk)) & 0x80000000u;  // own spin -1 => sign bit
-    const float zf = __fadd_rn(b, hq);
-    return __fmul_rn(nbeta2, __int_as_float(__float_as_int(zf) ^ sgn));
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long f2_add(unsigned long long a, unsigned long long b)
+{
+    unsigned long long r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long f2_sub(unsigned long long a, unsigned long long b)
+{
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long f2_mul(unsigned long long a, unsigned long long b)
+{
+    unsigned long long r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b,
+                                                     unsigned long long c)
+{
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
 }
 
 // Gaussian: Metropolis on 4 chains of one replica word; nbeta2[kk] = -2 beta
-// of the chain's slot. bq[kk] receives s_new * b / qJ for the energy of
-// colour-1 sites. The four decisions come from screen_logp; if any draw of
-// the word falls in the screen's band, all four are redone with the exact
-// threshold (dE <= 0 gives x >= 0, whose threshold is 0xFFFFFFFF).
-template <bool ENERGY>
+// of the chain's slot. With energy (colour-1 sites), bq[kk] receives
+// s_new * b / qJ. The four decisions come from the screen of screen_logp,
+// evaluated for the chain pairs (0, 1) and (2, 3) in packed FP32 (the same
+// roundings: the local-field sum, b + h, -2 beta (s (b + h)), the exponent
+// x log2 e + 32, fl(r) - A and the band 2^-12 A); if any draw of the word
+// falls in the screen's band, all four are redone with the exact threshold
+// (dE <= 0 gives x >= 0, whose threshold is 0xFFFFFFFF).
 __device__ __forceinline__ uint32_t gauss_word(uint32_t s, uint32_t nxp, uint32_t nxm,
                                                uint32_t nyp, uint32_t nym, uint32_t nzp,
                                                uint32_t nzm, const float (&j)[6], float hq,
                                                const float (&nbeta2)[4],
                                                const uint32_t (&rnd)[4][4], int lane,
-                                               uint32_t valid, int (&bq)[4])
+                                               uint32_t valid, bool energy, int (&bq)[4])
 {
+    const uint32_t nb[6] = {nxp, nxm, nyp, nym, nzp, nzm};
+    const unsigned long long hq2 = f2_pack(hq, hq);
+    const unsigned long long l2e = f2_pack(1.44269502f, 1.44269502f);
+    const unsigned long long c32 = f2_pack(32.0f, 32.0f);
+    const unsigned long long band = f2_pack(2.44140625e-4f, 2.44140625e-4f);  // 2^-12
     uint32_t fm = 0;
     bool amb = false;
+    float b[4], x[4];
 #pragma unroll
-    for (int kk = 0; kk < 4; ++kk) {
-        const float b = gauss_field(kk, nxp, nxm, nyp, nym, nzp, nzm, j);
-        const float u = screen_logp(gauss_logp(kk, s, b, hq, nbeta2[kk]), rnd[kk][lane], amb);
-        fm |= (__float_as_uint(u) >> (31 - 8 * kk)) & (1u << (8 * kk));
-        if (ENERGY) {
-            const int q = __float2int_rn(__fmul_rn(b, 131072.0f));
-            bq[kk] = (((s ^ fm) >> (8 * kk)) & 1u) ? -q : q;
-        }
+    for (int q = 0; q < 2; ++q) {
+        const int k0 = 2 * q, k1 = 2 * q + 1;
+        const int sh0 = 31 - 8 * k0, sh1 = 31 - 8 * k1;
+        unsigned long long t[6];
+#pragma unroll
+        for (int d = 0; d < 6; ++d)
+            t[d] = f2_pack(__int_as_float(__float_as_int(j[d]) ^ ((nb[d] << sh0) & 0x80000000u)),
+                           __int_as_float(__float_as_int(j[d]) ^ ((nb[d] << sh1) & 0x80000000u)));
+        const unsigned long long bp = f2_add(f2_add(f2_add(t[0], t[1]), f2_add(t[2], t[3])),
+                                             f2_add(t[4], t[5]));
+        f2_unpack(bp, b[k0], b[k1]);
+        float z0, z1;
+        f2_unpack(f2_add(bp, hq2), z0, z1);
+        const unsigned long long zs =
+            f2_pack(__int_as_float(__float_as_int(z0) ^ ((s << sh0) & 0x80000000u)),
+                    __int_as_float(__float_as_int(z1) ^ ((s << sh1) & 0x80000000u)));
+        const unsigned long long xp = f2_mul(f2_pack(nbeta2[k0], nbeta2[k1]), zs);
+        f2_unpack(xp, x[k0], x[k1]);
+        float y0, y1;
+        f2_unpack(f2_fma(xp, l2e, c32), y0, y1);
+        float a0, a1;
+        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(a0) : "f"(y0));
+        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(a1) : "f"(y1));
+        const unsigned long long ap = f2_pack(a0, a1);
+        float u0, u1, w0, w1;
+        f2_unpack(f2_sub(f2_pack(__uint2float_rn(rnd[k0][lane]), __uint2float_rn(rnd[k1][lane])), ap),
+                  u0, u1);
+        f2_unpack(f2_mul(ap, band), w0, w1);
+        amb |= fabsf(u0) <= w0;
+        amb |= fabsf(u1) <= w1;
+        fm |= (__float_as_uint(u0) >> sh0) & (1u << (8 * k0));
+        fm |= (__float_as_uint(u1) >> sh1) & (1u << (8 * k1));
     }
     if (amb) {
         fm = 0;
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-            const float b = gauss_field(kk, nxp, nxm, nyp, nym, nzp, nzm, j);
-            const uint32_t flip =
-                rnd[kk][lane] <= thr_of_logp(gauss_logp(kk, s, b, hq, nbeta2[kk])) ? 1u : 0u;
-            fm |= flip << (8 * kk);
-            if (ENERGY) {
-                const int q = __float2int_rn(__fmul_rn(b, 131072.0f));
-                bq[kk] = (((s >> (8 * kk)) ^ flip) & 1u) ? -q : q;
-            }
+        for (int kk = 0; kk < 4; ++kk)
+            fm |= (rnd[kk][lane] <= thr_of_logp(x[kk]) ? 1u : 0u) << (8 * kk);
+    }
+    if (energy) {
+        const uint32_t sn = s ^ fm;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            float e0, e1;
+            f2_unpack(f2_mul(f2_pack(b[2 * q], b[2 * q + 1]), f2_pack(131072.0f, 131072.0f)), e0, e1);
+            const int q0 = __float2int_rn(e0), q1 = __float2int_rn(e1);
+            bq[2 * q] = ((sn >> (16 * q)) & 1u) ? -q0 : q0;
+            bq[2 * q + 1] = ((sn >> (16 * q + 8)) & 1u) ? -q1 : q1;
         }
     }
     return fm & valid;
@@ -421,8 +484,8 @@ __device__ __forceinline__ void half_sweep(const Smem &sm, const Ctx &cx, uint32
                                          sm.Jg[N + st.i + st.dym], sm.Jg[2 * N + st.i],
                                          sm.Jg[2 * N + st.i + st.dzm]};
                     int bq[4];
-                    fm = gauss_word<true>(s, nxp, nxm, nyp, nym, nzp, nzm, jv, cx.hq, nbeta2, rnd,
-                                          lane, valid, bq);
+                    fm = gauss_word(s, nxp, nxm, nyp, nym, nzp, nzm, jv, cx.hq, nbeta2, rnd,
+                                    lane, valid, COL == 1, bq);
                     if (COL == 1) {
 #pragma unroll
                         for (int kk = 0; kk < 4; ++kk) bg[kk] += bq[kk];
@@ -560,10 +623,10 @@ __device__ __forceinline__ void half_sweep_packed(const Smem &sm, const Ctx &cx,
                                          sm.Jg[N + st.i + st.dym], sm.Jg[2 * N + st.i],
                                          sm.Jg[2 * N + st.i + st.dzm]};
                     int bq0[4], bq1[4];
-                    fm.x = gauss_word<true>(s.x, nxp.x, nxm.x, nyp.x, nym.x, nzp.x, nzm.x, jv,
-                                            cx.hq, nbeta2, rnd[0], lane, valid, bq0);
-                    fm.y = gauss_word<true>(s.y, nxp.y, nxm.y, nyp.y, nym.y, nzp.y, nzm.y, jv,
-                                            cx.hq, nbeta2, rnd[1], lane, valid, bq1);
+                    fm.x = gauss_word(s.x, nxp.x, nxm.x, nyp.x, nym.x, nzp.x, nzm.x, jv,
+                                      cx.hq, nbeta2, rnd[0], lane, valid, COL == 1, bq0);
+                    fm.y = gauss_word(s.y, nxp.y, nxm.y, nyp.y, nym.y, nzp.y, nzm.y, jv,
+                                      cx.hq, nbeta2, rnd[1], lane, valid, COL == 1, bq1);
                     if (COL == 1) {
 #pragma unroll
                         for (int kk = 0; kk < 4; ++kk) {
@@ -750,6 +813,203 @@ __device__ __forceinline__ void half_sweep_bits(const Smem &sm, const Ctx &cx, u
     }
 }
 
+// 32-bit bit-sliced ripple add (see bs_add).
+template <int D, int K>
+__device__ __forceinline__ void bs_add32(uint32_t (&c)[D], const uint32_t (&x)[K])
+{
+    uint32_t carry = 0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        const uint32_t a = c[k];
+        const uint32_t b = k < K ? x[k] : 0u;
+        c[k] = a ^ b ^ carry;
+        carry = (a & b) | (carry & (a ^ b));
+    }
+}
+
+// Integer products through inline PTX, so that shifts by a runtime amount
+// (a multiply by a power of two held in a register) and bit-field adds
+// issue on the FMA pipe instead of the ALU pipe, which the sign flips of the
+// local field already load.
+__device__ __forceinline__ uint32_t mul_lo(uint32_t a, uint32_t b)
+{
+    uint32_t r;
+    asm("mul.lo.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+    return r;
+}
+__device__ __forceinline__ uint32_t mad_hi(uint32_t a, uint32_t b, uint32_t c)
+{
+    uint32_t r;
+    asm("mad.hi.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c));
+    return r;
+}
+
+// Local field of one chain from the neighbour words nb (the six bonds in the
+// order +x, -x, +y, -y, +z, -z, couplings j), mp = 2^(31 - p) for the chain
+// at bit p: nb * mp moves the chain's bit to bit 31, where it flips the sign
+// of the coupling. Exact on the 2^-17 grid in any order, as in gauss_field.
+__device__ __forceinline__ float gauss_field_mp(uint32_t mp, const uint32_t (&nb)[6],
+                                                const float (&j)[6])
+{
+    float t[6];
+#pragma unroll
+    for (int d = 0; d < 6; ++d)
+        t[d] = __int_as_float(__float_as_int(j[d]) ^ (mul_lo(nb[d], mp) & 0x80000000u));
+    return __fadd_rn(__fadd_rn(__fadd_rn(t[0], t[1]), __fadd_rn(t[2], t[3])), __fadd_rn(t[4], t[5]));
+}
+
+// ---------------------------------------------------------------------------
+// Half-sweep of colour COL for Gaussian couplings on the bit-per-chain state
+// in shared memory (skewed rows, bits_row). A warp task is 32 work items
+// (lane = item u: 4 consecutive colour-COL sites, one Philox counter group)
+// times one chain set: csb consecutive 4-slot groups (bytes of the site row,
+// 8 chains each: slots 4j..4j+3 of replica 0 in bits 0-3, of replica 1 in
+// bits 4-7) inside one 32-bit word of the row. The lane loads its four
+// sites' words (own spin and six neighbours) and couplings once; then, for
+// each chain of a group (the 8 unrolled), one Philox call gives the chain's
+// four random words and each site's local field is the six couplings with
+// the neighbours' sign bits. The rule, the random numbers and every
+// rounding are those of half_sweep (gauss_word: the screened test, the exact
+// threshold for draws in the band), so the result is the byte-per-chain
+// path's bit for bit; what is shared is the per-site work (indices, loads),
+// now spread over 8-32 chains instead of 4. Each decision is kept as a sign
+// bit (bit 31 set = flip), which gives both the chain's flip bit and the
+// sign of s_new * b. Lanes past the last item take a real item and store
+// nothing.
+// For COL == 1: each chain's s_new * b over the task's sites (at most
+// 128 x 96 x 2^17 < 2^31 in units 2^-17) is one warp reduction, added to
+// sm.B (which starts at 0); M by bit-sliced counters and warp transposes
+// (sm.M starts at N and each -1 among a colour-1 site and its x-partner
+// subtracts 2).
+// ---------------------------------------------------------------------------
+template <int L>
+__device__ __forceinline__ void half_sweep_bits_gauss(const Smem &sm, const Ctx &cx,
+                                                      uint32_t n_sweep, const int COL,
+                                                      const int csb)
+{
+    constexpr int N = L * L * L;
+    constexpr int U = (N / 2) / kSiteRun;
+    constexpr int NUB = (U + 31) / 32;  // blocks of 32 work items
+    constexpr int NJ = N + N / 8;       // skewed coupling plane
+    constexpr int DM = 4;               // counter planes: per lane at most 8
+    constexpr uint32_t SB = 0x80000000u;
+    const int RB = cx.RB, nt = cx.nt;
+    const int ngrp = (nt + 3) >> 2;     // 4-slot groups holding real chains
+    const int ncs = (ngrp + csb - 1) / csb;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nwarp = blockDim.x >> 5;
+    for (int tk = warp; tk < NUB * ncs; tk += nwarp) {
+        const int ub = tk / ncs, cs = tk - ub * ncs;
+        const bool live = ub * 32 + lane < U;
+        const int u = live ? ub * 32 + lane : U - 1;
+        const int g0 = cs * csb;          // first group of the set
+        const int wb = g0 & ~3;           // byte of the row word holding the set
+        const int sh0 = 8 * (g0 & 3);     // bit of the set's first chain in that word
+        uint32_t sw[4], nw[4][6];
+        float jv[4][6];
+        int own[4];
+        uint32_t xodd = 0;  // bit l: site l has odd x (its x-partner is the -x neighbour)
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+            const SiteNb<L> st(u * kSiteRun + l, COL);
+            xodd |= (uint32_t)(st.x & 1) << l;
+            own[l] = bits_row<true>(st.i, RB) + wb;
+            sw[l] = lds32(sm.spins, own[l]);
+            const int nbi[6] = {st.i + st.dxp, st.i + st.dxm, st.i + st.dyp,
+                                st.i + st.dym, st.i + st.dzp, st.i + st.dzm};
+#pragma unroll
+            for (int d = 0; d < 6; ++d) nw[l][d] = lds32(sm.spins, bits_row<true>(nbi[d], RB) + wb);
+            const int ji = bits_jidx(st.i);
+            jv[l][0] = sm.Jg[ji];
+            jv[l][1] = sm.Jg[bits_jidx(nbi[1])];
+            jv[l][2] = sm.Jg[NJ + ji];
+            jv[l][3] = sm.Jg[NJ + bits_jidx(nbi[3])];
+            jv[l][4] = sm.Jg[2 * NJ + ji];
+            jv[l][5] = sm.Jg[2 * NJ + bits_jidx(nbi[5])];
+        }
+        uint32_t fb[4] = {0u, 0u, 0u, 0u};  // flipped chains per site
+        const int gend = min(g0 + csb, ngrp);
+#pragma unroll 1
+        for (int j = g0; j < gend; ++j) {
+            const int pb = sh0 + 8 * (j - g0);    // bit of the group's chain 0
+            const uint32_t mpb = 1u << (31 - pb);
+            uint32_t gb[4] = {0u, 0u, 0u, 0u};    // the group's flips per site, bit k8
+            // the replicas' 4 chains unrolled, the replicas rolled: a body of
+            // 4 Philox calls keeps the instruction working set in cache
+#pragma unroll 1
+            for (int r = 0; r < 2; ++r)
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                const int k8 = 4 * r + kk;
+                const int t = 4 * j + kk;
+                if (t < nt) {  // padding slots (the same for the whole warp) never flip
+                    const uint32_t mp = mpb >> k8;
+                    const uint32_t c2 = ((uint32_t)COL << 24) | ((uint32_t)r << 16) | (uint32_t)t;
+                    const u32x4 o = philox10_rk(cx.k0r, cx.k1, (uint32_t)u, n_sweep, c2, cx.seed_hi);
+                    const float nbeta2 = __fmul_rn(2.0f, sm.negbeta[t]);
+                    float b[4], x[4];
+                    uint32_t so[4], dm[4];  // own sign, decision: bit 31
+                    bool amb = false;
+#pragma unroll
+                    for (int l = 0; l < 4; ++l) {
+                        b[l] = gauss_field_mp(mp, nw[l], jv[l]);
+                        so[l] = mul_lo(sw[l], mp) & SB;
+                        x[l] = __fmul_rn(nbeta2, __int_as_float(__float_as_int(__fadd_rn(b[l], cx.hq)) ^ so[l]));
+                        dm[l] = __float_as_uint(screen_logp(x[l], o.v[l], amb)) & SB;
+                    }
+                    if (amb) {
+#pragma unroll
+                        for (int l = 0; l < 4; ++l) dm[l] = o.v[l] <= thr_of_logp(x[l]) ? SB : 0u;
+                    }
+#pragma unroll
+                    for (int l = 0; l < 4; ++l) gb[l] = mad_hi(dm[l], 2u << k8, gb[l]);
+                    if (COL == 1) {
+                        int e = 0;
+#pragma unroll
+                        for (int l = 0; l < 4; ++l)  // s_new * b: the sign of b flipped where s_new = -1
+                            e += __float2int_rn(__fmul_rn(__int_as_float(__float_as_int(b[l]) ^ so[l] ^ dm[l]),
+                                                          131072.0f));
+                        e = __reduce_add_sync(0xFFFFFFFFu, live ? e : 0);
+                        if (lane == 0) atomicAdd(&sm.B[r * cx.Tp + t], (unsigned long long)(long long)e);
+                    }
+                }
+            }
+#pragma unroll
+            for (int l = 0; l < 4; ++l) fb[l] |= gb[l] << pb;
+        }
+        const uint32_t setm = (csb == 4 ? 0xFFFFFFFFu : ((1u << (8 * csb)) - 1u) << sh0);
+        uint32_t cm[DM] = {0u, 0u, 0u, 0u};
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+            const uint32_t sn = sw[l] ^ fb[l];
+            if (live) {
+                if (csb == 4)
+                    sts32(sm.spins, own[l], sn);
+                else if (csb == 2)
+                    *reinterpret_cast<uint16_t *>(sm.spins + own[l] + (g0 & 3)) = (uint16_t)(sn >> sh0);
+                else
+                    sm.spins[own[l] + (g0 & 3)] = (uint8_t)(sn >> sh0);
+            }
+            if (COL == 1) {
+                // the x-partner of a colour-1 site is its +x or -x neighbour
+                const uint32_t part = ((xodd >> l) & 1u) ? nw[l][1] : nw[l][0];
+                const uint32_t msk = live ? setm : 0u;
+                const uint32_t mm[2] = {(sn ^ part) & msk, (sn & part) & msk};
+                bs_add32<DM, 2>(cm, mm);
+            }
+        }
+        if (COL == 1) {
+            long long vm = 0;  // lane b: the -1 count of chain bit b of the word
+#pragma unroll
+            for (int k = 0; k < DM; ++k) vm += (long long)warp_column_popc(cm[k]) << k;
+            const int j = (wb + (lane >> 3)), k8 = lane & 7;
+            const int t = 4 * j + (k8 & 3), r = k8 >> 2;
+            if (((setm >> lane) & 1u) && t < nt)
+                atomicAdd(&sm.M[r * cx.Tp + t], (unsigned long long)(-2 * vm));
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Replica exchange between slots p and p+1 of each replica (pairs of one
 // parity), then the state swap of accepted pairs as byte permutations of the
@@ -849,7 +1109,8 @@ __device__ __forceinline__ void exchange_apply(const Smem &sm, const Ctx &cx)
 // an accepted pair (p, p+1) swaps bits p and p+1. Pairs of one parity are
 // disjoint, so one masked exchange per replica applies them all.
 // Sites [site0, site1) (a cluster CTA's slab; the whole lattice by default).
-template <int L>
+// SKEW: the rows at bits_row (Gaussian bit-parallel state).
+template <int L, bool SKEW = false>
 __device__ __forceinline__ void exchange_apply_packed(const Smem &sm, const Ctx &cx, int site0 = 0,
                                                       int site1 = L * L * L)
 {
@@ -857,7 +1118,7 @@ __device__ __forceinline__ void exchange_apply_packed(const Smem &sm, const Ctx 
     const unsigned long long a0 = sm.accm[0], a1 = sm.accm[1];
     if (!(a0 | a1)) return;
     for (int site = site0 + threadIdx.x; site < site1; site += blockDim.x) {
-        uint8_t *row = sm.spins + (size_t)site * RB;
+        uint8_t *row = sm.spins + bits_row<SKEW>(site, RB);
         unsigned long long w0 = 0, w1 = 0;
         for (int jj = 0; jj < WR; ++jj) {
             const unsigned long long b = row[jj];
@@ -969,7 +1230,7 @@ __device__ __forceinline__ void measure_energies(const Smem &sm, const Ctx &cx, 
 // instances): only the sites of this CTA's z-planes [cx.z0, cx.z1), i.e.
 // the partial xy marginal over those planes and the complete xz and yz lines
 // inside them (the other lines count 0).
-template <int L, bool PACK, bool SLAB = false>
+template <int L, bool PACK, bool SLAB = false, bool SKEW = false>
 __device__ __forceinline__ void measure_marginals(const Smem &sm, const Ctx &cx, int j0, int nw)
 {
     constexpr int LL = L * L;
@@ -1003,7 +1264,7 @@ __device__ __forceinline__ void measure_marginals(const Smem &sm, const Ctx &cx,
             } else if constexpr (PACK) {  // q of the group's 4 slots: the two nibbles' xor
 #pragma unroll 4
                 for (int m = 0; m < L; ++m) {
-                    const uint32_t b = sm.spins[(size_t)(base + m * step) * RB + j0 + jj];
+                    const uint32_t b = sm.spins[bits_row<SKEW>(base + m * step, RB) + j0 + jj];
                     cnt += expand4((b ^ (b >> 4)) & 15u);
                 }
             } else {
@@ -1124,22 +1385,25 @@ __device__ __forceinline__ void measure_projections(const Smem &sm, const Ctx &c
     }
 }
 
-template <int L, bool PACK>
+template <int L, bool PACK, bool SKEW = false>
 __device__ __forceinline__ void measure_step(const Smem &sm, const Ctx &cx, const Int8Args &a,
                                              int bin)
 {
     // energies and magnetisations first, so that the projection phase reads
     // nothing the next sweep overwrites
     measure_energies(sm, cx, a, bin);
-    for (int j0 = 0; j0 < cx.WR; j0 += a.mchunk) {
-        const int nw = min(a.mchunk, cx.WR - j0);
-        measure_marginals<L, PACK>(sm, cx, j0, nw);
+    // only the words holding real slots (the bit-per-chain rows are padded
+    // to 32 slots)
+    const int WRv = (cx.nt + 3) >> 2;
+    for (int j0 = 0; j0 < WRv; j0 += a.mchunk) {
+        const int nw = min(a.mchunk, WRv - j0);
+        measure_marginals<L, PACK, false, SKEW>(sm, cx, j0, nw);
         __syncthreads();
         measure_projections<L>(sm, cx, a, bin, j0, nw);
         // the next chunk's marginals overwrite this chunk's; after the last
         // chunk the next sweep touches nothing this phase reads (spins, B and
         // M are not read here), so no barrier is needed
-        if (j0 + a.mchunk < cx.WR) __syncthreads();
+        if (j0 + a.mchunk < WRv) __syncthreads();
     }
 }
 
@@ -1159,12 +1423,42 @@ __device__ __forceinline__ void copy16_cg(void *dst, const void *src, size_t byt
     for (size_t k = threadIdx.x; k < bytes / 16; k += blockDim.x) d[k] = __ldcg(s + k);
 }
 
+// The Gaussian bit-parallel state between its global-memory rows [N][RB]
+// and the skewed shared-memory rows (bits_row), 4 bytes per thread and step
+// (RB is 8 or 16): IN copies to shared memory (through L2 only with CG).
+template <bool IN, bool CG>
+__device__ __forceinline__ void copy_rows_skewed(uint8_t *smem, uint8_t *gmem, int N, int RB)
+{
+    const int lrb = RB == 16 ? 4 : 3;
+    for (int k = threadIdx.x; k < N * RB / 4; k += blockDim.x) {
+        const int i = (4 * k) >> lrb;
+        const int so = bits_row<true>(i, RB) + 4 * k - (i << lrb);
+        uint32_t *g = reinterpret_cast<uint32_t *>(gmem) + k;
+        uint32_t *sp = reinterpret_cast<uint32_t *>(smem + so);
+        if (IN)
+            *sp = CG ? __ldcg(g) : *g;
+        else
+            *g = *sp;
+    }
+}
+
+// Couplings [3][N] into the skewed planes [3][N + N/8] (bits_jidx).
+__device__ __forceinline__ void copy_couplings_skewed(float *smem, const float *gmem, int N)
+{
+    const int NJ = N + N / 8;
+    for (int k = threadIdx.x; k < 3 * N; k += blockDim.x) {
+        const int d = k / N, i = k - d * N;
+        smem[d * NJ + bits_jidx(i)] = gmem[k];
+    }
+}
+
 
 // ---------------------------------------------------------------------------
 // The fused kernel: for each sample of this CTA, load, run n_sweeps sweeps
 // (half-sweeps, energies, exchange, measurement), store.
 // ---------------------------------------------------------------------------
-// BITS: the packed state in shared memory, swept bit-parallel (+-J).
+// BITS: the packed state in shared memory, swept bit-parallel (+-J), or by
+// chain sets of the bit-per-chain rows (Gaussian couplings).
 template <int L, bool GST, bool WIDE, bool BITS>
 struct Bounds {
     static constexpr int threads = BITS ? kBitsThreads : KernelBounds<L, GST, WIDE>::threads;
@@ -1186,6 +1480,7 @@ __global__ void __launch_bounds__(Bounds<L, GST, WIDE, BITS>::threads,
     cx.Tp = a.Tp;
     // global-memory instances and the bit-parallel ones keep the packed state
     constexpr bool PACK = GST || BITS;
+    constexpr bool SKEW = BITS && GAUSS;  // skewed rows (bits_row)
     cx.WR = a.Tp / 4;
     cx.RB = PACK ? a.Tp / 4 : 2 * a.Tp;
     cx.seed_lo = a.seed_lo;
@@ -1256,6 +1551,12 @@ __global__ void __launch_bounds__(Bounds<L, GST, WIDE, BITS>::threads,
                 sm.J8 = const_cast<uint8_t *>(a.J8) + (size_t)s * N * 8;
             else
                 sm.Jg = const_cast<float *>(a.Jg) + (size_t)s * 3 * N;
+        } else if (SKEW) {
+            if (segd)
+                copy_rows_skewed<true, true>(sm.spins, a.spins + (size_t)s * N * cx.RB, N, cx.RB);
+            else
+                copy_rows_skewed<true, false>(sm.spins, a.spins + (size_t)s * N * cx.RB, N, cx.RB);
+            copy_couplings_skewed(sm.Jg, a.Jg + (size_t)s * 3 * N, N);
         } else {
             if (segd)
                 copy16_cg(sm.spins, a.spins + (size_t)s * N * cx.RB, (size_t)N * cx.RB);
@@ -1292,7 +1593,9 @@ __global__ void __launch_bounds__(Bounds<L, GST, WIDE, BITS>::threads,
                 if (stop) break;
             }
             auto colour = [&](const int col) {
-                if constexpr (BITS)
+                if constexpr (BITS && GAUSS)
+                    half_sweep_bits_gauss<L>(sm, cx, (uint32_t)n, col, a.csb);
+                else if constexpr (BITS)
                     half_sweep_bits<L>(sm, cx, (uint32_t)n, col);
                 else if constexpr (PACK)
                     half_sweep_packed<L, GAUSS>(sm, cx, (uint32_t)n, col);
@@ -1300,12 +1603,14 @@ __global__ void __launch_bounds__(Bounds<L, GST, WIDE, BITS>::threads,
                     half_sweep<L, GAUSS>(sm, cx, (uint32_t)n, col);
                 if (col == 0)  // the bit-parallel sweep subtracts from 3N and N
                     for (int k = threadIdx.x; k < 2 * a.Tp; k += blockDim.x) {
-                        sm.B[k] = BITS ? 3ull * N : 0ull;
+                        sm.B[k] = (BITS && !GAUSS) ? 3ull * N : 0ull;
                         sm.M[k] = BITS ? (unsigned long long)N : 0ull;
                     }
                 __syncthreads();
             };
-            if constexpr (BITS || unroll_colours<L, GAUSS, GST, WIDE>()) {
+            // the Gaussian bit-per-chain sweep keeps one code path for both
+            // colours (its unrolled chain bodies are large)
+            if constexpr (BITS ? !GAUSS : unroll_colours<L, GAUSS, GST, WIDE>()) {
                 colour(0);
                 colour(1);
             } else {
@@ -1318,16 +1623,19 @@ __global__ void __launch_bounds__(Bounds<L, GST, WIDE, BITS>::threads,
                 if (threadIdx.x < 32) exchange_decide(sm, cx, a, (int)(e & 1), (uint32_t)n, 0u, stamp);
                 __syncthreads();
                 if constexpr (PACK)
-                    exchange_apply_packed<L>(sm, cx);
+                    exchange_apply_packed<L, SKEW>(sm, cx);
                 else
                     exchange_apply<L>(sm, cx);
                 __syncthreads();
             }
             if (n >= a.n_therm && (n - a.n_therm) % a.measure_every == 0)
-                measure_step<L, PACK>(sm, cx, a, log_bin(n, a.n_bins));
+                measure_step<L, PACK, SKEW>(sm, cx, a, log_bin(n, a.n_bins));
         }
         __syncthreads();
-        if (!GST) copy16(a.spins + (size_t)s * N * cx.RB, sm.spins, (size_t)N * cx.RB);
+        if (SKEW)
+            copy_rows_skewed<false, false>(sm.spins, a.spins + (size_t)s * N * cx.RB, N, cx.RB);
+        else if (!GST)
+            copy16(a.spins + (size_t)s * N * cx.RB, sm.spins, (size_t)N * cx.RB);
         for (int k = threadIdx.x; k < 2 * a.Tp; k += blockDim.x) {
             a.B[s * 2 * a.Tp + k] = (int64_t)sm.B[k];
             a.M[s * 2 * a.Tp + k] = (int64_t)sm.M[k];

@@ -55,6 +55,9 @@ struct Int8Args {
     // k0r[r] = k0 + r * 0x9E3779B9, fixed per launch, read as constant
     // operands instead of the per-round key increment
     uint32_t k0r[10];
+    // bit-parallel state with Gaussian couplings: 4-slot groups (bytes of a
+    // site row) in the chain set of one warp task, 1, 2 or 4
+    int csb;
 };
 
 struct Int8Launch {
@@ -63,7 +66,8 @@ struct Int8Launch {
     bool gst;   // state kept in global memory (large L) instead of shared memory
     bool wide;  // shared-memory state, one CTA of up to 512 threads per SM (L = 10, 12)
     int cluster;  // > 1: global-memory state, each sample swept by a cluster of this many CTAs
-    bool bits;    // packed state in shared memory, swept bit-parallel (+-J)
+    bool bits;    // packed state in shared memory, swept bit-parallel
+    int csb;      // bit-parallel Gaussian sweep: 4-slot groups per warp task's chain set
 };
 
 // Shared-memory bytes of the fused kernel, or 0 when the state does not fit
@@ -91,14 +95,16 @@ bool int8_gst_has(int L);
 cudaError_t int8_launch_gst(int L, bool gauss, const Int8Args &a, const Int8Launch &cfg,
                             cudaStream_t st);
 int int8_ctas_per_sm_gst(int L, bool gauss, int threads, size_t smem);
-// The bit-parallel instances (+-J, packed state in shared memory, slots
-// padded to a multiple of 32 so that a site row is whole 64-bit words; the
-// CTA's warps a multiple of the words per site), in their own translation
-// unit.
+// The bit-parallel instances (packed state in shared memory, slots padded
+// to a multiple of 32 so that a site row is whole 64-bit words; +-J and
+// Gaussian couplings), in their own translation units.
 bool int8_bits_has(int L);
-size_t int8_smem_bytes_bits(int L, int Tp, int mchunk);
-cudaError_t int8_launch_bits(int L, const Int8Args &a, const Int8Launch &cfg, cudaStream_t st);
-int int8_ctas_per_sm_bits(int L, int threads, size_t smem);
+size_t int8_smem_bytes_bits(int L, int Tp, int mchunk, bool gauss);
+cudaError_t int8_launch_bits(int L, bool gauss, const Int8Args &a, const Int8Launch &cfg,
+                             cudaStream_t st);
+int int8_ctas_per_sm_bits(int L, bool gauss, int threads, size_t smem);
+cudaError_t int8_launch_bits_gauss(int L, const Int8Args &a, const Int8Launch &cfg, cudaStream_t st);
+int int8_ctas_per_sm_bits_gauss(int L, int threads, size_t smem);
 // The cluster instances (one sample per thread-block cluster of k = 2, 4 or
 // 8 CTAs, each sweeping L/k z-planes of the packed global-memory state), for
 // L = 20, 24, 28, 32, 40, 48, 64; in their own translation unit. cfg.grid must be a

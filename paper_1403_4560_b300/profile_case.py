@@ -34,6 +34,7 @@ def main():
     ap.add_argument("--measure-every", type=int, default=1)
     ap.add_argument("--state-mode", type=int, default=0)
     ap.add_argument("--cluster", type=int, default=0)
+    ap.add_argument("--chain-set", type=int, default=0)
     ap.add_argument("--h", type=float, default=0.2)
     args = ap.parse_args()
 
@@ -46,7 +47,7 @@ def main():
     stream = torch.cuda.current_stream()
     opt = dict(threads_per_block=args.threads, layout=args.layout, n_therm=args.n_therm,
                exchange_every=args.exchange_every, measure_every=args.measure_every,
-               state_mode=args.state_mode, cluster=args.cluster)
+               state_mode=args.state_mode, cluster=args.cluster, chain_set=args.chain_set)
     if args.layout == sgmc.SG_LAYOUT_MSC64:
         opt["rng_group"] = 64
     with sgmc.Ensemble(args.L, args.h, T, args.dist, args.samples, 7, J=J, spins=s0,
@@ -63,7 +64,8 @@ def main():
         print(json.dumps({"L": args.L, "dist": args.dist, "samples": args.samples,
                           "nt": args.nt, "sweeps": args.sweeps, "n_therm": args.n_therm,
                           "exchange_every": args.exchange_every,
-                          "threads": args.threads, "state_mode": args.state_mode,
+                          "threads": ens.info().threads_per_block,
+                          "chain_set": ens.info().chain_set, "state_mode": args.state_mode,
                           "ms": ms,
                           "attempts_per_ns": att / (ms * 1e6)}))
 

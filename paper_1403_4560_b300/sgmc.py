@@ -35,7 +35,8 @@ class Options(ctypes.Structure):
                 ("sweeps_per_launch", ctypes.c_int32), ("watchdog_cycles", ctypes.c_uint64),
                 ("sample_base", ctypes.c_int64), ("log_bins", ctypes.c_int32),
                 ("pq_hist", ctypes.c_int32), ("state_mode", ctypes.c_int32),
-                ("segments", ctypes.c_int32), ("cluster", ctypes.c_int32)]
+                ("segments", ctypes.c_int32), ("cluster", ctypes.c_int32),
+                ("chain_set", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -44,7 +45,8 @@ class Info(ctypes.Structure):
                 ("attempts_per_sweep", ctypes.c_int64), ("device_bytes", ctypes.c_size_t),
                 ("log_bins", ctypes.c_int32), ("pq_hist", ctypes.c_int32),
                 ("threads_per_block", ctypes.c_int32), ("grid", ctypes.c_int32),
-                ("state_in_shared", ctypes.c_int32), ("cluster", ctypes.c_int32)]
+                ("state_in_shared", ctypes.c_int32), ("cluster", ctypes.c_int32),
+                ("chain_set", ctypes.c_int32)]
 
 
 class TuneReport(ctypes.Structure):
@@ -171,7 +173,10 @@ def _ptr(a: np.ndarray):
 def default_options(**kw) -> Options:
     o = Options()
     lib().sg_options_default(ctypes.byref(o))
+    names = {f for f, _ in Options._fields_}
     for k, v in kw.items():
+        if k not in names:
+            raise TypeError(f"unknown sg_options field {k!r}")
         setattr(o, k, v)
     return o
 

@@ -149,9 +149,9 @@ def test_state_mode_requests_that_cannot_be_met_are_rejected():
     with pytest.raises(sgmc.SgError) as ei:  # no global-memory kernel below L = 10
         sgmc.Ensemble(8, 0.2, T, "gauss", 4, 1, state_mode=2)
     assert ei.value.status == sgmc.SG_EUNSUPPORTED
-    with pytest.raises(sgmc.SgError) as ei:
-        sgmc.Ensemble(8, 0.2, T, "gauss", 4, 1, state_mode=3)
-    assert ei.value.status == sgmc.SG_EINVAL
+    with pytest.raises(sgmc.SgError) as ei:  # one bit per chain: L = 4..16 only
+        sgmc.Ensemble(18, 0.2, T, "gauss", 4, 1, state_mode=3)
+    assert ei.value.status == sgmc.SG_EUNSUPPORTED
 
 
 @pytest.mark.parametrize("nt,dist", [(64, "pmj"), (1, "gauss"), (9, "gauss")])
