@@ -253,6 +253,29 @@ __device__ __forceinline__ uint32_t pmj_word(uint32_t s, uint32_t nxp, uint32_t 
     return fm & valid;
 }
 
+// Integer products through inline PTX, so that shifts by a runtime amount
+// (a multiply by a power of two held in a register) and bit-field adds
+// issue on the FMA pipe instead of the ALU pipe, which the sign flips of the
+// local field already load.
+__device__ __forceinline__ uint32_t mul_lo(uint32_t a, uint32_t b)
+{
+    uint32_t r;
+    asm("mul.lo.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+    return r;
+}
+__device__ __forceinline__ uint32_t mad_lo(uint32_t a, uint32_t b, uint32_t c)
+{
+    uint32_t r;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c));
+    return r;
+}
+__device__ __forceinline__ uint32_t mad_hi(uint32_t a, uint32_t b, uint32_t c)
+{
+    uint32_t r;
+    asm("mad.hi.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c));
+    return r;
+}
+
 // Two FP32 values in one 64-bit register pair, and the packed FP32
 // arithmetic of sm_100-class GPUs on them: one instruction rounds both
 // lanes exactly as the scalar operation would (IEEE round to nearest even,
@@ -313,26 +336,26 @@ __device__ __forceinline__ uint32_t gauss_word(uint32_t s, uint32_t nxp, uint32_
     const unsigned long long l2e = f2_pack(1.44269502f, 1.44269502f);
     const unsigned long long c32 = f2_pack(32.0f, 32.0f);
     const unsigned long long band = f2_pack(2.44140625e-4f, 2.44140625e-4f);  // 2^-12
-    uint32_t fm = 0;
+    // the sign bit of chain kk's value flipped where bit 8 kk of w is set;
+    // for kk = 0, J + w * 2^31 flips exactly bit 31 (one multiply-add)
+    auto flip = [](float v, uint32_t w, int kk) {
+        return kk == 0 ? __uint_as_float(mad_lo(w, 0x80000000u, __float_as_uint(v)))
+                       : __uint_as_float(__float_as_uint(v) ^ ((w << (31 - 8 * kk)) & 0x80000000u));
+    };
     bool amb = false;
-    float b[4], x[4];
+    float b[4], x[4], u[4];
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
         const int k0 = 2 * q, k1 = 2 * q + 1;
-        const int sh0 = 31 - 8 * k0, sh1 = 31 - 8 * k1;
         unsigned long long t[6];
 #pragma unroll
-        for (int d = 0; d < 6; ++d)
-            t[d] = f2_pack(__int_as_float(__float_as_int(j[d]) ^ ((nb[d] << sh0) & 0x80000000u)),
-                           __int_as_float(__float_as_int(j[d]) ^ ((nb[d] << sh1) & 0x80000000u)));
+        for (int d = 0; d < 6; ++d) t[d] = f2_pack(flip(j[d], nb[d], k0), flip(j[d], nb[d], k1));
         const unsigned long long bp = f2_add(f2_add(f2_add(t[0], t[1]), f2_add(t[2], t[3])),
                                              f2_add(t[4], t[5]));
         f2_unpack(bp, b[k0], b[k1]);
         float z0, z1;
         f2_unpack(f2_add(bp, hq2), z0, z1);
-        const unsigned long long zs =
-            f2_pack(__int_as_float(__float_as_int(z0) ^ ((s << sh0) & 0x80000000u)),
-                    __int_as_float(__float_as_int(z1) ^ ((s << sh1) & 0x80000000u)));
+        const unsigned long long zs = f2_pack(flip(z0, s, k0), flip(z1, s, k1));
         const unsigned long long xp = f2_mul(f2_pack(nbeta2[k0], nbeta2[k1]), zs);
         f2_unpack(xp, x[k0], x[k1]);
         float y0, y1;
@@ -341,15 +364,19 @@ __device__ __forceinline__ uint32_t gauss_word(uint32_t s, uint32_t nxp, uint32_
         asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(a0) : "f"(y0));
         asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(a1) : "f"(y1));
         const unsigned long long ap = f2_pack(a0, a1);
-        float u0, u1, w0, w1;
+        float w0, w1;
         f2_unpack(f2_sub(f2_pack(__uint2float_rn(rnd[k0][lane]), __uint2float_rn(rnd[k1][lane])), ap),
-                  u0, u1);
+                  u[k0], u[k1]);
         f2_unpack(f2_mul(ap, band), w0, w1);
-        amb |= fabsf(u0) <= w0;
-        amb |= fabsf(u1) <= w1;
-        fm |= (__float_as_uint(u0) >> sh0) & (1u << (8 * k0));
-        fm |= (__float_as_uint(u1) >> sh1) & (1u << (8 * k1));
+        amb |= fabsf(u[k0]) <= w0;
+        amb |= fabsf(u[k1]) <= w1;
     }
+    // the decisions are the sign bits: the top bytes of the four u gathered
+    // into one word, bit 7 of each byte moved to bit 0
+    const uint32_t top = __byte_perm(__byte_perm(__float_as_uint(u[0]), __float_as_uint(u[1]), 0x0073),
+                                     __byte_perm(__float_as_uint(u[2]), __float_as_uint(u[3]), 0x0073),
+                                     0x5410);
+    uint32_t fm = (top >> 7) & 0x01010101u;
     if (amb) {
         fm = 0;
 #pragma unroll
@@ -825,23 +852,6 @@ __device__ __forceinline__ void bs_add32(uint32_t (&c)[D], const uint32_t (&x)[K
         c[k] = a ^ b ^ carry;
         carry = (a & b) | (carry & (a ^ b));
     }
-}
-
-// Integer products through inline PTX, so that shifts by a runtime amount
-// (a multiply by a power of two held in a register) and bit-field adds
-// issue on the FMA pipe instead of the ALU pipe, which the sign flips of the
-// local field already load.
-__device__ __forceinline__ uint32_t mul_lo(uint32_t a, uint32_t b)
-{
-    uint32_t r;
-    asm("mul.lo.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
-    return r;
-}
-__device__ __forceinline__ uint32_t mad_hi(uint32_t a, uint32_t b, uint32_t c)
-{
-    uint32_t r;
-    asm("mad.hi.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c));
-    return r;
 }
 
 // Local field of one chain from the neighbour words nb (the six bonds in the
