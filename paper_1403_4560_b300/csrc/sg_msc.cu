@@ -239,12 +239,30 @@ __device__ __forceinline__ void msc_half(const MscSmem &sm, const MscArgs &a, in
 #pragma unroll
     for (int k = 0; k < kDM; ++k) cm[k] = 0;
     const uint32_t c2 = ((uint32_t)c << 24) | ((uint32_t)r << 16) | (uint32_t)t;
-    for (int grp = tid; grp < NG; grp += tpc) {
-        const u32x4 rnd = philox10(a.seed_lo ^ kTagMet, (uint32_t)(g + a.s_key0 / 64), (uint32_t)grp, n_sweep, c2,
-                                   a.seed_hi);
+    // A warp of the team takes blocks of 32 Philox groups (128 colour
+    // sites): lane l draws the four random words of group 32 blk + l, then
+    // the warp updates the block's sites in four steps of 32 consecutive
+    // colour sites, each lane taking its site's word by a shuffle from the
+    // lane that drew it. Consecutive lanes so read consecutive site words
+    // (in shared memory, and the couplings through L1), where a lane per
+    // group would put the lanes' words 8 sites apart, in two banks.
+    constexpr int NB = (NG + 31) / 32;
+    const int lane = threadIdx.x & 31;
+    for (int blk = tid >> 5; blk < NB; blk += tpc >> 5) {
+        const u32x4 rnd = philox10(a.seed_lo ^ kTagMet, (uint32_t)(g + a.s_key0 / 64),
+                                   (uint32_t)(32 * blk + lane), n_sweep, c2, a.seed_hi);
 #pragma unroll
-        for (int lane = 0; lane < 4; ++lane) {
-            const MscSite<L> st(4 * grp + lane, c);
+        for (int step = 0; step < 4; ++step) {
+            const int src = 8 * step + (lane >> 2);
+            const uint32_t w0 = __shfl_sync(0xFFFFFFFFu, rnd.v[0], src);
+            const uint32_t w1 = __shfl_sync(0xFFFFFFFFu, rnd.v[1], src);
+            const uint32_t w2 = __shfl_sync(0xFFFFFFFFu, rnd.v[2], src);
+            const uint32_t w3 = __shfl_sync(0xFFFFFFFFu, rnd.v[3], src);
+            const int jj = 128 * blk + 32 * step + lane;
+            if (jj >= N / 2) continue;
+            const int k = lane & 3;  // the site's place in its group = its word
+            const uint32_t rr = k == 0 ? w0 : k == 1 ? w1 : k == 2 ? w2 : w3;
+            const MscSite<L> st(jj, c);
             const int i = st.i;
             const uint64_t s = w[i];
             const uint64_t n0 = w[i + st.dxp], n1 = w[i + st.dxm];
@@ -262,7 +280,6 @@ __device__ __forceinline__ void msc_half(const MscSmem &sm, const MscArgs &a, in
             const uint64_t sb = d3 ^ d4 ^ d5, cb = (d3 & d4) | (d5 & (d3 ^ d4));
             const uint64_t u0 = sa ^ sb, cc = sa & sb;
             const uint64_t u1 = ca ^ cb ^ cc, u2 = (ca & cb) | (cc & (ca ^ cb));
-            const uint32_t rr = rnd.v[lane];
             const uint64_t acc0 = ge_const(u0, u1, u2, ustar_of(thr, rr));      // s = +1
             const uint64_t acc1 = ge_const(u0, u1, u2, ustar_of(thr + 8, rr));  // s = -1
             const uint64_t f = (~s & acc0) | (s & acc1);
@@ -282,7 +299,6 @@ __device__ __forceinline__ void msc_half(const MscSmem &sm, const MscArgs &a, in
     }
     if (c == 1) {
         // per-sample column counts: warp transpose-popc of every plane half
-        const int lane = threadIdx.x & 31;
         long long vu_lo = 0, vu_hi = 0, vm_lo = 0, vm_hi = 0;
 #pragma unroll
         for (int k = 0; k < kDU; ++k) {
