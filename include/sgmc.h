@@ -418,12 +418,12 @@ sg_status sg_get_info(const sg_ensemble *e, sg_info *out);
  * wave would give some SMs one CTA more than others (then k >= 3 CTAs on
  * every SM), each sample's sweeps are split into segments that the CTAs
  * claim in order (sg_options.segments). MSC64 runs one launch per sweep;
- * at L >= 14 a call whose sweeps all thermalise (global sweep index below
- * n_therm) runs each exchange unit as two CTAs, one per replica (twice the
- * grid), and calls with a measured sweep run the fused unit CTAs.
- *   grid      CTAs of each launch (may be NULL)
+ * at L >= 14 (library CTA size) each exchange unit runs as two CTAs, one per
+ * replica (twice the grid), and every measured sweep adds one launch of the
+ * overlap measurement (one CTA per slot and word group).
+ *   grid      CTAs of each sweep launch (may be NULL)
  *   segments  segments per sample of the first launch, 1 = unsplit (may be NULL)
- *   launches  fused-kernel launches of the call (may be NULL)
+ *   launches  kernel launches of the call (may be NULL)
  * SG_EINVAL for a NULL ensemble or n_sweeps < 0. Touches no device state.
  */
 sg_status sg_launch_plan(const sg_ensemble *e, int64_t n_sweeps, int32_t *grid,

@@ -934,11 +934,10 @@ static unsigned long long segment_wait_cycles(const sg_ensemble *e, int n_sweeps
     return std::min(std::max(want, 1ull << 24), 1ull << 30);
 }
 
-// Whether the next n sweeps of e (global indices sweeps_done ..) are all
-// before n_therm, i.e. none is measured.
-static bool msc_thermalising(const sg_ensemble *e, int64_t n)
+// Whether global sweep n of e is measured.
+static bool msc_measured(const sg_ensemble *e, int64_t n)
 {
-    return e->sweeps_done + n <= e->opt.n_therm;
+    return n >= e->opt.n_therm && (n - e->opt.n_therm) % e->opt.measure_every == 0;
 }
 
 static sg_status launch_sweeps(sg_ensemble *e, int64_t n, cudaStream_t s, bool device_counter)
@@ -948,10 +947,14 @@ static sg_status launch_sweeps(sg_ensemble *e, int64_t n, cudaStream_t s, bool d
         MscArgs a = make_msc_args(e);
         if (device_counter) a.sweep0_dev = e->sweep_ctr;
         const int threads = msc_threads(e->L, e->opt.threads_per_block);
-        const bool split = msc_split(e->L, e->opt.threads_per_block) && msc_thermalising(e, n);
+        const bool split = msc_split(e->L, e->opt.threads_per_block);
         for (int64_t k = 0; k < n; ++k) {
             a.sweep_offset = (int)k;
             SG_CUDA(msc_sweep(a, e->L, threads, s, split), "MSC sweep kernel launch");
+            // a split sweep is measured by a kernel of its own (with a device
+            // sweep counter the host cannot tell, and the kernel decides)
+            if (split && (device_counter || msc_measured(e, e->sweeps_done + k)))
+                SG_CUDA(msc_measure_split(a, e->L, s), "MSC measurement kernel launch");
         }
         if (device_counter) SG_CUDA(advance_counter(e->sweep_ctr, n, s), "counter");
         return SG_OK;
@@ -1015,13 +1018,12 @@ sg_status sg_sweep_batch(sg_ensemble *const *es, int n_ens, int64_t n, int use_g
     }
     // graph path: the sweep index comes from a device counter, so one
     // instantiated graph serves every call with the same ensembles and n
-    // the key holds each ensemble's kernel choice that depends on the sweep
-    // index (multispin-coded launches without a measured sweep run split)
+    // (no kernel choice depends on the sweep index: the kernels decide on
+    // the device which sweeps they measure)
     std::string key = std::to_string(n);
     for (int k = 0; k < n_ens; ++k) {
         char buf[40];
-        std::snprintf(buf, sizeof buf, ":%p%s", (void *)es[k],
-                      es[k]->msc && msc_thermalising(es[k], n) ? "t" : "");
+        std::snprintf(buf, sizeof buf, ":%p", (void *)es[k]);
         key += buf;
     }
     cudaGraphExec_t exec = nullptr;
@@ -1413,9 +1415,12 @@ sg_status sg_launch_plan(const sg_ensemble *e, int64_t n_sweeps, int32_t *grid, 
     if (!e || n_sweeps < 0) return fail(SG_EINVAL, "bad arguments");
     int g = 0, seg = 1, nl = 0;
     if (e->msc) {
-        const bool split = msc_split(e->L, e->opt.threads_per_block) && msc_thermalising(e, n_sweeps);
+        const bool split = msc_split(e->L, e->opt.threads_per_block);
         g = (e->nt / 2 + 1) * (int)(e->S / 64) * (split ? 2 : 1);
-        nl = (int)std::min<int64_t>(n_sweeps, INT32_MAX);
+        int64_t meas = 0;  // measurement launches of split sweeps
+        if (split)
+            for (int64_t k = 0; k < n_sweeps; ++k) meas += msc_measured(e, e->sweeps_done + k) ? 1 : 0;
+        nl = (int)std::min<int64_t>(n_sweeps + meas, INT32_MAX);
     } else if (n_sweeps > 0) {
         int64_t chunk = e->opt.sweeps_per_launch > 0 ? e->opt.sweeps_per_launch : n_sweeps;
         chunk = std::min<int64_t>(std::max<int64_t>(chunk, 1), 1 << 30);

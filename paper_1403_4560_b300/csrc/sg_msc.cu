@@ -322,7 +322,9 @@ __device__ __forceinline__ void msc_half(const MscSmem &sm, const MscArgs &a, in
 // bit-sliced 2D marginals, bit-sliced projections, then per sample the
 // integer projections, the FP32 DFT and the FP64 accumulation.
 // ---------------------------------------------------------------------------
-template <int L, bool WIDE>
+// QW: sm.w holds the slots' overlap words q = w(r=0) ^ w(r=1) themselves (N
+// words per slot) rather than the two replica chains.
+template <int L, bool WIDE, bool QW = false>
 __device__ __forceinline__ void msc_measure(const MscSmem &sm, const MscArgs &a, int g, int k0,
                                             int nk, int t0, int bin, uint64_t *w_dst, int nw)
 {
@@ -337,7 +339,7 @@ __device__ __forceinline__ void msc_measure(const MscSmem &sm, const MscArgs &a,
     // (A) marginal counts of q = -1 (bit set) over the summed axis
     for (int id = threadIdx.x; id < nk * 3 * LL; id += blockDim.x) {
         const int kk = id / (3 * LL), pid = id - kk * (3 * LL);
-        const uint64_t *w0 = sm.w + (size_t)(2 * (k0 + kk)) * N;
+        const uint64_t *w0 = sm.w + (size_t)((QW ? 1 : 2) * (k0 + kk)) * N;
         const uint64_t *w1 = w0 + N;
         uint64_t *margk = sm.marg + (size_t)kk * 3 * LL * kDG;
         const int plane = pid / LL, ab = pid % LL;
@@ -362,7 +364,7 @@ __device__ __forceinline__ void msc_measure(const MscSmem &sm, const MscArgs &a,
             int mm = m + rot;
             if (mm >= L) mm -= L;
             const int i = base + mm * step;
-            qs[m] = m < L ? (w0[i] ^ w1[i]) : 0ull;
+            qs[m] = m < L ? (QW ? w0[i] : (w0[i] ^ w1[i])) : 0ull;
         }
         uint64_t cnt[kDG];
         count16(qs, cnt);
@@ -370,7 +372,9 @@ __device__ __forceinline__ void msc_measure(const MscSmem &sm, const MscArgs &a,
         for (int p = 0; p < kDG; ++p) margk[((size_t)plane * LL + A * L + Bc) * kDG + p] = cnt[p];
     }
     __syncthreads();
-    if constexpr (msc_proj_in_w(L, msc_measured_slots(L, WIDE))) {
+    // (with QW the projections may take the overlap words' space: the
+    // barrier above ends every read of them)
+    if constexpr (!QW && msc_proj_in_w(L, msc_measured_slots(L, WIDE))) {
         // the chains are final: store them now (unless they are stored
         // already), their space takes the projections
         if (w_dst)
@@ -739,6 +743,64 @@ __global__ void __launch_bounds__(kMscSplitThreads, 3) msc_split_sweep_kernel(co
     }
 }
 
+// ---------------------------------------------------------------------------
+// Overlap measurement after a split sweep (L >= 14): one CTA per (slot t,
+// word group g) reads the slot's two replica chains as stored by
+// msc_split_sweep_kernel (after the sweep and the exchange), keeps their
+// overlap words q = w(r=0) ^ w(r=1) in shared memory, and runs the three
+// phases of msc_measure for that slot, with the energies from B and M as
+// stored. The counts, their order and every rounding are those of the fused
+// kernel's measurement, so the accumulators are identical. The CTA needs
+// the overlap words, the marginals and the energies (about 66 KB at L = 16,
+// the projections taking the words' space), so three share an SM and
+// overlap one another's phases, where the fused kernel measured inside its
+// one 197 KB CTA per SM. A sweep that is not measured returns at once.
+// ---------------------------------------------------------------------------
+constexpr int kMscMeasThreads = 256;
+
+__host__ __device__ inline size_t msc_carve_meas(uint8_t *base, int L, MscSmem *sm)
+{
+    const size_t N = (size_t)L * L * L;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        uint8_t *p = base ? base + off : nullptr;
+        off = a16(off + bytes);
+        return p;
+    };
+    MscSmem s{};
+    s.w = reinterpret_cast<uint64_t *>(take(N * 8));
+    s.B = reinterpret_cast<long long *>(take(2 * 64 * 8));
+    s.M = reinterpret_cast<long long *>(take(2 * 64 * 8));
+    s.marg = reinterpret_cast<uint64_t *>(take((size_t)3 * L * L * kDG * 8));
+    s.proj = s.w;  // [9][L][msc_dp(L)] after the marginals, in the overlap words' space
+    if (sm) *sm = s;
+    return off;
+}
+
+template <int L>
+__global__ void __launch_bounds__(kMscMeasThreads, 3) msc_measure_kernel(const MscArgs a)
+{
+    static_assert((size_t)9 * L * msc_dp(L) <= (size_t)L * L * L, "projections fit the words' space");
+    constexpr int N = L * L * L;
+    extern __shared__ __align__(16) uint8_t msc_smem[];
+    MscSmem sm;
+    msc_carve_meas(msc_smem, L, &sm);
+    const int t = blockIdx.x, g = blockIdx.y;
+    const int64_t n = (a.sweep0_dev ? *a.sweep0_dev : a.sweep0) + a.sweep_offset;
+    if (!(n >= a.n_therm && (n - a.n_therm) % a.measure_every == 0)) return;
+    const uint64_t *w0 = a.W + (((size_t)g * a.nt + t) * 2) * N, *w1 = w0 + N;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) sm.w[i] = w0[i] ^ w1[i];
+    for (int q = threadIdx.x; q < 2 * 64; q += blockDim.x) {
+        const int r = q / 64, b = q % 64;
+        const int64_t s = 64 * (int64_t)g + b;
+        const size_t o = ((size_t)s * 2 + r) * a.nt + t;
+        sm.B[q] = a.B[o];
+        sm.M[q] = a.M[o];
+    }
+    __syncthreads();
+    msc_measure<L, true, true>(sm, a, g, 0, 1, t, log_bin(n, a.n_bins), nullptr, 0);
+}
+
 // ---- conversion, generation and standalone kernels ------------------------
 
 __device__ __forceinline__ int nb_site(int L, int i, int d, int step)
@@ -1016,6 +1078,21 @@ cudaError_t msc_split_launch_t(const MscArgs &a, cudaStream_t st)
 }
 
 template <int L>
+cudaError_t msc_measure_launch_t(const MscArgs &a, cudaStream_t st)
+{
+    if constexpr (msc_j_shared(L)) {
+        return cudaErrorInvalidValue;
+    } else {
+        static cudaError_t attr_m = cudaFuncSetAttribute(
+            msc_measure_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMscMaxSmem);
+        if (attr_m != cudaSuccess) return attr_m;
+        const dim3 grid((unsigned)a.nt, (unsigned)a.G);
+        msc_measure_kernel<L><<<grid, kMscMeasThreads, msc_carve_meas(nullptr, L, nullptr), st>>>(a);
+        return cudaGetLastError();
+    }
+}
+
+template <int L>
 cudaError_t msc_launch_t(const MscArgs &a, int threads, cudaStream_t st)
 {
     static cudaError_t attr_n = cudaFuncSetAttribute(
@@ -1067,6 +1144,14 @@ int msc_threads(int L, int requested)
 }
 
 bool msc_split(int L, int requested) { return requested <= 0 && L >= 14 && msc_supported_L(L); }
+
+cudaError_t msc_measure_split(const MscArgs &a, int L, cudaStream_t st)
+{
+#define X(LL) if (L == LL) return msc_measure_launch_t<LL>(a, st);
+    SG_MSC_FOR_EACH_L(X)
+#undef X
+    return cudaErrorInvalidValue;
+}
 
 cudaError_t msc_sweep(const MscArgs &a, int L, int threads, cudaStream_t st, bool split)
 {

@@ -36,13 +36,16 @@ bool msc_supported_L(int L);
 // Threads per CTA of the sweep kernel: `requested` (0 = library choice for
 // L) clamped to [128, 512] and rounded down to a multiple of 128.
 int msc_threads(int L, int requested);
-// Whether thermalising sweeps run split by replica (L >= 14 and no requested
-// CTA size): msc_split_sweep_kernel, one replica's chains of an exchange unit
-// per CTA (256 threads), which does not measure; the caller
-// passes split only for launches without measured sweeps; else the fused
-// msc_sweep_kernel with `threads` threads.
+// Whether sweeps run split by replica (L >= 14 and no requested CTA size):
+// msc_split_sweep_kernel, one replica's chains of an exchange unit per CTA
+// (256 threads), which does not measure, followed for a measured sweep by
+// msc_measure_split; else the fused msc_sweep_kernel with `threads` threads.
 bool msc_split(int L, int requested);
 cudaError_t msc_sweep(const MscArgs &a, int L, int threads, cudaStream_t st, bool split);
+// The overlap measurement of the sweep base + a.sweep_offset after a split
+// sweep (one CTA per slot and word group; returns at once on the device when
+// that sweep is not measured).
+cudaError_t msc_measure_split(const MscArgs &a, int L, cudaStream_t st);
 // skip (device, may be null): when *skip is nonzero the import writes nothing
 cudaError_t msc_import_spins(uint64_t *W, const int8_t *canon, int64_t G, int L, int nt,
                              cudaStream_t st, const int *skip = nullptr);

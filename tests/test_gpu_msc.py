@@ -190,12 +190,13 @@ def test_msc_autotune_changes_speed_not_results():
 @pytest.mark.parametrize("L,nt,ee,me,S", [(14, 5, 1, 1, 128), (14, 6, 2, 3, 64), (16, 4, 1, 1, 64),
                                           (16, 3, 0, 2, 128)])
 def test_replica_split_sweep_equals_fused_kernel_and_oracle(L, nt, ee, me, S):
-    """At L >= 14 launches whose sweeps all thermalise run split by replica
-    (one replica's chains of an exchange unit per CTA); the measuring ones
-    run fused. A run of a thermalising then a measuring launch must equal the
-    fused kernel throughout (an explicit CTA size selects it) bit for bit,
-    through plain launches and a replayed CUDA graph (one graph per phase),
-    and the oracle on sample 0."""
+    """At L >= 14 the sweeps run split by replica (one replica's chains of an
+    exchange unit per CTA), and each measured sweep is measured by a kernel
+    of its own (one CTA per slot and word group, from the stored chains). A
+    run of a thermalising then a measuring call must equal the fused kernel
+    throughout (an explicit CTA size selects it) bit for bit, through plain
+    launches and a replayed CUDA graph (whose measurement kernels decide on
+    the device which sweeps they measure), and the oracle on sample 0."""
     T = inputs.geometric_ladder(0.4, 1.5, nt)
     J, s0 = inputs.make_instance("pmj", L, S, nt, seed=300 + L + nt)
     opt = dict(exchange_every=ee, measure_every=me, n_therm=9, log_bins=3, pq_hist=1)
@@ -203,8 +204,10 @@ def test_replica_split_sweep_equals_fused_kernel_and_oracle(L, nt, ee, me, S):
     for tpb, graph in ((0, False), (0, True), (512, False)):
         with sgmc.Ensemble(L, 0.2, T, "pmj", S, 4, J=J, spins=s0, threads_per_block=tpb, **MSC,
                            **opt) as e:
-            split_grid = e.launch_plan(9)["grid"]
-            assert split_grid == (2 if tpb == 0 else 1) * e.info().grid
+            plan = e.launch_plan(18)
+            assert plan["grid"] == (2 if tpb == 0 else 1) * e.info().grid
+            n_meas = sum(1 for n in range(9, 18) if (n - 9) % me == 0)
+            assert plan["launches"] == 18 + (n_meas if tpb == 0 else 0)
             if graph:
                 sgmc.sweep_batch([e], 9, use_graph=True)
                 sgmc.sweep_batch([e], 9, use_graph=True)
