@@ -161,6 +161,20 @@ __device__ __forceinline__ void bs_add(uint64_t (&c)[D], const uint64_t (&x)[K])
     }
 }
 
+// The same on 32 lanes.
+template <int D, int K>
+__device__ __forceinline__ void bs_add32(uint32_t (&c)[D], const uint32_t (&x)[K])
+{
+    uint32_t carry = 0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        const uint32_t a = c[k];
+        const uint32_t b = k < K ? x[k] : 0u;
+        c[k] = a ^ b ^ carry;
+        carry = (a & b) | (carry & (a ^ b));
+    }
+}
+
 // 32x32 bit transpose across a warp by five shuffle stages: afterwards bit k
 // of lane l's word is bit l of lane k's word before.
 __device__ __forceinline__ uint32_t warp_transpose32(uint32_t x)

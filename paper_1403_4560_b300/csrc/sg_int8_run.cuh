@@ -840,20 +840,6 @@ __device__ __forceinline__ void half_sweep_bits(const Smem &sm, const Ctx &cx, u
     }
 }
 
-// 32-bit bit-sliced ripple add (see bs_add).
-template <int D, int K>
-__device__ __forceinline__ void bs_add32(uint32_t (&c)[D], const uint32_t (&x)[K])
-{
-    uint32_t carry = 0;
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-        const uint32_t a = c[k];
-        const uint32_t b = k < K ? x[k] : 0u;
-        c[k] = a ^ b ^ carry;
-        carry = (a & b) | (carry & (a ^ b));
-    }
-}
-
 // Local field of one chain from the neighbour words nb (the six bonds in the
 // order +x, -x, +y, -y, +z, -z, couplings j), mp = 2^(31 - p) for the chain
 // at bit p: nb * mp moves the chain's bit to bit 31, where it flips the sign
