@@ -73,6 +73,46 @@ __device__ __forceinline__ u32x4 philox10_rk(const uint32_t *k0r, uint32_t k1, u
     return r;
 }
 
+// Four calls of philox10_rk with the same key and counter words c0, c1, c3
+// and four values of c2, round by round: the round key of k1 is formed once
+// per round for all four, and the first round's product of c0 is shared.
+// out[q] equals philox10_rk(k0r, k1, c0, c1, c2[q], c3) bit for bit.
+__device__ __forceinline__ void philox10x4_rk(const uint32_t *k0r, uint32_t k1, uint32_t c0,
+                                              uint32_t c1, const uint32_t (&c2)[4], uint32_t c3,
+                                              u32x4 (&out)[4])
+{
+    uint32_t a[4], b[4], c[4], d[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        a[q] = c0;
+        b[q] = c1;
+        c[q] = c2[q];
+        d[q] = c3;
+    }
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint64_t pa = (uint64_t)0xD2511F53u * a[q];
+            const uint64_t pb = (uint64_t)0xCD9E8D57u * c[q];
+            const uint32_t n0 = (uint32_t)(pb >> 32) ^ b[q] ^ k0r[round];
+            const uint32_t n2 = (uint32_t)(pa >> 32) ^ d[q] ^ k1;
+            b[q] = (uint32_t)pb;
+            d[q] = (uint32_t)pa;
+            a[q] = n0;
+            c[q] = n2;
+        }
+        k1 += 0xBB67AE85u;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        out[q].v[0] = a[q];
+        out[q].v[1] = b[q];
+        out[q].v[2] = c[q];
+        out[q].v[3] = d[q];
+    }
+}
+
 // e^x * 2^k on [-64, 0] from IEEE basic operations only, so that host and
 // device agree bit for bit: Cody-Waite reduction x = n*ln2 + r with ln2 split
 // into 0.693359375 + (-2.12194440e-4), then e^r by its degree-7 Taylor

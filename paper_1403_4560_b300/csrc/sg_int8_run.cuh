@@ -471,14 +471,17 @@ __device__ __forceinline__ void half_sweep(const Smem &sm, const Ctx &cx, uint32
         {
             const uint32_t c0 = (uint32_t)u;
             uint32_t rnd[4][4];
+            {
+                uint32_t c2[4];
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-                const uint32_t c2 = ((uint32_t)COL << 24) | ((uint32_t)r << 16) | (uint32_t)(t0 + kk);
-                const u32x4 o = philox10_rk(cx.k0r, cx.k1, c0, n_sweep, c2, cx.seed_hi);
-                rnd[kk][0] = o.v[0];
-                rnd[kk][1] = o.v[1];
-                rnd[kk][2] = o.v[2];
-                rnd[kk][3] = o.v[3];
+                for (int kk = 0; kk < 4; ++kk)
+                    c2[kk] = ((uint32_t)COL << 24) | ((uint32_t)r << 16) | (uint32_t)(t0 + kk);
+                u32x4 o[4];
+                philox10x4_rk(cx.k0r, cx.k1, c0, n_sweep, c2, cx.seed_hi, o);
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) rnd[kk][q] = o[kk].v[q];
             }
 #pragma unroll
             for (int lane = 0; lane < 4; ++lane) {
