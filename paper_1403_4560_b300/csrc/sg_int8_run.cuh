@@ -53,9 +53,10 @@ constexpr int kSiteRun = 4;
 // register / resident-warp trade-off:
 //   L <= 8 in shared memory: several samples fit per SM, so up to 192
 //     threads and four CTAs per SM (at most 80 registers);
-//   L = 10, 12 in shared memory: two samples fit per SM; 336 threads and
+//   L = 10, 12 in shared memory: two samples fit per SM; 320 threads and
 //     two CTAs per SM (at most 96 registers, no spills with one replica per
-//     work item) give up to 21 warps instead of 13.5;
+//     work item) give up to 20 warps instead of 13.5 (an eleventh warp per
+//     CTA would leave two CTAs at most 88 registers, where L = 12 spills);
 //   the same lattices with many temperatures (one sample per SM: WIDE),
 //     larger lattices (one CTA per SM in shared memory), and the
 //     global-memory state: up to 512 threads with 128 registers.

@@ -323,7 +323,8 @@ __device__ __forceinline__ void msc_half(const MscSmem &sm, const MscArgs &a, in
 // integer projections, the FP32 DFT and the FP64 accumulation.
 // ---------------------------------------------------------------------------
 // QW: sm.w holds the slots' overlap words q = w(r=0) ^ w(r=1) themselves (N
-// words per slot) rather than the two replica chains.
+// words per slot) rather than the two replica chains (the measurement
+// kernel), and each projection sum is split over two lanes.
 template <int L, bool WIDE, bool QW = false>
 __device__ __forceinline__ void msc_measure(const MscSmem &sm, const MscArgs &a, int g, int k0,
                                             int nk, int t0, int bin, uint64_t *w_dst, int nw)
@@ -383,6 +384,50 @@ __device__ __forceinline__ void msc_measure(const MscSmem &sm, const MscArgs &a,
     }
     // (B) projection counts: sum of L marginal entries per (v, d)
     constexpr int DP = msc_dp(L);
+    if constexpr (QW) {
+        // the measurement kernel: two lanes per (v, d), each adding half of
+        // the entries, the halves joined by a shuffle (half the serial adds)
+        static_assert(L % 2 == 0, "even L");
+        const int items = nk * 9 * L * 2;
+        for (int base = 0; base < items; base += blockDim.x) {  // whole warps per pass
+            const int id2 = base + (int)threadIdx.x, id = id2 >> 1, hf = id2 & 1;
+            const bool valid = id2 < items;
+            uint64_t acc[DP];
+#pragma unroll
+            for (int p = 0; p < DP; ++p) acc[p] = 0;
+            if (valid) {
+                const int kk = id / (9 * L), pid = id - kk * (9 * L);
+                const uint64_t *margk = sm.marg + (size_t)kk * 3 * LL * kDG;
+                const int v = pid / L, d = pid % L;
+                const int plane = (v == 0 || v == 1 || v == 3 || v == 4) ? 0 : (v == 2 || v == 5 || v == 6) ? 1 : 2;
+#pragma unroll
+                for (int e = 0; e < L / 2; ++e) {
+                    const int aa = hf * (L / 2) + e;
+                    int A, Bc;
+                    if (v == 0) {
+                        A = d; Bc = aa;
+                    } else if (v == 1 || v == 2) {
+                        A = aa; Bc = d;
+                    } else if (v == 3 || v == 5 || v == 7) {
+                        A = aa; Bc = (d - aa + L) % L;
+                    } else {
+                        A = aa; Bc = (aa - d + L) % L;
+                    }
+                    const uint64_t *m = margk + ((size_t)plane * LL + A * L + Bc) * kDG;
+                    const uint64_t x[kDG] = {m[0], m[1], m[2], m[3], m[4]};
+                    bs_add<DP, kDG>(acc, x);
+                }
+            }
+            uint64_t oth[DP];
+#pragma unroll
+            for (int p = 0; p < DP; ++p) oth[p] = __shfl_xor_sync(0xFFFFFFFFu, acc[p], 1);
+            if (valid && hf == 0) {
+                bs_add<DP, DP>(acc, oth);
+#pragma unroll
+                for (int p = 0; p < DP; ++p) sm.proj[(size_t)id * DP + p] = acc[p];  // [kk][v][d]
+            }
+        }
+    } else
     for (int id = threadIdx.x; id < nk * 9 * L; id += blockDim.x) {
         const int kk = id / (9 * L), pid = id - kk * (9 * L);
         const uint64_t *margk = sm.marg + (size_t)kk * 3 * LL * kDG;
@@ -754,9 +799,11 @@ __global__ void __launch_bounds__(kMscSplitThreads, 3) msc_split_sweep_kernel(co
 // the overlap words, the marginals and the energies (about 66 KB at L = 16,
 // the projections taking the words' space), so three share an SM and
 // overlap one another's phases, where the fused kernel measured inside its
-// one 197 KB CTA per SM. A sweep that is not measured returns at once.
+// one 197 KB CTA per SM. Its 9 warps take the 18 DFT tasks of a slot in two
+// even rounds, and its projection sums run on two lanes each (the QW form
+// of msc_measure). A sweep that is not measured returns at once.
 // ---------------------------------------------------------------------------
-constexpr int kMscMeasThreads = 256;
+constexpr int kMscMeasThreads = 288;
 
 __host__ __device__ inline size_t msc_carve_meas(uint8_t *base, int L, MscSmem *sm)
 {
