@@ -1083,12 +1083,42 @@ __device__ __forceinline__ void exchange_decide(const Smem &sm, const Ctx &cx, c
 }
 
 // All threads: apply the accepted swaps row by row (after a block barrier
-// that publishes the selectors).
+// that publishes the selectors). Up to 8 words per replica row (32 slots),
+// a thread keeps one replica (blockDim.x is even) with its selectors in
+// registers, and leaves the words that no accepted pair touches unwritten.
 template <int L>
 __device__ __forceinline__ void exchange_apply(const Smem &sm, const Ctx &cx)
 {
     constexpr int N = L * L * L;
+    constexpr int kMaxW = 8;
+    constexpr uint32_t kIdent = 0x3210u;
     const int WR = cx.WR, RB = cx.RB;
+    if (WR <= kMaxW) {
+        const int r = threadIdx.x & 1;
+        if (!sm.anyswap[r]) return;
+        const uint32_t *sel = sm.sel + r * WR * 2;
+        uint32_t s1[kMaxW], s2[kMaxW], touched = 0;
+#pragma unroll
+        for (int jj = 0; jj < kMaxW; ++jj) {
+            s1[jj] = jj < WR ? sel[2 * jj] : kIdent;
+            s2[jj] = jj < WR ? sel[2 * jj + 1] : kIdent;
+            if (s1[jj] != kIdent || s2[jj] != kIdent) touched |= 1u << jj;
+        }
+        for (int site = threadIdx.x >> 1; site < N; site += blockDim.x >> 1) {
+            uint8_t *row = sm.spins + site * RB + 4 * r;  // word j at row + 8j
+            uint32_t w[kMaxW];
+#pragma unroll
+            for (int jj = 0; jj < kMaxW; ++jj) w[jj] = jj < WR ? lds32(row, 8 * jj) : 0u;
+#pragma unroll
+            for (int jj = 0; jj < kMaxW; ++jj) {
+                if (!((touched >> jj) & 1u)) continue;
+                const uint32_t next = jj + 1 < kMaxW ? w[jj + 1] : 0u;
+                const uint32_t prev = jj > 0 ? w[jj - 1] : 0u;
+                sts32(row, 8 * jj, __byte_perm(__byte_perm(w[jj], next, s1[jj]), prev, s2[jj]));
+            }
+        }
+        return;
+    }
     for (int id = threadIdx.x; id < 2 * N; id += blockDim.x) {
         const int r = id & 1, site = id >> 1;
         if (!sm.anyswap[r]) continue;
