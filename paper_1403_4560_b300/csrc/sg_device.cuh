@@ -176,6 +176,66 @@ __device__ __forceinline__ float screen_logp(float x, uint32_t r, bool &amb)
     return u;
 }
 
+// Two FP32 values in one 64-bit register pair, and the packed FP32
+// arithmetic of sm_100-class GPUs on them: one instruction rounds both
+// lanes exactly as the scalar operation would (IEEE round to nearest even,
+// no flush to zero), so pairs of chains share an issue slot.
+__device__ __forceinline__ unsigned long long f2_pack(float lo, float hi)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(unsigned long long v, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long f2_add(unsigned long long a, unsigned long long b)
+{
+    unsigned long long r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long f2_sub(unsigned long long a, unsigned long long b)
+{
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long f2_mul(unsigned long long a, unsigned long long b)
+{
+    unsigned long long r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b,
+                                                     unsigned long long c)
+{
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
+// screen_logp for two log-probabilities at once (x of a chain pair, packed
+// as by f2_pack), in packed FP32: the same operations and roundings per
+// lane. u0, u1 receive fl(r) - A, whose sign bits are the decisions; amb0,
+// amb1 are set where the draw falls in the band.
+__device__ __forceinline__ void screen_pair(unsigned long long xp, uint32_t r0, uint32_t r1,
+                                            bool &amb0, bool &amb1, float &u0, float &u1)
+{
+    float y0, y1;
+    f2_unpack(f2_fma(xp, f2_pack(1.44269502f, 1.44269502f), f2_pack(32.0f, 32.0f)), y0, y1);
+    float a0, a1;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(a0) : "f"(y0));
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(a1) : "f"(y1));
+    const unsigned long long ap = f2_pack(a0, a1);
+    f2_unpack(f2_sub(f2_pack(__uint2float_rn(r0), __uint2float_rn(r1)), ap), u0, u1);
+    float w0, w1;
+    f2_unpack(f2_mul(ap, f2_pack(2.44140625e-4f, 2.44140625e-4f)), w0, w1);  // 2^-12 A
+    amb0 = fabsf(u0) <= w0;
+    amb1 = fabsf(u1) <= w1;
+}
+
 // Logarithmic bin of a measurement taken at global sweep n (0-based):
 // floor(log2(n + 1)), with every later sweep in the last of n_bins bins. Bin b
 // covers sweeps 2^b - 1 .. 2^(b+1) - 2, the second half of a run of 2^(b+1)

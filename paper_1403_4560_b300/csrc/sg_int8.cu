@@ -302,13 +302,20 @@ __global__ void thr_map_kernel(const float *x, int n, uint32_t *out)
 // Metropolis decision of the Gaussian sweep for (x, r) pairs: the screen,
 // and the exact threshold where the screen is undecided. out bit 0: accept;
 // bit 1: the screen was undecided.
+// The sweep's decision for each (x, r): screen_pair (the packed screen of
+// the Gaussian sweep's chain pairs) on the entries 2m and 2m + 1, and the
+// exact threshold where the entry's draw falls in the band.
 __global__ void accept_map_kernel(const float *x, const uint32_t *r, int n, uint8_t *out)
 {
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-        bool amb = false;
-        const float u = screen_logp(x[k], r[k], amb);
-        const bool acc = amb ? (r[k] <= thr_of_logp(x[k])) : (__float_as_uint(u) >> 31) != 0u;
-        out[k] = (uint8_t)((acc ? 1 : 0) | (amb ? 2 : 0));
+    for (int m = blockIdx.x * blockDim.x + threadIdx.x; 2 * m < n; m += gridDim.x * blockDim.x) {
+        const int k[2] = {2 * m, 2 * m + 1 < n ? 2 * m + 1 : 2 * m};
+        bool amb[2];
+        float u[2];
+        screen_pair(f2_pack(x[k[0]], x[k[1]]), r[k[0]], r[k[1]], amb[0], amb[1], u[0], u[1]);
+        for (int q = 0; q < 2; ++q) {
+            const bool acc = amb[q] ? (r[k[q]] <= thr_of_logp(x[k[q]])) : (__float_as_uint(u[q]) >> 31) != 0u;
+            out[k[q]] = (uint8_t)((acc ? 1 : 0) | (amb[q] ? 2 : 0));
+        }
     }
 }
 

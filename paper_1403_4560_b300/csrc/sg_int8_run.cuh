@@ -277,52 +277,11 @@ __device__ __forceinline__ uint32_t mad_hi(uint32_t a, uint32_t b, uint32_t c)
     return r;
 }
 
-// Two FP32 values in one 64-bit register pair, and the packed FP32
-// arithmetic of sm_100-class GPUs on them: one instruction rounds both
-// lanes exactly as the scalar operation would (IEEE round to nearest even,
-// no flush to zero), so pairs of chains share an issue slot.
-__device__ __forceinline__ unsigned long long f2_pack(float lo, float hi)
-{
-    unsigned long long r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-    return r;
-}
-__device__ __forceinline__ void f2_unpack(unsigned long long v, float &lo, float &hi)
-{
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-}
-__device__ __forceinline__ unsigned long long f2_add(unsigned long long a, unsigned long long b)
-{
-    unsigned long long r;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ unsigned long long f2_sub(unsigned long long a, unsigned long long b)
-{
-    unsigned long long r;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ unsigned long long f2_mul(unsigned long long a, unsigned long long b)
-{
-    unsigned long long r;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-    return r;
-}
-__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b,
-                                                     unsigned long long c)
-{
-    unsigned long long r;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-    return r;
-}
-
 // Gaussian: Metropolis on 4 chains of one replica word; nbeta2[kk] = -2 beta
 // of the chain's slot. With energy (colour-1 sites), bq[kk] receives
-// s_new * b / qJ. The four decisions come from the screen of screen_logp,
-// evaluated for the chain pairs (0, 1) and (2, 3) in packed FP32 (the same
-// roundings: the local-field sum, b + h, -2 beta (s (b + h)), the exponent
-// x log2 e + 32, fl(r) - A and the band 2^-12 A); if any draw of the word
+// s_new * b / qJ. The four decisions come from screen_pair for the chain
+// pairs (0, 1) and (2, 3), the local-field sums, b + h and -2 beta (s (b + h))
+// packed the same way (the roundings of the scalar form); if any draw of the word
 // falls in the screen's band, all four are redone with the exact threshold
 // (dE <= 0 gives x >= 0, whose threshold is 0xFFFFFFFF).
 __device__ __forceinline__ uint32_t gauss_word(uint32_t s, uint32_t nxp, uint32_t nxm,
@@ -334,9 +293,6 @@ __device__ __forceinline__ uint32_t gauss_word(uint32_t s, uint32_t nxp, uint32_
 {
     const uint32_t nb[6] = {nxp, nxm, nyp, nym, nzp, nzm};
     const unsigned long long hq2 = f2_pack(hq, hq);
-    const unsigned long long l2e = f2_pack(1.44269502f, 1.44269502f);
-    const unsigned long long c32 = f2_pack(32.0f, 32.0f);
-    const unsigned long long band = f2_pack(2.44140625e-4f, 2.44140625e-4f);  // 2^-12
     // the sign bit of chain kk's value flipped where bit 8 kk of w is set;
     // for kk = 0, J + w * 2^31 flips exactly bit 31 (one multiply-add)
     auto flip = [](float v, uint32_t w, int kk) {
@@ -359,18 +315,9 @@ __device__ __forceinline__ uint32_t gauss_word(uint32_t s, uint32_t nxp, uint32_
         const unsigned long long zs = f2_pack(flip(z0, s, k0), flip(z1, s, k1));
         const unsigned long long xp = f2_mul(f2_pack(nbeta2[k0], nbeta2[k1]), zs);
         f2_unpack(xp, x[k0], x[k1]);
-        float y0, y1;
-        f2_unpack(f2_fma(xp, l2e, c32), y0, y1);
-        float a0, a1;
-        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(a0) : "f"(y0));
-        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(a1) : "f"(y1));
-        const unsigned long long ap = f2_pack(a0, a1);
-        float w0, w1;
-        f2_unpack(f2_sub(f2_pack(__uint2float_rn(rnd[k0][lane]), __uint2float_rn(rnd[k1][lane])), ap),
-                  u[k0], u[k1]);
-        f2_unpack(f2_mul(ap, band), w0, w1);
-        amb |= fabsf(u[k0]) <= w0;
-        amb |= fabsf(u[k1]) <= w1;
+        bool b0, b1;
+        screen_pair(xp, rnd[k0][lane], rnd[k1][lane], b0, b1, u[k0], u[k1]);
+        amb |= b0 | b1;
     }
     // the decisions are the sign bits: the top bytes of the four u gathered
     // into one word, bit 7 of each byte moved to bit 0
