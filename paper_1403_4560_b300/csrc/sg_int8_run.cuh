@@ -1213,9 +1213,12 @@ __device__ __forceinline__ void measure_marginals(const Smem &sm, const Ctx &cx,
     constexpr int LL = L * L;
     const int RB = cx.RB;
     {
+        // id / nw by a multiply-high with ceil(2^32 / nw): exact for
+        // 2 <= nw <= 16 and id < 3 L^2 nw, L <= 64 (checked exhaustively)
+        const uint32_t inv_nw = nw > 1 ? (uint32_t)((0xFFFFFFFFull + (unsigned)nw) / (unsigned)nw) : 0u;
         for (int id = threadIdx.x; id < 3 * LL * nw; id += blockDim.x) {
-            const int jj = id % nw;
-            const int rest = id / nw;
+            const int rest = nw > 1 ? (int)__umulhi((uint32_t)id, inv_nw) : id;
+            const int jj = id - rest * nw;
             const int ab = rest % LL;
             const int plane = rest / LL;
             const int A = ab % L, Bc = ab / L;  // A varies fastest
