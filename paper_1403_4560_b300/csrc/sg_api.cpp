@@ -1501,8 +1501,9 @@ sg_status sg_autotune(sg_ensemble *e, int64_t trial_sweeps, sg_tune_report *rep)
         const sg_options orig = e->opt;
         const int64_t done0 = e->sweeps_done;
         double best = 1e300, def = 0.0;
-        // candidates: the library choice (0: split by replica for L >= 12),
-        // then fused CTAs of 128, 256 and 512 threads
+        // candidates: the library choice (0: at L >= 14 split by replica, the
+        // measured sweeps by the measurement kernel), then fused CTAs of 128,
+        // 256 and 512 threads
         int best_t = 0, nc = 0;
         cudaError_t ce = save(false);
         const int cands[4] = {0, 128, 256, 512};

@@ -658,21 +658,21 @@ __global__ void __launch_bounds__(MAXT, MINB) msc_sweep_kernel(const MscArgs a)
 }
 
 // ---------------------------------------------------------------------------
-// Thermalising sweeps of large lattices (L >= 14): the exchange unit split by
-// replica. A CTA holds one replica's chains of the unit (the sweep and the
-// exchange never mix replicas: methods section, each replica has its own
-// tempering ladder), so at L = 16 it needs 64 KB of shared memory instead of
-// 197 KB and three CTAs share an SM. It does not measure (the overlap needs
-// both replicas): the host uses it only for launches whose sweeps all lie
-// before n_therm. Same random numbers, decisions and order as
+// Sweeps of large lattices (L >= 14): the exchange unit split by replica. A
+// CTA holds one replica's chains of the unit (the sweep and the exchange
+// never mix replicas: methods section, each replica has its own tempering
+// ladder), so at L = 16 it needs 64 KB of shared memory instead of 197 KB and
+// three CTAs share an SM. It does not measure (the overlap needs both
+// replicas): a measured sweep is followed by msc_measure_kernel, which reads
+// the stored chains. Same random numbers, decisions and order as
 // msc_sweep_kernel: the results are identical. (B300, +-J, 4096 samples,
-// 2 x 32 temperatures, thermalising attempts/ns, the library's fused shape
-// -> split: L = 14 2436 -> 2886, L = 16 2969 -> 3117; at L = 12 the fused
-// 256-thread CTA stays ahead, 2661 against 2541. Measuring sweeps
-// stay fused: a separate measurement kernel after the split sweep ran them up
-// to 5 % slower, and the replica pair run as a cluster, each CTA measuring one
-// slot through the peer's shared memory, slower still: measuring at L = 12 /
-// 14 / 16 1549 / 1800 / 2057 against 1911 / 1831 / 2199 fused.)
+// 2 x 32 temperatures, attempts/ns, fused -> split: thermalising L = 14
+// 2436 -> 2886, L = 16 2969 -> 3117 when first built; with the consecutive-
+// site lanes L = 16 3641 split, measuring every sweep 2338 fused -> 2665
+// split plus the measurement kernel. At L = 12 the fused 256-thread CTA stays
+// ahead: measuring 2234 against 1975 split, thermalising 3137 against 2714.
+// The replica pair run as a cluster, each CTA measuring one slot through the
+// peer's shared memory, measured slower than both.)
 // ---------------------------------------------------------------------------
 constexpr int kMscSplitThreads = 256;
 
