@@ -46,6 +46,20 @@ def test_options_default_and_status_strings(lib):
     assert lib.sg_status_str(99) == b"unknown status"
 
 
+def test_options_reject_unknown_names_and_validate_chain_set(lib):
+    """Option names are checked by the binding (a misspelt option must not be
+    dropped silently), and sg_ensemble_bytes refuses a chain set that is not
+    1, 2 or 4 four-slot groups."""
+    with pytest.raises(TypeError):
+        sgmc.default_options(chain_sets=2)
+    o = sgmc.default_options(state_mode=3, chain_set=2)
+    assert (o.state_mode, o.chain_set) == (3, 2)
+    assert lib.sg_ensemble_bytes(8, 24, 4, sgmc.SG_GAUSS, ctypes.byref(o)) > 0
+    for bad in (3, 8, -1):
+        o.chain_set = bad
+        assert lib.sg_ensemble_bytes(8, 24, 4, sgmc.SG_GAUSS, ctypes.byref(o)) == 0
+
+
 def test_ensemble_bytes_validates_arguments(lib):
     assert lib.sg_ensemble_bytes(4, 8, 16, 0, None) > 16 * 64 * 16
     assert lib.sg_ensemble_bytes(5, 8, 16, 0, None) == 0   # odd L
