@@ -54,7 +54,7 @@ TRAFFIC_BYTES_PER_LAUNCH = 61.6e6
 # the bench's own 512-sample, 256-sweep segmented launch;
 # its ncu summary is kept under profiles/). Reset to None whenever
 # the kernel changes, until it is captured again.
-INSTR_PER_ATTEMPT = 67.0
+INSTR_PER_ATTEMPT = 66.6
 # SM issue peak: 148 SMs x 4 schedulers x 1 warp instruction per cycle x 32
 # threads x 2.032 GHz (maximum SM clock), in thread instructions per second.
 ISSUE_PEAK = 148 * 4 * 32 * 2.032e9
