@@ -140,7 +140,6 @@ __device__ __forceinline__ float exp_cw32_scaled(float x)
     return __fmul_rn(p, __int_as_float((ni + 127 + K) << 23));
 }
 
-__device__ __forceinline__ float exp_cw32(float x) { return exp_cw32_scaled<0>(x); }
 
 // Acceptance threshold for an FP32 log-probability x: a uniform 32-bit word
 // r is accepted iff r <= thr, i.e. with probability (thr + 1)/2^32; thr is
