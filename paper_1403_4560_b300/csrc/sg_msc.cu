@@ -186,9 +186,11 @@ __device__ __forceinline__ uint64_t ge_const(uint64_t u0, uint64_t u1, uint64_t 
 // u >= ustar.
 __device__ __forceinline__ int ustar_of(const uint32_t *thr_sb, uint32_t r)
 {
-    int c = 0;
-#pragma unroll
-    for (int u = 0; u < 7; ++u) c += r > thr_sb[u];
+    // thr_sb[0..6] does not decrease with u, so {u : r > thr_sb[u]} is the
+    // prefix 0 .. ustar - 1, whose length three steps of a binary search find
+    int c = r > thr_sb[3] ? 4 : 0;
+    c += r > thr_sb[c + 1] ? 2 : 0;
+    c += r > thr_sb[c] ? 1 : 0;
     return c;
 }
 
