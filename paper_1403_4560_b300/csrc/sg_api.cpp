@@ -526,6 +526,7 @@ MscArgs make_msc_args(sg_ensemble *e)
     a.measure_every = e->opt.measure_every;
     a.n_therm = e->opt.n_therm;
     a.s_key0 = e->opt.sample_base;
+    a.status = e->status;
     return a;
 }
 

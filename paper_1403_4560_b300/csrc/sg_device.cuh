@@ -292,4 +292,72 @@ __device__ __forceinline__ uint32_t warp_transpose32(uint32_t x)
 // lanes whose word has bit l set.
 __device__ __forceinline__ int warp_column_popc(uint32_t x) { return __popc(warp_transpose32(x)); }
 
+// ---- untiled bulk copies (TMA) counted on a shared-memory mbarrier --------
+// cp.async.bulk moves one contiguous block from global to shared memory on
+// the SM's copy engine, so a CTA has its whole state in flight at once
+// instead of one load per thread and loop trip; the barrier's phase
+// completes when the bytes announced by mbar_expect_tx have landed. Both
+// addresses must be 16-byte aligned and the size a multiple of 16.
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// One arrival (the thread that announces the bytes) completes a phase.
+__device__ __forceinline__ void mbar_init(uint64_t *bar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_load(void *dst_smem, const void *src_gmem, uint32_t bytes,
+                                          uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_u32(dst_smem)),
+        "l"((unsigned long long)__cvta_generic_to_global(src_gmem)), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Ask the copy engine to bring a block into L2 ahead of its plain loads.
+__device__ __forceinline__ void bulk_prefetch_l2(const void *src_gmem, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(
+                     (unsigned long long)__cvta_generic_to_global(src_gmem)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// Wait until phase `parity` of the barrier has completed; false once `limit`
+// clock cycles have passed without it (the caller reports and gives up).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsigned long long limit)
+{
+    const uint32_t b = smem_u32(bar);
+    const long long t0 = clock64();
+    for (;;) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(b), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if ((unsigned long long)(clock64() - t0) > limit) return false;
+    }
+}
+
+// Bound of a bulk-copy wait: 2^30 cycles, about half a second at 2 GHz, far
+// beyond the microseconds a copy of a CTA's state takes.
+constexpr unsigned long long kBulkWaitCycles = 1ull << 30;
+
 }  // namespace sg

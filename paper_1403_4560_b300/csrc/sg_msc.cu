@@ -28,8 +28,30 @@ namespace sg {
 namespace {
 
 constexpr int kMscThreads = 512;
-constexpr int kDU = 9;  // bit planes of the per-thread unsatisfied-bond counter
-constexpr int kDM = 8;  // bit planes of the per-thread (-1 spin) counter
+// Colour sites one thread visits in a half-sweep when its chain's team has
+// at least tpc_min threads: the warps of a team take blocks of 128 colour
+// sites (32 Philox groups of four) in turn, a lane one site per block step.
+__host__ __device__ constexpr int msc_sites_per_thread(int L, int tpc_min)
+{
+    return 4 * ((((L * L * L / 8) + 31) / 32 + tpc_min / 32 - 1) / (tpc_min / 32));
+}
+// Bit planes that hold every count 0..x.
+__host__ __device__ constexpr int msc_planes(int x) { return x < 2 ? 1 : 1 + msc_planes(x / 2); }
+// Bit planes of a thread's unsatisfied-bond counter (at most 6 per site) and
+// (-1)-spin counter (a colour-1 site and its colour-0 x-partner: at most 2
+// per site): as few as the counts can reach, since every plane costs each
+// site's ripple add and each half-sweep's warp transposes.
+__host__ __device__ constexpr int msc_du(int L, int tpc_min)
+{
+    return msc_planes(6 * msc_sites_per_thread(L, tpc_min));
+}
+__host__ __device__ constexpr int msc_dm(int L, int tpc_min)
+{
+    return msc_planes(2 * msc_sites_per_thread(L, tpc_min));
+}
+static_assert(msc_du(16, 32) == 9 && msc_dm(16, 32) == 8, "L = 16, teams of one warp");
+static_assert(msc_du(16, 128) == 7 && msc_dm(16, 128) == 6, "L = 16, teams of four warps");
+static_assert(msc_du(10, 32) == 7 && msc_dm(10, 32) == 6, "L = 10, teams of one warp");
 // Bit planes of a projection count (0..L^2): the fewest with 2^planes > L^2,
 // 9 at L = 16. Fewer planes make the carry chain of the projection sums
 // shorter and let more phases share one warp transpose.
@@ -226,13 +248,15 @@ struct MscSite {
 // ---------------------------------------------------------------------------
 // w: the chain's words; thr: its slot's 16 thresholds; bm: its row of
 // sm.B / sm.M.
-template <int L>
+// TPC_MIN: a lower bound on tpc, which sizes the energy counters.
+template <int L, int TPC_MIN>
 __device__ __forceinline__ void msc_half(const MscSmem &sm, const MscArgs &a, int g, uint64_t *w,
                                          const uint32_t *thr, int bm, int t, int r, int tpc, int c,
                                          uint32_t n_sweep)
 {
     constexpr int N = L * L * L;
     constexpr int NG = (N / 2) / 4;  // Philox groups of four colour-c sites
+    constexpr int kDU = msc_du(L, TPC_MIN), kDM = msc_dm(L, TPC_MIN);
     const int tid = threadIdx.x % tpc;
     const uint64_t *J = msc_j_shared(L) ? sm.J : a.Jw + (size_t)g * 3 * N;
     uint64_t cu[kDU], cm[kDM];
@@ -586,7 +610,8 @@ __global__ void __launch_bounds__(MAXT, MINB) msc_sweep_kernel(const MscArgs a)
     const int q = threadIdx.x / tpc;
     for (int c = 0; c < 2; ++c) {
         if (q < nq)
-            msc_half<L>(sm, a, g, sm.w + (size_t)q * N, sm.thr + (q >> 1) * 16, q, t0 + (q >> 1),
+            // (at least 128 threads for at most four chains)
+            msc_half<L, 32>(sm, a, g, sm.w + (size_t)q * N, sm.thr + (q >> 1) * 16, q, t0 + (q >> 1),
                         q & 1, tpc, c, (uint32_t)n);
         __syncthreads();
     }
@@ -713,10 +738,16 @@ __global__ void __launch_bounds__(kMscSplitThreads, 3) msc_split_sweep_kernel(co
     int t0, cnt;
     if (!unit_slots(blockIdx.x, par, a.nt, &t0, &cnt)) return;
 
-    // chain k of this CTA: slot t0 + k of replica r
-    for (int k = 0; k < cnt; ++k) {
-        const uint64_t *src = a.W + (((size_t)g * a.nt + t0 + k) * 2 + r) * N;
-        for (int i = threadIdx.x; i < N; i += blockDim.x) sm.w[(size_t)k * N + i] = src[i];
+    // chain k of this CTA: slot t0 + k of replica r, brought in by bulk
+    // copies (N * 8 bytes each: a multiple of 16 for even L) while the
+    // threads set up the rest
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar);
+        mbar_expect_tx(&bar, (uint32_t)(cnt * N * 8));
+        for (int k = 0; k < cnt; ++k)
+            bulk_load(sm.w + (size_t)k * N, a.W + (((size_t)g * a.nt + t0 + k) * 2 + r) * N,
+                      (uint32_t)(N * 8), &bar);
     }
     for (int k = threadIdx.x; k < cnt * 16; k += blockDim.x) sm.thr[k] = a.thr[t0 * 16 + k];
     for (int k = threadIdx.x; k < 2 * 64; k += blockDim.x) {
@@ -725,12 +756,18 @@ __global__ void __launch_bounds__(kMscSplitThreads, 3) msc_split_sweep_kernel(co
     }
     if (threadIdx.x == 0) sm.swap[0] = 0;
     __syncthreads();
+    if (__syncthreads_or(!mbar_wait(&bar, 0, kBulkWaitCycles))) {
+        if (threadIdx.x == 0) atomicCAS(a.status, 0, (int)SG_ETIMEOUT);
+        mbar_wait(&bar, 0, kBulkWaitCycles);  // the copies still in flight, bounded again
+        return;
+    }
 
     const int tpc = blockDim.x / cnt;  // threads per chain: whole warps
     const int k = threadIdx.x / tpc;
     for (int c = 0; c < 2; ++c) {
         if (k < cnt)
-            msc_half<L>(sm, a, g, sm.w + (size_t)k * N, sm.thr + k * 16, k, t0 + k, r, tpc, c,
+            msc_half<L, kMscSplitThreads / 2>(sm, a, g, sm.w + (size_t)k * N, sm.thr + k * 16, k,
+                                              t0 + k, r, tpc, c,
                         (uint32_t)n);
         __syncthreads();
     }
@@ -820,7 +857,9 @@ __host__ __device__ inline size_t msc_carve_meas(uint8_t *base, int L, MscSmem *
     s.w = reinterpret_cast<uint64_t *>(take(N * 8));
     s.B = reinterpret_cast<long long *>(take(2 * 64 * 8));
     s.M = reinterpret_cast<long long *>(take(2 * 64 * 8));
-    s.marg = reinterpret_cast<uint64_t *>(take((size_t)3 * L * L * kDG * 8));
+    // the marginals' space first receives replica 1's chain
+    const size_t marg = (size_t)3 * L * L * kDG * 8;
+    s.marg = reinterpret_cast<uint64_t *>(take(marg > N * 8 ? marg : N * 8));
     s.proj = s.w;  // [9][L][msc_dp(L)] after the marginals, in the overlap words' space
     if (sm) *sm = s;
     return off;
@@ -837,8 +876,20 @@ __global__ void __launch_bounds__(kMscMeasThreads, 3) msc_measure_kernel(const M
     const int t = blockIdx.x, g = blockIdx.y;
     const int64_t n = (a.sweep0_dev ? *a.sweep0_dev : a.sweep0) + a.sweep_offset;
     if (!(n >= a.n_therm && (n - a.n_therm) % a.measure_every == 0)) return;
-    const uint64_t *w0 = a.W + (((size_t)g * a.nt + t) * 2) * N, *w1 = w0 + N;
-    for (int i = threadIdx.x; i < N; i += blockDim.x) sm.w[i] = w0[i] ^ w1[i];
+    const int bin = log_bin(n, a.n_bins);
+    // the two chains by bulk copies (replica 0 into the words' space, replica
+    // 1 into the marginals'), and this (slot, word group, bin)'s accumulator
+    // block on its way to L2 for the last phase
+    const uint64_t *w0 = a.W + (((size_t)g * a.nt + t) * 2) * N;
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar);
+        mbar_expect_tx(&bar, (uint32_t)(2 * N * 8));
+        bulk_load(sm.w, w0, (uint32_t)(N * 8), &bar);
+        bulk_load(sm.marg, w0 + N, (uint32_t)(N * 8), &bar);
+        bulk_prefetch_l2(a.acc + (((size_t)g * a.nt + t) * a.n_bins + bin) * SG_NACC * 64,
+                         (uint32_t)(SG_NACC * 64 * sizeof(double)));
+    }
     for (int q = threadIdx.x; q < 2 * 64; q += blockDim.x) {
         const int r = q / 64, b = q % 64;
         const int64_t s = 64 * (int64_t)g + b;
@@ -847,7 +898,14 @@ __global__ void __launch_bounds__(kMscMeasThreads, 3) msc_measure_kernel(const M
         sm.M[q] = a.M[o];
     }
     __syncthreads();
-    msc_measure<L, true, true>(sm, a, g, 0, 1, t, log_bin(n, a.n_bins), nullptr, 0);
+    if (__syncthreads_or(!mbar_wait(&bar, 0, kBulkWaitCycles))) {
+        if (threadIdx.x == 0) atomicCAS(a.status, 0, (int)SG_ETIMEOUT);
+        mbar_wait(&bar, 0, kBulkWaitCycles);  // the copies still in flight, bounded again
+        return;
+    }
+    for (int i = threadIdx.x; i < N; i += blockDim.x) sm.w[i] ^= sm.marg[i];
+    __syncthreads();
+    msc_measure<L, true, true>(sm, a, g, 0, 1, t, bin, nullptr, 0);
 }
 
 // ---- conversion, generation and standalone kernels ------------------------
@@ -1117,11 +1175,14 @@ cudaError_t msc_split_launch_t(const MscArgs &a, cudaStream_t st)
     if constexpr (msc_j_shared(L)) {
         return cudaErrorInvalidValue;
     } else {
+        // (the kernel's own mbarrier takes a few bytes of static shared memory,
+        // so the dynamic size asked for is the carve's, not the SM maximum)
+        const size_t smem = msc_carve_split(nullptr, L, nullptr);
         static cudaError_t attr_s = cudaFuncSetAttribute(
-            msc_split_sweep_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMscMaxSmem);
+            msc_split_sweep_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (attr_s != cudaSuccess) return attr_s;
         const dim3 grid((unsigned)(a.nt / 2 + 1), (unsigned)a.G, 2u);
-        msc_split_sweep_kernel<L><<<grid, kMscSplitThreads, msc_carve_split(nullptr, L, nullptr), st>>>(a);
+        msc_split_sweep_kernel<L><<<grid, kMscSplitThreads, smem, st>>>(a);
         return cudaGetLastError();
     }
 }
@@ -1132,11 +1193,12 @@ cudaError_t msc_measure_launch_t(const MscArgs &a, cudaStream_t st)
     if constexpr (msc_j_shared(L)) {
         return cudaErrorInvalidValue;
     } else {
+        const size_t smem = msc_carve_meas(nullptr, L, nullptr);
         static cudaError_t attr_m = cudaFuncSetAttribute(
-            msc_measure_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMscMaxSmem);
+            msc_measure_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (attr_m != cudaSuccess) return attr_m;
         const dim3 grid((unsigned)a.nt, (unsigned)a.G);
-        msc_measure_kernel<L><<<grid, kMscMeasThreads, msc_carve_meas(nullptr, L, nullptr), st>>>(a);
+        msc_measure_kernel<L><<<grid, kMscMeasThreads, smem, st>>>(a);
         return cudaGetLastError();
     }
 }

@@ -29,6 +29,7 @@ struct MscArgs {
     int exchange_every, measure_every;
     int64_t n_therm;
     int64_t s_key0;             // global index of local sample 0 (multiple of 64)
+    int *status;                // device status word (SG_ETIMEOUT if a bulk copy never lands)
 };
 
 size_t msc_smem_bytes(int L);
