@@ -292,6 +292,55 @@ __device__ __forceinline__ uint32_t warp_transpose32(uint32_t x)
 // lanes whose word has bit l set.
 __device__ __forceinline__ int warp_column_popc(uint32_t x) { return __popc(warp_transpose32(x)); }
 
+// Warp totals of a bit-sliced counter over 64 bit lanes (plane k of c holds
+// bit k of every bit lane's count). A butterfly of bit-sliced adds: the first
+// stage leaves each thread the half of the 64 bit lanes it keeps (threads
+// 0-15 bits 0-31, 16-31 bits 32-63) summed with its partner's, the next four
+// sum those 32-bit planes over the rest of the threads, one plane wider per
+// stage. Afterwards thread l holds, for bit lanes b0 = 32 (l >> 4) + (l & 15)
+// and b0 + 16, the sum over the warp's 32 threads of their counts (v0, v1).
+// D + 5 planes hold every total, so nothing overflows; the result equals the
+// per-plane transpose-and-popcount sums, with fewer shuffles and operations.
+template <int D>
+__device__ __forceinline__ void warp_bs_totals(const uint64_t (&c)[D], uint32_t &v0, uint32_t &v1)
+{
+    constexpr int E = D + 5;
+    const int lane = threadIdx.x & 31;
+    const bool hi = lane & 16;
+    uint32_t x[E];
+    uint32_t carry = 0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        const uint32_t lo32 = (uint32_t)c[k], hi32 = (uint32_t)(c[k] >> 32);
+        const uint32_t keep = hi ? hi32 : lo32;
+        const uint32_t y = __shfl_xor_sync(0xFFFFFFFFu, hi ? lo32 : hi32, 16);
+        x[k] = keep ^ y ^ carry;
+        carry = (keep & y) | (carry & (keep ^ y));
+    }
+    x[D] = carry;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        const int m = 8 >> s, P = D + 1 + s;  // planes in use before this stage
+        uint32_t cy = 0;
+#pragma unroll
+        for (int k = 0; k < P; ++k) {
+            const uint32_t a = x[k];
+            const uint32_t y = __shfl_xor_sync(0xFFFFFFFFu, a, m);
+            x[k] = a ^ y ^ cy;
+            cy = (a & y) | (cy & (a ^ y));
+        }
+        x[P] = cy;
+    }
+    const int j = lane & 15;
+    v0 = 0;
+    v1 = 0;
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+        v0 |= ((x[k] >> j) & 1u) << k;
+        v1 |= ((x[k] >> (j + 16)) & 1u) << k;
+    }
+}
+
 // ---- untiled bulk copies (TMA) counted on a shared-memory mbarrier --------
 // cp.async.bulk moves one contiguous block from global to shared memory on
 // the SM's copy engine, so a CTA has its whole state in flight at once

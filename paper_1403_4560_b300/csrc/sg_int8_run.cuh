@@ -765,22 +765,15 @@ __device__ __forceinline__ void half_sweep_bits(const Smem &sm, const Ctx &cx, u
             }
         }
         if (COL == 1) {
-            // per chain, the warp's counts: transposes hand lane b the counts
-            // of chain bits b (low word) and 32 + b (high word)
-            long long vu[2] = {0, 0}, vm[2] = {0, 0};
-#pragma unroll
-            for (int k = 0; k < DU; ++k) {
-                vu[0] += (long long)warp_column_popc((uint32_t)cu[k]) << k;
-                vu[1] += (long long)warp_column_popc((uint32_t)(cu[k] >> 32)) << k;
-            }
-#pragma unroll
-            for (int k = 0; k < DM; ++k) {
-                vm[0] += (long long)warp_column_popc((uint32_t)cm[k]) << k;
-                vm[1] += (long long)warp_column_popc((uint32_t)(cm[k] >> 32)) << k;
-            }
+            // per chain, the warp's counts by a bit-sliced butterfly: lane l
+            // ends with chain bits b0 = 32 (l >> 4) + (l & 15) and b0 + 16
+            uint32_t tu[2], tm[2];
+            warp_bs_totals<DU>(cu, tu[0], tu[1]);
+            warp_bs_totals<DM>(cm, tm[0], tm[1]);
+            const long long vu[2] = {tu[0], tu[1]}, vm[2] = {tm[0], tm[1]};
 #pragma unroll
             for (int hf = 0; hf < 2; ++hf) {
-                const int b = 32 * hf + lane;
+                const int b = 32 * (lane >> 4) + (lane & 15) + 16 * hf;
                 const int t = 4 * (8 * w + (b >> 3)) + (b & 3), r = (b >> 2) & 1;
                 if (t < nt) {
                     atomicAdd(&sm.B[r * cx.Tp + t], (unsigned long long)(-2 * vu[hf]));

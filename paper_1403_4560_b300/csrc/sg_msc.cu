@@ -324,22 +324,16 @@ __device__ __forceinline__ void msc_half(const MscSmem &sm, const MscArgs &a, in
         }
     }
     if (c == 1) {
-        // per-sample column counts: warp transpose-popc of every plane half
-        long long vu_lo = 0, vu_hi = 0, vm_lo = 0, vm_hi = 0;
-#pragma unroll
-        for (int k = 0; k < kDU; ++k) {
-            vu_lo += (long long)warp_column_popc((uint32_t)cu[k]) << k;
-            vu_hi += (long long)warp_column_popc((uint32_t)(cu[k] >> 32)) << k;
-        }
-#pragma unroll
-        for (int k = 0; k < kDM; ++k) {
-            vm_lo += (long long)warp_column_popc((uint32_t)cm[k]) << k;
-            vm_hi += (long long)warp_column_popc((uint32_t)(cm[k] >> 32)) << k;
-        }
-        atomicAdd((unsigned long long *)&sm.B[bm * 64 + lane], (unsigned long long)vu_lo);
-        atomicAdd((unsigned long long *)&sm.B[bm * 64 + 32 + lane], (unsigned long long)vu_hi);
-        atomicAdd((unsigned long long *)&sm.M[bm * 64 + lane], (unsigned long long)vm_lo);
-        atomicAdd((unsigned long long *)&sm.M[bm * 64 + 32 + lane], (unsigned long long)vm_hi);
+        // per-sample warp totals by a bit-sliced butterfly (thread l ends with
+        // samples b0 = 32 (l >> 4) + (l & 15) and b0 + 16 of the word)
+        uint32_t u0, u1, m0, m1;
+        warp_bs_totals<kDU>(cu, u0, u1);
+        warp_bs_totals<kDM>(cm, m0, m1);
+        const int b0 = 32 * (lane >> 4) + (lane & 15);
+        atomicAdd((unsigned long long *)&sm.B[bm * 64 + b0], (unsigned long long)u0);
+        atomicAdd((unsigned long long *)&sm.B[bm * 64 + b0 + 16], (unsigned long long)u1);
+        atomicAdd((unsigned long long *)&sm.M[bm * 64 + b0], (unsigned long long)m0);
+        atomicAdd((unsigned long long *)&sm.M[bm * 64 + b0 + 16], (unsigned long long)m1);
     }
 }
 
