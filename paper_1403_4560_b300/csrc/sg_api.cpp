@@ -527,6 +527,7 @@ MscArgs make_msc_args(sg_ensemble *e)
     a.n_therm = e->opt.n_therm;
     a.s_key0 = e->opt.sample_base;
     a.status = e->status;
+    for (int r = 0; r < 10; ++r) a.k0r[r] = (a.seed_lo ^ 0x4D455452u) + (uint32_t)r * 0x9E3779B9u;
     return a;
 }
 

@@ -60,6 +60,15 @@ __host__ __device__ constexpr int msc_dp(int L)
     return L * L < 32 ? 5 : L * L < 64 ? 6 : L * L < 128 ? 7 : L * L < 256 ? 8 : 9;
 }
 constexpr int kDG = 5;  // bit planes of a 2D marginal entry (<= L <= 16 sites)
+// Row stride, in 8-byte words, of the marginal array [3][L][L*kDG]. Padded
+// (the measurement kernel) by one word where L * kDG words would put every
+// row at the same bank offset (L = 8, 16): at L = 16 the marginal stores
+// then take 2 wavefronts per warp instead of 16 and the projection loads 2
+// instead of 3.6 on average.
+__host__ __device__ constexpr int msc_marg_row(int L, bool pad)
+{
+    return L * kDG + ((pad && L % 8 == 0) ? 1 : 0);
+}
 
 
 
@@ -123,7 +132,7 @@ struct MscSmem {
     uint32_t *thr;      // [2][16]  +-J thresholds of the unit's slots (sb*8 + u)
     long long *B, *M;   // [4][64]  per-sample energies of the unit's chains
     uint64_t *swap;     // [2]      exchange masks per replica
-    uint64_t *marg;     // [ms][3][L*L][kDG] bit-sliced 2D marginal counts of q = -1
+    uint64_t *marg;     // [ms][3][L][row] bit-sliced 2D marginal counts of q = -1 (msc_marg_row)
     uint64_t *proj;     // [ms][9][L][msc_dp(L)] bit-sliced projection counts of q = -1
 };
 
@@ -275,8 +284,8 @@ __device__ __forceinline__ void msc_half(const MscSmem &sm, const MscArgs &a, in
     constexpr int NB = (NG + 31) / 32;
     const int lane = threadIdx.x & 31;
     for (int blk = tid >> 5; blk < NB; blk += tpc >> 5) {
-        const u32x4 rnd = philox10(a.seed_lo ^ kTagMet, (uint32_t)(g + a.s_key0 / 64),
-                                   (uint32_t)(32 * blk + lane), n_sweep, c2, a.seed_hi);
+        const u32x4 rnd = philox10_rk(a.k0r, (uint32_t)(g + a.s_key0 / 64),
+                                      (uint32_t)(32 * blk + lane), n_sweep, c2, a.seed_hi);
 #pragma unroll
         for (int step = 0; step < 4; ++step) {
             const int src = 8 * step + (lane >> 2);
@@ -351,6 +360,7 @@ __device__ __forceinline__ void msc_measure(const MscSmem &sm, const MscArgs &a,
 {
     constexpr int N = L * L * L;
     constexpr int LL = L * L;
+    constexpr int ROW = msc_marg_row(L, QW);
     // the unit's slots k0 .. k0 + nk - 1 (temperatures t0 ..) in one pass: one
     // barrier per phase for all of them, and more independent tasks per phase.
     // The wide instance unrolls the serial loops of (B) and (C) so their
@@ -362,7 +372,7 @@ __device__ __forceinline__ void msc_measure(const MscSmem &sm, const MscArgs &a,
         const int kk = id / (3 * LL), pid = id - kk * (3 * LL);
         const uint64_t *w0 = sm.w + (size_t)((QW ? 1 : 2) * (k0 + kk)) * N;
         const uint64_t *w1 = w0 + N;
-        uint64_t *margk = sm.marg + (size_t)kk * 3 * LL * kDG;
+        uint64_t *margk = sm.marg + (size_t)kk * 3 * L * ROW;
         const int plane = pid / LL, ab = pid % LL;
         const int A = ab % L, Bc = ab / L;  // consecutive lanes: consecutive A
         int base, step;
@@ -390,7 +400,7 @@ __device__ __forceinline__ void msc_measure(const MscSmem &sm, const MscArgs &a,
         uint64_t cnt[kDG];
         count16(qs, cnt);
 #pragma unroll
-        for (int p = 0; p < kDG; ++p) margk[((size_t)plane * LL + A * L + Bc) * kDG + p] = cnt[p];
+        for (int p = 0; p < kDG; ++p) margk[((size_t)plane * L + A) * ROW + Bc * kDG + p] = cnt[p];
     }
     __syncthreads();
     // (with QW the projections may take the overlap words' space: the
@@ -417,7 +427,7 @@ __device__ __forceinline__ void msc_measure(const MscSmem &sm, const MscArgs &a,
             for (int p = 0; p < DP; ++p) acc[p] = 0;
             if (valid) {
                 const int kk = id / (9 * L), pid = id - kk * (9 * L);
-                const uint64_t *margk = sm.marg + (size_t)kk * 3 * LL * kDG;
+                const uint64_t *margk = sm.marg + (size_t)kk * 3 * L * ROW;
                 const int v = pid / L, d = pid % L;
                 const int plane = (v == 0 || v == 1 || v == 3 || v == 4) ? 0 : (v == 2 || v == 5 || v == 6) ? 1 : 2;
 #pragma unroll
@@ -433,7 +443,7 @@ __device__ __forceinline__ void msc_measure(const MscSmem &sm, const MscArgs &a,
                     } else {
                         A = aa; Bc = (aa - d + L) % L;
                     }
-                    const uint64_t *m = margk + ((size_t)plane * LL + A * L + Bc) * kDG;
+                    const uint64_t *m = margk + ((size_t)plane * L + A) * ROW + Bc * kDG;
                     const uint64_t x[kDG] = {m[0], m[1], m[2], m[3], m[4]};
                     bs_add<DP, kDG>(acc, x);
                 }
@@ -450,7 +460,7 @@ __device__ __forceinline__ void msc_measure(const MscSmem &sm, const MscArgs &a,
     } else
     for (int id = threadIdx.x; id < nk * 9 * L; id += blockDim.x) {
         const int kk = id / (9 * L), pid = id - kk * (9 * L);
-        const uint64_t *margk = sm.marg + (size_t)kk * 3 * LL * kDG;
+        const uint64_t *margk = sm.marg + (size_t)kk * 3 * L * ROW;
         const int v = pid / L, d = pid % L;
         const int plane = (v == 0 || v == 1 || v == 3 || v == 4) ? 0 : (v == 2 || v == 5 || v == 6) ? 1 : 2;
         uint64_t acc[DP];
@@ -467,7 +477,7 @@ __device__ __forceinline__ void msc_measure(const MscSmem &sm, const MscArgs &a,
             } else {
                 A = aa; Bc = (aa - d + L) % L;
             }
-            const uint64_t *m = margk + ((size_t)plane * LL + A * L + Bc) * kDG;
+            const uint64_t *m = margk + ((size_t)plane * L + A) * ROW + Bc * kDG;
             const uint64_t x[kDG] = {m[0], m[1], m[2], m[3], m[4]};
             bs_add<DP, kDG>(acc, x);
         };
@@ -852,7 +862,7 @@ __host__ __device__ inline size_t msc_carve_meas(uint8_t *base, int L, MscSmem *
     s.B = reinterpret_cast<long long *>(take(2 * 64 * 8));
     s.M = reinterpret_cast<long long *>(take(2 * 64 * 8));
     // the marginals' space first receives replica 1's chain
-    const size_t marg = (size_t)3 * L * L * kDG * 8;
+    const size_t marg = (size_t)3 * L * msc_marg_row(L, true) * 8;
     s.marg = reinterpret_cast<uint64_t *>(take(marg > N * 8 ? marg : N * 8));
     s.proj = s.w;  // [9][L][msc_dp(L)] after the marginals, in the overlap words' space
     if (sm) *sm = s;

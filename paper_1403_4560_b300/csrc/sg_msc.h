@@ -30,6 +30,9 @@ struct MscArgs {
     int64_t n_therm;
     int64_t s_key0;             // global index of local sample 0 (multiple of 64)
     int *status;                // device status word (SG_ETIMEOUT if a bulk copy never lands)
+    // round keys of the Metropolis key word k0 = seed_lo ^ tag: k0r[r] = k0 +
+    // r * 0x9E3779B9, fixed per launch, read from the kernel's parameters
+    uint32_t k0r[10];
 };
 
 size_t msc_smem_bytes(int L);
