@@ -596,12 +596,15 @@ __global__ void __launch_bounds__(MAXT, MINB) msc_sweep_kernel(const MscArgs a)
     const bool meas = n >= a.n_therm && (n - a.n_therm) % a.measure_every == 0;
     const int nq = 2 * cnt;
 
-    // load the unit's chains (index q = 2k + r is contiguous in W) and tables
-    const uint64_t *src = a.W + ((size_t)g * a.nt + t0) * 2 * N;
-    for (int k = threadIdx.x; k < nq * N; k += blockDim.x) sm.w[k] = src[k];
-    if (msc_j_shared(L)) {
-        const uint64_t *jsrc = a.Jw + (size_t)g * 3 * N;
-        for (int k = threadIdx.x; k < 3 * N; k += blockDim.x) sm.J[k] = jsrc[k];
+    // the unit's chains (index q = 2k + r is contiguous in W) and, for small
+    // lattices, the word group's couplings by bulk copies (sizes multiples of
+    // 16 bytes for even L) while the threads set up the tables
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar);
+        mbar_expect_tx(&bar, (uint32_t)((nq + (msc_j_shared(L) ? 3 : 0)) * N * 8));
+        bulk_load(sm.w, a.W + ((size_t)g * a.nt + t0) * 2 * N, (uint32_t)(nq * N * 8), &bar);
+        if (msc_j_shared(L)) bulk_load(sm.J, a.Jw + (size_t)g * 3 * N, (uint32_t)(3 * N * 8), &bar);
     }
     for (int k = threadIdx.x; k < cnt * 16; k += blockDim.x) sm.thr[k] = a.thr[t0 * 16 + k];
     for (int k = threadIdx.x; k < 4 * 64; k += blockDim.x) {
@@ -609,6 +612,11 @@ __global__ void __launch_bounds__(MAXT, MINB) msc_sweep_kernel(const MscArgs a)
         sm.M[k] = 0;
     }
     __syncthreads();
+    if (__syncthreads_or(!mbar_wait(&bar, 0, kBulkWaitCycles))) {
+        if (threadIdx.x == 0) atomicCAS(a.status, 0, (int)SG_ETIMEOUT);
+        mbar_wait(&bar, 0, kBulkWaitCycles);  // the copies still in flight, bounded again
+        return;
+    }
 
     const int tpc = blockDim.x / nq;  // threads per chain
     const int q = threadIdx.x / tpc;
@@ -1210,10 +1218,14 @@ cudaError_t msc_measure_launch_t(const MscArgs &a, cudaStream_t st)
 template <int L>
 cudaError_t msc_launch_t(const MscArgs &a, int threads, cudaStream_t st)
 {
+    // the largest carve of the instance (the kernel's mbarrier takes a few
+    // bytes of static shared memory beside it)
     static cudaError_t attr_n = cudaFuncSetAttribute(
-        msc_sweep_kernel<L, kMscNarrow, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMscMaxSmem);
+        msc_sweep_kernel<L, kMscNarrow, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        (int)msc_carve(nullptr, L, nullptr, msc_measured_slots(L, false)));
     static cudaError_t attr_w = cudaFuncSetAttribute(
-        msc_sweep_kernel<L, kMscThreads, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMscMaxSmem);
+        msc_sweep_kernel<L, kMscThreads, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        (int)msc_carve(nullptr, L, nullptr, msc_measured_slots(L, true)));
     if (attr_n != cudaSuccess) return attr_n;
     if (attr_w != cudaSuccess) return attr_w;
     const size_t smem = msc_carve(nullptr, L, nullptr, msc_measured_slots(L, threads != kMscNarrow));
