@@ -645,7 +645,8 @@ __device__ __forceinline__ void half_sweep_packed(const Smem &sm, const Ctx &cx,
 // exchange.
 // Work: a warp task is 32 work items (4 consecutive colour sites each) of
 // one word w, so that the lanes' per-chain energy counts (bit-sliced, per
-// item) reduce by warp transposes; the host sizes the CTA to the number of
+// item) reduce over the warp (the +-J sweep's by a butterfly of bit-sliced
+// adds, the Gaussian sweep's M by transposes); the host sizes the CTA to the number of
 // tasks (at most 8 warps), so small lattices run more, smaller CTAs per SM.
 // (Splitting a word's chains over several warps, which then combine their
 // flips with shared-memory atomics, measured slower on B300: L = 10, 24

@@ -40,7 +40,7 @@ __host__ __device__ constexpr int msc_planes(int x) { return x < 2 ? 1 : 1 + msc
 // Bit planes of a thread's unsatisfied-bond counter (at most 6 per site) and
 // (-1)-spin counter (a colour-1 site and its colour-0 x-partner: at most 2
 // per site): as few as the counts can reach, since every plane costs each
-// site's ripple add and each half-sweep's warp transposes.
+// site's ripple add and each half-sweep's warp reduction.
 __host__ __device__ constexpr int msc_du(int L, int tpc_min)
 {
     return msc_planes(6 * msc_sites_per_thread(L, tpc_min));
