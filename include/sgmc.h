@@ -418,7 +418,7 @@ sg_status sg_get_info(const sg_ensemble *e, sg_info *out);
  * wave would give some SMs one CTA more than others (then k >= 3 CTAs on
  * every SM), each sample's sweeps are split into segments that the CTAs
  * claim in order (sg_options.segments). MSC64 runs one launch per sweep;
- * at L >= 14 (library CTA size) each exchange unit runs as two CTAs, one per
+ * at L >= 12 (library CTA size) each exchange unit runs as two CTAs, one per
  * replica (twice the grid), and every measured sweep adds one launch of the
  * overlap measurement (one CTA per slot and word group).
  *   grid      CTAs of each sweep launch (may be NULL)

@@ -1503,7 +1503,7 @@ sg_status sg_autotune(sg_ensemble *e, int64_t trial_sweeps, sg_tune_report *rep)
         const sg_options orig = e->opt;
         const int64_t done0 = e->sweeps_done;
         double best = 1e300, def = 0.0;
-        // candidates: the library choice (0: at L >= 14 split by replica, the
+        // candidates: the library choice (0: at L >= 12 split by replica, the
         // measured sweeps by the measurement kernel), then fused CTAs of 128,
         // 256 and 512 threads
         int best_t = 0, nc = 0;

@@ -697,7 +697,7 @@ __global__ void __launch_bounds__(MAXT, MINB) msc_sweep_kernel(const MscArgs a)
 }
 
 // ---------------------------------------------------------------------------
-// Sweeps of large lattices (L >= 14): the exchange unit split by replica. A
+// Sweeps of large lattices (L >= 12): the exchange unit split by replica. A
 // CTA holds one replica's chains of the unit (the sweep and the exchange
 // never mix replicas: methods section, each replica has its own tempering
 // ladder), so at L = 16 it needs 64 KB of shared memory instead of 197 KB and
@@ -708,10 +708,14 @@ __global__ void __launch_bounds__(MAXT, MINB) msc_sweep_kernel(const MscArgs a)
 // 2 x 32 temperatures, attempts/ns, fused -> split: thermalising L = 14
 // 2436 -> 2886, L = 16 2969 -> 3117 when first built; with the consecutive-
 // site lanes L = 16 3641 split, measuring every sweep 2338 fused -> 2665
-// split plus the measurement kernel. At L = 12 the fused 256-thread CTA stays
-// ahead: measuring 2234 against 1975 split, thermalising 3137 against 2714.
-// The replica pair run as a cluster, each CTA measuring one slot through the
-// peer's shared memory, measured slower than both.)
+// split plus the measurement kernel. At L = 12 the fused 256-thread CTA was
+// ahead then (measuring 2234 against 1975 split); with the bulk copies,
+// smaller energy counters and padded marginals the split path leads there
+// too, measuring 2613 against 2541 fused, thermalising 3664 against 3626,
+// while at L = 10 the fused narrow CTAs stay ahead (2 x 56 T, 8192 samples:
+// measuring 2510 fused against 2272 split). The replica pair run as a
+// cluster, each CTA measuring one slot through the peer's shared memory,
+// measured slower than both.)
 // ---------------------------------------------------------------------------
 constexpr int kMscSplitThreads = 256;
 
@@ -840,7 +844,7 @@ __global__ void __launch_bounds__(kMscSplitThreads, 3) msc_split_sweep_kernel(co
 }
 
 // ---------------------------------------------------------------------------
-// Overlap measurement after a split sweep (L >= 14): one CTA per (slot t,
+// Overlap measurement after a split sweep (L >= 12): one CTA per (slot t,
 // word group g) reads the slot's two replica chains as stored by
 // msc_split_sweep_kernel (after the sweep and the exchange), keeps their
 // overlap words q = w(r=0) ^ w(r=1) in shared memory, and runs the three
@@ -1270,7 +1274,7 @@ int msc_threads(int L, int requested)
     return L <= 10 ? 128 : L == 12 ? 256 : kMscThreads;
 }
 
-bool msc_split(int L, int requested) { return requested <= 0 && L >= 14 && msc_supported_L(L); }
+bool msc_split(int L, int requested) { return requested <= 0 && L >= 12 && msc_supported_L(L); }
 
 cudaError_t msc_measure_split(const MscArgs &a, int L, cudaStream_t st)
 {

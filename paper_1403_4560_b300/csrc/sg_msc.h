@@ -40,7 +40,7 @@ bool msc_supported_L(int L);
 // Threads per CTA of the sweep kernel: `requested` (0 = library choice for
 // L) clamped to [128, 512] and rounded down to a multiple of 128.
 int msc_threads(int L, int requested);
-// Whether sweeps run split by replica (L >= 14 and no requested CTA size):
+// Whether sweeps run split by replica (L >= 12 and no requested CTA size):
 // msc_split_sweep_kernel, one replica's chains of an exchange unit per CTA
 // (256 threads), which does not measure, followed for a measured sweep by
 // msc_measure_split; else the fused msc_sweep_kernel with `threads` threads.

@@ -187,10 +187,10 @@ def test_msc_autotune_changes_speed_not_results():
         assert a.sweeps_done == b.sweeps_done == 25
 
 
-@pytest.mark.parametrize("L,nt,ee,me,S", [(14, 5, 1, 1, 128), (14, 6, 2, 3, 64), (16, 4, 1, 1, 64),
-                                          (16, 3, 0, 2, 128)])
+@pytest.mark.parametrize("L,nt,ee,me,S", [(12, 5, 1, 1, 128), (14, 5, 1, 1, 128), (14, 6, 2, 3, 64),
+                                          (16, 4, 1, 1, 64), (16, 3, 0, 2, 128)])
 def test_replica_split_sweep_equals_fused_kernel_and_oracle(L, nt, ee, me, S):
-    """At L >= 14 the sweeps run split by replica (one replica's chains of an
+    """At L >= 12 the sweeps run split by replica (one replica's chains of an
     exchange unit per CTA), and each measured sweep is measured by a kernel
     of its own (one CTA per slot and word group, from the stored chains). A
     run of a thermalising then a measuring call must equal the fused kernel
