@@ -239,11 +239,14 @@ __device__ __forceinline__ int ustar_of(const uint32_t *thr_sb, uint32_t r)
     return c;
 }
 
-// Site index and neighbour offsets of the colour-c site with
-// colour-compressed index jj.
+// Site index and periodic neighbour indices of the colour-c site with
+// colour-compressed index jj. For L a power of two the coordinates are bit
+// fields of the index, and a neighbour is the index with one field stepped
+// modulo L (an add and a masked merge); else boundary tests pick the
+// wrap-around offsets.
 template <int L>
 struct MscSite {
-    int i, x, dxp, dxm, dyp, dym, dzp, dzm;
+    int i, x, ixp, ixm, iyp, iym, izp, izm;
     __device__ __forceinline__ MscSite(int jj, int c)
     {
         constexpr int H = L / 2;
@@ -253,12 +256,22 @@ struct MscSite {
         const int z = row / L;
         x = 2 * x2 + ((c + y + z) & 1);
         i = x + L * row;
-        dxp = (x == L - 1) ? -(L - 1) : 1;
-        dxm = (x == 0) ? (L - 1) : -1;
-        dyp = (y == L - 1) ? -(L - 1) * L : L;
-        dym = (y == 0) ? (L - 1) * L : -L;
-        dzp = (z == L - 1) ? -(L - 1) * L * L : L * L;
-        dzm = (z == 0) ? (L - 1) * L * L : -L * L;
+        if constexpr ((L & (L - 1)) == 0) {
+            constexpr int MX = L - 1, MY = (L - 1) * L, MZ = (L - 1) * L * L;
+            ixp = (i & ~MX) | ((i + 1) & MX);
+            ixm = (i & ~MX) | ((i - 1) & MX);
+            iyp = (i & ~MY) | ((i + L) & MY);
+            iym = (i & ~MY) | ((i - L) & MY);
+            izp = (i & ~MZ) | ((i + L * L) & MZ);
+            izm = (i & ~MZ) | ((i - L * L) & MZ);
+        } else {
+            ixp = i + ((x == L - 1) ? -(L - 1) : 1);
+            ixm = i + ((x == 0) ? (L - 1) : -1);
+            iyp = i + ((y == L - 1) ? -(L - 1) * L : L);
+            iym = i + ((y == 0) ? (L - 1) * L : -L);
+            izp = i + ((z == L - 1) ? -(L - 1) * L * L : L * L);
+            izm = i + ((z == 0) ? (L - 1) * L * L : -L * L);
+        }
     }
 };
 
@@ -267,16 +280,21 @@ struct MscSite {
 // Thread team: the threads with (threadIdx.x / tpc) == q, tpc threads per
 // chain. For c == 1 the team also accumulates the per-sample unsatisfied-bond
 // and (-1)-spin counts of the post-sweep configuration into sm.B / sm.M
-// (raw counts; converted to B and M afterwards).
+// (raw counts; converted to B and M afterwards). CT >= 0 fixes the colour
+// at compile time (the split sweep: each colour its own code path, colour 0
+// without the energy bookkeeping and its branches; B300, L = 16, +3 %);
+// CT = -1 takes it from c_rt (the fused kernel, whose narrow instance ran
+// 7 % slower at L = 10 with a code path per colour).
 // ---------------------------------------------------------------------------
 // w: the chain's words; thr: its slot's 16 thresholds; bm: its row of
 // sm.B / sm.M.
 // TPC_MIN: a lower bound on tpc, which sizes the energy counters.
-template <int L, int TPC_MIN>
+template <int L, int TPC_MIN, int CT>
 __device__ __forceinline__ void msc_half(const MscSmem &sm, const MscArgs &a, int g, uint64_t *w,
-                                         const uint32_t *thr, int bm, int t, int r, int tpc, int c,
-                                         uint32_t n_sweep)
+                                         const uint32_t *thr, int bm, int t, int r, int tpc,
+                                         int c_rt, uint32_t n_sweep)
 {
+    const int c = CT >= 0 ? CT : c_rt;
     constexpr int N = L * L * L;
     constexpr int NG = (N / 2) / 4;  // Philox groups of four colour-c sites
     constexpr int kDU = msc_du(L, TPC_MIN), kDM = msc_dm(L, TPC_MIN);
@@ -320,22 +338,23 @@ __device__ __forceinline__ void msc_half(const MscSmem &sm, const MscArgs &a, in
             const uint32_t w2 = __shfl_sync(0xFFFFFFFFu, rnd.v[2], src);
             const uint32_t w3 = __shfl_sync(0xFFFFFFFFu, rnd.v[3], src);
             const int jj = 128 * blk + 32 * step + lane;
-            if (jj >= N / 2) continue;
+            if constexpr ((N / 2) % 128 != 0)  // a colour of whole blocks has no tail
+                if (jj >= N / 2) continue;
             const int k = lane & 3;  // the site's place in its group = its word
             const uint32_t rr = k == 0 ? w0 : k == 1 ? w1 : k == 2 ? w2 : w3;
             const MscSite<L> st(jj, c);
             const int i = st.i;
             const uint64_t s = w[i];
-            const uint64_t n0 = w[i + st.dxp], n1 = w[i + st.dxm];
-            const uint64_t n2 = w[i + st.dyp], n3 = w[i + st.dym];
-            const uint64_t n4 = w[i + st.dzp], n5 = w[i + st.dzm];
+            const uint64_t n0 = w[st.ixp], n1 = w[st.ixm];
+            const uint64_t n2 = w[st.iyp], n3 = w[st.iym];
+            const uint64_t n4 = w[st.izp], n5 = w[st.izm];
             // unsatisfied bonds: s ^ s_nb ^ jbit
             const uint64_t d0 = s ^ n0 ^ ldJ<L>(J + i);
-            const uint64_t d1 = s ^ n1 ^ ldJ<L>(J + i + st.dxm);
+            const uint64_t d1 = s ^ n1 ^ ldJ<L>(J + st.ixm);
             const uint64_t d2 = s ^ n2 ^ ldJ<L>(J + N + i);
-            const uint64_t d3 = s ^ n3 ^ ldJ<L>(J + N + i + st.dym);
+            const uint64_t d3 = s ^ n3 ^ ldJ<L>(J + N + st.iym);
             const uint64_t d4 = s ^ n4 ^ ldJ<L>(J + 2 * N + i);
-            const uint64_t d5 = s ^ n5 ^ ldJ<L>(J + 2 * N + i + st.dzm);
+            const uint64_t d5 = s ^ n5 ^ ldJ<L>(J + 2 * N + st.izm);
             // 3-bit count u of the six: two full adders and a carry merge
             const uint64_t sa = d0 ^ d1 ^ d2, ca = (d0 & d1) | (d2 & (d0 ^ d1));
             const uint64_t sb = d3 ^ d4 ^ d5, cb = (d3 & d4) | (d5 & (d3 ^ d4));
@@ -681,8 +700,8 @@ __global__ void __launch_bounds__(MAXT, MINB) msc_sweep_kernel(const MscArgs a)
     for (int c = 0; c < 2; ++c) {
         if (q < nq)
             // (at least 128 threads for at most four chains)
-            msc_half<L, 32>(sm, a, g, sm.w + (size_t)q * N, sm.thr + (q >> 1) * 16, q, t0 + (q >> 1),
-                        q & 1, tpc, c, (uint32_t)n);
+            msc_half<L, 32, -1>(sm, a, g, sm.w + (size_t)q * N, sm.thr + (q >> 1) * 16, q,
+                                t0 + (q >> 1), q & 1, tpc, c, (uint32_t)n);
         __syncthreads();
     }
     // raw counts -> B = 3N - 2 * (unsatisfied bonds), M = N - 2 * (#-1 spins)
@@ -838,13 +857,14 @@ __global__ void __launch_bounds__(kMscSplitThreads, 3) msc_split_sweep_kernel(co
 
     const int tpc = blockDim.x / cnt;  // threads per chain: whole warps
     const int k = threadIdx.x / tpc;
-    for (int c = 0; c < 2; ++c) {
-        if (k < cnt)
-            msc_half<L, kMscSplitThreads / 2>(sm, a, g, sm.w + (size_t)k * N, sm.thr + k * 16, k,
-                                              t0 + k, r, tpc, c,
-                        (uint32_t)n);
-        __syncthreads();
-    }
+    if (k < cnt)
+        msc_half<L, kMscSplitThreads / 2, 0>(sm, a, g, sm.w + (size_t)k * N, sm.thr + k * 16, k,
+                                             t0 + k, r, tpc, 0, (uint32_t)n);
+    __syncthreads();
+    if (k < cnt)
+        msc_half<L, kMscSplitThreads / 2, 1>(sm, a, g, sm.w + (size_t)k * N, sm.thr + k * 16, k,
+                                             t0 + k, r, tpc, 1, (uint32_t)n);
+    __syncthreads();
     // raw counts -> B = 3N - 2 * (unsatisfied bonds), M = N - 2 * (#-1 spins)
     for (int q = threadIdx.x; q < cnt * 64; q += blockDim.x) {
         sm.B[q] = 3LL * N - 2 * sm.B[q];
