@@ -572,8 +572,10 @@ __device__ __forceinline__ void msc_measure(const MscSmem &sm, const MscArgs &a,
     // plane p of P_v[d0 + j] for the G = 32 / DP phases of a group, and one
     // bit transpose hands lane b the G counts of sample 32*half + b, packed
     // DP bits each; the lane then runs the FP32 DFT over d in ascending
-    // order and the FP64 accumulation. The v = 0 tasks also produce Q, and
-    // E and M are added straight from the per-sample energies.
+    // order and the FP64 accumulation. The v = 0 tasks also produce Q and its
+    // moments, and the v = 8 tasks (the other round of the task loop, other
+    // warps) add E and M straight from the per-sample energies, so no warp
+    // carries both extra parts.
     {
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
         constexpr int G = 32 / DP;
@@ -590,7 +592,10 @@ __device__ __forceinline__ void msc_measure(const MscSmem &sm, const MscArgs &a,
             double q[9];
             if (v == 0) {
 #pragma unroll
-                for (int k2 = 0; k2 < 9; ++k2) q[k2] = ac[64 * k2];
+                for (int k2 = 0; k2 < 5; ++k2) q[k2] = ac[64 * k2];
+            } else if (v == 8) {
+#pragma unroll
+                for (int k2 = 5; k2 < 9; ++k2) q[k2] = ac[64 * k2];
             }
             float re = 0.0f, im = 0.0f;
             int Qi = 0;
@@ -630,6 +635,9 @@ __device__ __forceinline__ void msc_measure(const MscSmem &sm, const MscArgs &a,
                 q[2] = __dadd_rn(q[2], Q2);
                 q[3] = __dadd_rn(q[3], __dmul_rn(Q2, Q));
                 q[4] = __dadd_rn(q[4], __dmul_rn(Q2, Q2));
+#pragma unroll
+                for (int k2 = 0; k2 < 5; ++k2) ac[64 * k2] = q[k2];
+            } else if (v == 8) {
                 for (int r = 0; r < 2; ++r) {
                     const long long Bv = sm.B[(2 * k + r) * 64 + b];
                     const long long Mv = sm.M[(2 * k + r) * 64 + b];
@@ -643,7 +651,7 @@ __device__ __forceinline__ void msc_measure(const MscSmem &sm, const MscArgs &a,
                     q[8] = __dadd_rn(q[8], __dmul_rn(m, m));
                 }
 #pragma unroll
-                for (int k2 = 0; k2 < 9; ++k2) ac[64 * k2] = q[k2];
+                for (int k2 = 5; k2 < 9; ++k2) ac[64 * k2] = q[k2];
             }
         }
     }
