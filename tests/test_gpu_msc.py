@@ -97,6 +97,38 @@ def test_msc_full_size_sampled_parity():
         np.testing.assert_array_equal(acc[s:s + 1], st.acc)
 
 
+def _paper_ladder():
+    """The 56 temperatures of the paper's geometry as bench.py draws them."""
+    return np.ascontiguousarray((1.0 / (0.1 * 18.0 ** (np.arange(56) / 55.0)))[::-1])
+
+
+@pytest.mark.parametrize("L,S,ladder", [(16, 4096, "bench"), (10, 8192, "paper")])
+def test_msc_bench_form_graph_replays_full_size_sampled_parity(L, S, ladder):
+    """The multispin-coded ensembles as bench.py times them: a library-drawn
+    instance, h = 0.1, exchange and measurement every sweep, sweeps through a
+    replayed CUDA graph (device sweep counter; at L = 16 split sweeps whose
+    measurement kernels decide on the device which sweeps they measure, at
+    L = 10 the fused narrow kernel). Sampled samples, from each end of the
+    word groups and the middle, against the oracle from its own generators."""
+    h, seed, reps = 0.1, 5, 2
+    T = inputs.geometric_ladder(0.4, 1.5, 32) if ladder == "bench" else _paper_ladder()
+    with sgmc.Ensemble(L, h, T, "pmj", S, seed, n_therm=0, **MSC) as e:
+        for _ in range(reps):
+            sgmc.sweep_batch([e], 4, use_graph=True)
+        e.synchronize()
+        assert e.sweeps_done == 4 * reps
+        spins, (B, M), acc = e.spins(), e.energies(), e.accumulators()
+    for s in (0, 65, S // 2 + 31, S - 1):
+        J = orc.pmj_couplings(seed, 1, L, s_base=s)
+        s0 = orc.init_spins(seed, 1, len(T), L, s_base=s)
+        st = oracle_state(L, T, h, seed, J, s0, s_base=s)
+        st.run(4 * reps)
+        np.testing.assert_array_equal(spins[s:s + 1], st.spins)
+        np.testing.assert_array_equal(B[s:s + 1], st.B)
+        np.testing.assert_array_equal(M[s:s + 1], st.M)
+        np.testing.assert_array_equal(acc[s:s + 1], st.acc)
+
+
 def test_msc_standalone_exchange_and_measure():
     L, S, nt = 4, 64, 5
     T = inputs.geometric_ladder(0.3, 3.0, nt)
