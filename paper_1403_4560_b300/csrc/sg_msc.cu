@@ -86,6 +86,51 @@ __device__ __forceinline__ void bs_ripple(uint64_t (&c)[D], uint64_t carry)
     }
 }
 
+// ---- exact FP64 values of the accumulation from integer operations --------
+// B300 issues FP64 at a few lanes per cycle, and the accumulation phase of
+// the measurement is partly bound by it. The conversions and products below
+// are exact in FP64 (24-bit significands and their squares, integers below
+// 2^53), so their results are unique: assembled from bit fields they equal
+// the FP64 instructions' results bit for bit, and only the rounded sums and
+// products stay on the FP64 pipe. Branch-free, with selects for zero.
+
+// (double)f for f zero or normal. The DFT sums of the measurement are: their
+// terms are integer multiples of FP32 twiddles, so every nonzero sum is a
+// multiple of the smallest twiddle's ulp (far above 2^-126) and below 2^13.
+__device__ __forceinline__ double f64_of_f32(float f)
+{
+    const uint32_t u = __float_as_uint(f);
+    const uint64_t bits = ((uint64_t)(u & 0x80000000u) << 32) |
+                          ((uint64_t)(((u >> 23) & 0xFFu) + 896u) << 52) |
+                          ((uint64_t)(u & 0x7FFFFFu) << 29);
+    return __longlong_as_double(
+        (long long)((u & 0x7FFFFFFFu) ? bits : ((uint64_t)(u & 0x80000000u) << 32)));
+}
+
+// (double)f * (double)f for f zero or normal: the 48-bit square of the 24-bit
+// significand, its leading bit moved to bit 52.
+__device__ __forceinline__ double f64_sq_of_f32(float f)
+{
+    const uint32_t u = __float_as_uint(f);
+    const int e = (int)((u >> 23) & 0xFFu);
+    const uint64_t m = (uint64_t)((u & 0x7FFFFFu) | 0x800000u);
+    const uint64_t p = m * m;  // in [2^46, 2^48)
+    const uint32_t top = (uint32_t)(p >> 47);
+    const uint64_t frac = (p << (6 - top)) & ((1ull << 52) - 1);
+    const uint64_t ex = (uint64_t)(2 * e - 300 + 46 + (int)top + 1023);
+    return __longlong_as_double((long long)((u & 0x7FFFFFFFu) ? ((ex << 52) | frac) : 0ull));
+}
+
+// (double)v for |v| < 2^53.
+__device__ __forceinline__ double f64_of_i64(long long v)
+{
+    const uint64_t a = (uint64_t)(v < 0 ? -v : v);
+    const int pos = 63 - __clzll((long long)(a | 1ull));  // leading bit (0 for a = 0, 1)
+    const uint64_t bits = (v < 0 ? (1ull << 63) : 0ull) | ((uint64_t)(pos + 1023) << 52) |
+                          ((a << (52 - pos)) & ((1ull << 52) - 1));
+    return __longlong_as_double((long long)(a ? bits : 0ull));
+}
+
 // Carry-save adder: three words in, their bitwise sum as (sum, carry).
 __device__ __forceinline__ void csa(uint64_t &h, uint64_t &l, uint64_t a, uint64_t b, uint64_t c)
 {
@@ -621,34 +666,35 @@ __device__ __forceinline__ void msc_measure(const MscSmem &sm, const MscArgs &a,
             } else {
                 for (int d0 = 0; d0 < L; d0 += G) add_group(d0);
             }
-            const double dr = (double)re, di = (double)im;
-            acv[0] = __dadd_rn(o0, dr);
-            acv[64] = __dadd_rn(o1, di);
-            acv[128] = __dadd_rn(o2, __dadd_rn(__dmul_rn(dr, dr), __dmul_rn(di, di)));
+            // (the exact conversions and squares from integer operations)
+            acv[0] = __dadd_rn(o0, f64_of_f32(re));
+            acv[64] = __dadd_rn(o1, f64_of_f32(im));
+            acv[128] = __dadd_rn(o2, __dadd_rn(f64_sq_of_f32(re), f64_sq_of_f32(im)));
             if (v == 0) {
                 if (a.hist)  // P(q): replicas agree on (N + Q) / 2 sites
                     atomicAdd(a.hist + ((size_t)t * a.n_bins + bin) * (N + 1) + ((N + Qi) >> 1), 1ull);
-                const double Q = (double)Qi;
-                const double Q2 = __dmul_rn(Q, Q);
+                // |Q| <= N <= 4096: Q^2, Q^3 = Q^2 Q and Q^4 = Q^2 Q^2 are
+                // integers below 2^53, as exact as their FP64 products
+                const long long Q1 = Qi, Q2 = Q1 * Q1;
                 q[0] = __dadd_rn(q[0], 1.0);
-                q[1] = __dadd_rn(q[1], Q);
-                q[2] = __dadd_rn(q[2], Q2);
-                q[3] = __dadd_rn(q[3], __dmul_rn(Q2, Q));
-                q[4] = __dadd_rn(q[4], __dmul_rn(Q2, Q2));
+                q[1] = __dadd_rn(q[1], f64_of_i64(Q1));
+                q[2] = __dadd_rn(q[2], f64_of_i64(Q2));
+                q[3] = __dadd_rn(q[3], f64_of_i64(Q2 * Q1));
+                q[4] = __dadd_rn(q[4], f64_of_i64(Q2 * Q2));
 #pragma unroll
                 for (int k2 = 0; k2 < 5; ++k2) ac[64 * k2] = q[k2];
             } else if (v == 8) {
                 for (int r = 0; r < 2; ++r) {
                     const long long Bv = sm.B[(2 * k + r) * 64 + b];
                     const long long Mv = sm.M[(2 * k + r) * 64 + b];
-                    const double e = -__dadd_rn((double)Bv, __dmul_rn(a.h_d, (double)Mv));
+                    const double e = -__dadd_rn(f64_of_i64(Bv), __dmul_rn(a.h_d, f64_of_i64(Mv)));
                     q[5] = __dadd_rn(q[5], e);
                     q[6] = __dadd_rn(q[6], __dmul_rn(e, e));
                 }
                 for (int r = 0; r < 2; ++r) {
-                    const double m = (double)sm.M[(2 * k + r) * 64 + b];
-                    q[7] = __dadd_rn(q[7], m);
-                    q[8] = __dadd_rn(q[8], __dmul_rn(m, m));
+                    const long long Mv = sm.M[(2 * k + r) * 64 + b];  // |M| <= N: M^2 exact
+                    q[7] = __dadd_rn(q[7], f64_of_i64(Mv));
+                    q[8] = __dadd_rn(q[8], f64_of_i64(Mv * Mv));
                 }
 #pragma unroll
                 for (int k2 = 5; k2 < 9; ++k2) ac[64 * k2] = q[k2];
