@@ -405,6 +405,51 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsign
     }
 }
 
+// ---- exact FP64 values of the accumulation from integer operations --------
+// B300 issues FP64 at a few lanes per cycle, and the accumulation phase of
+// the overlap measurement is partly bound by it. The conversions and products below
+// are exact in FP64 (24-bit significands and their squares, integers below
+// 2^53), so their results are unique: assembled from bit fields they equal
+// the FP64 instructions' results bit for bit, and only the rounded sums and
+// products stay on the FP64 pipe. Branch-free, with selects for zero.
+
+// (double)f for f zero or normal. The DFT sums of the measurement are: their
+// terms are integer multiples of FP32 twiddles, so every nonzero sum is a
+// multiple of the smallest twiddle's ulp (far above 2^-126), and |sum| <= L^3.
+__device__ __forceinline__ double f64_of_f32(float f)
+{
+    const uint32_t u = __float_as_uint(f);
+    const uint64_t bits = ((uint64_t)(u & 0x80000000u) << 32) |
+                          ((uint64_t)(((u >> 23) & 0xFFu) + 896u) << 52) |
+                          ((uint64_t)(u & 0x7FFFFFu) << 29);
+    return __longlong_as_double(
+        (long long)((u & 0x7FFFFFFFu) ? bits : ((uint64_t)(u & 0x80000000u) << 32)));
+}
+
+// (double)f * (double)f for f zero or normal: the 48-bit square of the 24-bit
+// significand, its leading bit moved to bit 52.
+__device__ __forceinline__ double f64_sq_of_f32(float f)
+{
+    const uint32_t u = __float_as_uint(f);
+    const int e = (int)((u >> 23) & 0xFFu);
+    const uint64_t m = (uint64_t)((u & 0x7FFFFFu) | 0x800000u);
+    const uint64_t p = m * m;  // in [2^46, 2^48)
+    const uint32_t top = (uint32_t)(p >> 47);
+    const uint64_t frac = (p << (6 - top)) & ((1ull << 52) - 1);
+    const uint64_t ex = (uint64_t)(2 * e - 300 + 46 + (int)top + 1023);
+    return __longlong_as_double((long long)((u & 0x7FFFFFFFu) ? ((ex << 52) | frac) : 0ull));
+}
+
+// (double)v for |v| < 2^53.
+__device__ __forceinline__ double f64_of_i64(long long v)
+{
+    const uint64_t a = (uint64_t)(v < 0 ? -v : v);
+    const int pos = 63 - __clzll((long long)(a | 1ull));  // leading bit (0 for a = 0, 1)
+    const uint64_t bits = (v < 0 ? (1ull << 63) : 0ull) | ((uint64_t)(pos + 1023) << 52) |
+                          ((a << (52 - pos)) & ((1ull << 52) - 1));
+    return __longlong_as_double((long long)(a ? bits : 0ull));
+}
+
 // Bound of a bulk-copy wait: 2^30 cycles, about half a second at 2 GHz, far
 // beyond the microseconds a copy of a CTA's state takes.
 constexpr unsigned long long kBulkWaitCycles = 1ull << 30;

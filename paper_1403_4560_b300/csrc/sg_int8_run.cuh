@@ -1329,10 +1329,10 @@ __device__ __forceinline__ void measure_projections(const Smem &sm, const Ctx &c
                         im = __fmaf_rn(Pf, sm.twid[L + d], im);
                     }
                     if (!live) continue;
-                    const double dr = (double)re, di = (double)im;
-                    old[0] = __dadd_rn(old[0], dr);
-                    old[1] = __dadd_rn(old[1], di);
-                    old[2] = __dadd_rn(old[2], __dadd_rn(__dmul_rn(dr, dr), __dmul_rn(di, di)));
+                    // (the exact conversions and squares from integer operations)
+                    old[0] = __dadd_rn(old[0], f64_of_f32(re));
+                    old[1] = __dadd_rn(old[1], f64_of_f32(im));
+                    old[2] = __dadd_rn(old[2], __dadd_rn(f64_sq_of_f32(re), f64_sq_of_f32(im)));
 #pragma unroll
                     for (int q = 0; q < 3; ++q) acv[q * nt] = old[q];
                     if (v == 0) {
