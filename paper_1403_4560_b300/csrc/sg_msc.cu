@@ -805,6 +805,18 @@ __global__ void __launch_bounds__(MAXT, MINB) msc_sweep_kernel(const MscArgs a)
 // ---------------------------------------------------------------------------
 constexpr int kMscSplitThreads = 256;
 
+// Whether sweep n walks the word groups from the last: the opposite of
+// sweep n - 1 when that one was not measured (in the thermalisation by the
+// parity of n), forward after a measured sweep, whose measurement ended on
+// the first groups. The order changes no result, only which chains are
+// still in L2 when they are read.
+__device__ __forceinline__ bool msc_groups_reversed(const MscArgs &a, int64_t n)
+{
+    if (n - 1 < a.n_therm) return (n & 1) != 0;
+    const int64_t m = a.n_therm + a.measure_every * ((n - 1 - a.n_therm) / a.measure_every);
+    return ((n - m) & 1) == 0;  // n = m + 1 forward, then alternating
+}
+
 __host__ __device__ inline size_t msc_carve_split(uint8_t *base, int L, MscSmem *sm)
 {
     const size_t N = (size_t)L * L * L;
@@ -833,8 +845,13 @@ __global__ void __launch_bounds__(kMscSplitThreads, 3) msc_split_sweep_kernel(co
     extern __shared__ __align__(16) uint8_t msc_smem[];
     MscSmem sm;
     msc_carve_split(msc_smem, L, &sm);
-    const int g = blockIdx.y, r = blockIdx.z;
+    // word groups outermost (both replicas of a group's units together), so
+    // the chains written last are whole groups, which the next reader takes
+    // first: the measurement walks the groups in reverse, and a sweep after an
+    // unmeasured one walks them opposite to it
     const int64_t n = (a.sweep0_dev ? *a.sweep0_dev : a.sweep0) + a.sweep_offset;
+    const int r = blockIdx.y;
+    const int g = msc_groups_reversed(a, n) ? (int)(a.G - 1) - (int)blockIdx.z : (int)blockIdx.z;
     const bool xchg = a.exchange_every > 0 && (n + 1) % a.exchange_every == 0;
     const int par = xchg ? (int)(((n + 1) / a.exchange_every - 1) & 1) : 0;
     int t0, cnt;
@@ -976,7 +993,10 @@ __global__ void __launch_bounds__(kMscMeasThreads, 3) msc_measure_kernel(const M
     extern __shared__ __align__(16) uint8_t msc_smem[];
     MscSmem sm;
     msc_carve_meas(msc_smem, L, &sm);
-    const int t = blockIdx.x, g = blockIdx.y;
+    // the word groups in reverse of the sweep's order: the chains stored
+    // last by the sweep, still in L2, are read first, and the next sweep
+    // starts on the groups read last
+    const int t = blockIdx.x, g = (int)(a.G - 1) - (int)blockIdx.y;
     const int64_t n = (a.sweep0_dev ? *a.sweep0_dev : a.sweep0) + a.sweep_offset;
     if (!(n >= a.n_therm && (n - a.n_therm) % a.measure_every == 0)) return;
     const int bin = log_bin(n, a.n_bins);
@@ -1284,7 +1304,7 @@ cudaError_t msc_split_launch_t(const MscArgs &a, cudaStream_t st)
         static cudaError_t attr_s = cudaFuncSetAttribute(
             msc_split_sweep_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (attr_s != cudaSuccess) return attr_s;
-        const dim3 grid((unsigned)(a.nt / 2 + 1), (unsigned)a.G, 2u);
+        const dim3 grid((unsigned)(a.nt / 2 + 1), 2u, (unsigned)a.G);
         msc_split_sweep_kernel<L><<<grid, kMscSplitThreads, smem, st>>>(a);
         return cudaGetLastError();
     }
