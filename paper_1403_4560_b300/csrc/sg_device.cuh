@@ -1,6 +1,8 @@
 // sg_device.cuh -- device-side building blocks of the EA spin-glass engine:
 // the counter-based random number generator, the FP32 exponential used for
-// continuous acceptance probabilities, and the 32-bit threshold map.
+// continuous acceptance probabilities, the 32-bit threshold map, packed FP32
+// pairs, bit-sliced counters and their warp reductions, untiled TMA bulk
+// copies on an mbarrier, and exact FP64 values assembled from bit fields.
 //
 // Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random
 // numbers: as easy as 1, 2, 3", SC'11). The paper drew its numbers from a
