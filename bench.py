@@ -48,7 +48,7 @@ WORKLOAD = ("gaussian EA 3D, L=8 and 12 x h=0.1,0.2,0.3, 512 samples each, "
 # workload (L = 12, 512 samples, 256 sweeps), from the one-pass ncu capture
 # summarised under profiles/. Must be reset to
 # None whenever the kernel changes, until it is captured again.
-TRAFFIC_BYTES_PER_LAUNCH = 61.5e6
+TRAFFIC_BYTES_PER_LAUNCH = 65.9e6
 # Thread instructions per attempt of the same kernel in the same launch shape
 # (ncu smsp__thread_inst_executed.sum over the launch's attempts, captured on
 # the bench's own 512-sample, 256-sweep segmented launch;

@@ -910,7 +910,12 @@ static int int8_segments(const sg_ensemble *e, int n_sweeps, int *grid)
             const int64_t waves = (e->S + e->launch.grid - 1) / e->launch.grid;
             if ((double)e->S / ((double)waves * e->launch.grid) > 0.97) return 1;
         }
-        const int64_t by_balance = (8 * (int64_t)*grid + e->S - 1) / e->S;
+        // at least 16 units per CTA slot: the last units end at different
+        // times, and shorter units shorten that tail (B300, Gaussian L = 12,
+        // 512 samples on 296 CTAs, 256-sweep launches, attempts/ns by
+        // segments: 5 376.5, 6 382.0, 8 386.0, 11 385.6, 16 385.3; each
+        // segment adds one reload of the sample's state)
+        const int64_t by_balance = (16 * (int64_t)*grid + e->S - 1) / e->S;
         const int64_t by_length = (n_sweeps + 63) / 64;
         want = std::max(by_balance, by_length);
         want = std::min<int64_t>(want, std::max(1, n_sweeps / 16));
